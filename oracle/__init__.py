@@ -1,0 +1,190 @@
+"""CPU oracle of the PL Morse-Smale segmentation (ctypes driver over
+``ms_oracle.c``).
+
+TEST INFRASTRUCTURE: only the test suite, the smoke check and the CPU
+baseline leg of ``bench.py`` may import this package.  It shares no code with
+the CUDA library, and the CUDA library never calls it.
+
+The C file states which passage of the paper each function follows; this
+driver only converts numpy arrays and builds the shared object with gcc.
+Fields are numpy arrays of shape (nz, ny, nx) (x fastest) in float32,
+float16 or float64; ``dims`` is always (nx, ny, nz).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ms_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_OUT_DIR, "libmsoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_DT = {np.dtype(np.float32): 0, np.dtype(np.float16): 1, np.dtype(np.float64): 2}
+_ERR = {1: "NaN in the input field", 2: "invalid argument", 3: "out of memory",
+        4: "pointer cycle (not a forest)"}
+
+i32p = ctypes.POINTER(ctypes.c_int32)
+i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    """Compile ms_oracle.c with gcc (plain C11, -O2, no arch flags)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.ms_oracle_neighbors.argtypes = [i64p, ctypes.c_int64, i64p]
+            L.ms_oracle_neighbors.restype = ctypes.c_int
+            L.ms_oracle_steepest.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i32p, i32p]
+            L.ms_oracle_steepest.restype = ctypes.c_int
+            L.ms_oracle_follow.argtypes = [i32p, ctypes.c_int64, i32p]
+            L.ms_oracle_follow.restype = ctypes.c_int
+            L.ms_oracle_follow_brute.argtypes = [i32p, ctypes.c_int64, i32p]
+            L.ms_oracle_follow_brute.restype = ctypes.c_int
+            L.ms_oracle_walk.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, ctypes.c_int64,
+                                         ctypes.c_int, ctypes.c_int64, i64p]
+            L.ms_oracle_walk.restype = ctypes.c_int64
+            L.ms_oracle_steepest_at.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i64p,
+                                                ctypes.c_int64, i32p, i32p]
+            L.ms_oracle_steepest_at.restype = ctypes.c_int
+            L.ms_oracle_ms_rank.argtypes = [i32p, i32p, ctypes.c_int64, i32p]
+            L.ms_oracle_ms_rank.restype = ctypes.c_int64
+            L.ms_oracle_segment.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i32p, i32p, i32p,
+                                            i64p, i32p, i32p]
+            L.ms_oracle_segment.restype = ctypes.c_int
+            L.ms_oracle_link_stats.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i32p, i64p]
+            L.ms_oracle_link_stats.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _dims_of(field: np.ndarray):
+    if field.ndim == 2:
+        ny, nx = field.shape
+        return (nx, ny, 1)
+    if field.ndim != 3:
+        raise ValueError("field must be (ny, nx) or (nz, ny, nx)")
+    nz, ny, nx = field.shape
+    return (nx, ny, nz)
+
+
+def _prep(field: np.ndarray):
+    f = np.ascontiguousarray(field)
+    if f.dtype not in _DT:
+        raise TypeError(f"unsupported dtype {f.dtype}")
+    dims = (ctypes.c_int64 * 3)(*_dims_of(f))
+    return f, _DT[f.dtype], dims
+
+
+def _ptr32(a):
+    return a.ctypes.data_as(i32p)
+
+
+def _check(st):
+    if st != 0:
+        raise ValueError(_ERR.get(st, f"oracle error {st}"))
+
+
+def neighbors(dims, v: int):
+    out = (ctypes.c_int64 * 14)()
+    d = (ctypes.c_int64 * 3)(*dims)
+    c = lib().ms_oracle_neighbors(d, int(v), out)
+    if c < 0:
+        raise ValueError("bad vertex")
+    return sorted(out[i] for i in range(c))
+
+
+def steepest(field: np.ndarray):
+    """(up, dn) int32 arrays of length N: the highest / lowest vertex of
+    N(v) u {v} under the (value, index) order."""
+    f, dt, dims = _prep(field)
+    n = f.size
+    up = np.empty(n, np.int32)
+    dn = np.empty(n, np.int32)
+    _check(lib().ms_oracle_steepest(f.ctypes.data, dt, dims, _ptr32(up), _ptr32(dn)))
+    return up, dn
+
+
+def steepest_at(field: np.ndarray, vertices):
+    f, dt, dims = _prep(field)
+    vs = np.ascontiguousarray(np.asarray(vertices, dtype=np.int64))
+    up = np.empty(vs.size, np.int32)
+    dn = np.empty(vs.size, np.int32)
+    _check(lib().ms_oracle_steepest_at(f.ctypes.data, dt, dims, vs.ctypes.data_as(i64p), vs.size,
+                                       _ptr32(up), _ptr32(dn)))
+    return up, dn
+
+
+def follow(ptr: np.ndarray, brute: bool = False) -> np.ndarray:
+    p = np.ascontiguousarray(ptr, dtype=np.int32)
+    out = np.empty_like(p)
+    fn = lib().ms_oracle_follow_brute if brute else lib().ms_oracle_follow
+    _check(fn(_ptr32(p), p.size, _ptr32(out)))
+    return out
+
+
+def ms_rank(asc: np.ndarray, desc: np.ndarray):
+    a = np.ascontiguousarray(asc, dtype=np.int32)
+    d = np.ascontiguousarray(desc, dtype=np.int32)
+    ms = np.empty_like(a)
+    k = lib().ms_oracle_ms_rank(_ptr32(a), _ptr32(d), a.size, _ptr32(ms))
+    if k < 0:
+        raise MemoryError("oracle ms_rank")
+    return ms, int(k)
+
+
+def walk(field: np.ndarray, v: int, direction: int, max_steps: int = 1 << 40):
+    """Extremum reached from v (direction > 0: maximum, < 0: minimum) and
+    the number of steps, by walking straight from the field."""
+    f, dt, dims = _prep(field)
+    steps = ctypes.c_int64(0)
+    r = lib().ms_oracle_walk(f.ctypes.data, dt, dims, int(v), int(direction), int(max_steps),
+                             ctypes.byref(steps))
+    if r < 0:
+        raise ValueError("walk exceeded max_steps")
+    return int(r), int(steps.value)
+
+
+def segment(field: np.ndarray):
+    """The full segmentation: dict with asc (minimum reached), desc (maximum
+    reached), ms (dense pair rank), K, up and dn."""
+    f, dt, dims = _prep(field)
+    n = f.size
+    asc = np.empty(n, np.int32)
+    desc = np.empty(n, np.int32)
+    ms = np.empty(n, np.int32)
+    up = np.empty(n, np.int32)
+    dn = np.empty(n, np.int32)
+    k = ctypes.c_int64(0)
+    _check(lib().ms_oracle_segment(f.ctypes.data, dt, dims, _ptr32(asc), _ptr32(desc), _ptr32(ms),
+                                   ctypes.byref(k), _ptr32(up), _ptr32(dn)))
+    return {"asc": asc, "desc": desc, "ms": ms, "K": int(k.value), "up": up, "dn": dn}
+
+
+def link_stats(field: np.ndarray, with_links: bool = False):
+    """Per vertex: chi(Lk-), chi(Lk+), #components(Lk-), #components(Lk+),
+    interior flag -- as an (N, 5) int32 array; optionally the link vertex
+    sets as an (N, 14) int64 array padded with -1."""
+    f, dt, dims = _prep(field)
+    n = f.size
+    out = np.empty((n, 5), np.int32)
+    links = np.empty((n, 14), np.int64) if with_links else None
+    _check(lib().ms_oracle_link_stats(f.ctypes.data, dt, dims, _ptr32(out),
+                                      links.ctypes.data_as(i64p) if with_links else None))
+    return (out, links) if with_links else out

@@ -1,0 +1,463 @@
+/*
+ * Plain, single-threaded CPU oracle of the vertex-based piecewise-linear
+ * Morse-Smale (MS) segmentation of a scalar field on a regular grid.
+ *
+ * TEST INFRASTRUCTURE.  This file exists to check the CUDA path; it is not
+ * part of the product.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may build, load or call it.  It shares no
+ * code, header, table or helper with the CUDA library.
+ *
+ * Every function follows a definition of the paper written out directly,
+ * with no blocking, fusion or reordering:
+ *
+ *   order       Sec. 3.1 + Sec. 4.1: vertices are totally ordered by
+ *               (f value, vertex index); ties in f go to the index, the
+ *               smaller index being lower.  Values are compared as real
+ *               numbers (float32/float16 inputs are widened exactly to
+ *               double), so -0.0 and +0.0 tie and are split by the index.
+ *   neighbours  Sec. 4.2: N(v) = the vertices joined to v by an edge of the
+ *               triangulation.  The triangulation of the grid is the
+ *               Freudenthal (Kuhn) one whose 2D form is drawn in Fig. 1:
+ *               each cell is cut into simplices along its (0,..,0)->(1,..,1)
+ *               diagonal, so u and v share an edge iff u - v is a non-zero
+ *               vector with all components in {0, 1} or all in {0, -1}.
+ *   steepest    Sec. 3.3 + Sec. 4.2: up(v) is the highest vertex of
+ *               N(v) u {v}, dn(v) the lowest; up(v) == v iff v is a
+ *               maximum, dn(v) == v iff v is a minimum.
+ *   extremities Sec. 3.3 + Sec. 3.4: the forward integral line of v follows
+ *               up until it stops at a maximum M (the "descending"
+ *               segmentation label, Sec. 4.2), the backward one follows dn to
+ *               a minimum m (the "ascending" label).  Computed by walking
+ *               the line and memoising every vertex on it.  The label is the
+ *               extremum's linear vertex index.
+ *   MS id       Sec. 3.4 + Sec. 4.2.2: v1 ~ v2 iff (m, M) agree; the id of a
+ *               vertex is the 0-based rank of its (m, M) pair among all
+ *               distinct pairs that occur, sorted with m first.
+ *   links       Sec. 3.2: lower/upper link of a vertex, their Euler
+ *               characteristic and number of connected components
+ *               (Banchoff's classification), from an explicit enumeration of
+ *               the simplices of the triangulation.
+ *
+ * Vertex numbering: v = x + nx*(y + ny*z), x fastest (Fig. 1 numbers the
+ * nodes of its grid along x first).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { OR_F32 = 0, OR_F16 = 1, OR_F64 = 2 };
+enum { OR_OK = 0, OR_ERR_NAN = 1, OR_ERR_ARG = 2, OR_ERR_NOMEM = 3, OR_ERR_CYCLE = 4 };
+
+typedef struct {
+  const void *data;
+  int dtype;
+  int64_t nx, ny, nz, n;
+} field_t;
+
+/* IEEE 754 binary16 -> double, written from the format's definition:
+ * sign, 5-bit biased exponent (bias 15), 10-bit fraction; subnormals have
+ * an implicit leading 0 and exponent -14. */
+static double half_to_double(uint16_t h) {
+  int s = (h >> 15) & 1, e = (h >> 10) & 31, m = h & 1023;
+  double v;
+  if (e == 0)
+    v = ldexp((double)m, -24);
+  else if (e == 31)
+    v = m ? NAN : INFINITY;
+  else
+    v = ldexp((double)(m + 1024), e - 25);
+  return s ? -v : v;
+}
+
+static double value_at(const field_t *F, int64_t v) {
+  switch (F->dtype) {
+    case OR_F32: return (double)((const float *)F->data)[v];
+    case OR_F16: return half_to_double(((const uint16_t *)F->data)[v]);
+    default: return ((const double *)F->data)[v];
+  }
+}
+
+/* u is lower than w in the total order of Sec. 4.1. */
+static int lower(const field_t *F, int64_t u, int64_t w) {
+  double a = value_at(F, u), b = value_at(F, w);
+  if (a < b) return 1;
+  if (a > b) return 0;
+  return u < w;
+}
+
+static int make_field(field_t *F, const void *data, int dtype, const int64_t dims[3]) {
+  if (!data || !dims || dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return OR_ERR_ARG;
+  if (dtype != OR_F32 && dtype != OR_F16 && dtype != OR_F64) return OR_ERR_ARG;
+  F->data = data;
+  F->dtype = dtype;
+  F->nx = dims[0];
+  F->ny = dims[1];
+  F->nz = dims[2];
+  F->n = dims[0] * dims[1] * dims[2];
+  return OR_OK;
+}
+
+/* N(v): every grid vertex u != v with u - v in {0,1}^3 or v - u in {0,1}^3,
+ * inside the box.  Returns the count (at most 14) and writes the indices in
+ * increasing offset-loop order. */
+static int neighbours_of(const field_t *F, int64_t v, int64_t *out) {
+  int64_t x = v % F->nx, y = (v / F->nx) % F->ny, z = v / (F->nx * F->ny);
+  int c = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!dx && !dy && !dz) continue;
+        int nonneg = dx >= 0 && dy >= 0 && dz >= 0;
+        int nonpos = dx <= 0 && dy <= 0 && dz <= 0;
+        if (!nonneg && !nonpos) continue;
+        int64_t X = x + dx, Y = y + dy, Z = z + dz;
+        if (X < 0 || Y < 0 || Z < 0 || X >= F->nx || Y >= F->ny || Z >= F->nz) continue;
+        out[c++] = X + F->nx * (Y + F->ny * Z);
+      }
+  return c;
+}
+
+int ms_oracle_neighbors(const int64_t dims[3], int64_t v, int64_t *out) {
+  field_t F;
+  static const float dummy = 0.f;
+  if (make_field(&F, &dummy, OR_F32, dims) != OR_OK || v < 0 || v >= F.n) return -1;
+  return neighbours_of(&F, v, out);
+}
+
+/* Highest (dir > 0) or lowest (dir < 0) vertex of N(v) u {v}. */
+static int64_t steepest_at(const field_t *F, int64_t v, int dir) {
+  int64_t nb[14];
+  int c = neighbours_of(F, v, nb);
+  int64_t best = v;
+  for (int i = 0; i < c; ++i) {
+    if (dir > 0) {
+      if (lower(F, best, nb[i])) best = nb[i];
+    } else {
+      if (lower(F, nb[i], best)) best = nb[i];
+    }
+  }
+  return best;
+}
+
+static int has_nan(const field_t *F) {
+  for (int64_t v = 0; v < F->n; ++v)
+    if (isnan(value_at(F, v))) return 1;
+  return 0;
+}
+
+int ms_oracle_steepest(const void *field, int dtype, const int64_t dims[3], int32_t *up,
+                       int32_t *dn) {
+  field_t F;
+  int st = make_field(&F, field, dtype, dims);
+  if (st) return st;
+  if (has_nan(&F)) return OR_ERR_NAN;
+  for (int64_t v = 0; v < F.n; ++v) {
+    up[v] = (int32_t)steepest_at(&F, v, +1);
+    dn[v] = (int32_t)steepest_at(&F, v, -1);
+  }
+  return OR_OK;
+}
+
+/* Follow the line v -> ptr(v) -> ... to its fixed point, for every v,
+ * memoising each vertex of a walked line so that each vertex is visited
+ * once.  Fails (instead of looping) if a walk is longer than n steps. */
+int ms_oracle_follow(const int32_t *ptr, int64_t n, int32_t *out) {
+  int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  if (!stack) return OR_ERR_NOMEM;
+  for (int64_t v = 0; v < n; ++v) out[v] = -1;
+  for (int64_t v = 0; v < n; ++v) {
+    if (out[v] >= 0) continue;
+    int64_t top = 0, w = v;
+    while (out[w] < 0 && ptr[w] != w) {
+      if (top >= n) {
+        free(stack);
+        return OR_ERR_CYCLE;
+      }
+      stack[top++] = w;
+      w = ptr[w];
+    }
+    int32_t root = out[w] >= 0 ? out[w] : (int32_t)w;
+    out[w] = root;
+    while (top > 0) out[stack[--top]] = root;
+  }
+  free(stack);
+  return OR_OK;
+}
+
+/* The same fixed point, walking every vertex's line independently. */
+int ms_oracle_follow_brute(const int32_t *ptr, int64_t n, int32_t *out) {
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t w = v, steps = 0;
+    while (ptr[w] != w) {
+      w = ptr[w];
+      if (++steps > n) return OR_ERR_CYCLE;
+    }
+    out[v] = (int32_t)w;
+  }
+  return OR_OK;
+}
+
+/* Walk the integral line of one vertex straight from the field: returns the
+ * extremum reached (dir > 0: maximum, dir < 0: minimum) and its number of
+ * steps, or -1 if more than max_steps steps are taken. */
+int64_t ms_oracle_walk(const void *field, int dtype, const int64_t dims[3], int64_t v, int dir,
+                       int64_t max_steps, int64_t *steps_out) {
+  field_t F;
+  if (make_field(&F, field, dtype, dims) || v < 0 || v >= F.n) return -1;
+  int64_t steps = 0, w = v;
+  for (;;) {
+    int64_t s = steepest_at(&F, w, dir);
+    if (s == w) break;
+    w = s;
+    if (++steps > max_steps) return -1;
+  }
+  if (steps_out) *steps_out = steps;
+  return w;
+}
+
+/* up(v) and dn(v) of single vertices, evaluated straight from the field. */
+int ms_oracle_steepest_at(const void *field, int dtype, const int64_t dims[3], const int64_t *vs,
+                          int64_t count, int32_t *up, int32_t *dn) {
+  field_t F;
+  int st = make_field(&F, field, dtype, dims);
+  if (st) return st;
+  for (int64_t i = 0; i < count; ++i) {
+    if (vs[i] < 0 || vs[i] >= F.n) return OR_ERR_ARG;
+    up[i] = (int32_t)steepest_at(&F, vs[i], +1);
+    dn[i] = (int32_t)steepest_at(&F, vs[i], -1);
+  }
+  return OR_OK;
+}
+
+static int cmp_i64(const void *a, const void *b) {
+  int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+  return (x > y) - (x < y);
+}
+
+/* Dense rank of the (m, M) pair of every vertex among the distinct pairs,
+ * lexicographic with m first.  Returns the number of distinct pairs K, or
+ * -1 on allocation failure. */
+int64_t ms_oracle_ms_rank(const int32_t *asc, const int32_t *desc, int64_t n, int32_t *ms) {
+  if (n <= 0) return 0;
+  int64_t *key = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t *uniq = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  if (!key || !uniq) {
+    free(key);
+    free(uniq);
+    return -1;
+  }
+  for (int64_t v = 0; v < n; ++v) {
+    key[v] = (int64_t)asc[v] * n + (int64_t)desc[v];
+    uniq[v] = key[v];
+  }
+  qsort(uniq, (size_t)n, sizeof(int64_t), cmp_i64);
+  int64_t k = 0;
+  for (int64_t i = 0; i < n; ++i)
+    if (i == 0 || uniq[i] != uniq[k - 1]) uniq[k++] = uniq[i];
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t lo = 0, hi = k; /* first index with uniq[i] >= key[v] */
+    while (lo < hi) {
+      int64_t mid = lo + (hi - lo) / 2;
+      if (uniq[mid] < key[v])
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    ms[v] = (int32_t)lo;
+  }
+  free(key);
+  free(uniq);
+  return k;
+}
+
+/* The whole segmentation of one field: up/dn (may be NULL), the ascending
+ * labels (minimum reached), the descending labels (maximum reached), the MS
+ * ids and their count. */
+int ms_oracle_segment(const void *field, int dtype, const int64_t dims[3], int32_t *asc,
+                      int32_t *desc, int32_t *ms, int64_t *k_out, int32_t *up_out,
+                      int32_t *dn_out) {
+  field_t F;
+  int st = make_field(&F, field, dtype, dims);
+  if (st) return st;
+  if (F.n > INT32_MAX) return OR_ERR_ARG;
+  int32_t *up = up_out ? up_out : (int32_t *)malloc(sizeof(int32_t) * (size_t)F.n);
+  int32_t *dn = dn_out ? dn_out : (int32_t *)malloc(sizeof(int32_t) * (size_t)F.n);
+  if (!up || !dn) {
+    if (!up_out) free(up);
+    if (!dn_out) free(dn);
+    return OR_ERR_NOMEM;
+  }
+  st = ms_oracle_steepest(field, dtype, dims, up, dn);
+  if (!st) st = ms_oracle_follow(up, F.n, desc);
+  if (!st) st = ms_oracle_follow(dn, F.n, asc);
+  if (!st) {
+    int64_t k = ms_oracle_ms_rank(asc, desc, F.n, ms);
+    if (k < 0)
+      st = OR_ERR_NOMEM;
+    else if (k_out)
+      *k_out = k;
+  }
+  if (!up_out) free(up);
+  if (!dn_out) free(dn);
+  return st;
+}
+
+/* ---------------------------------------------------------------------
+ * Links (Sec. 3.2).  The triangulation is enumerated explicitly: over the
+ * axes of extent >= 2 (d of them), every grid cell with minimum corner c is
+ * cut into d! simplices, one per ordering (a_1..a_d) of the axes, with
+ * vertices c, c+e_a1, c+e_a1+e_a2, ..., c+e_a1+..+e_ad.  The link of v is
+ * the set of faces, not containing v, of the simplices containing v.
+ * --------------------------------------------------------------------- */
+typedef struct {
+  int64_t v[3];
+  int k; /* number of vertices, 1..3 */
+} lsimp_t;
+
+static int cmp_lsimp(const void *a, const void *b) {
+  const lsimp_t *p = (const lsimp_t *)a, *q = (const lsimp_t *)b;
+  if (p->k != q->k) return p->k - q->k;
+  for (int i = 0; i < p->k; ++i)
+    if (p->v[i] != q->v[i]) return p->v[i] < q->v[i] ? -1 : 1;
+  return 0;
+}
+
+static int64_t uf_find(int64_t *par, int64_t i) {
+  while (par[i] != i) i = par[i];
+  return i;
+}
+
+/* Per vertex, into out[5*v .. 5*v+4]: chi(Lk-), chi(Lk+), number of
+ * connected components of Lk- and of Lk+, and 1 if v is interior to the
+ * box in every axis of extent >= 2.  Also returns, through link_out (may be
+ * NULL, 14 entries per vertex, -1 padded), the vertex set of Lk(v). */
+int ms_oracle_link_stats(const void *field, int dtype, const int64_t dims[3], int32_t *out,
+                         int64_t *link_out) {
+  field_t F;
+  int st = make_field(&F, field, dtype, dims);
+  if (st) return st;
+  if (has_nan(&F)) return OR_ERR_NAN;
+  int64_t ext[3] = {F.nx, F.ny, F.nz};
+  int axes[3], d = 0;
+  for (int a = 0; a < 3; ++a)
+    if (ext[a] >= 2) axes[d++] = a;
+  /* orderings of the active axes */
+  int perms[6][3], np = 0;
+  if (d == 0) {
+    np = 0;
+  } else if (d == 1) {
+    perms[0][0] = 0;
+    np = 1;
+  } else if (d == 2) {
+    perms[0][0] = 0; perms[0][1] = 1;
+    perms[1][0] = 1; perms[1][1] = 0;
+    np = 2;
+  } else {
+    int p[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    memcpy(perms, p, sizeof(p));
+    np = 6;
+  }
+  lsimp_t buf[8 * 6 * 7];
+  for (int64_t v = 0; v < F.n; ++v) {
+    int64_t p[3] = {v % F.nx, (v / F.nx) % F.ny, v / (F.nx * F.ny)};
+    int nb = 0;
+    for (int s = 0; s < (1 << d); ++s) {
+      int64_t c[3] = {p[0], p[1], p[2]};
+      int ok = 1;
+      for (int i = 0; i < d; ++i) {
+        int a = axes[i];
+        if (s & (1 << i)) c[a] -= 1;
+        if (c[a] < 0 || c[a] > ext[a] - 2) ok = 0;
+      }
+      if (!ok) continue;
+      for (int q = 0; q < np; ++q) {
+        /* chain vertices of this simplex */
+        int64_t chain[4][3];
+        memcpy(chain[0], c, sizeof(c));
+        for (int j = 1; j <= d; ++j) {
+          memcpy(chain[j], chain[j - 1], sizeof(c));
+          chain[j][axes[perms[q][j - 1]]] += 1;
+        }
+        int at = -1;
+        for (int j = 0; j <= d; ++j)
+          if (chain[j][0] == p[0] && chain[j][1] == p[1] && chain[j][2] == p[2]) at = j;
+        if (at < 0) continue;
+        int64_t opp[3];
+        int m = 0;
+        for (int j = 0; j <= d; ++j)
+          if (j != at) opp[m++] = chain[j][0] + F.nx * (chain[j][1] + F.ny * chain[j][2]);
+        /* all non-empty faces of the opposite simplex */
+        for (int sub = 1; sub < (1 << m); ++sub) {
+          lsimp_t t;
+          t.k = 0;
+          for (int j = 0; j < m; ++j)
+            if (sub & (1 << j)) t.v[t.k++] = opp[j];
+          for (int i = 1; i < t.k; ++i) /* sort the face's vertices */
+            for (int j = i; j > 0 && t.v[j - 1] > t.v[j]; --j) {
+              int64_t tmp = t.v[j];
+              t.v[j] = t.v[j - 1];
+              t.v[j - 1] = tmp;
+            }
+          for (int j = t.k; j < 3; ++j) t.v[j] = -1;
+          buf[nb++] = t;
+        }
+      }
+    }
+    qsort(buf, (size_t)nb, sizeof(lsimp_t), cmp_lsimp);
+    int nu = 0;
+    for (int i = 0; i < nb; ++i)
+      if (nu == 0 || cmp_lsimp(&buf[i], &buf[nu - 1]) != 0) buf[nu++] = buf[i];
+    /* Euler characteristics and components of the lower and upper links */
+    int chi_lo = 0, chi_up = 0;
+    int64_t lv[14];
+    int nlv = 0;
+    for (int i = 0; i < nu; ++i) {
+      int all_lo = 1, all_up = 1;
+      for (int j = 0; j < buf[i].k; ++j) {
+        if (!lower(&F, buf[i].v[j], v)) all_lo = 0;
+        if (!lower(&F, v, buf[i].v[j])) all_up = 0;
+      }
+      int sign = (buf[i].k % 2 == 1) ? 1 : -1;
+      if (all_lo) chi_lo += sign;
+      if (all_up) chi_up += sign;
+      if (buf[i].k == 1 && nlv < 14) lv[nlv++] = buf[i].v[0];
+    }
+    int comps[2] = {0, 0};
+    for (int side = 0; side < 2; ++side) {
+      int64_t par[14];
+      int in[14];
+      for (int i = 0; i < nlv; ++i) {
+        par[i] = i;
+        in[i] = side == 0 ? lower(&F, lv[i], v) : lower(&F, v, lv[i]);
+      }
+      for (int i = 0; i < nu; ++i) {
+        if (buf[i].k != 2) continue;
+        int a = -1, b = -1;
+        for (int j = 0; j < nlv; ++j) {
+          if (lv[j] == buf[i].v[0]) a = j;
+          if (lv[j] == buf[i].v[1]) b = j;
+        }
+        if (a < 0 || b < 0 || !in[a] || !in[b]) continue;
+        int64_t ra = uf_find(par, a), rb = uf_find(par, b);
+        if (ra != rb) par[ra] = rb;
+      }
+      for (int i = 0; i < nlv; ++i)
+        if (in[i] && uf_find(par, i) == i) comps[side]++;
+    }
+    int interior = 1;
+    for (int i = 0; i < d; ++i) {
+      int a = axes[i];
+      if (p[a] == 0 || p[a] == ext[a] - 1) interior = 0;
+    }
+    out[5 * v + 0] = chi_lo;
+    out[5 * v + 1] = chi_up;
+    out[5 * v + 2] = comps[0];
+    out[5 * v + 3] = comps[1];
+    out[5 * v + 4] = interior;
+    if (link_out) {
+      for (int i = 0; i < 14; ++i) link_out[14 * v + i] = i < nlv ? lv[i] : -1;
+    }
+  }
+  return OR_OK;
+}
