@@ -1,0 +1,385 @@
+#!/usr/bin/env python3
+"""Throughput of the PL Morse-Smale segmentation on one GB300 (or N
+replicas, one per GPU).
+
+One step = one full segmentation (order keys, steepest neighbours, path
+compression, MS ids) of the workload's field through the C ABI
+(``ms_segment``), inputs and outputs resident in HBM.  The default workload
+is a 512^3 float32 field of seeded white noise blurred by a periodic
+Gaussian (sigma = 4 voxels): the shape of the paper's 512^3 strong-scaling
+dataset with dense extrema.  The field (512 MiB) and the three label arrays
+(1.5 GiB) are each larger than the 129 MB L2, so nothing stays cached
+between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(the plain single-threaded restatement of the paper's definitions) on a
+bounded slab of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthfields as sf  # noqa: E402
+
+METRIC = "MS-segmented vertices/s at 512³ fp32 (% HBM roofline); batched/served p99 latency"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic bytes per vertex of the whole path: read the field once, write
+# three int32 labels.
+PATH_BYTES = {"f32": 16, "f16": 14}
+# Algorithmic bytes per vertex of one launch of each stage's kernel.
+STAGE_BYTES = {
+    "steepest": {"f32": 4 + 8, "f16": 2 + 8},  # field in, up + dn out
+    "compress": {"f32": 16, "f16": 16},        # one round: read + write up and dn
+    "pairs": {"f32": 12, "f16": 12},           # read asc + desc, write ms
+}
+
+WORKLOADS = {
+    "noise512": dict(dims=(512, 512, 512), kind="noise", dtype="f32",
+                     desc="512^3 fp32 white noise, periodic Gaussian sigma=4 (radius 16), seed 0"),
+    "noise512q": dict(dims=(512, 512, 512), kind="noiseq", dtype="f32",
+                      desc="512^3 fp32 sigma=4 smoothed noise quantised to 256 levels, seed 0"),
+    "gauss64": dict(dims=(64, 64, 64), kind="gauss", dtype="f32",
+                    desc="64^3 fp32 sum of 8 Gaussians + 1e-3 noise, seed 0"),
+    "broad1024": dict(dims=(1024, 1024, 1024), kind="broad", dtype="f32",
+                      desc="1024^3 fp32 two sigma=300 Gaussians + linear ramp, seed 0"),
+    "broad32768": dict(dims=(32768, 32768, 1), kind="broad", dtype="f32",
+                       desc="32768^2 fp32 two sigma=300 Gaussians + linear ramp, seed 0"),
+    "noise256": dict(dims=(256, 256, 256), kind="noise", dtype="f32",
+                     desc="256^3 fp32 sigma=4 smoothed noise, seed 0"),
+}
+
+
+def cache_dir():
+    d = os.environ.get("MS_FIELD_CACHE") or os.path.join(tempfile.gettempdir(), "msseg_fields")
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
+def make_field(name, z0=None, z1=None):
+    w = WORKLOADS[name]
+    path = os.path.join(cache_dir(), f"{name}.npy")
+    if os.path.exists(path):
+        f = np.load(path, mmap_mode="r")
+    else:
+        dims = w["dims"]
+        if w["kind"] == "noise":
+            f = sf.smoothed_noise(dims, 0, sigma=4.0, radius=16)
+        elif w["kind"] == "noiseq":
+            f = sf.quantize_levels(sf.smoothed_noise(dims, 0, sigma=4.0, radius=16))
+        elif w["kind"] == "gauss":
+            f = sf.gaussian_sum(dims, 0)
+        else:
+            f = sf.broad_gaussians_ramp(dims, 0)
+        if w["dtype"] == "f16":
+            f = f.astype(np.float16)
+        tmp = path + f".{os.getpid()}.tmp.npy"
+        np.save(tmp, f)
+        os.replace(tmp, path)
+    if z0 is not None:
+        return np.ascontiguousarray(f[z0:z1])
+    return np.ascontiguousarray(f)
+
+
+def source_hash():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2303_15491_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as fh:
+                h.update(fn.encode() + fh.read())
+    return h.hexdigest()
+
+
+def peaks():
+    try:
+        with open(PEAKS_PATH) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms while the
+    timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.out is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.out.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on bounded slabs of the workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    w = WORKLOADS[args.workload]
+    nx, ny, nz = w["dims"]
+    slab = max(1, min(nz, args.ref_slab))
+    times = []
+    verts = nx * ny * slab
+    for step in range(args.warmup + args.steps):
+        z0 = (step * slab) % max(1, nz - slab + 1)
+        f = make_field(args.workload, z0, z0 + slab)
+        t = time.perf_counter()
+        oracle.segment(f)
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = verts * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "vertices/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"],
+                   "sample": f"z-slab {nx}x{ny}x{slab} per step (different slab each step)"},
+        "cpu_baseline": {"value": value, "unit": "vertices/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{nx}x{ny}x{slab} slab of {args.workload} per step"},
+        "e2e": {"value": value, "unit": "vertices/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(args):
+    import oracle
+
+    w = WORKLOADS[args.workload]
+    nx, ny, nz = w["dims"]
+    slab = max(1, min(nz, args.cpu_slab))
+    f = make_field(args.workload, 0, slab)
+    t = time.perf_counter()
+    oracle.segment(f)
+    dt = time.perf_counter() - t
+    return {"value": nx * ny * slab / dt, "unit": "vertices/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {nx}x{ny}x{slab} z-slab of {args.workload} ({nx*ny*slab} vertices, "
+                      f"{dt:.1f} s single-threaded)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="noise512", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-slab", type=int, default=48)
+    ap.add_argument("--ref-slab", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    import paper_2303_15491_gb300 as ms
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    w = WORKLOADS[args.workload]
+    f_np = make_field(args.workload)
+    dims = w["dims"]
+    n = int(np.prod(dims))
+    dtype = ms.MS_F16 if w["dtype"] == "f16" else ms.MS_F32
+    field = torch.from_numpy(f_np).to(dev)
+    asc = torch.empty(n, dtype=torch.int32, device=dev)
+    desc = torch.empty_like(asc)
+    msid = torch.empty_like(asc)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = ms.ms_create(dev, stream)  # the library launches on this stream
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        ms.ms_segment(ctx, field, dims, dtype, asc, desc, msid)
+    k_regions = ms.ms_last_region_count(ctx)
+
+    # ---- device-resident timed region
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ms.ms_profile_enable(ctx, True)
+    with ClockSampler(dev) as clk:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        # events on the stream the library's kernels are launched on
+        ev0.record(stream)
+        t_host = time.perf_counter()
+        for _ in range(args.steps):
+            ms.ms_segment(ctx, field, dims, dtype, asc, desc, msid)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_host = time.perf_counter() - t_host
+    prof = ms.ms_profile_read(ctx)
+    ms.ms_profile_enable(ctx, False)
+    barrier()
+    torch.cuda.synchronize()
+    elapsed_ms = max(ev0.elapsed_time(ev1), 1e3 * t_host)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = ws * n * args.steps / (elapsed_ms / 1e3)
+
+    # ---- end to end through ms_segment_host (pinned host memory)
+    h_field = torch.from_numpy(f_np).pin_memory()
+    h_asc = torch.empty(n, dtype=torch.int32).pin_memory()
+    h_desc = torch.empty_like(h_asc).pin_memory()
+    h_ms = torch.empty_like(h_asc).pin_memory()
+    ms.ms_segment_host(ctx, h_field, dims, dtype, h_asc, h_desc, h_ms)  # warm the io buffers
+    barrier()
+    t = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ms.ms_segment_host(ctx, h_field, dims, dtype, h_asc, h_desc, h_ms)
+    e2e_s = time.perf_counter() - t
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = ws * n * args.e2e_steps / e2e_s
+    esz = 2 if w["dtype"] == "f16" else 4
+
+    # ---- roofline of the dominant kernel and of the whole path
+    hbm, peak_kind = peaks()
+    stages = prof["stages"]
+    dom = max(("steepest", "compress", "pairs"), key=lambda s: stages[s]["ms"])
+    launches = max(1, stages[dom]["launches"])
+    per_launch_s = stages[dom]["ms"] / 1e3 / launches
+    alg_bytes = STAGE_BYTES[dom][w["dtype"]] * n
+    achieved = alg_bytes / per_launch_s / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            ent = tj.get(dom)
+            if ent and ent.get("csrc_sha1") == source_hash() and ent.get("workload") == args.workload:
+                traffic = ent["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+    path_gbs = PATH_BYTES[w["dtype"]] * n / (ms_per_step / 1e3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "vertices/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"], "dims": list(dims),
+                   "input_dtype": w["dtype"], "regions_K": k_regions,
+                   "l2": "inputs larger than L2 (field 512 MiB, labels 3 x 512 MiB > 129 MB L2)",
+                   "parallelism": f"replicas x{ws} (no data-path collective)"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic,
+                     "alg_bytes_per_vertex": STAGE_BYTES[dom][w["dtype"]],
+                     "avg_launch_ms": per_launch_s * 1e3},
+        "path_roofline": {"alg_bytes_per_vertex": PATH_BYTES[w["dtype"]], "achieved": path_gbs,
+                          "peak": hbm, "unit": "GB/s", "frac": path_gbs / hbm},
+        "stages_ms_per_step": {k: v["ms"] / max(1, prof["calls"]) for k, v in stages.items()
+                               if v["launches"] or v["ms"]},
+        "gpu_launches": prof["launches"],
+        "e2e": {"value": e2e_value, "unit": "vertices/s", "h2d_bytes_per_step": n * esz,
+                "d2h_bytes_per_step": 3 * n * 4, "api": "ms_segment_host, pinned host buffers"},
+        "clocks": clk.summary(),
+    }
+    ms.ms_destroy(ctx)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,170 @@
+/*
+ * ms.h -- C ABI of the GB300 (sm_103a) piecewise-linear Morse-Smale
+ * segmentation library (libmsseg.so).
+ *
+ * What it computes (paper: "Parallel Computation of Piecewise Linear
+ * Morse-Smale Segmentations", arXiv 2303.15491):
+ *
+ *   Input  (Sec. 3.1): a scalar field f on the vertices of a regular grid of
+ *          nx*ny*nz vertices, linearly interpolated on the grid's implicit
+ *          Freudenthal triangulation (each cell cut along its
+ *          (0,0,0)->(1,1,1) diagonal; in 2D the (x,y)->(x+1,y+1) diagonal
+ *          drawn in Fig. 1).  Vertex (x,y,z) has index v = x + nx*(y + ny*z).
+ *          N(v), the vertices sharing an edge with v, are the grid points at
+ *          offsets +-(1,0,0), +-(0,1,0), +-(0,0,1), +-(1,1,0), +-(1,0,1),
+ *          +-(0,1,1), +-(1,1,1) that lie inside the box (14 in the interior
+ *          of a 3D grid, 6 in 2D).
+ *   Order  (Sec. 4.1): vertices are compared by (f value, index); equal
+ *          values (including -0.0 and +0.0) are ordered by index, the
+ *          smaller index being lower.  NaN values are rejected.
+ *   up/dn  (Sec. 4.2.1): up(v) is the highest vertex of N(v) u {v}, dn(v)
+ *          the lowest; a vertex with up(v) == v is a maximum, dn(v) == v a
+ *          minimum.
+ *   labels (Sec. 3.3, 3.4, 4.2.1): desc(v) is the maximum reached by
+ *          following up from v (path compression until every pointer is at
+ *          its fixed point), asc(v) the minimum reached by following dn.
+ *          Following the paper's naming, the DEScending segmentation holds
+ *          the maxima and the ASCending one the minima (Sec. 4.2, Fig. 1).
+ *          Labels are the extremum's vertex index.
+ *   MS id  (Sec. 3.4, 4.2.2): vertices with the same (asc, desc) pair form
+ *          one MS region; ms(v) is the 0-based rank of v's pair among the K
+ *          distinct pairs that occur, sorted lexicographically with asc
+ *          first.
+ *
+ * Conventions for every entry point:
+ *   - dims = {nx, ny, nz}, each >= 1, N = nx*ny*nz <= 2^31 - 1 (otherwise
+ *     MS_ERR_TOO_LARGE).  A 2D field is nz == 1; the 3D stencil clipped to
+ *     the box is then exactly the 2D one.
+ *   - Pointers named field / out_* / ptr / keys / asc / desc / ms are DEVICE
+ *     pointers (cudaMalloc'd or managed) owned by the caller, unless the
+ *     function name ends in _host.  The library owns only its scratch memory
+ *     and never frees caller memory.  Fields are densely packed, x fastest.
+ *   - Every call is ordered on the context's stream and returns after the
+ *     work has completed, with a status.  On error the outputs are
+ *     unspecified.  A context is not thread-safe: use one per host thread.
+ */
+#ifndef MS_H_
+#define MS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ms_ctx ms_ctx;
+
+typedef enum { MS_F32 = 0, MS_F16 = 1 } ms_dtype;
+
+typedef enum {
+  MS_OK = 0,
+  MS_ERR_INVALID_ARG = 1,       /* null pointer, dims < 1, host pointer where a device one is needed */
+  MS_ERR_UNSUPPORTED_DTYPE = 2, /* dtype not MS_F32 / MS_F16 */
+  MS_ERR_TOO_LARGE = 3,         /* N > 2^31 - 1 or a size beyond a stated maximum */
+  MS_ERR_NAN_INPUT = 4,         /* the field holds a NaN */
+  MS_ERR_OUT_OF_MEMORY = 5,     /* scratch allocation failed */
+  MS_ERR_CUDA = 6,              /* a CUDA runtime call or kernel launch failed */
+  MS_ERR_NOT_CONVERGED = 7,     /* path compression hit its round cap (input is not a forest) */
+  MS_ERR_TIMEOUT = 8,           /* a bounded wait gave up */
+  MS_ERR_BUSY = 9               /* a server slot or budget is not available */
+} ms_status;
+
+/* Human-readable name of a status.  Never NULL; static storage. */
+const char *ms_status_string(ms_status s);
+
+/* Create a context on CUDA device `device`.  cuda_stream is a cudaStream_t
+ * to run on (borrowed, not destroyed by ms_destroy), or NULL for a stream
+ * the context creates and owns.  *out is set only on MS_OK. */
+ms_status ms_create(ms_ctx **out, int device, void *cuda_stream);
+
+/* Release the context's stream (if owned) and scratch memory.  NULL is a
+ * no-op. */
+ms_status ms_destroy(ms_ctx *ctx);
+
+/* Full segmentation (Sec. 4.2): order keys, steepest neighbours, path
+ * compression, MS ids.  field: N values of `dtype`; out_asc, out_desc,
+ * out_ms: int32[N] each (distinct, non-overlapping, 4-byte aligned).
+ * Errors: MS_ERR_INVALID_ARG, MS_ERR_UNSUPPORTED_DTYPE, MS_ERR_TOO_LARGE,
+ * MS_ERR_NAN_INPUT, MS_ERR_OUT_OF_MEMORY, MS_ERR_CUDA, MS_ERR_NOT_CONVERGED. */
+ms_status ms_segment(ms_ctx *ctx, const void *field, const int64_t dims[3], ms_dtype dtype,
+                     int32_t *out_asc, int32_t *out_desc, int32_t *out_ms);
+
+/* The same segmentation from and to HOST memory: copies the field to the
+ * device, segments it and copies the three label arrays back, all on the
+ * context's stream (pinned host buffers make the copies asynchronous DMA;
+ * pageable ones also work).  Device buffers are the context's scratch. */
+ms_status ms_segment_host(ms_ctx *ctx, const void *host_field, const int64_t dims[3],
+                          ms_dtype dtype, int32_t *host_asc, int32_t *host_desc,
+                          int32_t *host_ms);
+
+/* K, the number of MS regions found by the last successful ms_segment /
+ * ms_segment_host / ms_pair_rank on this context (0 before any). */
+ms_status ms_last_region_count(const ms_ctx *ctx, int64_t *k);
+
+/* ---- the four steps of the path, callable one at a time ----------------- */
+
+/* Step 1 (Sec. 4.1 order field, without the sort): keys[v] is a uint32 such
+ * that (keys[u], u) < (keys[w], w) exactly when u is lower than w in the
+ * (value, index) order: IEEE bits with -0.0 mapped to +0.0, the sign bit
+ * flipped for positives and all bits flipped for negatives (fp16 values are
+ * widened exactly to fp32 first).  n = number of values.  MS_ERR_NAN_INPUT
+ * if any value is NaN (keys then unspecified). */
+ms_status ms_order_keys(ms_ctx *ctx, const void *field, int64_t n, ms_dtype dtype,
+                        uint32_t *keys);
+
+/* Step 2 (Sec. 4.2.1 first step): up[v] / dn[v] = index of the highest /
+ * lowest vertex of N(v) u {v}.  up and dn: int32[N], distinct buffers. */
+ms_status ms_steepest(ms_ctx *ctx, const void *field, const int64_t dims[3], ms_dtype dtype,
+                      int32_t *up, int32_t *dn);
+
+/* Step 3 (Sec. 4.2.1 path compression, Fig. 3): replaces ptr[v] by
+ * ptr[ptr[v]] until every entry is a fixed point, in place.  ptr: int32[n]
+ * forming a forest whose roots are self-pointers (as up / dn are).  Entries
+ * outside [0, n) give MS_ERR_INVALID_ARG; a cycle gives
+ * MS_ERR_NOT_CONVERGED after ceil(log2 n) + 2 doubling rounds. */
+ms_status ms_compress(ms_ctx *ctx, int32_t *ptr, int64_t n);
+
+/* Step 4 (Sec. 4.2.2): ms[v] = rank of (asc[v], desc[v]) among the distinct
+ * pairs, lexicographic with asc first; *k_out (may be NULL) = K.  asc, desc
+ * values must lie in [0, n) (else MS_ERR_INVALID_ARG). */
+ms_status ms_pair_rank(ms_ctx *ctx, const int32_t *asc, const int32_t *desc, int64_t n,
+                       int32_t *ms, int64_t *k_out);
+
+
+/* ---- measurement ---------------------------------------------------------- */
+
+/* Stages of one segmentation, as timed by the profiler. */
+typedef enum {
+  MS_STAGE_STEEPEST = 0, /* order keys + steepest neighbours (steps 1-2) */
+  MS_STAGE_COMPRESS = 1, /* path compression (step 3) */
+  MS_STAGE_PAIRS = 2,    /* MS ids: pair set, sort, lookup (step 4) */
+  MS_STAGE_H2D = 3,      /* ms_segment_host: field upload */
+  MS_STAGE_D2H = 4,      /* ms_segment_host: label download */
+  MS_STAGE_COUNT = 5
+} ms_stage;
+
+typedef struct {
+  int64_t calls;                   /* segmentations since the profiler was enabled */
+  int64_t launches;                /* CUDA kernels this library launched in them */
+  int64_t stage_launches[8];       /* kernels per stage */
+  double stage_ms[8];              /* summed device time per stage (CUDA events on the
+                                      context's stream) */
+} ms_profile;
+
+/* Enable (on != 0) or disable the per-stage profiler of a context; enabling
+ * resets its counters.  With the profiler on, each stage of a call is
+ * bracketed by CUDA events on the context's stream and their elapsed times
+ * are summed when the call completes.  Off by default. */
+ms_status ms_profile_enable(ms_ctx *ctx, int on);
+
+/* Copy the profiler's counters (zeros if it was never enabled). */
+ms_status ms_profile_read(const ms_ctx *ctx, ms_profile *out);
+
+/* Name of a stage ("steepest", "compress", ...); "?" if out of range. */
+const char *ms_profile_stage_name(int stage);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MS_H_ */

@@ -1,0 +1,216 @@
+"""Python binding of libmsseg -- the GB300 (sm_103a) piecewise-linear
+Morse-Smale segmentation library declared in ``include/ms.h``.
+
+The functions carry the C names and only marshal arguments: device tensors
+become raw pointers, ``dims`` tuples become ``int64_t[3]``, and a non-OK
+status becomes an ``MSError``.  Every step of the computation runs in the
+library's CUDA kernels; there is no Python or CPU fallback -- if the library
+cannot be built or loaded, importing the binding's functions raises.
+
+PyTorch supplies device memory and streams only.  Fields are torch tensors
+of shape (nz, ny, nx) or (ny, nx), x fastest, dtype float32 or float16, on a
+CUDA device; label outputs are int32 tensors of the same number of elements.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+__all__ = [
+    "MSError", "MS_F32", "MS_F16", "load", "ms_status_string", "ms_create", "ms_destroy",
+    "ms_segment", "ms_segment_host", "ms_last_region_count", "ms_order_keys", "ms_steepest",
+    "ms_compress", "ms_pair_rank", "segment", "EXPORTED_SYMBOLS", "ms_profile_enable",
+    "ms_profile_read", "ms_profile_stage_name", "STAGES",
+]
+
+MS_F32, MS_F16 = 0, 1
+STATUS = ["MS_OK", "MS_ERR_INVALID_ARG", "MS_ERR_UNSUPPORTED_DTYPE", "MS_ERR_TOO_LARGE",
+          "MS_ERR_NAN_INPUT", "MS_ERR_OUT_OF_MEMORY", "MS_ERR_CUDA", "MS_ERR_NOT_CONVERGED",
+          "MS_ERR_TIMEOUT", "MS_ERR_BUSY"]
+
+EXPORTED_SYMBOLS = [
+    "ms_status_string", "ms_create", "ms_destroy", "ms_segment", "ms_segment_host",
+    "ms_last_region_count", "ms_order_keys", "ms_steepest", "ms_compress", "ms_pair_rank",
+    "ms_profile_enable", "ms_profile_read", "ms_profile_stage_name",
+]
+STAGES = ["steepest", "compress", "pairs", "h2d", "d2h"]
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("stage_launches", ctypes.c_int64 * 8), ("stage_ms", ctypes.c_double * 8)]
+
+_lock = threading.Lock()
+_lib = None
+
+c_i64p = ctypes.POINTER(ctypes.c_int64)
+c_vp = ctypes.c_void_p
+
+
+class MSError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = int(status)
+        self.name = STATUS[status] if 0 <= status < len(STATUS) else f"status {status}"
+        super().__init__(f"{where}: {self.name}" if where else self.name)
+
+
+def load(build: bool = True) -> ctypes.CDLL:
+    """Load libmsseg.so from the package's build folder (compiling it first
+    if it is missing or stale and ``build`` is true)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB
+            if not os.path.exists(path):
+                raise OSError(f"libmsseg.so not built at {path}")
+            L = ctypes.CDLL(path)
+            L.ms_status_string.argtypes = [ctypes.c_int]
+            L.ms_status_string.restype = ctypes.c_char_p
+            L.ms_create.argtypes = [ctypes.POINTER(c_vp), ctypes.c_int, c_vp]
+            L.ms_destroy.argtypes = [c_vp]
+            L.ms_segment.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
+            L.ms_segment_host.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
+            L.ms_last_region_count.argtypes = [c_vp, c_i64p]
+            L.ms_order_keys.argtypes = [c_vp, c_vp, ctypes.c_int64, ctypes.c_int, c_vp]
+            L.ms_steepest.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp]
+            L.ms_compress.argtypes = [c_vp, c_vp, ctypes.c_int64]
+            L.ms_pair_rank.argtypes = [c_vp, c_vp, c_vp, ctypes.c_int64, c_vp, c_i64p]
+            L.ms_profile_enable.argtypes = [c_vp, ctypes.c_int]
+            L.ms_profile_read.argtypes = [c_vp, ctypes.POINTER(_Profile)]
+            L.ms_profile_stage_name.argtypes = [ctypes.c_int]
+            L.ms_profile_stage_name.restype = ctypes.c_char_p
+            for name in EXPORTED_SYMBOLS[1:]:
+                if name == "ms_profile_stage_name":
+                    continue
+                getattr(L, name).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise MSError(st, where)
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return 0
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):  # numpy
+        return t.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(t)}")
+
+
+def _dims(dims):
+    d = tuple(int(v) for v in dims)
+    if len(d) != 3:
+        raise ValueError("dims must be (nx, ny, nz)")
+    return (ctypes.c_int64 * 3)(*d)
+
+
+def dims_of(field):
+    """(nx, ny, nz) of a (nz, ny, nx) or (ny, nx) array / tensor."""
+    shp = tuple(field.shape)
+    if len(shp) == 2:
+        return (shp[1], shp[0], 1)
+    if len(shp) == 3:
+        return (shp[2], shp[1], shp[0])
+    raise ValueError("field must be 2D (ny, nx) or 3D (nz, ny, nx)")
+
+
+def dtype_code(field) -> int:
+    name = str(field.dtype)
+    if name.endswith("float32"):
+        return MS_F32
+    if name.endswith("float16"):
+        return MS_F16
+    return 99  # rejected by the library as MS_ERR_UNSUPPORTED_DTYPE
+
+
+def ms_status_string(status: int) -> str:
+    return load().ms_status_string(int(status)).decode()
+
+
+def ms_create(device: int = 0, stream=None) -> int:
+    """Returns the context handle (an int).  ``stream``: a torch.cuda.Stream,
+    a raw cudaStream_t int, or None for a context-owned stream."""
+    h = c_vp()
+    s = getattr(stream, "cuda_stream", stream)
+    _check(load().ms_create(ctypes.byref(h), int(device), s if s else None), "ms_create")
+    return h.value
+
+
+def ms_destroy(ctx: int) -> None:
+    _check(load().ms_destroy(ctx), "ms_destroy")
+
+
+def ms_segment(ctx, field, dims, dtype, out_asc, out_desc, out_ms) -> None:
+    _check(load().ms_segment(ctx, _ptr(field), _dims(dims), int(dtype), _ptr(out_asc),
+                             _ptr(out_desc), _ptr(out_ms)), "ms_segment")
+
+
+def ms_segment_host(ctx, host_field, dims, dtype, host_asc, host_desc, host_ms) -> None:
+    _check(load().ms_segment_host(ctx, _ptr(host_field), _dims(dims), int(dtype), _ptr(host_asc),
+                                  _ptr(host_desc), _ptr(host_ms)), "ms_segment_host")
+
+
+def ms_last_region_count(ctx) -> int:
+    k = ctypes.c_int64(0)
+    _check(load().ms_last_region_count(ctx, ctypes.byref(k)), "ms_last_region_count")
+    return int(k.value)
+
+
+def ms_order_keys(ctx, field, n, dtype, keys) -> None:
+    _check(load().ms_order_keys(ctx, _ptr(field), int(n), int(dtype), _ptr(keys)), "ms_order_keys")
+
+
+def ms_steepest(ctx, field, dims, dtype, up, dn) -> None:
+    _check(load().ms_steepest(ctx, _ptr(field), _dims(dims), int(dtype), _ptr(up), _ptr(dn)),
+           "ms_steepest")
+
+
+def ms_compress(ctx, ptr, n) -> None:
+    _check(load().ms_compress(ctx, _ptr(ptr), int(n)), "ms_compress")
+
+
+def ms_pair_rank(ctx, asc, desc, n, ms) -> int:
+    k = ctypes.c_int64(0)
+    _check(load().ms_pair_rank(ctx, _ptr(asc), _ptr(desc), int(n), _ptr(ms), ctypes.byref(k)),
+           "ms_pair_rank")
+    return int(k.value)
+
+
+def ms_profile_enable(ctx, on: bool = True) -> None:
+    _check(load().ms_profile_enable(ctx, 1 if on else 0), "ms_profile_enable")
+
+
+def ms_profile_read(ctx) -> dict:
+    """{'calls', 'launches', 'stages': {name: {'ms': total, 'launches': n}}}"""
+    p = _Profile()
+    _check(load().ms_profile_read(ctx, ctypes.byref(p)), "ms_profile_read")
+    return {"calls": int(p.calls), "launches": int(p.launches),
+            "stages": {STAGES[i]: {"ms": float(p.stage_ms[i]), "launches": int(p.stage_launches[i])}
+                       for i in range(len(STAGES))}}
+
+
+def ms_profile_stage_name(stage: int) -> str:
+    return load().ms_profile_stage_name(int(stage)).decode()
+
+
+def segment(ctx, field):
+    """Convenience over ms_segment for a CUDA tensor: allocates the three
+    int32 outputs with torch and returns (asc, desc, ms, K)."""
+    import torch
+
+    n = field.numel()
+    asc = torch.empty(n, dtype=torch.int32, device=field.device)
+    desc = torch.empty_like(asc)
+    ms = torch.empty_like(asc)
+    ms_segment(ctx, field, dims_of(field), dtype_code(field), asc, desc, ms)
+    return asc, desc, ms, ms_last_region_count(ctx)

@@ -1,0 +1,467 @@
+// C ABI of libmsseg (declared in include/ms.h): context, argument checks,
+// scratch memory and the order in which the steps of Sec. 4.2 are queued.
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "ms_internal.cuh"
+
+using namespace msseg;
+
+struct ms_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  DevStatus *dst = nullptr;  // device status block
+  DevStatus *hst = nullptr;  // pinned host copy
+  void *scratch = nullptr;   // pair-rank working memory
+  size_t scratch_bytes = 0;
+  void *io = nullptr;        // device buffers of ms_segment_host
+  size_t io_bytes = 0;
+  int64_t last_k = 0;
+  // profiler
+  bool prof_on = false;
+  ms_profile prof{};
+  cudaEvent_t ev[MS_STAGE_COUNT][2] = {};
+  bool ev_pending[MS_STAGE_COUNT] = {};
+};
+
+namespace msseg {
+thread_local long long tl_launches = 0;
+}
+
+namespace {
+
+constexpr int64_t kMaxVertices = 2147483647LL;
+
+ms_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MS_OK;
+  if (e == cudaErrorMemoryAllocation) return MS_ERR_OUT_OF_MEMORY;
+  return MS_ERR_CUDA;
+}
+
+#define MS_TRY(expr)                       \
+  do {                                     \
+    ms_status _s = cuda_status((expr));    \
+    if (_s != MS_OK) return _s;            \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+bool is_device_pointer(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+ms_status check_dims(const int64_t dims[3], int64_t *n_out) {
+  if (!dims) return MS_ERR_INVALID_ARG;
+  if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return MS_ERR_INVALID_ARG;
+  if (dims[0] > kMaxVertices || dims[1] > kMaxVertices || dims[2] > kMaxVertices)
+    return MS_ERR_TOO_LARGE;
+  const int64_t xy = dims[0] * dims[1];
+  if (xy > kMaxVertices || xy * dims[2] > kMaxVertices) return MS_ERR_TOO_LARGE;
+  *n_out = xy * dims[2];
+  return MS_OK;
+}
+
+ms_status check_dtype(int dtype) {
+  return (dtype == MS_F32 || dtype == MS_F16) ? MS_OK : MS_ERR_UNSUPPORTED_DTYPE;
+}
+
+int bit_width(int64_t x) {  // bits needed to hold values 0..x
+  int b = 0;
+  while (x > 0) {
+    ++b;
+    x >>= 1;
+  }
+  return b;
+}
+
+int round_cap(int64_t n) { return bit_width(n) + 2; }
+
+ms_status reset_status(ms_ctx *c) {
+  MS_TRY(cudaMemsetAsync(c->dst, 0, sizeof(DevStatus), c->stream));
+  return MS_OK;
+}
+
+ms_status read_status(ms_ctx *c) {
+  MS_TRY(cudaMemcpyAsync(c->hst, c->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream));
+  MS_TRY(cudaStreamSynchronize(c->stream));
+  return MS_OK;
+}
+
+ms_status ensure_scratch(ms_ctx *c, size_t bytes) {
+  if (c->scratch_bytes >= bytes) return MS_OK;
+  if (c->scratch) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->scratch);
+    c->scratch = nullptr;
+    c->scratch_bytes = 0;
+  }
+  if (cudaMalloc(&c->scratch, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return MS_ERR_OUT_OF_MEMORY;
+  }
+  c->scratch_bytes = bytes;
+  return MS_OK;
+}
+
+unsigned int pow2_at_least(uint64_t x) {
+  uint64_t p = 1024;
+  while (p < x && p < (1ull << 31)) p <<= 1;
+  return (unsigned int)p;
+}
+
+// Compression schedule: `first` rounds queued blind, then one status read;
+// if the last round still had work, the rest of the cap is queued and read.
+ms_status compress_pair(ms_ctx *c, int32_t *a, int32_t *b, int64_t n) {
+  const int cap = round_cap(n);
+  const int first = cap < 8 ? cap : 8;
+  for (int r = 0; r < first; ++r) MS_TRY(launch_compress_round(a, b, n, 4, r, c->dst, c->stream));
+  ms_status s = read_status(c);
+  if (s != MS_OK) return s;
+  if (c->hst->round_open[first - 1] == 0u) return MS_OK;
+  for (int r = first; r < cap; ++r) MS_TRY(launch_compress_round(a, b, n, 4, r, c->dst, c->stream));
+  s = read_status(c);
+  if (s != MS_OK) return s;
+  return c->hst->round_open[cap - 1] ? MS_ERR_NOT_CONVERGED : MS_OK;
+}
+
+// Dense pair ranks (Sec. 4.2.2).  `guess` is a first estimate of the number
+// of distinct pairs; `bound` a hard upper bound.
+ms_status rank_pairs(ms_ctx *c, const int32_t *asc, const int32_t *desc, int64_t n, int32_t *ms,
+                     uint64_t guess, uint64_t bound) {
+  if (n == 0) {
+    c->last_k = 0;
+    return MS_OK;
+  }
+  if (bound < 1) bound = 1;
+  if (guess > bound) guess = bound;
+  if (guess < 1) guess = 1;
+  for (;;) {
+    const unsigned int cap = pow2_at_least(2 * guess + 2);
+    ms_status s = ensure_scratch(c, rank_scratch_bytes(cap));
+    if (s != MS_OK) return s;
+    RankScratch rs;
+    rank_scratch_carve(c->scratch, cap, &rs);
+    MS_TRY(cudaMemsetAsync(&c->dst->n_unique, 0, sizeof(unsigned int), c->stream));
+    MS_TRY(cudaMemsetAsync(&c->dst->hash_overflow, 0, sizeof(unsigned int), c->stream));
+    MS_TRY(launch_pairs_insert(asc, desc, n, rs, c->dst, c->stream));
+    s = read_status(c);
+    if (s != MS_OK) return s;
+    if (c->hst->bad_index) return MS_ERR_INVALID_ARG;
+    if (c->hst->hash_overflow) {
+      if (guess >= bound) return MS_ERR_CUDA;  // cannot happen: the bound is exact
+      guess = guess * 4 < bound ? guess * 4 : bound;
+      continue;
+    }
+    const unsigned int m = c->hst->n_unique;
+    MS_TRY(launch_pairs_sort(rs, m, bit_width(n - 1), c->stream));
+    MS_TRY(launch_pairs_assign(rs, m, c->stream));
+    MS_TRY(launch_pairs_lookup(asc, desc, n, rs, ms, c->stream));
+    MS_TRY(cudaStreamSynchronize(c->stream));
+    c->last_k = m;
+    return MS_OK;
+  }
+}
+
+// Brackets one stage of a call with CUDA events on the context's stream
+// (profiler on only); the elapsed times are collected by finish_profile once
+// the call has synchronised.
+struct StageTimer {
+  ms_ctx *c;
+  int stage;
+  long long l0;
+  StageTimer(ms_ctx *ctx, int st) : c(ctx), stage(st), l0(tl_launches) {
+    if (c->prof_on) cudaEventRecord(c->ev[stage][0], c->stream);
+  }
+  void stop() {
+    if (!c->prof_on) return;
+    cudaEventRecord(c->ev[stage][1], c->stream);
+    c->ev_pending[stage] = true;
+    c->prof.stage_launches[stage] += tl_launches - l0;
+  }
+};
+
+void finish_profile(ms_ctx *c, long long launches0) {
+  if (!c->prof_on) return;
+  cudaStreamSynchronize(c->stream);
+  for (int s = 0; s < MS_STAGE_COUNT; ++s) {
+    if (!c->ev_pending[s]) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[s][0], c->ev[s][1]) == cudaSuccess) c->prof.stage_ms[s] += ms;
+    c->ev_pending[s] = false;
+  }
+  cudaGetLastError();
+  c->prof.calls += 1;
+  c->prof.launches += tl_launches - launches0;
+}
+
+ms_status segment_device(ms_ctx *c, const void *field, const int64_t dims[3], int dtype,
+                         int64_t n, int32_t *asc, int32_t *desc, int32_t *ms) {
+  ms_status s = reset_status(c);
+  if (s != MS_OK) return s;
+  // up is built in place in desc and dn in asc: after compression each holds
+  // the extremum its integral line reaches.
+  StageTimer t0(c, MS_STAGE_STEEPEST);
+  MS_TRY(launch_steepest_simple(field, dims, dtype, desc, asc, c->dst, c->stream));
+  t0.stop();
+  StageTimer t1(c, MS_STAGE_COMPRESS);
+  s = compress_pair(c, desc, asc, n);  // also reads the status block back
+  t1.stop();
+  if (c->hst->nan_flag) return MS_ERR_NAN_INPUT;
+  if (s != MS_OK) return s;
+  const uint64_t nmax = c->hst->n_max, nmin = c->hst->n_min;
+  uint64_t bound = nmin * nmax;
+  if (bound > (uint64_t)n) bound = (uint64_t)n;
+  const uint64_t guess = 8 * (nmin + nmax) + 1024;
+  StageTimer t2(c, MS_STAGE_PAIRS);
+  s = rank_pairs(c, asc, desc, n, ms, guess, bound);
+  t2.stop();
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ms_status_string(ms_status s) {
+  switch (s) {
+    case MS_OK: return "MS_OK";
+    case MS_ERR_INVALID_ARG: return "MS_ERR_INVALID_ARG";
+    case MS_ERR_UNSUPPORTED_DTYPE: return "MS_ERR_UNSUPPORTED_DTYPE";
+    case MS_ERR_TOO_LARGE: return "MS_ERR_TOO_LARGE";
+    case MS_ERR_NAN_INPUT: return "MS_ERR_NAN_INPUT";
+    case MS_ERR_OUT_OF_MEMORY: return "MS_ERR_OUT_OF_MEMORY";
+    case MS_ERR_CUDA: return "MS_ERR_CUDA";
+    case MS_ERR_NOT_CONVERGED: return "MS_ERR_NOT_CONVERGED";
+    case MS_ERR_TIMEOUT: return "MS_ERR_TIMEOUT";
+    case MS_ERR_BUSY: return "MS_ERR_BUSY";
+  }
+  return "MS_ERR_UNKNOWN";
+}
+
+ms_status ms_create(ms_ctx **out, int device, void *cuda_stream) {
+  if (!out) return MS_ERR_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return MS_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) return MS_ERR_INVALID_ARG;
+  DeviceGuard g(device);
+  ms_ctx *c = new (std::nothrow) ms_ctx();
+  if (!c) return MS_ERR_OUT_OF_MEMORY;
+  c->device = device;
+  ms_status s = MS_OK;
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    s = cuda_status(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = s == MS_OK;
+  }
+  if (s == MS_OK) s = cuda_status(cudaMalloc(&c->dst, sizeof(DevStatus)));
+  if (s == MS_OK) s = cuda_status(cudaMallocHost(&c->hst, sizeof(DevStatus)));
+  if (s != MS_OK) {
+    ms_destroy(c);
+    return s;
+  }
+  *out = c;
+  return MS_OK;
+}
+
+ms_status ms_destroy(ms_ctx *c) {
+  if (!c) return MS_OK;
+  DeviceGuard g(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->io) cudaFree(c->io);
+  if (c->dst) cudaFree(c->dst);
+  if (c->hst) cudaFreeHost(c->hst);
+  for (int i = 0; i < MS_STAGE_COUNT; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (c->ev[i][j]) cudaEventDestroy(c->ev[i][j]);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return MS_OK;
+}
+
+ms_status ms_last_region_count(const ms_ctx *c, int64_t *k) {
+  if (!c || !k) return MS_ERR_INVALID_ARG;
+  *k = c->last_k;
+  return MS_OK;
+}
+
+ms_status ms_segment(ms_ctx *c, const void *field, const int64_t dims[3], ms_dtype dtype,
+                     int32_t *out_asc, int32_t *out_desc, int32_t *out_ms) {
+  if (!c) return MS_ERR_INVALID_ARG;
+  int64_t n = 0;
+  ms_status s = check_dims(dims, &n);
+  if (s != MS_OK) return s;
+  s = check_dtype(dtype);
+  if (s != MS_OK) return s;
+  DeviceGuard g(c->device);
+  if (!is_device_pointer(field) || !is_device_pointer(out_asc) || !is_device_pointer(out_desc) ||
+      !is_device_pointer(out_ms))
+    return MS_ERR_INVALID_ARG;
+  if (out_asc == out_desc || out_asc == out_ms || out_desc == out_ms) return MS_ERR_INVALID_ARG;
+  const long long l0 = tl_launches;
+  s = segment_device(c, field, dims, dtype, n, out_asc, out_desc, out_ms);
+  if (s == MS_OK) finish_profile(c, l0);
+  return s;
+}
+
+ms_status ms_segment_host(ms_ctx *c, const void *host_field, const int64_t dims[3],
+                          ms_dtype dtype, int32_t *host_asc, int32_t *host_desc,
+                          int32_t *host_ms) {
+  if (!c || !host_field || !host_asc || !host_desc || !host_ms) return MS_ERR_INVALID_ARG;
+  int64_t n = 0;
+  ms_status s = check_dims(dims, &n);
+  if (s != MS_OK) return s;
+  s = check_dtype(dtype);
+  if (s != MS_OK) return s;
+  DeviceGuard g(c->device);
+  const size_t esz = dtype == MS_F16 ? 2 : 4;
+  const size_t fbytes = ((size_t)n * esz + 255) & ~(size_t)255;
+  const size_t lbytes = ((size_t)n * 4 + 255) & ~(size_t)255;
+  const size_t need = fbytes + 3 * lbytes;
+  if (c->io_bytes < need) {
+    if (c->io) {
+      cudaStreamSynchronize(c->stream);
+      cudaFree(c->io);
+      c->io = nullptr;
+      c->io_bytes = 0;
+    }
+    if (cudaMalloc(&c->io, need) != cudaSuccess) {
+      cudaGetLastError();
+      return MS_ERR_OUT_OF_MEMORY;
+    }
+    c->io_bytes = need;
+  }
+  char *base = static_cast<char *>(c->io);
+  void *dfield = base;
+  int32_t *dasc = reinterpret_cast<int32_t *>(base + fbytes);
+  int32_t *ddesc = reinterpret_cast<int32_t *>(base + fbytes + lbytes);
+  int32_t *dms = reinterpret_cast<int32_t *>(base + fbytes + 2 * lbytes);
+  const long long l0 = tl_launches;
+  StageTimer th(c, MS_STAGE_H2D);
+  MS_TRY(cudaMemcpyAsync(dfield, host_field, (size_t)n * esz, cudaMemcpyHostToDevice, c->stream));
+  th.stop();
+  s = segment_device(c, dfield, dims, dtype, n, dasc, ddesc, dms);
+  if (s != MS_OK) return s;
+  StageTimer td(c, MS_STAGE_D2H);
+  MS_TRY(cudaMemcpyAsync(host_asc, dasc, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
+  MS_TRY(cudaMemcpyAsync(host_desc, ddesc, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
+  MS_TRY(cudaMemcpyAsync(host_ms, dms, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
+  td.stop();
+  MS_TRY(cudaStreamSynchronize(c->stream));
+  finish_profile(c, l0);
+  return MS_OK;
+}
+
+ms_status ms_order_keys(ms_ctx *c, const void *field, int64_t n, ms_dtype dtype, uint32_t *keys) {
+  if (!c || n < 0) return MS_ERR_INVALID_ARG;
+  if (n > kMaxVertices) return MS_ERR_TOO_LARGE;
+  ms_status s = check_dtype(dtype);
+  if (s != MS_OK) return s;
+  DeviceGuard g(c->device);
+  if (n == 0) return MS_OK;
+  if (!is_device_pointer(field) || !is_device_pointer(keys)) return MS_ERR_INVALID_ARG;
+  s = reset_status(c);
+  if (s != MS_OK) return s;
+  MS_TRY(launch_order_keys(field, n, dtype, keys, c->dst, c->stream));
+  s = read_status(c);
+  if (s != MS_OK) return s;
+  return c->hst->nan_flag ? MS_ERR_NAN_INPUT : MS_OK;
+}
+
+ms_status ms_steepest(ms_ctx *c, const void *field, const int64_t dims[3], ms_dtype dtype,
+                      int32_t *up, int32_t *dn) {
+  if (!c) return MS_ERR_INVALID_ARG;
+  int64_t n = 0;
+  ms_status s = check_dims(dims, &n);
+  if (s != MS_OK) return s;
+  s = check_dtype(dtype);
+  if (s != MS_OK) return s;
+  DeviceGuard g(c->device);
+  if (!is_device_pointer(field) || !is_device_pointer(up) || !is_device_pointer(dn) || up == dn)
+    return MS_ERR_INVALID_ARG;
+  s = reset_status(c);
+  if (s != MS_OK) return s;
+  MS_TRY(launch_steepest_simple(field, dims, dtype, up, dn, c->dst, c->stream));
+  s = read_status(c);
+  if (s != MS_OK) return s;
+  return c->hst->nan_flag ? MS_ERR_NAN_INPUT : MS_OK;
+}
+
+ms_status ms_compress(ms_ctx *c, int32_t *ptr, int64_t n) {
+  if (!c || n < 0) return MS_ERR_INVALID_ARG;
+  if (n > kMaxVertices) return MS_ERR_TOO_LARGE;
+  DeviceGuard g(c->device);
+  if (n == 0) return MS_OK;
+  if (!is_device_pointer(ptr)) return MS_ERR_INVALID_ARG;
+  ms_status s = reset_status(c);
+  if (s != MS_OK) return s;
+  MS_TRY(launch_check_range(ptr, n, c->dst, c->stream));
+  s = read_status(c);
+  if (s != MS_OK) return s;
+  if (c->hst->bad_index) return MS_ERR_INVALID_ARG;
+  return compress_pair(c, ptr, nullptr, n);
+}
+
+ms_status ms_pair_rank(ms_ctx *c, const int32_t *asc, const int32_t *desc, int64_t n,
+                       int32_t *ms, int64_t *k_out) {
+  if (!c || n < 0) return MS_ERR_INVALID_ARG;
+  if (n > kMaxVertices) return MS_ERR_TOO_LARGE;
+  DeviceGuard g(c->device);
+  if (n > 0 && (!is_device_pointer(asc) || !is_device_pointer(desc) || !is_device_pointer(ms)))
+    return MS_ERR_INVALID_ARG;
+  ms_status s = reset_status(c);
+  if (s != MS_OK) return s;
+  const uint64_t guess = (uint64_t)(n < (1 << 16) ? n : (1 << 16));
+  s = rank_pairs(c, asc, desc, n, ms, guess, (uint64_t)n);
+  if (s == MS_OK && k_out) *k_out = c->last_k;
+  return s;
+}
+
+ms_status ms_profile_enable(ms_ctx *c, int on) {
+  if (!c) return MS_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (on) {
+    for (int i = 0; i < MS_STAGE_COUNT; ++i)
+      for (int j = 0; j < 2; ++j)
+        if (!c->ev[i][j]) MS_TRY(cudaEventCreate(&c->ev[i][j]));
+  }
+  c->prof = ms_profile{};
+  for (int i = 0; i < MS_STAGE_COUNT; ++i) c->ev_pending[i] = false;
+  c->prof_on = on != 0;
+  return MS_OK;
+}
+
+ms_status ms_profile_read(const ms_ctx *c, ms_profile *out) {
+  if (!c || !out) return MS_ERR_INVALID_ARG;
+  *out = c->prof;
+  return MS_OK;
+}
+
+const char *ms_profile_stage_name(int stage) {
+  static const char *names[MS_STAGE_COUNT] = {"steepest", "compress", "pairs", "h2d", "d2h"};
+  return (stage >= 0 && stage < MS_STAGE_COUNT) ? names[stage] : "?";
+}
+
+}  // extern "C"

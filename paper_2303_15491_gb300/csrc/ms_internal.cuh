@@ -1,0 +1,82 @@
+// Internal declarations shared by the CUDA translation units of libmsseg.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ms.h"
+
+namespace msseg {
+
+// Device-side status words, zeroed at the start of every call.
+struct DevStatus {
+  unsigned int nan_flag;       // a NaN was seen in the field
+  unsigned int bad_index;      // an index outside [0, n) was seen
+  unsigned int not_converged;  // set by the last compression round that did not finish
+  unsigned int hash_overflow;  // the pair table ran out of room
+  unsigned int n_unique;       // distinct (asc, desc) pairs inserted
+  unsigned int n_max;          // maxima found by the steepest step
+  unsigned int n_min;          // minima found by the steepest step
+  unsigned int pad;
+  unsigned int round_open[64];  // round_open[r] != 0: round r left work for round r+1
+};
+
+// Order key of an IEEE binary32 bit pattern (Sec. 4.1): -0 is folded onto +0
+// so that equal reals tie and fall through to the index comparison; then
+// positives get the sign bit set and negatives are complemented, which makes
+// unsigned integer order equal real order.  NaN patterns are the caller's to
+// reject; no real value maps to 0 or to 0xFFFFFFFF.
+__host__ __device__ __forceinline__ uint32_t order_key_bits(uint32_t b) {
+  if ((b << 1) == 0u) b = 0u;
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__host__ __device__ __forceinline__ bool is_nan_bits(uint32_t b) {
+  return (b & 0x7fffffffu) > 0x7f800000u;
+}
+
+__device__ __forceinline__ uint32_t load_bits(const void *field, int dtype, int64_t i) {
+  if (dtype == MS_F16) {
+    const __half h = reinterpret_cast<const __half *>(field)[i];
+    return __float_as_uint(__half2float(h));  // exact widening
+  }
+  return __ldg(reinterpret_cast<const uint32_t *>(field) + i);
+}
+
+// Kernels launched by this host thread (read by the profiler).
+extern thread_local long long tl_launches;
+
+// ---- launchers (stream-ordered, no synchronisation) ----------------------
+cudaError_t launch_order_keys(const void *field, int64_t n, int dtype, uint32_t *keys,
+                              DevStatus *st, cudaStream_t s);
+cudaError_t launch_steepest_simple(const void *field, const int64_t dims[3], int dtype,
+                                   int32_t *up, int32_t *dn, DevStatus *st, cudaStream_t s);
+cudaError_t launch_check_range(const int32_t *p, int64_t n, DevStatus *st, cudaStream_t s);
+cudaError_t launch_compress_round(int32_t *a, int32_t *b, int64_t n, int iters, int round,
+                                  DevStatus *st, cudaStream_t s);
+
+// Pair ranking (Sec. 4.2.2) working memory.
+struct RankScratch {
+  unsigned long long *table_keys;  // capacity entries, empty = ~0ull
+  int32_t *table_vals;             // capacity entries
+  unsigned long long *list;        // unique keys, up to max_unique
+  unsigned long long *tmp;         // sort ping-pong, up to max_unique
+  unsigned int *hist;              // 256 * kSortBlocks
+  unsigned int capacity;           // power of two
+  unsigned int max_unique;         // capacity / 2
+};
+constexpr int kSortBlocks = 240;
+size_t rank_scratch_bytes(unsigned int capacity);
+void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs);
+cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t n,
+                                const RankScratch &rs, DevStatus *st, cudaStream_t s);
+cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int n_unique, int key_bits,
+                              cudaStream_t s);
+cudaError_t launch_pairs_assign(const RankScratch &rs, unsigned int n_unique, cudaStream_t s);
+cudaError_t launch_pairs_lookup(const int32_t *asc, const int32_t *desc, int64_t n,
+                                const RankScratch &rs, int32_t *ms, cudaStream_t s);
+cudaError_t launch_fill_u64(unsigned long long *p, size_t count, unsigned long long v,
+                            cudaStream_t s);
+
+}  // namespace msseg

@@ -1,0 +1,294 @@
+// Step 4 of the segmentation: MS ids (Sec. 3.4, Sec. 4.2.2).  Vertices with
+// the same (asc, desc) pair share a region; the id is the rank of the pair
+// among the distinct pairs, lexicographic with asc first.
+//
+//   insert : every vertex's pair goes into an open-addressing hash set
+//            (lanes of a warp holding the same pair insert it once); each new
+//            pair is also appended to a compact list.
+//   sort   : LSD radix sort of the list on the compacted key (asc << b) | desc,
+//            b = bit width of n - 1, 8 bits per pass, stable scatter.
+//   assign : the sorted position of each pair is stored in its table slot.
+//   lookup : every vertex reads its pair's rank from the table.
+#include "ms_internal.cuh"
+
+namespace msseg {
+namespace {
+
+constexpr unsigned long long kEmpty = ~0ull;
+
+__device__ __forceinline__ unsigned long long pack_pair(int32_t a, int32_t d) {
+  return ((unsigned long long)(uint32_t)a << 32) | (uint32_t)d;
+}
+
+// 64-bit finaliser of MurmurHash3 (Appleby): spreads the pair over the table.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+__device__ __forceinline__ unsigned int lane_id() { return threadIdx.x & 31u; }
+
+__device__ void table_insert(const RankScratch &rs, unsigned long long key, DevStatus *st) {
+  const unsigned int mask = rs.capacity - 1u;
+  unsigned int slot = (unsigned int)mix64(key) & mask;
+  for (unsigned int probe = 0; probe < rs.capacity; ++probe) {
+    unsigned long long cur = *(volatile unsigned long long *)&rs.table_keys[slot];
+    if (cur == key) return;
+    if (cur == kEmpty) {
+      cur = atomicCAS(&rs.table_keys[slot], kEmpty, key);
+      if (cur == kEmpty) {
+        const unsigned int at = atomicAdd(&st->n_unique, 1u);
+        if (at < rs.max_unique)
+          rs.list[at] = key;
+        else
+          atomicOr(&st->hash_overflow, 1u);
+        return;
+      }
+      if (cur == key) return;
+    }
+    slot = (slot + 1u) & mask;
+  }
+  atomicOr(&st->hash_overflow, 1u);
+}
+
+__device__ __forceinline__ int table_find(const RankScratch &rs, unsigned long long key) {
+  const unsigned int mask = rs.capacity - 1u;
+  unsigned int slot = (unsigned int)mix64(key) & mask;
+  for (unsigned int probe = 0; probe < rs.capacity; ++probe) {
+    const unsigned long long cur = __ldg(&rs.table_keys[slot]);
+    if (cur == key) return (int)slot;
+    if (cur == kEmpty) return -1;
+    slot = (slot + 1u) & mask;
+  }
+  return -1;
+}
+
+__global__ void k_pairs_insert(const int32_t *__restrict__ asc, const int32_t *__restrict__ desc,
+                               int64_t n, RankScratch rs, DevStatus *st) {
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // the loop bound keeps whole warps together for __match_any_sync
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t v = base + threadIdx.x;
+    unsigned long long key = kEmpty;
+    if (v < n) {
+      const int32_t a = asc[v], d = desc[v];
+      if (a < 0 || d < 0 || (int64_t)a >= n || (int64_t)d >= n)
+        bad = true;
+      else
+        key = pack_pair(a, d);
+    }
+    const unsigned int peers = __match_any_sync(0xffffffffu, key);
+    if (key != kEmpty && (__ffs(peers) - 1) == (int)lane_id()) table_insert(rs, key, st);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(&st->bad_index, 1u);
+}
+
+__device__ __forceinline__ unsigned int sort_digit(unsigned long long key, int b, int shift) {
+  const unsigned long long compact = ((key >> 32) << b) | (key & 0xffffffffull);
+  return (unsigned int)(compact >> shift) & 255u;
+}
+
+__global__ void k_radix_hist(const unsigned long long *__restrict__ in, unsigned int m, int b,
+                             int shift, unsigned int *__restrict__ hist) {
+  __shared__ unsigned int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const unsigned int chunk = (m + gridDim.x - 1) / gridDim.x;
+  const unsigned int lo = blockIdx.x * chunk;
+  const unsigned int hi = min(m, lo + chunk);
+  for (unsigned int i = lo + threadIdx.x; i < hi; i += blockDim.x)
+    atomicAdd(&h[sort_digit(in[i], b, shift)], 1u);
+  __syncthreads();
+  hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of len entries by one block of 1024 threads.
+__global__ void k_scan_exclusive(unsigned int *__restrict__ a, unsigned int len) {
+  __shared__ unsigned int part[1024];
+  const unsigned int per = (len + blockDim.x - 1) / blockDim.x;
+  const unsigned int lo = threadIdx.x * per;
+  const unsigned int hi = min(len, lo + per);
+  unsigned int s = 0;
+  for (unsigned int i = lo; i < hi; ++i) s += a[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (unsigned int off = 1; off < blockDim.x; off <<= 1) {
+    const unsigned int t = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += t;
+    __syncthreads();
+  }
+  unsigned int run = part[threadIdx.x] - s;
+  for (unsigned int i = lo; i < hi; ++i) {
+    const unsigned int x = a[i];
+    a[i] = run;
+    run += x;
+  }
+}
+
+// Stable scatter: block j re-reads the chunk it histogrammed, 256 keys at a
+// time; a key's destination is its digit's running offset for this block,
+// plus the keys with the same digit in earlier warps of the tile, plus the
+// ones in earlier lanes of its own warp.
+__global__ void __launch_bounds__(256) k_radix_scatter(const unsigned long long *__restrict__ in,
+                                                       unsigned long long *__restrict__ out,
+                                                       unsigned int m, int b, int shift,
+                                                       const unsigned int *__restrict__ hist) {
+  __shared__ unsigned int run[256];
+  __shared__ unsigned int wcnt[8][256];
+  const unsigned int warp = threadIdx.x >> 5, lane = lane_id();
+  run[threadIdx.x] = hist[threadIdx.x * gridDim.x + blockIdx.x];
+  const unsigned int chunk = (m + gridDim.x - 1) / gridDim.x;
+  const unsigned int lo = blockIdx.x * chunk;
+  const unsigned int hi = min(m, lo + chunk);
+  for (unsigned int t0 = lo; t0 < hi; t0 += 256) {
+    for (int w = 0; w < 8; ++w) wcnt[w][threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned int i = t0 + threadIdx.x;
+    const bool valid = i < hi;
+    unsigned long long key = 0;
+    unsigned int d = 0x100u + lane;  // invalid lanes get distinct private digits
+    if (valid) {
+      key = in[i];
+      d = sort_digit(key, b, shift);
+    }
+    const unsigned int peers = __match_any_sync(0xffffffffu, d);
+    const unsigned int below = __popc(peers & ((1u << lane) - 1u));
+    if (valid && below == 0) wcnt[warp][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      unsigned int pre = 0;
+      for (unsigned int w = 0; w < warp; ++w) pre += wcnt[w][d];
+      out[run[d] + pre + below] = key;
+    }
+    __syncthreads();
+    unsigned int tot = 0;
+    for (int w = 0; w < 8; ++w) tot += wcnt[w][threadIdx.x];
+    run[threadIdx.x] += tot;
+    __syncthreads();
+  }
+}
+
+__global__ void k_pairs_assign(const unsigned long long *__restrict__ sorted, unsigned int m,
+                               RankScratch rs) {
+  const unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int slot = table_find(rs, sorted[i]);
+  if (slot >= 0) rs.table_vals[slot] = (int32_t)i;
+}
+
+__global__ void k_pairs_lookup(const int32_t *__restrict__ asc, const int32_t *__restrict__ desc,
+                               int64_t n, RankScratch rs, int32_t *__restrict__ ms) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t v = base + threadIdx.x;
+    unsigned long long key = kEmpty;
+    if (v < n) key = pack_pair(asc[v], desc[v]);
+    const unsigned int peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    int32_t r = -1;
+    if (key != kEmpty && leader == (int)lane_id()) {
+      const int slot = table_find(rs, key);
+      r = slot >= 0 ? rs.table_vals[slot] : -1;
+    }
+    r = __shfl_sync(0xffffffffu, r, leader);
+    if (v < n) ms[v] = r;
+  }
+}
+
+int sm_count() {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+unsigned int grid_n(int64_t n, int per_sm) {
+  int64_t blocks = (n + 255) / 256;
+  const int64_t cap = (int64_t)sm_count() * per_sm;
+  if (blocks > cap) blocks = cap;
+  return (unsigned int)(blocks > 0 ? blocks : 1);
+}
+
+}  // namespace
+
+size_t rank_scratch_bytes(unsigned int capacity) {
+  const size_t maxu = capacity / 2;
+  return (size_t)capacity * 8 + (size_t)capacity * 4 + maxu * 8 * 2 +
+         256 * (size_t)kSortBlocks * 4 + 4 * 256;
+}
+
+void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs) {
+  char *p = static_cast<char *>(base);
+  rs->capacity = capacity;
+  rs->max_unique = capacity / 2;
+  rs->table_keys = reinterpret_cast<unsigned long long *>(p);
+  p += (size_t)capacity * 8;
+  rs->list = reinterpret_cast<unsigned long long *>(p);
+  p += (size_t)rs->max_unique * 8;
+  rs->tmp = reinterpret_cast<unsigned long long *>(p);
+  p += (size_t)rs->max_unique * 8;
+  rs->table_vals = reinterpret_cast<int32_t *>(p);
+  p += (size_t)capacity * 4;
+  rs->hist = reinterpret_cast<unsigned int *>(p);
+}
+
+cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t n,
+                                const RankScratch &rs, DevStatus *st, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(rs.table_keys, 0xff, (size_t)rs.capacity * 8, s);
+  if (e != cudaSuccess || n <= 0) return e;
+  ++tl_launches;
+  k_pairs_insert<<<grid_n(n, 8), 256, 0, s>>>(asc, desc, n, rs, st);
+  return cudaGetLastError();
+}
+
+// Sorts rs.list[0, m) in place (the result always ends in rs.list).
+cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bits,
+                              cudaStream_t s) {
+  if (m <= 1) return cudaSuccess;
+  unsigned long long *src = rs.list, *dst = rs.tmp;
+  const int b = key_bits;  // bit width of one label
+  const int total = 2 * b;
+  for (int shift = 0; shift < total; shift += 8) {
+    ++tl_launches;
+    k_radix_hist<<<kSortBlocks, 256, 0, s>>>(src, m, b, shift, rs.hist);
+    ++tl_launches;
+    k_scan_exclusive<<<1, 1024, 0, s>>>(rs.hist, 256u * kSortBlocks);
+    ++tl_launches;
+    k_radix_scatter<<<kSortBlocks, 256, 0, s>>>(src, dst, m, b, shift, rs.hist);
+    unsigned long long *t = src;
+    src = dst;
+    dst = t;
+  }
+  if (src != rs.list)
+    return cudaMemcpyAsync(rs.list, src, (size_t)m * 8, cudaMemcpyDeviceToDevice, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pairs_assign(const RankScratch &rs, unsigned int m, cudaStream_t s) {
+  if (m == 0) return cudaSuccess;
+  ++tl_launches;
+  k_pairs_assign<<<(m + 255) / 256, 256, 0, s>>>(rs.list, m, rs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pairs_lookup(const int32_t *asc, const int32_t *desc, int64_t n,
+                                const RankScratch &rs, int32_t *ms, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  ++tl_launches;
+  k_pairs_lookup<<<grid_n(n, 8), 256, 0, s>>>(asc, desc, n, rs, ms);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_u64(unsigned long long *p, size_t count, unsigned long long v,
+                            cudaStream_t s) {
+  (void)v;
+  return cudaMemsetAsync(p, 0xff, count * 8, s);
+}
+
+}  // namespace msseg

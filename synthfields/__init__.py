@@ -130,11 +130,12 @@ def quantize_levels(f: np.ndarray, levels: int = 256) -> np.ndarray:
 
 
 def broad_gaussians_ramp(dims, seed: int, sigma: float = 300.0,
-                         dtype=np.float32, chunk: int = 64) -> np.ndarray:
+                         dtype=np.float32, rows: int = 2048) -> np.ndarray:
     """Two broad Gaussians (amplitudes +1 and -1, centres uniform in the
     middle half of the box) plus a gentle linear ramp.  3D ramp:
     0.5*(x+2y+3z)/(6(n-1)); 2D (nz == 1): 0.5*(x+2y)/(3(n-1)), with n the
-    largest extent.  Built slab by slab so that 1024^3 fits in float32."""
+    largest extent.  Built in blocks of ``rows`` rows so that 1024^3 and
+    32768^2 fit in float32 without large temporaries."""
     nx, ny, nz = (int(d) for d in dims)
     g = rng_for(seed)
     ext = np.array([nx - 1, ny - 1, nz - 1], dtype=np.float64)
@@ -142,23 +143,21 @@ def broad_gaussians_ramp(dims, seed: int, sigma: float = 300.0,
     amps = (1.0, -1.0)
     n = max(nx, ny, nz)
     x = np.arange(nx, dtype=np.float64)
-    y = np.arange(ny, dtype=np.float64)
     gx = [np.exp(-((x - c[i, 0]) ** 2) / (2 * sigma ** 2)) for i in range(2)]
-    gy = [np.exp(-((y - c[i, 1]) ** 2) / (2 * sigma ** 2)) for i in range(2)]
-    gxy = [gy[i][:, None] * gx[i][None, :] for i in range(2)]
     if nz > 1:
-        rxy = 0.5 * (x[None, :] + 2.0 * y[:, None]) / (6.0 * (n - 1))
-        rz = 0.5 * 3.0 / (6.0 * (n - 1))
+        cx, cy, cz = 0.5 / (6.0 * (n - 1)), 0.5 * 2.0 / (6.0 * (n - 1)), 0.5 * 3.0 / (6.0 * (n - 1))
     else:
-        rxy = 0.5 * (x[None, :] + 2.0 * y[:, None]) / (3.0 * max(n - 1, 1))
-        rz = 0.0
+        cx, cy, cz = 0.5 / (3.0 * max(n - 1, 1)), 0.5 * 2.0 / (3.0 * max(n - 1, 1)), 0.0
     out = np.empty((nz, ny, nx), dtype=dtype)
     for z in range(nz):
-        acc = rxy + rz * z
-        for i in range(2):
-            gz = math.exp(-((z - c[i, 2]) ** 2) / (2 * sigma ** 2)) if nz > 1 else 1.0
-            acc = acc + amps[i] * gz * gxy[i]
-        out[z] = acc.astype(dtype)
+        gz = [math.exp(-((z - c[i, 2]) ** 2) / (2 * sigma ** 2)) if nz > 1 else 1.0 for i in range(2)]
+        for y0 in range(0, ny, rows):
+            y = np.arange(y0, min(ny, y0 + rows), dtype=np.float64)[:, None]
+            acc = cx * x[None, :] + cy * y + cz * z
+            for i in range(2):
+                gy = np.exp(-((y - c[i, 1]) ** 2) / (2 * sigma ** 2))
+                acc = acc + (amps[i] * gz[i]) * gy * gx[i][None, :]
+            out[z, y0:y0 + y.shape[0]] = acc.astype(dtype)
     return out
 
 
