@@ -42,11 +42,12 @@ FALLBACK_HBM_GBS = 6800.0
 # Algorithmic bytes per vertex of the whole path: read the field once, write
 # three int32 labels.
 PATH_BYTES = {"f32": 16, "f16": 14}
-# Algorithmic bytes per vertex of one launch of each stage's kernel.
+# Algorithmic bytes per vertex of one launch of each per-vertex stage kernel:
+# tile_local reads the field and writes one 16-bit pair number per vertex;
+# write reads that number and writes the three int32 labels.
 STAGE_BYTES = {
-    "steepest": {"f32": 4 + 8, "f16": 2 + 8},  # field in, up + dn out
-    "compress": {"f32": 16, "f16": 16},        # one round: read + write up and dn
-    "pairs": {"f32": 12, "f16": 12},           # read asc + desc, write ms
+    "tile_local": {"f32": 4 + 2, "f16": 2 + 2},
+    "write": {"f32": 2 + 12, "f16": 2 + 12},
 }
 
 WORKLOADS = {
@@ -331,7 +332,7 @@ def main():
     # ---- roofline of the dominant kernel and of the whole path
     hbm, peak_kind = peaks()
     stages = prof["stages"]
-    dom = max(("steepest", "compress", "pairs"), key=lambda s: stages[s]["ms"])
+    dom = max(("tile_local", "write"), key=lambda s: stages[s]["ms"])
     launches = max(1, stages[dom]["launches"])
     per_launch_s = stages[dom]["ms"] / 1e3 / launches
     alg_bytes = STAGE_BYTES[dom][w["dtype"]] * n

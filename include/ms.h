@@ -90,6 +90,13 @@ ms_status ms_destroy(ms_ctx *ctx);
 ms_status ms_segment(ms_ctx *ctx, const void *field, const int64_t dims[3], ms_dtype dtype,
                      int32_t *out_asc, int32_t *out_desc, int32_t *out_ms);
 
+/* The same segmentation computed by the four step kernels below, one after
+ * the other, each through global memory (slower than ms_segment; kept as an
+ * independent GPU cross-check of the fused path).  Same arguments, outputs
+ * and errors as ms_segment. */
+ms_status ms_segment_staged(ms_ctx *ctx, const void *field, const int64_t dims[3], ms_dtype dtype,
+                            int32_t *out_asc, int32_t *out_desc, int32_t *out_ms);
+
 /* The same segmentation from and to HOST memory: copies the field to the
  * device, segments it and copies the three label arrays back, all on the
  * context's stream (pinned host buffers make the copies asynchronous DMA;
@@ -134,13 +141,19 @@ ms_status ms_pair_rank(ms_ctx *ctx, const int32_t *asc, const int32_t *desc, int
 
 /* ---- measurement ---------------------------------------------------------- */
 
-/* Stages of one segmentation, as timed by the profiler. */
+/* Stages of one segmentation, as timed by the profiler.  For ms_segment:
+ *   TILE_LOCAL  one kernel: order keys, steepest neighbours, path compression
+ *               inside each tile, numbering of each tile's (asc, desc) root pairs
+ *   RESOLVE     exits followed across tiles, global pair set, sort, MS ids
+ *   WRITE       one kernel: the three label arrays streamed out
+ * For ms_segment_staged the same three slots hold steepest neighbours, the
+ * compression rounds and the pair ranking. */
 typedef enum {
-  MS_STAGE_STEEPEST = 0, /* order keys + steepest neighbours (steps 1-2) */
-  MS_STAGE_COMPRESS = 1, /* path compression (step 3) */
-  MS_STAGE_PAIRS = 2,    /* MS ids: pair set, sort, lookup (step 4) */
-  MS_STAGE_H2D = 3,      /* ms_segment_host: field upload */
-  MS_STAGE_D2H = 4,      /* ms_segment_host: label download */
+  MS_STAGE_TILE_LOCAL = 0,
+  MS_STAGE_RESOLVE = 1,
+  MS_STAGE_WRITE = 2,
+  MS_STAGE_H2D = 3, /* ms_segment_host: field upload */
+  MS_STAGE_D2H = 4, /* ms_segment_host: label download */
   MS_STAGE_COUNT = 5
 } ms_stage;
 
@@ -161,7 +174,8 @@ ms_status ms_profile_enable(ms_ctx *ctx, int on);
 /* Copy the profiler's counters (zeros if it was never enabled). */
 ms_status ms_profile_read(const ms_ctx *ctx, ms_profile *out);
 
-/* Name of a stage ("steepest", "compress", ...); "?" if out of range. */
+/* Name of a stage ("tile_local", "resolve", "write", "h2d", "d2h"); "?" if out
+ * of range. */
 const char *ms_profile_stage_name(int stage);
 
 #ifdef __cplusplus

@@ -23,7 +23,7 @@ __all__ = [
     "MSError", "MS_F32", "MS_F16", "load", "ms_status_string", "ms_create", "ms_destroy",
     "ms_segment", "ms_segment_host", "ms_last_region_count", "ms_order_keys", "ms_steepest",
     "ms_compress", "ms_pair_rank", "segment", "EXPORTED_SYMBOLS", "ms_profile_enable",
-    "ms_profile_read", "ms_profile_stage_name", "STAGES",
+    "ms_profile_read", "ms_profile_stage_name", "STAGES", "ms_segment_staged",
 ]
 
 MS_F32, MS_F16 = 0, 1
@@ -34,9 +34,9 @@ STATUS = ["MS_OK", "MS_ERR_INVALID_ARG", "MS_ERR_UNSUPPORTED_DTYPE", "MS_ERR_TOO
 EXPORTED_SYMBOLS = [
     "ms_status_string", "ms_create", "ms_destroy", "ms_segment", "ms_segment_host",
     "ms_last_region_count", "ms_order_keys", "ms_steepest", "ms_compress", "ms_pair_rank",
-    "ms_profile_enable", "ms_profile_read", "ms_profile_stage_name",
+    "ms_profile_enable", "ms_profile_read", "ms_profile_stage_name", "ms_segment_staged",
 ]
-STAGES = ["steepest", "compress", "pairs", "h2d", "d2h"]
+STAGES = ["tile_local", "resolve", "write", "h2d", "d2h"]
 
 
 class _Profile(ctypes.Structure):
@@ -72,6 +72,7 @@ def load(build: bool = True) -> ctypes.CDLL:
             L.ms_create.argtypes = [ctypes.POINTER(c_vp), ctypes.c_int, c_vp]
             L.ms_destroy.argtypes = [c_vp]
             L.ms_segment.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
+            L.ms_segment_staged.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
             L.ms_segment_host.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
             L.ms_last_region_count.argtypes = [c_vp, c_i64p]
             L.ms_order_keys.argtypes = [c_vp, c_vp, ctypes.c_int64, ctypes.c_int, c_vp]
@@ -153,6 +154,11 @@ def ms_destroy(ctx: int) -> None:
 def ms_segment(ctx, field, dims, dtype, out_asc, out_desc, out_ms) -> None:
     _check(load().ms_segment(ctx, _ptr(field), _dims(dims), int(dtype), _ptr(out_asc),
                              _ptr(out_desc), _ptr(out_ms)), "ms_segment")
+
+
+def ms_segment_staged(ctx, field, dims, dtype, out_asc, out_desc, out_ms) -> None:
+    _check(load().ms_segment_staged(ctx, _ptr(field), _dims(dims), int(dtype), _ptr(out_asc),
+                                    _ptr(out_desc), _ptr(out_ms)), "ms_segment_staged")
 
 
 def ms_segment_host(ctx, host_field, dims, dtype, host_asc, host_desc, host_ms) -> None:

@@ -6,6 +6,7 @@
 #include <new>
 
 #include "ms_internal.cuh"
+#include "ms_tiled.cuh"
 
 using namespace msseg;
 
@@ -19,6 +20,10 @@ struct ms_ctx {
   size_t scratch_bytes = 0;
   void *io = nullptr;        // device buffers of ms_segment_host
   size_t io_bytes = 0;
+  void *tscratch = nullptr;  // tiled path working memory
+  size_t tscratch_bytes = 0;
+  unsigned long long *hcount = nullptr;  // pinned copy of the tiled pair count
+  unsigned long long pool_hint = 0;      // pair-pool capacity that sufficed last time
   int64_t last_k = 0;
   // profiler
   bool prof_on = false;
@@ -212,16 +217,90 @@ void finish_profile(ms_ctx *c, long long launches0) {
   c->prof.launches += tl_launches - launches0;
 }
 
+ms_status ensure_buffer(ms_ctx *c, void **buf, size_t *have, size_t bytes) {
+  if (*have >= bytes) return MS_OK;
+  if (*buf) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+  }
+  if (cudaMalloc(buf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return MS_ERR_OUT_OF_MEMORY;
+  }
+  *have = bytes;
+  return MS_OK;
+}
+
+// The tiled path (ms_tiled.cu): tile-local steepest + compression + pair
+// numbering, global resolution of tile exits and pair ranks, label write.
+ms_status segment_tiled(ms_ctx *c, const void *field, const int64_t dims[3], int dtype, int64_t n,
+                        int32_t *asc, int32_t *desc, int32_t *ms) {
+  const TileGeom g = tile_geom(dims);
+  unsigned long long cap = c->pool_hint;
+  if (cap == 0) cap = std::max<unsigned long long>(1ull << 16, (unsigned long long)n / 16);
+  if (cap > (unsigned long long)n) cap = (unsigned long long)n;
+  TiledScratch ts;
+  unsigned long long npairs = 0;
+  for (;;) {
+    ms_status s = reset_status(c);
+    if (s != MS_OK) return s;
+    s = ensure_buffer(c, &c->tscratch, &c->tscratch_bytes, tiled_scratch_bytes(g, cap));
+    if (s != MS_OK) return s;
+    tiled_scratch_carve(c->tscratch, g, cap, &ts);
+    StageTimer t0(c, MS_STAGE_TILE_LOCAL);
+    MS_TRY(launch_tile_local(field, dtype, g, ts, c->dst, c->stream));
+    t0.stop();
+    MS_TRY(cudaMemcpyAsync(c->hcount, ts.pool_count, sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, c->stream));
+    s = read_status(c);
+    if (s != MS_OK) return s;
+    if (c->hst->nan_flag) return MS_ERR_NAN_INPUT;
+    npairs = *c->hcount;
+    if (!c->hst->pool_overflow) break;
+    cap = npairs;  // exact now
+  }
+  c->pool_hint = std::max(c->pool_hint, cap);
+  StageTimer t2(c, MS_STAGE_RESOLVE);
+  const unsigned int hcap = pow2_at_least(2 * npairs + 2);
+  ms_status s = ensure_scratch(c, rank_scratch_bytes(hcap));
+  if (s != MS_OK) return s;
+  RankScratch rs;
+  rank_scratch_carve(c->scratch, hcap, &rs);
+  MS_TRY(launch_resolve_pairs(g, ts, rs, npairs, c->dst, c->stream));
+  s = read_status(c);
+  if (s != MS_OK) return s;
+  if (c->hst->not_converged) return MS_ERR_NOT_CONVERGED;
+  if (c->hst->hash_overflow) return MS_ERR_CUDA;  // cannot happen: capacity >= 2 * pairs
+  const unsigned int m = c->hst->n_unique;
+  MS_TRY(launch_pairs_sort(rs, m, bit_width(n - 1), c->stream));
+  MS_TRY(launch_pairs_assign(rs, m, c->stream));
+  MS_TRY(launch_pair_ids(ts, rs, npairs, c->stream));
+  t2.stop();
+  StageTimer t3(c, MS_STAGE_WRITE);
+  MS_TRY(launch_tile_write(g, ts, asc, desc, ms, c->stream));
+  t3.stop();
+  MS_TRY(cudaStreamSynchronize(c->stream));
+  c->last_k = m;
+  return MS_OK;
+}
+
 ms_status segment_device(ms_ctx *c, const void *field, const int64_t dims[3], int dtype,
+                         int64_t n, int32_t *asc, int32_t *desc, int32_t *ms) {
+  return segment_tiled(c, field, dims, dtype, n, asc, desc, ms);
+}
+
+ms_status segment_staged(ms_ctx *c, const void *field, const int64_t dims[3], int dtype,
                          int64_t n, int32_t *asc, int32_t *desc, int32_t *ms) {
   ms_status s = reset_status(c);
   if (s != MS_OK) return s;
   // up is built in place in desc and dn in asc: after compression each holds
   // the extremum its integral line reaches.
-  StageTimer t0(c, MS_STAGE_STEEPEST);
+  StageTimer t0(c, MS_STAGE_TILE_LOCAL);
   MS_TRY(launch_steepest_simple(field, dims, dtype, desc, asc, c->dst, c->stream));
   t0.stop();
-  StageTimer t1(c, MS_STAGE_COMPRESS);
+  StageTimer t1(c, MS_STAGE_RESOLVE);
   s = compress_pair(c, desc, asc, n);  // also reads the status block back
   t1.stop();
   if (c->hst->nan_flag) return MS_ERR_NAN_INPUT;
@@ -230,7 +309,7 @@ ms_status segment_device(ms_ctx *c, const void *field, const int64_t dims[3], in
   uint64_t bound = nmin * nmax;
   if (bound > (uint64_t)n) bound = (uint64_t)n;
   const uint64_t guess = 8 * (nmin + nmax) + 1024;
-  StageTimer t2(c, MS_STAGE_PAIRS);
+  StageTimer t2(c, MS_STAGE_WRITE);
   s = rank_pairs(c, asc, desc, n, ms, guess, bound);
   t2.stop();
   return s;
@@ -277,6 +356,7 @@ ms_status ms_create(ms_ctx **out, int device, void *cuda_stream) {
   }
   if (s == MS_OK) s = cuda_status(cudaMalloc(&c->dst, sizeof(DevStatus)));
   if (s == MS_OK) s = cuda_status(cudaMallocHost(&c->hst, sizeof(DevStatus)));
+  if (s == MS_OK) s = cuda_status(cudaMallocHost(&c->hcount, sizeof(unsigned long long)));
   if (s != MS_OK) {
     ms_destroy(c);
     return s;
@@ -291,6 +371,8 @@ ms_status ms_destroy(ms_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->scratch) cudaFree(c->scratch);
   if (c->io) cudaFree(c->io);
+  if (c->tscratch) cudaFree(c->tscratch);
+  if (c->hcount) cudaFreeHost(c->hcount);
   if (c->dst) cudaFree(c->dst);
   if (c->hst) cudaFreeHost(c->hst);
   for (int i = 0; i < MS_STAGE_COUNT; ++i)
@@ -322,6 +404,25 @@ ms_status ms_segment(ms_ctx *c, const void *field, const int64_t dims[3], ms_dty
   if (out_asc == out_desc || out_asc == out_ms || out_desc == out_ms) return MS_ERR_INVALID_ARG;
   const long long l0 = tl_launches;
   s = segment_device(c, field, dims, dtype, n, out_asc, out_desc, out_ms);
+  if (s == MS_OK) finish_profile(c, l0);
+  return s;
+}
+
+ms_status ms_segment_staged(ms_ctx *c, const void *field, const int64_t dims[3], ms_dtype dtype,
+                            int32_t *out_asc, int32_t *out_desc, int32_t *out_ms) {
+  if (!c) return MS_ERR_INVALID_ARG;
+  int64_t n = 0;
+  ms_status s = check_dims(dims, &n);
+  if (s != MS_OK) return s;
+  s = check_dtype(dtype);
+  if (s != MS_OK) return s;
+  DeviceGuard g(c->device);
+  if (!is_device_pointer(field) || !is_device_pointer(out_asc) || !is_device_pointer(out_desc) ||
+      !is_device_pointer(out_ms))
+    return MS_ERR_INVALID_ARG;
+  if (out_asc == out_desc || out_asc == out_ms || out_desc == out_ms) return MS_ERR_INVALID_ARG;
+  const long long l0 = tl_launches;
+  s = segment_staged(c, field, dims, dtype, n, out_asc, out_desc, out_ms);
   if (s == MS_OK) finish_profile(c, l0);
   return s;
 }
@@ -460,7 +561,7 @@ ms_status ms_profile_read(const ms_ctx *c, ms_profile *out) {
 }
 
 const char *ms_profile_stage_name(int stage) {
-  static const char *names[MS_STAGE_COUNT] = {"steepest", "compress", "pairs", "h2d", "d2h"};
+  static const char *names[MS_STAGE_COUNT] = {"tile_local", "resolve", "write", "h2d", "d2h"};
   return (stage >= 0 && stage < MS_STAGE_COUNT) ? names[stage] : "?";
 }
 

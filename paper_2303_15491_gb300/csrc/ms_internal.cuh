@@ -18,7 +18,7 @@ struct DevStatus {
   unsigned int n_unique;       // distinct (asc, desc) pairs inserted
   unsigned int n_max;          // maxima found by the steepest step
   unsigned int n_min;          // minima found by the steepest step
-  unsigned int pad;
+  unsigned int pool_overflow;  // the tiled path's pair pool ran out of room
   unsigned int round_open[64];  // round_open[r] != 0: round r left work for round r+1
 };
 

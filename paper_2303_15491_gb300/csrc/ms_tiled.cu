@@ -1,0 +1,499 @@
+// The fused, tiled form of the segmentation used by ms_segment.
+//
+// The grid is cut into tiles of TX x TY x TZ vertices.  Three phases:
+//
+//  1. k_tile_local (one CTA per tile, persistent): streams the tile's field
+//     plus a one-vertex halo from HBM, computes up / dn of every tile vertex
+//     (Sec. 4.2.1 first step), compresses the paths inside the tile in shared
+//     memory (Sec. 4.2.1 second step, Fig. 3) until each pointer reaches a
+//     local maximum/minimum or the first vertex outside the tile (an "exit"),
+//     then numbers the distinct (dn-root, up-root) pairs of the tile.  Per
+//     vertex it writes only the 16-bit number of its pair; per tile the pair
+//     list (roots as global vertex indices, exits flagged) and, for the
+//     vertices on the tile's faces, their local roots (other tiles' paths
+//     enter through those vertices).
+//  2. k_resolve_pairs: every tile pair's exits are followed from face to face
+//     through the other tiles' face roots until they end at an extremum;
+//     the resulting (asc, desc) pairs are deduplicated in a global hash set,
+//     sorted (ms_rank.cu) and each tile pair gets its MS id (Sec. 4.2.2).
+//  3. k_tile_write: per tile, the small pair table is staged in shared memory
+//     and the three int32 labels of every vertex are streamed out.
+//
+// Steepest neighbours without 14 comparisons: the Freudenthal neighbourhood
+// of v together with v is the union of the two unit cubes [v, v+(1,1,1)] and
+// [v-(1,1,1), v] (their 2 x 8 corners minus the shared v are the 14 offsets
+// whose components are all >= 0 or all <= 0).  The maximum over a unit cube
+// is separable: pairs along x, then y, then z.  Every comparison is between
+// two candidate sets one of which lies entirely at higher vertex indices (the
+// +x / +y / +z half, or the upper cube), so the (value, index) order needs
+// only the 32-bit order key: on equal keys the higher-index operand wins for
+// the maximum and the lower-index one for the minimum.
+#include "ms_internal.cuh"
+#include "ms_tiled.cuh"
+
+namespace msseg {
+namespace {
+
+constexpr uint32_t kEmpty32 = 0xffffffffu;
+
+struct Cand {
+  uint32_t k;  // order key (max side) or key - 1 (min side)
+  uint32_t i;  // extended-box index of the candidate
+};
+
+// b lies at higher vertex indices than a.
+__device__ __forceinline__ Cand cmax(Cand a, Cand b) {
+  const bool t = b.k >= a.k;
+  return Cand{t ? b.k : a.k, t ? b.i : a.i};
+}
+__device__ __forceinline__ Cand cmin(Cand a, Cand b) {
+  const bool t = b.k < a.k;
+  return Cand{t ? b.k : a.k, t ? b.i : a.i};
+}
+
+__device__ __forceinline__ uint32_t key_at(const void *__restrict__ field, int dtype,
+                                           const TileGeom &g, int64_t x, int64_t y, int64_t z) {
+  if (x < 0 || y < 0 || z < 0 || x >= g.nx || y >= g.ny || z >= g.nz) return 0u;
+  return order_key_bits(load_bits(field, dtype, x + g.nx * (y + g.ny * z)));
+}
+
+__device__ __forceinline__ int ext_of(int lx, int ly, int lz) {
+  return (lx + 1) + kEX * ((ly + 1) + kEY * (lz + 1));
+}
+
+__device__ __forceinline__ bool ext_is_halo(int e) {
+  const int ex = e % kEX, r = e / kEX, ey = r % kEY, ez = r / kEY;
+  return ex == 0 || ey == 0 || ez == 0 || ex == kEX - 1 || ey == kEY - 1 || ez == kEZ - 1;
+}
+
+__device__ __forceinline__ int64_t ext_to_global(const TileGeom &g, int64_t x0, int64_t y0,
+                                                 int64_t z0, int e) {
+  const int ex = e % kEX, r = e / kEX, ey = r % kEY, ez = r / kEY;
+  return (x0 + ex - 1) + g.nx * ((y0 + ey - 1) + g.ny * (z0 + ez - 1));
+}
+
+__device__ __forceinline__ void tile_origin(const TileGeom &g, int64_t t, int64_t *x0, int64_t *y0,
+                                            int64_t *z0) {
+  const int64_t tx = t % g.tx, r = t / g.tx, ty = r % g.ty, tz = r / g.ty;
+  *x0 = tx * kTX;
+  *y0 = ty * kTY;
+  *z0 = tz * kTZ;
+}
+
+// Slot of a face vertex in its tile's face-root array (first face that
+// contains it, in the order z-low, z-high, y-low, y-high, x-low, x-high), or
+// -1 for an interior vertex.
+__device__ __forceinline__ int face_slot(int lx, int ly, int lz) {
+  if (lz == 0) return lx + kTX * ly;
+  if (lz == kTZ - 1) return kTX * kTY + lx + kTX * ly;
+  if (ly == 0) return 2 * kTX * kTY + lx + kTX * lz;
+  if (ly == kTY - 1) return 2 * kTX * kTY + kTX * kTZ + lx + kTX * lz;
+  if (lx == 0) return 2 * kTX * kTY + 2 * kTX * kTZ + ly + kTY * lz;
+  if (lx == kTX - 1) return 2 * kTX * kTY + 2 * kTX * kTZ + kTY * kTZ + ly + kTY * lz;
+  return -1;
+}
+
+__device__ __forceinline__ uint32_t hash32(uint32_t k) { return (k * 0x9E3779B1u) >> (32 - kHashBits); }
+
+// One CTA per tile (persistent).  Thread (lane, warp) owns the z-column of
+// vertices (x0 + lane, y0 + warp, z0 .. z0 + TZ - 1).
+__global__ void __launch_bounds__(kThreads, 2)
+    k_tile_local(const void *__restrict__ field, int dtype, TileGeom g, TiledScratch ts,
+                 DevStatus *st) {
+  extern __shared__ uint32_t dsmem[];
+  uint32_t *P = dsmem;         // kExt words: up | dn << 16, extended-box indices
+  uint32_t *H = dsmem + kExt;  // kHash words: pair set, key = up-root | dn-root << 16, then number
+  __shared__ int s_scan[kThreads / 32];
+  __shared__ long long s_base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lx = lane, ly = warp;
+  bool nan = false;
+
+  for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    int64_t x0, y0, z0;
+    tile_origin(g, tile, &x0, &y0, &z0);
+    for (int i = threadIdx.x; i < kExt; i += kThreads) P[i] = (uint32_t)i | ((uint32_t)i << 16);
+    for (int i = threadIdx.x; i < kHash; i += kThreads) H[i] = kEmpty32;
+    __syncthreads();
+
+    // ---- steepest neighbours, streaming the column along z
+    const int64_t x = x0 + lx, y = y0 + ly;
+    const bool col_in = x < g.nx && y < g.ny;
+    // edge lanes fetch the keys just left / right of the warp's 32 columns
+    const int64_t xe = lane == 0 ? x0 - 1 : (lane == 31 ? x0 + kTX : x);
+    Cand hi_prev_max{}, hi_prev_min{}, lo_prev_max{}, lo_prev_min{}, lo_prev2_max{}, lo_prev2_min{};
+#pragma unroll 2
+    for (int p = 0; p < kTZ + 2; ++p) {
+      const int64_t z = z0 - 1 + p;
+      const uint32_t kA = key_at(field, dtype, g, x, y - 1, z);
+      const uint32_t kB = key_at(field, dtype, g, x, y, z);
+      const uint32_t kC = key_at(field, dtype, g, x, y + 1, z);
+      const uint32_t eA = key_at(field, dtype, g, xe, y - 1, z);
+      const uint32_t eB = key_at(field, dtype, g, xe, y, z);
+      const uint32_t eC = key_at(field, dtype, g, xe, y + 1, z);
+      // a NaN's key lies below the key of -inf or above the key of +inf
+      if (p >= 1 && p <= kTZ && col_in && z < g.nz)
+        nan |= kB < 0x007fffffu || kB > 0xff800000u;
+      uint32_t kAm = __shfl_up_sync(0xffffffffu, kA, 1);
+      uint32_t kBm = __shfl_up_sync(0xffffffffu, kB, 1);
+      uint32_t kBp = __shfl_down_sync(0xffffffffu, kB, 1);
+      uint32_t kCp = __shfl_down_sync(0xffffffffu, kC, 1);
+      if (lane == 0) {
+        kAm = eA;
+        kBm = eB;
+      }
+      if (lane == 31) {
+        kBp = eB;
+        kCp = eC;
+      }
+      const int base = ext_of(lx, ly, p - 1);
+      // max side
+      const Cand h1hiB = cmax(Cand{kB, (uint32_t)base}, Cand{kBp, (uint32_t)(base + 1)});
+      const Cand h1hiC = cmax(Cand{kC, (uint32_t)(base + kEX)}, Cand{kCp, (uint32_t)(base + kEX + 1)});
+      const Cand h1loA = cmax(Cand{kAm, (uint32_t)(base - kEX - 1)}, Cand{kA, (uint32_t)(base - kEX)});
+      const Cand h1loB = cmax(Cand{kBm, (uint32_t)(base - 1)}, Cand{kB, (uint32_t)base});
+      const Cand h2hi_max = cmax(h1hiB, h1hiC);
+      const Cand h2lo_max = cmax(h1loA, h1loB);
+      // min side (key - 1 sends the out-of-box key 0 to the top)
+      const Cand n1hiB = cmin(Cand{kB - 1u, (uint32_t)base}, Cand{kBp - 1u, (uint32_t)(base + 1)});
+      const Cand n1hiC =
+          cmin(Cand{kC - 1u, (uint32_t)(base + kEX)}, Cand{kCp - 1u, (uint32_t)(base + kEX + 1)});
+      const Cand n1loA =
+          cmin(Cand{kAm - 1u, (uint32_t)(base - kEX - 1)}, Cand{kA - 1u, (uint32_t)(base - kEX)});
+      const Cand n1loB = cmin(Cand{kBm - 1u, (uint32_t)(base - 1)}, Cand{kB - 1u, (uint32_t)base});
+      const Cand h2hi_min = cmin(n1hiB, n1hiC);
+      const Cand h2lo_min = cmin(n1loA, n1loB);
+      if (p >= 2) {
+        const int lz = p - 2;
+        const Cand up = cmax(cmax(lo_prev2_max, lo_prev_max), cmax(hi_prev_max, h2hi_max));
+        const Cand dn = cmin(cmin(lo_prev2_min, lo_prev_min), cmin(hi_prev_min, h2hi_min));
+        if (col_in && z0 + lz < g.nz) P[ext_of(lx, ly, lz)] = up.i | (dn.i << 16);
+      }
+      lo_prev2_max = lo_prev_max;
+      lo_prev2_min = lo_prev_min;
+      lo_prev_max = h2lo_max;
+      lo_prev_min = h2lo_min;
+      hi_prev_max = h2hi_max;
+      hi_prev_min = h2hi_min;
+    }
+    __syncthreads();
+
+    // ---- path compression inside the tile: halo entries and extrema are
+    // self-pointers, so every pointer ends on a local extremum or an exit.
+    for (int round = 0; round < kMaxTileRounds; ++round) {
+      bool changed = false;
+#pragma unroll
+      for (int lz = 0; lz < kTZ; ++lz) {
+        const int e = ext_of(lx, ly, lz);
+        const uint32_t w = P[e];
+        const uint32_t u = w & 0xffffu, d = w >> 16;
+        const uint32_t uu = P[u] & 0xffffu, dd = P[d] >> 16;
+        if (uu != u || dd != d) {
+          P[e] = uu | (dd << 16);
+          changed = true;
+        }
+      }
+      if (!__syncthreads_or(changed)) break;
+    }
+
+    // ---- distinct (up-root, dn-root) pairs of the tile
+    uint32_t slots[kTZ];
+#pragma unroll
+    for (int lz = 0; lz < kTZ; ++lz) {
+      slots[lz] = kEmpty32;
+      if (!col_in || z0 + lz >= g.nz) continue;
+      const uint32_t key = P[ext_of(lx, ly, lz)];
+      uint32_t s = hash32(key);
+      for (int probe = 0; probe < kHash; ++probe) {
+        uint32_t cur = H[s];
+        if (cur == kEmpty32) cur = atomicCAS(&H[s], kEmpty32, key);
+        if (cur == kEmpty32 || cur == key) {
+          slots[lz] = s;
+          break;
+        }
+        s = (s + 1) & (kHash - 1);
+      }
+    }
+    __syncthreads();
+    // number the used slots in slot order: per-thread counts, block scan
+    constexpr int kPer = kHash / kThreads;
+    int cnt = 0;
+    for (int j = 0; j < kPer; ++j) cnt += H[threadIdx.x * kPer + j] != kEmpty32;
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_scan[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      int v = lane < kThreads / 32 ? s_scan[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (lane < kThreads / 32) s_scan[lane] = v;  // inclusive per warp
+      if (lane == kThreads / 32 - 1) {
+        const long long total = v;
+        const long long b = (long long)atomicAdd(ts.pool_count, (unsigned long long)total);
+        s_base = b;
+        ts.tile_base[tile] = b;
+        ts.tile_count[tile] = (int32_t)total;
+      }
+    }
+    __syncthreads();
+    const long long base = s_base;
+    int id = (warp > 0 ? s_scan[warp - 1] : 0) + incl - cnt;
+    for (int j = 0; j < kPer; ++j) {
+      const int s = threadIdx.x * kPer + j;
+      const uint32_t key = H[s];
+      if (key == kEmpty32) continue;
+      const long long at = base + id;
+      if (at < (long long)ts.pool_cap) {
+        const int u = (int)(key & 0xffffu), d = (int)(key >> 16);
+        const int64_t gu = ext_to_global(g, x0, y0, z0, u);
+        const int64_t gd = ext_to_global(g, x0, y0, z0, d);
+        ts.pool_roots[at] = make_int2((int)gd | (ext_is_halo(d) ? kExitFlag : 0),
+                                      (int)gu | (ext_is_halo(u) ? kExitFlag : 0));
+      } else {
+        atomicOr(&st->pool_overflow, 1u);
+      }
+      H[s] = (uint32_t)id;
+      ++id;
+    }
+    __syncthreads();
+    // per-vertex pair numbers and face roots
+    uint16_t *pid = ts.pid + tile * (int64_t)kTileV;
+    uint32_t *face = ts.face + tile * (int64_t)kFace;
+#pragma unroll
+    for (int lz = 0; lz < kTZ; ++lz) {
+      if (slots[lz] == kEmpty32) continue;
+      pid[lx + kTX * (ly + kTY * lz)] = (uint16_t)H[slots[lz]];
+      const int fs = face_slot(lx, ly, lz);
+      if (fs >= 0) face[fs] = P[ext_of(lx, ly, lz)];
+    }
+    __syncthreads();
+  }
+  if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&st->nan_flag, 1u);
+}
+
+// Follow an exit (a vertex on another tile's face) through the face roots
+// until an extremum; `up` selects the direction.
+__device__ int32_t chase(const TileGeom &g, const TiledScratch &ts, int32_t r, bool up,
+                         DevStatus *st) {
+  for (int64_t hop = 0; hop <= g.ntiles; ++hop) {
+    if (!(r & kExitFlag)) return r;
+    const int64_t e = r & ~kExitFlag;
+    const int64_t x = e % g.nx, q = e / g.nx, y = q % g.ny, z = q / g.ny;
+    const int64_t tile = (x / kTX) + g.tx * ((y / kTY) + g.ty * (z / kTZ));
+    int64_t x0, y0, z0;
+    tile_origin(g, tile, &x0, &y0, &z0);
+    const int fs = face_slot((int)(x - x0), (int)(y - y0), (int)(z - z0));
+    if (fs < 0) break;
+    const uint32_t w = ts.face[tile * (int64_t)kFace + fs];
+    const int loc = up ? (int)(w & 0xffffu) : (int)(w >> 16);
+    r = (int32_t)ext_to_global(g, x0, y0, z0, loc) | (ext_is_halo(loc) ? kExitFlag : 0);
+  }
+  atomicOr(&st->not_converged, 1u);
+  return 0;
+}
+
+// 64-bit finaliser of MurmurHash3 (Appleby).
+__device__ __forceinline__ unsigned long long mix64t(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
+__global__ void k_resolve_pairs(TileGeom g, TiledScratch ts, RankScratch rs, DevStatus *st) {
+  const unsigned long long npairs = *ts.pool_count;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < npairs;
+       base += stride) {
+    const unsigned long long p = base + threadIdx.x;
+    unsigned long long key = ~0ull;
+    if (p < npairs && p < ts.pool_cap) {
+      const int2 r = ts.pool_roots[p];
+      const int32_t a = chase(g, ts, r.x, false, st);
+      const int32_t d = chase(g, ts, r.y, true, st);
+      ts.pool_final[p] = make_int4(a, d, -1, 0);
+      key = ((unsigned long long)(uint32_t)a << 32) | (uint32_t)d;
+    }
+    const unsigned int peers = __match_any_sync(0xffffffffu, key);
+    if (key != ~0ull && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) {
+      // insert into the global pair set
+      const unsigned int mask = rs.capacity - 1u;
+      unsigned int slot = (unsigned int)mix64t(key) & mask;
+      for (unsigned int probe = 0; probe < rs.capacity; ++probe) {
+        unsigned long long cur = *(volatile unsigned long long *)&rs.table_keys[slot];
+        if (cur == key) break;
+        if (cur == ~0ull) {
+          cur = atomicCAS(&rs.table_keys[slot], ~0ull, key);
+          if (cur == ~0ull) {
+            const unsigned int at = atomicAdd(&st->n_unique, 1u);
+            if (at < rs.max_unique)
+              rs.list[at] = key;
+            else
+              atomicOr(&st->hash_overflow, 1u);
+            break;
+          }
+          if (cur == key) break;
+        }
+        slot = (slot + 1u) & mask;
+      }
+    }
+  }
+}
+
+__global__ void k_pair_ids(TiledScratch ts, RankScratch rs) {
+  const unsigned long long npairs = *ts.pool_count;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+       p < npairs && p < ts.pool_cap; p += stride) {
+    int4 f = ts.pool_final[p];
+    const unsigned long long key = ((unsigned long long)(uint32_t)f.x << 32) | (uint32_t)f.y;
+    const unsigned int mask = rs.capacity - 1u;
+    unsigned int slot = (unsigned int)mix64t(key) & mask;
+    int r = -1;
+    for (unsigned int probe = 0; probe < rs.capacity; ++probe) {
+      const unsigned long long cur = rs.table_keys[slot];
+      if (cur == key) {
+        r = rs.table_vals[slot];
+        break;
+      }
+      if (cur == ~0ull) break;
+      slot = (slot + 1u) & mask;
+    }
+    f.z = r;
+    ts.pool_final[p] = f;
+  }
+}
+
+// Per tile: stage the pair table, stream the labels out.
+__global__ void __launch_bounds__(kThreads)
+    k_tile_write(TileGeom g, TiledScratch ts, int32_t *__restrict__ asc, int32_t *__restrict__ desc,
+                 int32_t *__restrict__ ms) {
+  __shared__ int4 T[kStageCap];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    int64_t x0, y0, z0;
+    tile_origin(g, tile, &x0, &y0, &z0);
+    const long long b = ts.tile_base[tile];
+    const int cnt = ts.tile_count[tile];
+    const int4 *src = ts.pool_final + b;
+    const bool staged = cnt <= kStageCap;
+    if (staged)
+      for (int i = threadIdx.x; i < cnt; i += kThreads) T[i] = src[i];
+    __syncthreads();
+    const uint16_t *pid = ts.pid + tile * (int64_t)kTileV;
+    const int64_t x = x0 + lane, y = y0 + warp;
+    if (x < g.nx && y < g.ny) {
+      for (int lz = 0; lz < kTZ; ++lz) {
+        const int64_t z = z0 + lz;
+        if (z >= g.nz) break;
+        const int id = pid[lane + kTX * (warp + kTY * lz)];
+        const int4 t = staged ? T[id] : src[id];
+        const int64_t v = x + g.nx * (y + g.ny * z);
+        __stcs(asc + v, t.x);
+        __stcs(desc + v, t.y);
+        __stcs(ms + v, t.z);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int sms() {
+  int dev = 0, n = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n;
+}
+
+}  // namespace
+
+TileGeom tile_geom(const int64_t dims[3]) {
+  TileGeom g;
+  g.nx = dims[0];
+  g.ny = dims[1];
+  g.nz = dims[2];
+  g.tx = (g.nx + kTX - 1) / kTX;
+  g.ty = (g.ny + kTY - 1) / kTY;
+  g.tz = (g.nz + kTZ - 1) / kTZ;
+  g.ntiles = g.tx * g.ty * g.tz;
+  return g;
+}
+
+size_t tiled_scratch_bytes(const TileGeom &g, unsigned long long pool_cap) {
+  const size_t pid = (size_t)g.ntiles * kTileV * 2;
+  const size_t face = (size_t)g.ntiles * kFace * 4;
+  const size_t meta = (size_t)g.ntiles * (8 + 4);
+  return 4 * 256 + pid + face + meta + (size_t)pool_cap * (8 + 16) + 8 * 256;
+}
+
+void tiled_scratch_carve(void *base, const TileGeom &g, unsigned long long pool_cap,
+                         TiledScratch *ts) {
+  char *p = static_cast<char *>(base);
+  auto take = [&](size_t bytes) {
+    char *r = p;
+    p += (bytes + 255) & ~(size_t)255;
+    return r;
+  };
+  ts->pool_count = reinterpret_cast<unsigned long long *>(take(256));
+  ts->pool_final = reinterpret_cast<int4 *>(take((size_t)pool_cap * 16));
+  ts->pool_roots = reinterpret_cast<int2 *>(take((size_t)pool_cap * 8));
+  ts->tile_base = reinterpret_cast<long long *>(take((size_t)g.ntiles * 8));
+  ts->tile_count = reinterpret_cast<int32_t *>(take((size_t)g.ntiles * 4));
+  ts->face = reinterpret_cast<uint32_t *>(take((size_t)g.ntiles * kFace * 4));
+  ts->pid = reinterpret_cast<uint16_t *>(take((size_t)g.ntiles * kTileV * 2));
+  ts->pool_cap = pool_cap;
+}
+
+cudaError_t launch_tile_local(const void *field, int dtype, const TileGeom &g,
+                              const TiledScratch &ts, DevStatus *st, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ts.pool_count, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  constexpr int kSmem = (kExt + kHash) * 4;
+  e = cudaFuncSetAttribute(k_tile_local, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  if (e != cudaSuccess) return e;
+  const int64_t grid = std::min<int64_t>(g.ntiles, (int64_t)sms() * 2);
+  ++tl_launches;
+  k_tile_local<<<(unsigned)grid, kThreads, kSmem, s>>>(field, dtype, g, ts, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_resolve_pairs(const TileGeom &g, const TiledScratch &ts, const RankScratch &rs,
+                                 unsigned long long npairs, DevStatus *st, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(rs.table_keys, 0xff, (size_t)rs.capacity * 8, s);
+  if (e != cudaSuccess || npairs == 0) return e;
+  unsigned long long blocks = (npairs + 255) / 256;
+  const unsigned long long cap = (unsigned long long)sms() * 16;
+  if (blocks > cap) blocks = cap;
+  ++tl_launches;
+  k_resolve_pairs<<<(unsigned)blocks, 256, 0, s>>>(g, ts, rs, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_ids(const TiledScratch &ts, const RankScratch &rs, unsigned long long npairs,
+                            cudaStream_t s) {
+  if (npairs == 0) return cudaSuccess;
+  unsigned long long blocks = (npairs + 255) / 256;
+  const unsigned long long cap = (unsigned long long)sms() * 16;
+  if (blocks > cap) blocks = cap;
+  ++tl_launches;
+  k_pair_ids<<<(unsigned)blocks, 256, 0, s>>>(ts, rs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_write(const TileGeom &g, const TiledScratch &ts, int32_t *asc,
+                              int32_t *desc, int32_t *ms, cudaStream_t s) {
+  const int64_t grid = std::min<int64_t>(g.ntiles, (int64_t)sms() * 4);
+  ++tl_launches;
+  k_tile_write<<<(unsigned)grid, kThreads, 0, s>>>(g, ts, asc, desc, ms);
+  return cudaGetLastError();
+}
+
+}  // namespace msseg

@@ -1,0 +1,56 @@
+// Shapes, scratch layout and launchers of the tiled segmentation (ms_tiled.cu).
+#pragma once
+
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "ms_internal.cuh"
+
+namespace msseg {
+
+constexpr int kTX = 32, kTY = 16, kTZ = 16;               // tile, x fastest
+constexpr int kThreads = kTX * kTY;                      // one thread per (x, y) column
+constexpr int kEX = kTX + 2, kEY = kTY + 2, kEZ = kTZ + 2;  // tile + 1-vertex halo
+constexpr int kExt = kEX * kEY * kEZ;                    // 11016 < 2^16
+constexpr int kTileV = kTX * kTY * kTZ;                  // 8192
+constexpr int kFace = 2 * (kTX * kTY + kTX * kTZ + kTY * kTZ);  // face-root slots per tile
+constexpr int kHashBits = 13;
+constexpr int kHash = 1 << kHashBits;                    // >= kTileV: never overflows
+constexpr int kMaxTileRounds = 16;                       // 2^15 > kExt: doubling always ends
+constexpr int kStageCap = 2048;                          // pair-table entries staged in smem
+constexpr int32_t kExitFlag = (int32_t)0x80000000u;
+
+static_assert(kExt < 65536, "extended-box indices must fit 16 bits");
+static_assert(kHash >= kTileV, "pair table must hold one pair per vertex");
+
+struct TileGeom {
+  int64_t nx, ny, nz;
+  int64_t tx, ty, tz, ntiles;
+};
+
+struct TiledScratch {
+  unsigned long long *pool_count;  // pairs reserved by all tiles
+  unsigned long long pool_cap;
+  int2 *pool_roots;   // per tile pair: (dn-root, up-root), global index | kExitFlag if an exit
+  int4 *pool_final;   // per tile pair: (asc, desc, ms, 0)
+  long long *tile_base;
+  int32_t *tile_count;
+  uint32_t *face;     // per tile kFace words: up-root | dn-root << 16 (extended-box indices)
+  uint16_t *pid;      // per tile kTileV pair numbers, tile-local order x, y, z
+};
+
+TileGeom tile_geom(const int64_t dims[3]);
+size_t tiled_scratch_bytes(const TileGeom &g, unsigned long long pool_cap);
+void tiled_scratch_carve(void *base, const TileGeom &g, unsigned long long pool_cap,
+                         TiledScratch *ts);
+cudaError_t launch_tile_local(const void *field, int dtype, const TileGeom &g,
+                              const TiledScratch &ts, DevStatus *st, cudaStream_t s);
+cudaError_t launch_resolve_pairs(const TileGeom &g, const TiledScratch &ts, const RankScratch &rs,
+                                 unsigned long long npairs, DevStatus *st, cudaStream_t s);
+cudaError_t launch_pair_ids(const TiledScratch &ts, const RankScratch &rs,
+                            unsigned long long npairs, cudaStream_t s);
+cudaError_t launch_tile_write(const TileGeom &g, const TiledScratch &ts, int32_t *asc,
+                              int32_t *desc, int32_t *ms, cudaStream_t s);
+
+}  // namespace msseg

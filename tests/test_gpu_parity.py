@@ -284,3 +284,28 @@ def test_borrowed_stream(ctx):
         assert_same_labels(gpu_segment(h, f), oracle.segment(f), "borrowed stream")
     finally:
         ms.ms_destroy(h)
+
+
+@pytest.mark.parametrize("dims", [(40, 41, 42), (64, 64, 64), (300, 257, 1)])
+def test_staged_path_matches_oracle(ctx, dims):
+    """The step-by-step GPU path (ms_segment_staged) is an independent GPU
+    form of the same method; it must agree with the oracle too."""
+    f = sf.smoothed_noise(dims, 12, sigma=2.5, radius=10)
+    ref = oracle.segment(f)
+    dev = to_dev(f)
+    n = f.size
+    out = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(3)]
+    ms.ms_segment_staged(ctx, dev, dims, ms.MS_F32, *out)
+    got = tuple(o.cpu().numpy() for o in out) + (ms.ms_last_region_count(ctx),)
+    assert_same_labels(got, ref, f"staged {dims}")
+
+
+@pytest.mark.parametrize("dims", [(32, 16, 16), (33, 17, 17), (31, 15, 15), (64, 32, 48),
+                                  (97, 50, 35), (32, 16, 1), (1, 16, 16), (32, 1, 16)])
+def test_tile_boundaries(ctx, dims):
+    """Exact tile multiples, one past, one short, and flat boxes: paths that
+    cross tile faces, edges and corners."""
+    for seed, f in enumerate([sf.smoothed_noise(dims, 21, sigma=3.0, radius=12),
+                              sf.random_ties(dims, 22, levels=2),
+                              sf.broad_gaussians_ramp(dims, 23, sigma=20.0)]):
+        run_and_compare(ctx, f, f"tile boundary {dims} case {seed}")
