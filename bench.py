@@ -312,22 +312,24 @@ def main():
     value = ws * n * args.steps / (elapsed_ms / 1e3)
 
     # ---- end to end through ms_segment_host (pinned host memory)
-    h_field = torch.from_numpy(f_np).pin_memory()
-    h_asc = torch.empty(n, dtype=torch.int32).pin_memory()
-    h_desc = torch.empty_like(h_asc).pin_memory()
-    h_ms = torch.empty_like(h_asc).pin_memory()
-    ms.ms_segment_host(ctx, h_field, dims, dtype, h_asc, h_desc, h_ms)  # warm the io buffers
-    barrier()
-    t = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        ms.ms_segment_host(ctx, h_field, dims, dtype, h_asc, h_desc, h_ms)
-    e2e_s = time.perf_counter() - t
-    if dist is not None:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = ws * n * args.e2e_steps / e2e_s
     esz = 2 if w["dtype"] == "f16" else 4
+    e2e_value = None
+    if args.e2e_steps > 0:
+        h_field = torch.from_numpy(f_np).pin_memory()
+        h_asc = torch.empty(n, dtype=torch.int32).pin_memory()
+        h_desc = torch.empty_like(h_asc).pin_memory()
+        h_ms = torch.empty_like(h_asc).pin_memory()
+        ms.ms_segment_host(ctx, h_field, dims, dtype, h_asc, h_desc, h_ms)  # warm the io buffers
+        barrier()
+        t = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ms.ms_segment_host(ctx, h_field, dims, dtype, h_asc, h_desc, h_ms)
+        e2e_s = time.perf_counter() - t
+        if dist is not None:
+            tt = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e_value = ws * n * args.e2e_steps / e2e_s
 
     # ---- roofline of the dominant kernel and of the whole path
     hbm, peak_kind = peaks()
@@ -368,8 +370,9 @@ def main():
         "stages_ms_per_step": {k: v["ms"] / max(1, prof["calls"]) for k, v in stages.items()
                                if v["launches"] or v["ms"]},
         "gpu_launches": prof["launches"],
-        "e2e": {"value": e2e_value, "unit": "vertices/s", "h2d_bytes_per_step": n * esz,
-                "d2h_bytes_per_step": 3 * n * 4, "api": "ms_segment_host, pinned host buffers"},
+        "e2e": None if e2e_value is None else {
+            "value": e2e_value, "unit": "vertices/s", "h2d_bytes_per_step": n * esz,
+            "d2h_bytes_per_step": 3 * n * 4, "api": "ms_segment_host, pinned host buffers"},
         "clocks": clk.summary(),
     }
     ms.ms_destroy(ctx)

@@ -51,12 +51,6 @@ __device__ __forceinline__ Cand cmin(Cand a, Cand b) {
   return Cand{t ? b.k : a.k, t ? b.i : a.i};
 }
 
-__device__ __forceinline__ uint32_t key_at(const void *__restrict__ field, int dtype,
-                                           const TileGeom &g, int64_t x, int64_t y, int64_t z) {
-  if (x < 0 || y < 0 || z < 0 || x >= g.nx || y >= g.ny || z >= g.nz) return 0u;
-  return order_key_bits(load_bits(field, dtype, x + g.nx * (y + g.ny * z)));
-}
-
 __device__ __forceinline__ int ext_of(int lx, int ly, int lz) {
   return (lx + 1) + kEX * ((ly + 1) + kEY * (lz + 1));
 }
@@ -95,79 +89,104 @@ __device__ __forceinline__ int face_slot(int lx, int ly, int lz) {
 
 __device__ __forceinline__ uint32_t hash32(uint32_t k) { return (k * 0x9E3779B1u) >> (32 - kHashBits); }
 
+// Order key of one field value (Sec. 4.1): see order_key_bits; written
+// branch-free.  Out-of-box positions get the sentinel 0, which no real value
+// has.
+__device__ __forceinline__ uint32_t key_of(uint32_t b) {
+  b = (b == 0x80000000u) ? 0u : b;
+  const uint32_t m = (uint32_t)((int32_t)b >> 31);
+  return b ^ (m | 0x80000000u);
+}
+
+__device__ __forceinline__ uint32_t raw_bits(const void *__restrict__ field, int dtype, int64_t i) {
+  if (dtype == MS_F16)
+    return __float_as_uint(__half2float(reinterpret_cast<const __half *>(field)[i]));
+  return __ldg(reinterpret_cast<const uint32_t *>(field) + i);
+}
+
 // One CTA per tile (persistent).  Thread (lane, warp) owns the z-column of
 // vertices (x0 + lane, y0 + warp, z0 .. z0 + TZ - 1).
+//
+// Shared memory (dynamic): K, the order keys of the tile and its halo in
+// extended-box order (also reused for the pair set once the steepest step is
+// done), and P, the up / dn pointers in the same order.
 __global__ void __launch_bounds__(kThreads, 2)
     k_tile_local(const void *__restrict__ field, int dtype, TileGeom g, TiledScratch ts,
                  DevStatus *st) {
   extern __shared__ uint32_t dsmem[];
-  uint32_t *P = dsmem;         // kExt words: up | dn << 16, extended-box indices
-  uint32_t *H = dsmem + kExt;  // kHash words: pair set, key = up-root | dn-root << 16, then number
+  uint32_t *K = dsmem;         // kExt keys, then the kHash-word pair set
+  uint32_t *H = dsmem;
+  uint32_t *P = dsmem + kExt;  // kExt words: up | dn << 16, extended-box indices
   __shared__ int s_scan[kThreads / 32];
   __shared__ long long s_base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = lane, ly = warp;
   bool nan = false;
+  const int64_t plane = g.nx * g.ny;
 
   for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
     int64_t x0, y0, z0;
     tile_origin(g, tile, &x0, &y0, &z0);
-    for (int i = threadIdx.x; i < kExt; i += kThreads) P[i] = (uint32_t)i | ((uint32_t)i << 16);
-    for (int i = threadIdx.x; i < kHash; i += kThreads) H[i] = kEmpty32;
+
+    // ---- order keys of the tile + halo into K; halo pointers are self-loops
+    {
+      const bool x_in = x0 + lx < g.nx;
+      const int64_t xedge = lane == 0 ? x0 - 1 : x0 + kTX;  // lanes 0, 1 fetch ex = 0, 33
+      const bool xe_in = lane < 2 && xedge >= 0 && xedge < g.nx;
+#pragma unroll 4
+      for (int r = warp; r < kEY * kEZ; r += kThreads / 32) {
+        const int ey = r % kEY, ez = r / kEY;
+        const int64_t y = y0 + ey - 1, z = z0 + ez - 1;
+        const bool row_in = y >= 0 && y < g.ny && z >= 0 && z < g.nz;
+        const int64_t row = y * g.nx + z * plane;
+        uint32_t b = 0, be = 0;
+        if (row_in && x_in) b = raw_bits(field, dtype, row + x0 + lx);
+        if (row_in && xe_in) be = raw_bits(field, dtype, row + xedge);
+        const int ebase = kEX * r;
+        const bool interior = ey >= 1 && ey <= kTY && ez >= 1 && ez <= kTZ;
+        if (row_in && x_in && interior) nan |= is_nan_bits(b);
+        K[ebase + lx + 1] = (row_in && x_in) ? key_of(b) : 0u;
+        if (lane < 2) K[ebase + (lane == 0 ? 0 : kEX - 1)] = (row_in && xe_in) ? key_of(be) : 0u;
+        // halo rows / edges: self pointers
+        if (!interior) P[ebase + lx + 1] = (uint32_t)(ebase + lx + 1) * 0x10001u;
+        if (lane < 2) {
+          const int e = ebase + (lane == 0 ? 0 : kEX - 1);
+          P[e] = (uint32_t)e * 0x10001u;
+        }
+      }
+    }
     __syncthreads();
 
-    // ---- steepest neighbours, streaming the column along z
+    // ---- steepest neighbours from K, streaming the column along z
     const int64_t x = x0 + lx, y = y0 + ly;
     const bool col_in = x < g.nx && y < g.ny;
-    // edge lanes fetch the keys just left / right of the warp's 32 columns
-    const int64_t xe = lane == 0 ? x0 - 1 : (lane == 31 ? x0 + kTX : x);
     Cand hi_prev_max{}, hi_prev_min{}, lo_prev_max{}, lo_prev_min{}, lo_prev2_max{}, lo_prev2_min{};
 #pragma unroll 2
     for (int p = 0; p < kTZ + 2; ++p) {
-      const int64_t z = z0 - 1 + p;
-      const uint32_t kA = key_at(field, dtype, g, x, y - 1, z);
-      const uint32_t kB = key_at(field, dtype, g, x, y, z);
-      const uint32_t kC = key_at(field, dtype, g, x, y + 1, z);
-      const uint32_t eA = key_at(field, dtype, g, xe, y - 1, z);
-      const uint32_t eB = key_at(field, dtype, g, xe, y, z);
-      const uint32_t eC = key_at(field, dtype, g, xe, y + 1, z);
-      // a NaN's key lies below the key of -inf or above the key of +inf
-      if (p >= 1 && p <= kTZ && col_in && z < g.nz)
-        nan |= kB < 0x007fffffu || kB > 0xff800000u;
-      uint32_t kAm = __shfl_up_sync(0xffffffffu, kA, 1);
-      uint32_t kBm = __shfl_up_sync(0xffffffffu, kB, 1);
-      uint32_t kBp = __shfl_down_sync(0xffffffffu, kB, 1);
-      uint32_t kCp = __shfl_down_sync(0xffffffffu, kC, 1);
-      if (lane == 0) {
-        kAm = eA;
-        kBm = eB;
-      }
-      if (lane == 31) {
-        kBp = eB;
-        kCp = eC;
-      }
-      const int base = ext_of(lx, ly, p - 1);
-      // max side
-      const Cand h1hiB = cmax(Cand{kB, (uint32_t)base}, Cand{kBp, (uint32_t)(base + 1)});
-      const Cand h1hiC = cmax(Cand{kC, (uint32_t)(base + kEX)}, Cand{kCp, (uint32_t)(base + kEX + 1)});
-      const Cand h1loA = cmax(Cand{kAm, (uint32_t)(base - kEX - 1)}, Cand{kA, (uint32_t)(base - kEX)});
-      const Cand h1loB = cmax(Cand{kBm, (uint32_t)(base - 1)}, Cand{kB, (uint32_t)base});
+      const int e = (lx + 1) + kEX * ((ly + 1) + kEY * p);
+      const uint32_t kAm = K[e - kEX - 1], kA = K[e - kEX];
+      const uint32_t kBm = K[e - 1], kB = K[e], kBp = K[e + 1];
+      const uint32_t kC = K[e + kEX], kCp = K[e + kEX + 1];
+      const uint32_t ue = (uint32_t)e;
+      const Cand h1hiB = cmax(Cand{kB, ue}, Cand{kBp, ue + 1});
+      const Cand h1hiC = cmax(Cand{kC, ue + kEX}, Cand{kCp, ue + kEX + 1});
+      const Cand h1loA = cmax(Cand{kAm, ue - kEX - 1}, Cand{kA, ue - kEX});
+      const Cand h1loB = cmax(Cand{kBm, ue - 1}, Cand{kB, ue});
       const Cand h2hi_max = cmax(h1hiB, h1hiC);
       const Cand h2lo_max = cmax(h1loA, h1loB);
-      // min side (key - 1 sends the out-of-box key 0 to the top)
-      const Cand n1hiB = cmin(Cand{kB - 1u, (uint32_t)base}, Cand{kBp - 1u, (uint32_t)(base + 1)});
-      const Cand n1hiC =
-          cmin(Cand{kC - 1u, (uint32_t)(base + kEX)}, Cand{kCp - 1u, (uint32_t)(base + kEX + 1)});
-      const Cand n1loA =
-          cmin(Cand{kAm - 1u, (uint32_t)(base - kEX - 1)}, Cand{kA - 1u, (uint32_t)(base - kEX)});
-      const Cand n1loB = cmin(Cand{kBm - 1u, (uint32_t)(base - 1)}, Cand{kB - 1u, (uint32_t)base});
+      // min side: key - 1 sends the out-of-box key 0 to the top
+      const Cand n1hiB = cmin(Cand{kB - 1u, ue}, Cand{kBp - 1u, ue + 1});
+      const Cand n1hiC = cmin(Cand{kC - 1u, ue + kEX}, Cand{kCp - 1u, ue + kEX + 1});
+      const Cand n1loA = cmin(Cand{kAm - 1u, ue - kEX - 1}, Cand{kA - 1u, ue - kEX});
+      const Cand n1loB = cmin(Cand{kBm - 1u, ue - 1}, Cand{kB - 1u, ue});
       const Cand h2hi_min = cmin(n1hiB, n1hiC);
       const Cand h2lo_min = cmin(n1loA, n1loB);
       if (p >= 2) {
         const int lz = p - 2;
+        const int ev = e - kEX * kEY;  // the vertex of plane p - 1
         const Cand up = cmax(cmax(lo_prev2_max, lo_prev_max), cmax(hi_prev_max, h2hi_max));
         const Cand dn = cmin(cmin(lo_prev2_min, lo_prev_min), cmin(hi_prev_min, h2hi_min));
-        if (col_in && z0 + lz < g.nz) P[ext_of(lx, ly, lz)] = up.i | (dn.i << 16);
+        P[ev] = (col_in && z0 + lz < g.nz) ? (up.i | (dn.i << 16)) : (uint32_t)ev * 0x10001u;
       }
       lo_prev2_max = lo_prev_max;
       lo_prev2_min = lo_prev_min;
@@ -178,23 +197,32 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     __syncthreads();
 
-    // ---- path compression inside the tile: halo entries and extrema are
+    // ---- path compression inside the tile.  Halo entries and extrema are
     // self-pointers, so every pointer ends on a local extremum or an exit.
-    for (int round = 0; round < kMaxTileRounds; ++round) {
-      bool changed = false;
+    // Each warp jumps its own vertices in place until they are all done;
+    // reads of other vertices' pointers may see them before or after their
+    // own jumps, and either lies on the same path.
+    for (int i = threadIdx.x; i < kHash; i += kThreads) H[i] = kEmpty32;
+    {
+      volatile uint32_t *VP = P;
+      uint32_t done = 0;
+      for (int it = 0; it < kExt; ++it) {
 #pragma unroll
-      for (int lz = 0; lz < kTZ; ++lz) {
-        const int e = ext_of(lx, ly, lz);
-        const uint32_t w = P[e];
-        const uint32_t u = w & 0xffffu, d = w >> 16;
-        const uint32_t uu = P[u] & 0xffffu, dd = P[d] >> 16;
-        if (uu != u || dd != d) {
-          P[e] = uu | (dd << 16);
-          changed = true;
+        for (int lz = 0; lz < kTZ; ++lz) {
+          if (done & (1u << lz)) continue;
+          const int e = ext_of(lx, ly, lz);
+          const uint32_t w = VP[e];
+          const uint32_t u = w & 0xffffu, d = w >> 16;
+          const uint32_t uu = VP[u] & 0xffffu, dd = VP[d] >> 16;
+          if (uu != u || dd != d)
+            VP[e] = uu | (dd << 16);
+          else
+            done |= 1u << lz;
         }
+        if (__all_sync(0xffffffffu, done == 0xffffu)) break;
       }
-      if (!__syncthreads_or(changed)) break;
     }
+    __syncthreads();
 
     // ---- distinct (up-root, dn-root) pairs of the tile
     uint32_t slots[kTZ];
@@ -262,13 +290,25 @@ __global__ void __launch_bounds__(kThreads, 2)
       ++id;
     }
     __syncthreads();
-    // per-vertex pair numbers and face roots
-    uint16_t *pid = ts.pid + tile * (int64_t)kTileV;
+    // per-vertex pair numbers (the column's 16 numbers are contiguous) and
+    // face roots
+    uint32_t packed[kTZ / 2];
+#pragma unroll
+    for (int lz = 0; lz < kTZ; lz += 2) {
+      const uint32_t a = slots[lz] == kEmpty32 ? 0u : H[slots[lz]];
+      const uint32_t b = slots[lz + 1] == kEmpty32 ? 0u : H[slots[lz + 1]];
+      packed[lz / 2] = (a & 0xffffu) | (b << 16);
+    }
+    uint4 *pid4 = reinterpret_cast<uint4 *>(ts.pid + tile * (int64_t)kTileV +
+                                            (int64_t)(ly * kTX + lx) * kTZ);
+    if (col_in) {
+      pid4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+      pid4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+    }
     uint32_t *face = ts.face + tile * (int64_t)kFace;
 #pragma unroll
     for (int lz = 0; lz < kTZ; ++lz) {
       if (slots[lz] == kEmpty32) continue;
-      pid[lx + kTX * (ly + kTY * lz)] = (uint16_t)H[slots[lz]];
       const int fs = face_slot(lx, ly, lz);
       if (fs >= 0) face[fs] = P[ext_of(lx, ly, lz)];
     }
@@ -372,12 +412,15 @@ __global__ void k_pair_ids(TiledScratch ts, RankScratch rs) {
   }
 }
 
-// Per tile: stage the pair table, stream the labels out.
+// Per tile: stage the pair table, stream the labels out.  Thread (lane,
+// warp) writes the z-column (x0 + lane, y0 + warp, .); its 16 pair numbers
+// are one 32-byte vector.
 __global__ void __launch_bounds__(kThreads)
     k_tile_write(TileGeom g, TiledScratch ts, int32_t *__restrict__ asc, int32_t *__restrict__ desc,
                  int32_t *__restrict__ ms) {
   __shared__ int4 T[kStageCap];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t plane = g.nx * g.ny;
   for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
     int64_t x0, y0, z0;
     tile_origin(g, tile, &x0, &y0, &z0);
@@ -385,18 +428,28 @@ __global__ void __launch_bounds__(kThreads)
     const int cnt = ts.tile_count[tile];
     const int4 *src = ts.pool_final + b;
     const bool staged = cnt <= kStageCap;
+    const int64_t x = x0 + lane, y = y0 + warp;
+    const bool col_in = x < g.nx && y < g.ny;
+    uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
+    if (col_in) {
+      const uint4 *pid4 = reinterpret_cast<const uint4 *>(ts.pid + tile * (int64_t)kTileV +
+                                                          (int64_t)(warp * kTX + lane) * kTZ);
+      q0 = __ldcs(pid4);
+      q1 = __ldcs(pid4 + 1);
+    }
     if (staged)
       for (int i = threadIdx.x; i < cnt; i += kThreads) T[i] = src[i];
     __syncthreads();
-    const uint16_t *pid = ts.pid + tile * (int64_t)kTileV;
-    const int64_t x = x0 + lane, y = y0 + warp;
-    if (x < g.nx && y < g.ny) {
+    if (col_in) {
+      const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+      const int nz_here = (int)std::min<int64_t>(kTZ, g.nz - z0);
+      const int64_t v0 = x + g.nx * y + plane * z0;
+#pragma unroll
       for (int lz = 0; lz < kTZ; ++lz) {
-        const int64_t z = z0 + lz;
-        if (z >= g.nz) break;
-        const int id = pid[lane + kTX * (warp + kTY * lz)];
+        if (lz >= nz_here) break;
+        const int id = (int)((w[lz / 2] >> (16 * (lz & 1))) & 0xffffu);
         const int4 t = staged ? T[id] : src[id];
-        const int64_t v = x + g.nx * (y + g.ny * z);
+        const int64_t v = v0 + plane * lz;
         __stcs(asc + v, t.x);
         __stcs(desc + v, t.y);
         __stcs(ms + v, t.z);
@@ -456,7 +509,8 @@ cudaError_t launch_tile_local(const void *field, int dtype, const TileGeom &g,
                               const TiledScratch &ts, DevStatus *st, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ts.pool_count, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  constexpr int kSmem = (kExt + kHash) * 4;
+  constexpr int kSmem = 2 * kExt * 4;
+  static_assert(kHash <= kExt, "the pair set reuses the key area");
   e = cudaFuncSetAttribute(k_tile_local, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>(g.ntiles, (int64_t)sms() * 2);
