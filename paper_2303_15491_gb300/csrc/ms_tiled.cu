@@ -28,6 +28,9 @@
 // +x / +y / +z half, or the upper cube), so the (value, index) order needs
 // only the 32-bit order key: on equal keys the higher-index operand wins for
 // the maximum and the lower-index one for the minimum.
+#include <cuda.h>
+#include <string.h>
+
 #include "ms_internal.cuh"
 #include "ms_tiled.cuh"
 
@@ -51,19 +54,21 @@ __device__ __forceinline__ Cand cmin(Cand a, Cand b) {
   return Cand{t ? b.k : a.k, t ? b.i : a.i};
 }
 
+// Box index of tile-local vertex (lx, ly, lz); lx, ly, lz may be -1 or one
+// past the tile (the halo).
 __device__ __forceinline__ int ext_of(int lx, int ly, int lz) {
-  return (lx + 1) + kEX * ((ly + 1) + kEY * (lz + 1));
+  return (lx + kXO) + kEX * ((ly + 1) + kEY * (lz + 1));
 }
 
 __device__ __forceinline__ bool ext_is_halo(int e) {
   const int ex = e % kEX, r = e / kEX, ey = r % kEY, ez = r / kEY;
-  return ex == 0 || ey == 0 || ez == 0 || ex == kEX - 1 || ey == kEY - 1 || ez == kEZ - 1;
+  return ex == kXO - 1 || ex == kXO + kTX || ey == 0 || ez == 0 || ey == kEY - 1 || ez == kEZ - 1;
 }
 
 __device__ __forceinline__ int64_t ext_to_global(const TileGeom &g, int64_t x0, int64_t y0,
                                                  int64_t z0, int e) {
   const int ex = e % kEX, r = e / kEX, ey = r % kEY, ez = r / kEY;
-  return (x0 + ex - 1) + g.nx * ((y0 + ey - 1) + g.ny * (z0 + ez - 1));
+  return (x0 + ex - kXO) + g.nx * ((y0 + ey - 1) + g.ny * (z0 + ez - 1));
 }
 
 __device__ __forceinline__ void tile_origin(const TileGeom &g, int64_t t, int64_t *x0, int64_t *y0,
@@ -104,55 +109,117 @@ __device__ __forceinline__ uint32_t raw_bits(const void *__restrict__ field, int
   return __ldg(reinterpret_cast<const uint32_t *>(field) + i);
 }
 
+// ---- TMA and mbarrier helpers (inline PTX, sm_90+ forms, single CTA) -----
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Box load of the tile + halo: x from x0 - kXO, y from y0 - 1, z from z0 - 1;
+// the unit zero-fills whatever lies outside the field.
+__device__ __forceinline__ void tma_load_box(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                             int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+constexpr long long kWaitPolls = 1ll << 26;  // about a second of polling: a TMA never takes that
+
 // One CTA per tile (persistent).  Thread (lane, warp) owns the z-column of
 // vertices (x0 + lane, y0 + warp, z0 .. z0 + TZ - 1).
 //
-// Shared memory (dynamic): K, the order keys of the tile and its halo in
-// extended-box order (also reused for the pair set once the steepest step is
-// done), and P, the up / dn pointers in the same order.
+// Shared memory (dynamic): K, the order keys of the tile and its halo in box
+// order (reused for the pair set once the steepest step is done), and P, the
+// up / dn pointers in the same order.
+template <bool kTma>
 __global__ void __launch_bounds__(kThreads, 2)
     k_tile_local(const void *__restrict__ field, int dtype, TileGeom g, TiledScratch ts,
-                 DevStatus *st) {
-  extern __shared__ uint32_t dsmem[];
-  uint32_t *K = dsmem;         // kExt keys, then the kHash-word pair set
+                 DevStatus *st, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) uint32_t dsmem[];
+  uint32_t *K = dsmem;         // kExt words: keys, then the kHash-word pair set
   uint32_t *H = dsmem;
-  uint32_t *P = dsmem + kExt;  // kExt words: up | dn << 16, extended-box indices
+  uint32_t *P = dsmem + kExt;  // kExt words: up | dn << 16, box indices
+  __shared__ __align__(8) uint64_t s_bar;
   __shared__ int s_scan[kThreads / 32];
   __shared__ long long s_base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = lane, ly = warp;
   bool nan = false;
   const int64_t plane = g.nx * g.ny;
+  uint32_t parity = 0;
+  if (kTma && threadIdx.x == 0) mbar_init(&s_bar, 1);
+  __syncthreads();
 
   for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
     int64_t x0, y0, z0;
     tile_origin(g, tile, &x0, &y0, &z0);
 
-    // ---- order keys of the tile + halo into K; halo pointers are self-loops
+    // ---- field values of the tile + halo into K
+    if (kTma) {
+      if (threadIdx.x == 0) {
+        // K was last written by ordinary stores; order them before the copy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&s_bar, (uint32_t)(kExt * 4));
+        tma_load_box(K, &tmap, &s_bar, (int)(x0 - kXO), (int)(y0 - 1), (int)(z0 - 1));
+      }
+      long long polls = 0;
+      while (!mbar_try_wait(&s_bar, parity)) {
+        if (++polls > kWaitPolls) {
+          if (threadIdx.x == 0) atomicOr(&st->timeout, 1u);
+          return;
+        }
+      }
+      parity ^= 1u;
+    }
+    // ---- order keys in place (sentinel 0 outside the field); halo pointers
+    // are self-loops
     {
-      const bool x_in = x0 + lx < g.nx;
-      const int64_t xedge = lane == 0 ? x0 - 1 : x0 + kTX;  // lanes 0, 1 fetch ex = 0, 33
-      const bool xe_in = lane < 2 && xedge >= 0 && xedge < g.nx;
+      const int64_t xl = x0 + lx;
+      const bool x_in = xl < g.nx;
+      const int exe = lane == 0 ? kXO - 1 : kXO + kTX;  // lanes 0, 1: the halo columns
+      const int64_t xe = x0 + exe - kXO;
+      const bool xe_in = xe >= 0 && xe < g.nx;
 #pragma unroll 4
       for (int r = warp; r < kEY * kEZ; r += kThreads / 32) {
         const int ey = r % kEY, ez = r / kEY;
         const int64_t y = y0 + ey - 1, z = z0 + ez - 1;
         const bool row_in = y >= 0 && y < g.ny && z >= 0 && z < g.nz;
         const int64_t row = y * g.nx + z * plane;
-        uint32_t b = 0, be = 0;
-        if (row_in && x_in) b = raw_bits(field, dtype, row + x0 + lx);
-        if (row_in && xe_in) be = raw_bits(field, dtype, row + xedge);
-        const int ebase = kEX * r;
+        const int eb = kEX * r;
+        uint32_t b, be = 0;
+        if (kTma) {
+          b = K[eb + kXO + lx];
+          if (lane < 2) be = K[eb + exe];
+        } else {
+          b = (row_in && x_in) ? raw_bits(field, dtype, row + xl) : 0u;
+          if (lane < 2 && row_in && xe_in) be = raw_bits(field, dtype, row + xe);
+        }
         const bool interior = ey >= 1 && ey <= kTY && ez >= 1 && ez <= kTZ;
         if (row_in && x_in && interior) nan |= is_nan_bits(b);
-        K[ebase + lx + 1] = (row_in && x_in) ? key_of(b) : 0u;
-        if (lane < 2) K[ebase + (lane == 0 ? 0 : kEX - 1)] = (row_in && xe_in) ? key_of(be) : 0u;
-        // halo rows / edges: self pointers
-        if (!interior) P[ebase + lx + 1] = (uint32_t)(ebase + lx + 1) * 0x10001u;
-        if (lane < 2) {
-          const int e = ebase + (lane == 0 ? 0 : kEX - 1);
-          P[e] = (uint32_t)e * 0x10001u;
-        }
+        K[eb + kXO + lx] = (row_in && x_in) ? key_of(b) : 0u;
+        if (lane < 2) K[eb + exe] = (row_in && xe_in) ? key_of(be) : 0u;
+        if (!interior) P[eb + kXO + lx] = (uint32_t)(eb + kXO + lx) * 0x10001u;
+        if (lane < 2) P[eb + exe] = (uint32_t)(eb + exe) * 0x10001u;
       }
     }
     __syncthreads();
@@ -160,10 +227,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     // ---- steepest neighbours from K, streaming the column along z
     const int64_t x = x0 + lx, y = y0 + ly;
     const bool col_in = x < g.nx && y < g.ny;
+    const int nz_here = (int)min((int64_t)kTZ, g.nz - z0);
     Cand hi_prev_max{}, hi_prev_min{}, lo_prev_max{}, lo_prev_min{}, lo_prev2_max{}, lo_prev2_min{};
 #pragma unroll 2
     for (int p = 0; p < kTZ + 2; ++p) {
-      const int e = (lx + 1) + kEX * ((ly + 1) + kEY * p);
+      const int e = (lx + kXO) + kEX * ((ly + 1) + kEY * p);
       const uint32_t kAm = K[e - kEX - 1], kA = K[e - kEX];
       const uint32_t kBm = K[e - 1], kB = K[e], kBp = K[e + 1];
       const uint32_t kC = K[e + kEX], kCp = K[e + kEX + 1];
@@ -186,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const int ev = e - kEX * kEY;  // the vertex of plane p - 1
         const Cand up = cmax(cmax(lo_prev2_max, lo_prev_max), cmax(hi_prev_max, h2hi_max));
         const Cand dn = cmin(cmin(lo_prev2_min, lo_prev_min), cmin(hi_prev_min, h2hi_min));
-        P[ev] = (col_in && z0 + lz < g.nz) ? (up.i | (dn.i << 16)) : (uint32_t)ev * 0x10001u;
+        P[ev] = (col_in && lz < nz_here) ? (up.i | (dn.i << 16)) : (uint32_t)ev * 0x10001u;
       }
       lo_prev2_max = lo_prev_max;
       lo_prev2_min = lo_prev_min;
@@ -199,55 +267,79 @@ __global__ void __launch_bounds__(kThreads, 2)
 
     // ---- path compression inside the tile.  Halo entries and extrema are
     // self-pointers, so every pointer ends on a local extremum or an exit.
-    // Each warp jumps its own vertices in place until they are all done;
-    // reads of other vertices' pointers may see them before or after their
-    // own jumps, and either lies on the same path.
+    // Each thread keeps its own 16 pointers in registers (it alone writes
+    // them) and jumps them in place until done; its reads of other vertices'
+    // pointers may see them before or after their own jumps, and either lies
+    // on the same path.
     for (int i = threadIdx.x; i < kHash; i += kThreads) H[i] = kEmpty32;
+    uint32_t w[kTZ];
+#pragma unroll
+    for (int lz = 0; lz < kTZ; ++lz) w[lz] = P[ext_of(lx, ly, lz)];
     {
       volatile uint32_t *VP = P;
       uint32_t done = 0;
       for (int it = 0; it < kExt; ++it) {
 #pragma unroll
-        for (int lz = 0; lz < kTZ; ++lz) {
-          if (done & (1u << lz)) continue;
-          const int e = ext_of(lx, ly, lz);
-          const uint32_t w = VP[e];
-          const uint32_t u = w & 0xffffu, d = w >> 16;
-          const uint32_t uu = VP[u] & 0xffffu, dd = VP[d] >> 16;
-          if (uu != u || dd != d)
-            VP[e] = uu | (dd << 16);
-          else
-            done |= 1u << lz;
+        for (int h = 0; h < kTZ; h += 8) {
+          uint32_t gu[8], gd[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const bool act = !(done & (1u << (h + j)));
+            gu[j] = act ? VP[w[h + j] & 0xffffu] : 0u;
+            gd[j] = act ? VP[w[h + j] >> 16] : 0u;
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int lz = h + j;
+            if (done & (1u << lz)) continue;
+            const uint32_t nw = (gu[j] & 0xffffu) | (gd[j] & 0xffff0000u);
+            if (nw != w[lz]) {
+              w[lz] = nw;
+              VP[ext_of(lx, ly, lz)] = nw;
+            } else {
+              done |= 1u << lz;
+            }
+          }
         }
         if (__all_sync(0xffffffffu, done == 0xffffu)) break;
       }
     }
     __syncthreads();
 
-    // ---- distinct (up-root, dn-root) pairs of the tile
+    // ---- distinct (up-root, dn-root) pairs of the tile; lanes of a warp
+    // with the same pair insert it once
     uint32_t slots[kTZ];
 #pragma unroll
     for (int lz = 0; lz < kTZ; ++lz) {
-      slots[lz] = kEmpty32;
-      if (!col_in || z0 + lz >= g.nz) continue;
-      const uint32_t key = P[ext_of(lx, ly, lz)];
-      uint32_t s = hash32(key);
-      for (int probe = 0; probe < kHash; ++probe) {
-        uint32_t cur = H[s];
-        if (cur == kEmpty32) cur = atomicCAS(&H[s], kEmpty32, key);
-        if (cur == kEmpty32 || cur == key) {
-          slots[lz] = s;
-          break;
+      const bool valid = col_in && lz < nz_here;
+      const uint32_t key = valid ? w[lz] : kEmpty32;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      uint32_t slot = kEmpty32;
+      if (valid && leader == lane) {
+        uint32_t s = hash32(key);
+        for (int probe = 0; probe < kHash; ++probe) {
+          uint32_t cur = H[s];
+          if (cur == kEmpty32) cur = atomicCAS(&H[s], kEmpty32, key);
+          if (cur == kEmpty32 || cur == key) {
+            slot = s;
+            break;
+          }
+          s = (s + 1) & (kHash - 1);
         }
-        s = (s + 1) & (kHash - 1);
       }
+      slots[lz] = __shfl_sync(0xffffffffu, slot, leader);
+      if (!valid) slots[lz] = kEmpty32;
     }
     __syncthreads();
-    // number the used slots in slot order: per-thread counts, block scan
+    // number the used slots: thread t owns slots t, t + 512, ...; ids follow
+    // (thread, slot) order through a block scan of the per-thread counts
     constexpr int kPer = kHash / kThreads;
     int cnt = 0;
-    for (int j = 0; j < kPer; ++j) cnt += H[threadIdx.x * kPer + j] != kEmpty32;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) cnt += H[threadIdx.x + kThreads * j] != kEmpty32;
     int incl = cnt;
+#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += t;
@@ -256,6 +348,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     if (warp == 0) {
       int v = lane < kThreads / 32 ? s_scan[lane] : 0;
+#pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, v, o);
         if (lane >= o) v += t;
@@ -272,8 +365,9 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     const long long base = s_base;
     int id = (warp > 0 ? s_scan[warp - 1] : 0) + incl - cnt;
+#pragma unroll
     for (int j = 0; j < kPer; ++j) {
-      const int s = threadIdx.x * kPer + j;
+      const int s = threadIdx.x + kThreads * j;
       const uint32_t key = H[s];
       if (key == kEmpty32) continue;
       const long long at = base + id;
@@ -291,26 +385,26 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     __syncthreads();
     // per-vertex pair numbers (the column's 16 numbers are contiguous) and
-    // face roots
-    uint32_t packed[kTZ / 2];
-#pragma unroll
-    for (int lz = 0; lz < kTZ; lz += 2) {
-      const uint32_t a = slots[lz] == kEmpty32 ? 0u : H[slots[lz]];
-      const uint32_t b = slots[lz + 1] == kEmpty32 ? 0u : H[slots[lz + 1]];
-      packed[lz / 2] = (a & 0xffffu) | (b << 16);
-    }
-    uint4 *pid4 = reinterpret_cast<uint4 *>(ts.pid + tile * (int64_t)kTileV +
-                                            (int64_t)(ly * kTX + lx) * kTZ);
+    // the face roots (the column's final pointers)
     if (col_in) {
+      uint32_t packed[kTZ / 2];
+#pragma unroll
+      for (int lz = 0; lz < kTZ; lz += 2) {
+        const uint32_t a = slots[lz] == kEmpty32 ? 0u : H[slots[lz]];
+        const uint32_t b = slots[lz + 1] == kEmpty32 ? 0u : H[slots[lz + 1]];
+        packed[lz / 2] = (a & 0xffffu) | (b << 16);
+      }
+      uint4 *pid4 = reinterpret_cast<uint4 *>(ts.pid + tile * (int64_t)kTileV +
+                                              (int64_t)(ly * kTX + lx) * kTZ);
       pid4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
       pid4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-    }
-    uint32_t *face = ts.face + tile * (int64_t)kFace;
+      uint32_t *face = ts.face + tile * (int64_t)kFace;
+      const bool side = lx == 0 || lx == kTX - 1 || ly == 0 || ly == kTY - 1;
 #pragma unroll
-    for (int lz = 0; lz < kTZ; ++lz) {
-      if (slots[lz] == kEmpty32) continue;
-      const int fs = face_slot(lx, ly, lz);
-      if (fs >= 0) face[fs] = P[ext_of(lx, ly, lz)];
+      for (int lz = 0; lz < kTZ; ++lz) {
+        if (lz >= nz_here) break;
+        if (side || lz == 0 || lz == kTZ - 1) face[face_slot(lx, ly, lz)] = w[lz];
+      }
     }
     __syncthreads();
   }
@@ -505,17 +599,62 @@ void tiled_scratch_carve(void *base, const TileGeom &g, unsigned long long pool_
   ts->pool_cap = pool_cap;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// A 3D tensor map over a float32 field for the box load; false when the
+// field's layout does not meet TMA's rules (16-byte aligned base and row /
+// plane strides) or the driver entry point is missing.
+bool make_box_map(const void *field, int dtype, const TileGeom &g, CUtensorMap *map) {
+  if (dtype != MS_F32) return false;
+  if ((reinterpret_cast<uintptr_t>(field) & 15) != 0) return false;
+  if ((g.nx * 4) % 16 != 0) return false;
+  if (g.nx > (1ll << 31) || g.ny > (1ll << 31) || g.nz > (1ll << 31)) return false;
+  EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)(g.nx * g.ny) * 4};
+  const cuuint32_t box[3] = {kEX, kEY, kEZ};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<void *>(field), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_tile_local(const void *field, int dtype, const TileGeom &g,
-                              const TiledScratch &ts, DevStatus *st, cudaStream_t s) {
+                              const TiledScratch &ts, DevStatus *st, cudaStream_t s,
+                              bool allow_tma) {
   cudaError_t e = cudaMemsetAsync(ts.pool_count, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   constexpr int kSmem = 2 * kExt * 4;
   static_assert(kHash <= kExt, "the pair set reuses the key area");
-  e = cudaFuncSetAttribute(k_tile_local, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  const bool tma = allow_tma && make_box_map(field, dtype, g, &map);
+  auto kern = tma ? k_tile_local<true> : k_tile_local<false>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e != cudaSuccess) return e;
   const int64_t grid = std::min<int64_t>(g.ntiles, (int64_t)sms() * 2);
   ++tl_launches;
-  k_tile_local<<<(unsigned)grid, kThreads, kSmem, s>>>(field, dtype, g, ts, st);
+  kern<<<(unsigned)grid, kThreads, kSmem, s>>>(field, dtype, g, ts, st, map);
   return cudaGetLastError();
 }
 

@@ -11,13 +11,17 @@ namespace msseg {
 
 constexpr int kTX = 32, kTY = 16, kTZ = 16;               // tile, x fastest
 constexpr int kThreads = kTX * kTY;                      // one thread per (x, y) column
-constexpr int kEX = kTX + 2, kEY = kTY + 2, kEZ = kTZ + 2;  // tile + 1-vertex halo
-constexpr int kExt = kEX * kEY * kEZ;                    // 11016 < 2^16
+// The tile plus a one-vertex halo is staged in a box of kEX x kEY x kEZ
+// values whose x range starts 4 values left of the tile (x0 - 4, a 16-byte
+// boundary for float32 rows), so the tile's column lx sits at box column
+// lx + kXO and the halo columns at kXO - 1 and kXO + kTX.
+constexpr int kXO = 4;
+constexpr int kEX = kTX + 2 * kXO, kEY = kTY + 2, kEZ = kTZ + 2;  // 40 x 18 x 18
+constexpr int kExt = kEX * kEY * kEZ;                    // 12960 < 2^16
 constexpr int kTileV = kTX * kTY * kTZ;                  // 8192
 constexpr int kFace = 2 * (kTX * kTY + kTX * kTZ + kTY * kTZ);  // face-root slots per tile
 constexpr int kHashBits = 13;
 constexpr int kHash = 1 << kHashBits;                    // >= kTileV: never overflows
-constexpr int kMaxTileRounds = 16;                       // 2^15 > kExt: doubling always ends
 constexpr int kStageCap = 2048;                          // pair-table entries staged in smem
 constexpr int32_t kExitFlag = (int32_t)0x80000000u;
 
@@ -37,7 +41,7 @@ struct TiledScratch {
   long long *tile_base;
   int32_t *tile_count;
   uint32_t *face;     // per tile kFace words: up-root | dn-root << 16 (extended-box indices)
-  uint16_t *pid;      // per tile kTileV pair numbers, tile-local order x, y, z
+  uint16_t *pid;      // per tile kTileV pair numbers; the 16 of column (lx, ly) are contiguous
 };
 
 TileGeom tile_geom(const int64_t dims[3]);
@@ -45,7 +49,8 @@ size_t tiled_scratch_bytes(const TileGeom &g, unsigned long long pool_cap);
 void tiled_scratch_carve(void *base, const TileGeom &g, unsigned long long pool_cap,
                          TiledScratch *ts);
 cudaError_t launch_tile_local(const void *field, int dtype, const TileGeom &g,
-                              const TiledScratch &ts, DevStatus *st, cudaStream_t s);
+                              const TiledScratch &ts, DevStatus *st, cudaStream_t s,
+                              bool allow_tma = true);
 cudaError_t launch_resolve_pairs(const TileGeom &g, const TiledScratch &ts, const RankScratch &rs,
                                  unsigned long long npairs, DevStatus *st, cudaStream_t s);
 cudaError_t launch_pair_ids(const TiledScratch &ts, const RankScratch &rs,
