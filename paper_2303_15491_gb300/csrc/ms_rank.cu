@@ -107,27 +107,59 @@ __global__ void k_radix_hist(const unsigned long long *__restrict__ in, unsigned
   hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of len entries by one block of 1024 threads.
-__global__ void k_scan_exclusive(unsigned int *__restrict__ a, unsigned int len) {
-  __shared__ unsigned int part[1024];
-  const unsigned int per = (len + blockDim.x - 1) / blockDim.x;
-  const unsigned int lo = threadIdx.x * per;
-  const unsigned int hi = min(len, lo + per);
-  unsigned int s = 0;
-  for (unsigned int i = lo; i < hi; ++i) s += a[i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (unsigned int off = 1; off < blockDim.x; off <<= 1) {
-    const unsigned int t = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-    __syncthreads();
-    part[threadIdx.x] += t;
-    __syncthreads();
+// Exclusive scan of the digit-major histogram (256 rows of `cols` block
+// counts) by one block of 1024 threads: each warp scans 8 rows with lane
+// prefixes, the 256 row totals are scanned, and the row offsets are added.
+__global__ void __launch_bounds__(1024) k_scan_hist(unsigned int *__restrict__ a, int cols) {
+  __shared__ unsigned int rowsum[256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int per = (cols + 31) / 32;  // entries per lane within a row
+  for (int row = warp; row < 256; row += 32) {
+    unsigned int *r = a + (size_t)row * cols;
+    unsigned int s = 0;
+    for (int j = 0; j < per; ++j) {
+      const int c = lane * per + j;
+      if (c < cols) s += r[c];
+    }
+    unsigned int incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    unsigned int run = incl - s;
+    for (int j = 0; j < per; ++j) {
+      const int c = lane * per + j;
+      if (c < cols) {
+        const unsigned int x = r[c];
+        r[c] = run;
+        run += x;
+      }
+    }
+    if (lane == 31) rowsum[row] = incl;
   }
-  unsigned int run = part[threadIdx.x] - s;
-  for (unsigned int i = lo; i < hi; ++i) {
-    const unsigned int x = a[i];
-    a[i] = run;
-    run += x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned int v[8], s = 0;
+    for (int j = 0; j < 8; ++j) {
+      v[j] = rowsum[lane * 8 + j];
+      s += v[j];
+    }
+    unsigned int incl = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    unsigned int run = incl - s;
+    for (int j = 0; j < 8; ++j) {
+      rowsum[lane * 8 + j] = run;
+      run += v[j];
+    }
+  }
+  __syncthreads();
+  for (int row = warp; row < 256; row += 32) {
+    const unsigned int off = rowsum[row];
+    unsigned int *r = a + (size_t)row * cols;
+    for (int c = lane; c < cols; c += 32) r[c] += off;
   }
 }
 
@@ -258,7 +290,7 @@ cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bit
     ++tl_launches;
     k_radix_hist<<<kSortBlocks, 256, 0, s>>>(src, m, b, shift, rs.hist);
     ++tl_launches;
-    k_scan_exclusive<<<1, 1024, 0, s>>>(rs.hist, 256u * kSortBlocks);
+    k_scan_hist<<<1, 1024, 0, s>>>(rs.hist, kSortBlocks);
     ++tl_launches;
     k_radix_scatter<<<kSortBlocks, 256, 0, s>>>(src, dst, m, b, shift, rs.hist);
     unsigned long long *t = src;

@@ -44,18 +44,6 @@ struct Cand {
   uint32_t i;  // extended-box index of the candidate
 };
 
-// b lies at higher vertex indices than a.
-__device__ __forceinline__ Cand cmax(Cand a, Cand b) {
-  const bool t = b.k >= a.k;
-  return Cand{t ? b.k : a.k, t ? b.i : a.i};
-}
-__device__ __forceinline__ Cand cmin(Cand a, Cand b) {
-  const bool t = b.k < a.k;
-  return Cand{t ? b.k : a.k, t ? b.i : a.i};
-}
-
-// Box index of tile-local vertex (lx, ly, lz); lx, ly, lz may be -1 or one
-// past the tile (the halo).
 __device__ __forceinline__ int ext_of(int lx, int ly, int lz) {
   return (lx + kXO) + kEX * ((ly + 1) + kEY * (lz + 1));
 }
@@ -73,10 +61,12 @@ __device__ __forceinline__ int64_t ext_to_global(const TileGeom &g, int64_t x0, 
 
 __device__ __forceinline__ void tile_origin(const TileGeom &g, int64_t t, int64_t *x0, int64_t *y0,
                                             int64_t *z0) {
-  const int64_t tx = t % g.tx, r = t / g.tx, ty = r % g.ty, tz = r / g.ty;
-  *x0 = tx * kTX;
-  *y0 = ty * kTY;
-  *z0 = tz * kTZ;
+  uint32_t r, tx, ty, tz;
+  g.div_tx.divmod((uint32_t)t, &r, &tx);
+  g.div_ty.divmod(r, &tz, &ty);
+  *x0 = (int64_t)tx * kTX;
+  *y0 = (int64_t)ty * kTY;
+  *z0 = (int64_t)tz * kTZ;
 }
 
 // Slot of a face vertex in its tile's face-root array (first face that
@@ -145,18 +135,115 @@ __device__ __forceinline__ void tma_load_box(void *dst, const CUtensorMap *map, 
 
 constexpr long long kWaitPolls = 1ll << 26;  // about a second of polling: a TMA never takes that
 
+// Comparisons of staged values.  Interior tiles (tile and halo inside the
+// field) compare the raw float32 values: IEEE ">=" is the real order, equal
+// reals (including -0 and +0) tie and fall to the index rule, and nvcc does
+// not flush subnormals in comparisons unless told to.  Boundary tiles hold
+// integer order keys with the out-of-field sentinel 0, and the minimum side
+// compares key - 1 so that the sentinel sorts last there too.
+template <bool kRaw>
+struct Ord;
+template <>
+struct Ord<true> {
+  static __device__ __forceinline__ bool ge(uint32_t b, uint32_t a) {
+    return __uint_as_float(b) >= __uint_as_float(a);
+  }
+  static __device__ __forceinline__ bool lt(uint32_t b, uint32_t a) {
+    return __uint_as_float(b) < __uint_as_float(a);
+  }
+  static __device__ __forceinline__ uint32_t mk(uint32_t k) { return k; }
+};
+template <>
+struct Ord<false> {
+  static __device__ __forceinline__ bool ge(uint32_t b, uint32_t a) { return b >= a; }
+  static __device__ __forceinline__ bool lt(uint32_t b, uint32_t a) { return b < a; }
+  static __device__ __forceinline__ uint32_t mk(uint32_t k) { return k - 1u; }
+};
+
+// b lies at higher vertex indices than a.
+template <bool kRaw>
+__device__ __forceinline__ Cand omax(Cand a, Cand b) {
+  const bool t = Ord<kRaw>::ge(b.k, a.k);
+  return Cand{t ? b.k : a.k, t ? b.i : a.i};
+}
+template <bool kRaw>
+__device__ __forceinline__ Cand omin(Cand a, Cand b) {
+  const bool t = Ord<kRaw>::lt(b.k, a.k);
+  return Cand{t ? b.k : a.k, t ? b.i : a.i};
+}
+
+// up / dn of the column (lx, ly, 0..TZ-1) from the staged values K into P,
+// streaming planes along z.  N(v) u {v} is the union of the unit cubes
+// [v, v+(1,1,1)] and [v-(1,1,1), v]; each cube's extremum is taken along x,
+// then y, then z.
+template <bool kRaw>
+__device__ __forceinline__ void steepest_column(const uint32_t *__restrict__ K, uint32_t *P,
+                                                int lx, int ly, bool col_in, int nz_here,
+                                                bool *nan) {
+  Cand hi_prev_max{}, hi_prev_min{}, lo_prev_max{}, lo_prev_min{}, lo_prev2_max{}, lo_prev2_min{};
+#pragma unroll 2
+  for (int p = 0; p < kTZ + 2; ++p) {
+    const int e = (lx + kXO) + kEX * ((ly + 1) + kEY * p);
+    const uint32_t kAm = K[e - kEX - 1], kA = K[e - kEX];
+    const uint32_t kBm = K[e - 1], kB = K[e], kBp = K[e + 1];
+    const uint32_t kC = K[e + kEX], kCp = K[e + kEX + 1];
+    if (kRaw && p >= 1 && p <= nz_here && col_in) *nan |= is_nan_bits(kB);
+    const uint32_t ue = (uint32_t)e;
+    const Cand h1hiB = omax<kRaw>(Cand{kB, ue}, Cand{kBp, ue + 1});
+    const Cand h1hiC = omax<kRaw>(Cand{kC, ue + kEX}, Cand{kCp, ue + kEX + 1});
+    const Cand h1loA = omax<kRaw>(Cand{kAm, ue - kEX - 1}, Cand{kA, ue - kEX});
+    const Cand h1loB = omax<kRaw>(Cand{kBm, ue - 1}, Cand{kB, ue});
+    const Cand h2hi_max = omax<kRaw>(h1hiB, h1hiC);
+    const Cand h2lo_max = omax<kRaw>(h1loA, h1loB);
+    typedef Ord<kRaw> O;
+    const Cand n1hiB = omin<kRaw>(Cand{O::mk(kB), ue}, Cand{O::mk(kBp), ue + 1});
+    const Cand n1hiC = omin<kRaw>(Cand{O::mk(kC), ue + kEX}, Cand{O::mk(kCp), ue + kEX + 1});
+    const Cand n1loA = omin<kRaw>(Cand{O::mk(kAm), ue - kEX - 1}, Cand{O::mk(kA), ue - kEX});
+    const Cand n1loB = omin<kRaw>(Cand{O::mk(kBm), ue - 1}, Cand{O::mk(kB), ue});
+    const Cand h2hi_min = omin<kRaw>(n1hiB, n1hiC);
+    const Cand h2lo_min = omin<kRaw>(n1loA, n1loB);
+    if (p >= 2) {
+      const int lz = p - 2;
+      const int ev = e - kEX * kEY;  // the vertex of plane p - 1
+      const Cand up =
+          omax<kRaw>(omax<kRaw>(lo_prev2_max, lo_prev_max), omax<kRaw>(hi_prev_max, h2hi_max));
+      const Cand dn =
+          omin<kRaw>(omin<kRaw>(lo_prev2_min, lo_prev_min), omin<kRaw>(hi_prev_min, h2hi_min));
+      P[ev] = (col_in && lz < nz_here) ? (up.i | (dn.i << 16)) : (uint32_t)ev * 0x10001u;
+    }
+    lo_prev2_max = lo_prev_max;
+    lo_prev2_min = lo_prev_min;
+    lo_prev_max = h2lo_max;
+    lo_prev_min = h2lo_min;
+    hi_prev_max = h2hi_max;
+    hi_prev_min = h2hi_min;
+  }
+}
+
+// First-fit insert of key into the open-addressing pair set H, starting at
+// slot s; returns the key's slot.
+__device__ __forceinline__ uint32_t pairset_insert(uint32_t *H, uint32_t key, uint32_t s) {
+  for (int probe = 0; probe < kHash; ++probe) {
+    uint32_t cur = H[s];
+    if (cur == kEmpty32) cur = atomicCAS(&H[s], kEmpty32, key);
+    if (cur == kEmpty32 || cur == key) return s;
+    s = (s + 1) & (kHash - 1);
+  }
+  return kEmpty32;  // unreachable: the set holds one slot per vertex
+}
+
 // One CTA per tile (persistent).  Thread (lane, warp) owns the z-column of
 // vertices (x0 + lane, y0 + warp, z0 .. z0 + TZ - 1).
 //
-// Shared memory (dynamic): K, the order keys of the tile and its halo in box
-// order (reused for the pair set once the steepest step is done), and P, the
-// up / dn pointers in the same order.
+// Shared memory (dynamic): K, the staged field values of the tile and its
+// halo in box order (reused for the pair set once the steepest step is
+// done), and P, the up / dn pointers in the same order.
 template <bool kTma>
 __global__ void __launch_bounds__(kThreads, 2)
     k_tile_local(const void *__restrict__ field, int dtype, TileGeom g, TiledScratch ts,
                  DevStatus *st, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) uint32_t dsmem[];
-  uint32_t *K = dsmem;         // kExt words: keys, then the kHash-word pair set
+  uint32_t *K = dsmem;         // kExt words: values / keys, then the kHash-word pair set
   uint32_t *H = dsmem;
   uint32_t *P = dsmem + kExt;  // kExt words: up | dn << 16, box indices
   __shared__ __align__(8) uint64_t s_bar;
@@ -165,7 +252,6 @@ __global__ void __launch_bounds__(kThreads, 2)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = lane, ly = warp;
   bool nan = false;
-  const int64_t plane = g.nx * g.ny;
   uint32_t parity = 0;
   if (kTma && threadIdx.x == 0) mbar_init(&s_bar, 1);
   __syncthreads();
@@ -173,6 +259,9 @@ __global__ void __launch_bounds__(kThreads, 2)
   for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
     int64_t x0, y0, z0;
     tile_origin(g, tile, &x0, &y0, &z0);
+    // tile and halo entirely inside the field: raw float comparisons
+    const bool raw = kTma && x0 >= 1 && y0 >= 1 && z0 >= 1 && x0 + kTX < g.nx &&
+                     y0 + kTY < g.ny && z0 + kTZ < g.nz;
 
     // ---- field values of the tile + halo into K
     if (kTma) {
@@ -191,144 +280,102 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
       parity ^= 1u;
     }
-    // ---- order keys in place (sentinel 0 outside the field); halo pointers
-    // are self-loops
+    // ---- boundary tiles: order keys in place (sentinel 0 outside the
+    // field).  All tiles: halo pointers are self-loops.
     {
-      const int64_t xl = x0 + lx;
-      const bool x_in = xl < g.nx;
       const int exe = lane == 0 ? kXO - 1 : kXO + kTX;  // lanes 0, 1: the halo columns
-      const int64_t xe = x0 + exe - kXO;
-      const bool xe_in = xe >= 0 && xe < g.nx;
+      const int64_t xl = x0 + lx, xe = x0 + exe - kXO;
+      const bool x_in = xl < g.nx, xe_in = xe >= 0 && xe < g.nx;
 #pragma unroll 4
       for (int r = warp; r < kEY * kEZ; r += kThreads / 32) {
         const int ey = r % kEY, ez = r / kEY;
-        const int64_t y = y0 + ey - 1, z = z0 + ez - 1;
-        const bool row_in = y >= 0 && y < g.ny && z >= 0 && z < g.nz;
-        const int64_t row = y * g.nx + z * plane;
-        const int eb = kEX * r;
-        uint32_t b, be = 0;
-        if (kTma) {
-          b = K[eb + kXO + lx];
-          if (lane < 2) be = K[eb + exe];
-        } else {
-          b = (row_in && x_in) ? raw_bits(field, dtype, row + xl) : 0u;
-          if (lane < 2 && row_in && xe_in) be = raw_bits(field, dtype, row + xe);
-        }
         const bool interior = ey >= 1 && ey <= kTY && ez >= 1 && ez <= kTZ;
-        if (row_in && x_in && interior) nan |= is_nan_bits(b);
-        K[eb + kXO + lx] = (row_in && x_in) ? key_of(b) : 0u;
-        if (lane < 2) K[eb + exe] = (row_in && xe_in) ? key_of(be) : 0u;
+        const int eb = kEX * r;
+        if (!raw) {
+          const int64_t y = y0 + ey - 1, z = z0 + ez - 1;
+          const bool row_in = y >= 0 && y < g.ny && z >= 0 && z < g.nz;
+          uint32_t b, be = 0;
+          if (kTma) {
+            b = K[eb + kXO + lx];
+            if (lane < 2) be = K[eb + exe];
+          } else {
+            const int64_t row = y * g.nx + z * g.nx * g.ny;
+            b = (row_in && x_in) ? raw_bits(field, dtype, row + xl) : 0u;
+            if (lane < 2 && row_in && xe_in) be = raw_bits(field, dtype, row + xe);
+          }
+          if (row_in && x_in && interior) nan |= is_nan_bits(b);
+          K[eb + kXO + lx] = (row_in && x_in) ? key_of(b) : 0u;
+          if (lane < 2) K[eb + exe] = (row_in && xe_in) ? key_of(be) : 0u;
+        }
         if (!interior) P[eb + kXO + lx] = (uint32_t)(eb + kXO + lx) * 0x10001u;
         if (lane < 2) P[eb + exe] = (uint32_t)(eb + exe) * 0x10001u;
       }
     }
     __syncthreads();
 
-    // ---- steepest neighbours from K, streaming the column along z
-    const int64_t x = x0 + lx, y = y0 + ly;
-    const bool col_in = x < g.nx && y < g.ny;
+    // ---- steepest neighbours
+    const bool col_in = x0 + lx < g.nx && y0 + ly < g.ny;
     const int nz_here = (int)min((int64_t)kTZ, g.nz - z0);
-    Cand hi_prev_max{}, hi_prev_min{}, lo_prev_max{}, lo_prev_min{}, lo_prev2_max{}, lo_prev2_min{};
-#pragma unroll 2
-    for (int p = 0; p < kTZ + 2; ++p) {
-      const int e = (lx + kXO) + kEX * ((ly + 1) + kEY * p);
-      const uint32_t kAm = K[e - kEX - 1], kA = K[e - kEX];
-      const uint32_t kBm = K[e - 1], kB = K[e], kBp = K[e + 1];
-      const uint32_t kC = K[e + kEX], kCp = K[e + kEX + 1];
-      const uint32_t ue = (uint32_t)e;
-      const Cand h1hiB = cmax(Cand{kB, ue}, Cand{kBp, ue + 1});
-      const Cand h1hiC = cmax(Cand{kC, ue + kEX}, Cand{kCp, ue + kEX + 1});
-      const Cand h1loA = cmax(Cand{kAm, ue - kEX - 1}, Cand{kA, ue - kEX});
-      const Cand h1loB = cmax(Cand{kBm, ue - 1}, Cand{kB, ue});
-      const Cand h2hi_max = cmax(h1hiB, h1hiC);
-      const Cand h2lo_max = cmax(h1loA, h1loB);
-      // min side: key - 1 sends the out-of-box key 0 to the top
-      const Cand n1hiB = cmin(Cand{kB - 1u, ue}, Cand{kBp - 1u, ue + 1});
-      const Cand n1hiC = cmin(Cand{kC - 1u, ue + kEX}, Cand{kCp - 1u, ue + kEX + 1});
-      const Cand n1loA = cmin(Cand{kAm - 1u, ue - kEX - 1}, Cand{kA - 1u, ue - kEX});
-      const Cand n1loB = cmin(Cand{kBm - 1u, ue - 1}, Cand{kB - 1u, ue});
-      const Cand h2hi_min = cmin(n1hiB, n1hiC);
-      const Cand h2lo_min = cmin(n1loA, n1loB);
-      if (p >= 2) {
-        const int lz = p - 2;
-        const int ev = e - kEX * kEY;  // the vertex of plane p - 1
-        const Cand up = cmax(cmax(lo_prev2_max, lo_prev_max), cmax(hi_prev_max, h2hi_max));
-        const Cand dn = cmin(cmin(lo_prev2_min, lo_prev_min), cmin(hi_prev_min, h2hi_min));
-        P[ev] = (col_in && lz < nz_here) ? (up.i | (dn.i << 16)) : (uint32_t)ev * 0x10001u;
-      }
-      lo_prev2_max = lo_prev_max;
-      lo_prev2_min = lo_prev_min;
-      lo_prev_max = h2lo_max;
-      lo_prev_min = h2lo_min;
-      hi_prev_max = h2hi_max;
-      hi_prev_min = h2hi_min;
+    if (raw)
+      steepest_column<true>(K, P, lx, ly, col_in, nz_here, &nan);
+    else
+      steepest_column<false>(K, P, lx, ly, col_in, nz_here, &nan);
+    if (__syncthreads_or(nan)) {
+      // the call fails with MS_ERR_NAN_INPUT; skip the rest of this tile
+      if (threadIdx.x == 0) ts.tile_count[tile] = 0;
+      __syncthreads();
+      continue;
     }
-    __syncthreads();
 
     // ---- path compression inside the tile.  Halo entries and extrema are
     // self-pointers, so every pointer ends on a local extremum or an exit.
     // Each thread keeps its own 16 pointers in registers (it alone writes
-    // them) and jumps them in place until done; its reads of other vertices'
-    // pointers may see them before or after their own jumps, and either lies
-    // on the same path.
+    // them) and jumps them in place until a pass changes nothing in its
+    // warp; reads of other vertices' pointers may see them before or after
+    // their own jumps, and either lies on the same path.
     for (int i = threadIdx.x; i < kHash; i += kThreads) H[i] = kEmpty32;
     uint32_t w[kTZ];
 #pragma unroll
     for (int lz = 0; lz < kTZ; ++lz) w[lz] = P[ext_of(lx, ly, lz)];
-    {
-      volatile uint32_t *VP = P;
-      uint32_t done = 0;
-      for (int it = 0; it < kExt; ++it) {
+    for (int it = 0; it < kExt; ++it) {
+      bool changed = false;
 #pragma unroll
-        for (int h = 0; h < kTZ; h += 8) {
-          uint32_t gu[8], gd[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const bool act = !(done & (1u << (h + j)));
-            gu[j] = act ? VP[w[h + j] & 0xffffu] : 0u;
-            gd[j] = act ? VP[w[h + j] >> 16] : 0u;
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int lz = h + j;
-            if (done & (1u << lz)) continue;
-            const uint32_t nw = (gu[j] & 0xffffu) | (gd[j] & 0xffff0000u);
-            if (nw != w[lz]) {
-              w[lz] = nw;
-              VP[ext_of(lx, ly, lz)] = nw;
-            } else {
-              done |= 1u << lz;
-            }
-          }
+      for (int lz = 0; lz < kTZ; ++lz) {
+        const uint32_t gu = P[w[lz] & 0xffffu], gd = P[w[lz] >> 16];
+        const uint32_t nw = __byte_perm(gu, gd, 0x7610);  // up of gu, dn of gd
+        if (nw != w[lz]) {
+          w[lz] = nw;
+          P[ext_of(lx, ly, lz)] = nw;
+          changed = true;
         }
-        if (__all_sync(0xffffffffu, done == 0xffffu)) break;
       }
+      if (!__any_sync(0xffffffffu, changed)) break;
     }
     __syncthreads();
 
-    // ---- distinct (up-root, dn-root) pairs of the tile; lanes of a warp
-    // with the same pair insert it once
-    uint32_t slots[kTZ];
+    // ---- distinct (up-root, dn-root) pairs of the tile: look each key up at
+    // its hash slot; only misses take the insert path, where lanes of a warp
+    // with the same key elect one to insert it
+    uint32_t slots[kTZ], cur[kTZ];
+#pragma unroll
+    for (int lz = 0; lz < kTZ; ++lz) {
+      slots[lz] = hash32(w[lz]);
+      cur[lz] = H[slots[lz]];
+    }
 #pragma unroll
     for (int lz = 0; lz < kTZ; ++lz) {
       const bool valid = col_in && lz < nz_here;
-      const uint32_t key = valid ? w[lz] : kEmpty32;
-      const unsigned peers = __match_any_sync(0xffffffffu, key);
-      const int leader = __ffs(peers) - 1;
-      uint32_t slot = kEmpty32;
-      if (valid && leader == lane) {
-        uint32_t s = hash32(key);
-        for (int probe = 0; probe < kHash; ++probe) {
-          uint32_t cur = H[s];
-          if (cur == kEmpty32) cur = atomicCAS(&H[s], kEmpty32, key);
-          if (cur == kEmpty32 || cur == key) {
-            slot = s;
-            break;
-          }
-          s = (s + 1) & (kHash - 1);
+      const bool need = valid && cur[lz] != w[lz];
+      if (__any_sync(0xffffffffu, need)) {
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if (need) {
+          const unsigned peers = __match_any_sync(m, w[lz]);
+          const int leader = __ffs(peers) - 1;
+          uint32_t sl = 0;
+          if (lane == leader) sl = pairset_insert(H, w[lz], slots[lz]);
+          slots[lz] = __shfl_sync(peers, sl, leader);
         }
       }
-      slots[lz] = __shfl_sync(0xffffffffu, slot, leader);
       if (!valid) slots[lz] = kEmpty32;
     }
     __syncthreads();
@@ -417,14 +464,14 @@ __device__ int32_t chase(const TileGeom &g, const TiledScratch &ts, int32_t r, b
                          DevStatus *st) {
   for (int64_t hop = 0; hop <= g.ntiles; ++hop) {
     if (!(r & kExitFlag)) return r;
-    const int64_t e = r & ~kExitFlag;
-    const int64_t x = e % g.nx, q = e / g.nx, y = q % g.ny, z = q / g.ny;
-    const int64_t tile = (x / kTX) + g.tx * ((y / kTY) + g.ty * (z / kTZ));
-    int64_t x0, y0, z0;
-    tile_origin(g, tile, &x0, &y0, &z0);
+    uint32_t q, x, y, z;
+    g.div_nx.divmod((uint32_t)(r & ~kExitFlag), &q, &x);
+    g.div_ny.divmod(q, &z, &y);
+    const int64_t tile = (int64_t)(x / kTX) + g.tx * ((int64_t)(y / kTY) + g.ty * (int64_t)(z / kTZ));
+    const int64_t x0 = x - x % kTX, y0 = y - y % kTY, z0 = z - z % kTZ;
     const int fs = face_slot((int)(x - x0), (int)(y - y0), (int)(z - z0));
     if (fs < 0) break;
-    const uint32_t w = ts.face[tile * (int64_t)kFace + fs];
+    const uint32_t w = __ldg(&ts.face[tile * (int64_t)kFace + fs]);
     const int loc = up ? (int)(w & 0xffffu) : (int)(w >> 16);
     r = (int32_t)ext_to_global(g, x0, y0, z0, loc) | (ext_is_halo(loc) ? kExitFlag : 0);
   }
@@ -453,17 +500,21 @@ __global__ void k_resolve_pairs(TileGeom g, TiledScratch ts, RankScratch rs, Dev
       const int2 r = ts.pool_roots[p];
       const int32_t a = chase(g, ts, r.x, false, st);
       const int32_t d = chase(g, ts, r.y, true, st);
-      ts.pool_final[p] = make_int4(a, d, -1, 0);
       key = ((unsigned long long)(uint32_t)a << 32) | (uint32_t)d;
     }
     const unsigned int peers = __match_any_sync(0xffffffffu, key);
-    if (key != ~0ull && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) {
+    const int leader = __ffs(peers) - 1;
+    unsigned int slot_out = 0xffffffffu;
+    if (key != ~0ull && leader == (int)(threadIdx.x & 31)) {
       // insert into the global pair set
       const unsigned int mask = rs.capacity - 1u;
       unsigned int slot = (unsigned int)mix64t(key) & mask;
       for (unsigned int probe = 0; probe < rs.capacity; ++probe) {
         unsigned long long cur = *(volatile unsigned long long *)&rs.table_keys[slot];
-        if (cur == key) break;
+        if (cur == key) {
+          slot_out = slot;
+          break;
+        }
         if (cur == ~0ull) {
           cur = atomicCAS(&rs.table_keys[slot], ~0ull, key);
           if (cur == ~0ull) {
@@ -472,37 +523,31 @@ __global__ void k_resolve_pairs(TileGeom g, TiledScratch ts, RankScratch rs, Dev
               rs.list[at] = key;
             else
               atomicOr(&st->hash_overflow, 1u);
+            slot_out = slot;
             break;
           }
-          if (cur == key) break;
+          if (cur == key) {
+            slot_out = slot;
+            break;
+          }
         }
         slot = (slot + 1u) & mask;
       }
+      if (slot_out == 0xffffffffu) atomicOr(&st->hash_overflow, 1u);
     }
+    slot_out = __shfl_sync(0xffffffffu, slot_out, leader);
+    if (key != ~0ull)
+      ts.pool_final[p] = make_int4((int)(key >> 32), (int)(uint32_t)key, -1, (int)slot_out);
   }
 }
 
 __global__ void k_pair_ids(TiledScratch ts, RankScratch rs) {
-  const unsigned long long npairs = *ts.pool_count;
+  const unsigned long long npairs = min(*ts.pool_count, ts.pool_cap);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-       p < npairs && p < ts.pool_cap; p += stride) {
-    int4 f = ts.pool_final[p];
-    const unsigned long long key = ((unsigned long long)(uint32_t)f.x << 32) | (uint32_t)f.y;
-    const unsigned int mask = rs.capacity - 1u;
-    unsigned int slot = (unsigned int)mix64t(key) & mask;
-    int r = -1;
-    for (unsigned int probe = 0; probe < rs.capacity; ++probe) {
-      const unsigned long long cur = rs.table_keys[slot];
-      if (cur == key) {
-        r = rs.table_vals[slot];
-        break;
-      }
-      if (cur == ~0ull) break;
-      slot = (slot + 1u) & mask;
-    }
-    f.z = r;
-    ts.pool_final[p] = f;
+  for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < npairs;
+       p += stride) {
+    const int slot = ts.pool_final[p].w;
+    ts.pool_final[p].z = rs.table_vals[slot];
   }
 }
 
@@ -571,6 +616,10 @@ TileGeom tile_geom(const int64_t dims[3]) {
   g.ty = (g.ny + kTY - 1) / kTY;
   g.tz = (g.nz + kTZ - 1) / kTZ;
   g.ntiles = g.tx * g.ty * g.tz;
+  g.div_nx = FastDivU32((uint32_t)g.nx);
+  g.div_ny = FastDivU32((uint32_t)g.ny);
+  g.div_tx = FastDivU32((uint32_t)g.tx);
+  g.div_ty = FastDivU32((uint32_t)g.ty);
   return g;
 }
 

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 
+#include "fastdiv.h"
 #include "ms_internal.cuh"
 
 namespace msseg {
@@ -31,13 +32,14 @@ static_assert(kHash >= kTileV, "pair table must hold one pair per vertex");
 struct TileGeom {
   int64_t nx, ny, nz;
   int64_t tx, ty, tz, ntiles;
+  FastDivU32 div_nx, div_ny, div_tx, div_ty;  // coordinates from linear indices
 };
 
 struct TiledScratch {
   unsigned long long *pool_count;  // pairs reserved by all tiles
   unsigned long long pool_cap;
   int2 *pool_roots;   // per tile pair: (dn-root, up-root), global index | kExitFlag if an exit
-  int4 *pool_final;   // per tile pair: (asc, desc, ms, 0)
+  int4 *pool_final;   // per tile pair: (asc, desc, ms, slot of the pair in the global set)
   long long *tile_base;
   int32_t *tile_count;
   uint32_t *face;     // per tile kFace words: up-root | dn-root << 16 (extended-box indices)

@@ -309,3 +309,29 @@ def test_tile_boundaries(ctx, dims):
                               sf.random_ties(dims, 22, levels=2),
                               sf.broad_gaussians_ramp(dims, 23, sigma=20.0)]):
         run_and_compare(ctx, f, f"tile boundary {dims} case {seed}")
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_interior_tiles_signed_zero_and_subnormals(ctx, seed):
+    """Tiles whose halo lies inside the field compare raw float values; the
+    order there must still tie -0 with +0 (broken by index) and order
+    subnormals exactly.  The grid has interior and boundary tiles."""
+    dims = (100, 52, 50)
+    g = sf.rng_for(100 + seed)
+    tiny = np.float32(1.4e-45)
+    f = (g.integers(-3, 4, size=(50, 52, 100)).astype(np.float32) * tiny)
+    zeros = g.uniform(size=f.shape) < 0.3
+    f[zeros] = np.where(g.uniform(size=zeros.sum()) < 0.5, np.float32(0.0), np.float32(-0.0))
+    run_and_compare(ctx, f, f"subnormal/zero field seed {seed}")
+    # the same with infinities sprinkled in
+    inf = g.uniform(size=f.shape) < 0.01
+    f[inf] = np.where(g.uniform(size=inf.sum()) < 0.5, np.float32(np.inf), np.float32(-np.inf))
+    run_and_compare(ctx, f, f"subnormal/zero/inf field seed {seed}")
+
+
+def test_nan_in_interior_tile(ctx):
+    f = sf.smoothed_noise((100, 52, 50), 3, sigma=3.0)
+    f[25, 26, 50] = np.nan
+    with pytest.raises(ms.MSError) as e:
+        gpu_segment(ctx, f)
+    assert e.value.name == "MS_ERR_NAN_INPUT"
