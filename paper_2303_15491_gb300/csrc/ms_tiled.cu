@@ -82,6 +82,67 @@ __device__ __forceinline__ int face_slot(int lx, int ly, int lz) {
   return -1;
 }
 
+// Inverse of face_slot's layout: the vertex a face slot describes.
+__device__ __forceinline__ void face_coords(int fs, int *lx, int *ly, int *lz) {
+  constexpr int kZ = kTX * kTY, kY = kTX * kTZ, kX = kTY * kTZ;
+  if (fs < 2 * kZ) {
+    *lz = fs < kZ ? 0 : kTZ - 1;
+    const int r = fs % kZ;
+    *lx = r % kTX;
+    *ly = r / kTX;
+  } else if (fs < 2 * kZ + 2 * kY) {
+    const int q = fs - 2 * kZ;
+    *ly = q < kY ? 0 : kTY - 1;
+    const int r = q % kY;
+    *lx = r % kTX;
+    *lz = r / kTX;
+  } else {
+    const int q = fs - 2 * kZ - 2 * kY;
+    *lx = q < kX ? 0 : kTX - 1;
+    const int r = q % kX;
+    *ly = r % kTY;
+    *lz = r / kTY;
+  }
+}
+
+// Exclusive block scan of two values per thread (kThreads threads); also
+// returns both totals.  Uses scratch[2][kThreads / 32]; ends with a barrier.
+__device__ __forceinline__ void block_scan2(int a, int b, int *ea, int *eb, int *ta, int *tb,
+                                            int (*scratch)[kThreads / 32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int xa = __shfl_up_sync(0xffffffffu, ia, o);
+    const int xb = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) {
+      ia += xa;
+      ib += xb;
+    }
+  }
+  if (lane == 31) {
+    scratch[0][warp] = ia;
+    scratch[1][warp] = ib;
+  }
+  __syncthreads();
+  int pa = 0, pb = 0, sa = 0, sb = 0;
+#pragma unroll
+  for (int k = 0; k < kThreads / 32; ++k) {
+    const int va = scratch[0][k], vb = scratch[1][k];
+    if (k < warp) {
+      pa += va;
+      pb += vb;
+    }
+    sa += va;
+    sb += vb;
+  }
+  *ea = pa + ia - a;
+  *eb = pb + ib - b;
+  *ta = sa;
+  *tb = sb;
+  __syncthreads();
+}
+
 __device__ __forceinline__ uint32_t hash32(uint32_t k) { return (k * 0x9E3779B1u) >> (32 - kHashBits); }
 
 // Order key of one field value (Sec. 4.1): see order_key_bits; written
@@ -243,16 +304,17 @@ __global__ void __launch_bounds__(kThreads, 2)
     k_tile_local(const void *__restrict__ field, int dtype, TileGeom g, TiledScratch ts,
                  DevStatus *st, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) uint32_t dsmem[];
-  uint32_t *K = dsmem;         // kExt words: values / keys, then the kHash-word pair set
-  uint32_t *H = dsmem;
+  uint32_t *K = dsmem;         // kExt words: values / keys, then pair-numbering scratch
   uint32_t *P = dsmem + kExt;  // kExt words: up | dn << 16, box indices
   __shared__ __align__(8) uint64_t s_bar;
-  __shared__ int s_scan[kThreads / 32];
   __shared__ long long s_base;
+  __shared__ int s_abort;
+  __shared__ int s_scan2[2][kThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = lane, ly = warp;
   bool nan = false;
   uint32_t parity = 0;
+  if (threadIdx.x == 0) s_abort = 0;
   if (kTma && threadIdx.x == 0) mbar_init(&s_bar, 1);
   __syncthreads();
 
@@ -271,13 +333,19 @@ __global__ void __launch_bounds__(kThreads, 2)
         mbar_expect_tx(&s_bar, (uint32_t)(kExt * 4));
         tma_load_box(K, &tmap, &s_bar, (int)(x0 - kXO), (int)(y0 - 1), (int)(z0 - 1));
       }
-      long long polls = 0;
-      while (!mbar_try_wait(&s_bar, parity)) {
-        if (++polls > kWaitPolls) {
-          if (threadIdx.x == 0) atomicOr(&st->timeout, 1u);
-          return;
+      if (threadIdx.x == 0) {
+        long long polls = 0;
+        while (!mbar_try_wait(&s_bar, parity)) {
+          if (++polls > kWaitPolls) {
+            atomicOr(&st->timeout, 1u);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(64);
         }
       }
+      __syncthreads();
+      if (s_abort) return;  // block-uniform
       parity ^= 1u;
     }
     // ---- boundary tiles: order keys in place (sentinel 0 outside the
@@ -333,7 +401,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     // them) and jumps them in place until a pass changes nothing in its
     // warp; reads of other vertices' pointers may see them before or after
     // their own jumps, and either lies on the same path.
-    for (int i = threadIdx.x; i < kHash; i += kThreads) H[i] = kEmpty32;
     uint32_t w[kTZ];
 #pragma unroll
     for (int lz = 0; lz < kTZ; ++lz) w[lz] = P[ext_of(lx, ly, lz)];
@@ -353,105 +420,202 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     __syncthreads();
 
-    // ---- distinct (up-root, dn-root) pairs of the tile: look each key up at
-    // its hash slot; only misses take the insert path, where lanes of a warp
-    // with the same key elect one to insert it
-    uint32_t slots[kTZ], cur[kTZ];
-#pragma unroll
-    for (int lz = 0; lz < kTZ; ++lz) {
-      slots[lz] = hash32(w[lz]);
-      cur[lz] = H[slots[lz]];
+    // ---- face roots (final pointers of the tile's face vertices), written
+    // cooperatively from P: other tiles' paths enter through these vertices
+    {
+      uint32_t *face = ts.face + tile * (int64_t)kFace;
+      for (int fs = threadIdx.x; fs < kFace; fs += kThreads) {
+        int fx, fy, fz;
+        face_coords(fs, &fx, &fy, &fz);
+        if (x0 + fx < g.nx && y0 + fy < g.ny && fz < nz_here) face[fs] = P[ext_of(fx, fy, fz)];
+      }
     }
+    __syncthreads();
+
+    // ---- distinct (up-root, dn-root) pairs of the tile.  Roots are box
+    // positions: flag them, rank the flags with popcounts (dense root ids),
+    // flag the (up id, dn id) cells of a dense table and rank those.  No
+    // atomics; tiles with too many roots for the table use a hash set.
+    uint8_t *FU = reinterpret_cast<uint8_t *>(K);
+    uint8_t *FD = FU + kExt;
+    uint32_t *WU = K + (2 * kExt) / 4, *WD = WU + kBoxWords;  // after the flag bytes
+    uint32_t *PU = WD + kBoxWords, *PDp = PU + kBoxWords;
+    for (int i = threadIdx.x; i < kExt / 2; i += kThreads) reinterpret_cast<uint32_t *>(K)[i] = 0u;
+    __syncthreads();
 #pragma unroll
     for (int lz = 0; lz < kTZ; ++lz) {
-      const bool valid = col_in && lz < nz_here;
-      const bool need = valid && cur[lz] != w[lz];
-      if (__any_sync(0xffffffffu, need)) {
-        const unsigned m = __ballot_sync(0xffffffffu, need);
-        if (need) {
-          const unsigned peers = __match_any_sync(m, w[lz]);
-          const int leader = __ffs(peers) - 1;
-          uint32_t sl = 0;
-          if (lane == leader) sl = pairset_insert(H, w[lz], slots[lz]);
-          slots[lz] = __shfl_sync(peers, sl, leader);
+      if (col_in && lz < nz_here) {
+        FU[w[lz] & 0xffffu] = 1;
+        FD[w[lz] >> 16] = 1;
+      }
+    }
+    __syncthreads();
+    for (int j = warp; j < 2 * kBoxWords; j += kThreads / 32) {
+      const uint8_t *F = j < kBoxWords ? FU : FD;
+      const int jj = j < kBoxWords ? j : j - kBoxWords;
+      const int pos = 32 * jj + lane;
+      const unsigned bits = __ballot_sync(0xffffffffu, pos < kExt && F[pos] != 0);
+      if (lane == 0) (j < kBoxWords ? WU : WD)[jj] = bits;
+    }
+    __syncthreads();
+    int nU, nD;
+    {
+      const int cu = threadIdx.x < kBoxWords ? __popc(WU[threadIdx.x]) : 0;
+      const int cd = threadIdx.x < kBoxWords ? __popc(WD[threadIdx.x]) : 0;
+      int eu, ed;
+      block_scan2(cu, cd, &eu, &ed, &nU, &nD, s_scan2);
+      if (threadIdx.x < kBoxWords) {
+        PU[threadIdx.x] = eu;
+        PDp[threadIdx.x] = ed;
+      }
+    }
+    const bool dense = nU <= kMaxRoots && nD <= kMaxRoots && nU * nD <= kMaxCells;
+    __syncthreads();
+    uint32_t cell[kTZ];
+    if (dense) {
+      uint16_t *inv_u = reinterpret_cast<uint16_t *>(P);
+      uint16_t *inv_d = inv_u + kMaxRoots;
+      uint8_t *PA = reinterpret_cast<uint8_t *>(P + kMaxRoots);
+      uint32_t *PAW = P + kMaxRoots + kMaxCells / 4, *PAP = PAW + kMaxCells / 32;
+      if (threadIdx.x < kBoxWords) {
+        for (int d = 0; d < 2; ++d) {
+          uint32_t bits = d ? WD[threadIdx.x] : WU[threadIdx.x];
+          int k = d ? PDp[threadIdx.x] : PU[threadIdx.x];
+          uint16_t *inv = d ? inv_d : inv_u;
+          while (bits) {
+            const int b = __ffs(bits) - 1;
+            inv[k++] = (uint16_t)(32 * threadIdx.x + b);
+            bits &= bits - 1;
+          }
         }
       }
-      if (!valid) slots[lz] = kEmpty32;
-    }
-    __syncthreads();
-    // number the used slots: thread t owns slots t, t + 512, ...; ids follow
-    // (thread, slot) order through a block scan of the per-thread counts
-    constexpr int kPer = kHash / kThreads;
-    int cnt = 0;
+      const int ncell = nU * nD;
+      for (int i = threadIdx.x; i < (ncell + 3) / 4; i += kThreads)
+        reinterpret_cast<uint32_t *>(PA)[i] = 0u;
+      __syncthreads();
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) cnt += H[threadIdx.x + kThreads * j] != kEmpty32;
-    int incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_scan[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      int v = lane < kThreads / 32 ? s_scan[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
+      for (int lz = 0; lz < kTZ; ++lz) {
+        const uint32_t ru = w[lz] & 0xffffu, rd = w[lz] >> 16;
+        const int iu = PU[ru >> 5] + __popc(WU[ru >> 5] & ((1u << (ru & 31)) - 1u));
+        const int id = PDp[rd >> 5] + __popc(WD[rd >> 5] & ((1u << (rd & 31)) - 1u));
+        cell[lz] = (uint32_t)(iu * nD + id);
+        if (col_in && lz < nz_here) PA[cell[lz]] = 1;
       }
-      if (lane < kThreads / 32) s_scan[lane] = v;  // inclusive per warp
-      if (lane == kThreads / 32 - 1) {
-        const long long total = v;
+      __syncthreads();
+      const int nwc = (ncell + 31) / 32;
+      for (int j = warp; j < nwc; j += kThreads / 32) {
+        const int pos = 32 * j + lane;
+        const unsigned bits = __ballot_sync(0xffffffffu, pos < ncell && PA[pos] != 0);
+        if (lane == 0) PAW[j] = bits;
+      }
+      __syncthreads();
+      int npairs;
+      {
+        const int c = threadIdx.x < nwc ? __popc(PAW[threadIdx.x]) : 0;
+        int e, dummy_e, dummy_t;
+        block_scan2(c, 0, &e, &dummy_e, &npairs, &dummy_t, s_scan2);
+        if (threadIdx.x < nwc) PAP[threadIdx.x] = e;
+        if (threadIdx.x == 0) {
+          const long long b = (long long)atomicAdd(ts.pool_count, (unsigned long long)npairs);
+          s_base = b;
+          ts.tile_base[tile] = b;
+          ts.tile_count[tile] = npairs;
+        }
+      }
+      __syncthreads();
+      const long long base = s_base;
+      if (threadIdx.x < nwc) {
+        uint32_t bits = PAW[threadIdx.x];
+        int k = PAP[threadIdx.x];
+        while (bits) {
+          const int b = __ffs(bits) - 1;
+          const int pos = 32 * threadIdx.x + b;
+          const int iu = pos / nD, id = pos - iu * nD;
+          const long long at = base + k;
+          if (at < (long long)ts.pool_cap) {
+            const int u = inv_u[iu], d = inv_d[id];
+            const int64_t gu = ext_to_global(g, x0, y0, z0, u);
+            const int64_t gd = ext_to_global(g, x0, y0, z0, d);
+            ts.pool_roots[at] = make_int2((int)gd | (ext_is_halo(d) ? kExitFlag : 0),
+                                          (int)gu | (ext_is_halo(u) ? kExitFlag : 0));
+          } else {
+            atomicOr(&st->pool_overflow, 1u);
+          }
+          ++k;
+          bits &= bits - 1;
+        }
+      }
+#pragma unroll
+      for (int lz = 0; lz < kTZ; ++lz) {
+        const uint32_t c = (col_in && lz < nz_here) ? cell[lz] : 0u;
+        cell[lz] = PAP[c >> 5] + __popc(PAW[c >> 5] & ((1u << (c & 31)) - 1u));
+      }
+    } else {
+      // many roots: open-addressing hash set of the 32-bit root pairs in K
+      uint32_t *H = K;
+      for (int i = threadIdx.x; i < kHash; i += kThreads) H[i] = kEmpty32;
+      __syncthreads();
+#pragma unroll
+      for (int lz = 0; lz < kTZ; ++lz) {
+        const bool valid = col_in && lz < nz_here;
+        const uint32_t key = valid ? w[lz] : kEmpty32;
+        const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+        const bool lead = valid && (lane == 0 || prev != key);
+        uint32_t sl = kEmpty32;
+        if (lead) sl = pairset_insert(H, key, hash32(key));
+        const unsigned leaders = __ballot_sync(0xffffffffu, lead || !valid);
+        const int src = 31 - __clz(leaders & (0xffffffffu >> (31 - lane)));
+        sl = __shfl_sync(0xffffffffu, sl, src);
+        cell[lz] = valid ? sl : 0u;
+      }
+      __syncthreads();
+      // number the used slots: thread t owns slots t, t + 512, ...
+      constexpr int kPer = kHash / kThreads;
+      int cnt = 0;
+#pragma unroll
+      for (int j = 0; j < kPer; ++j) cnt += H[threadIdx.x + kThreads * j] != kEmpty32;
+      int ex, dummy_e, total, dummy_t;
+      block_scan2(cnt, 0, &ex, &dummy_e, &total, &dummy_t, s_scan2);
+      if (threadIdx.x == 0) {
         const long long b = (long long)atomicAdd(ts.pool_count, (unsigned long long)total);
         s_base = b;
         ts.tile_base[tile] = b;
-        ts.tile_count[tile] = (int32_t)total;
+        ts.tile_count[tile] = total;
       }
-    }
-    __syncthreads();
-    const long long base = s_base;
-    int id = (warp > 0 ? s_scan[warp - 1] : 0) + incl - cnt;
+      __syncthreads();
+      const long long base = s_base;
+      int id = ex;
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const int s = threadIdx.x + kThreads * j;
-      const uint32_t key = H[s];
-      if (key == kEmpty32) continue;
-      const long long at = base + id;
-      if (at < (long long)ts.pool_cap) {
-        const int u = (int)(key & 0xffffu), d = (int)(key >> 16);
-        const int64_t gu = ext_to_global(g, x0, y0, z0, u);
-        const int64_t gd = ext_to_global(g, x0, y0, z0, d);
-        ts.pool_roots[at] = make_int2((int)gd | (ext_is_halo(d) ? kExitFlag : 0),
-                                      (int)gu | (ext_is_halo(u) ? kExitFlag : 0));
-      } else {
-        atomicOr(&st->pool_overflow, 1u);
+      for (int j = 0; j < kPer; ++j) {
+        const int sl = threadIdx.x + kThreads * j;
+        const uint32_t key = H[sl];
+        if (key == kEmpty32) continue;
+        const long long at = base + id;
+        if (at < (long long)ts.pool_cap) {
+          const int u = (int)(key & 0xffffu), d = (int)(key >> 16);
+          const int64_t gu = ext_to_global(g, x0, y0, z0, u);
+          const int64_t gd = ext_to_global(g, x0, y0, z0, d);
+          ts.pool_roots[at] = make_int2((int)gd | (ext_is_halo(d) ? kExitFlag : 0),
+                                        (int)gu | (ext_is_halo(u) ? kExitFlag : 0));
+        } else {
+          atomicOr(&st->pool_overflow, 1u);
+        }
+        H[sl] = (uint32_t)id;
+        ++id;
       }
-      H[s] = (uint32_t)id;
-      ++id;
+      __syncthreads();
+#pragma unroll
+      for (int lz = 0; lz < kTZ; ++lz) cell[lz] = H[cell[lz]];
     }
-    __syncthreads();
-    // per-vertex pair numbers (the column's 16 numbers are contiguous) and
-    // the face roots (the column's final pointers)
+    // per-vertex pair numbers: the column's 16 numbers are one 32-byte vector
     if (col_in) {
       uint32_t packed[kTZ / 2];
 #pragma unroll
-      for (int lz = 0; lz < kTZ; lz += 2) {
-        const uint32_t a = slots[lz] == kEmpty32 ? 0u : H[slots[lz]];
-        const uint32_t b = slots[lz + 1] == kEmpty32 ? 0u : H[slots[lz + 1]];
-        packed[lz / 2] = (a & 0xffffu) | (b << 16);
-      }
+      for (int lz = 0; lz < kTZ; lz += 2) packed[lz / 2] = (cell[lz] & 0xffffu) | (cell[lz + 1] << 16);
       uint4 *pid4 = reinterpret_cast<uint4 *>(ts.pid + tile * (int64_t)kTileV +
                                               (int64_t)(ly * kTX + lx) * kTZ);
       pid4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
       pid4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
-      uint32_t *face = ts.face + tile * (int64_t)kFace;
-      const bool side = lx == 0 || lx == kTX - 1 || ly == 0 || ly == kTY - 1;
-#pragma unroll
-      for (int lz = 0; lz < kTZ; ++lz) {
-        if (lz >= nz_here) break;
-        if (side || lz == 0 || lz == kTZ - 1) face[face_slot(lx, ly, lz)] = w[lz];
-      }
     }
     __syncthreads();
   }
