@@ -139,6 +139,35 @@ ms_status ms_pair_rank(ms_ctx *ctx, const int32_t *asc, const int32_t *desc, int
                        int32_t *ms, int64_t *k_out);
 
 
+/* ---- step 4 without allocation --------------------------------------------- */
+
+/* Largest n that ms_pair_rank_noalloc accepts (64^3 vertices). */
+#define MS_NOALLOC_MAX_N 262144
+
+/* MS ids exactly as ms_pair_rank computes them, for callers that cannot
+ * allocate device memory -- code running where a memory pool or framework
+ * owns the whole device, or a latency-critical loop that cannot afford the
+ * synchronisation and possible failure of cudaMalloc.  The paper has no
+ * counterpart: this is an interface convenience, not part of the method.
+ *
+ * asc, desc: int32[n] device arrays with values in [0, n); ms: int32[n]
+ * device output; *k_out (may be NULL) receives K; cuda_stream: the stream to
+ * run on (NULL = the legacy default stream).  Needs no ms_ctx.  n above
+ * MS_NOALLOC_MAX_N gives MS_ERR_TOO_LARGE, values outside [0, n)
+ * MS_ERR_INVALID_ARG.  The call returns after its work has completed.
+ *
+ * Its working memory is one static device array of about 10.3 MB inside the
+ * library (hash set, sort buffers and a status block), which every GPU that
+ * loads the library holds until the process exits; the call itself performs
+ * no cudaMalloc / cudaFree and calls no allocating routine.  The first call
+ * on a device looks the array's device address up (cudaGetSymbolAddress) and
+ * caches it, so make that first call before any stream capture on the
+ * device.  Every call reuses the same array: the call clears what must start
+ * empty, but calls that overlap on the GPU (two streams, two threads) race on
+ * it and must be serialised by the caller. */
+ms_status ms_pair_rank_noalloc(const int32_t *asc, const int32_t *desc, int64_t n, int32_t *ms,
+                               int64_t *k_out, void *cuda_stream);
+
 /* ---- measurement ---------------------------------------------------------- */
 
 /* Stages of one segmentation, as timed by the profiler.  For ms_segment:

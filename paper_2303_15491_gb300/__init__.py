@@ -24,6 +24,7 @@ __all__ = [
     "ms_segment", "ms_segment_host", "ms_last_region_count", "ms_order_keys", "ms_steepest",
     "ms_compress", "ms_pair_rank", "segment", "EXPORTED_SYMBOLS", "ms_profile_enable",
     "ms_profile_read", "ms_profile_stage_name", "STAGES", "ms_segment_staged",
+    "ms_pair_rank_noalloc", "MS_NOALLOC_MAX_N",
 ]
 
 MS_F32, MS_F16 = 0, 1
@@ -35,7 +36,9 @@ EXPORTED_SYMBOLS = [
     "ms_status_string", "ms_create", "ms_destroy", "ms_segment", "ms_segment_host",
     "ms_last_region_count", "ms_order_keys", "ms_steepest", "ms_compress", "ms_pair_rank",
     "ms_profile_enable", "ms_profile_read", "ms_profile_stage_name", "ms_segment_staged",
+    "ms_pair_rank_noalloc",
 ]
+MS_NOALLOC_MAX_N = 262144
 STAGES = ["tile_local", "resolve", "write", "h2d", "d2h"]
 
 
@@ -79,6 +82,7 @@ def load(build: bool = True) -> ctypes.CDLL:
             L.ms_steepest.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp]
             L.ms_compress.argtypes = [c_vp, c_vp, ctypes.c_int64]
             L.ms_pair_rank.argtypes = [c_vp, c_vp, c_vp, ctypes.c_int64, c_vp, c_i64p]
+            L.ms_pair_rank_noalloc.argtypes = [c_vp, c_vp, ctypes.c_int64, c_vp, c_i64p, c_vp]
             L.ms_profile_enable.argtypes = [c_vp, ctypes.c_int]
             L.ms_profile_read.argtypes = [c_vp, ctypes.POINTER(_Profile)]
             L.ms_profile_stage_name.argtypes = [ctypes.c_int]
@@ -189,6 +193,17 @@ def ms_pair_rank(ctx, asc, desc, n, ms) -> int:
     k = ctypes.c_int64(0)
     _check(load().ms_pair_rank(ctx, _ptr(asc), _ptr(desc), int(n), _ptr(ms), ctypes.byref(k)),
            "ms_pair_rank")
+    return int(k.value)
+
+
+def ms_pair_rank_noalloc(asc, desc, n, ms, stream=None) -> int:
+    """MS ids of (asc, desc) without allocating device memory (n <=
+    MS_NOALLOC_MAX_N); returns K.  ``stream``: torch.cuda.Stream, raw
+    cudaStream_t int, or None for the default stream."""
+    k = ctypes.c_int64(0)
+    s = getattr(stream, "cuda_stream", stream)
+    _check(load().ms_pair_rank_noalloc(_ptr(asc), _ptr(desc), int(n), _ptr(ms), ctypes.byref(k),
+                                       s if s else None), "ms_pair_rank_noalloc")
     return int(k.value)
 
 
