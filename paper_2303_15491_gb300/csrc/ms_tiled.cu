@@ -82,6 +82,19 @@ __device__ __forceinline__ int face_slot(int lx, int ly, int lz) {
   return -1;
 }
 
+// Reference to a tile root at box index e: its global vertex index, with
+// kExitFlag set when e lies in the halo (the path continues in another tile).
+__device__ __forceinline__ int32_t root_ref(const TileGeom &g, int64_t x0, int64_t y0, int64_t z0,
+                                            int e) {
+  const uint32_t ue = (uint32_t)e;
+  const uint32_t ez = ue / (kEX * kEY), r = ue - ez * (kEX * kEY);
+  const uint32_t ey = r / kEX, ex = r - ey * kEX;
+  const bool halo = ex == kXO - 1 || ex == kXO + kTX || ey == 0 || ez == 0 || ey == kEY - 1 ||
+                    ez == kEZ - 1;
+  const int64_t v = (x0 + (int)ex - kXO) + g.nx * ((y0 + (int)ey - 1) + g.ny * (z0 + (int)ez - 1));
+  return (int32_t)v | (halo ? kExitFlag : 0);
+}
+
 // Inverse of face_slot's layout: the vertex a face slot describes.
 __device__ __forceinline__ void face_coords(int fs, int *lx, int *ly, int *lz) {
   constexpr int kZ = kTX * kTY, kY = kTX * kTZ, kX = kTY * kTZ;
@@ -432,181 +445,98 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
     __syncthreads();
 
-    // ---- distinct (up-root, dn-root) pairs of the tile.  Roots are box
-    // positions: flag them, rank the flags with popcounts (dense root ids),
-    // flag the (up id, dn id) cells of a dense table and rank those.  No
-    // atomics; tiles with too many roots for the table use a hash set.
-    uint8_t *FU = reinterpret_cast<uint8_t *>(K);
-    uint8_t *FD = FU + kExt;
-    uint32_t *WU = K + (2 * kExt) / 4, *WD = WU + kBoxWords;  // after the flag bytes
-    uint32_t *PU = WD + kBoxWords, *PDp = PU + kBoxWords;
-    for (int i = threadIdx.x; i < kExt / 2; i += kThreads) reinterpret_cast<uint32_t *>(K)[i] = 0u;
-    __syncthreads();
-#pragma unroll
-    for (int lz = 0; lz < kTZ; ++lz) {
-      if (col_in && lz < nz_here) {
-        FU[w[lz] & 0xffffu] = 1;
-        FD[w[lz] >> 16] = 1;
-      }
-    }
-    __syncthreads();
-    for (int j = warp; j < 2 * kBoxWords; j += kThreads / 32) {
-      const uint8_t *F = j < kBoxWords ? FU : FD;
-      const int jj = j < kBoxWords ? j : j - kBoxWords;
-      const int pos = 32 * jj + lane;
-      const unsigned bits = __ballot_sync(0xffffffffu, pos < kExt && F[pos] != 0);
-      if (lane == 0) (j < kBoxWords ? WU : WD)[jj] = bits;
-    }
-    __syncthreads();
-    int nU, nD;
+    // ---- distinct (up-root, dn-root) pairs of the tile, with uniform work:
+    // (1) in each warp row, the first lane of every run of equal pairs is the
+    //     run's leader and appends the pair to its warp's candidate list;
+    //     every vertex remembers its run's candidate index;
+    // (2) each warp inserts its candidates into an open-addressing set H;
+    // (3) the used slots of H are numbered by a block scan, which is also the
+    //     order of the tile's pair list; candidates take their slot's number.
+    uint32_t *H = K;                                           // kHash words
+    uint32_t *CK = P;                                          // kTileV candidate pairs, then the pair list
+    uint16_t *CS = reinterpret_cast<uint16_t *>(P + kTileV);   // candidate slot, then number
+    for (int i = threadIdx.x; i < kHash; i += kThreads) H[i] = kEmpty32;
+    uint32_t cidx[kTZ / 2];  // two 16-bit candidate indices per word
+    int ncand = 0;           // this warp's candidates so far
     {
-      const int cu = threadIdx.x < kBoxWords ? __popc(WU[threadIdx.x]) : 0;
-      const int cd = threadIdx.x < kBoxWords ? __popc(WD[threadIdx.x]) : 0;
-      int eu, ed;
-      block_scan2(cu, cd, &eu, &ed, &nU, &nD, s_scan2);
-      if (threadIdx.x < kBoxWords) {
-        PU[threadIdx.x] = eu;
-        PDp[threadIdx.x] = ed;
-      }
-    }
-    const bool dense = nU <= kMaxRoots && nD <= kMaxRoots && nU * nD <= kMaxCells;
-    __syncthreads();
-    uint32_t cell[kTZ];
-    if (dense) {
-      uint16_t *inv_u = reinterpret_cast<uint16_t *>(P);
-      uint16_t *inv_d = inv_u + kMaxRoots;
-      uint8_t *PA = reinterpret_cast<uint8_t *>(P + kMaxRoots);
-      uint32_t *PAW = P + kMaxRoots + kMaxCells / 4, *PAP = PAW + kMaxCells / 32;
-      if (threadIdx.x < kBoxWords) {
-        for (int d = 0; d < 2; ++d) {
-          uint32_t bits = d ? WD[threadIdx.x] : WU[threadIdx.x];
-          int k = d ? PDp[threadIdx.x] : PU[threadIdx.x];
-          uint16_t *inv = d ? inv_d : inv_u;
-          while (bits) {
-            const int b = __ffs(bits) - 1;
-            inv[k++] = (uint16_t)(32 * threadIdx.x + b);
-            bits &= bits - 1;
-          }
-        }
-      }
-      const int ncell = nU * nD;
-      for (int i = threadIdx.x; i < (ncell + 3) / 4; i += kThreads)
-        reinterpret_cast<uint32_t *>(PA)[i] = 0u;
-      __syncthreads();
-#pragma unroll
-      for (int lz = 0; lz < kTZ; ++lz) {
-        const uint32_t ru = w[lz] & 0xffffu, rd = w[lz] >> 16;
-        const int iu = PU[ru >> 5] + __popc(WU[ru >> 5] & ((1u << (ru & 31)) - 1u));
-        const int id = PDp[rd >> 5] + __popc(WD[rd >> 5] & ((1u << (rd & 31)) - 1u));
-        cell[lz] = (uint32_t)(iu * nD + id);
-        if (col_in && lz < nz_here) PA[cell[lz]] = 1;
-      }
-      __syncthreads();
-      const int nwc = (ncell + 31) / 32;
-      for (int j = warp; j < nwc; j += kThreads / 32) {
-        const int pos = 32 * j + lane;
-        const unsigned bits = __ballot_sync(0xffffffffu, pos < ncell && PA[pos] != 0);
-        if (lane == 0) PAW[j] = bits;
-      }
-      __syncthreads();
-      int npairs;
-      {
-        const int c = threadIdx.x < nwc ? __popc(PAW[threadIdx.x]) : 0;
-        int e, dummy_e, dummy_t;
-        block_scan2(c, 0, &e, &dummy_e, &npairs, &dummy_t, s_scan2);
-        if (threadIdx.x < nwc) PAP[threadIdx.x] = e;
-        if (threadIdx.x == 0) {
-          const long long b = (long long)atomicAdd(ts.pool_count, (unsigned long long)npairs);
-          s_base = b;
-          ts.tile_base[tile] = b;
-          ts.tile_count[tile] = npairs;
-        }
-      }
-      __syncthreads();
-      const long long base = s_base;
-      if (threadIdx.x < nwc) {
-        uint32_t bits = PAW[threadIdx.x];
-        int k = PAP[threadIdx.x];
-        while (bits) {
-          const int b = __ffs(bits) - 1;
-          const int pos = 32 * threadIdx.x + b;
-          const int iu = pos / nD, id = pos - iu * nD;
-          const long long at = base + k;
-          if (at < (long long)ts.pool_cap) {
-            const int u = inv_u[iu], d = inv_d[id];
-            const int64_t gu = ext_to_global(g, x0, y0, z0, u);
-            const int64_t gd = ext_to_global(g, x0, y0, z0, d);
-            ts.pool_roots[at] = make_int2((int)gd | (ext_is_halo(d) ? kExitFlag : 0),
-                                          (int)gu | (ext_is_halo(u) ? kExitFlag : 0));
-          } else {
-            atomicOr(&st->pool_overflow, 1u);
-          }
-          ++k;
-          bits &= bits - 1;
-        }
-      }
-#pragma unroll
-      for (int lz = 0; lz < kTZ; ++lz) {
-        const uint32_t c = (col_in && lz < nz_here) ? cell[lz] : 0u;
-        cell[lz] = PAP[c >> 5] + __popc(PAW[c >> 5] & ((1u << (c & 31)) - 1u));
-      }
-    } else {
-      // many roots: open-addressing hash set of the 32-bit root pairs in K
-      uint32_t *H = K;
-      for (int i = threadIdx.x; i < kHash; i += kThreads) H[i] = kEmpty32;
-      __syncthreads();
+      const int seg = warp * (kTZ * 32);
 #pragma unroll
       for (int lz = 0; lz < kTZ; ++lz) {
         const bool valid = col_in && lz < nz_here;
         const uint32_t key = valid ? w[lz] : kEmpty32;
         const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
         const bool lead = valid && (lane == 0 || prev != key);
-        uint32_t sl = kEmpty32;
-        if (lead) sl = pairset_insert(H, key, hash32(key));
-        const unsigned leaders = __ballot_sync(0xffffffffu, lead || !valid);
-        const int src = 31 - __clz(leaders & (0xffffffffu >> (31 - lane)));
-        sl = __shfl_sync(0xffffffffu, sl, src);
-        cell[lz] = valid ? sl : 0u;
+        const unsigned lm = __ballot_sync(0xffffffffu, lead);
+        const int my = seg + ncand + __popc(lm & ((1u << lane) - 1u));
+        if (lead) CK[my] = key;
+        // the run's leader is the highest leader lane at or below this lane
+        const unsigned upto = lm & (0xffffffffu >> (31 - lane));
+        const int src = upto ? 31 - __clz(upto) : lane;
+        const int ci = __shfl_sync(0xffffffffu, my, src);
+        const uint32_t c = valid ? (uint32_t)ci : 0u;
+        if (lz & 1)
+          cidx[lz / 2] |= c << 16;
+        else
+          cidx[lz / 2] = c;
+        ncand += __popc(lm);
       }
-      __syncthreads();
-      // number the used slots: thread t owns slots t, t + 512, ...
-      constexpr int kPer = kHash / kThreads;
-      int cnt = 0;
+    }
+    __syncthreads();  // H cleared, candidates written
+    {
+      const int seg = warp * (kTZ * 32);
+      for (int i = lane; i < ncand; i += 32) CS[seg + i] = (uint16_t)pairset_insert(H, CK[seg + i], hash32(CK[seg + i]));
+    }
+    __syncthreads();
+    // number the used slots: thread t owns slots t, t + 512, ...
+    constexpr int kPer = kHash / kThreads;
+    int cnt = 0;
 #pragma unroll
-      for (int j = 0; j < kPer; ++j) cnt += H[threadIdx.x + kThreads * j] != kEmpty32;
-      int ex, dummy_e, total, dummy_t;
-      block_scan2(cnt, 0, &ex, &dummy_e, &total, &dummy_t, s_scan2);
-      if (threadIdx.x == 0) {
-        const long long b = (long long)atomicAdd(ts.pool_count, (unsigned long long)total);
-        s_base = b;
-        ts.tile_base[tile] = b;
-        ts.tile_count[tile] = total;
-      }
-      __syncthreads();
-      const long long base = s_base;
+    for (int j = 0; j < kPer; ++j) cnt += H[threadIdx.x + kThreads * j] != kEmpty32;
+    int ex, dummy_e, npairs, dummy_t;
+    block_scan2(cnt, 0, &ex, &dummy_e, &npairs, &dummy_t, s_scan2);
+    {
       int id = ex;
 #pragma unroll
       for (int j = 0; j < kPer; ++j) {
         const int sl = threadIdx.x + kThreads * j;
         const uint32_t key = H[sl];
-        if (key == kEmpty32) continue;
-        const long long at = base + id;
-        if (at < (long long)ts.pool_cap) {
-          const int u = (int)(key & 0xffffu), d = (int)(key >> 16);
-          const int64_t gu = ext_to_global(g, x0, y0, z0, u);
-          const int64_t gd = ext_to_global(g, x0, y0, z0, d);
-          ts.pool_roots[at] = make_int2((int)gd | (ext_is_halo(d) ? kExitFlag : 0),
-                                        (int)gu | (ext_is_halo(u) ? kExitFlag : 0));
-        } else {
-          atomicOr(&st->pool_overflow, 1u);
+        if (key != kEmpty32) {
+          CK[id] = key;  // the pair list replaces the (inserted) candidates
+          H[sl] = (uint32_t)id;
+          ++id;
         }
-        H[sl] = (uint32_t)id;
-        ++id;
       }
-      __syncthreads();
-#pragma unroll
-      for (int lz = 0; lz < kTZ; ++lz) cell[lz] = H[cell[lz]];
     }
+    if (threadIdx.x == 0) {
+      const long long b = (long long)atomicAdd(ts.pool_count, (unsigned long long)npairs);
+      s_base = b;
+      ts.tile_base[tile] = b;
+      ts.tile_count[tile] = npairs;
+    }
+    __syncthreads();
+    {
+      const int seg = warp * (kTZ * 32);
+      for (int i = lane; i < ncand; i += 32) CS[seg + i] = (uint16_t)H[CS[seg + i]];
+    }
+    {
+      // the tile's pair list to the pool: global root indices, exits flagged
+      const long long base = s_base;
+      const uint32_t *PL = CK;
+      for (int i = threadIdx.x; i < npairs; i += kThreads) {
+        const long long at = base + i;
+        if (at >= (long long)ts.pool_cap) {
+          atomicOr(&st->pool_overflow, 1u);
+          break;
+        }
+        const uint32_t key = PL[i];
+        const int u = (int)(key & 0xffffu), d = (int)(key >> 16);
+        ts.pool_roots[at] = make_int2(root_ref(g, x0, y0, z0, d), root_ref(g, x0, y0, z0, u));
+      }
+    }
+    __syncthreads();
+    uint32_t cell[kTZ];
+#pragma unroll
+    for (int lz = 0; lz < kTZ; ++lz) cell[lz] = CS[(cidx[lz / 2] >> (16 * (lz & 1))) & 0xffffu];
     // per-vertex pair numbers: the column's 16 numbers are one 32-byte vector
     if (col_in) {
       uint32_t packed[kTZ / 2];

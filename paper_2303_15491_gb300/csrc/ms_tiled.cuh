@@ -24,18 +24,12 @@ constexpr int kFace = 2 * (kTX * kTY + kTX * kTZ + kTY * kTZ);  // face-root slo
 constexpr int kHashBits = 13;
 constexpr int kHash = 1 << kHashBits;                    // >= kTileV: never overflows
 constexpr int kStageCap = 2048;                          // pair-table entries staged in smem
-constexpr int kBoxWords = (kExt + 31) / 32;              // one bit per box position
-constexpr int kMaxRoots = 1024;                          // dense pair table: roots per side
-constexpr int kMaxCells = 8192;                          // dense pair table: up x dn cells
 constexpr int32_t kExitFlag = (int32_t)0x80000000u;
 
 static_assert(kExt < 65536, "extended-box indices must fit 16 bits");
 static_assert(kHash >= kTileV, "pair table must hold one pair per vertex");
-static_assert(kBoxWords <= kThreads, "one thread per flag word");
-static_assert(2 * kExt + 4 * kBoxWords * 4 <= kExt * 4, "flag bytes, words and prefixes fit the key area");
-static_assert((2 * kExt) % 16 == 0, "flag bytes end on a word boundary");
-static_assert(kMaxRoots * 4 + kMaxCells + 2 * (kMaxCells / 32) * 4 <= kExt * 4, "dense table fits the pointer area");
-static_assert(kMaxCells / 32 <= kThreads, "one thread per cell word");
+static_assert(kHash <= kExt, "the pair set fits the key area");
+static_assert(kTileV + kTileV / 2 <= kExt, "candidates (later the pair list) and their 16-bit slots fit the pointer area");
 
 struct TileGeom {
   int64_t nx, ny, nz;
