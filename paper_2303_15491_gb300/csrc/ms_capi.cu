@@ -276,10 +276,9 @@ ms_status segment_tiled(ms_ctx *c, const void *field, const int64_t dims[3], int
   const unsigned int m = c->hst->n_unique;
   MS_TRY(launch_pairs_sort(rs, m, bit_width(n - 1), c->stream));
   MS_TRY(launch_pairs_assign(rs, m, c->stream));
-  MS_TRY(launch_pair_ids(ts, rs, npairs, c->stream));
   t2.stop();
   StageTimer t3(c, MS_STAGE_WRITE);
-  MS_TRY(launch_tile_write(g, ts, asc, desc, ms, c->stream));
+  MS_TRY(launch_tile_write(g, ts, rs, asc, desc, ms, c->stream));
   t3.stop();
   MS_TRY(cudaStreamSynchronize(c->stream));
   c->last_k = m;

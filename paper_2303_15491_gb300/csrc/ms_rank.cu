@@ -9,6 +9,8 @@
 //            b = bit width of n - 1, 8 bits per pass, stable scatter.
 //   assign : the sorted position of each pair is stored in its table slot.
 //   lookup : every vertex reads its pair's rank from the table.
+#include <algorithm>
+
 #include "ms_internal.cuh"
 
 namespace msseg {
@@ -107,66 +109,11 @@ __global__ void k_radix_hist(const unsigned long long *__restrict__ in, unsigned
   hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of the digit-major histogram (256 rows of `cols` block
-// counts) by one block of 1024 threads: each warp scans 8 rows with lane
-// prefixes, the 256 row totals are scanned, and the row offsets are added.
-__global__ void __launch_bounds__(1024) k_scan_hist(unsigned int *__restrict__ a, int cols) {
-  __shared__ unsigned int rowsum[256];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int per = (cols + 31) / 32;  // entries per lane within a row
-  for (int row = warp; row < 256; row += 32) {
-    unsigned int *r = a + (size_t)row * cols;
-    unsigned int s = 0;
-    for (int j = 0; j < per; ++j) {
-      const int c = lane * per + j;
-      if (c < cols) s += r[c];
-    }
-    unsigned int incl = s;
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    unsigned int run = incl - s;
-    for (int j = 0; j < per; ++j) {
-      const int c = lane * per + j;
-      if (c < cols) {
-        const unsigned int x = r[c];
-        r[c] = run;
-        run += x;
-      }
-    }
-    if (lane == 31) rowsum[row] = incl;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    unsigned int v[8], s = 0;
-    for (int j = 0; j < 8; ++j) {
-      v[j] = rowsum[lane * 8 + j];
-      s += v[j];
-    }
-    unsigned int incl = s;
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    unsigned int run = incl - s;
-    for (int j = 0; j < 8; ++j) {
-      rowsum[lane * 8 + j] = run;
-      run += v[j];
-    }
-  }
-  __syncthreads();
-  for (int row = warp; row < 256; row += 32) {
-    const unsigned int off = rowsum[row];
-    unsigned int *r = a + (size_t)row * cols;
-    for (int c = lane; c < cols; c += 32) r[c] += off;
-  }
-}
-
 // Stable scatter: block j re-reads the chunk it histogrammed, 256 keys at a
-// time; a key's destination is its digit's running offset for this block,
-// plus the keys with the same digit in earlier warps of the tile, plus the
-// ones in earlier lanes of its own warp.
+// time; a key's destination is its digit's start (all keys of lower digits)
+// plus the keys of the same digit in earlier blocks, in earlier warps of the
+// tile and in earlier lanes of its own warp.  The per-block digit offsets are
+// computed here from the raw histogram (no separate scan launch).
 __global__ void __launch_bounds__(256) k_radix_scatter(const unsigned long long *__restrict__ in,
                                                        unsigned long long *__restrict__ out,
                                                        unsigned int m, int b, int shift,
@@ -174,7 +121,28 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const unsigned long long 
   __shared__ unsigned int run[256];
   __shared__ unsigned int wcnt[8][256];
   const unsigned int warp = threadIdx.x >> 5, lane = lane_id();
-  run[threadIdx.x] = hist[threadIdx.x * gridDim.x + blockIdx.x];
+  {
+    // digit d = threadIdx.x: total over all blocks, and over blocks before this one
+    const unsigned int *row = hist + threadIdx.x * gridDim.x;
+    unsigned int tot = 0, before = 0;
+    for (unsigned int j = 0; j < gridDim.x; ++j) {
+      const unsigned int v = row[j];
+      tot += v;
+      if (j < blockIdx.x) before += v;
+    }
+    // exclusive scan of the 256 digit totals
+    unsigned int incl = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)lane >= o) incl += t;
+    }
+    if (lane == 31) wcnt[0][warp] = incl;
+    __syncthreads();
+    unsigned int wbase = 0;
+    for (unsigned int k = 0; k < warp; ++k) wbase += wcnt[0][k];
+    run[threadIdx.x] = wbase + incl - tot + before;
+    __syncthreads();
+  }
   const unsigned int chunk = (m + gridDim.x - 1) / gridDim.x;
   const unsigned int lo = blockIdx.x * chunk;
   const unsigned int hi = min(m, lo + chunk);
@@ -286,13 +254,14 @@ cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bit
   unsigned long long *src = rs.list, *dst = rs.tmp;
   const int b = key_bits;  // bit width of one label
   const int total = 2 * b;
+  // enough blocks to spread the keys, few enough that each block's offset
+  // computation (a pass over its digit's row) stays small
+  const unsigned int blocks = std::max(1u, std::min((unsigned)kSortBlocks, (m + 4095) / 4096));
   for (int shift = 0; shift < total; shift += 8) {
     ++tl_launches;
-    k_radix_hist<<<kSortBlocks, 256, 0, s>>>(src, m, b, shift, rs.hist);
+    k_radix_hist<<<blocks, 256, 0, s>>>(src, m, b, shift, rs.hist);
     ++tl_launches;
-    k_scan_hist<<<1, 1024, 0, s>>>(rs.hist, kSortBlocks);
-    ++tl_launches;
-    k_radix_scatter<<<kSortBlocks, 256, 0, s>>>(src, dst, m, b, shift, rs.hist);
+    k_radix_scatter<<<blocks, 256, 0, s>>>(src, dst, m, b, shift, rs.hist);
     unsigned long long *t = src;
     src = dst;
     dst = t;

@@ -630,27 +630,17 @@ __global__ void k_resolve_pairs(TileGeom g, TiledScratch ts, RankScratch rs, Dev
       if (slot_out == 0xffffffffu) atomicOr(&st->hash_overflow, 1u);
     }
     slot_out = __shfl_sync(0xffffffffu, slot_out, leader);
-    if (key != ~0ull)
-      ts.pool_final[p] = make_int4((int)(key >> 32), (int)(uint32_t)key, -1, (int)slot_out);
+    if (key != ~0ull) ts.pool_slot[p] = slot_out;
   }
 }
 
-__global__ void k_pair_ids(TiledScratch ts, RankScratch rs) {
-  const unsigned long long npairs = min(*ts.pool_count, ts.pool_cap);
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < npairs;
-       p += stride) {
-    const int slot = ts.pool_final[p].w;
-    ts.pool_final[p].z = rs.table_vals[slot];
-  }
-}
-
-// Per tile: stage the pair table, stream the labels out.  Thread (lane,
-// warp) writes the z-column (x0 + lane, y0 + warp, .); its 16 pair numbers
-// are one 32-byte vector.
+// Per tile: stage the pair table -- each tile pair's (asc, desc) and MS id,
+// read from the global pair set at the pair's slot -- and stream the labels
+// out.  Thread (lane, warp) writes the z-column (x0 + lane, y0 + warp, .);
+// its 16 pair numbers are one 32-byte vector.
 __global__ void __launch_bounds__(kThreads)
-    k_tile_write(TileGeom g, TiledScratch ts, int32_t *__restrict__ asc, int32_t *__restrict__ desc,
-                 int32_t *__restrict__ ms) {
+    k_tile_write(TileGeom g, TiledScratch ts, RankScratch rs, int32_t *__restrict__ asc,
+                 int32_t *__restrict__ desc, int32_t *__restrict__ ms) {
   __shared__ int4 T[kStageCap];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t plane = g.nx * g.ny;
@@ -659,7 +649,7 @@ __global__ void __launch_bounds__(kThreads)
     tile_origin(g, tile, &x0, &y0, &z0);
     const long long b = ts.tile_base[tile];
     const int cnt = ts.tile_count[tile];
-    const int4 *src = ts.pool_final + b;
+    const uint32_t *src = ts.pool_slot + b;
     const bool staged = cnt <= kStageCap;
     const int64_t x = x0 + lane, y = y0 + warp;
     const bool col_in = x < g.nx && y < g.ny;
@@ -671,7 +661,11 @@ __global__ void __launch_bounds__(kThreads)
       q1 = __ldcs(pid4 + 1);
     }
     if (staged)
-      for (int i = threadIdx.x; i < cnt; i += kThreads) T[i] = src[i];
+      for (int i = threadIdx.x; i < cnt; i += kThreads) {
+        const uint32_t sl = __ldcs(src + i);
+        const unsigned long long key = __ldg(&rs.table_keys[sl]);
+        T[i] = make_int4((int)(key >> 32), (int)(uint32_t)key, __ldg(&rs.table_vals[sl]), 0);
+      }
     __syncthreads();
     if (col_in) {
       const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
@@ -681,7 +675,14 @@ __global__ void __launch_bounds__(kThreads)
       for (int lz = 0; lz < kTZ; ++lz) {
         if (lz >= nz_here) break;
         const int id = (int)((w[lz / 2] >> (16 * (lz & 1))) & 0xffffu);
-        const int4 t = staged ? T[id] : src[id];
+        int4 t;
+        if (staged) {
+          t = T[id];
+        } else {
+          const uint32_t sl = src[id];
+          const unsigned long long key = rs.table_keys[sl];
+          t = make_int4((int)(key >> 32), (int)(uint32_t)key, rs.table_vals[sl], 0);
+        }
         const int64_t v = v0 + plane * lz;
         __stcs(asc + v, t.x);
         __stcs(desc + v, t.y);
@@ -721,7 +722,7 @@ size_t tiled_scratch_bytes(const TileGeom &g, unsigned long long pool_cap) {
   const size_t pid = (size_t)g.ntiles * kTileV * 2;
   const size_t face = (size_t)g.ntiles * kFace * 4;
   const size_t meta = (size_t)g.ntiles * (8 + 4);
-  return 4 * 256 + pid + face + meta + (size_t)pool_cap * (8 + 16) + 8 * 256;
+  return 4 * 256 + pid + face + meta + (size_t)pool_cap * (8 + 4) + 8 * 256;
 }
 
 void tiled_scratch_carve(void *base, const TileGeom &g, unsigned long long pool_cap,
@@ -733,7 +734,7 @@ void tiled_scratch_carve(void *base, const TileGeom &g, unsigned long long pool_
     return r;
   };
   ts->pool_count = reinterpret_cast<unsigned long long *>(take(256));
-  ts->pool_final = reinterpret_cast<int4 *>(take((size_t)pool_cap * 16));
+  ts->pool_slot = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
   ts->pool_roots = reinterpret_cast<int2 *>(take((size_t)pool_cap * 8));
   ts->tile_base = reinterpret_cast<long long *>(take((size_t)g.ntiles * 8));
   ts->tile_count = reinterpret_cast<int32_t *>(take((size_t)g.ntiles * 4));
@@ -813,22 +814,11 @@ cudaError_t launch_resolve_pairs(const TileGeom &g, const TiledScratch &ts, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_pair_ids(const TiledScratch &ts, const RankScratch &rs, unsigned long long npairs,
-                            cudaStream_t s) {
-  if (npairs == 0) return cudaSuccess;
-  unsigned long long blocks = (npairs + 255) / 256;
-  const unsigned long long cap = (unsigned long long)sms() * 16;
-  if (blocks > cap) blocks = cap;
-  ++tl_launches;
-  k_pair_ids<<<(unsigned)blocks, 256, 0, s>>>(ts, rs);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_tile_write(const TileGeom &g, const TiledScratch &ts, int32_t *asc,
-                              int32_t *desc, int32_t *ms, cudaStream_t s) {
+cudaError_t launch_tile_write(const TileGeom &g, const TiledScratch &ts, const RankScratch &rs,
+                              int32_t *asc, int32_t *desc, int32_t *ms, cudaStream_t s) {
   const int64_t grid = std::min<int64_t>(g.ntiles, (int64_t)sms() * 4);
   ++tl_launches;
-  k_tile_write<<<(unsigned)grid, kThreads, 0, s>>>(g, ts, asc, desc, ms);
+  k_tile_write<<<(unsigned)grid, kThreads, 0, s>>>(g, ts, rs, asc, desc, ms);
   return cudaGetLastError();
 }
 

@@ -41,7 +41,7 @@ struct TiledScratch {
   unsigned long long *pool_count;  // pairs reserved by all tiles
   unsigned long long pool_cap;
   int2 *pool_roots;   // per tile pair: (dn-root, up-root), global index | kExitFlag if an exit
-  int4 *pool_final;   // per tile pair: (asc, desc, ms, slot of the pair in the global set)
+  uint32_t *pool_slot;  // per tile pair: slot of its (asc, desc) pair in the global pair set
   long long *tile_base;
   int32_t *tile_count;
   uint32_t *face;     // per tile kFace words: up-root | dn-root << 16 (extended-box indices)
@@ -57,9 +57,7 @@ cudaError_t launch_tile_local(const void *field, int dtype, const TileGeom &g,
                               bool allow_tma = true);
 cudaError_t launch_resolve_pairs(const TileGeom &g, const TiledScratch &ts, const RankScratch &rs,
                                  unsigned long long npairs, DevStatus *st, cudaStream_t s);
-cudaError_t launch_pair_ids(const TiledScratch &ts, const RankScratch &rs,
-                            unsigned long long npairs, cudaStream_t s);
-cudaError_t launch_tile_write(const TileGeom &g, const TiledScratch &ts, int32_t *asc,
-                              int32_t *desc, int32_t *ms, cudaStream_t s);
+cudaError_t launch_tile_write(const TileGeom &g, const TiledScratch &ts, const RankScratch &rs,
+                              int32_t *asc, int32_t *desc, int32_t *ms, cudaStream_t s);
 
 }  // namespace msseg
