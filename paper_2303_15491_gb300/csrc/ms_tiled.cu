@@ -48,17 +48,6 @@ __device__ __forceinline__ int ext_of(int lx, int ly, int lz) {
   return (lx + kXO) + kEX * ((ly + 1) + kEY * (lz + 1));
 }
 
-__device__ __forceinline__ bool ext_is_halo(int e) {
-  const int ex = e % kEX, r = e / kEX, ey = r % kEY, ez = r / kEY;
-  return ex == kXO - 1 || ex == kXO + kTX || ey == 0 || ez == 0 || ey == kEY - 1 || ez == kEZ - 1;
-}
-
-__device__ __forceinline__ int64_t ext_to_global(const TileGeom &g, int64_t x0, int64_t y0,
-                                                 int64_t z0, int e) {
-  const int ex = e % kEX, r = e / kEX, ey = r % kEY, ez = r / kEY;
-  return (x0 + ex - kXO) + g.nx * ((y0 + ey - 1) + g.ny * (z0 + ez - 1));
-}
-
 __device__ __forceinline__ void tile_origin(const TileGeom &g, int64_t t, int64_t *x0, int64_t *y0,
                                             int64_t *z0) {
   uint32_t r, tx, ty, tz;
@@ -553,21 +542,29 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // Follow an exit (a vertex on another tile's face) through the face roots
-// until an extremum; `up` selects the direction.
+// until an extremum; `up` selects the direction.  All indices fit 31 bits
+// (N < 2^31), so the hops use 32-bit arithmetic.
 __device__ int32_t chase(const TileGeom &g, const TiledScratch &ts, int32_t r, bool up,
                          DevStatus *st) {
+  const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny, gtx = (uint32_t)g.tx,
+                 gty = (uint32_t)g.ty;
   for (int64_t hop = 0; hop <= g.ntiles; ++hop) {
     if (!(r & kExitFlag)) return r;
     uint32_t q, x, y, z;
     g.div_nx.divmod((uint32_t)(r & ~kExitFlag), &q, &x);
     g.div_ny.divmod(q, &z, &y);
-    const int64_t tile = (int64_t)(x / kTX) + g.tx * ((int64_t)(y / kTY) + g.ty * (int64_t)(z / kTZ));
-    const int64_t x0 = x - x % kTX, y0 = y - y % kTY, z0 = z - z % kTZ;
-    const int fs = face_slot((int)(x - x0), (int)(y - y0), (int)(z - z0));
+    const uint32_t tx = x / kTX, ty = y / kTY, tz = z / kTZ;
+    const uint32_t tile = tx + gtx * (ty + gty * tz);
+    const int fs = face_slot((int)(x - tx * kTX), (int)(y - ty * kTY), (int)(z - tz * kTZ));
     if (fs < 0) break;
-    const uint32_t w = __ldg(&ts.face[tile * (int64_t)kFace + fs]);
-    const int loc = up ? (int)(w & 0xffffu) : (int)(w >> 16);
-    r = (int32_t)ext_to_global(g, x0, y0, z0, loc) | (ext_is_halo(loc) ? kExitFlag : 0);
+    const uint32_t w = __ldg(&ts.face[(size_t)tile * kFace + fs]);
+    const uint32_t loc = up ? (w & 0xffffu) : (w >> 16);
+    const uint32_t ez = loc / (kEX * kEY), rr = loc - ez * (kEX * kEY);
+    const uint32_t ey = rr / kEX, ex = rr - ey * kEX;
+    const bool halo = ex == kXO - 1 || ex == kXO + kTX || ey == 0 || ez == 0 || ey == kEY - 1 ||
+                      ez == kEZ - 1;
+    const uint32_t gx = tx * kTX + ex - kXO, gy = ty * kTY + ey - 1, gz = tz * kTZ + ez - 1;
+    r = (int32_t)(gx + nx * (gy + ny * gz)) | (halo ? kExitFlag : 0);
   }
   atomicOr(&st->not_converged, 1u);
   return 0;
@@ -584,53 +581,39 @@ __device__ __forceinline__ unsigned long long mix64t(unsigned long long k) {
 }
 
 __global__ void k_resolve_pairs(TileGeom g, TiledScratch ts, RankScratch rs, DevStatus *st) {
-  const unsigned long long npairs = *ts.pool_count;
+  const unsigned long long npairs = min(*ts.pool_count, ts.pool_cap);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < npairs;
-       base += stride) {
-    const unsigned long long p = base + threadIdx.x;
-    unsigned long long key = ~0ull;
-    if (p < npairs && p < ts.pool_cap) {
-      const int2 r = ts.pool_roots[p];
-      const int32_t a = chase(g, ts, r.x, false, st);
-      const int32_t d = chase(g, ts, r.y, true, st);
-      key = ((unsigned long long)(uint32_t)a << 32) | (uint32_t)d;
-    }
-    const unsigned int peers = __match_any_sync(0xffffffffu, key);
-    const int leader = __ffs(peers) - 1;
-    unsigned int slot_out = 0xffffffffu;
-    if (key != ~0ull && leader == (int)(threadIdx.x & 31)) {
-      // insert into the global pair set
-      const unsigned int mask = rs.capacity - 1u;
-      unsigned int slot = (unsigned int)mix64t(key) & mask;
-      for (unsigned int probe = 0; probe < rs.capacity; ++probe) {
-        unsigned long long cur = *(volatile unsigned long long *)&rs.table_keys[slot];
-        if (cur == key) {
-          slot_out = slot;
+  const unsigned int mask = rs.capacity - 1u;
+  for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < npairs;
+       p += stride) {
+    const int2 r = ts.pool_roots[p];
+    const int32_t a = chase(g, ts, r.x, false, st);
+    const int32_t d = chase(g, ts, r.y, true, st);
+    const unsigned long long key = ((unsigned long long)(uint32_t)a << 32) | (uint32_t)d;
+    // insert into the global pair set (first fit, open addressing)
+    unsigned int slot = (unsigned int)mix64t(key) & mask, found = 0xffffffffu;
+    for (unsigned int probe = 0; probe < rs.capacity; ++probe) {
+      unsigned long long cur = *(volatile unsigned long long *)&rs.table_keys[slot];
+      if (cur == ~0ull) {
+        cur = atomicCAS(&rs.table_keys[slot], ~0ull, key);
+        if (cur == ~0ull) {
+          const unsigned int at = atomicAdd(&st->n_unique, 1u);
+          if (at < rs.max_unique)
+            rs.list[at] = key;
+          else
+            atomicOr(&st->hash_overflow, 1u);
+          found = slot;
           break;
         }
-        if (cur == ~0ull) {
-          cur = atomicCAS(&rs.table_keys[slot], ~0ull, key);
-          if (cur == ~0ull) {
-            const unsigned int at = atomicAdd(&st->n_unique, 1u);
-            if (at < rs.max_unique)
-              rs.list[at] = key;
-            else
-              atomicOr(&st->hash_overflow, 1u);
-            slot_out = slot;
-            break;
-          }
-          if (cur == key) {
-            slot_out = slot;
-            break;
-          }
-        }
-        slot = (slot + 1u) & mask;
       }
-      if (slot_out == 0xffffffffu) atomicOr(&st->hash_overflow, 1u);
+      if (cur == key) {
+        found = slot;
+        break;
+      }
+      slot = (slot + 1u) & mask;
     }
-    slot_out = __shfl_sync(0xffffffffu, slot_out, leader);
-    if (key != ~0ull) ts.pool_slot[p] = slot_out;
+    if (found == 0xffffffffu) atomicOr(&st->hash_overflow, 1u);
+    ts.pool_slot[p] = found;
   }
 }
 
