@@ -263,16 +263,30 @@ ms_status segment_tiled(ms_ctx *c, const void *field, const int64_t dims[3], int
   }
   c->pool_hint = std::max(c->pool_hint, cap);
   StageTimer t2(c, MS_STAGE_RESOLVE);
-  const unsigned int hcap = pow2_at_least(2 * npairs + 2);
-  ms_status s = ensure_scratch(c, rank_scratch_bytes(hcap));
-  if (s != MS_OK) return s;
+  // The global pair set holds the distinct (asc, desc) pairs, usually far
+  // fewer than the tile pairs: size it from the last call's count (or a
+  // quarter of the tile pairs) and fall back to the exact bound if it fills.
+  const uint64_t exact = 2 * npairs + 2;
+  uint64_t want = c->last_k ? 4 * (uint64_t)c->last_k : npairs / 4;
+  if (want < (1u << 16)) want = 1u << 16;
+  if (want > exact) want = exact;
   RankScratch rs;
-  rank_scratch_carve(c->scratch, hcap, &rs);
-  MS_TRY(launch_resolve_pairs(g, ts, rs, npairs, c->dst, c->stream));
-  s = read_status(c);
-  if (s != MS_OK) return s;
-  if (c->hst->not_converged) return MS_ERR_NOT_CONVERGED;
-  if (c->hst->hash_overflow) return MS_ERR_CUDA;  // cannot happen: capacity >= 2 * pairs
+  ms_status s;
+  for (;;) {
+    const unsigned int hcap = pow2_at_least(want);
+    s = ensure_scratch(c, rank_scratch_bytes(hcap));
+    if (s != MS_OK) return s;
+    rank_scratch_carve(c->scratch, hcap, &rs);
+    MS_TRY(cudaMemsetAsync(&c->dst->n_unique, 0, sizeof(unsigned int), c->stream));
+    MS_TRY(cudaMemsetAsync(&c->dst->hash_overflow, 0, sizeof(unsigned int), c->stream));
+    MS_TRY(launch_resolve_pairs(g, ts, rs, npairs, c->dst, c->stream));
+    s = read_status(c);
+    if (s != MS_OK) return s;
+    if (c->hst->not_converged) return MS_ERR_NOT_CONVERGED;
+    if (!c->hst->hash_overflow) break;
+    if (want >= exact) return MS_ERR_CUDA;  // cannot happen: the exact bound always fits
+    want = exact;
+  }
   const unsigned int m = c->hst->n_unique;
   MS_TRY(launch_pairs_sort(rs, m, bit_width(n - 1), c->stream));
   MS_TRY(launch_pairs_assign(rs, m, c->stream));

@@ -235,52 +235,111 @@ __device__ __forceinline__ Cand omin(Cand a, Cand b) {
   return Cand{t ? b.k : a.k, t ? b.i : a.i};
 }
 
-// up / dn of the column (lx, ly, 0..TZ-1) from the staged values K into P,
-// streaming planes along z.  N(v) u {v} is the union of the unit cubes
-// [v, v+(1,1,1)] and [v-(1,1,1), v]; each cube's extremum is taken along x,
-// then y, then z.
+// Cube extrema.  A unit cube with minimum corner c = (cx, cy, cz), cx in
+// [-1, TX-1], cy in [-1, TY-1], cz in [-1, TZ-1] (tile coordinates), has its
+// (max, min) winners' box indices at C[cube_of(c)] as max | min << 16.
+constexpr int kCX = kTX + 1, kCY = kTY + 1;
+__device__ __forceinline__ int cube_of(int cx, int cy, int cz) {
+  return (cx + 1) + kCX * ((cy + 1) + kCY * (cz + 1));
+}
+
+// Max and min of two candidates in one step (b at higher indices); the
+// min side compares Ord::mk-transformed keys.
 template <bool kRaw>
-__device__ __forceinline__ void steepest_column(const uint32_t *__restrict__ K, uint32_t *P,
-                                                int lx, int ly, bool col_in, int nz_here,
-                                                bool *nan) {
-  Cand hi_prev_max{}, hi_prev_min{}, lo_prev_max{}, lo_prev_min{}, lo_prev2_max{}, lo_prev2_min{};
-#pragma unroll 2
-  for (int p = 0; p < kTZ + 2; ++p) {
-    const int e = (lx + kXO) + kEX * ((ly + 1) + kEY * p);
-    const uint32_t kAm = K[e - kEX - 1], kA = K[e - kEX];
-    const uint32_t kBm = K[e - 1], kB = K[e], kBp = K[e + 1];
-    const uint32_t kC = K[e + kEX], kCp = K[e + kEX + 1];
-    if (kRaw && p >= 1 && p <= nz_here && col_in) *nan |= is_nan_bits(kB);
-    const uint32_t ue = (uint32_t)e;
-    const Cand h1hiB = omax<kRaw>(Cand{kB, ue}, Cand{kBp, ue + 1});
-    const Cand h1hiC = omax<kRaw>(Cand{kC, ue + kEX}, Cand{kCp, ue + kEX + 1});
-    const Cand h1loA = omax<kRaw>(Cand{kAm, ue - kEX - 1}, Cand{kA, ue - kEX});
-    const Cand h1loB = omax<kRaw>(Cand{kBm, ue - 1}, Cand{kB, ue});
-    const Cand h2hi_max = omax<kRaw>(h1hiB, h1hiC);
-    const Cand h2lo_max = omax<kRaw>(h1loA, h1loB);
-    typedef Ord<kRaw> O;
-    const Cand n1hiB = omin<kRaw>(Cand{O::mk(kB), ue}, Cand{O::mk(kBp), ue + 1});
-    const Cand n1hiC = omin<kRaw>(Cand{O::mk(kC), ue + kEX}, Cand{O::mk(kCp), ue + kEX + 1});
-    const Cand n1loA = omin<kRaw>(Cand{O::mk(kAm), ue - kEX - 1}, Cand{O::mk(kA), ue - kEX});
-    const Cand n1loB = omin<kRaw>(Cand{O::mk(kBm), ue - 1}, Cand{O::mk(kB), ue});
-    const Cand h2hi_min = omin<kRaw>(n1hiB, n1hiC);
-    const Cand h2lo_min = omin<kRaw>(n1loA, n1loB);
-    if (p >= 2) {
-      const int lz = p - 2;
-      const int ev = e - kEX * kEY;  // the vertex of plane p - 1
-      const Cand up =
-          omax<kRaw>(omax<kRaw>(lo_prev2_max, lo_prev_max), omax<kRaw>(hi_prev_max, h2hi_max));
-      const Cand dn =
-          omin<kRaw>(omin<kRaw>(lo_prev2_min, lo_prev_min), omin<kRaw>(hi_prev_min, h2hi_min));
-      P[ev] = (col_in && lz < nz_here) ? (up.i | (dn.i << 16)) : (uint32_t)ev * 0x10001u;
+__device__ __forceinline__ void mm2(Cand a_max, Cand a_min, Cand b_max, Cand b_min, Cand *o_max,
+                                    Cand *o_min) {
+  *o_max = omax<kRaw>(a_max, b_max);
+  *o_min = omin<kRaw>(a_min, b_min);
+}
+
+// The extremum pair of one cube from 8 box loads, x pairs, then y, then z.
+template <bool kRaw>
+__device__ __forceinline__ uint32_t cube_extrema(const uint32_t *__restrict__ K, int cx, int cy,
+                                                 int cz) {
+  typedef Ord<kRaw> O;
+  Cand zmax[2], zmin[2];
+#pragma unroll
+  for (int dz = 0; dz < 2; ++dz) {
+    Cand ymax[2], ymin[2];
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      const uint32_t e = (uint32_t)((cx + kXO) + kEX * ((cy + dy + 1) + kEY * (cz + dz + 1)));
+      const uint32_t k0 = K[e], k1 = K[e + 1];
+      ymax[dy] = omax<kRaw>(Cand{k0, e}, Cand{k1, e + 1});
+      ymin[dy] = omin<kRaw>(Cand{O::mk(k0), e}, Cand{O::mk(k1), e + 1});
     }
-    lo_prev2_max = lo_prev_max;
-    lo_prev2_min = lo_prev_min;
-    lo_prev_max = h2lo_max;
-    lo_prev_min = h2lo_min;
-    hi_prev_max = h2hi_max;
-    hi_prev_min = h2hi_min;
+    zmax[dz] = omax<kRaw>(ymax[0], ymax[1]);
+    zmin[dz] = omin<kRaw>(ymin[0], ymin[1]);
   }
+  const Cand m = omax<kRaw>(zmax[0], zmax[1]), n = omin<kRaw>(zmin[0], zmin[1]);
+  return m.i | (n.i << 16);
+}
+
+// up / dn of the tile's vertices.  N(v) u {v} is the union of the unit cubes
+// [v, v+(1,1,1)] and [v-(1,1,1), v]; a cube's extremum is taken along x, then
+// y, then z, and each cube serves two vertices (as the upper cube of its
+// minimum corner and the lower cube of its maximum corner), so it is
+// computed once: the cubes with c = (lx, ly, .) by thread (lx, ly) streaming
+// z, the remaining cubes (some coordinate -1) spread over the block.  The
+// results go to w[] in registers; C lives in P's area until then.
+template <bool kRaw>
+__device__ __forceinline__ void steepest_tile(const uint32_t *__restrict__ K, uint32_t *C, int lx,
+                                              int ly, bool col_in, int nz_here, uint32_t *w,
+                                              bool *nan) {
+  typedef Ord<kRaw> O;
+  {
+    Cand h2max{}, h2min{};
+#pragma unroll 2
+    for (int p = 0; p <= kTZ; ++p) {
+      const uint32_t e = (uint32_t)((lx + kXO) + kEX * ((ly + 1) + kEY * (p + 1)));
+      const uint32_t k00 = K[e], k10 = K[e + 1], k01 = K[e + kEX], k11 = K[e + kEX + 1];
+      if (kRaw && p < nz_here && col_in) *nan |= is_nan_bits(k00);
+      const Cand a_max = omax<kRaw>(Cand{k00, e}, Cand{k10, e + 1});
+      const Cand b_max = omax<kRaw>(Cand{k01, e + kEX}, Cand{k11, e + kEX + 1});
+      const Cand a_min = omin<kRaw>(Cand{O::mk(k00), e}, Cand{O::mk(k10), e + 1});
+      const Cand b_min = omin<kRaw>(Cand{O::mk(k01), e + kEX}, Cand{O::mk(k11), e + kEX + 1});
+      const Cand pmax = omax<kRaw>(a_max, b_max), pmin = omin<kRaw>(a_min, b_min);
+      if (p >= 1) {
+        const Cand m = omax<kRaw>(h2max, pmax), n = omin<kRaw>(h2min, pmin);
+        C[cube_of(lx, ly, p - 1)] = m.i | (n.i << 16);
+      }
+      h2max = pmax;
+      h2min = pmin;
+    }
+  }
+  // cubes with a coordinate at -1: cz = -1 (kCX x kCY), then cy = -1 with cz
+  // >= 0 (kCX x kTZ), then cx = -1 with cy, cz >= 0 (kTY x kTZ)
+  constexpr int kA = kCX * kCY, kB = kCX * kTZ, kCn = kTY * kTZ;
+  for (int j = threadIdx.x; j < kA + kB + kCn; j += kThreads) {
+    int cx, cy, cz;
+    if (j < kA) {
+      cz = -1;
+      cx = j % kCX - 1;
+      cy = j / kCX - 1;
+    } else if (j < kA + kB) {
+      const int q = j - kA;
+      cy = -1;
+      cx = q % kCX - 1;
+      cz = q / kCX;
+    } else {
+      const int q = j - kA - kB;
+      cx = -1;
+      cy = q % kTY;
+      cz = q / kTY;
+    }
+    C[cube_of(cx, cy, cz)] = cube_extrema<kRaw>(K, cx, cy, cz);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int lz = 0; lz < kTZ; ++lz) {
+    const uint32_t ev = (uint32_t)ext_of(lx, ly, lz);
+    const uint32_t hi = C[cube_of(lx, ly, lz)], lo = C[cube_of(lx - 1, ly - 1, lz - 1)];
+    const uint32_t ua = lo & 0xffffu, ub = hi & 0xffffu, da = lo >> 16, db = hi >> 16;
+    const uint32_t up = O::ge(K[ub], K[ua]) ? ub : ua;  // the upper cube lies at higher indices
+    const uint32_t dn = O::lt(O::mk(K[db]), O::mk(K[da])) ? db : da;
+    w[lz] = (col_in && lz < nz_here) ? (up | (dn << 16)) : ev * 0x10001u;
+  }
+  __syncthreads();  // C is dead; P may be written
 }
 
 // First-fit insert of key into the open-addressing pair set H, starting at
@@ -377,25 +436,39 @@ __global__ void __launch_bounds__(kThreads, 2)
           K[eb + kXO + lx] = (row_in && x_in) ? key_of(b) : 0u;
           if (lane < 2) K[eb + exe] = (row_in && xe_in) ? key_of(be) : 0u;
         }
-        if (!interior) P[eb + kXO + lx] = (uint32_t)(eb + kXO + lx) * 0x10001u;
-        if (lane < 2) P[eb + exe] = (uint32_t)(eb + exe) * 0x10001u;
       }
     }
     __syncthreads();
 
-    // ---- steepest neighbours
+    // ---- steepest neighbours: the extremum of every unit cube the tile's
+    // vertices need, once each, into C (in P's area); then per vertex the
+    // better of its two cubes; then P = pointers, halo = self-loops
     const bool col_in = x0 + lx < g.nx && y0 + ly < g.ny;
     const int nz_here = (int)min((int64_t)kTZ, g.nz - z0);
+    uint32_t w[kTZ];
     if (raw)
-      steepest_column<true>(K, P, lx, ly, col_in, nz_here, &nan);
+      steepest_tile<true>(K, P, lx, ly, col_in, nz_here, w, &nan);
     else
-      steepest_column<false>(K, P, lx, ly, col_in, nz_here, &nan);
+      steepest_tile<false>(K, P, lx, ly, col_in, nz_here, w, &nan);
     if (__syncthreads_or(nan)) {
       // the call fails with MS_ERR_NAN_INPUT; skip the rest of this tile
       if (threadIdx.x == 0) ts.tile_count[tile] = 0;
       __syncthreads();
       continue;
     }
+#pragma unroll
+    for (int lz = 0; lz < kTZ; ++lz) P[ext_of(lx, ly, lz)] = w[lz];
+    for (int r = warp; r < kEY * kEZ; r += kThreads / 32) {
+      const int ey = r % kEY, ez = r / kEY;
+      const int eb = kEX * r;
+      if (ey == 0 || ez == 0 || ey == kEY - 1 || ez == kEZ - 1)
+        P[eb + kXO + lx] = (uint32_t)(eb + kXO + lx) * 0x10001u;
+      if (lane < 2) {
+        const int e = eb + (lane == 0 ? kXO - 1 : kXO + kTX);
+        P[e] = (uint32_t)e * 0x10001u;
+      }
+    }
+    __syncthreads();
 
     // ---- path compression inside the tile.  Halo entries and extrema are
     // self-pointers, so every pointer ends on a local extremum or an exit.
@@ -403,9 +476,6 @@ __global__ void __launch_bounds__(kThreads, 2)
     // them) and jumps them in place until a pass changes nothing in its
     // warp; reads of other vertices' pointers may see them before or after
     // their own jumps, and either lies on the same path.
-    uint32_t w[kTZ];
-#pragma unroll
-    for (int lz = 0; lz < kTZ; ++lz) w[lz] = P[ext_of(lx, ly, lz)];
     for (int it = 0; it < kExt; ++it) {
       bool changed = false;
 #pragma unroll

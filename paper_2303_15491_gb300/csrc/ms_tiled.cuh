@@ -29,6 +29,7 @@ constexpr int32_t kExitFlag = (int32_t)0x80000000u;
 static_assert(kExt < 65536, "extended-box indices must fit 16 bits");
 static_assert(kHash >= kTileV, "pair table must hold one pair per vertex");
 static_assert(kHash <= kExt, "the pair set fits the key area");
+static_assert((kTX + 1) * (kTY + 1) * (kTZ + 1) <= kExt, "cube extrema fit the pointer area");
 static_assert(kTileV + kTileV / 2 <= kExt, "candidates (later the pair list) and their 16-bit slots fit the pointer area");
 
 struct TileGeom {
