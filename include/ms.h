@@ -156,7 +156,7 @@ ms_status ms_pair_rank(ms_ctx *ctx, const int32_t *asc, const int32_t *desc, int
  * MS_NOALLOC_MAX_N gives MS_ERR_TOO_LARGE, values outside [0, n)
  * MS_ERR_INVALID_ARG.  The call returns after its work has completed.
  *
- * Its working memory is one static device array of about 11.5 MB inside the
+ * Its working memory is one static device array of about 10.3 MB inside the
  * library (hash set, sort buffers and a status block), which every GPU that
  * loads the library holds until the process exits; the call itself performs
  * no cudaMalloc / cudaFree and calls no allocating routine.  The first call

@@ -22,7 +22,7 @@ struct ms_ctx {
   size_t io_bytes = 0;
   void *tscratch = nullptr;  // tiled path working memory
   size_t tscratch_bytes = 0;
-  unsigned long long *hcount = nullptr;  // pinned copy of the tiled pool counts (3)
+  unsigned long long *hcount = nullptr;  // pinned copy of the tiled pair count
   unsigned long long pool_hint = 0;      // pair-pool capacity that sufficed last time
   int64_t last_k = 0;
   // profiler
@@ -242,7 +242,7 @@ ms_status segment_tiled(ms_ctx *c, const void *field, const int64_t dims[3], int
   if (cap == 0) cap = std::max<unsigned long long>(1ull << 16, (unsigned long long)n / 16);
   if (cap > (unsigned long long)n) cap = (unsigned long long)n;
   TiledScratch ts;
-  unsigned long long npairs = 0, n_dn = 0, n_up = 0;
+  unsigned long long npairs = 0;
   for (;;) {
     ms_status s = reset_status(c);
     if (s != MS_OK) return s;
@@ -252,16 +252,14 @@ ms_status segment_tiled(ms_ctx *c, const void *field, const int64_t dims[3], int
     StageTimer t0(c, MS_STAGE_TILE_LOCAL);
     MS_TRY(launch_tile_local(field, dtype, g, ts, c->dst, c->stream));
     t0.stop();
-    MS_TRY(cudaMemcpyAsync(c->hcount, ts.pool_count, 3 * sizeof(unsigned long long),
+    MS_TRY(cudaMemcpyAsync(c->hcount, ts.pool_count, sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, c->stream));
     s = read_status(c);
     if (s != MS_OK) return s;
     if (c->hst->nan_flag) return MS_ERR_NAN_INPUT;
-    npairs = c->hcount[0];
-    n_dn = c->hcount[1];
-    n_up = c->hcount[2];
+    npairs = *c->hcount;
     if (!c->hst->pool_overflow) break;
-    cap = std::max(npairs, std::max(n_dn, n_up));  // exact now
+    cap = npairs;  // exact now
   }
   c->pool_hint = std::max(c->pool_hint, cap);
   StageTimer t2(c, MS_STAGE_RESOLVE);
@@ -281,7 +279,6 @@ ms_status segment_tiled(ms_ctx *c, const void *field, const int64_t dims[3], int
     rank_scratch_carve(c->scratch, hcap, &rs);
     MS_TRY(cudaMemsetAsync(&c->dst->n_unique, 0, sizeof(unsigned int), c->stream));
     MS_TRY(cudaMemsetAsync(&c->dst->hash_overflow, 0, sizeof(unsigned int), c->stream));
-    MS_TRY(launch_resolve_roots(g, ts, n_dn, n_up, c->dst, c->stream));
     MS_TRY(launch_resolve_pairs(g, ts, rs, npairs, c->dst, c->stream));
     s = read_status(c);
     if (s != MS_OK) return s;
@@ -372,7 +369,7 @@ ms_status ms_create(ms_ctx **out, int device, void *cuda_stream) {
   }
   if (s == MS_OK) s = cuda_status(cudaMalloc(&c->dst, sizeof(DevStatus)));
   if (s == MS_OK) s = cuda_status(cudaMallocHost(&c->hst, sizeof(DevStatus)));
-  if (s == MS_OK) s = cuda_status(cudaMallocHost(&c->hcount, 3 * sizeof(unsigned long long)));
+  if (s == MS_OK) s = cuda_status(cudaMallocHost(&c->hcount, sizeof(unsigned long long)));
   if (s != MS_OK) {
     ms_destroy(c);
     return s;

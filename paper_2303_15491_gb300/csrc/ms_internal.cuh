@@ -68,7 +68,7 @@ struct RankScratch {
   unsigned int capacity;           // power of two
   unsigned int max_unique;         // capacity / 2
 };
-constexpr int kSortBlocks = 1024;  // most blocks of one radix pass
+constexpr int kSortBlocks = 240;
 size_t rank_scratch_bytes(unsigned int capacity);
 void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs);
 cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t n,

@@ -254,8 +254,9 @@ cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bit
   unsigned long long *src = rs.list, *dst = rs.tmp;
   const int b = key_bits;  // bit width of one label
   const int total = 2 * b;
-  // about 1024 keys per block (4 tiles of the scatter), at most kSortBlocks
-  const unsigned int blocks = std::max(1u, std::min((unsigned)kSortBlocks, (m + 1023) / 1024));
+  // enough blocks to spread the keys, few enough that each block's offset
+  // computation (a pass over its digit's row) stays small
+  const unsigned int blocks = std::max(1u, std::min((unsigned)kSortBlocks, (m + 4095) / 4096));
   for (int shift = 0; shift < total; shift += 8) {
     ++tl_launches;
     k_radix_hist<<<blocks, 256, 0, s>>>(src, m, b, shift, rs.hist);

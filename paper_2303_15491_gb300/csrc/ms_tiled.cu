@@ -371,7 +371,6 @@ __global__ void __launch_bounds__(kThreads, 2)
   __shared__ long long s_base;
   __shared__ int s_abort;
   __shared__ int s_scan2[2][kThreads / 32];
-  __shared__ long long s_rbase[2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int lx = lane, ly = warp;
   bool nan = false;
@@ -567,81 +566,30 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
       }
     }
+    if (threadIdx.x == 0) {
+      const long long b = (long long)atomicAdd(ts.pool_count, (unsigned long long)npairs);
+      s_base = b;
+      ts.tile_base[tile] = b;
+      ts.tile_count[tile] = npairs;
+    }
     __syncthreads();
     {
       const int seg = warp * (kTZ * 32);
       for (int i = lane; i < ncand; i += 32) CS[seg + i] = (uint16_t)H[CS[seg + i]];
     }
-    // ---- the tile's distinct roots: flag them in the (now free) key area,
-    // rank the flags with popcounts, list them; pairs then name their roots
-    // by index into the per-tile root lists
-    uint8_t *FU = reinterpret_cast<uint8_t *>(K), *FD = FU + kExt;
-    uint32_t *WU = K + (2 * kExt) / 4, *WD = WU + kBoxWords;  // after the flag bytes
-    uint32_t *PU = WD + kBoxWords, *PD = PU + kBoxWords;
-    __syncthreads();
-    for (int i = threadIdx.x; i < kExt / 2; i += kThreads) K[i] = 0u;
-    __syncthreads();
-    for (int i = threadIdx.x; i < npairs; i += kThreads) {
-      const uint32_t key = CK[i];
-      FU[key & 0xffffu] = 1;
-      FD[key >> 16] = 1;
-    }
-    __syncthreads();
-    for (int j = warp; j < 2 * kBoxWords; j += kThreads / 32) {
-      const bool dn = j >= kBoxWords;
-      const int jj = dn ? j - kBoxWords : j;
-      const int pos = 32 * jj + lane;
-      const unsigned bits = __ballot_sync(0xffffffffu, pos < kExt && (dn ? FD : FU)[pos] != 0);
-      if (lane == 0) (dn ? WD : WU)[jj] = bits;
-    }
-    __syncthreads();
-    int nU, nD;
     {
-      const int cu = threadIdx.x < kBoxWords ? __popc(WU[threadIdx.x]) : 0;
-      const int cd = threadIdx.x < kBoxWords ? __popc(WD[threadIdx.x]) : 0;
-      int eu, ed;
-      block_scan2(cu, cd, &eu, &ed, &nU, &nD, s_scan2);
-      if (threadIdx.x < kBoxWords) {
-        PU[threadIdx.x] = eu;
-        PD[threadIdx.x] = ed;
-      }
-    }
-    if (threadIdx.x == 0) {
-      const long long b = (long long)atomicAdd(&ts.pool_count[0], (unsigned long long)npairs);
-      s_base = b;
-      ts.tile_base[tile] = b;
-      ts.tile_count[tile] = npairs;
-      s_rbase[0] = (long long)atomicAdd(&ts.pool_count[1], (unsigned long long)nD);
-      s_rbase[1] = (long long)atomicAdd(&ts.pool_count[2], (unsigned long long)nU);
-    }
-    __syncthreads();
-    const long long base = s_base, dbase = s_rbase[0], ubase = s_rbase[1];
-    const long long cap = (long long)ts.pool_cap;
-    if (base + npairs > cap || dbase + nD > cap || ubase + nU > cap) {
-      if (threadIdx.x == 0) atomicOr(&st->pool_overflow, 1u);
-    } else {
-      if (threadIdx.x < kBoxWords) {
-        uint32_t bits = WD[threadIdx.x];
-        long long k = dbase + PD[threadIdx.x];
-        while (bits) {
-          const int b = __ffs(bits) - 1;
-          ts.dn_ref[k++] = root_ref(g, x0, y0, z0, 32 * threadIdx.x + b);
-          bits &= bits - 1;
-        }
-        bits = WU[threadIdx.x];
-        k = ubase + PU[threadIdx.x];
-        while (bits) {
-          const int b = __ffs(bits) - 1;
-          ts.up_ref[k++] = root_ref(g, x0, y0, z0, 32 * threadIdx.x + b);
-          bits &= bits - 1;
-        }
-      }
+      // the tile's pair list to the pool: global root indices, exits flagged
+      const long long base = s_base;
+      const uint32_t *PL = CK;
       for (int i = threadIdx.x; i < npairs; i += kThreads) {
-        const uint32_t key = CK[i];
-        const uint32_t u = key & 0xffffu, d = key >> 16;
-        const int iu = PU[u >> 5] + __popc(WU[u >> 5] & ((1u << (u & 31)) - 1u));
-        const int id = PD[d >> 5] + __popc(WD[d >> 5] & ((1u << (d & 31)) - 1u));
-        ts.pool_pairs[base + i] = make_int2((int)(dbase + id), (int)(ubase + iu));
+        const long long at = base + i;
+        if (at >= (long long)ts.pool_cap) {
+          atomicOr(&st->pool_overflow, 1u);
+          break;
+        }
+        const uint32_t key = PL[i];
+        const int u = (int)(key & 0xffffu), d = (int)(key >> 16);
+        ts.pool_roots[at] = make_int2(root_ref(g, x0, y0, z0, d), root_ref(g, x0, y0, z0, u));
       }
     }
     __syncthreads();
@@ -702,32 +650,15 @@ __device__ __forceinline__ unsigned long long mix64t(unsigned long long k) {
   return k;
 }
 
-// Every tile root reference (an extremum or an exit) to the extremum its
-// path reaches: dn-roots through the face roots' dn halves, up-roots through
-// the up halves.
-__global__ void k_resolve_roots(TileGeom g, TiledScratch ts, unsigned long long n_dn,
-                                unsigned long long n_up, DevStatus *st) {
-  const unsigned long long total = n_dn + n_up;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += stride) {
-    if (i < n_dn)
-      ts.dn_label[i] = chase(g, ts, ts.dn_ref[i], false, st);
-    else
-      ts.up_label[i - n_dn] = chase(g, ts, ts.up_ref[i - n_dn], true, st);
-  }
-}
-
-// Every tile pair to its (asc, desc) pair, inserted into the global pair set.
 __global__ void k_resolve_pairs(TileGeom g, TiledScratch ts, RankScratch rs, DevStatus *st) {
-  const unsigned long long npairs = min(ts.pool_count[0], ts.pool_cap);
+  const unsigned long long npairs = min(*ts.pool_count, ts.pool_cap);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned int mask = rs.capacity - 1u;
   for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < npairs;
        p += stride) {
-    const int2 r = ts.pool_pairs[p];
-    const int32_t a = ts.dn_label[r.x];
-    const int32_t d = ts.up_label[r.y];
+    const int2 r = ts.pool_roots[p];
+    const int32_t a = chase(g, ts, r.x, false, st);
+    const int32_t d = chase(g, ts, r.y, true, st);
     const unsigned long long key = ((unsigned long long)(uint32_t)a << 32) | (uint32_t)d;
     // insert into the global pair set (first fit, open addressing)
     unsigned int slot = (unsigned int)mix64t(key) & mask, found = 0xffffffffu;
@@ -844,7 +775,7 @@ size_t tiled_scratch_bytes(const TileGeom &g, unsigned long long pool_cap) {
   const size_t pid = (size_t)g.ntiles * kTileV * 2;
   const size_t face = (size_t)g.ntiles * kFace * 4;
   const size_t meta = (size_t)g.ntiles * (8 + 4);
-  return 4 * 256 + pid + face + meta + (size_t)pool_cap * (8 + 4 + 4 * 4) + 12 * 256;
+  return 4 * 256 + pid + face + meta + (size_t)pool_cap * (8 + 4) + 8 * 256;
 }
 
 void tiled_scratch_carve(void *base, const TileGeom &g, unsigned long long pool_cap,
@@ -857,11 +788,7 @@ void tiled_scratch_carve(void *base, const TileGeom &g, unsigned long long pool_
   };
   ts->pool_count = reinterpret_cast<unsigned long long *>(take(256));
   ts->pool_slot = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
-  ts->pool_pairs = reinterpret_cast<int2 *>(take((size_t)pool_cap * 8));
-  ts->dn_ref = reinterpret_cast<int32_t *>(take((size_t)pool_cap * 4));
-  ts->up_ref = reinterpret_cast<int32_t *>(take((size_t)pool_cap * 4));
-  ts->dn_label = reinterpret_cast<int32_t *>(take((size_t)pool_cap * 4));
-  ts->up_label = reinterpret_cast<int32_t *>(take((size_t)pool_cap * 4));
+  ts->pool_roots = reinterpret_cast<int2 *>(take((size_t)pool_cap * 8));
   ts->tile_base = reinterpret_cast<long long *>(take((size_t)g.ntiles * 8));
   ts->tile_count = reinterpret_cast<int32_t *>(take((size_t)g.ntiles * 4));
   ts->face = reinterpret_cast<uint32_t *>(take((size_t)g.ntiles * kFace * 4));
@@ -912,7 +839,7 @@ bool make_box_map(const void *field, int dtype, const TileGeom &g, CUtensorMap *
 cudaError_t launch_tile_local(const void *field, int dtype, const TileGeom &g,
                               const TiledScratch &ts, DevStatus *st, cudaStream_t s,
                               bool allow_tma) {
-  cudaError_t e = cudaMemsetAsync(ts.pool_count, 0, 3 * sizeof(unsigned long long), s);
+  cudaError_t e = cudaMemsetAsync(ts.pool_count, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   constexpr int kSmem = 2 * kExt * 4;
   static_assert(kHash <= kExt, "the pair set reuses the key area");
@@ -925,19 +852,6 @@ cudaError_t launch_tile_local(const void *field, int dtype, const TileGeom &g,
   const int64_t grid = std::min<int64_t>(g.ntiles, (int64_t)sms() * 2);
   ++tl_launches;
   kern<<<(unsigned)grid, kThreads, kSmem, s>>>(field, dtype, g, ts, st, map);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_resolve_roots(const TileGeom &g, const TiledScratch &ts,
-                                 unsigned long long n_dn, unsigned long long n_up, DevStatus *st,
-                                 cudaStream_t s) {
-  const unsigned long long total = n_dn + n_up;
-  if (total == 0) return cudaSuccess;
-  unsigned long long blocks = (total + 255) / 256;
-  const unsigned long long cap = (unsigned long long)sms() * 16;
-  if (blocks > cap) blocks = cap;
-  ++tl_launches;
-  k_resolve_roots<<<(unsigned)blocks, 256, 0, s>>>(g, ts, n_dn, n_up, st);
   return cudaGetLastError();
 }
 

@@ -24,15 +24,11 @@ constexpr int kFace = 2 * (kTX * kTY + kTX * kTZ + kTY * kTZ);  // face-root slo
 constexpr int kHashBits = 13;
 constexpr int kHash = 1 << kHashBits;                    // >= kTileV: never overflows
 constexpr int kStageCap = 2048;                          // pair-table entries staged in smem
-constexpr int kBoxWords = (kExt + 31) / 32;              // one flag bit per box position
 constexpr int32_t kExitFlag = (int32_t)0x80000000u;
 
 static_assert(kExt < 65536, "extended-box indices must fit 16 bits");
 static_assert(kHash >= kTileV, "pair table must hold one pair per vertex");
 static_assert(kHash <= kExt, "the pair set fits the key area");
-static_assert(kBoxWords <= kThreads, "one thread per flag word");
-static_assert(2 * kExt + 4 * kBoxWords * 4 <= kExt * 4, "root flags, words and prefixes fit the key area");
-static_assert((2 * kExt) % 16 == 0, "flag bytes end on a word boundary");
 static_assert((kTX + 1) * (kTY + 1) * (kTZ + 1) <= kExt, "cube extrema fit the pointer area");
 static_assert(kTileV + kTileV / 2 <= kExt, "candidates (later the pair list) and their 16-bit slots fit the pointer area");
 
@@ -43,14 +39,10 @@ struct TileGeom {
 };
 
 struct TiledScratch {
-  unsigned long long *pool_count;  // [0] tile pairs, [1] tile dn-roots, [2] tile up-roots
-  unsigned long long pool_cap;     // capacity of each of the three pools
-  int2 *pool_pairs;     // per tile pair: (dn-root, up-root) as indices into the root pools
+  unsigned long long *pool_count;  // pairs reserved by all tiles
+  unsigned long long pool_cap;
+  int2 *pool_roots;   // per tile pair: (dn-root, up-root), global index | kExitFlag if an exit
   uint32_t *pool_slot;  // per tile pair: slot of its (asc, desc) pair in the global pair set
-  int32_t *dn_ref;      // per tile dn-root: global vertex index | kExitFlag if an exit
-  int32_t *up_ref;      // per tile up-root: likewise
-  int32_t *dn_label;    // per tile dn-root: the minimum its path reaches
-  int32_t *up_label;    // per tile up-root: the maximum its path reaches
   long long *tile_base;
   int32_t *tile_count;
   uint32_t *face;     // per tile kFace words: up-root | dn-root << 16 (extended-box indices)
@@ -64,9 +56,6 @@ void tiled_scratch_carve(void *base, const TileGeom &g, unsigned long long pool_
 cudaError_t launch_tile_local(const void *field, int dtype, const TileGeom &g,
                               const TiledScratch &ts, DevStatus *st, cudaStream_t s,
                               bool allow_tma = true);
-cudaError_t launch_resolve_roots(const TileGeom &g, const TiledScratch &ts,
-                                 unsigned long long n_dn, unsigned long long n_up, DevStatus *st,
-                                 cudaStream_t s);
 cudaError_t launch_resolve_pairs(const TileGeom &g, const TiledScratch &ts, const RankScratch &rs,
                                  unsigned long long npairs, DevStatus *st, cudaStream_t s);
 cudaError_t launch_tile_write(const TileGeom &g, const TiledScratch &ts, const RankScratch &rs,
