@@ -299,9 +299,16 @@ ms_status segment_tiled(ms_ctx *c, const void *field, const int64_t dims[3], int
   return MS_OK;
 }
 
+ms_status segment_staged(ms_ctx *c, const void *field, const int64_t dims[3], int dtype,
+                         int64_t n, int32_t *asc, int32_t *desc, int32_t *ms);
+
+// Grids at least kTZ / 2 planes deep take the tiled path; flatter ones (2D
+// grids in particular) would leave most of every 32 x 16 x 16 tile empty,
+// so they take the step-by-step path.
 ms_status segment_device(ms_ctx *c, const void *field, const int64_t dims[3], int dtype,
                          int64_t n, int32_t *asc, int32_t *desc, int32_t *ms) {
-  return segment_tiled(c, field, dims, dtype, n, asc, desc, ms);
+  if (dims[2] >= kTZ / 2) return segment_tiled(c, field, dims, dtype, n, asc, desc, ms);
+  return segment_staged(c, field, dims, dtype, n, asc, desc, ms);
 }
 
 ms_status segment_staged(ms_ctx *c, const void *field, const int64_t dims[3], int dtype,

@@ -1,0 +1,106 @@
+"""Parity at the full workload sizes: 512^3 smoothed noise (and its 256-level
+quantisation), 1024^3 and 32768^2 broad Gaussians + ramp.  The oracle cannot
+label 10^8-10^9 vertices in seconds, so the GPU labels are checked
+  * vertex by vertex on samples: the oracle walks each sampled vertex's
+    integral lines straight from the field;
+  * by the local characterisation on a large sample: desc(v) = desc(up(v)),
+    asc(v) = asc(dn(v)) with up / dn from the oracle, and every label is an
+    extremum -- together these fix the labels uniquely;
+  * for the MS ids by properties that hold at any size: sorted by (asc, desc),
+    the ids start at 0, step by one exactly where the pair changes, end at K-1.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2303_15491_gb300 as ms
+import synthfields as sf
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+
+CACHE = os.environ.get("MS_FIELD_CACHE") or "/tmp/msseg_fields"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    h = ms.ms_create(0)
+    yield h
+    ms.ms_destroy(h)
+
+
+def cached(name, make):
+    os.makedirs(CACHE, exist_ok=True)
+    path = os.path.join(CACHE, name + ".npy")
+    if os.path.exists(path):
+        return np.load(path)
+    f = make()
+    tmp = path + f".{os.getpid()}.tmp.npy"
+    np.save(tmp, f)
+    os.replace(tmp, path)
+    return f
+
+
+def check_full(ctx, f, n_walk=600, n_local=1 << 20, seed=0):
+    dev = torch.from_numpy(f).cuda()
+    asc_d, desc_d, ms_d, k = ms.segment(ctx, dev)
+    n = f.size
+    # MS ids from (asc, desc), on the device (property check, any size)
+    key = (asc_d.to(torch.int64) << 32) | desc_d.to(torch.int64)
+    order = torch.argsort(key)
+    sk, sm = key[order], ms_d[order]
+    del order
+    step = (sk[1:] != sk[:-1]).to(torch.int32)
+    assert int(sm[0]) == 0 and int(sm[-1]) == k - 1
+    assert bool(torch.equal(sm[1:] - sm[:-1], step))
+    del key, sk, sm, step
+    labels_up = torch.unique(desc_d).cpu().numpy()
+    labels_dn = torch.unique(asc_d).cpu().numpy()
+    asc, desc = asc_d.cpu().numpy(), desc_d.cpu().numpy()
+    del asc_d, desc_d, ms_d, dev
+    g = sf.rng_for(seed)
+    # vertex-by-vertex: walks straight from the field
+    for v in g.integers(0, n, n_walk):
+        assert oracle.walk(f, int(v), +1)[0] == desc[v], v
+        assert oracle.walk(f, int(v), -1)[0] == asc[v], v
+    # local characterisation on a large sample
+    vs = g.integers(0, n, n_local).astype(np.int64)
+    up, dn = oracle.steepest_at(f, vs)
+    assert np.array_equal(desc[vs], desc[up])
+    assert np.array_equal(asc[vs], asc[dn])
+    # every label is an extremum, and every sampled extremum labels itself
+    for lab, is_up in ((labels_up, True), (labels_dn, False)):
+        for chunk in np.array_split(lab, max(1, lab.size // (1 << 20))):
+            u, d = oracle.steepest_at(f, chunk.astype(np.int64))
+            assert np.array_equal(u if is_up else d, chunk)
+    maxima = vs[up == vs]
+    minima = vs[dn == vs]
+    assert np.array_equal(desc[maxima], maxima) and np.array_equal(asc[minima], minima)
+    return k
+
+
+def test_noise_512(ctx):
+    f = cached("noise512", lambda: sf.smoothed_noise((512, 512, 512), 0, sigma=4.0, radius=16))
+    k = check_full(ctx, f)
+    assert k > 1000
+
+
+def test_noise_512_quantised(ctx):
+    f = cached("noise512q", lambda: sf.quantize_levels(
+        cached("noise512", lambda: sf.smoothed_noise((512, 512, 512), 0, sigma=4.0, radius=16))))
+    check_full(ctx, f, seed=1)
+
+
+def test_broad_1024(ctx):
+    f = cached("broad1024", lambda: sf.broad_gaussians_ramp((1024, 1024, 1024), 0))
+    check_full(ctx, f, n_walk=200, seed=2)
+
+
+def test_broad_32768_2d(ctx):
+    f = cached("broad32768", lambda: sf.broad_gaussians_ramp((32768, 32768, 1), 0))
+    check_full(ctx, f, n_walk=200, seed=3)
