@@ -90,6 +90,20 @@ ms_status ms_destroy(ms_ctx *ctx);
 ms_status ms_segment(ms_ctx *ctx, const void *field, const int64_t dims[3], ms_dtype dtype,
                      int32_t *out_asc, int32_t *out_desc, int32_t *out_ms);
 
+/* Many segmentations in one call (ensemble members, time steps): fields[f]
+ * with dims[f] and dtypes[f] -> asc[f], desc[f], ms[f], exactly as n_fields
+ * separate ms_segment calls would give them.  All pointer arrays are HOST
+ * arrays of n_fields DEVICE pointers; k_out (may be NULL) is a host array of
+ * n_fields that receives each field's region count K.  When every field has
+ * at most 2^24 vertices and at least 8 planes, all fields go through one
+ * launch per stage (tiles of all fields in one work list, one global pair set
+ * keyed by field); otherwise the fields are segmented one after the other.
+ * A NaN in any field fails the whole call (MS_ERR_NAN_INPUT).
+ * ms_last_region_count then returns the sum of the fields' K. */
+ms_status ms_segment_batch(ms_ctx *ctx, int n_fields, const void *const *fields,
+                           const int64_t (*dims)[3], const ms_dtype *dtypes, int32_t *const *asc,
+                           int32_t *const *desc, int32_t *const *ms, int64_t *k_out);
+
 /* The same segmentation computed by the four step kernels below, one after
  * the other, each through global memory (slower than ms_segment; kept as an
  * independent GPU cross-check of the fused path).  Same arguments, outputs

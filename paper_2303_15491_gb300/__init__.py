@@ -24,7 +24,7 @@ __all__ = [
     "ms_segment", "ms_segment_host", "ms_last_region_count", "ms_order_keys", "ms_steepest",
     "ms_compress", "ms_pair_rank", "segment", "EXPORTED_SYMBOLS", "ms_profile_enable",
     "ms_profile_read", "ms_profile_stage_name", "STAGES", "ms_segment_staged",
-    "ms_pair_rank_noalloc", "MS_NOALLOC_MAX_N",
+    "ms_pair_rank_noalloc", "MS_NOALLOC_MAX_N", "ms_segment_batch",
 ]
 
 MS_F32, MS_F16 = 0, 1
@@ -36,7 +36,7 @@ EXPORTED_SYMBOLS = [
     "ms_status_string", "ms_create", "ms_destroy", "ms_segment", "ms_segment_host",
     "ms_last_region_count", "ms_order_keys", "ms_steepest", "ms_compress", "ms_pair_rank",
     "ms_profile_enable", "ms_profile_read", "ms_profile_stage_name", "ms_segment_staged",
-    "ms_pair_rank_noalloc",
+    "ms_pair_rank_noalloc", "ms_segment_batch",
 ]
 MS_NOALLOC_MAX_N = 262144
 STAGES = ["tile_local", "resolve", "write", "h2d", "d2h"]
@@ -75,6 +75,8 @@ def load(build: bool = True) -> ctypes.CDLL:
             L.ms_create.argtypes = [ctypes.POINTER(c_vp), ctypes.c_int, c_vp]
             L.ms_destroy.argtypes = [c_vp]
             L.ms_segment.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
+            L.ms_segment_batch.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                           c_i64p]
             L.ms_segment_staged.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
             L.ms_segment_host.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
             L.ms_last_region_count.argtypes = [c_vp, c_i64p]
@@ -158,6 +160,20 @@ def ms_destroy(ctx: int) -> None:
 def ms_segment(ctx, field, dims, dtype, out_asc, out_desc, out_ms) -> None:
     _check(load().ms_segment(ctx, _ptr(field), _dims(dims), int(dtype), _ptr(out_asc),
                              _ptr(out_desc), _ptr(out_ms)), "ms_segment")
+
+
+def ms_segment_batch(ctx, fields, dims_list, dtypes, ascs, descs, mss) -> list:
+    """Segment many fields in one call; returns the list of per-field K.
+    fields / ascs / descs / mss: device tensors (or pointers); dims_list:
+    (nx, ny, nz) per field; dtypes: MS_F32 / MS_F16 per field."""
+    n = len(fields)
+    ptrs = lambda xs: (c_vp * n)(*[_ptr(x) for x in xs])
+    dims = (ctypes.c_int64 * (3 * n))(*[int(v) for d in dims_list for v in d])
+    dts = (ctypes.c_int * n)(*[int(t) for t in dtypes])
+    ks = (ctypes.c_int64 * n)()
+    _check(load().ms_segment_batch(ctx, n, ptrs(fields), ctypes.cast(dims, c_vp), ctypes.cast(dts, c_vp),
+                                   ptrs(ascs), ptrs(descs), ptrs(mss), ks), "ms_segment_batch")
+    return [int(k) for k in ks]
 
 
 def ms_segment_staged(ctx, field, dims, dtype, out_asc, out_desc, out_ms) -> None:

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "ms_internal.cuh"
 #include "ms_tiled.cuh"
@@ -24,6 +25,10 @@ struct ms_ctx {
   size_t tscratch_bytes = 0;
   unsigned long long *hcount = nullptr;  // pinned copy of the tiled pair count
   unsigned long long pool_hint = 0;      // pair-pool capacity that sufficed last time
+  void *batch_dev = nullptr;             // field descriptors + tensor maps on the device
+  size_t batch_dev_bytes = 0;
+  void *batch_host = nullptr;            // their pinned staging copy
+  size_t batch_host_bytes = 0;
   int64_t last_k = 0;
   // profiler
   bool prof_on = false;
@@ -235,43 +240,94 @@ ms_status ensure_buffer(ms_ctx *c, void **buf, size_t *have, size_t bytes) {
 
 // The tiled path (ms_tiled.cu): tile-local steepest + compression + pair
 // numbering, global resolution of tile exits and pair ranks, label write.
-ms_status segment_tiled(ms_ctx *c, const void *field, const int64_t dims[3], int dtype, int64_t n,
-                        int32_t *asc, int32_t *desc, int32_t *ms) {
-  const TileGeom g = tile_geom(dims);
+// One field of a segmentation request, as the tiled path sees it.
+struct FieldArg {
+  const void *field;
+  const int64_t *dims;
+  int dtype;
+  int64_t n;
+  int32_t *asc, *desc, *ms;
+};
+
+// The tiled path (ms_tiled.cu) over one field or a batch of fields: one
+// launch per stage covers every tile of every field.  Batches key the global
+// pair set by (field, asc, desc); each field's MS ids start at its first pair
+// in the sorted set.  k_out[f] receives each field's region count.
+ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
+  const int key_mode = nf > 1 ? kKeyBatch : kKeyOne;
+  // ---- descriptors and tensor maps, staged in pinned memory then copied
+  const size_t desc_bytes = ((size_t)nf * sizeof(FieldDesc) + 127) & ~(size_t)127;
+  const size_t bytes = desc_bytes + (size_t)nf * sizeof(CUtensorMap);
+  ms_status s = ensure_buffer(c, &c->batch_dev, &c->batch_dev_bytes, bytes);
+  if (s != MS_OK) return s;
+  if (c->batch_host_bytes < bytes) {
+    if (c->batch_host) {
+      cudaStreamSynchronize(c->stream);
+      cudaFreeHost(c->batch_host);
+      c->batch_host = nullptr;
+      c->batch_host_bytes = 0;
+    }
+    if (cudaMallocHost(&c->batch_host, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return MS_ERR_OUT_OF_MEMORY;
+    }
+    c->batch_host_bytes = bytes;
+  }
+  MS_TRY(cudaStreamSynchronize(c->stream));  // the staging buffer may still be in flight
+  FieldDesc *hd = static_cast<FieldDesc *>(c->batch_host);
+  CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(static_cast<char *>(c->batch_host) + desc_bytes);
+  long long total_tiles = 0;
+  int64_t total_n = 0, max_n = 0;
+  for (int f = 0; f < nf; ++f) {
+    make_field_desc(fa[f].field, fa[f].dtype, fa[f].dims, total_tiles, fa[f].asc, fa[f].desc,
+                    fa[f].ms, true, &hd[f], &hm[f]);
+    total_tiles += hd[f].g.ntiles;
+    total_n += fa[f].n;
+    max_n = std::max(max_n, fa[f].n);
+  }
+  MS_TRY(cudaMemcpyAsync(c->batch_dev, c->batch_host, bytes, cudaMemcpyHostToDevice, c->stream));
+  Batch b;
+  b.fields = static_cast<const FieldDesc *>(c->batch_dev);
+  b.tmaps = reinterpret_cast<const CUtensorMap *>(static_cast<const char *>(c->batch_dev) + desc_bytes);
+  b.n_fields = nf;
+  b.key_mode = key_mode;
+  b.total_tiles = total_tiles;
+
+  // ---- tile pass; the pair pool is sized from the last call, exact on overflow
   unsigned long long cap = c->pool_hint;
-  if (cap == 0) cap = std::max<unsigned long long>(1ull << 16, (unsigned long long)n / 16);
-  if (cap > (unsigned long long)n) cap = (unsigned long long)n;
+  if (cap == 0) cap = std::max<unsigned long long>(1ull << 16, (unsigned long long)total_n / 16);
+  if (cap > (unsigned long long)total_n) cap = (unsigned long long)total_n;
   TiledScratch ts;
   unsigned long long npairs = 0;
   for (;;) {
-    ms_status s = reset_status(c);
+    s = reset_status(c);
     if (s != MS_OK) return s;
-    s = ensure_buffer(c, &c->tscratch, &c->tscratch_bytes, tiled_scratch_bytes(g, cap));
+    s = ensure_buffer(c, &c->tscratch, &c->tscratch_bytes, tiled_scratch_bytes(total_tiles, nf, cap));
     if (s != MS_OK) return s;
-    tiled_scratch_carve(c->tscratch, g, cap, &ts);
+    tiled_scratch_carve(c->tscratch, total_tiles, nf, cap, &ts);
     StageTimer t0(c, MS_STAGE_TILE_LOCAL);
-    MS_TRY(launch_tile_local(field, dtype, g, ts, c->dst, c->stream));
+    MS_TRY(launch_tile_local(b, ts, c->dst, c->stream));
     t0.stop();
     MS_TRY(cudaMemcpyAsync(c->hcount, ts.pool_count, sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, c->stream));
     s = read_status(c);
     if (s != MS_OK) return s;
     if (c->hst->nan_flag) return MS_ERR_NAN_INPUT;
+    if (c->hst->timeout) return MS_ERR_TIMEOUT;
     npairs = *c->hcount;
     if (!c->hst->pool_overflow) break;
     cap = npairs;  // exact now
   }
   c->pool_hint = std::max(c->pool_hint, cap);
+
+  // ---- exits followed, pairs deduplicated; the set is sized from the last
+  // call's region count (or a quarter of the tile pairs), exact on overflow
   StageTimer t2(c, MS_STAGE_RESOLVE);
-  // The global pair set holds the distinct (asc, desc) pairs, usually far
-  // fewer than the tile pairs: size it from the last call's count (or a
-  // quarter of the tile pairs) and fall back to the exact bound if it fills.
   const uint64_t exact = 2 * npairs + 2;
   uint64_t want = c->last_k ? 4 * (uint64_t)c->last_k : npairs / 4;
   if (want < (1u << 16)) want = 1u << 16;
   if (want > exact) want = exact;
   RankScratch rs;
-  ms_status s;
   for (;;) {
     const unsigned int hcap = pow2_at_least(want);
     s = ensure_scratch(c, rank_scratch_bytes(hcap));
@@ -279,7 +335,7 @@ ms_status segment_tiled(ms_ctx *c, const void *field, const int64_t dims[3], int
     rank_scratch_carve(c->scratch, hcap, &rs);
     MS_TRY(cudaMemsetAsync(&c->dst->n_unique, 0, sizeof(unsigned int), c->stream));
     MS_TRY(cudaMemsetAsync(&c->dst->hash_overflow, 0, sizeof(unsigned int), c->stream));
-    MS_TRY(launch_resolve_pairs(g, ts, rs, npairs, c->dst, c->stream));
+    MS_TRY(launch_resolve_pairs(b, ts, rs, npairs, c->dst, c->stream));
     s = read_status(c);
     if (s != MS_OK) return s;
     if (c->hst->not_converged) return MS_ERR_NOT_CONVERGED;
@@ -288,13 +344,28 @@ ms_status segment_tiled(ms_ctx *c, const void *field, const int64_t dims[3], int
     want = exact;
   }
   const unsigned int m = c->hst->n_unique;
-  MS_TRY(launch_pairs_sort(rs, m, bit_width(n - 1), c->stream));
+  if (key_mode == kKeyBatch)
+    MS_TRY(launch_pairs_sort(rs, m, 0, c->stream, bit_width(nf - 1) + 48));
+  else
+    MS_TRY(launch_pairs_sort(rs, m, bit_width(max_n - 1), c->stream));
   MS_TRY(launch_pairs_assign(rs, m, c->stream));
+  MS_TRY(launch_field_starts(b, ts, rs, m, c->stream));
   t2.stop();
   StageTimer t3(c, MS_STAGE_WRITE);
-  MS_TRY(launch_tile_write(g, ts, rs, asc, desc, ms, c->stream));
+  MS_TRY(launch_tile_write(b, ts, rs, c->stream));
   t3.stop();
-  MS_TRY(cudaStreamSynchronize(c->stream));
+  if (key_mode == kKeyBatch) {
+    uint32_t *hf = reinterpret_cast<uint32_t *>(c->batch_host);  // reuse the staging buffer
+    MS_TRY(cudaMemcpyAsync(hf, ts.fstart, (size_t)nf * 4, cudaMemcpyDeviceToHost, c->stream));
+    MS_TRY(cudaStreamSynchronize(c->stream));
+    for (int f = 0; f < nf; ++f) {
+      const uint32_t end = f + 1 < nf ? hf[f + 1] : m;
+      if (k_out) k_out[f] = (int64_t)(end - hf[f]);
+    }
+  } else {
+    MS_TRY(cudaStreamSynchronize(c->stream));
+    if (k_out) k_out[0] = m;
+  }
   c->last_k = m;
   return MS_OK;
 }
@@ -307,7 +378,13 @@ ms_status segment_staged(ms_ctx *c, const void *field, const int64_t dims[3], in
 // so they take the step-by-step path.
 ms_status segment_device(ms_ctx *c, const void *field, const int64_t dims[3], int dtype,
                          int64_t n, int32_t *asc, int32_t *desc, int32_t *ms) {
-  if (dims[2] >= kTZ / 2) return segment_tiled(c, field, dims, dtype, n, asc, desc, ms);
+  if (dims[2] >= kTZ / 2) {
+    const FieldArg fa{field, dims, dtype, n, asc, desc, ms};
+    int64_t k = 0;
+    const ms_status s = segment_tiled(c, &fa, 1, &k);
+    if (s == MS_OK) c->last_k = k;
+    return s;
+  }
   return segment_staged(c, field, dims, dtype, n, asc, desc, ms);
 }
 
@@ -392,6 +469,8 @@ ms_status ms_destroy(ms_ctx *c) {
   if (c->scratch) cudaFree(c->scratch);
   if (c->io) cudaFree(c->io);
   if (c->tscratch) cudaFree(c->tscratch);
+  if (c->batch_dev) cudaFree(c->batch_dev);
+  if (c->batch_host) cudaFreeHost(c->batch_host);
   if (c->hcount) cudaFreeHost(c->hcount);
   if (c->dst) cudaFree(c->dst);
   if (c->hst) cudaFreeHost(c->hst);
@@ -444,6 +523,55 @@ ms_status ms_segment_staged(ms_ctx *c, const void *field, const int64_t dims[3],
   const long long l0 = tl_launches;
   s = segment_staged(c, field, dims, dtype, n, out_asc, out_desc, out_ms);
   if (s == MS_OK) finish_profile(c, l0);
+  return s;
+}
+
+ms_status ms_segment_batch(ms_ctx *c, int n_fields, const void *const *fields,
+                           const int64_t (*dims)[3], const ms_dtype *dtypes, int32_t *const *asc,
+                           int32_t *const *desc, int32_t *const *ms, int64_t *k_out) {
+  if (!c || n_fields < 0 || (n_fields > 0 && (!fields || !dims || !dtypes || !asc || !desc || !ms)))
+    return MS_ERR_INVALID_ARG;
+  if (n_fields == 0) return MS_OK;
+  DeviceGuard g(c->device);
+  std::vector<FieldArg> fa((size_t)n_fields);
+  bool batchable = n_fields <= kBatchMaxFields;
+  for (int f = 0; f < n_fields; ++f) {
+    int64_t n = 0;
+    ms_status s = check_dims(dims[f], &n);
+    if (s != MS_OK) return s;
+    s = check_dtype(dtypes[f]);
+    if (s != MS_OK) return s;
+    if (!is_device_pointer(fields[f]) || !is_device_pointer(asc[f]) || !is_device_pointer(desc[f]) ||
+        !is_device_pointer(ms[f]))
+      return MS_ERR_INVALID_ARG;
+    if (asc[f] == desc[f] || asc[f] == ms[f] || desc[f] == ms[f]) return MS_ERR_INVALID_ARG;
+    fa[f] = FieldArg{fields[f], dims[f], (int)dtypes[f], n, asc[f], desc[f], ms[f]};
+    batchable = batchable && n <= kBatchMaxN && dims[f][2] >= kTZ / 2;
+  }
+  const long long l0 = tl_launches;
+  ms_status s = MS_OK;
+  int64_t total_k = 0;
+  if (batchable) {
+    std::vector<int64_t> k((size_t)n_fields, 0);
+    s = segment_tiled(c, fa.data(), n_fields, k.data());
+    for (int f = 0; f < n_fields && s == MS_OK; ++f) {
+      if (k_out) k_out[f] = k[f];
+      total_k += k[f];
+    }
+  } else {
+    for (int f = 0; f < n_fields && s == MS_OK; ++f) {
+      s = segment_device(c, fa[f].field, fa[f].dims, fa[f].dtype, fa[f].n, fa[f].asc, fa[f].desc,
+                         fa[f].ms);
+      if (s == MS_OK) {
+        if (k_out) k_out[f] = c->last_k;
+        total_k += c->last_k;
+      }
+    }
+  }
+  if (s == MS_OK) {
+    c->last_k = total_k;
+    finish_profile(c, l0);
+  }
   return s;
 }
 

@@ -73,8 +73,10 @@ size_t rank_scratch_bytes(unsigned int capacity);
 void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs);
 cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t n,
                                 const RankScratch &rs, DevStatus *st, cudaStream_t s);
+// Sorts the pair list: (asc << 32) | desc keys with labels below 2^key_bits,
+// or (raw_bits > 0) keys compared on their low raw_bits bits as they are.
 cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int n_unique, int key_bits,
-                              cudaStream_t s);
+                              cudaStream_t s, int raw_bits = 0);
 cudaError_t launch_pairs_assign(const RankScratch &rs, unsigned int n_unique, cudaStream_t s);
 cudaError_t launch_pairs_lookup(const int32_t *asc, const int32_t *desc, int64_t n,
                                 const RankScratch &rs, int32_t *ms, cudaStream_t s);

@@ -90,8 +90,10 @@ __global__ void k_pairs_insert(const int32_t *__restrict__ asc, const int32_t *_
   if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(&st->bad_index, 1u);
 }
 
+// b >= 0: the key is (asc << 32) | desc with labels below 2^b, sorted on the
+// compacted (asc << b) | desc; b < 0: the key is sorted as it is.
 __device__ __forceinline__ unsigned int sort_digit(unsigned long long key, int b, int shift) {
-  const unsigned long long compact = ((key >> 32) << b) | (key & 0xffffffffull);
+  const unsigned long long compact = b >= 0 ? (((key >> 32) << b) | (key & 0xffffffffull)) : key;
   return (unsigned int)(compact >> shift) & 255u;
 }
 
@@ -249,11 +251,11 @@ cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t
 
 // Sorts rs.list[0, m) in place (the result always ends in rs.list).
 cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bits,
-                              cudaStream_t s) {
+                              cudaStream_t s, int raw_bits) {
   if (m <= 1) return cudaSuccess;
   unsigned long long *src = rs.list, *dst = rs.tmp;
-  const int b = key_bits;  // bit width of one label
-  const int total = 2 * b;
+  const int b = raw_bits > 0 ? -1 : key_bits;  // bit width of one label, or raw keys
+  const int total = raw_bits > 0 ? raw_bits : 2 * key_bits;
   // enough blocks to spread the keys, few enough that each block's offset
   // computation (a pass over its digit's row) stays small
   const unsigned int blocks = std::max(1u, std::min((unsigned)kSortBlocks, (m + 4095) / 4096));

@@ -360,10 +360,20 @@ __device__ __forceinline__ uint32_t pairset_insert(uint32_t *H, uint32_t key, ui
 // Shared memory (dynamic): K, the staged field values of the tile and its
 // halo in box order (reused for the pair set once the steepest step is
 // done), and P, the up / dn pointers in the same order.
-template <bool kTma>
-__global__ void __launch_bounds__(kThreads, 2)
-    k_tile_local(const void *__restrict__ field, int dtype, TileGeom g, TiledScratch ts,
-                 DevStatus *st, const __grid_constant__ CUtensorMap tmap) {
+// Field of global tile gt: the last field whose first tile is <= gt.
+__device__ __forceinline__ int field_of(const Batch &b, int64_t gt) {
+  int lo = 0, hi = b.n_fields - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (b.fields[mid].tile_base <= gt)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScratch ts, DevStatus *st) {
   extern __shared__ __align__(128) uint32_t dsmem[];
   uint32_t *K = dsmem;         // kExt words: values / keys, then pair-numbering scratch
   uint32_t *P = dsmem + kExt;  // kExt words: up | dn << 16, box indices
@@ -376,23 +386,30 @@ __global__ void __launch_bounds__(kThreads, 2)
   bool nan = false;
   uint32_t parity = 0;
   if (threadIdx.x == 0) s_abort = 0;
-  if (kTma && threadIdx.x == 0) mbar_init(&s_bar, 1);
+  if (threadIdx.x == 0) mbar_init(&s_bar, 1);
   __syncthreads();
 
-  for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+  for (int64_t gt = blockIdx.x; gt < bt.total_tiles; gt += gridDim.x) {
+    const int fi = field_of(bt, gt);
+    const FieldDesc &fd = bt.fields[fi];
+    const TileGeom &g = fd.g;
+    const void *__restrict__ field = fd.field;
+    const int dtype = fd.dtype;
+    const bool tma = fd.tma != 0;
+    const int64_t tile = gt - fd.tile_base;  // within the field
     int64_t x0, y0, z0;
     tile_origin(g, tile, &x0, &y0, &z0);
     // tile and halo entirely inside the field: raw float comparisons
-    const bool raw = kTma && x0 >= 1 && y0 >= 1 && z0 >= 1 && x0 + kTX < g.nx &&
+    const bool raw = tma && x0 >= 1 && y0 >= 1 && z0 >= 1 && x0 + kTX < g.nx &&
                      y0 + kTY < g.ny && z0 + kTZ < g.nz;
 
     // ---- field values of the tile + halo into K
-    if (kTma) {
+    if (tma) {
       if (threadIdx.x == 0) {
         // K was last written by ordinary stores; order them before the copy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&s_bar, (uint32_t)(kExt * 4));
-        tma_load_box(K, &tmap, &s_bar, (int)(x0 - kXO), (int)(y0 - 1), (int)(z0 - 1));
+        tma_load_box(K, &bt.tmaps[fi], &s_bar, (int)(x0 - kXO), (int)(y0 - 1), (int)(z0 - 1));
       }
       if (threadIdx.x == 0) {
         long long polls = 0;
@@ -424,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, 2)
           const int64_t y = y0 + ey - 1, z = z0 + ez - 1;
           const bool row_in = y >= 0 && y < g.ny && z >= 0 && z < g.nz;
           uint32_t b, be = 0;
-          if (kTma) {
+          if (tma) {
             b = K[eb + kXO + lx];
             if (lane < 2) be = K[eb + exe];
           } else {
@@ -452,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       steepest_tile<false>(K, P, lx, ly, col_in, nz_here, w, &nan);
     if (__syncthreads_or(nan)) {
       // the call fails with MS_ERR_NAN_INPUT; skip the rest of this tile
-      if (threadIdx.x == 0) ts.tile_count[tile] = 0;
+      if (threadIdx.x == 0) ts.tile_count[gt] = 0;
       __syncthreads();
       continue;
     }
@@ -495,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     // ---- face roots (final pointers of the tile's face vertices), written
     // cooperatively from P: other tiles' paths enter through these vertices
     {
-      uint32_t *face = ts.face + tile * (int64_t)kFace;
+      uint32_t *face = ts.face + gt * (int64_t)kFace;
       for (int fs = threadIdx.x; fs < kFace; fs += kThreads) {
         int fx, fy, fz;
         face_coords(fs, &fx, &fy, &fz);
@@ -569,8 +586,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     if (threadIdx.x == 0) {
       const long long b = (long long)atomicAdd(ts.pool_count, (unsigned long long)npairs);
       s_base = b;
-      ts.tile_base[tile] = b;
-      ts.tile_count[tile] = npairs;
+      ts.tile_base[gt] = b;
+      ts.tile_count[gt] = npairs;
     }
     __syncthreads();
     {
@@ -590,6 +607,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const uint32_t key = PL[i];
         const int u = (int)(key & 0xffffu), d = (int)(key >> 16);
         ts.pool_roots[at] = make_int2(root_ref(g, x0, y0, z0, d), root_ref(g, x0, y0, z0, u));
+        ts.pool_field[at] = (uint32_t)fi;
       }
     }
     __syncthreads();
@@ -601,7 +619,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       uint32_t packed[kTZ / 2];
 #pragma unroll
       for (int lz = 0; lz < kTZ; lz += 2) packed[lz / 2] = (cell[lz] & 0xffffu) | (cell[lz + 1] << 16);
-      uint4 *pid4 = reinterpret_cast<uint4 *>(ts.pid + tile * (int64_t)kTileV +
+      uint4 *pid4 = reinterpret_cast<uint4 *>(ts.pid + gt * (int64_t)kTileV +
                                               (int64_t)(ly * kTX + lx) * kTZ);
       pid4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
       pid4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
@@ -614,7 +632,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // Follow an exit (a vertex on another tile's face) through the face roots
 // until an extremum; `up` selects the direction.  All indices fit 31 bits
 // (N < 2^31), so the hops use 32-bit arithmetic.
-__device__ int32_t chase(const TileGeom &g, const TiledScratch &ts, int32_t r, bool up,
+__device__ int32_t chase(const TileGeom &g, const uint32_t *__restrict__ face, int32_t r, bool up,
                          DevStatus *st) {
   const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny, gtx = (uint32_t)g.tx,
                  gty = (uint32_t)g.ty;
@@ -627,7 +645,7 @@ __device__ int32_t chase(const TileGeom &g, const TiledScratch &ts, int32_t r, b
     const uint32_t tile = tx + gtx * (ty + gty * tz);
     const int fs = face_slot((int)(x - tx * kTX), (int)(y - ty * kTY), (int)(z - tz * kTZ));
     if (fs < 0) break;
-    const uint32_t w = __ldg(&ts.face[(size_t)tile * kFace + fs]);
+    const uint32_t w = __ldg(&face[(size_t)tile * kFace + fs]);
     const uint32_t loc = up ? (w & 0xffffu) : (w >> 16);
     const uint32_t ez = loc / (kEX * kEY), rr = loc - ez * (kEX * kEY);
     const uint32_t ey = rr / kEX, ex = rr - ey * kEX;
@@ -650,16 +668,22 @@ __device__ __forceinline__ unsigned long long mix64t(unsigned long long k) {
   return k;
 }
 
-__global__ void k_resolve_pairs(TileGeom g, TiledScratch ts, RankScratch rs, DevStatus *st) {
+__global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, DevStatus *st) {
   const unsigned long long npairs = min(*ts.pool_count, ts.pool_cap);
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned int mask = rs.capacity - 1u;
   for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < npairs;
        p += stride) {
     const int2 r = ts.pool_roots[p];
-    const int32_t a = chase(g, ts, r.x, false, st);
-    const int32_t d = chase(g, ts, r.y, true, st);
-    const unsigned long long key = ((unsigned long long)(uint32_t)a << 32) | (uint32_t)d;
+    const uint32_t fi = ts.pool_field[p];
+    const FieldDesc &fd = bt.fields[fi];
+    const uint32_t *face = ts.face + fd.tile_base * (long long)kFace;
+    const int32_t a = chase(fd.g, face, r.x, false, st);
+    const int32_t d = chase(fd.g, face, r.y, true, st);
+    const unsigned long long key =
+        bt.key_mode == kKeyBatch
+            ? (((unsigned long long)fi << 48) | ((unsigned long long)(uint32_t)a << 24) | (uint32_t)d)
+            : (((unsigned long long)(uint32_t)a << 32) | (uint32_t)d);
     // insert into the global pair set (first fit, open addressing)
     unsigned int slot = (unsigned int)mix64t(key) & mask, found = 0xffffffffu;
     for (unsigned int probe = 0; probe < rs.capacity; ++probe) {
@@ -687,40 +711,55 @@ __global__ void k_resolve_pairs(TileGeom g, TiledScratch ts, RankScratch rs, Dev
   }
 }
 
+// Many-field batches: the first sorted pair of each field (its ids start there).
+__global__ void k_field_starts(const unsigned long long *__restrict__ sorted, unsigned int m,
+                               uint32_t *__restrict__ fstart) {
+  const unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const unsigned int f = (unsigned int)(sorted[i] >> 48);
+  if (i == 0 || (unsigned int)(sorted[i - 1] >> 48) != f) fstart[f] = i;
+}
+
 // Per tile: stage the pair table -- each tile pair's (asc, desc) and MS id,
 // read from the global pair set at the pair's slot -- and stream the labels
 // out.  Thread (lane, warp) writes the z-column (x0 + lane, y0 + warp, .);
 // its 16 pair numbers are one 32-byte vector.
-__global__ void __launch_bounds__(kThreads)
-    k_tile_write(TileGeom g, TiledScratch ts, RankScratch rs, int32_t *__restrict__ asc,
-                 int32_t *__restrict__ desc, int32_t *__restrict__ ms) {
+__global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch ts, RankScratch rs) {
   __shared__ int4 T[kStageCap];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t plane = g.nx * g.ny;
-  for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+  for (int64_t gt = blockIdx.x; gt < bt.total_tiles; gt += gridDim.x) {
+    const int fi = field_of(bt, gt);
+    const FieldDesc &fd = bt.fields[fi];
+    const TileGeom &g = fd.g;
+    const int64_t plane = g.nx * g.ny;
     int64_t x0, y0, z0;
-    tile_origin(g, tile, &x0, &y0, &z0);
-    const long long b = ts.tile_base[tile];
-    const int cnt = ts.tile_count[tile];
+    tile_origin(g, gt - fd.tile_base, &x0, &y0, &z0);
+    const long long b = ts.tile_base[gt];
+    const int cnt = ts.tile_count[gt];
     const uint32_t *src = ts.pool_slot + b;
     const bool staged = cnt <= kStageCap;
+    const bool batch = bt.key_mode == kKeyBatch;
+    const int first = batch ? (int)ts.fstart[fi] : 0;
     const int64_t x = x0 + lane, y = y0 + warp;
     const bool col_in = x < g.nx && y < g.ny;
     uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
     if (col_in) {
-      const uint4 *pid4 = reinterpret_cast<const uint4 *>(ts.pid + tile * (int64_t)kTileV +
+      const uint4 *pid4 = reinterpret_cast<const uint4 *>(ts.pid + gt * (int64_t)kTileV +
                                                           (int64_t)(warp * kTX + lane) * kTZ);
       q0 = __ldcs(pid4);
       q1 = __ldcs(pid4 + 1);
     }
+    auto entry = [&](uint32_t sl) {
+      const unsigned long long key = __ldg(&rs.table_keys[sl]);
+      const int r = __ldg(&rs.table_vals[sl]) - first;
+      return batch ? make_int4((int)((key >> 24) & 0xffffffull), (int)(key & 0xffffffull), r, 0)
+                   : make_int4((int)(key >> 32), (int)(uint32_t)key, r, 0);
+    };
     if (staged)
-      for (int i = threadIdx.x; i < cnt; i += kThreads) {
-        const uint32_t sl = __ldcs(src + i);
-        const unsigned long long key = __ldg(&rs.table_keys[sl]);
-        T[i] = make_int4((int)(key >> 32), (int)(uint32_t)key, __ldg(&rs.table_vals[sl]), 0);
-      }
+      for (int i = threadIdx.x; i < cnt; i += kThreads) T[i] = entry(__ldcs(src + i));
     __syncthreads();
     if (col_in) {
+      int32_t *__restrict__ asc = fd.asc, *__restrict__ desc = fd.desc, *__restrict__ ms = fd.ms;
       const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
       const int nz_here = (int)std::min<int64_t>(kTZ, g.nz - z0);
       const int64_t v0 = x + g.nx * y + plane * z0;
@@ -728,14 +767,7 @@ __global__ void __launch_bounds__(kThreads)
       for (int lz = 0; lz < kTZ; ++lz) {
         if (lz >= nz_here) break;
         const int id = (int)((w[lz / 2] >> (16 * (lz & 1))) & 0xffffu);
-        int4 t;
-        if (staged) {
-          t = T[id];
-        } else {
-          const uint32_t sl = src[id];
-          const unsigned long long key = rs.table_keys[sl];
-          t = make_int4((int)(key >> 32), (int)(uint32_t)key, rs.table_vals[sl], 0);
-        }
+        const int4 t = staged ? T[id] : entry(src[id]);
         const int64_t v = v0 + plane * lz;
         __stcs(asc + v, t.x);
         __stcs(desc + v, t.y);
@@ -771,15 +803,15 @@ TileGeom tile_geom(const int64_t dims[3]) {
   return g;
 }
 
-size_t tiled_scratch_bytes(const TileGeom &g, unsigned long long pool_cap) {
-  const size_t pid = (size_t)g.ntiles * kTileV * 2;
-  const size_t face = (size_t)g.ntiles * kFace * 4;
-  const size_t meta = (size_t)g.ntiles * (8 + 4);
-  return 4 * 256 + pid + face + meta + (size_t)pool_cap * (8 + 4) + 8 * 256;
+size_t tiled_scratch_bytes(long long total_tiles, int n_fields, unsigned long long pool_cap) {
+  const size_t pid = (size_t)total_tiles * kTileV * 2;
+  const size_t face = (size_t)total_tiles * kFace * 4;
+  const size_t meta = (size_t)total_tiles * (8 + 4);
+  return 16 * 256 + pid + face + meta + (size_t)pool_cap * (8 + 4 + 4) + (size_t)n_fields * 4;
 }
 
-void tiled_scratch_carve(void *base, const TileGeom &g, unsigned long long pool_cap,
-                         TiledScratch *ts) {
+void tiled_scratch_carve(void *base, long long total_tiles, int n_fields,
+                         unsigned long long pool_cap, TiledScratch *ts) {
   char *p = static_cast<char *>(base);
   auto take = [&](size_t bytes) {
     char *r = p;
@@ -789,10 +821,12 @@ void tiled_scratch_carve(void *base, const TileGeom &g, unsigned long long pool_
   ts->pool_count = reinterpret_cast<unsigned long long *>(take(256));
   ts->pool_slot = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
   ts->pool_roots = reinterpret_cast<int2 *>(take((size_t)pool_cap * 8));
-  ts->tile_base = reinterpret_cast<long long *>(take((size_t)g.ntiles * 8));
-  ts->tile_count = reinterpret_cast<int32_t *>(take((size_t)g.ntiles * 4));
-  ts->face = reinterpret_cast<uint32_t *>(take((size_t)g.ntiles * kFace * 4));
-  ts->pid = reinterpret_cast<uint16_t *>(take((size_t)g.ntiles * kTileV * 2));
+  ts->pool_field = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
+  ts->tile_base = reinterpret_cast<long long *>(take((size_t)total_tiles * 8));
+  ts->tile_count = reinterpret_cast<int32_t *>(take((size_t)total_tiles * 4));
+  ts->face = reinterpret_cast<uint32_t *>(take((size_t)total_tiles * kFace * 4));
+  ts->pid = reinterpret_cast<uint16_t *>(take((size_t)total_tiles * kTileV * 2));
+  ts->fstart = reinterpret_cast<uint32_t *>(take((size_t)n_fields * 4));
   ts->pool_cap = pool_cap;
 }
 
@@ -836,26 +870,35 @@ bool make_box_map(const void *field, int dtype, const TileGeom &g, CUtensorMap *
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-cudaError_t launch_tile_local(const void *field, int dtype, const TileGeom &g,
-                              const TiledScratch &ts, DevStatus *st, cudaStream_t s,
-                              bool allow_tma) {
+void make_field_desc(const void *field, int dtype, const int64_t dims[3], long long tile_base,
+                     int32_t *asc, int32_t *desc, int32_t *ms, bool allow_tma, FieldDesc *fd,
+                     CUtensorMap *map) {
+  fd->field = field;
+  fd->asc = asc;
+  fd->desc = desc;
+  fd->ms = ms;
+  fd->g = tile_geom(dims);
+  fd->tile_base = tile_base;
+  fd->dtype = dtype;
+  memset(map, 0, sizeof(*map));
+  fd->tma = (allow_tma && make_box_map(field, dtype, fd->g, map)) ? 1 : 0;
+}
+
+cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus *st,
+                              cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ts.pool_count, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   constexpr int kSmem = 2 * kExt * 4;
   static_assert(kHash <= kExt, "the pair set reuses the key area");
-  CUtensorMap map;
-  memset(&map, 0, sizeof(map));
-  const bool tma = allow_tma && make_box_map(field, dtype, g, &map);
-  auto kern = tma ? k_tile_local<true> : k_tile_local<false>;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  e = cudaFuncSetAttribute(k_tile_local, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e != cudaSuccess) return e;
-  const int64_t grid = std::min<int64_t>(g.ntiles, (int64_t)sms() * 2);
+  const int64_t grid = std::min<int64_t>(b.total_tiles, (int64_t)sms() * 2);
   ++tl_launches;
-  kern<<<(unsigned)grid, kThreads, kSmem, s>>>(field, dtype, g, ts, st, map);
+  k_tile_local<<<(unsigned)grid, kThreads, kSmem, s>>>(b, ts, st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_resolve_pairs(const TileGeom &g, const TiledScratch &ts, const RankScratch &rs,
+cudaError_t launch_resolve_pairs(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
                                  unsigned long long npairs, DevStatus *st, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(rs.table_keys, 0xff, (size_t)rs.capacity * 8, s);
   if (e != cudaSuccess || npairs == 0) return e;
@@ -863,15 +906,23 @@ cudaError_t launch_resolve_pairs(const TileGeom &g, const TiledScratch &ts, cons
   const unsigned long long cap = (unsigned long long)sms() * 16;
   if (blocks > cap) blocks = cap;
   ++tl_launches;
-  k_resolve_pairs<<<(unsigned)blocks, 256, 0, s>>>(g, ts, rs, st);
+  k_resolve_pairs<<<(unsigned)blocks, 256, 0, s>>>(b, ts, rs, st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_write(const TileGeom &g, const TiledScratch &ts, const RankScratch &rs,
-                              int32_t *asc, int32_t *desc, int32_t *ms, cudaStream_t s) {
-  const int64_t grid = std::min<int64_t>(g.ntiles, (int64_t)sms() * 4);
+cudaError_t launch_field_starts(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
+                                unsigned int m, cudaStream_t s) {
+  if (b.key_mode != kKeyBatch || m == 0) return cudaSuccess;
   ++tl_launches;
-  k_tile_write<<<(unsigned)grid, kThreads, 0, s>>>(g, ts, rs, asc, desc, ms);
+  k_field_starts<<<(m + 255) / 256, 256, 0, s>>>(rs.list, m, ts.fstart);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_write(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
+                              cudaStream_t s) {
+  const int64_t grid = std::min<int64_t>(b.total_tiles, (int64_t)sms() * 4);
+  ++tl_launches;
+  k_tile_write<<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
   return cudaGetLastError();
 }
 

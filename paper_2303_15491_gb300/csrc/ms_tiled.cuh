@@ -3,6 +3,8 @@
 
 #include <stdint.h>
 
+#include <cuda.h>
+
 #include <algorithm>
 
 #include "fastdiv.h"
@@ -38,10 +40,36 @@ struct TileGeom {
   FastDivU32 div_nx, div_ny, div_tx, div_ty;  // coordinates from linear indices
 };
 
+// One field of a (possibly one-field) batch, resident on the device.
+struct FieldDesc {
+  const void *field;
+  int32_t *asc, *desc, *ms;
+  TileGeom g;
+  long long tile_base;  // global index of the field's first tile
+  int dtype;
+  int tma;              // 1: the batch's tmaps[field] describes this field
+};
+
+// Key layouts of the global pair set.
+enum { kKeyOne = 0,     // one field: (asc << 32) | desc
+       kKeyBatch = 1 };  // many fields, each N <= 2^24: (field << 48) | (asc << 24) | desc
+constexpr int64_t kBatchMaxN = 1ll << 24;
+constexpr int kBatchMaxFields = 1 << 16;
+
+struct Batch {
+  const FieldDesc *fields;    // n_fields descriptors
+  const CUtensorMap *tmaps;   // n_fields tensor maps (64-byte aligned)
+  int n_fields;
+  int key_mode;
+  long long total_tiles;
+};
+
 struct TiledScratch {
   unsigned long long *pool_count;  // pairs reserved by all tiles
   unsigned long long pool_cap;
   int2 *pool_roots;   // per tile pair: (dn-root, up-root), global index | kExitFlag if an exit
+  uint32_t *pool_field;  // per tile pair: its field
+  uint32_t *fstart;      // per field: index of its first pair in the sorted pair list
   uint32_t *pool_slot;  // per tile pair: slot of its (asc, desc) pair in the global pair set
   long long *tile_base;
   int32_t *tile_count;
@@ -50,15 +78,20 @@ struct TiledScratch {
 };
 
 TileGeom tile_geom(const int64_t dims[3]);
-size_t tiled_scratch_bytes(const TileGeom &g, unsigned long long pool_cap);
-void tiled_scratch_carve(void *base, const TileGeom &g, unsigned long long pool_cap,
-                         TiledScratch *ts);
-cudaError_t launch_tile_local(const void *field, int dtype, const TileGeom &g,
-                              const TiledScratch &ts, DevStatus *st, cudaStream_t s,
-                              bool allow_tma = true);
-cudaError_t launch_resolve_pairs(const TileGeom &g, const TiledScratch &ts, const RankScratch &rs,
+size_t tiled_scratch_bytes(long long total_tiles, int n_fields, unsigned long long pool_cap);
+void tiled_scratch_carve(void *base, long long total_tiles, int n_fields,
+                         unsigned long long pool_cap, TiledScratch *ts);
+// Host side of a field descriptor (and its tensor map when TMA applies).
+void make_field_desc(const void *field, int dtype, const int64_t dims[3], long long tile_base,
+                     int32_t *asc, int32_t *desc, int32_t *ms, bool allow_tma, FieldDesc *fd,
+                     CUtensorMap *map);
+cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus *st,
+                              cudaStream_t s);
+cudaError_t launch_resolve_pairs(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
                                  unsigned long long npairs, DevStatus *st, cudaStream_t s);
-cudaError_t launch_tile_write(const TileGeom &g, const TiledScratch &ts, const RankScratch &rs,
-                              int32_t *asc, int32_t *desc, int32_t *ms, cudaStream_t s);
+cudaError_t launch_field_starts(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
+                                unsigned int m, cudaStream_t s);
+cudaError_t launch_tile_write(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
+                              cudaStream_t s);
 
 }  // namespace msseg

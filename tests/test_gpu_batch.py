@@ -1,0 +1,80 @@
+"""Batched segmentation: many fields of uneven, non-cubic shapes (float32 and
+float16, smoothed noise and Gaussian sums) in one ms_segment_batch call must
+give, field by field, exactly the oracle's labels -- and exactly what separate
+ms_segment calls give."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2303_15491_gb300 as ms
+import synthfields as sf
+from gpu_util import assert_same_labels
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    h = ms.ms_create(0)
+    yield h
+    ms.ms_destroy(h)
+
+
+def run_batch(ctx, fields):
+    devs = [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in fields]
+    outs = [[torch.empty(f.size, dtype=torch.int32, device="cuda") for _ in range(3)] for f in fields]
+    dims = [ms.dims_of(f) for f in fields]
+    dts = [ms.dtype_code(f) for f in fields]
+    ks = ms.ms_segment_batch(ctx, devs, dims, dts, [o[0] for o in outs], [o[1] for o in outs],
+                             [o[2] for o in outs])
+    return [(o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy(), k) for o, k in zip(outs, ks)]
+
+
+def small_batch(n, seed):
+    specs = sf.batch_specs(n, seed=seed, lo=16, hi=72)
+    return [sf.batch_field(s) for s in specs]
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_batch_matches_oracle(ctx, seed):
+    fields = small_batch(14, seed)
+    assert {f.dtype for f in fields} == {np.dtype(np.float32), np.dtype(np.float16)}
+    for i, (f, got) in enumerate(zip(fields, run_batch(ctx, fields))):
+        assert_same_labels(got, oracle.segment(f), f"batch field {i} {f.shape} {f.dtype}")
+
+
+def test_batch_equals_single_calls_and_is_deterministic(ctx):
+    fields = small_batch(9, 5) + [sf.quantize_levels(sf.smoothed_noise((40, 33, 20), 3, sigma=3.0), 16)]
+    a = run_batch(ctx, fields)
+    b = run_batch(ctx, fields)
+    for f, x, y in zip(fields, a, b):
+        dev = torch.from_numpy(np.ascontiguousarray(f)).cuda()
+        single = ms.segment(ctx, dev)
+        for u, v, w in zip(x[:3], y[:3], single[:3]):
+            assert np.array_equal(u, v) and np.array_equal(u, w.cpu().numpy())
+        assert x[3] == y[3] == single[3]
+
+
+def test_batch_with_flat_field_falls_back(ctx):
+    fields = small_batch(4, 7) + [sf.smoothed_noise((50, 40, 1), 2, sigma=2.0)]
+    for f, got in zip(fields, run_batch(ctx, fields)):
+        assert_same_labels(got, oracle.segment(f), f"mixed batch {f.shape}")
+
+
+def test_batch_nan_fails_whole_call(ctx):
+    fields = small_batch(4, 9)
+    fields[2] = fields[2].copy()
+    fields[2].flat[7] = np.nan
+    with pytest.raises(ms.MSError) as e:
+        run_batch(ctx, fields)
+    assert e.value.name == "MS_ERR_NAN_INPUT"
+
+
+def test_batch_region_count_sum(ctx):
+    fields = small_batch(6, 11)
+    res = run_batch(ctx, fields)
+    assert ms.ms_last_region_count(ctx) == sum(r[3] for r in res)
