@@ -63,6 +63,10 @@ WORKLOADS = {
                        desc="32768^2 fp32 two sigma=300 Gaussians + linear ramp, seed 0"),
     "noise256": dict(dims=(256, 256, 256), kind="noise", dtype="f32",
                      desc="256^3 fp32 sigma=4 smoothed noise, seed 0"),
+    "batch256": dict(dims=None, kind="batch", dtype="mixed",
+                     desc="256 fields, dims log-uniform in [32, 256] per axis, fp32/fp16 and smoothed "
+                          "noise (sigma 2-6) / 8-Gaussian sums 50/50, seed 0; one ms_segment_batch call "
+                          "per step vs 256 ms_segment calls"),
 }
 
 
@@ -231,6 +235,87 @@ def cpu_baseline(args):
                       f"{dt:.1f} s single-threaded)"}
 
 
+def batch_fields():
+    specs = sf.batch_specs(256, seed=0)
+    out = []
+    for i, sp in enumerate(specs):
+        path = os.path.join(cache_dir(), f"batch256_{i:03d}.npy")
+        if os.path.exists(path):
+            out.append(np.load(path))
+            continue
+        f = sf.batch_field(sp)
+        tmp = path + f".{os.getpid()}.tmp.npy"
+        np.save(tmp, f)
+        os.replace(tmp, path)
+        out.append(f)
+    return out
+
+
+def run_batch_bench(args):
+    """Many uneven fields per step: one ms_segment_batch call against the same
+    fields through one ms_segment call each."""
+    import torch
+
+    import paper_2303_15491_gb300 as ms
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local if ws > 1 else 0)
+    dev = torch.cuda.current_device()
+    fields_np = batch_fields()
+    fields = [torch.from_numpy(f).to(dev) for f in fields_np]
+    outs = [[torch.empty(f.size, dtype=torch.int32, device=dev) for _ in range(3)] for f in fields_np]
+    dims = [ms.dims_of(f) for f in fields_np]
+    dts = [ms.dtype_code(f) for f in fields_np]
+    n = int(sum(f.size for f in fields_np))
+    stream = torch.cuda.Stream(device=dev)
+    ctx = ms.ms_create(dev, stream)
+    asc, desc, mso = [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs]
+
+    def batched():
+        return ms.ms_segment_batch(ctx, fields, dims, dts, asc, desc, mso)
+
+    def plain():
+        for f, o in zip(fields, outs):
+            ms.ms_segment(ctx, f, ms.dims_of(f), ms.dtype_code(f), o[0], o[1], o[2])
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        t = time.perf_counter()
+        for _ in range(steps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return max(ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t)) / steps
+
+    ms.ms_profile_enable(ctx, True)
+    with ClockSampler(dev) as clk:
+        t_batch = timed(batched, args.steps)
+    prof = ms.ms_profile_read(ctx)
+    ms.ms_profile_enable(ctx, False)
+    t_plain = timed(plain, max(1, args.steps // 4))
+    ks = batched()
+    ms.ms_destroy(ctx)
+    line = {
+        "metric": METRIC, "value": n / (t_batch / 1e3), "unit": "vertices/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "batch256", "desc": WORKLOADS["batch256"]["desc"], "fields": len(fields),
+                   "vertices": n, "regions_K_total": int(sum(ks)),
+                   "l2": "fields 1.1 GB + labels 3.6 GB, larger than L2"},
+        "plain_ms_per_step": t_plain, "speedup_vs_plain": t_plain / t_batch,
+        "gpu_launches": prof["launches"],
+        "stages_ms_per_step": {k: v["ms"] / max(1, prof["calls"]) for k, v in prof["stages"].items()
+                               if v["launches"] or v["ms"]},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -245,8 +330,14 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.impl == "reference" and args.workload != "batch256":
         return run_reference(args)
+    if args.workload == "batch256":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no CPU "
+                              "reference arm; the oracle arm runs on the 512^3 workload"}))
+            return 0
+        return run_batch_bench(args)
 
     import torch
 
