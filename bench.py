@@ -238,7 +238,11 @@ def cpu_baseline(args):
 def batch_fields():
     specs = sf.batch_specs(256, seed=0)
     out = []
+    t0 = time.perf_counter()
     for i, sp in enumerate(specs):
+        if i % 32 == 0:
+            print(f"[bench] batch fields {i}/256 ({time.perf_counter() - t0:.0f} s)", file=sys.stderr,
+                  flush=True)
         path = os.path.join(cache_dir(), f"batch256_{i:03d}.npy")
         if os.path.exists(path):
             out.append(np.load(path))
@@ -291,9 +295,12 @@ def run_batch_bench(args):
         torch.cuda.synchronize()
         return max(ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t)) / steps
 
+    print("[bench] fields on device; timing the batched call", file=sys.stderr, flush=True)
     ms.ms_profile_enable(ctx, True)
     with ClockSampler(dev) as clk:
         t_batch = timed(batched, args.steps)
+    print(f"[bench] batched {t_batch:.2f} ms/step; timing 256 single calls", file=sys.stderr,
+          flush=True)
     prof = ms.ms_profile_read(ctx)
     ms.ms_profile_enable(ctx, False)
     t_plain = timed(plain, max(1, args.steps // 4))

@@ -169,6 +169,7 @@ ms_status rank_pairs(ms_ctx *c, const int32_t *asc, const int32_t *desc, int64_t
     if (s != MS_OK) return s;
     RankScratch rs;
     rank_scratch_carve(c->scratch, cap, &rs);
+    if (guess < bound) rs.probe_limit = kEstimateProbeLimit;
     MS_TRY(cudaMemsetAsync(&c->dst->n_unique, 0, sizeof(unsigned int), c->stream));
     MS_TRY(cudaMemsetAsync(&c->dst->hash_overflow, 0, sizeof(unsigned int), c->stream));
     MS_TRY(launch_pairs_insert(asc, desc, n, rs, c->dst, c->stream));
@@ -333,6 +334,7 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
     s = ensure_scratch(c, rank_scratch_bytes(hcap));
     if (s != MS_OK) return s;
     rank_scratch_carve(c->scratch, hcap, &rs);
+    if (want < exact) rs.probe_limit = kEstimateProbeLimit;
     MS_TRY(cudaMemsetAsync(&c->dst->n_unique, 0, sizeof(unsigned int), c->stream));
     MS_TRY(cudaMemsetAsync(&c->dst->hash_overflow, 0, sizeof(unsigned int), c->stream));
     MS_TRY(launch_resolve_pairs(b, ts, rs, npairs, c->dst, c->stream));

@@ -67,8 +67,14 @@ struct RankScratch {
   unsigned int *hist;              // 256 * kSortBlocks
   unsigned int capacity;           // power of two
   unsigned int max_unique;         // capacity / 2
+  unsigned int probe_limit;        // longest insert probe before the set counts as full
 };
 constexpr int kSortBlocks = 240;
+// Insert probes allowed when the set was sized from an estimate: at a load
+// factor of at most one half such a run essentially never happens, and a
+// full-capacity probe on an over-full set would take time quadratic in its
+// size.  Sets sized from an exact bound probe up to their capacity.
+constexpr unsigned int kEstimateProbeLimit = 256;
 size_t rank_scratch_bytes(unsigned int capacity);
 void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs);
 cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t n,

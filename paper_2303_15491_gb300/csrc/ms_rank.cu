@@ -35,9 +35,10 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
 __device__ __forceinline__ unsigned int lane_id() { return threadIdx.x & 31u; }
 
 __device__ void table_insert(const RankScratch &rs, unsigned long long key, DevStatus *st) {
+  if (*(volatile unsigned int *)&st->hash_overflow) return;  // the caller retries larger
   const unsigned int mask = rs.capacity - 1u;
   unsigned int slot = (unsigned int)mix64(key) & mask;
-  for (unsigned int probe = 0; probe < rs.capacity; ++probe) {
+  for (unsigned int probe = 0; probe < rs.probe_limit; ++probe) {
     unsigned long long cur = *(volatile unsigned long long *)&rs.table_keys[slot];
     if (cur == key) return;
     if (cur == kEmpty) {
@@ -229,6 +230,7 @@ void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs) {
   char *p = static_cast<char *>(base);
   rs->capacity = capacity;
   rs->max_unique = capacity / 2;
+  rs->probe_limit = capacity;
   rs->table_keys = reinterpret_cast<unsigned long long *>(p);
   p += (size_t)capacity * 8;
   rs->list = reinterpret_cast<unsigned long long *>(p);

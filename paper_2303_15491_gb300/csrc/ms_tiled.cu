@@ -684,9 +684,11 @@ __global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, DevSt
         bt.key_mode == kKeyBatch
             ? (((unsigned long long)fi << 48) | ((unsigned long long)(uint32_t)a << 24) | (uint32_t)d)
             : (((unsigned long long)(uint32_t)a << 32) | (uint32_t)d);
-    // insert into the global pair set (first fit, open addressing)
+    // insert into the global pair set (first fit, open addressing); stop as
+    // soon as the set is known to be too small (the host retries larger)
     unsigned int slot = (unsigned int)mix64t(key) & mask, found = 0xffffffffu;
-    for (unsigned int probe = 0; probe < rs.capacity; ++probe) {
+    if (*(volatile unsigned int *)&st->hash_overflow) continue;
+    for (unsigned int probe = 0; probe < rs.probe_limit; ++probe) {
       unsigned long long cur = *(volatile unsigned long long *)&rs.table_keys[slot];
       if (cur == ~0ull) {
         cur = atomicCAS(&rs.table_keys[slot], ~0ull, key);

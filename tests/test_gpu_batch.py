@@ -78,3 +78,28 @@ def test_batch_region_count_sum(ctx):
     fields = small_batch(6, 11)
     res = run_batch(ctx, fields)
     assert ms.ms_last_region_count(ctx) == sum(r[3] for r in res)
+
+
+def test_batch_with_many_distinct_pairs(ctx):
+    """Barely smoothed noise: a large share of the tile pairs are distinct
+    final pairs, so the first (estimated) pair-set size is too small and the
+    call must retry with the exact bound -- correctly and quickly."""
+    fields = [sf.smoothed_noise((48, 40, 36), s, sigma=0.6, radius=2) for s in range(6)]
+    fresh = ms.ms_create(0)  # no size hint from earlier calls
+    try:
+        for f, got in zip(fields, run_batch(fresh, fields)):
+            assert_same_labels(got, oracle.segment(f), f"noisy batch {f.shape}")
+    finally:
+        ms.ms_destroy(fresh)
+
+
+def test_single_field_many_distinct_pairs(ctx):
+    f = sf.smoothed_noise((96, 80, 72), 8, sigma=0.5, radius=2)
+    fresh = ms.ms_create(0)
+    try:
+        dev = torch.from_numpy(f).cuda()
+        got = ms.segment(fresh, dev)
+        got = (got[0].cpu().numpy(), got[1].cpu().numpy(), got[2].cpu().numpy(), got[3])
+        assert_same_labels(got, oracle.segment(f), "noisy single field")
+    finally:
+        ms.ms_destroy(fresh)
