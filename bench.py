@@ -63,6 +63,11 @@ WORKLOADS = {
                        desc="32768^2 fp32 two sigma=300 Gaussians + linear ramp, seed 0"),
     "noise256": dict(dims=(256, 256, 256), kind="noise", dtype="f32",
                      desc="256^3 fp32 sigma=4 smoothed noise, seed 0"),
+    "serve": dict(dims=None, kind="serve", dtype="f32",
+                  desc="request loop: 64 requests (2D squares side log-uniform 512-16384, 3D cubes "
+                       "side log-uniform 64-768, 50/50), fp32 sub-boxes of sigma=4 smoothed-noise "
+                       "bases (16384^2 and 768^3, generated on the device), 120 GB budget; "
+                       "saturation and Poisson arrivals vs the plain one-call-per-field path"),
     "batch256": dict(dims=None, kind="batch", dtype="mixed",
                      desc="256 fields, dims log-uniform in [32, 256] per axis, fp32/fp16 and smoothed "
                           "noise (sigma 2-6) / 8-Gaussian sums 50/50, seed 0; one ms_segment_batch call "
@@ -323,6 +328,187 @@ def run_batch_bench(args):
     return 0
 
 
+def device_smoothed_noise(shape, seed, dev, sigma=4.0, radius=16):
+    """Seeded N(0,1) white noise on the device, filtered by a periodic
+    Gaussian (sigma, truncated at radius) one axis after the other: the
+    smoothed-noise recipe of the synthetic fields, generated where it is used
+    so that multi-GB bases need no host round trip."""
+    import torch
+    import torch.nn.functional as F
+
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    x = torch.randn(shape, generator=g, device=dev, dtype=torch.float32)
+    t = torch.arange(-radius, radius + 1, device=dev, dtype=torch.float64)
+    w = torch.exp(-0.5 * (t / sigma) ** 2)
+    w = (w / w.sum()).float().view(1, 1, -1)
+    for ax in range(x.ndim):
+        if x.shape[ax] == 1:
+            continue
+        y = x.movedim(ax, -1).contiguous()
+        sh = y.shape
+        y = y.view(-1, 1, sh[-1])
+        out = torch.empty_like(y)
+        rows = max(1, (1 << 27) // sh[-1])  # bound the padded temporaries
+        for r0 in range(0, y.shape[0], rows):
+            yy = F.pad(y[r0:r0 + rows], (radius, radius), mode="circular")
+            out[r0:r0 + rows] = F.conv1d(yy, w)
+        del y
+        x = out.view(sh).movedim(-1, ax).contiguous()
+        del out
+    return x
+
+
+def run_serve_bench(args):
+    """The request loop (ms_server) against the plain path on the same requests:
+    (1) saturation -- all requests submitted at once -- for throughput, and
+    (2) a Poisson stream at a stated rate for p50 / p99 latency, through the
+    server with --slots slots and through a one-slot server (the plain path
+    behind a FIFO queue)."""
+    import torch
+
+    import paper_2303_15491_gb300 as ms
+
+    torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    specs = sf.serve_specs(args.serve_requests, seed=0)
+    rng = np.random.default_rng(12345)
+    side2 = max(d[0] for d, _ in specs if d[2] == 1)
+    side3 = max(d[0] for d, _ in specs if d[2] > 1)
+    t0 = time.perf_counter()
+    base2 = device_smoothed_noise((side2, side2), 1, dev)
+    base3 = device_smoothed_noise((side3, side3, side3), 2, dev)
+    reqs = []
+    for dims, _ in specs:
+        s_ = dims[0]
+        if dims[2] == 1:
+            y0, x0 = (int(v) for v in rng.integers(0, side2 - s_ + 1, size=2))
+            f = base2[y0:y0 + s_, x0:x0 + s_].contiguous()
+        else:
+            z0, y0, x0 = (int(v) for v in rng.integers(0, side3 - s_ + 1, size=3))
+            f = base3[z0:z0 + s_, y0:y0 + s_, x0:x0 + s_].contiguous()
+        outs = [torch.empty(f.numel(), dtype=torch.int32, device=dev) for _ in range(3)]
+        reqs.append((f, tuple(dims), outs))
+    del base2, base3
+    torch.cuda.synchronize()
+    nvert = [int(f.numel()) for f, _, _ in reqs]
+    total = int(sum(nvert))
+    print(f"[bench] {len(reqs)} requests, {total / 1e9:.2f} G vertices on device "
+          f"({time.perf_counter() - t0:.0f} s)", file=sys.stderr, flush=True)
+
+    # ---- plain path: one ms_segment call after the other on one context
+    stream = torch.cuda.Stream(device=dev)
+    ctx = ms.ms_create(dev, stream)
+    for f, dims, o in reqs:  # warm: scratch grows to the largest request
+        ms.ms_segment(ctx, f, dims, ms.MS_F32, *o)
+    plain_k = []
+    service = []
+    ms.ms_profile_enable(ctx, True)
+    t = time.perf_counter()
+    for f, dims, o in reqs:
+        ti = time.perf_counter()
+        ms.ms_segment(ctx, f, dims, ms.MS_F32, *o)  # returns after completion
+        service.append(time.perf_counter() - ti)
+        plain_k.append(ms.ms_last_region_count(ctx))
+    t_plain = time.perf_counter() - t
+    plain_launches = ms.ms_profile_read(ctx)["launches"]
+    ms.ms_destroy(ctx)
+
+    budget = int(args.serve_budget_gb * (1 << 30))
+
+    def run_stream(slots, arrivals):
+        """Submit request j at arrivals[j] (seconds from the start; None = all at
+        once); returns (makespan s, latencies ms, stats, region counts)."""
+        srv = ms.ms_server_create(dev, budget, slots)
+        try:
+            # warm every slot's scratch: `slots` copies of the largest 2D and of
+            # the largest 3D request at once (an idle slot takes one each)
+            for big in (max((r for r in reqs if r[1][2] == 1), key=lambda r: r[0].numel()),
+                        max((r for r in reqs if r[1][2] > 1), key=lambda r: r[0].numel())):
+                f, dims, _ = big
+                tmp = [[torch.empty(f.numel(), dtype=torch.int32, device=dev) for _ in range(3)]
+                       for _ in range(slots)]
+                torch.cuda.synchronize()
+                ts = [ms.ms_server_submit(srv, f, dims, ms.MS_F32, *o) for o in tmp]
+                for tk in ts:
+                    ms.ms_server_wait(srv, tk, -1)
+                del tmp
+            base = ms.ms_server_stats(srv)
+            order = list(range(len(arrivals)))
+            tickets, sub_t = [None] * len(order), [0.0] * len(order)
+            lat, ks, pending = [0.0] * len(order), [0] * len(order), {}
+            start = time.perf_counter()
+            for j in order:
+                i = j % len(reqs)
+                if i in pending:  # the previous use of request i's buffers must be done
+                    jp = pending.pop(i)
+                    st, ks[jp], lat[jp] = ms.ms_server_wait(srv, tickets[jp], -1)
+                    assert st == 0, ms.STATUS[st]
+                if arrivals[j] is not None:
+                    delay = start + arrivals[j] - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                f, dims, o = reqs[i]
+                sub_t[j] = time.perf_counter() - start
+                tickets[j] = ms.ms_server_submit(srv, f, dims, ms.MS_F32, *o)
+                pending[i] = j
+            for i, jp in pending.items():
+                st, ks[jp], lat[jp] = ms.ms_server_wait(srv, tickets[jp], -1)
+                assert st == 0, ms.STATUS[st]
+            makespan = max(sub_t[j] + lat[j] / 1e3 for j in order)
+            stats = ms.ms_server_stats(srv)
+            stats["launches"] -= base["launches"]
+        finally:
+            ms.ms_server_destroy(srv)
+        return makespan, lat, stats, ks
+
+    def pct(xs, q):
+        return float(np.percentile(np.asarray(xs), q))
+
+    # ---- saturation: every request submitted at once, passes times over
+    n_sat = len(reqs) * args.serve_passes
+    with ClockSampler(dev) as clk:
+        sat_t, sat_lat, sat_stats, sat_k = run_stream(args.slots, [None] * n_sat)
+    sat_vps = total * args.serve_passes / sat_t
+    plain_vps = total / t_plain
+    print(f"[bench] plain {t_plain * 1e3:.1f} ms/pass, saturated server "
+          f"{sat_t * 1e3 / args.serve_passes:.1f} ms/pass", file=sys.stderr, flush=True)
+    assert sat_k[:len(reqs)] == plain_k, "served region counts differ from the plain path"
+
+    # ---- Poisson arrivals at rho x the plain path's request capacity
+    rate = args.serve_load * len(reqs) / t_plain  # requests per second
+    gaps = np.random.default_rng(777).exponential(1.0 / rate, size=n_sat)
+    arrivals = list(np.cumsum(gaps) - gaps[0])
+    p_t, p_lat, p_stats, _ = run_stream(args.slots, arrivals)
+    q_t, q_lat, _, _ = run_stream(1, arrivals)
+    line = {
+        "metric": METRIC, "value": sat_vps, "unit": "vertices/s", "n_gpus": 1,
+        "steps": args.serve_passes, "warmup": 1, "ms_per_step": sat_t * 1e3 / args.serve_passes,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "serve", "desc": WORKLOADS["serve"]["desc"], "requests": len(reqs),
+                   "vertices_per_pass": total, "slots": args.slots,
+                   "budget_bytes": budget, "l2": "inputs and labels larger than L2"},
+        "plain": {"ms_per_pass": t_plain * 1e3, "vertices_per_s": plain_vps,
+                  "service_ms_p50": 1e3 * pct(service, 50), "service_ms_p99": 1e3 * pct(service, 99)},
+        "speedup_vs_plain": sat_vps / plain_vps,
+        "saturated": {"latency_ms_p50": pct(sat_lat, 50), "latency_ms_p99": pct(sat_lat, 99),
+                      "peak_bytes": sat_stats["peak_bytes"]},
+        "poisson": {"rate_req_per_s": rate, "load_vs_plain_capacity": args.serve_load,
+                    "requests": n_sat,
+                    "served": {"latency_ms_p50": pct(p_lat, 50), "latency_ms_p99": pct(p_lat, 99),
+                               "vertices_per_s": total * args.serve_passes / p_t,
+                               "peak_bytes": p_stats["peak_bytes"]},
+                    "plain_fifo": {"latency_ms_p50": pct(q_lat, 50), "latency_ms_p99": pct(q_lat, 99),
+                                   "vertices_per_s": total * args.serve_passes / q_t}},
+        "gpu_launches": sat_stats["launches"],
+        "plain_gpu_launches": plain_launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,9 +520,20 @@ def main():
     ap.add_argument("--cpu-slab", type=int, default=48)
     ap.add_argument("--ref-slab", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-passes", type=int, default=6)
+    ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "serve":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no CPU "
+                              "reference arm; the oracle arm runs on the 512^3 workload"}))
+            return 0
+        return run_serve_bench(args)
     if args.impl == "reference" and args.workload != "batch256":
         return run_reference(args)
     if args.workload == "batch256":

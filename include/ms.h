@@ -153,6 +153,52 @@ ms_status ms_pair_rank(ms_ctx *ctx, const int32_t *asc, const int32_t *desc, int
                        int32_t *ms, int64_t *k_out);
 
 
+/* ---- serving ---------------------------------------------------------------- */
+
+/* A request loop for segmentations of mixed sizes.  The server owns n_slots
+ * worker threads, each with its own context (stream and resident scratch) on
+ * `device`, so requests run concurrently and their kernels overlap on the GPU.
+ * A submitted request waits until a slot is idle and its estimated device
+ * memory -- its field and three label arrays plus about 10 bytes of scratch
+ * per vertex -- fits in what budget_bytes has left; among waiting requests the
+ * first that fits is admitted (one passed over 8 times is admitted next, once
+ * it fits).  Results are exactly those of ms_segment. */
+typedef struct ms_server ms_server;
+
+typedef struct {
+  uint64_t admitted, completed, queued; /* requests */
+  size_t bytes_in_use;                  /* estimated bytes of running requests */
+  size_t peak_bytes;                    /* the largest bytes_in_use so far */
+  size_t budget_bytes;
+  uint64_t launches;                    /* kernel launches of completed requests */
+} ms_server_info;
+
+/* n_slots in [1, 64], budget_bytes > 0.  *out is set only on MS_OK. */
+ms_status ms_server_create(ms_server **out, int device, size_t budget_bytes, int n_slots);
+
+/* Queue one segmentation (arguments as ms_segment, device pointers).  The
+ * field must already hold its values -- the server's streams do not wait on
+ * the caller's -- and all four buffers must stay valid and untouched until the
+ * request completes.  *ticket identifies it.  A request whose
+ * estimate exceeds the whole budget is refused with MS_ERR_TOO_LARGE. */
+ms_status ms_server_submit(ms_server *srv, const void *field, const int64_t dims[3],
+                           ms_dtype dtype, int32_t *out_asc, int32_t *out_desc, int32_t *out_ms,
+                           uint64_t *ticket);
+
+/* Wait up to timeout_ms (< 0: no limit) for a request.  MS_OK: it completed,
+ * *result (may be NULL) holds its status, *k_out its region count and
+ * *latency_ms the time from submission to completion (both may be NULL); the
+ * ticket is then released.  MS_ERR_TIMEOUT: still running (wait again).
+ * MS_ERR_INVALID_ARG: unknown ticket. */
+ms_status ms_server_wait(ms_server *srv, uint64_t ticket, int64_t timeout_ms, ms_status *result,
+                         int64_t *k_out, double *latency_ms);
+
+ms_status ms_server_stats(ms_server *srv, ms_server_info *out);
+
+/* Finish every submitted request, then stop the workers and free the
+ * contexts.  NULL is a no-op. */
+ms_status ms_server_destroy(ms_server *srv);
+
 /* ---- step 4 without allocation --------------------------------------------- */
 
 /* Largest n that ms_pair_rank_noalloc accepts (64^3 vertices). */

@@ -24,7 +24,8 @@ __all__ = [
     "ms_segment", "ms_segment_host", "ms_last_region_count", "ms_order_keys", "ms_steepest",
     "ms_compress", "ms_pair_rank", "segment", "EXPORTED_SYMBOLS", "ms_profile_enable",
     "ms_profile_read", "ms_profile_stage_name", "STAGES", "ms_segment_staged",
-    "ms_pair_rank_noalloc", "MS_NOALLOC_MAX_N", "ms_segment_batch",
+    "ms_pair_rank_noalloc", "MS_NOALLOC_MAX_N", "ms_segment_batch", "ms_server_create",
+    "ms_server_submit", "ms_server_wait", "ms_server_stats", "ms_server_destroy",
 ]
 
 MS_F32, MS_F16 = 0, 1
@@ -36,9 +37,17 @@ EXPORTED_SYMBOLS = [
     "ms_status_string", "ms_create", "ms_destroy", "ms_segment", "ms_segment_host",
     "ms_last_region_count", "ms_order_keys", "ms_steepest", "ms_compress", "ms_pair_rank",
     "ms_profile_enable", "ms_profile_read", "ms_profile_stage_name", "ms_segment_staged",
-    "ms_pair_rank_noalloc", "ms_segment_batch",
+    "ms_pair_rank_noalloc", "ms_segment_batch", "ms_server_create", "ms_server_submit",
+    "ms_server_wait", "ms_server_stats", "ms_server_destroy",
 ]
 MS_NOALLOC_MAX_N = 262144
+
+
+class _ServerInfo(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("queued", ctypes.c_uint64), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+                ("launches", ctypes.c_uint64)]
 STAGES = ["tile_local", "resolve", "write", "h2d", "d2h"]
 
 
@@ -77,6 +86,15 @@ def load(build: bool = True) -> ctypes.CDLL:
             L.ms_segment.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
             L.ms_segment_batch.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                            c_i64p]
+            L.ms_server_create.argtypes = [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_size_t,
+                                           ctypes.c_int]
+            L.ms_server_submit.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp,
+                                           ctypes.POINTER(ctypes.c_uint64)]
+            L.ms_server_wait.argtypes = [c_vp, ctypes.c_uint64, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int), c_i64p,
+                                         ctypes.POINTER(ctypes.c_double)]
+            L.ms_server_stats.argtypes = [c_vp, ctypes.POINTER(_ServerInfo)]
+            L.ms_server_destroy.argtypes = [c_vp]
             L.ms_segment_staged.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
             L.ms_segment_host.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
             L.ms_last_region_count.argtypes = [c_vp, c_i64p]
@@ -174,6 +192,39 @@ def ms_segment_batch(ctx, fields, dims_list, dtypes, ascs, descs, mss) -> list:
     _check(load().ms_segment_batch(ctx, n, ptrs(fields), ctypes.cast(dims, c_vp), ctypes.cast(dts, c_vp),
                                    ptrs(ascs), ptrs(descs), ptrs(mss), ks), "ms_segment_batch")
     return [int(k) for k in ks]
+
+
+def ms_server_create(device: int = 0, budget_bytes: int = 120 << 30, n_slots: int = 4) -> int:
+    h = c_vp()
+    _check(load().ms_server_create(ctypes.byref(h), int(device), int(budget_bytes), int(n_slots)),
+           "ms_server_create")
+    return h.value
+
+
+def ms_server_submit(srv, field, dims, dtype, out_asc, out_desc, out_ms) -> int:
+    t = ctypes.c_uint64(0)
+    _check(load().ms_server_submit(srv, _ptr(field), _dims(dims), int(dtype), _ptr(out_asc),
+                                   _ptr(out_desc), _ptr(out_ms), ctypes.byref(t)), "ms_server_submit")
+    return int(t.value)
+
+
+def ms_server_wait(srv, ticket: int, timeout_ms: int = -1):
+    """(status, K, latency_ms) of a finished request; raises MSError with
+    MS_ERR_TIMEOUT if it is still running after timeout_ms."""
+    st, k, lat = ctypes.c_int(0), ctypes.c_int64(0), ctypes.c_double(0.0)
+    _check(load().ms_server_wait(srv, int(ticket), int(timeout_ms), ctypes.byref(st), ctypes.byref(k),
+                                 ctypes.byref(lat)), "ms_server_wait")
+    return int(st.value), int(k.value), float(lat.value)
+
+
+def ms_server_stats(srv) -> dict:
+    i = _ServerInfo()
+    _check(load().ms_server_stats(srv, ctypes.byref(i)), "ms_server_stats")
+    return {f: int(getattr(i, f)) for f, _ in _ServerInfo._fields_}
+
+
+def ms_server_destroy(srv) -> None:
+    _check(load().ms_server_destroy(srv), "ms_server_destroy")
 
 
 def ms_segment_staged(ctx, field, dims, dtype, out_asc, out_desc, out_ms) -> None:

@@ -631,12 +631,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
 
 // Follow an exit (a vertex on another tile's face) through the face roots
 // until an extremum; `up` selects the direction.  All indices fit 31 bits
-// (N < 2^31), so the hops use 32-bit arithmetic.
+// (N < 2^31), so the hops use 32-bit arithmetic.  A path may leave and
+// re-enter the same tile many times, so the number of hops is not bounded by
+// the tile count; but every hop lands on a different halo vertex of the same
+// strictly monotone path, so it is bounded by the number of face slots and by
+// N.  The cap only guards against a corrupted face array.
 __device__ int32_t chase(const TileGeom &g, const uint32_t *__restrict__ face, int32_t r, bool up,
                          DevStatus *st) {
   const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny, gtx = (uint32_t)g.tx,
                  gty = (uint32_t)g.ty;
-  for (int64_t hop = 0; hop <= g.ntiles; ++hop) {
+  const int64_t n = g.nx * g.ny * g.nz, slots = g.ntiles * kFace;
+  const int64_t max_hops = n < slots ? n : slots;
+  for (int64_t hop = 0; hop <= max_hops; ++hop) {
     if (!(r & kExitFlag)) return r;
     uint32_t q, x, y, z;
     g.div_nx.divmod((uint32_t)(r & ~kExitFlag), &q, &x);
@@ -838,18 +844,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_tiled_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {  // initialised once, thread-safe
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
+    const bool ok = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                     cudaEnableDefault, &q) == cudaSuccess &&
+                    q == cudaDriverEntryPointSuccess;
     cudaGetLastError();
-  }
+    return ok ? reinterpret_cast<EncodeTiledFn>(p) : nullptr;
+  }();
   return fn;
 }
 

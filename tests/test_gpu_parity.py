@@ -335,3 +335,39 @@ def test_nan_in_interior_tile(ctx):
     with pytest.raises(ms.MSError) as e:
         gpu_segment(ctx, f)
     assert e.value.name == "MS_ERR_NAN_INPUT"
+
+
+def zigzag_field(nx=64, ny=40, nz=40, x0=31):
+    """A strictly increasing path that steps +(1,1,0) and (-1,0,-1) in turn,
+    so it crosses the x tile face between x0 and x0+1 at every step (about
+    2 min(ny, nz) crossings of the same two tiles, far more than there are
+    tiles), on a low smooth background."""
+    f = sf.smoothed_noise((nx, ny, nz), 41, sigma=2.0) - np.float32(1000.0)
+    x, y, z = x0, 0, nz - 1
+    k = 0
+    while True:
+        f[z, y, x] = k
+        k += 1
+        if k % 2 == 1:
+            x, y = x + 1, y + 1
+        else:
+            x, z = x - 1, z - 1
+        if y >= ny or z < 0:
+            break
+    return f
+
+
+@pytest.mark.parametrize("sign", [1, -1])
+def test_paths_reentering_the_same_tiles(ctx, sign):
+    """A steepest path may leave and re-enter the same tiles many times: the
+    number of face hops is not bounded by the tile count."""
+    f = zigzag_field()
+    if sign < 0:  # the same path for steepest descent
+        f = -f
+    run_and_compare(ctx, f, f"zigzag path sign {sign}")
+
+
+def test_small_grid_with_more_face_hops_than_tiles(ctx):
+    # 18^3 has 4 tiles; a descending path of this seeded field changes tiles 5 times
+    f = sf.smoothed_noise((18, 18, 18), 109732, sigma=2.5)
+    run_and_compare(ctx, f, "18^3 smoothed noise")
