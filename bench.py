@@ -63,6 +63,8 @@ WORKLOADS = {
                        desc="32768^2 fp32 two sigma=300 Gaussians + linear ramp, seed 0"),
     "noise256": dict(dims=(256, 256, 256), kind="noise", dtype="f32",
                      desc="256^3 fp32 sigma=4 smoothed noise, seed 0"),
+    "noise384": dict(dims=(384, 384, 384), kind="noise", dtype="f32",
+                     desc="384^3 fp32 sigma=4 smoothed noise, seed 0 (profiling size)"),
     "serve": dict(dims=None, kind="serve", dtype="f32",
                   desc="request loop: 64 requests (2D squares side log-uniform 512-16384, 3D cubes "
                        "side log-uniform 64-768, 50/50), fp32 sub-boxes of sigma=4 smoothed-noise "

@@ -23,6 +23,8 @@ struct ms_ctx {
   size_t io_bytes = 0;
   void *tscratch = nullptr;  // tiled path working memory
   size_t tscratch_bytes = 0;
+  void *graph = nullptr;     // the face graph, built only for long exit chains
+  size_t graph_bytes = 0;
   unsigned long long *hcount = nullptr;  // pinned copy of the tiled pair count
   unsigned long long pool_hint = 0;      // pair-pool capacity that sufficed last time
   void *batch_dev = nullptr;             // field descriptors + tensor maps on the device
@@ -239,6 +241,27 @@ ms_status ensure_buffer(ms_ctx *c, void **buf, size_t *have, size_t bytes) {
   return MS_OK;
 }
 
+// Pointer-jumps the face graph until every entry is final: `first` rounds
+// queued blind, one status read, then the rest of the cap if needed.
+// Pointer-jumps the face graph until every entry is final: a few rounds
+// queued blind, then one round at a time with a status read after each
+// (rounds over large graphs cost far more than the read).
+ms_status jump_face_graph(ms_ctx *c, const Batch &b, int2 *graph, long long slots) {
+  const int cap = std::min(64, round_cap(slots));
+  const int blind = std::min(cap, slots > (1ll << 24) ? 3 : 6);
+  MS_TRY(cudaMemsetAsync(c->dst->round_open, 0, sizeof(c->dst->round_open), c->stream));
+  MS_TRY(launch_face_graph_rounds(b, graph, 0, blind, c->dst, c->stream));
+  ms_status s = read_status(c);
+  if (s != MS_OK) return s;
+  for (int r = blind;; ++r) {
+    if (c->hst->round_open[r - 1] == 0u) return MS_OK;
+    if (r == cap) return MS_ERR_NOT_CONVERGED;
+    MS_TRY(launch_face_graph_rounds(b, graph, r, r + 1, c->dst, c->stream));
+    s = read_status(c);
+    if (s != MS_OK) return s;
+  }
+}
+
 // The tiled path (ms_tiled.cu): tile-local steepest + compression + pair
 // numbering, global resolution of tile exits and pair ranks, label write.
 // One field of a segmentation request, as the tiled path sees it.
@@ -277,14 +300,24 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
   MS_TRY(cudaStreamSynchronize(c->stream));  // the staging buffer may still be in flight
   FieldDesc *hd = static_cast<FieldDesc *>(c->batch_host);
   CUtensorMap *hm = reinterpret_cast<CUtensorMap *>(static_cast<char *>(c->batch_host) + desc_bytes);
-  long long total_tiles = 0;
+  // descriptor j describes field order[j]: the 3D fields first, then the 2D
+  // ones, so that each tile shape's kernels cover one contiguous tile range
+  std::vector<int> order;
+  order.reserve(nf);
+  for (int f = 0; f < nf; ++f)
+    if (fa[f].dims[2] != 1) order.push_back(f);
+  for (int f = 0; f < nf; ++f)
+    if (fa[f].dims[2] == 1) order.push_back(f);
+  long long total_tiles = 0, tiles3 = 0;
   int64_t total_n = 0, max_n = 0;
-  for (int f = 0; f < nf; ++f) {
-    make_field_desc(fa[f].field, fa[f].dtype, fa[f].dims, total_tiles, fa[f].asc, fa[f].desc,
-                    fa[f].ms, true, &hd[f], &hm[f]);
-    total_tiles += hd[f].g.ntiles;
-    total_n += fa[f].n;
-    max_n = std::max(max_n, fa[f].n);
+  for (int j = 0; j < nf; ++j) {
+    const FieldArg &a = fa[order[j]];
+    make_field_desc(a.field, a.dtype, a.dims, total_tiles, a.asc, a.desc, a.ms, true, &hd[j],
+                    &hm[j]);
+    total_tiles += hd[j].g.ntiles;
+    if (!hd[j].g.flat) tiles3 = total_tiles;
+    total_n += a.n;
+    max_n = std::max(max_n, a.n);
   }
   MS_TRY(cudaMemcpyAsync(c->batch_dev, c->batch_host, bytes, cudaMemcpyHostToDevice, c->stream));
   Batch b;
@@ -293,6 +326,8 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
   b.n_fields = nf;
   b.key_mode = key_mode;
   b.total_tiles = total_tiles;
+  b.tiles3 = tiles3;
+  b.f0 = hd[0];
 
   // ---- tile pass; the pair pool is sized from the last call, exact on overflow
   unsigned long long cap = c->pool_hint;
@@ -322,12 +357,38 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
   c->pool_hint = std::max(c->pool_hint, cap);
 
   // ---- exits followed, pairs deduplicated; the set is sized from the last
-  // call's region count (or a quarter of the tile pairs), exact on overflow
+  // call's region count (or a quarter of the tile pairs), exact on overflow.
+  // Exits are chased face to face; where a sample of the pairs shows long
+  // chains (smooth fields), through the face graph instead, pointer-jumped
+  // in O(log) rounds over all face slots.
   StageTimer t2(c, MS_STAGE_RESOLVE);
   const uint64_t exact = 2 * npairs + 2;
   uint64_t want = c->last_k ? 4 * (uint64_t)c->last_k : npairs / 4;
   if (want < (1u << 16)) want = 1u << 16;
   if (want > exact) want = exact;
+  const long long slots = face_graph_slots(b);
+  bool use_graph = false;
+  if (npairs >= kProbeMinPairs && slots < (1ll << 31)) {
+    const unsigned long long stride = npairs / kProbeSample;
+    MS_TRY(cudaMemsetAsync(&c->dst->pending, 0, sizeof(unsigned int), c->stream));
+    MS_TRY(launch_resolve_pairs(b, ts, RankScratch{}, npairs, kChaseProbe, nullptr, stride, false,
+                                c->dst, c->stream));
+    s = read_status(c);
+    if (s != MS_OK) return s;
+    if (c->hst->not_converged) return MS_ERR_NOT_CONVERGED;
+    const unsigned long long sampled = (npairs + stride - 1) / stride;
+    use_graph = (unsigned long long)c->hst->pending * 8 > sampled;
+  }
+  int2 *graph = nullptr;
+  if (use_graph) {
+    s = ensure_buffer(c, &c->graph, &c->graph_bytes, (size_t)slots * sizeof(int2));
+    if (s != MS_OK) return s;
+    graph = static_cast<int2 *>(c->graph);
+    MS_TRY(launch_face_graph_build(b, ts, graph, c->dst, c->stream));
+    s = jump_face_graph(c, b, graph, slots);
+    if (s != MS_OK) return s;
+    if (c->hst->bad_index) return MS_ERR_CUDA;  // an ill-formed face graph: cannot happen
+  }
   RankScratch rs;
   for (;;) {
     const unsigned int hcap = pow2_at_least(want);
@@ -337,10 +398,20 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
     if (want < exact) rs.probe_limit = kEstimateProbeLimit;
     MS_TRY(cudaMemsetAsync(&c->dst->n_unique, 0, sizeof(unsigned int), c->stream));
     MS_TRY(cudaMemsetAsync(&c->dst->hash_overflow, 0, sizeof(unsigned int), c->stream));
-    MS_TRY(launch_resolve_pairs(b, ts, rs, npairs, c->dst, c->stream));
+    MS_TRY(cudaMemsetAsync(&c->dst->pending, 0, sizeof(unsigned int), c->stream));
+    MS_TRY(launch_resolve_pairs(b, ts, rs, npairs, use_graph ? kChaseGraph : kChaseBudget, graph, 1,
+                                true, c->dst, c->stream));
     s = read_status(c);
     if (s != MS_OK) return s;
     if (c->hst->not_converged) return MS_ERR_NOT_CONVERGED;
+    if (!c->hst->hash_overflow && c->hst->pending) {
+      // the few pairs whose exits lead through more than kChaseHops tiles
+      MS_TRY(launch_resolve_pairs(b, ts, rs, npairs, kChasePending, nullptr, 1, false, c->dst,
+                                  c->stream));
+      s = read_status(c);
+      if (s != MS_OK) return s;
+      if (c->hst->not_converged) return MS_ERR_NOT_CONVERGED;
+    }
     if (!c->hst->hash_overflow) break;
     if (want >= exact) return MS_ERR_CUDA;  // cannot happen: the exact bound always fits
     want = exact;
@@ -360,9 +431,9 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
     uint32_t *hf = reinterpret_cast<uint32_t *>(c->batch_host);  // reuse the staging buffer
     MS_TRY(cudaMemcpyAsync(hf, ts.fstart, (size_t)nf * 4, cudaMemcpyDeviceToHost, c->stream));
     MS_TRY(cudaStreamSynchronize(c->stream));
-    for (int f = 0; f < nf; ++f) {
-      const uint32_t end = f + 1 < nf ? hf[f + 1] : m;
-      if (k_out) k_out[f] = (int64_t)(end - hf[f]);
+    for (int j = 0; j < nf; ++j) {
+      const uint32_t end = j + 1 < nf ? hf[j + 1] : m;
+      if (k_out) k_out[order[j]] = (int64_t)(end - hf[j]);
     }
   } else {
     MS_TRY(cudaStreamSynchronize(c->stream));
@@ -375,12 +446,15 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
 ms_status segment_staged(ms_ctx *c, const void *field, const int64_t dims[3], int dtype,
                          int64_t n, int32_t *asc, int32_t *desc, int32_t *ms);
 
-// Grids at least kTZ / 2 planes deep take the tiled path; flatter ones (2D
-// grids in particular) would leave most of every 32 x 16 x 16 tile empty,
-// so they take the step-by-step path.
+// 2D grids (nz = 1) take the tiled path with 2D tiles, grids at least
+// kTZ / 2 planes deep the tiled path with 3D tiles; the few planes in
+// between would leave most of every 32 x 16 x 16 tile empty, so they take
+// the step-by-step path.
+bool tiled_shape(const int64_t dims[3]) { return dims[2] == 1 || dims[2] >= kTZ / 2; }
+
 ms_status segment_device(ms_ctx *c, const void *field, const int64_t dims[3], int dtype,
                          int64_t n, int32_t *asc, int32_t *desc, int32_t *ms) {
-  if (dims[2] >= kTZ / 2) {
+  if (tiled_shape(dims)) {
     const FieldArg fa{field, dims, dtype, n, asc, desc, ms};
     int64_t k = 0;
     const ms_status s = segment_tiled(c, &fa, 1, &k);
@@ -471,6 +545,7 @@ ms_status ms_destroy(ms_ctx *c) {
   if (c->scratch) cudaFree(c->scratch);
   if (c->io) cudaFree(c->io);
   if (c->tscratch) cudaFree(c->tscratch);
+  if (c->graph) cudaFree(c->graph);
   if (c->batch_dev) cudaFree(c->batch_dev);
   if (c->batch_host) cudaFreeHost(c->batch_host);
   if (c->hcount) cudaFreeHost(c->hcount);
@@ -548,7 +623,7 @@ ms_status ms_segment_batch(ms_ctx *c, int n_fields, const void *const *fields,
       return MS_ERR_INVALID_ARG;
     if (asc[f] == desc[f] || asc[f] == ms[f] || desc[f] == ms[f]) return MS_ERR_INVALID_ARG;
     fa[f] = FieldArg{fields[f], dims[f], (int)dtypes[f], n, asc[f], desc[f], ms[f]};
-    batchable = batchable && n <= kBatchMaxN && dims[f][2] >= kTZ / 2;
+    batchable = batchable && n <= kBatchMaxN && tiled_shape(dims[f]);
   }
   const long long l0 = tl_launches;
   ms_status s = MS_OK;

@@ -107,6 +107,46 @@ __device__ __forceinline__ void face_coords(int fs, int *lx, int *ly, int *lz) {
   }
 }
 
+// ---- 2D tiles (k2TX x k2TY; see ms_tiled.cuh) -----------------------------
+__device__ __forceinline__ int ext2_of(int lx, int ly) { return (lx + kXO) + k2EX * (ly + 1); }
+
+__device__ __forceinline__ void tile_origin2(const TileGeom &g, int64_t t, int64_t *x0,
+                                             int64_t *y0) {
+  uint32_t tx, ty;
+  g.div_tx.divmod((uint32_t)t, &ty, &tx);
+  *x0 = (int64_t)tx * k2TX;
+  *y0 = (int64_t)ty * k2TY;
+}
+
+// Face slots of a 2D tile: the y-low row, the y-high row, the x-low column,
+// the x-high column (corners in the first that contains them).
+__device__ __forceinline__ int face_slot2(int lx, int ly) {
+  if (ly == 0) return lx;
+  if (ly == k2TY - 1) return k2TX + lx;
+  if (lx == 0) return 2 * k2TX + ly;
+  if (lx == k2TX - 1) return 2 * k2TX + k2TY + ly;
+  return -1;
+}
+
+__device__ __forceinline__ void face_coords2(int fs, int *lx, int *ly) {
+  if (fs < 2 * k2TX) {
+    *lx = fs % k2TX;
+    *ly = fs < k2TX ? 0 : k2TY - 1;
+  } else {
+    const int q = fs - 2 * k2TX;
+    *lx = q < k2TY ? 0 : k2TX - 1;
+    *ly = q % k2TY;
+  }
+}
+
+__device__ __forceinline__ int32_t root_ref2(const TileGeom &g, int64_t x0, int64_t y0, int e) {
+  const uint32_t ue = (uint32_t)e;
+  const uint32_t ey = ue / k2EX, ex = ue - ey * k2EX;
+  const bool halo = ex == kXO - 1 || ex == kXO + k2TX || ey == 0 || ey == k2EY - 1;
+  const int64_t v = (x0 + (int)ex - kXO) + g.nx * (y0 + (int)ey - 1);
+  return (int32_t)v | (halo ? kExitFlag : 0);
+}
+
 // Exclusive block scan of two values per thread (kThreads threads); also
 // returns both totals.  Uses scratch[2][kThreads / 32]; ends with a barrier.
 __device__ __forceinline__ void block_scan2(int a, int b, int *ea, int *eb, int *ta, int *tb,
@@ -193,6 +233,16 @@ __device__ __forceinline__ void tma_load_box(void *dst, const CUtensorMap *map, 
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// 2D box load of a 2D tile + halo: x from x0 - kXO, y from y0 - 1.
+__device__ __forceinline__ void tma_load_box2(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                              int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
       : "memory");
 }
 
@@ -354,6 +404,124 @@ __device__ __forceinline__ uint32_t pairset_insert(uint32_t *H, uint32_t key, ui
   return kEmpty32;  // unreachable: the set holds one slot per vertex
 }
 
+// The distinct (up-root, dn-root) pairs of a tile whose final pointers are
+// in w[] (one run of kRun per thread, both tile shapes), with uniform work:
+// (1) in each warp row, the first lane of every run of equal pairs is the
+//     run's leader and appends the pair to its warp's candidate list; every
+//     vertex remembers its run's candidate index;
+// (2) each warp inserts its candidates into an open-addressing set H;
+// (3) the used slots of H are numbered by a block scan, which is also the
+//     order of the tile's pair list; candidates take their slot's number.
+// Writes the pair list to the pool (roots through `ref`, exits flagged) and
+// the per-vertex pair numbers; K and P are free scratch here.  Valid run
+// entries are those of a column with col_in, below n_here.
+template <class RootRef>
+__device__ __forceinline__ void number_tile_pairs(uint32_t *K, uint32_t *P, const uint32_t (&w)[kRun],
+                                                  bool col_in, int n_here, int64_t gt, int fi,
+                                                  int n_fields,
+                                                  const TiledScratch &ts, DevStatus *st,
+                                                  long long *s_base, int (*s_scan2)[kThreads / 32],
+                                                  RootRef ref) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t *H = K;                                           // kHash words
+  uint32_t *CK = P;                                          // kTileV candidate pairs, then the pair list
+  uint16_t *CS = reinterpret_cast<uint16_t *>(P + kTileV);   // candidate slot, then number
+  for (int i = threadIdx.x; i < kHash; i += kThreads) H[i] = kEmpty32;
+  uint32_t cidx[kRun / 2];  // two 16-bit candidate indices per word
+  int ncand = 0;           // this warp's candidates so far
+  {
+    const int seg = warp * (kRun * 32);
+#pragma unroll
+    for (int j = 0; j < kRun; ++j) {
+      const bool valid = col_in && j < n_here;
+      const uint32_t key = valid ? w[j] : kEmpty32;
+      const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+      const bool lead = valid && (lane == 0 || prev != key);
+      const unsigned lm = __ballot_sync(0xffffffffu, lead);
+      const int my = seg + ncand + __popc(lm & ((1u << lane) - 1u));
+      if (lead) CK[my] = key;
+      // the run's leader is the highest leader lane at or below this lane
+      const unsigned upto = lm & (0xffffffffu >> (31 - lane));
+      const int src = upto ? 31 - __clz(upto) : lane;
+      const int ci = __shfl_sync(0xffffffffu, my, src);
+      const uint32_t c = valid ? (uint32_t)ci : 0u;
+      if (j & 1)
+        cidx[j / 2] |= c << 16;
+      else
+        cidx[j / 2] = c;
+      ncand += __popc(lm);
+    }
+  }
+  __syncthreads();  // H cleared, candidates written
+  {
+    const int seg = warp * (kRun * 32);
+    for (int i = lane; i < ncand; i += 32) CS[seg + i] = (uint16_t)pairset_insert(H, CK[seg + i], hash32(CK[seg + i]));
+  }
+  __syncthreads();
+  // number the used slots: thread t owns slots t, t + 512, ...
+  constexpr int kPer = kHash / kThreads;
+  int cnt = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) cnt += H[threadIdx.x + kThreads * j] != kEmpty32;
+  int ex, dummy_e, npairs, dummy_t;
+  block_scan2(cnt, 0, &ex, &dummy_e, &npairs, &dummy_t, s_scan2);
+  {
+    int id = ex;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int sl = threadIdx.x + kThreads * j;
+      const uint32_t key = H[sl];
+      if (key != kEmpty32) {
+        CK[id] = key;  // the pair list replaces the (inserted) candidates
+        H[sl] = (uint32_t)id;
+        ++id;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    const long long b = (long long)atomicAdd(ts.pool_count, (unsigned long long)npairs);
+    *s_base = b;
+    ts.tile_base[gt] = b;
+    ts.tile_count[gt] = npairs;
+  }
+  __syncthreads();
+  {
+    const int seg = warp * (kRun * 32);
+    for (int i = lane; i < ncand; i += 32) CS[seg + i] = (uint16_t)H[CS[seg + i]];
+  }
+  {
+    // the tile's pair list to the pool: global root indices, exits flagged
+    const long long base = *s_base;
+    const uint32_t *PL = CK;
+    for (int i = threadIdx.x; i < npairs; i += kThreads) {
+      const long long at = base + i;
+      if (at >= (long long)ts.pool_cap) {
+        atomicOr(&st->pool_overflow, 1u);
+        break;
+      }
+      const uint32_t key = PL[i];
+      const int u = (int)(key & 0xffffu), d = (int)(key >> 16);
+      ts.pool_roots[at] = make_int2(ref(d), ref(u));
+      if (n_fields > 1) ts.pool_field[at] = (uint32_t)fi;
+    }
+  }
+  __syncthreads();
+  uint32_t cell[kRun];
+#pragma unroll
+  for (int j = 0; j < kRun; ++j) cell[j] = CS[(cidx[j / 2] >> (16 * (j & 1))) & 0xffffu];
+  // per-vertex pair numbers: the column's 16 numbers are one 32-byte vector
+  if (col_in) {
+    uint32_t packed[kRun / 2];
+#pragma unroll
+    for (int j = 0; j < kRun; j += 2) packed[j / 2] = (cell[j] & 0xffffu) | (cell[j + 1] << 16);
+    uint4 *pid4 = reinterpret_cast<uint4 *>(ts.pid + gt * (int64_t)kTileV +
+                                            (int64_t)threadIdx.x * kRun);
+    pid4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+    pid4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+  }
+  __syncthreads();
+}
+
 // One CTA per tile (persistent).  Thread (lane, warp) owns the z-column of
 // vertices (x0 + lane, y0 + warp, z0 .. z0 + TZ - 1).
 //
@@ -389,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
   if (threadIdx.x == 0) mbar_init(&s_bar, 1);
   __syncthreads();
 
-  for (int64_t gt = blockIdx.x; gt < bt.total_tiles; gt += gridDim.x) {
+  for (int64_t gt = blockIdx.x; gt < bt.tiles3; gt += gridDim.x) {
     const int fi = field_of(bt, gt);
     const FieldDesc &fd = bt.fields[fi];
     const TileGeom &g = fd.g;
@@ -521,110 +689,191 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
     }
     __syncthreads();
 
-    // ---- distinct (up-root, dn-root) pairs of the tile, with uniform work:
-    // (1) in each warp row, the first lane of every run of equal pairs is the
-    //     run's leader and appends the pair to its warp's candidate list;
-    //     every vertex remembers its run's candidate index;
-    // (2) each warp inserts its candidates into an open-addressing set H;
-    // (3) the used slots of H are numbered by a block scan, which is also the
-    //     order of the tile's pair list; candidates take their slot's number.
-    uint32_t *H = K;                                           // kHash words
-    uint32_t *CK = P;                                          // kTileV candidate pairs, then the pair list
-    uint16_t *CS = reinterpret_cast<uint16_t *>(P + kTileV);   // candidate slot, then number
-    for (int i = threadIdx.x; i < kHash; i += kThreads) H[i] = kEmpty32;
-    uint32_t cidx[kTZ / 2];  // two 16-bit candidate indices per word
-    int ncand = 0;           // this warp's candidates so far
-    {
-      const int seg = warp * (kTZ * 32);
+    number_tile_pairs(K, P, w, col_in, nz_here, gt, fi, bt.n_fields, ts, st, &s_base, s_scan2,
+                      [&](int e) { return root_ref(g, x0, y0, z0, e); });
+  }
+  if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&st->nan_flag, 1u);
+}
+
+// up / dn of a thread's run of kRun vertices in a 2D tile.  N(v) u {v} is
+// the union of the unit squares [v, v+(1,1)] and [v-(1,1), v]; with
+// A(y) = extremum of {(x-1, y), (x, y)} and B(y) = extremum of {(x, y),
+// (x+1, y)}, the lower square is A(y-1), A(y) and the upper one B(y), B(y+1).
+// The thread streams the rows y0 - 1 .. y0 + kRun of its column, keeping two
+// rows of A and B in registers (every operand pair again has its second
+// operand at higher vertex indices).
+template <bool kRaw>
+__device__ __forceinline__ void steepest_run2(const uint32_t *__restrict__ K, int cx, int cy0,
+                                              bool col_in, int n_here, uint32_t *w, bool *nan) {
+  typedef Ord<kRaw> O;
+  const uint32_t e0 = (uint32_t)((cx + kXO) + k2EX * cy0);  // box row of y = cy0 - 1
+  Cand a0x, a0n, a1x, a1n, b1x, b1n;
+  uint32_t kc1;
+  {
+    const uint32_t e = e0;
+    const uint32_t kl = K[e - 1], kc = K[e];
+    a0x = omax<kRaw>(Cand{kl, e - 1}, Cand{kc, e});
+    a0n = omin<kRaw>(Cand{O::mk(kl), e - 1}, Cand{O::mk(kc), e});
+  }
+  {
+    const uint32_t e = e0 + k2EX;
+    const uint32_t kl = K[e - 1], kc = K[e], kr = K[e + 1];
+    a1x = omax<kRaw>(Cand{kl, e - 1}, Cand{kc, e});
+    a1n = omin<kRaw>(Cand{O::mk(kl), e - 1}, Cand{O::mk(kc), e});
+    b1x = omax<kRaw>(Cand{kc, e}, Cand{kr, e + 1});
+    b1n = omin<kRaw>(Cand{O::mk(kc), e}, Cand{O::mk(kr), e + 1});
+    kc1 = kc;
+  }
 #pragma unroll
-      for (int lz = 0; lz < kTZ; ++lz) {
-        const bool valid = col_in && lz < nz_here;
-        const uint32_t key = valid ? w[lz] : kEmpty32;
-        const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-        const bool lead = valid && (lane == 0 || prev != key);
-        const unsigned lm = __ballot_sync(0xffffffffu, lead);
-        const int my = seg + ncand + __popc(lm & ((1u << lane) - 1u));
-        if (lead) CK[my] = key;
-        // the run's leader is the highest leader lane at or below this lane
-        const unsigned upto = lm & (0xffffffffu >> (31 - lane));
-        const int src = upto ? 31 - __clz(upto) : lane;
-        const int ci = __shfl_sync(0xffffffffu, my, src);
-        const uint32_t c = valid ? (uint32_t)ci : 0u;
-        if (lz & 1)
-          cidx[lz / 2] |= c << 16;
-        else
-          cidx[lz / 2] = c;
-        ncand += __popc(lm);
-      }
-    }
-    __syncthreads();  // H cleared, candidates written
-    {
-      const int seg = warp * (kTZ * 32);
-      for (int i = lane; i < ncand; i += 32) CS[seg + i] = (uint16_t)pairset_insert(H, CK[seg + i], hash32(CK[seg + i]));
-    }
-    __syncthreads();
-    // number the used slots: thread t owns slots t, t + 512, ...
-    constexpr int kPer = kHash / kThreads;
-    int cnt = 0;
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) cnt += H[threadIdx.x + kThreads * j] != kEmpty32;
-    int ex, dummy_e, npairs, dummy_t;
-    block_scan2(cnt, 0, &ex, &dummy_e, &npairs, &dummy_t, s_scan2);
-    {
-      int id = ex;
-#pragma unroll
-      for (int j = 0; j < kPer; ++j) {
-        const int sl = threadIdx.x + kThreads * j;
-        const uint32_t key = H[sl];
-        if (key != kEmpty32) {
-          CK[id] = key;  // the pair list replaces the (inserted) candidates
-          H[sl] = (uint32_t)id;
-          ++id;
+  for (int j = 0; j < kRun; ++j) {
+    const uint32_t e = e0 + (uint32_t)(j + 2) * k2EX;  // the row below vertex j
+    const uint32_t kl = K[e - 1], kc = K[e], kr = K[e + 1];
+    const Cand a2x = omax<kRaw>(Cand{kl, e - 1}, Cand{kc, e});
+    const Cand a2n = omin<kRaw>(Cand{O::mk(kl), e - 1}, Cand{O::mk(kc), e});
+    const Cand b2x = omax<kRaw>(Cand{kc, e}, Cand{kr, e + 1});
+    const Cand b2n = omin<kRaw>(Cand{O::mk(kc), e}, Cand{O::mk(kr), e + 1});
+    const uint32_t up = omax<kRaw>(omax<kRaw>(a0x, a1x), omax<kRaw>(b1x, b2x)).i;
+    const uint32_t dn = omin<kRaw>(omin<kRaw>(a0n, a1n), omin<kRaw>(b1n, b2n)).i;
+    const bool valid = col_in && j < n_here;
+    if (kRaw && valid) *nan |= is_nan_bits(kc1);
+    const uint32_t ev = e0 + (uint32_t)(j + 1) * k2EX;
+    w[j] = valid ? (up | (dn << 16)) : ev * 0x10001u;
+    a0x = a1x;
+    a0n = a1n;
+    a1x = a2x;
+    a1n = a2n;
+    b1x = b2x;
+    b1n = b2n;
+    kc1 = kc;
+  }
+}
+
+// The 2D form of k_tile_local, for fields with nz = 1 (the tiles after the
+// 3D fields' in a batch).  Thread (lane, warp) owns the run of kRun vertices
+// at x = lane + 32 (warp % 4), y = kRun (warp / 4) + 0 .. kRun - 1.
+__global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScratch ts, DevStatus *st) {
+  extern __shared__ __align__(128) uint32_t dsmem[];
+  uint32_t *K = dsmem;          // k2Ext words: values / keys, then the pair set
+  uint32_t *P = dsmem + k2Ext;  // k2PArea words: up | dn << 16, then candidates
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ long long s_base;
+  __shared__ int s_abort;
+  __shared__ int s_scan2[2][kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cx = lane + 32 * (warp & 3), cy0 = kRun * (warp >> 2);
+  bool nan = false;
+  uint32_t parity = 0;
+  if (threadIdx.x == 0) s_abort = 0;
+  if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+  __syncthreads();
+
+  for (int64_t gt = bt.tiles3 + blockIdx.x; gt < bt.total_tiles; gt += gridDim.x) {
+    const int fi = field_of(bt, gt);
+    const FieldDesc &fd = bt.fields[fi];
+    const TileGeom &g = fd.g;
+    const void *__restrict__ field = fd.field;
+    const int dtype = fd.dtype;
+    const bool tma = fd.tma != 0;
+    int64_t x0, y0;
+    tile_origin2(g, gt - fd.tile_base, &x0, &y0);
+    const bool raw = tma && x0 >= 1 && y0 >= 1 && x0 + k2TX < g.nx && y0 + k2TY < g.ny;
+
+    if (tma) {
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&s_bar, (uint32_t)(k2Ext * 4));
+        tma_load_box2(K, &bt.tmaps[fi], &s_bar, (int)(x0 - kXO), (int)(y0 - 1));
+        long long polls = 0;
+        while (!mbar_try_wait(&s_bar, parity)) {
+          if (++polls > kWaitPolls) {
+            atomicOr(&st->timeout, 1u);
+            s_abort = 1;
+            break;
+          }
+          __nanosleep(64);
         }
       }
+      __syncthreads();
+      if (s_abort) return;  // block-uniform
+      parity ^= 1u;
     }
-    if (threadIdx.x == 0) {
-      const long long b = (long long)atomicAdd(ts.pool_count, (unsigned long long)npairs);
-      s_base = b;
-      ts.tile_base[gt] = b;
-      ts.tile_count[gt] = npairs;
-    }
-    __syncthreads();
-    {
-      const int seg = warp * (kTZ * 32);
-      for (int i = lane; i < ncand; i += 32) CS[seg + i] = (uint16_t)H[CS[seg + i]];
-    }
-    {
-      // the tile's pair list to the pool: global root indices, exits flagged
-      const long long base = s_base;
-      const uint32_t *PL = CK;
-      for (int i = threadIdx.x; i < npairs; i += kThreads) {
-        const long long at = base + i;
-        if (at >= (long long)ts.pool_cap) {
-          atomicOr(&st->pool_overflow, 1u);
-          break;
-        }
-        const uint32_t key = PL[i];
-        const int u = (int)(key & 0xffffu), d = (int)(key >> 16);
-        ts.pool_roots[at] = make_int2(root_ref(g, x0, y0, z0, d), root_ref(g, x0, y0, z0, u));
-        ts.pool_field[at] = (uint32_t)fi;
+    // boundary tiles: order keys in place, sentinel 0 outside the field
+    if (!raw) {
+      constexpr int kCols = k2TX + 2;  // the tile's columns and the two halo columns
+      for (int i = threadIdx.x; i < k2EY * kCols; i += kThreads) {
+        const int r = i / kCols, c = i - r * kCols + kXO - 1;
+        const int e = r * k2EX + c;
+        const int64_t x = x0 + c - kXO, y = y0 + r - 1;
+        const bool in = x >= 0 && x < g.nx && y >= 0 && y < g.ny;
+        uint32_t b = 0;
+        if (tma)
+          b = K[e];
+        else if (in)
+          b = raw_bits(field, dtype, y * g.nx + x);
+        if (in && r >= 1 && r <= k2TY && c >= kXO && c < kXO + k2TX) nan |= is_nan_bits(b);
+        K[e] = in ? key_of(b) : 0u;
       }
     }
     __syncthreads();
-    uint32_t cell[kTZ];
+
+    const bool col_in = x0 + cx < g.nx && y0 + cy0 < g.ny;
+    const int n_here = (int)min((int64_t)kRun, g.ny - (y0 + cy0));
+    uint32_t w[kRun];
+    if (raw)
+      steepest_run2<true>(K, cx, cy0, col_in, n_here, w, &nan);
+    else
+      steepest_run2<false>(K, cx, cy0, col_in, n_here, w, &nan);
+    if (__syncthreads_or(nan)) {
+      if (threadIdx.x == 0) ts.tile_count[gt] = 0;
+      __syncthreads();
+      continue;
+    }
 #pragma unroll
-    for (int lz = 0; lz < kTZ; ++lz) cell[lz] = CS[(cidx[lz / 2] >> (16 * (lz & 1))) & 0xffffu];
-    // per-vertex pair numbers: the column's 16 numbers are one 32-byte vector
-    if (col_in) {
-      uint32_t packed[kTZ / 2];
-#pragma unroll
-      for (int lz = 0; lz < kTZ; lz += 2) packed[lz / 2] = (cell[lz] & 0xffffu) | (cell[lz + 1] << 16);
-      uint4 *pid4 = reinterpret_cast<uint4 *>(ts.pid + gt * (int64_t)kTileV +
-                                              (int64_t)(ly * kTX + lx) * kTZ);
-      pid4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-      pid4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+    for (int j = 0; j < kRun; ++j) P[ext2_of(cx, cy0 + j)] = w[j];
+    // the halo ring points at itself
+    for (int i = threadIdx.x; i < 2 * (k2TX + 2) + 2 * k2TY; i += kThreads) {
+      int e;
+      if (i < k2TX + 2)
+        e = kXO - 1 + i;
+      else if (i < 2 * (k2TX + 2))
+        e = (k2EY - 1) * k2EX + kXO - 1 + (i - (k2TX + 2));
+      else {
+        const int q = i - 2 * (k2TX + 2);
+        e = (1 + (q >> 1)) * k2EX + ((q & 1) ? kXO + k2TX : kXO - 1);
+      }
+      P[e] = (uint32_t)e * 0x10001u;
     }
     __syncthreads();
+
+    // in-place pointer jumping, as in the 3D tiles
+    for (int it = 0; it < k2Ext; ++it) {
+      bool changed = false;
+#pragma unroll
+      for (int j = 0; j < kRun; ++j) {
+        const uint32_t gu = P[w[j] & 0xffffu], gd = P[w[j] >> 16];
+        const uint32_t nw = __byte_perm(gu, gd, 0x7610);
+        if (nw != w[j]) {
+          w[j] = nw;
+          P[ext2_of(cx, cy0 + j)] = nw;
+          changed = true;
+        }
+      }
+      if (!__any_sync(0xffffffffu, changed)) break;
+    }
+    __syncthreads();
+
+    {
+      uint32_t *face = ts.face + gt * (int64_t)kFace;
+      for (int fs = threadIdx.x; fs < k2Face; fs += kThreads) {
+        int fx, fy;
+        face_coords2(fs, &fx, &fy);
+        if (x0 + fx < g.nx && y0 + fy < g.ny) face[fs] = P[ext2_of(fx, fy)];
+      }
+    }
+    __syncthreads();
+
+    number_tile_pairs(K, P, w, col_in, n_here, gt, fi, bt.n_fields, ts, st, &s_base, s_scan2,
+                      [&](int e) { return root_ref2(g, x0, y0, e); });
   }
   if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&st->nan_flag, 1u);
 }
@@ -636,13 +885,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
 // the tile count; but every hop lands on a different halo vertex of the same
 // strictly monotone path, so it is bounded by the number of face slots and by
 // N.  The cap only guards against a corrupted face array.
+// Returns the extremum, or -1 once `budget` hops have not reached one (the
+// caller defers the pair).
 __device__ int32_t chase(const TileGeom &g, const uint32_t *__restrict__ face, int32_t r, bool up,
-                         DevStatus *st) {
+                         int64_t budget, DevStatus *st) {
   const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny, gtx = (uint32_t)g.tx,
                  gty = (uint32_t)g.ty;
   const int64_t n = g.nx * g.ny * g.nz, slots = g.ntiles * kFace;
   const int64_t max_hops = n < slots ? n : slots;
-  for (int64_t hop = 0; hop <= max_hops; ++hop) {
+  const int64_t lim = budget < max_hops ? budget : max_hops;
+  for (int64_t hop = 0; hop <= lim; ++hop) {
     if (!(r & kExitFlag)) return r;
     uint32_t q, x, y, z;
     g.div_nx.divmod((uint32_t)(r & ~kExitFlag), &q, &x);
@@ -660,9 +912,165 @@ __device__ int32_t chase(const TileGeom &g, const uint32_t *__restrict__ face, i
     const uint32_t gx = tx * kTX + ex - kXO, gy = ty * kTY + ey - 1, gz = tz * kTZ + ez - 1;
     r = (int32_t)(gx + nx * (gy + ny * gz)) | (halo ? kExitFlag : 0);
   }
+  if (!(r & kExitFlag)) return r;  // reached on the last hop
+  if (lim < max_hops) return -1;
   atomicOr(&st->not_converged, 1u);
   return 0;
 }
+
+// chase for 2D fields (k2TX x k2TY tiles).
+__device__ int32_t chase2(const TileGeom &g, const uint32_t *__restrict__ face, int32_t r, bool up,
+                          int64_t budget, DevStatus *st) {
+  const uint32_t nx = (uint32_t)g.nx, gtx = (uint32_t)g.tx;
+  const int64_t n = g.nx * g.ny, slots = g.ntiles * k2Face;
+  const int64_t max_hops = n < slots ? n : slots;
+  const int64_t lim = budget < max_hops ? budget : max_hops;
+  for (int64_t hop = 0; hop <= lim; ++hop) {
+    if (!(r & kExitFlag)) return r;
+    uint32_t x, y;
+    g.div_nx.divmod((uint32_t)(r & ~kExitFlag), &y, &x);
+    const uint32_t tx = x / k2TX, ty = y / k2TY;
+    const int fs = face_slot2((int)(x - tx * k2TX), (int)(y - ty * k2TY));
+    if (fs < 0) break;
+    const uint32_t w = __ldg(&face[(size_t)(tx + gtx * ty) * kFace + fs]);
+    const uint32_t loc = up ? (w & 0xffffu) : (w >> 16);
+    const uint32_t ey = loc / k2EX, ex = loc - ey * k2EX;
+    const bool halo = ex == kXO - 1 || ex == kXO + k2TX || ey == 0 || ey == k2EY - 1;
+    const uint32_t gx = tx * k2TX + ex - kXO, gy = ty * k2TY + ey - 1;
+    r = (int32_t)(gx + nx * gy) | (halo ? kExitFlag : 0);
+  }
+  if (!(r & kExitFlag)) return r;  // reached on the last hop
+  if (lim < max_hops) return -1;
+  atomicOr(&st->not_converged, 1u);
+  return 0;
+}
+
+// Global face-graph slot of a face vertex v (a tile exit) of a field whose
+// first tile is tile_base.
+__device__ __forceinline__ uint32_t slot_of_vertex(const TileGeom &g, long long tile_base,
+                                                   uint32_t v) {
+  if (g.flat) {
+    uint32_t x, y;
+    g.div_nx.divmod(v, &y, &x);
+    const uint32_t tx = x / k2TX, ty = y / k2TY;
+    const int fs = face_slot2((int)(x - tx * k2TX), (int)(y - ty * k2TY));
+    return (uint32_t)((tile_base + tx + (long long)g.tx * ty) * kFace + fs);
+  }
+  uint32_t q, x, y, z;
+  g.div_nx.divmod(v, &q, &x);
+  g.div_ny.divmod(q, &z, &y);
+  const uint32_t tx = x / kTX, ty = y / kTY, tz = z / kTZ;
+  const int fs = face_slot((int)(x - tx * kTX), (int)(y - ty * kTY), (int)(z - tz * kTZ));
+  return (uint32_t)((tile_base + tx + (long long)g.tx * (ty + (long long)g.ty * tz)) * kFace + fs);
+}
+
+// Face-graph slots are numbered kFace per tile; 2D tiles use the first
+// k2Face.  Valid slot i (of face_graph_valid(b)) -> (tile, face slot).
+__device__ __forceinline__ void valid_slot(const Batch &b, long long i, long long *gt, int *fs) {
+  const long long n3 = b.tiles3 * (long long)kFace;
+  if (i < n3) {
+    *gt = i / kFace;
+    *fs = (int)(i - *gt * kFace);
+  } else {
+    const long long j = i - n3;
+    *gt = b.tiles3 + j / k2Face;
+    *fs = (int)(j - (*gt - b.tiles3) * k2Face);
+  }
+}
+
+__host__ __device__ __forceinline__ long long face_graph_valid(const Batch &b) {
+  return b.tiles3 * (long long)kFace + (b.total_tiles - b.tiles3) * (long long)k2Face;
+}
+
+// The face graph from the tiles' face roots (local box indices): exits
+// become the global slot of the exit vertex, extrema their vertex index |
+// kSlotFinal.  Slots of vertices outside their field get a final dummy.
+__global__ void k_face_graph_build(Batch bt, TiledScratch ts, int2 *__restrict__ graph) {
+  const long long nvalid = face_graph_valid(bt);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nvalid;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long gt;
+    int fs;
+    valid_slot(bt, i, &gt, &fs);
+    const int fi = field_of(bt, gt);
+    const FieldDesc &fd = bt.fields[fi];
+    const TileGeom &g = fd.g;
+    const long long tile = gt - fd.tile_base;
+    const long long slot = gt * kFace + fs;
+    int32_t ru, rd;
+    bool in;
+    const uint32_t w = ts.face[slot];
+    if (g.flat) {
+      int64_t x0, y0;
+      tile_origin2(g, tile, &x0, &y0);
+      int fx, fy;
+      face_coords2(fs, &fx, &fy);
+      in = x0 + fx < g.nx && y0 + fy < g.ny;
+      ru = in ? root_ref2(g, x0, y0, (int)(w & 0xffffu)) : 0;
+      rd = in ? root_ref2(g, x0, y0, (int)(w >> 16)) : 0;
+    } else {
+      int64_t x0, y0, z0;
+      tile_origin(g, tile, &x0, &y0, &z0);
+      int fx, fy, fz;
+      face_coords(fs, &fx, &fy, &fz);
+      in = x0 + fx < g.nx && y0 + fy < g.ny && z0 + fz < g.nz;
+      ru = in ? root_ref(g, x0, y0, z0, (int)(w & 0xffffu)) : 0;
+      rd = in ? root_ref(g, x0, y0, z0, (int)(w >> 16)) : 0;
+    }
+    auto enc = [&](int32_t r) -> int32_t {
+      if (!(r & kExitFlag)) return (int32_t)((uint32_t)r | kSlotFinal);
+      return (int32_t)slot_of_vertex(g, fd.tile_base, (uint32_t)(r & ~kExitFlag));
+    };
+    graph[slot] = in ? make_int2(enc(ru), enc(rd)) : make_int2((int32_t)kSlotFinal, (int32_t)kSlotFinal);
+  }
+}
+
+// One in-place pointer-jumping round over the face graph (each entry moves to
+// its successor's entry; entries read mid-round are still on the same path).
+// Sets st->round_open[round] if any entry is still not final.
+__global__ void k_face_graph_round(Batch bt, int2 *__restrict__ graph, int round, DevStatus *st) {
+  const long long nvalid = face_graph_valid(bt);
+  const long long nslots = bt.total_tiles * (long long)kFace;
+  bool open = false;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nvalid;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long gt;
+    int fs;
+    valid_slot(bt, i, &gt, &fs);
+    const long long slot = gt * kFace + fs;
+    int2 a = graph[slot];
+    bool ch = false;
+    // two jumps per round: an entry then points (more than) three times as far
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (!((uint32_t)a.x & kSlotFinal)) {
+        if ((long long)a.x >= nslots) {  // cannot happen for a well-formed graph
+          atomicOr(&st->bad_index, 1u);
+          a.x = (int32_t)kSlotFinal;
+        } else {
+          a.x = graph[a.x].x;
+        }
+        ch = true;
+      }
+      if (!((uint32_t)a.y & kSlotFinal)) {
+        if ((long long)a.y >= nslots) {
+          atomicOr(&st->bad_index, 1u);
+          a.y = (int32_t)kSlotFinal;
+        } else {
+          a.y = graph[a.y].y;
+        }
+        ch = true;
+      }
+    }
+    if (ch) {
+      graph[slot] = a;
+      open |= !((uint32_t)a.x & kSlotFinal) || !((uint32_t)a.y & kSlotFinal);
+    }
+  }
+  if (__any_sync(0xffffffffu, open) && (threadIdx.x & 31) == 0) st->round_open[round] = 1u;
+}
+
+
 
 // 64-bit finaliser of MurmurHash3 (Appleby).
 __device__ __forceinline__ unsigned long long mix64t(unsigned long long k) {
@@ -674,18 +1082,56 @@ __device__ __forceinline__ unsigned long long mix64t(unsigned long long k) {
   return k;
 }
 
-__global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, DevStatus *st) {
+constexpr uint32_t kPendingSlot = 0xfffffffeu;
+
+// kSingle: one field, whose descriptor is bt.f0 (kernel parameters).
+template <bool kSingle>
+__global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, int mode,
+                                const int2 *__restrict__ graph, unsigned long long stride,
+                                DevStatus *st) {
   const unsigned long long npairs = min(*ts.pool_count, ts.pool_cap);
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long nwork = mode == kChaseProbe ? (npairs + stride - 1) / stride : npairs;
+  const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned int mask = rs.capacity - 1u;
-  for (unsigned long long p = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; p < npairs;
-       p += stride) {
+  for (unsigned long long w = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < nwork;
+       w += step) {
+    const unsigned long long p = mode == kChaseProbe ? w * stride : w;
+    if (mode == kChasePending && ts.pool_slot[p] != kPendingSlot) continue;
+    // a set found too small stops the pass early (the host retries larger);
+    // read here so that the read overlaps the chase
+    const unsigned int overflow = __ldcg(&st->hash_overflow);
     const int2 r = ts.pool_roots[p];
-    const uint32_t fi = ts.pool_field[p];
-    const FieldDesc &fd = bt.fields[fi];
-    const uint32_t *face = ts.face + fd.tile_base * (long long)kFace;
-    const int32_t a = chase(fd.g, face, r.x, false, st);
-    const int32_t d = chase(fd.g, face, r.y, true, st);
+    const uint32_t fi = kSingle ? 0u : ts.pool_field[p];
+    const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
+    int32_t a, d;
+    if (mode == kChaseGraph) {
+      auto final_of = [&](int32_t x, bool up) -> int32_t {
+        if (!(x & kExitFlag)) return x;
+        const int2 e = graph[slot_of_vertex(fd.g, fd.tile_base, (uint32_t)(x & ~kExitFlag))];
+        const uint32_t f = (uint32_t)(up ? e.x : e.y);
+        if (!(f & kSlotFinal)) atomicOr(&st->not_converged, 1u);
+        return (int32_t)(f & ~kSlotFinal);
+      };
+      a = final_of(r.x, false);
+      d = final_of(r.y, true);
+    } else {
+      const int64_t budget =
+          mode == kChaseProbe ? kProbeHops : mode == kChaseBudget ? kChaseHops : (1ll << 40);
+      const uint32_t *face = ts.face + fd.tile_base * (long long)kFace;
+      a = fd.g.flat ? chase2(fd.g, face, r.x, false, budget, st)
+                    : chase(fd.g, face, r.x, false, budget, st);
+      d = fd.g.flat ? chase2(fd.g, face, r.y, true, budget, st)
+                    : chase(fd.g, face, r.y, true, budget, st);
+      if (mode == kChaseProbe) {
+        if (a < 0 || d < 0) atomicAdd(&st->pending, 1u);
+        continue;
+      }
+      if (a < 0 || d < 0) {  // only with the budget: resolved by a later pass
+        ts.pool_slot[p] = kPendingSlot;
+        atomicAdd(&st->pending, 1u);
+        continue;
+      }
+    }
     const unsigned long long key =
         bt.key_mode == kKeyBatch
             ? (((unsigned long long)fi << 48) | ((unsigned long long)(uint32_t)a << 24) | (uint32_t)d)
@@ -693,9 +1139,9 @@ __global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, DevSt
     // insert into the global pair set (first fit, open addressing); stop as
     // soon as the set is known to be too small (the host retries larger)
     unsigned int slot = (unsigned int)mix64t(key) & mask, found = 0xffffffffu;
-    if (*(volatile unsigned int *)&st->hash_overflow) continue;
+    if (overflow) continue;
     for (unsigned int probe = 0; probe < rs.probe_limit; ++probe) {
-      unsigned long long cur = *(volatile unsigned long long *)&rs.table_keys[slot];
+      unsigned long long cur = __ldcg(&rs.table_keys[slot]);
       if (cur == ~0ull) {
         cur = atomicCAS(&rs.table_keys[slot], ~0ull, key);
         if (cur == ~0ull) {
@@ -730,30 +1176,49 @@ __global__ void k_field_starts(const unsigned long long *__restrict__ sorted, un
 
 // Per tile: stage the pair table -- each tile pair's (asc, desc) and MS id,
 // read from the global pair set at the pair's slot -- and stream the labels
-// out.  Thread (lane, warp) writes the z-column (x0 + lane, y0 + warp, .);
-// its 16 pair numbers are one 32-byte vector.
+// out.  Each thread writes the run of kRun vertices it owned in the tile
+// kernel (3D: the z-column (x0 + lane, y0 + warp, .); 2D: the y-run at
+// x0 + lane + 32 (warp % 4)); its 16 pair numbers are one 32-byte vector.
+// kFlat selects the 2D tiles, which follow the 3D ones.
+template <bool kFlat>
 __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch ts, RankScratch rs) {
   __shared__ int4 T[kStageCap];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t gt = blockIdx.x; gt < bt.total_tiles; gt += gridDim.x) {
+  const int64_t gt_end = kFlat ? bt.total_tiles : bt.tiles3;
+  for (int64_t gt = (kFlat ? bt.tiles3 : 0) + blockIdx.x; gt < gt_end; gt += gridDim.x) {
     const int fi = field_of(bt, gt);
     const FieldDesc &fd = bt.fields[fi];
     const TileGeom &g = fd.g;
-    const int64_t plane = g.nx * g.ny;
-    int64_t x0, y0, z0;
-    tile_origin(g, gt - fd.tile_base, &x0, &y0, &z0);
+    int64_t v0, stride;  // the run's first vertex and its step
+    int n_here;
+    bool col_in;
+    if (kFlat) {
+      int64_t x0, y0;
+      tile_origin2(g, gt - fd.tile_base, &x0, &y0);
+      const int64_t x = x0 + lane + 32 * (warp & 3), y = y0 + kRun * (warp >> 2);
+      col_in = x < g.nx && y < g.ny;
+      n_here = (int)std::min<int64_t>(kRun, g.ny - y);
+      v0 = x + g.nx * y;
+      stride = g.nx;
+    } else {
+      int64_t x0, y0, z0;
+      tile_origin(g, gt - fd.tile_base, &x0, &y0, &z0);
+      const int64_t x = x0 + lane, y = y0 + warp;
+      col_in = x < g.nx && y < g.ny;
+      n_here = (int)std::min<int64_t>(kTZ, g.nz - z0);
+      stride = g.nx * g.ny;
+      v0 = x + g.nx * y + stride * z0;
+    }
     const long long b = ts.tile_base[gt];
     const int cnt = ts.tile_count[gt];
     const uint32_t *src = ts.pool_slot + b;
     const bool staged = cnt <= kStageCap;
     const bool batch = bt.key_mode == kKeyBatch;
     const int first = batch ? (int)ts.fstart[fi] : 0;
-    const int64_t x = x0 + lane, y = y0 + warp;
-    const bool col_in = x < g.nx && y < g.ny;
     uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
     if (col_in) {
       const uint4 *pid4 = reinterpret_cast<const uint4 *>(ts.pid + gt * (int64_t)kTileV +
-                                                          (int64_t)(warp * kTX + lane) * kTZ);
+                                                          (int64_t)threadIdx.x * kRun);
       q0 = __ldcs(pid4);
       q1 = __ldcs(pid4 + 1);
     }
@@ -769,14 +1234,12 @@ __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch 
     if (col_in) {
       int32_t *__restrict__ asc = fd.asc, *__restrict__ desc = fd.desc, *__restrict__ ms = fd.ms;
       const uint32_t w[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-      const int nz_here = (int)std::min<int64_t>(kTZ, g.nz - z0);
-      const int64_t v0 = x + g.nx * y + plane * z0;
 #pragma unroll
-      for (int lz = 0; lz < kTZ; ++lz) {
-        if (lz >= nz_here) break;
-        const int id = (int)((w[lz / 2] >> (16 * (lz & 1))) & 0xffffu);
+      for (int j = 0; j < kRun; ++j) {
+        if (j >= n_here) break;
+        const int id = (int)((w[j / 2] >> (16 * (j & 1))) & 0xffffu);
         const int4 t = staged ? T[id] : entry(src[id]);
-        const int64_t v = v0 + plane * lz;
+        const int64_t v = v0 + stride * j;
         __stcs(asc + v, t.x);
         __stcs(desc + v, t.y);
         __stcs(ms + v, t.z);
@@ -800,9 +1263,11 @@ TileGeom tile_geom(const int64_t dims[3]) {
   g.nx = dims[0];
   g.ny = dims[1];
   g.nz = dims[2];
-  g.tx = (g.nx + kTX - 1) / kTX;
-  g.ty = (g.ny + kTY - 1) / kTY;
-  g.tz = (g.nz + kTZ - 1) / kTZ;
+  g.flat = g.nz == 1 ? 1 : 0;
+  const int64_t tx = g.flat ? k2TX : kTX, ty = g.flat ? k2TY : kTY;
+  g.tx = (g.nx + tx - 1) / tx;
+  g.ty = (g.ny + ty - 1) / ty;
+  g.tz = g.flat ? 1 : (g.nz + kTZ - 1) / kTZ;
   g.ntiles = g.tx * g.ty * g.tz;
   g.div_nx = FastDivU32((uint32_t)g.nx);
   g.div_ny = FastDivU32((uint32_t)g.ny);
@@ -856,7 +1321,8 @@ EncodeTiledFn encode_tiled_fn() {
   return fn;
 }
 
-// A 3D tensor map over a float32 field for the box load; false when the
+// A 3D (2D for flat fields) tensor map over a float32 field for the box
+// load; false when the
 // field's layout does not meet TMA's rules (16-byte aligned base and row /
 // plane strides) or the driver entry point is missing.
 bool make_box_map(const void *field, int dtype, const TileGeom &g, CUtensorMap *map) {
@@ -866,6 +1332,16 @@ bool make_box_map(const void *field, int dtype, const TileGeom &g, CUtensorMap *
   if (g.nx > (1ll << 31) || g.ny > (1ll << 31) || g.nz > (1ll << 31)) return false;
   EncodeTiledFn fn = encode_tiled_fn();
   if (!fn) return false;
+  if (g.flat) {
+    const cuuint64_t dims2[2] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny};
+    const cuuint64_t strides2[1] = {(cuuint64_t)g.nx * 4};
+    const cuuint32_t box2[2] = {k2EX, k2EY};
+    const cuuint32_t estr2[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void *>(field), dims2, strides2,
+              box2, estr2, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
   const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
   const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)(g.nx * g.ny) * 4};
   const cuuint32_t box[3] = {kEX, kEY, kEZ};
@@ -893,26 +1369,75 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
                               cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ts.pool_count, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  constexpr int kSmem = 2 * kExt * 4;
   static_assert(kHash <= kExt, "the pair set reuses the key area");
-  e = cudaFuncSetAttribute(k_tile_local, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-  if (e != cudaSuccess) return e;
-  const int64_t grid = std::min<int64_t>(b.total_tiles, (int64_t)sms() * 2);
-  ++tl_launches;
-  k_tile_local<<<(unsigned)grid, kThreads, kSmem, s>>>(b, ts, st);
-  return cudaGetLastError();
+  if (b.tiles3 > 0) {
+    constexpr int kSmem = 2 * kExt * 4;
+    e = cudaFuncSetAttribute(k_tile_local, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * 2);
+    ++tl_launches;
+    k_tile_local<<<(unsigned)grid, kThreads, kSmem, s>>>(b, ts, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (b.total_tiles > b.tiles3) {
+    constexpr int kSmem2 = (k2Ext + k2PArea) * 4;
+    e = cudaFuncSetAttribute(k_tile_local2, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem2);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = std::min<int64_t>(b.total_tiles - b.tiles3, (int64_t)sms() * 2);
+    ++tl_launches;
+    k_tile_local2<<<(unsigned)grid, kThreads, kSmem2, s>>>(b, ts, st);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 cudaError_t launch_resolve_pairs(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
-                                 unsigned long long npairs, DevStatus *st, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(rs.table_keys, 0xff, (size_t)rs.capacity * 8, s);
+                                 unsigned long long npairs, int mode, const int2 *graph,
+                                 unsigned long long stride, bool clear_table, DevStatus *st,
+                                 cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (clear_table) e = cudaMemsetAsync(rs.table_keys, 0xff, (size_t)rs.capacity * 8, s);
   if (e != cudaSuccess || npairs == 0) return e;
-  unsigned long long blocks = (npairs + 255) / 256;
+  if (stride == 0) stride = 1;
+  const unsigned long long work = mode == kChaseProbe ? (npairs + stride - 1) / stride : npairs;
+  unsigned long long blocks = (work + 255) / 256;
   const unsigned long long cap = (unsigned long long)sms() * 16;
   if (blocks > cap) blocks = cap;
   ++tl_launches;
-  k_resolve_pairs<<<(unsigned)blocks, 256, 0, s>>>(b, ts, rs, st);
+  if (b.n_fields == 1)
+    k_resolve_pairs<true><<<(unsigned)blocks, 256, 0, s>>>(b, ts, rs, mode, graph, stride, st);
+  else
+    k_resolve_pairs<false><<<(unsigned)blocks, 256, 0, s>>>(b, ts, rs, mode, graph, stride, st);
   return cudaGetLastError();
+}
+
+namespace {
+unsigned int graph_blocks(const Batch &b) {
+  const long long n = face_graph_valid(b);
+  long long blocks = (n + 255) / 256;
+  const long long cap = (long long)sms() * 8;
+  return (unsigned int)std::max<long long>(1, std::min(blocks, cap));
+}
+}  // namespace
+
+cudaError_t launch_face_graph_build(const Batch &b, const TiledScratch &ts, int2 *graph,
+                                    DevStatus *st, cudaStream_t s) {
+  (void)st;
+  ++tl_launches;
+  k_face_graph_build<<<graph_blocks(b), 256, 0, s>>>(b, ts, graph);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_graph_rounds(const Batch &b, int2 *graph, int r0, int r1, DevStatus *st,
+                                     cudaStream_t s) {
+  for (int r = r0; r < r1; ++r) {
+    ++tl_launches;
+    k_face_graph_round<<<graph_blocks(b), 256, 0, s>>>(b, graph, r, st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_field_starts(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
@@ -925,10 +1450,21 @@ cudaError_t launch_field_starts(const Batch &b, const TiledScratch &ts, const Ra
 
 cudaError_t launch_tile_write(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
                               cudaStream_t s) {
-  const int64_t grid = std::min<int64_t>(b.total_tiles, (int64_t)sms() * 4);
-  ++tl_launches;
-  k_tile_write<<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
-  return cudaGetLastError();
+  cudaError_t e = cudaSuccess;
+  if (b.tiles3 > 0) {
+    const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * 4);
+    ++tl_launches;
+    k_tile_write<false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (b.total_tiles > b.tiles3) {
+    const int64_t grid = std::min<int64_t>(b.total_tiles - b.tiles3, (int64_t)sms() * 4);
+    ++tl_launches;
+    k_tile_write<true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace msseg

@@ -28,6 +28,23 @@ constexpr int kHash = 1 << kHashBits;                    // >= kTileV: never ove
 constexpr int kStageCap = 2048;                          // pair-table entries staged in smem
 constexpr int32_t kExitFlag = (int32_t)0x80000000u;
 
+// 2D fields (nz = 1) use tiles of k2TX x k2TY vertices with the same 512
+// threads: thread (lane, warp) owns the y-run of 16 vertices at
+// x = lane + 32 (warp % 4), y = 16 (warp / 4) + 0..15.  The staged box is the
+// tile plus a one-vertex halo, x again from 4 values left of the tile.
+constexpr int k2TX = 128, k2TY = 64;
+constexpr int k2EX = k2TX + 2 * kXO, k2EY = k2TY + 2;    // 136 x 66
+constexpr int k2Ext = k2EX * k2EY;                       // 8976
+constexpr int k2Face = 2 * (k2TX + k2TY);                // face-root slots of a 2D tile
+constexpr int kRun = 16;                                 // vertices per thread, both shapes
+// The pointer area holds the extended box and, later, the candidate list and
+// its 16-bit slots.
+constexpr int k2PArea = k2Ext > kTileV + kTileV / 2 ? k2Ext : kTileV + kTileV / 2;
+
+static_assert(k2TX * k2TY == kTileV, "2D tiles hold as many vertices as 3D tiles");
+static_assert(k2TX * k2TY == kThreads * kRun && kTZ == kRun, "one run of 16 per thread");
+static_assert(k2Face <= kFace, "the face array has kFace slots per tile");
+static_assert(kHash <= k2Ext, "the 2D pair set fits the key area");
 static_assert(kExt < 65536, "extended-box indices must fit 16 bits");
 static_assert(kHash >= kTileV, "pair table must hold one pair per vertex");
 static_assert(kHash <= kExt, "the pair set fits the key area");
@@ -37,6 +54,7 @@ static_assert(kTileV + kTileV / 2 <= kExt, "candidates (later the pair list) and
 struct TileGeom {
   int64_t nx, ny, nz;
   int64_t tx, ty, tz, ntiles;
+  int flat;  // 1: nz = 1, 2D tiles of k2TX x k2TY
   FastDivU32 div_nx, div_ny, div_tx, div_ty;  // coordinates from linear indices
 };
 
@@ -62,6 +80,8 @@ struct Batch {
   int n_fields;
   int key_mode;
   long long total_tiles;
+  long long tiles3;  // tiles of the 3D fields, which come first; the rest are 2D
+  FieldDesc f0;      // n_fields == 1: the descriptor itself, read from kernel parameters
 };
 
 struct TiledScratch {
@@ -87,8 +107,35 @@ void make_field_desc(const void *field, int dtype, const int64_t dims[3], long l
                      CUtensorMap *map);
 cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus *st,
                               cudaStream_t s);
+// Exit resolution.  kChaseProbe chases the exits of a strided sample of the
+// tile pairs (every `stride`-th) for at most kProbeHops face hops and only
+// counts, in st->pending, the sampled pairs that need more: it decides
+// between the two ways below.  kChaseBudget follows every pair's exits for at
+// most kChaseHops hops, inserts the finished pairs and marks the others
+// pending; kChasePending follows the pending pairs without a budget.
+// kChaseGraph resolves every pair through the jumped face graph
+// (launch_face_graph_*).  clear_table: reset the pair set first.
+enum { kChaseProbe = 0, kChaseBudget = 1, kChasePending = 2, kChaseGraph = 3 };
+constexpr int kChaseHops = 16, kProbeHops = 4;
+// The probe samples about kProbeSample pairs, when there are kProbeMinPairs.
+constexpr unsigned long long kProbeSample = 16384, kProbeMinPairs = 65536;
 cudaError_t launch_resolve_pairs(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
-                                 unsigned long long npairs, DevStatus *st, cudaStream_t s);
+                                 unsigned long long npairs, int mode, const int2 *graph,
+                                 unsigned long long stride, bool clear_table, DevStatus *st,
+                                 cudaStream_t s);
+
+// The face graph: per face slot of every tile (kFace slots per tile, 3D
+// tiles first) the up and dn successor -- the global slot of the next face
+// vertex on the path, or the extremum's vertex index | kSlotFinal.
+constexpr uint32_t kSlotFinal = 0x80000000u;
+inline long long face_graph_slots(const Batch &b) { return b.total_tiles * (long long)kFace; }
+// Builds the graph from the tiles' face roots, then pointer-jumps it in place
+// until every entry is final (at most `rounds` rounds; rounds r use
+// st->round_open[r]).  queue_rounds queues rounds [r0, r1).
+cudaError_t launch_face_graph_build(const Batch &b, const TiledScratch &ts, int2 *graph,
+                                    DevStatus *st, cudaStream_t s);
+cudaError_t launch_face_graph_rounds(const Batch &b, int2 *graph, int r0, int r1, DevStatus *st,
+                                     cudaStream_t s);
 cudaError_t launch_field_starts(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
                                 unsigned int m, cudaStream_t s);
 cudaError_t launch_tile_write(const Batch &b, const TiledScratch &ts, const RankScratch &rs,

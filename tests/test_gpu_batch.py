@@ -103,3 +103,31 @@ def test_single_field_many_distinct_pairs(ctx):
         assert_same_labels(got, oracle.segment(f), "noisy single field")
     finally:
         ms.ms_destroy(fresh)
+
+
+def test_batch_mixed_2d_and_3d_fields(ctx):
+    """2D fields (2D tiles) interleaved with 3D ones in one batch: the host
+    groups them by tile shape, and each field's labels and region count must
+    still come back in the caller's order."""
+    three = small_batch(5, 21)
+    two = [sf.smoothed_noise((300, 200, 1), 31, sigma=3.0)[0],
+           sf.random_ties((129, 65, 1), 32, levels=3)[0],
+           sf.smoothed_noise((64, 64, 1), 33, sigma=2.0)[0].astype(np.float16),
+           sf.broad_gaussians_ramp((500, 70, 1), 34, sigma=50.0)[0]]
+    fields = [two[0], three[0], three[1], two[1], three[2], two[2], three[3], three[4], two[3]]
+    res = run_batch(ctx, fields)
+    for i, (f, got) in enumerate(zip(fields, res)):
+        assert_same_labels(got, oracle.segment(f), f"mixed batch field {i} {f.shape} {f.dtype}")
+    assert ms.ms_last_region_count(ctx) == sum(r[3] for r in res)
+
+
+def test_batch_long_paths_mixed_shapes(ctx):
+    """Smooth fields (long steepest paths through many tiles, resolved through
+    the face graph) batched with noise fields, in both tile shapes."""
+    fields = [sf.broad_gaussians_ramp((150, 140, 130), 61, sigma=60.0),
+              sf.smoothed_noise((70, 50, 40), 62, sigma=3.0),
+              sf.broad_gaussians_ramp((1500, 1100, 1), 63, sigma=300.0)[0],
+              sf.broad_gaussians_ramp((90, 200, 30), 64, sigma=40.0).astype(np.float16)]
+    res = run_batch(ctx, fields)
+    for i, (f, got) in enumerate(zip(fields, res)):
+        assert_same_labels(got, oracle.segment(f), f"long-path batch field {i} {f.shape} {f.dtype}")

@@ -371,3 +371,57 @@ def test_small_grid_with_more_face_hops_than_tiles(ctx):
     # 18^3 has 4 tiles; a descending path of this seeded field changes tiles 5 times
     f = sf.smoothed_noise((18, 18, 18), 109732, sigma=2.5)
     run_and_compare(ctx, f, "18^3 smoothed noise")
+
+
+# 2D grids (nz = 1) take 128 x 64 tiles: exact multiples, one past, one
+# short, many tiles, single rows and columns, and widths that are not a
+# multiple of 4 (no box loads).
+FLAT_DIMS = [(128, 64, 1), (129, 65, 1), (127, 63, 1), (256, 128, 1), (301, 200, 1), (4, 4, 1),
+             (1000, 3, 1), (3, 1000, 1), (1, 5000, 1), (5000, 1, 1), (515, 390, 1)]
+
+
+@pytest.mark.parametrize("dims", FLAT_DIMS)
+def test_flat_tiles(ctx, dims):
+    for case, f in enumerate([sf.smoothed_noise(dims, 51, sigma=3.0, radius=12),
+                              sf.random_ties(dims, 52, levels=2),
+                              sf.broad_gaussians_ramp(dims, 53, sigma=40.0)]):
+        run_and_compare(ctx, f, f"flat {dims} case {case}")
+
+
+def test_flat_long_paths_across_many_tiles(ctx):
+    f = sf.broad_gaussians_ramp((1500, 1100, 1), 54, sigma=300.0)
+    run_and_compare(ctx, f, "flat broad ramp")
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_flat_interior_tiles_signed_zero_subnormals_inf(ctx, seed):
+    """2D tiles whose halo lies inside the field compare raw values."""
+    g = sf.rng_for(200 + seed)
+    tiny = np.float32(1.4e-45)
+    f = g.integers(-3, 4, size=(200, 400)).astype(np.float32) * tiny
+    zeros = g.uniform(size=f.shape) < 0.3
+    f[zeros] = np.where(g.uniform(size=zeros.sum()) < 0.5, np.float32(0.0), np.float32(-0.0))
+    run_and_compare(ctx, f, f"flat subnormal/zero seed {seed}")
+    inf = g.uniform(size=f.shape) < 0.01
+    f[inf] = np.where(g.uniform(size=inf.sum()) < 0.5, np.float32(np.inf), np.float32(-np.inf))
+    run_and_compare(ctx, f, f"flat subnormal/zero/inf seed {seed}")
+
+
+def test_flat_nan_in_interior_tile(ctx):
+    f = sf.smoothed_noise((400, 200, 1), 5, sigma=3.0)
+    f[0, 100, 200] = np.nan
+    with pytest.raises(ms.MSError) as e:
+        gpu_segment(ctx, f)
+    assert e.value.name == "MS_ERR_NAN_INPUT"
+
+
+def test_flat_tiles_equal_staged_path(ctx):
+    f = sf.smoothed_noise((700, 333, 1), 55, sigma=4.0)
+    dev = to_dev(f)
+    n = f.size
+    tiled = ms.segment(ctx, dev)
+    outs = [torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(3)]
+    ms.ms_segment_staged(ctx, dev, (700, 333, 1), ms.MS_F32, *outs)
+    for a, b in zip(tiled[:3], outs):
+        assert torch.equal(a, b)
+    assert tiled[3] == ms.ms_last_region_count(ctx)
