@@ -541,6 +541,7 @@ __device__ __forceinline__ int field_of(const Batch &b, int64_t gt) {
   return lo;
 }
 
+template <bool kSingle>
 __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScratch ts, DevStatus *st) {
   extern __shared__ __align__(128) uint32_t dsmem[];
   uint32_t *K = dsmem;         // kExt words: values / keys, then pair-numbering scratch
@@ -558,8 +559,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
   __syncthreads();
 
   for (int64_t gt = blockIdx.x; gt < bt.tiles3; gt += gridDim.x) {
-    const int fi = field_of(bt, gt);
-    const FieldDesc &fd = bt.fields[fi];
+    const int fi = kSingle ? 0 : field_of(bt, gt);
+    const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
     const TileGeom &g = fd.g;
     const void *__restrict__ field = fd.field;
     const int dtype = fd.dtype;
@@ -751,6 +752,7 @@ __device__ __forceinline__ void steepest_run2(const uint32_t *__restrict__ K, in
 // The 2D form of k_tile_local, for fields with nz = 1 (the tiles after the
 // 3D fields' in a batch).  Thread (lane, warp) owns the run of kRun vertices
 // at x = lane + 32 (warp % 4), y = kRun (warp / 4) + 0 .. kRun - 1.
+template <bool kSingle>
 __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScratch ts, DevStatus *st) {
   extern __shared__ __align__(128) uint32_t dsmem[];
   uint32_t *K = dsmem;          // k2Ext words: values / keys, then the pair set
@@ -768,8 +770,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScra
   __syncthreads();
 
   for (int64_t gt = bt.tiles3 + blockIdx.x; gt < bt.total_tiles; gt += gridDim.x) {
-    const int fi = field_of(bt, gt);
-    const FieldDesc &fd = bt.fields[fi];
+    const int fi = kSingle ? 0 : field_of(bt, gt);
+    const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
     const TileGeom &g = fd.g;
     const void *__restrict__ field = fd.field;
     const int dtype = fd.dtype;
@@ -1093,13 +1095,15 @@ __global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, int m
   const unsigned long long nwork = mode == kChaseProbe ? (npairs + stride - 1) / stride : npairs;
   const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned int mask = rs.capacity - 1u;
+  // A set found too small stops the pass early (the host retries larger).
+  // The flag is one word that every warp would read: it is read on every
+  // 32nd iteration only, or that word's L2 line serialises the pass.
+  unsigned int overflow = 0, it = 0;
   for (unsigned long long w = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < nwork;
        w += step) {
+    if ((it++ & 31u) == 0) overflow = __ldcg(&st->hash_overflow);
     const unsigned long long p = mode == kChaseProbe ? w * stride : w;
     if (mode == kChasePending && ts.pool_slot[p] != kPendingSlot) continue;
-    // a set found too small stops the pass early (the host retries larger);
-    // read here so that the read overlaps the chase
-    const unsigned int overflow = __ldcg(&st->hash_overflow);
     const int2 r = ts.pool_roots[p];
     const uint32_t fi = kSingle ? 0u : ts.pool_field[p];
     const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
@@ -1140,16 +1144,13 @@ __global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, int m
     // soon as the set is known to be too small (the host retries larger)
     unsigned int slot = (unsigned int)mix64t(key) & mask, found = 0xffffffffu;
     if (overflow) continue;
+    bool fresh = false;  // this thread's CAS placed the key
     for (unsigned int probe = 0; probe < rs.probe_limit; ++probe) {
       unsigned long long cur = __ldcg(&rs.table_keys[slot]);
       if (cur == ~0ull) {
         cur = atomicCAS(&rs.table_keys[slot], ~0ull, key);
         if (cur == ~0ull) {
-          const unsigned int at = atomicAdd(&st->n_unique, 1u);
-          if (at < rs.max_unique)
-            rs.list[at] = key;
-          else
-            atomicOr(&st->hash_overflow, 1u);
+          fresh = true;
           found = slot;
           break;
         }
@@ -1159,6 +1160,22 @@ __global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, int m
         break;
       }
       slot = (slot + 1u) & mask;
+    }
+    // new keys join the list with one counter update per warp
+    const unsigned int am = __activemask();
+    const unsigned int nm = __ballot_sync(am, fresh);
+    if (nm) {
+      const int lane = threadIdx.x & 31, leader = __ffs(nm) - 1;
+      unsigned int base = 0;
+      if (lane == leader) base = atomicAdd(&st->n_unique, (unsigned int)__popc(nm));
+      base = __shfl_sync(am, base, leader);
+      if (fresh) {
+        const unsigned int at = base + __popc(nm & ((1u << lane) - 1u));
+        if (at < rs.max_unique)
+          rs.list[at] = key;
+        else
+          atomicOr(&st->hash_overflow, 1u);
+      }
     }
     if (found == 0xffffffffu) atomicOr(&st->hash_overflow, 1u);
     ts.pool_slot[p] = found;
@@ -1180,14 +1197,14 @@ __global__ void k_field_starts(const unsigned long long *__restrict__ sorted, un
 // kernel (3D: the z-column (x0 + lane, y0 + warp, .); 2D: the y-run at
 // x0 + lane + 32 (warp % 4)); its 16 pair numbers are one 32-byte vector.
 // kFlat selects the 2D tiles, which follow the 3D ones.
-template <bool kFlat>
+template <bool kFlat, bool kSingle>
 __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch ts, RankScratch rs) {
   __shared__ int4 T[kStageCap];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t gt_end = kFlat ? bt.total_tiles : bt.tiles3;
   for (int64_t gt = (kFlat ? bt.tiles3 : 0) + blockIdx.x; gt < gt_end; gt += gridDim.x) {
-    const int fi = field_of(bt, gt);
-    const FieldDesc &fd = bt.fields[fi];
+    const int fi = kSingle ? 0 : field_of(bt, gt);
+    const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
     const TileGeom &g = fd.g;
     int64_t v0, stride;  // the run's first vertex and its step
     int n_here;
@@ -1372,21 +1389,23 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
   static_assert(kHash <= kExt, "the pair set reuses the key area");
   if (b.tiles3 > 0) {
     constexpr int kSmem = 2 * kExt * 4;
-    e = cudaFuncSetAttribute(k_tile_local, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    auto kern = b.n_fields == 1 ? k_tile_local<true> : k_tile_local<false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * 2);
     ++tl_launches;
-    k_tile_local<<<(unsigned)grid, kThreads, kSmem, s>>>(b, ts, st);
+    kern<<<(unsigned)grid, kThreads, kSmem, s>>>(b, ts, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (b.total_tiles > b.tiles3) {
     constexpr int kSmem2 = (k2Ext + k2PArea) * 4;
-    e = cudaFuncSetAttribute(k_tile_local2, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem2);
+    auto kern = b.n_fields == 1 ? k_tile_local2<true> : k_tile_local2<false>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem2);
     if (e != cudaSuccess) return e;
     const int64_t grid = std::min<int64_t>(b.total_tiles - b.tiles3, (int64_t)sms() * 2);
     ++tl_launches;
-    k_tile_local2<<<(unsigned)grid, kThreads, kSmem2, s>>>(b, ts, st);
+    kern<<<(unsigned)grid, kThreads, kSmem2, s>>>(b, ts, st);
     e = cudaGetLastError();
   }
   return e;
@@ -1454,14 +1473,20 @@ cudaError_t launch_tile_write(const Batch &b, const TiledScratch &ts, const Rank
   if (b.tiles3 > 0) {
     const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * 4);
     ++tl_launches;
-    k_tile_write<false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
+    if (b.n_fields == 1)
+      k_tile_write<false, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
+    else
+      k_tile_write<false, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (b.total_tiles > b.tiles3) {
     const int64_t grid = std::min<int64_t>(b.total_tiles - b.tiles3, (int64_t)sms() * 4);
     ++tl_launches;
-    k_tile_write<true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
+    if (b.n_fields == 1)
+      k_tile_write<true, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
+    else
+      k_tile_write<true, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
     e = cudaGetLastError();
   }
   return e;
