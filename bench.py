@@ -524,8 +524,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=64)
-    ap.add_argument("--serve-passes", type=int, default=6)
-    ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--serve-passes", type=int, default=16)
+    ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     args = ap.parse_args()
     if args.warmup < 3:
