@@ -302,7 +302,9 @@ def run_batch_bench(args):
         torch.cuda.synchronize()
         return max(ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t)) / steps
 
-    print("[bench] fields on device; timing the batched call", file=sys.stderr, flush=True)
+    print("[bench] fields on device; autotuning the batched call", file=sys.stderr, flush=True)
+    tuning = ms.ms_batch_autotune(ctx, fields, dims, dts, asc, desc, mso)
+    print(f"[bench] tuning {tuning}; timing the batched call", file=sys.stderr, flush=True)
     ms.ms_profile_enable(ctx, True)
     with ClockSampler(dev) as clk:
         t_batch = timed(batched, args.steps)
@@ -321,6 +323,7 @@ def run_batch_bench(args):
                    "vertices": n, "regions_K_total": int(sum(ks)),
                    "l2": "fields 1.1 GB + labels 3.6 GB, larger than L2"},
         "plain_ms_per_step": t_plain, "speedup_vs_plain": t_plain / t_batch,
+        "tuning": tuning, "graph_replay": prof["stages"]["graph"]["launches"] > 0,
         "gpu_launches": prof["launches"],
         "stages_ms_per_step": {k: v["ms"] / max(1, prof["calls"]) for k, v in prof["stages"].items()
                                if v["launches"] or v["ms"]},

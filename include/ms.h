@@ -95,9 +95,17 @@ ms_status ms_segment(ms_ctx *ctx, const void *field, const int64_t dims[3], ms_d
  * separate ms_segment calls would give them.  All pointer arrays are HOST
  * arrays of n_fields DEVICE pointers; k_out (may be NULL) is a host array of
  * n_fields that receives each field's region count K.  When every field has
- * at most 2^24 vertices and at least 8 planes, all fields go through one
- * launch per stage (tiles of all fields in one work list, one global pair set
- * keyed by field); otherwise the fields are segmented one after the other.
+ * at most 2^24 vertices and is 2D (nz = 1) or has at least 8 planes, all
+ * fields go through one launch per stage (tiles of all fields in one work
+ * queue, one global pair set keyed by field); otherwise the fields are
+ * segmented one after the other.
+ * Repeats: the first call with a given set of fields (same pointers, dims and
+ * dtypes) runs step by step and records the sizes it met; the context then
+ * captures the whole pipeline (sized from them, with margins) in a CUDA graph,
+ * and later calls with the same fields replay it with one host
+ * synchronisation.  A replay whose sizes no longer suffice (the fields'
+ * contents changed) is detected on the device and the call runs step by step
+ * again, so results never depend on the path taken.
  * A NaN in any field fails the whole call (MS_ERR_NAN_INPUT).
  * ms_last_region_count then returns the sum of the fields' K. */
 ms_status ms_segment_batch(ms_ctx *ctx, int n_fields, const void *const *fields,
@@ -152,6 +160,33 @@ ms_status ms_compress(ms_ctx *ctx, int32_t *ptr, int64_t n);
 ms_status ms_pair_rank(ms_ctx *ctx, const int32_t *asc, const int32_t *desc, int64_t n,
                        int32_t *ms, int64_t *k_out);
 
+
+/* Launch choices of the batched path; they change scheduling only, never
+ * results.  The library has no counterpart in the paper for them. */
+typedef struct {
+  int tile_ctas;      /* tile kernels: CTAs per SM (1 or 2) */
+  int write_ctas;     /* label-writing kernels: CTAs per SM */
+  int resolve_blocks; /* exit resolution: 256-thread blocks per SM */
+  int chase_hops;     /* face hops of the first exit-chasing pass */
+  int dynamic;        /* 1: tiles taken from a work queue; 0: static stride */
+  double default_ms;  /* ms_batch_autotune: time of the default choices */
+  double best_ms;     /* ms_batch_autotune: time of the chosen ones */
+} ms_tuning;
+
+/* Time the batched path on these fields (arguments as ms_segment_batch; the
+ * outputs are written) under candidate launch choices -- one knob at a time,
+ * keeping a change only if it is at least 2 % faster -- and keep the fastest
+ * for later ms_segment_batch calls with the same fields.  *out (may be NULL)
+ * receives the choice.  MS_ERR_INVALID_ARG if the fields do not take the
+ * batched path. */
+ms_status ms_batch_autotune(ms_ctx *ctx, int n_fields, const void *const *fields,
+                            const int64_t (*dims)[3], const ms_dtype *dtypes,
+                            int32_t *const *asc, int32_t *const *desc, int32_t *const *ms,
+                            ms_tuning *out);
+
+/* Enable (on != 0, the default) or disable graph capture and replay of
+ * repeated batches on this context. */
+ms_status ms_batch_graphs(ms_ctx *ctx, int on);
 
 /* ---- serving ---------------------------------------------------------------- */
 
@@ -243,7 +278,8 @@ typedef enum {
   MS_STAGE_WRITE = 2,
   MS_STAGE_H2D = 3, /* ms_segment_host: field upload */
   MS_STAGE_D2H = 4, /* ms_segment_host: label download */
-  MS_STAGE_COUNT = 5
+  MS_STAGE_GRAPH = 5, /* ms_segment_batch: a whole replayed CUDA graph */
+  MS_STAGE_COUNT = 6
 } ms_stage;
 
 typedef struct {
@@ -263,8 +299,8 @@ ms_status ms_profile_enable(ms_ctx *ctx, int on);
 /* Copy the profiler's counters (zeros if it was never enabled). */
 ms_status ms_profile_read(const ms_ctx *ctx, ms_profile *out);
 
-/* Name of a stage ("tile_local", "resolve", "write", "h2d", "d2h"); "?" if out
- * of range. */
+/* Name of a stage ("tile_local", "resolve", "write", "h2d", "d2h", "graph");
+ * "?" if out of range. */
 const char *ms_profile_stage_name(int stage);
 
 #ifdef __cplusplus

@@ -26,6 +26,7 @@ __all__ = [
     "ms_profile_read", "ms_profile_stage_name", "STAGES", "ms_segment_staged",
     "ms_pair_rank_noalloc", "MS_NOALLOC_MAX_N", "ms_segment_batch", "ms_server_create",
     "ms_server_submit", "ms_server_wait", "ms_server_stats", "ms_server_destroy",
+    "ms_batch_autotune", "ms_batch_graphs",
 ]
 
 MS_F32, MS_F16 = 0, 1
@@ -38,9 +39,17 @@ EXPORTED_SYMBOLS = [
     "ms_last_region_count", "ms_order_keys", "ms_steepest", "ms_compress", "ms_pair_rank",
     "ms_profile_enable", "ms_profile_read", "ms_profile_stage_name", "ms_segment_staged",
     "ms_pair_rank_noalloc", "ms_segment_batch", "ms_server_create", "ms_server_submit",
-    "ms_server_wait", "ms_server_stats", "ms_server_destroy",
+    "ms_server_wait", "ms_server_stats", "ms_server_destroy", "ms_batch_autotune",
+    "ms_batch_graphs",
 ]
 MS_NOALLOC_MAX_N = 262144
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("tile_ctas", ctypes.c_int), ("write_ctas", ctypes.c_int),
+                ("resolve_blocks", ctypes.c_int), ("chase_hops", ctypes.c_int),
+                ("dynamic", ctypes.c_int), ("default_ms", ctypes.c_double),
+                ("best_ms", ctypes.c_double)]
 
 
 class _ServerInfo(ctypes.Structure):
@@ -48,7 +57,7 @@ class _ServerInfo(ctypes.Structure):
                 ("queued", ctypes.c_uint64), ("bytes_in_use", ctypes.c_size_t),
                 ("peak_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
                 ("launches", ctypes.c_uint64)]
-STAGES = ["tile_local", "resolve", "write", "h2d", "d2h"]
+STAGES = ["tile_local", "resolve", "write", "h2d", "d2h", "graph"]
 
 
 class _Profile(ctypes.Structure):
@@ -86,6 +95,9 @@ def load(build: bool = True) -> ctypes.CDLL:
             L.ms_segment.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
             L.ms_segment_batch.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                            c_i64p]
+            L.ms_batch_autotune.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                            ctypes.POINTER(_Tuning)]
+            L.ms_batch_graphs.argtypes = [c_vp, ctypes.c_int]
             L.ms_server_create.argtypes = [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_size_t,
                                            ctypes.c_int]
             L.ms_server_submit.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp,
@@ -193,6 +205,25 @@ def ms_segment_batch(ctx, fields, dims_list, dtypes, ascs, descs, mss) -> list:
                                    ptrs(ascs), ptrs(descs), ptrs(mss), ks), "ms_segment_batch")
     return [int(k) for k in ks]
 
+
+
+
+def ms_batch_autotune(ctx, fields, dims_list, dtypes, ascs, descs, mss) -> dict:
+    """Pick the batched path's launch choices for these fields (see ms.h);
+    returns them with the default and best times."""
+    n = len(fields)
+    ptrs = lambda xs: (c_vp * n)(*[_ptr(x) for x in xs])
+    dims = (ctypes.c_int64 * (3 * n))(*[int(v) for d in dims_list for v in d])
+    dts = (ctypes.c_int * n)(*[int(t) for t in dtypes])
+    t = _Tuning()
+    _check(load().ms_batch_autotune(ctx, n, ptrs(fields), ctypes.cast(dims, c_vp),
+                                    ctypes.cast(dts, c_vp), ptrs(ascs), ptrs(descs), ptrs(mss),
+                                    ctypes.byref(t)), "ms_batch_autotune")
+    return {f: getattr(t, f) for f, _ in _Tuning._fields_}
+
+
+def ms_batch_graphs(ctx, on: bool = True) -> None:
+    _check(load().ms_batch_graphs(ctx, 1 if on else 0), "ms_batch_graphs")
 
 def ms_server_create(device: int = 0, budget_bytes: int = 120 << 30, n_slots: int = 4) -> int:
     h = c_vp()

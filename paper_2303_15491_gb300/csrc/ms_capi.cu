@@ -3,6 +3,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -10,6 +11,29 @@
 #include "ms_tiled.cuh"
 
 using namespace msseg;
+
+// Sizes a step-by-step tiled call met (they size a captured replay).
+struct RunInfo {
+  unsigned long long npairs = 0;  // tile pairs
+  unsigned int m = 0;             // distinct (asc, desc) pairs
+  bool use_graph = false;         // exits resolved through the face graph
+  int rounds = 0;                 // face-graph rounds it took
+};
+
+// A repeated batch: its signature, tuning and captured pipeline.
+struct BatchPlan {
+  std::vector<int64_t> sig;
+  bool tuned = false;
+  Tuning tune;
+  cudaGraphExec_t exec = nullptr;
+  long long epoch = -1;      // ctx alloc_epoch the graph's buffers belong to
+  long long launches = 0;    // kernels per replay
+  std::vector<int> order;    // descriptor j describes field order[j]
+  void *host_desc = nullptr;  // pinned copy of the descriptors the graph uploads
+  size_t host_desc_bytes = 0;
+  uint32_t *hfstart = nullptr;  // pinned: first sorted pair of each descriptor
+  size_t hfstart_count = 0;
+};
 
 struct ms_ctx {
   int device = 0;
@@ -32,6 +56,11 @@ struct ms_ctx {
   void *batch_host = nullptr;            // their pinned staging copy
   size_t batch_host_bytes = 0;
   int64_t last_k = 0;
+  long long alloc_epoch = 0;  // bumped whenever a device buffer is reallocated
+  Tuning tune;                // launch choices without a tuned entry
+  RunInfo run;                // sizes met by the last step-by-step tiled call
+  BatchPlan plan;             // the last batch: its tuning and captured graph
+  bool graphs_on = true;
   // profiler
   bool prof_on = false;
   ms_profile prof{};
@@ -119,6 +148,7 @@ ms_status read_status(ms_ctx *c) {
 
 ms_status ensure_scratch(ms_ctx *c, size_t bytes) {
   if (c->scratch_bytes >= bytes) return MS_OK;
+  ++c->alloc_epoch;
   if (c->scratch) {
     cudaStreamSynchronize(c->stream);
     cudaFree(c->scratch);
@@ -227,6 +257,7 @@ void finish_profile(ms_ctx *c, long long launches0) {
 
 ms_status ensure_buffer(ms_ctx *c, void **buf, size_t *have, size_t bytes) {
   if (*have >= bytes) return MS_OK;
+  ++c->alloc_epoch;
   if (*buf) {
     cudaStreamSynchronize(c->stream);
     cudaFree(*buf);
@@ -254,7 +285,12 @@ ms_status jump_face_graph(ms_ctx *c, const Batch &b, int2 *graph, long long slot
   ms_status s = read_status(c);
   if (s != MS_OK) return s;
   for (int r = blind;; ++r) {
-    if (c->hst->round_open[r - 1] == 0u) return MS_OK;
+    if (c->hst->round_open[r - 1] == 0u) {
+      int used = r;  // the first round that left nothing open, counted from 1
+      while (used > 1 && c->hst->round_open[used - 2] == 0u) --used;
+      c->run.rounds = used;
+      return MS_OK;
+    }
     if (r == cap) return MS_ERR_NOT_CONVERGED;
     MS_TRY(launch_face_graph_rounds(b, graph, r, r + 1, c->dst, c->stream));
     s = read_status(c);
@@ -277,9 +313,17 @@ struct FieldArg {
 // launch per stage covers every tile of every field.  Batches key the global
 // pair set by (field, asc, desc); each field's MS ids start at its first pair
 // in the sorted set.  k_out[f] receives each field's region count.
-ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
+// Descriptors and tensor maps of a field table, staged in pinned memory and
+// copied to the device; fills b (tuning aside) and the field order.
+struct Staged {
+  Batch b;
+  std::vector<int> order;
+  int64_t total_n = 0, max_n = 0;
+  size_t bytes = 0;  // descriptor bytes on the device
+};
+
+ms_status stage_fields(ms_ctx *c, const FieldArg *fa, int nf, Staged *out) {
   const int key_mode = nf > 1 ? kKeyBatch : kKeyOne;
-  // ---- descriptors and tensor maps, staged in pinned memory then copied
   const size_t desc_bytes = ((size_t)nf * sizeof(FieldDesc) + 127) & ~(size_t)127;
   const size_t bytes = desc_bytes + (size_t)nf * sizeof(CUtensorMap);
   ms_status s = ensure_buffer(c, &c->batch_dev, &c->batch_dev_bytes, bytes);
@@ -328,6 +372,32 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
   b.total_tiles = total_tiles;
   b.tiles3 = tiles3;
   b.f0 = hd[0];
+  out->b = b;
+  out->order = std::move(order);
+  out->total_n = total_n;
+  out->max_n = max_n;
+  out->bytes = bytes;
+  return MS_OK;
+}
+
+int pair_key_bits(const Staged &sf, int *raw_bits) {
+  *raw_bits = sf.b.key_mode == kKeyBatch ? bit_width(sf.b.n_fields - 1) + 48 : 0;
+  return sf.b.key_mode == kKeyBatch ? 0 : bit_width(sf.max_n - 1);
+}
+
+// The tiled path, step by step (host reads sizes and statuses in between).
+ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
+                        const Tuning &tune) {
+  Staged sf;
+  ms_status s = stage_fields(c, fa, nf, &sf);
+  if (s != MS_OK) return s;
+  Batch b = sf.b;
+  b.tune = tune;
+  const int key_mode = b.key_mode;
+  const long long total_tiles = b.total_tiles;
+  const int64_t total_n = sf.total_n;
+  const std::vector<int> &order = sf.order;
+  c->run = RunInfo{};
 
   // ---- tile pass; the pair pool is sized from the last call, exact on overflow
   unsigned long long cap = c->pool_hint;
@@ -417,15 +487,19 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
     want = exact;
   }
   const unsigned int m = c->hst->n_unique;
-  if (key_mode == kKeyBatch)
-    MS_TRY(launch_pairs_sort(rs, m, 0, c->stream, bit_width(nf - 1) + 48));
-  else
-    MS_TRY(launch_pairs_sort(rs, m, bit_width(max_n - 1), c->stream));
+  c->run.npairs = npairs;
+  c->run.m = m;
+  c->run.use_graph = use_graph;
+  {
+    int raw = 0;
+    const int kb = pair_key_bits(sf, &raw);
+    MS_TRY(launch_pairs_sort(rs, m, kb, c->stream, raw));
+  }
   MS_TRY(launch_pairs_assign(rs, m, c->stream));
   MS_TRY(launch_field_starts(b, ts, rs, m, c->stream));
   t2.stop();
   StageTimer t3(c, MS_STAGE_WRITE);
-  MS_TRY(launch_tile_write(b, ts, rs, c->stream));
+  MS_TRY(launch_tile_write(b, ts, rs, c->dst, c->stream));
   t3.stop();
   if (key_mode == kKeyBatch) {
     uint32_t *hf = reinterpret_cast<uint32_t *>(c->batch_host);  // reuse the staging buffer
@@ -457,7 +531,7 @@ ms_status segment_device(ms_ctx *c, const void *field, const int64_t dims[3], in
   if (tiled_shape(dims)) {
     const FieldArg fa{field, dims, dtype, n, asc, desc, ms};
     int64_t k = 0;
-    const ms_status s = segment_tiled(c, &fa, 1, &k);
+    const ms_status s = segment_tiled(c, &fa, 1, &k, c->tune);
     if (s == MS_OK) c->last_k = k;
     return s;
   }
@@ -486,6 +560,242 @@ ms_status segment_staged(ms_ctx *c, const void *field, const int64_t dims[3], in
   s = rank_pairs(c, asc, desc, n, ms, guess, bound);
   t2.stop();
   return s;
+}
+
+// Checks a field table and converts it; *batchable: the fields can share the
+// tiled path's launches.
+ms_status batch_args(int n_fields, const void *const *fields, const int64_t (*dims)[3],
+                     const ms_dtype *dtypes, int32_t *const *asc, int32_t *const *desc,
+                     int32_t *const *ms, std::vector<FieldArg> *out, bool *batchable) {
+  if (n_fields < 0 || (n_fields > 0 && (!fields || !dims || !dtypes || !asc || !desc || !ms)))
+    return MS_ERR_INVALID_ARG;
+  std::vector<FieldArg> &fa = *out;
+  fa.assign((size_t)n_fields, FieldArg{});
+  *batchable = n_fields <= kBatchMaxFields;
+  for (int f = 0; f < n_fields; ++f) {
+    int64_t n = 0;
+    ms_status s = check_dims(dims[f], &n);
+    if (s != MS_OK) return s;
+    s = check_dtype(dtypes[f]);
+    if (s != MS_OK) return s;
+    if (!is_device_pointer(fields[f]) || !is_device_pointer(asc[f]) || !is_device_pointer(desc[f]) ||
+        !is_device_pointer(ms[f]))
+      return MS_ERR_INVALID_ARG;
+    if (asc[f] == desc[f] || asc[f] == ms[f] || desc[f] == ms[f]) return MS_ERR_INVALID_ARG;
+    fa[f] = FieldArg{fields[f], dims[f], (int)dtypes[f], n, asc[f], desc[f], ms[f]};
+    *batchable = *batchable && n <= kBatchMaxN && tiled_shape(dims[f]);
+  }
+  return MS_OK;
+}
+
+// ---- repeated batches: graph capture and replay --------------------------
+
+std::vector<int64_t> batch_signature(const FieldArg *fa, int nf) {
+  std::vector<int64_t> sig;
+  sig.reserve(1 + (size_t)nf * 8);
+  sig.push_back(nf);
+  for (int f = 0; f < nf; ++f) {
+    const FieldArg &a = fa[f];
+    sig.insert(sig.end(), {(int64_t)(intptr_t)a.field, a.dims[0], a.dims[1], a.dims[2], a.dtype,
+                           (int64_t)(intptr_t)a.asc, (int64_t)(intptr_t)a.desc,
+                           (int64_t)(intptr_t)a.ms});
+  }
+  return sig;
+}
+
+void drop_graph(BatchPlan *p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  p->exec = nullptr;
+  p->epoch = -1;
+}
+
+void reset_plan(BatchPlan *p) {
+  drop_graph(p);
+  if (p->host_desc) cudaFreeHost(p->host_desc);
+  if (p->hfstart) cudaFreeHost(p->hfstart);
+  *p = BatchPlan{};
+}
+
+// Capture the whole tiled pipeline for these fields as one CUDA graph, sized
+// from the step-by-step call that just ran (c->run) with margins; nothing in
+// it reads back to the host but the final status block and field starts.
+ms_status capture_plan(ms_ctx *c, const FieldArg *fa, int nf) {
+  BatchPlan &P = c->plan;
+  drop_graph(&P);
+  Staged sf;
+  ms_status s = stage_fields(c, fa, nf, &sf);  // also leaves the descriptors on the device
+  if (s != MS_OK) return s;
+  Batch b = sf.b;
+  b.tune = P.tuned ? P.tune : c->tune;
+  const RunInfo run = c->run;
+  // capacities: the sizes met, with margins; overflow is detected on the device
+  unsigned long long pool_cap = run.npairs + run.npairs / 8 + 4096;
+  if (pool_cap > (unsigned long long)sf.total_n) pool_cap = (unsigned long long)sf.total_n;
+  const unsigned int hcap = pow2_at_least(4ull * run.m + 4096);
+  s = ensure_buffer(c, &c->tscratch, &c->tscratch_bytes,
+                    tiled_scratch_bytes(b.total_tiles, nf, pool_cap));
+  if (s != MS_OK) return s;
+  s = ensure_scratch(c, rank_scratch_bytes(hcap));
+  if (s != MS_OK) return s;
+  const long long slots = face_graph_slots(b);
+  int2 *graph = nullptr;
+  if (run.use_graph) {
+    s = ensure_buffer(c, &c->graph, &c->graph_bytes, (size_t)slots * sizeof(int2));
+    if (s != MS_OK) return s;
+    graph = static_cast<int2 *>(c->graph);
+  }
+  TiledScratch ts;
+  tiled_scratch_carve(c->tscratch, b.total_tiles, nf, pool_cap, &ts);
+  RankScratch rs;
+  rank_scratch_carve(c->scratch, hcap, &rs);
+  if ((uint64_t)hcap < 2 * run.npairs + 2) rs.probe_limit = kEstimateProbeLimit;
+  // pinned copies the graph reads from and writes to
+  if (P.host_desc_bytes < sf.bytes) {
+    if (P.host_desc) cudaFreeHost(P.host_desc);
+    P.host_desc = nullptr;
+    P.host_desc_bytes = 0;
+    MS_TRY(cudaMallocHost(&P.host_desc, sf.bytes));
+    P.host_desc_bytes = sf.bytes;
+  }
+  memcpy(P.host_desc, c->batch_host, sf.bytes);
+  if (P.hfstart_count < (size_t)nf) {
+    if (P.hfstart) cudaFreeHost(P.hfstart);
+    P.hfstart = nullptr;
+    P.hfstart_count = 0;
+    MS_TRY(cudaMallocHost(reinterpret_cast<void **>(&P.hfstart), (size_t)nf * 4));
+    P.hfstart_count = (size_t)nf;
+  }
+  P.order = sf.order;
+  int raw = 0;
+  const int kb = pair_key_bits(sf, &raw);
+  const int rounds = std::max(3, run.rounds + 1);
+  MS_TRY(cudaStreamSynchronize(c->stream));
+
+  const long long l0 = tl_launches;
+  MS_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+  auto enqueue = [&]() -> cudaError_t {
+    cudaError_t e;
+    // the descriptors, in case another call on this context replaced them
+    if ((e = cudaMemcpyAsync(c->batch_dev, P.host_desc, sf.bytes, cudaMemcpyHostToDevice,
+                             c->stream)) != cudaSuccess)
+      return e;
+    if ((e = cudaMemsetAsync(c->dst, 0, sizeof(DevStatus), c->stream)) != cudaSuccess) return e;
+    if ((e = launch_tile_local(b, ts, c->dst, c->stream)) != cudaSuccess) return e;
+    if (run.use_graph) {
+      if ((e = launch_face_graph_build(b, ts, graph, c->dst, c->stream)) != cudaSuccess) return e;
+      if ((e = launch_face_graph_rounds(b, graph, 0, rounds, c->dst, c->stream)) != cudaSuccess)
+        return e;
+      if ((e = launch_resolve_pairs(b, ts, rs, pool_cap, kChaseGraph, graph, 1, true, c->dst,
+                                    c->stream)) != cudaSuccess)
+        return e;
+    } else {
+      if ((e = launch_resolve_pairs(b, ts, rs, pool_cap, kChaseBudget, nullptr, 1, true, c->dst,
+                                    c->stream)) != cudaSuccess)
+        return e;
+      if ((e = launch_resolve_pairs(b, ts, rs, pool_cap, kChasePending, nullptr, 1, false, c->dst,
+                                    c->stream)) != cudaSuccess)
+        return e;
+    }
+    if ((e = launch_pairs_sort(rs, rs.max_unique, kb, c->stream, raw, &c->dst->n_unique)) !=
+        cudaSuccess)
+      return e;
+    if ((e = launch_pairs_assign(rs, rs.max_unique, c->stream, &c->dst->n_unique)) != cudaSuccess)
+      return e;
+    if ((e = launch_field_starts(b, ts, rs, rs.max_unique, c->stream, &c->dst->n_unique)) !=
+        cudaSuccess)
+      return e;
+    if ((e = launch_tile_write(b, ts, rs, c->dst, c->stream)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(c->hst, c->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost,
+                             c->stream)) != cudaSuccess)
+      return e;
+    if (b.key_mode == kKeyBatch)
+      e = cudaMemcpyAsync(P.hfstart, ts.fstart, (size_t)nf * 4, cudaMemcpyDeviceToHost, c->stream);
+    return e;
+  };
+  const cudaError_t qe = enqueue();
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+  tl_launches = l0;  // capture launches nothing
+  if (qe != cudaSuccess || ce != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return MS_ERR_CUDA;
+  }
+  // kernel nodes per replay
+  size_t nn = 0;
+  cudaGraphGetNodes(g, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  cudaGraphGetNodes(g, nodes.data(), &nn);
+  long long kernels = 0;
+  for (cudaGraphNode_t n : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(n, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&P.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    P.exec = nullptr;
+    cudaGetLastError();
+    return MS_ERR_CUDA;
+  }
+  P.launches = kernels;
+  P.epoch = c->alloc_epoch;
+  return MS_OK;
+}
+
+// Replay the captured pipeline.  *fallback: the sizes it was captured with no
+// longer suffice (the caller runs the call step by step).
+ms_status replay_plan(ms_ctx *c, int nf, int64_t *k_out, bool *fallback) {
+  BatchPlan &P = c->plan;
+  *fallback = false;
+  if (c->prof_on) cudaEventRecord(c->ev[MS_STAGE_GRAPH][0], c->stream);
+  MS_TRY(cudaGraphLaunch(P.exec, c->stream));
+  if (c->prof_on) {
+    cudaEventRecord(c->ev[MS_STAGE_GRAPH][1], c->stream);
+    c->ev_pending[MS_STAGE_GRAPH] = true;
+    c->prof.stage_launches[MS_STAGE_GRAPH] += P.launches;
+  }
+  tl_launches += P.launches;
+  MS_TRY(cudaStreamSynchronize(c->stream));
+  const DevStatus &h = *c->hst;
+  if (h.nan_flag) return MS_ERR_NAN_INPUT;
+  if (h.timeout) return MS_ERR_TIMEOUT;
+  if (h.pool_overflow || h.hash_overflow || h.not_converged || h.bad_index) {
+    *fallback = true;
+    return MS_OK;
+  }
+  const unsigned int m = h.n_unique;
+  if (nf > 1) {
+    for (int j = 0; j < nf; ++j) {
+      const uint32_t end = j + 1 < nf ? P.hfstart[j + 1] : m;
+      k_out[P.order[j]] = (int64_t)(end - P.hfstart[j]);
+    }
+  } else {
+    k_out[0] = m;
+  }
+  c->last_k = m;
+  return MS_OK;
+}
+
+// A batch through the tiled path: replayed from its graph when the same fields
+// come again, else step by step (then captured for the next time).
+ms_status run_batch(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
+  BatchPlan &P = c->plan;
+  std::vector<int64_t> sig = batch_signature(fa, nf);
+  if (P.sig != sig) {
+    reset_plan(&P);
+    P.sig = std::move(sig);
+  }
+  if (c->graphs_on && P.exec && P.epoch == c->alloc_epoch) {
+    bool fallback = false;
+    const ms_status s = replay_plan(c, nf, k_out, &fallback);
+    if (s != MS_OK || !fallback) return s;
+    drop_graph(&P);
+  }
+  const ms_status s = segment_tiled(c, fa, nf, k_out, P.tuned ? P.tune : c->tune);
+  if (s != MS_OK) return s;
+  if (c->graphs_on && !P.exec && capture_plan(c, fa, nf) != MS_OK) drop_graph(&P);
+  return MS_OK;
 }
 
 }  // namespace
@@ -606,31 +916,21 @@ ms_status ms_segment_staged(ms_ctx *c, const void *field, const int64_t dims[3],
 ms_status ms_segment_batch(ms_ctx *c, int n_fields, const void *const *fields,
                            const int64_t (*dims)[3], const ms_dtype *dtypes, int32_t *const *asc,
                            int32_t *const *desc, int32_t *const *ms, int64_t *k_out) {
-  if (!c || n_fields < 0 || (n_fields > 0 && (!fields || !dims || !dtypes || !asc || !desc || !ms)))
-    return MS_ERR_INVALID_ARG;
+  if (!c || n_fields < 0) return MS_ERR_INVALID_ARG;
   if (n_fields == 0) return MS_OK;
   DeviceGuard g(c->device);
-  std::vector<FieldArg> fa((size_t)n_fields);
-  bool batchable = n_fields <= kBatchMaxFields;
-  for (int f = 0; f < n_fields; ++f) {
-    int64_t n = 0;
-    ms_status s = check_dims(dims[f], &n);
+  std::vector<FieldArg> fa;
+  bool batchable = false;
+  {
+    const ms_status s = batch_args(n_fields, fields, dims, dtypes, asc, desc, ms, &fa, &batchable);
     if (s != MS_OK) return s;
-    s = check_dtype(dtypes[f]);
-    if (s != MS_OK) return s;
-    if (!is_device_pointer(fields[f]) || !is_device_pointer(asc[f]) || !is_device_pointer(desc[f]) ||
-        !is_device_pointer(ms[f]))
-      return MS_ERR_INVALID_ARG;
-    if (asc[f] == desc[f] || asc[f] == ms[f] || desc[f] == ms[f]) return MS_ERR_INVALID_ARG;
-    fa[f] = FieldArg{fields[f], dims[f], (int)dtypes[f], n, asc[f], desc[f], ms[f]};
-    batchable = batchable && n <= kBatchMaxN && tiled_shape(dims[f]);
   }
   const long long l0 = tl_launches;
   ms_status s = MS_OK;
   int64_t total_k = 0;
   if (batchable) {
     std::vector<int64_t> k((size_t)n_fields, 0);
-    s = segment_tiled(c, fa.data(), n_fields, k.data());
+    s = run_batch(c, fa.data(), n_fields, k.data());
     for (int f = 0; f < n_fields && s == MS_OK; ++f) {
       if (k_out) k_out[f] = k[f];
       total_k += k[f];
@@ -650,6 +950,110 @@ ms_status ms_segment_batch(ms_ctx *c, int n_fields, const void *const *fields,
     finish_profile(c, l0);
   }
   return s;
+}
+
+ms_status ms_batch_graphs(ms_ctx *c, int on) {
+  if (!c) return MS_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  c->graphs_on = on != 0;
+  if (!c->graphs_on) drop_graph(&c->plan);
+  return MS_OK;
+}
+
+ms_status ms_batch_autotune(ms_ctx *c, int n_fields, const void *const *fields,
+                            const int64_t (*dims)[3], const ms_dtype *dtypes, int32_t *const *asc,
+                            int32_t *const *desc, int32_t *const *ms, ms_tuning *out) {
+  if (!c || n_fields <= 0) return MS_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  std::vector<FieldArg> fa;
+  bool batchable = false;
+  ms_status s = batch_args(n_fields, fields, dims, dtypes, asc, desc, ms, &fa, &batchable);
+  if (s != MS_OK) return s;
+  if (!batchable) return MS_ERR_INVALID_ARG;
+  BatchPlan &P = c->plan;
+  std::vector<int64_t> sig = batch_signature(fa.data(), n_fields);
+  if (P.sig != sig) {
+    reset_plan(&P);
+    P.sig = std::move(sig);
+  }
+  drop_graph(&P);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  MS_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return MS_ERR_CUDA;
+  }
+  std::vector<int64_t> k((size_t)n_fields, 0);
+  const bool prof = c->prof_on;
+  c->prof_on = false;  // candidates are not profiled calls
+  // median of three timed step-by-step runs (after one untimed run)
+  auto time_of = [&](const Tuning &t, double *ms_out) -> ms_status {
+    std::vector<float> v;
+    for (int r = 0; r < 4; ++r) {
+      cudaEventRecord(e0, c->stream);
+      const ms_status st = segment_tiled(c, fa.data(), n_fields, k.data(), t);
+      if (st != MS_OK) return st;
+      cudaEventRecord(e1, c->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return MS_ERR_CUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) v.push_back(ms);
+    }
+    std::sort(v.begin(), v.end());
+    *ms_out = v[v.size() / 2];
+    return MS_OK;
+  };
+  Tuning best = c->tune;
+  double t_default = 0, t_best = 0;
+  s = time_of(best, &t_default);
+  t_best = t_default;
+  struct Knob {
+    int Tuning::*field;
+    std::vector<int> values;
+  };
+  const Knob knobs[] = {{&Tuning::dynamic, {1, 0}},
+                        {&Tuning::tile_ctas, {2, 1}},
+                        {&Tuning::write_ctas, {2, 4, 8}},
+                        {&Tuning::resolve_blocks, {8, 16, 32}},
+                        {&Tuning::chase_hops, {8, 16, 32}}};
+  for (const Knob &kn : knobs) {
+    if (s != MS_OK) break;
+    const int start = best.*(kn.field);
+    for (int v : kn.values) {
+      if (v == start) continue;
+      Tuning t = best;
+      t.*(kn.field) = v;
+      double tm = 0;
+      s = time_of(t, &tm);
+      if (s != MS_OK) break;
+      if (tm < 0.98 * t_best) {
+        best = t;
+        t_best = tm;
+      }
+    }
+  }
+  c->prof_on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != MS_OK) return s;
+  P.tune = best;
+  P.tuned = true;
+  // leave the outputs as the chosen choices compute them (identical anyway)
+  s = segment_tiled(c, fa.data(), n_fields, k.data(), best);
+  if (s != MS_OK) return s;
+  if (out) {
+    out->tile_ctas = best.tile_ctas;
+    out->write_ctas = best.write_ctas;
+    out->resolve_blocks = best.resolve_blocks;
+    out->chase_hops = best.chase_hops;
+    out->dynamic = best.dynamic;
+    out->default_ms = t_default;
+    out->best_ms = t_best;
+  }
+  int64_t total = 0;
+  for (int64_t x : k) total += x;
+  c->last_k = total;
+  return MS_OK;
 }
 
 ms_status ms_segment_host(ms_ctx *c, const void *host_field, const int64_t dims[3],
@@ -786,7 +1190,8 @@ ms_status ms_profile_read(const ms_ctx *c, ms_profile *out) {
 }
 
 const char *ms_profile_stage_name(int stage) {
-  static const char *names[MS_STAGE_COUNT] = {"tile_local", "resolve", "write", "h2d", "d2h"};
+  static const char *names[MS_STAGE_COUNT] = {"tile_local", "resolve", "write",
+                                              "h2d",        "d2h",     "graph"};
   return (stage >= 0 && stage < MS_STAGE_COUNT) ? names[stage] : "?";
 }
 

@@ -82,9 +82,13 @@ cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t
                                 const RankScratch &rs, DevStatus *st, cudaStream_t s);
 // Sorts the pair list: (asc << 32) | desc keys with labels below 2^key_bits,
 // or (raw_bits > 0) keys compared on their low raw_bits bits as they are.
+// With m_dev, n_unique is a capacity that sizes the launches and the kernels
+// read the actual count from m_dev (no host round trip; graph-capturable).
 cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int n_unique, int key_bits,
-                              cudaStream_t s, int raw_bits = 0);
-cudaError_t launch_pairs_assign(const RankScratch &rs, unsigned int n_unique, cudaStream_t s);
+                              cudaStream_t s, int raw_bits = 0,
+                              const unsigned int *m_dev = nullptr);
+cudaError_t launch_pairs_assign(const RankScratch &rs, unsigned int n_unique, cudaStream_t s,
+                                const unsigned int *m_dev = nullptr);
 cudaError_t launch_pairs_lookup(const int32_t *asc, const int32_t *desc, int64_t n,
                                 const RankScratch &rs, int32_t *ms, cudaStream_t s);
 cudaError_t launch_fill_u64(unsigned long long *p, size_t count, unsigned long long v,

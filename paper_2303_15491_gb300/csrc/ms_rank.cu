@@ -98,8 +98,16 @@ __device__ __forceinline__ unsigned int sort_digit(unsigned long long key, int b
   return (unsigned int)(compact >> shift) & 255u;
 }
 
-__global__ void k_radix_hist(const unsigned long long *__restrict__ in, unsigned int m, int b,
-                             int shift, unsigned int *__restrict__ hist) {
+// m_dev (optional): the key count on the device, at most m (graph replays
+// size their launches from the capacity m and read the count here).
+__device__ __forceinline__ unsigned int count_of(unsigned int m, const unsigned int *m_dev) {
+  return m_dev ? min(*m_dev, m) : m;
+}
+
+__global__ void k_radix_hist(const unsigned long long *__restrict__ in, unsigned int m,
+                             const unsigned int *m_dev, int b, int shift,
+                             unsigned int *__restrict__ hist) {
+  m = count_of(m, m_dev);
   __shared__ unsigned int h[256];
   h[threadIdx.x] = 0;
   __syncthreads();
@@ -119,8 +127,10 @@ __global__ void k_radix_hist(const unsigned long long *__restrict__ in, unsigned
 // computed here from the raw histogram (no separate scan launch).
 __global__ void __launch_bounds__(256) k_radix_scatter(const unsigned long long *__restrict__ in,
                                                        unsigned long long *__restrict__ out,
-                                                       unsigned int m, int b, int shift,
+                                                       unsigned int m, const unsigned int *m_dev,
+                                                       int b, int shift,
                                                        const unsigned int *__restrict__ hist) {
+  m = count_of(m, m_dev);
   __shared__ unsigned int run[256];
   __shared__ unsigned int wcnt[8][256];
   const unsigned int warp = threadIdx.x >> 5, lane = lane_id();
@@ -178,7 +188,8 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const unsigned long long 
 }
 
 __global__ void k_pairs_assign(const unsigned long long *__restrict__ sorted, unsigned int m,
-                               RankScratch rs) {
+                               const unsigned int *m_dev, RankScratch rs) {
+  m = count_of(m, m_dev);
   const unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   const int slot = table_find(rs, sorted[i]);
@@ -253,7 +264,7 @@ cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t
 
 // Sorts rs.list[0, m) in place (the result always ends in rs.list).
 cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bits,
-                              cudaStream_t s, int raw_bits) {
+                              cudaStream_t s, int raw_bits, const unsigned int *m_dev) {
   if (m <= 1) return cudaSuccess;
   unsigned long long *src = rs.list, *dst = rs.tmp;
   const int b = raw_bits > 0 ? -1 : key_bits;  // bit width of one label, or raw keys
@@ -263,9 +274,9 @@ cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bit
   const unsigned int blocks = std::max(1u, std::min((unsigned)kSortBlocks, (m + 4095) / 4096));
   for (int shift = 0; shift < total; shift += 8) {
     ++tl_launches;
-    k_radix_hist<<<blocks, 256, 0, s>>>(src, m, b, shift, rs.hist);
+    k_radix_hist<<<blocks, 256, 0, s>>>(src, m, m_dev, b, shift, rs.hist);
     ++tl_launches;
-    k_radix_scatter<<<blocks, 256, 0, s>>>(src, dst, m, b, shift, rs.hist);
+    k_radix_scatter<<<blocks, 256, 0, s>>>(src, dst, m, m_dev, b, shift, rs.hist);
     unsigned long long *t = src;
     src = dst;
     dst = t;
@@ -275,10 +286,11 @@ cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bit
   return cudaGetLastError();
 }
 
-cudaError_t launch_pairs_assign(const RankScratch &rs, unsigned int m, cudaStream_t s) {
+cudaError_t launch_pairs_assign(const RankScratch &rs, unsigned int m, cudaStream_t s,
+                                const unsigned int *m_dev) {
   if (m == 0) return cudaSuccess;
   ++tl_launches;
-  k_pairs_assign<<<(m + 255) / 256, 256, 0, s>>>(rs.list, m, rs);
+  k_pairs_assign<<<(m + 255) / 256, 256, 0, s>>>(rs.list, m, m_dev, rs);
   return cudaGetLastError();
 }
 

@@ -522,6 +522,24 @@ __device__ __forceinline__ void number_tile_pairs(uint32_t *K, uint32_t *P, cons
   __syncthreads();
 }
 
+// Tile scheduling of the persistent kernels: a static stride over the tile
+// range, or a work queue -- an atomic counter that thread 0 reads one tile
+// ahead into *s_next (all threads have read the current index when it does).
+__device__ __forceinline__ long long queue_first(bool dyn, unsigned int *ctr, long long *s_next) {
+  if (!dyn) return blockIdx.x;
+  if (threadIdx.x == 0) *s_next = atomicAdd(ctr, 1u);
+  __syncthreads();
+  return *s_next;
+}
+__device__ __forceinline__ void queue_prefetch(bool dyn, unsigned int *ctr, long long *s_next) {
+  if (!dyn) return;
+  __syncthreads();
+  if (threadIdx.x == 0) *s_next = atomicAdd(ctr, 1u);
+}
+__device__ __forceinline__ long long queue_next(bool dyn, long long k, const long long *s_next) {
+  return dyn ? *s_next : k + gridDim.x;
+}
+
 // One CTA per tile (persistent).  Thread (lane, warp) owns the z-column of
 // vertices (x0 + lane, y0 + warp, z0 .. z0 + TZ - 1).
 //
@@ -558,7 +576,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
   if (threadIdx.x == 0) mbar_init(&s_bar, 1);
   __syncthreads();
 
-  for (int64_t gt = blockIdx.x; gt < bt.tiles3; gt += gridDim.x) {
+  __shared__ long long s_next;
+  const bool dyn = bt.tune.dynamic != 0;
+  for (long long k = queue_first(dyn, ts.queue + 0, &s_next); k < bt.tiles3;
+       k = queue_next(dyn, k, &s_next)) {
+    queue_prefetch(dyn, ts.queue + 0, &s_next);
+    const int64_t gt = k;
     const int fi = kSingle ? 0 : field_of(bt, gt);
     const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
     const TileGeom &g = fd.g;
@@ -769,7 +792,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScra
   if (threadIdx.x == 0) mbar_init(&s_bar, 1);
   __syncthreads();
 
-  for (int64_t gt = bt.tiles3 + blockIdx.x; gt < bt.total_tiles; gt += gridDim.x) {
+  __shared__ long long s_next;
+  const bool dyn = bt.tune.dynamic != 0;
+  for (long long k = queue_first(dyn, ts.queue + 1, &s_next); k < bt.total_tiles - bt.tiles3;
+       k = queue_next(dyn, k, &s_next)) {
+    queue_prefetch(dyn, ts.queue + 1, &s_next);
+    const int64_t gt = bt.tiles3 + k;
     const int fi = kSingle ? 0 : field_of(bt, gt);
     const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
     const TileGeom &g = fd.g;
@@ -1120,7 +1148,7 @@ __global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, int m
       d = final_of(r.y, true);
     } else {
       const int64_t budget =
-          mode == kChaseProbe ? kProbeHops : mode == kChaseBudget ? kChaseHops : (1ll << 40);
+          mode == kChaseProbe ? kProbeHops : mode == kChaseBudget ? bt.tune.chase_hops : (1ll << 40);
       const uint32_t *face = ts.face + fd.tile_base * (long long)kFace;
       a = fd.g.flat ? chase2(fd.g, face, r.x, false, budget, st)
                     : chase(fd.g, face, r.x, false, budget, st);
@@ -1184,7 +1212,8 @@ __global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, int m
 
 // Many-field batches: the first sorted pair of each field (its ids start there).
 __global__ void k_field_starts(const unsigned long long *__restrict__ sorted, unsigned int m,
-                               uint32_t *__restrict__ fstart) {
+                               const unsigned int *m_dev, uint32_t *__restrict__ fstart) {
+  if (m_dev) m = min(*m_dev, m);
   const unsigned int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   const unsigned int f = (unsigned int)(sorted[i] >> 48);
@@ -1198,11 +1227,24 @@ __global__ void k_field_starts(const unsigned long long *__restrict__ sorted, un
 // x0 + lane + 32 (warp % 4)); its 16 pair numbers are one 32-byte vector.
 // kFlat selects the 2D tiles, which follow the 3D ones.
 template <bool kFlat, bool kSingle>
-__global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch ts, RankScratch rs) {
+__global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch ts, RankScratch rs,
+                                                         const DevStatus *st) {
+  // A replayed graph runs this kernel even when an earlier stage found its
+  // buffers too small; the tile ranges and set slots are then not valid to
+  // read, and the host runs the call again step by step.
+  if (st->pool_overflow | st->hash_overflow | st->not_converged | st->bad_index | st->timeout |
+      st->nan_flag)
+    return;
   __shared__ int4 T[kStageCap];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t gt_end = kFlat ? bt.total_tiles : bt.tiles3;
-  for (int64_t gt = (kFlat ? bt.tiles3 : 0) + blockIdx.x; gt < gt_end; gt += gridDim.x) {
+  const int64_t base = kFlat ? bt.tiles3 : 0;
+  const long long count = kFlat ? bt.total_tiles - bt.tiles3 : bt.tiles3;
+  unsigned int *ctr = ts.queue + (kFlat ? 3 : 2);
+  __shared__ long long s_next;
+  const bool dyn = bt.tune.dynamic != 0;
+  for (long long k = queue_first(dyn, ctr, &s_next); k < count; k = queue_next(dyn, k, &s_next)) {
+    queue_prefetch(dyn, ctr, &s_next);
+    const int64_t gt = base + k;
     const int fi = kSingle ? 0 : field_of(bt, gt);
     const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
     const TileGeom &g = fd.g;
@@ -1309,6 +1351,7 @@ void tiled_scratch_carve(void *base, long long total_tiles, int n_fields,
     return r;
   };
   ts->pool_count = reinterpret_cast<unsigned long long *>(take(256));
+  ts->queue = reinterpret_cast<unsigned int *>(ts->pool_count + 1);
   ts->pool_slot = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
   ts->pool_roots = reinterpret_cast<int2 *>(take((size_t)pool_cap * 8));
   ts->pool_field = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
@@ -1382,17 +1425,27 @@ void make_field_desc(const void *field, int dtype, const int64_t dims[3], long l
   fd->tma = (allow_tma && make_box_map(field, dtype, fd->g, map)) ? 1 : 0;
 }
 
+namespace {
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+}  // namespace
+
 cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus *st,
                               cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(ts.pool_count, 0, sizeof(unsigned long long), s);
+  // the pool counter and the four work-queue counters after it
+  cudaError_t e = cudaMemsetAsync(ts.pool_count, 0, sizeof(unsigned long long) + 4 * sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   static_assert(kHash <= kExt, "the pair set reuses the key area");
   if (b.tiles3 > 0) {
     constexpr int kSmem = 2 * kExt * 4;
     auto kern = b.n_fields == 1 ? k_tile_local<true> : k_tile_local<false>;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    if (e != cudaSuccess) return e;
-    const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * 2);
+    if (!capturing(s)) {  // set by the step-by-step call that precedes every capture
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+      if (e != cudaSuccess) return e;
+    }
+    const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * b.tune.tile_ctas);
     ++tl_launches;
     kern<<<(unsigned)grid, kThreads, kSmem, s>>>(b, ts, st);
     e = cudaGetLastError();
@@ -1401,9 +1454,11 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
   if (b.total_tiles > b.tiles3) {
     constexpr int kSmem2 = (k2Ext + k2PArea) * 4;
     auto kern = b.n_fields == 1 ? k_tile_local2<true> : k_tile_local2<false>;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem2);
-    if (e != cudaSuccess) return e;
-    const int64_t grid = std::min<int64_t>(b.total_tiles - b.tiles3, (int64_t)sms() * 2);
+    if (!capturing(s)) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem2);
+      if (e != cudaSuccess) return e;
+    }
+    const int64_t grid = std::min<int64_t>(b.total_tiles - b.tiles3, (int64_t)sms() * b.tune.tile_ctas);
     ++tl_launches;
     kern<<<(unsigned)grid, kThreads, kSmem2, s>>>(b, ts, st);
     e = cudaGetLastError();
@@ -1421,7 +1476,7 @@ cudaError_t launch_resolve_pairs(const Batch &b, const TiledScratch &ts, const R
   if (stride == 0) stride = 1;
   const unsigned long long work = mode == kChaseProbe ? (npairs + stride - 1) / stride : npairs;
   unsigned long long blocks = (work + 255) / 256;
-  const unsigned long long cap = (unsigned long long)sms() * 16;
+  const unsigned long long cap = (unsigned long long)sms() * b.tune.resolve_blocks;
   if (blocks > cap) blocks = cap;
   ++tl_launches;
   if (b.n_fields == 1)
@@ -1460,33 +1515,33 @@ cudaError_t launch_face_graph_rounds(const Batch &b, int2 *graph, int r0, int r1
 }
 
 cudaError_t launch_field_starts(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
-                                unsigned int m, cudaStream_t s) {
+                                unsigned int m, cudaStream_t s, const unsigned int *m_dev) {
   if (b.key_mode != kKeyBatch || m == 0) return cudaSuccess;
   ++tl_launches;
-  k_field_starts<<<(m + 255) / 256, 256, 0, s>>>(rs.list, m, ts.fstart);
+  k_field_starts<<<(m + 255) / 256, 256, 0, s>>>(rs.list, m, m_dev, ts.fstart);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tile_write(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
-                              cudaStream_t s) {
+                              const DevStatus *st, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (b.tiles3 > 0) {
-    const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * 4);
+    const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * b.tune.write_ctas);
     ++tl_launches;
     if (b.n_fields == 1)
-      k_tile_write<false, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
+      k_tile_write<false, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
     else
-      k_tile_write<false, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
+      k_tile_write<false, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   if (b.total_tiles > b.tiles3) {
-    const int64_t grid = std::min<int64_t>(b.total_tiles - b.tiles3, (int64_t)sms() * 4);
+    const int64_t grid = std::min<int64_t>(b.total_tiles - b.tiles3, (int64_t)sms() * b.tune.write_ctas);
     ++tl_launches;
     if (b.n_fields == 1)
-      k_tile_write<true, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
+      k_tile_write<true, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
     else
-      k_tile_write<true, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs);
+      k_tile_write<true, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
     e = cudaGetLastError();
   }
   return e;

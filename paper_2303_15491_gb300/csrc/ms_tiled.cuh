@@ -74,6 +74,16 @@ enum { kKeyOne = 0,     // one field: (asc << 32) | desc
 constexpr int64_t kBatchMaxN = 1ll << 24;
 constexpr int kBatchMaxFields = 1 << 16;
 
+// Launch choices that change only scheduling, never results (picked by the
+// batch autotuner; the defaults are the single-field choices).
+struct Tuning {
+  int tile_ctas = 2;       // tile kernels: CTAs per SM (2 fit an SM)
+  int write_ctas = 4;      // write kernels: CTAs per SM
+  int resolve_blocks = 16;  // resolve: 256-thread blocks per SM
+  int chase_hops = 16;     // budget of the first exit-chasing pass
+  int dynamic = 1;         // tiles from a work queue (1) or a static stride (0)
+};
+
 struct Batch {
   const FieldDesc *fields;    // n_fields descriptors
   const CUtensorMap *tmaps;   // n_fields tensor maps (64-byte aligned)
@@ -82,10 +92,12 @@ struct Batch {
   long long total_tiles;
   long long tiles3;  // tiles of the 3D fields, which come first; the rest are 2D
   FieldDesc f0;      // n_fields == 1: the descriptor itself, read from kernel parameters
+  Tuning tune;
 };
 
 struct TiledScratch {
   unsigned long long *pool_count;  // pairs reserved by all tiles
+  unsigned int *queue;             // work-queue counters: tile 3D, tile 2D, write 3D, write 2D
   unsigned long long pool_cap;
   int2 *pool_roots;   // per tile pair: (dn-root, up-root), global index | kExitFlag if an exit
   uint32_t *pool_field;  // per tile pair: its field
@@ -111,12 +123,12 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
 // tile pairs (every `stride`-th) for at most kProbeHops face hops and only
 // counts, in st->pending, the sampled pairs that need more: it decides
 // between the two ways below.  kChaseBudget follows every pair's exits for at
-// most kChaseHops hops, inserts the finished pairs and marks the others
+// most Tuning::chase_hops hops, inserts the finished pairs and marks the others
 // pending; kChasePending follows the pending pairs without a budget.
 // kChaseGraph resolves every pair through the jumped face graph
 // (launch_face_graph_*).  clear_table: reset the pair set first.
 enum { kChaseProbe = 0, kChaseBudget = 1, kChasePending = 2, kChaseGraph = 3 };
-constexpr int kChaseHops = 16, kProbeHops = 4;
+constexpr int kProbeHops = 4;
 // The probe samples about kProbeSample pairs, when there are kProbeMinPairs.
 constexpr unsigned long long kProbeSample = 16384, kProbeMinPairs = 65536;
 cudaError_t launch_resolve_pairs(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
@@ -137,8 +149,8 @@ cudaError_t launch_face_graph_build(const Batch &b, const TiledScratch &ts, int2
 cudaError_t launch_face_graph_rounds(const Batch &b, int2 *graph, int r0, int r1, DevStatus *st,
                                      cudaStream_t s);
 cudaError_t launch_field_starts(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
-                                unsigned int m, cudaStream_t s);
+                                unsigned int m, cudaStream_t s, const unsigned int *m_dev = nullptr);
 cudaError_t launch_tile_write(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
-                              cudaStream_t s);
+                              const DevStatus *st, cudaStream_t s);
 
 }  // namespace msseg

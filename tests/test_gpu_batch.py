@@ -131,3 +131,96 @@ def test_batch_long_paths_mixed_shapes(ctx):
     res = run_batch(ctx, fields)
     for i, (f, got) in enumerate(zip(fields, res)):
         assert_same_labels(got, oracle.segment(f), f"long-path batch field {i} {f.shape} {f.dtype}")
+
+
+def _dev_batch(fields):
+    devs = [torch.from_numpy(np.ascontiguousarray(f)).cuda() for f in fields]
+    outs = [[torch.full((f.size,), -5, dtype=torch.int32, device="cuda") for _ in range(3)]
+            for f in fields]
+    return devs, outs
+
+
+def _call(ctx, fields, devs, outs):
+    ks = ms.ms_segment_batch(ctx, devs, [ms.dims_of(f) for f in fields],
+                             [ms.dtype_code(f) for f in fields], [o[0] for o in outs],
+                             [o[1] for o in outs], [o[2] for o in outs])
+    return [(o[0].cpu().numpy(), o[1].cpu().numpy(), o[2].cpu().numpy(), k) for o, k in zip(outs, ks)]
+
+
+def test_repeated_batch_replays_a_graph(ctx):
+    """The same fields again: the second and third calls replay the captured
+    graph (one graph stage per call), with the oracle's results."""
+    fields = small_batch(10, 41) + [sf.smoothed_noise((200, 150, 1), 42, sigma=3.0)[0]]
+    devs, outs = _dev_batch(fields)
+    refs = [oracle.segment(f) for f in fields]
+    ms.ms_profile_enable(ctx, True)
+    for call in range(3):
+        for o in outs:
+            for t in o:
+                t.fill_(-5)
+        torch.cuda.synchronize()
+        got = _call(ctx, fields, devs, outs)
+        for i, (g, r) in enumerate(zip(got, refs)):
+            assert_same_labels(g, r, f"call {call} field {i}")
+    prof = ms.ms_profile_read(ctx)
+    ms.ms_profile_enable(ctx, False)
+    assert prof["calls"] == 3
+    assert prof["stages"]["graph"]["launches"] > 0  # calls 2 and 3 replayed
+
+
+def test_replay_after_contents_change(ctx):
+    """Same pointers, new contents with many more regions than the graph was
+    sized for: the replay detects it and the call runs step by step."""
+    smooth = [sf.broad_gaussians_ramp((64, 48, 40), 50 + i, sigma=30.0) for i in range(4)]
+    noisy = [sf.smoothed_noise((64, 48, 40), 60 + i, sigma=1.0) for i in range(4)]
+    devs, outs = _dev_batch(smooth)
+    for _ in range(2):  # step by step, then a replay
+        _call(ctx, smooth, devs, outs)
+    for d, f in zip(devs, noisy):
+        d.copy_(torch.from_numpy(f))
+    torch.cuda.synchronize()
+    for call in range(2):
+        got = _call(ctx, noisy, devs, outs)
+        for i, (f, g) in enumerate(zip(noisy, got)):
+            assert_same_labels(g, oracle.segment(f), f"changed contents call {call} field {i}")
+    for d, f in zip(devs, smooth):  # and back
+        d.copy_(torch.from_numpy(f))
+    torch.cuda.synchronize()
+    got = _call(ctx, smooth, devs, outs)
+    for i, (f, g) in enumerate(zip(smooth, got)):
+        assert_same_labels(g, oracle.segment(f), f"restored contents field {i}")
+
+
+def test_graphs_off_and_autotune(ctx):
+    fields = small_batch(8, 71)
+    devs, outs = _dev_batch(fields)
+    refs = [oracle.segment(f) for f in fields]
+    ms.ms_batch_graphs(ctx, False)
+    try:
+        for _ in range(2):
+            for i, (g, r) in enumerate(zip(_call(ctx, fields, devs, outs), refs)):
+                assert_same_labels(g, r, f"graphs off field {i}")
+    finally:
+        ms.ms_batch_graphs(ctx, True)
+    t = ms.ms_batch_autotune(ctx, devs, [ms.dims_of(f) for f in fields],
+                             [ms.dtype_code(f) for f in fields], [o[0] for o in outs],
+                             [o[1] for o in outs], [o[2] for o in outs])
+    assert t["tile_ctas"] in (1, 2) and t["write_ctas"] in (2, 4, 8) and t["dynamic"] in (0, 1)
+    assert t["resolve_blocks"] in (8, 16, 32) and t["chase_hops"] in (8, 16, 32)
+    assert 0 < t["best_ms"] <= t["default_ms"]
+    for call in range(3):  # tuned, then captured and replayed with the tuning
+        for i, (g, r) in enumerate(zip(_call(ctx, fields, devs, outs), refs)):
+            assert_same_labels(g, r, f"tuned call {call} field {i}")
+
+
+def test_replay_reports_nan(ctx):
+    fields = small_batch(4, 81)
+    devs, outs = _dev_batch(fields)
+    for _ in range(2):
+        _call(ctx, fields, devs, outs)
+    flat = devs[1].view(-1)
+    flat[flat.numel() // 3] = float("nan")
+    torch.cuda.synchronize()
+    with pytest.raises(ms.MSError) as e:
+        _call(ctx, fields, devs, outs)
+    assert e.value.name == "MS_ERR_NAN_INPUT"
