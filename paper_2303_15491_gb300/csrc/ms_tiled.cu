@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
     }
     // ---- boundary tiles: order keys in place (sentinel 0 outside the
     // field).  All tiles: halo pointers are self-loops.
-    {
+    if (!raw) {
       const int exe = lane == 0 ? kXO - 1 : kXO + kTX;  // lanes 0, 1: the halo columns
       const int64_t xl = x0 + lx, xe = x0 + exe - kXO;
       const bool x_in = xl < g.nx, xe_in = xe >= 0 && xe < g.nx;
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
         const int ey = r % kEY, ez = r / kEY;
         const bool interior = ey >= 1 && ey <= kTY && ez >= 1 && ez <= kTZ;
         const int eb = kEX * r;
-        if (!raw) {
+        {
           const int64_t y = y0 + ey - 1, z = z0 + ez - 1;
           const bool row_in = y >= 0 && y < g.ny && z >= 0 && z < g.nz;
           uint32_t b, be = 0;
@@ -667,15 +667,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
     }
 #pragma unroll
     for (int lz = 0; lz < kTZ; ++lz) P[ext_of(lx, ly, lz)] = w[lz];
-    for (int r = warp; r < kEY * kEZ; r += kThreads / 32) {
-      const int ey = r % kEY, ez = r / kEY;
-      const int eb = kEX * r;
-      if (ey == 0 || ez == 0 || ey == kEY - 1 || ez == kEZ - 1)
-        P[eb + kXO + lx] = (uint32_t)(eb + kXO + lx) * 0x10001u;
+    // the halo points at itself: the 2 kEZ + 2 kTY box rows with ey or ez on
+    // the halo (one warp per row), then the two halo columns of the kTY x kTZ
+    // inner rows (one thread each)
+    for (int j = warp; j < 2 * kEZ + 2 * kTY; j += kThreads / 32) {
+      int ey, ez;
+      if (j < 2 * kEZ) {
+        ey = (j & 1) ? kEY - 1 : 0;
+        ez = j >> 1;
+      } else {
+        const int q = j - 2 * kEZ;
+        ez = (q & 1) ? kEZ - 1 : 0;
+        ey = 1 + (q >> 1);
+      }
+      const int eb = kEX * (ey + kEY * ez);
+      P[eb + kXO + lx] = (uint32_t)(eb + kXO + lx) * 0x10001u;
       if (lane < 2) {
         const int e = eb + (lane == 0 ? kXO - 1 : kXO + kTX);
         P[e] = (uint32_t)e * 0x10001u;
       }
+    }
+    static_assert(kThreads == 2 * kTY * kTZ, "one thread per inner-row halo column");
+    {
+      const int row = threadIdx.x >> 1;
+      const int e = kEX * ((1 + (row % kTY)) + kEY * (1 + row / kTY)) +
+                    ((threadIdx.x & 1) ? kXO + kTX : kXO - 1);
+      P[e] = (uint32_t)e * 0x10001u;
     }
     __syncthreads();
 
@@ -685,19 +702,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
     // them) and jumps them in place until a pass changes nothing in its
     // warp; reads of other vertices' pointers may see them before or after
     // their own jumps, and either lies on the same path.
-    for (int it = 0; it < kExt; ++it) {
-      bool changed = false;
+    // An entry that a pass leaves unchanged points at two roots (only roots
+    // point at themselves) and is final; a warp skips the entries that are
+    // final in all its lanes.
+    {
+      uint32_t open = 0xffffu;
+      for (int it = 0; it < kExt; ++it) {
+        uint32_t still = 0;
 #pragma unroll
-      for (int lz = 0; lz < kTZ; ++lz) {
-        const uint32_t gu = P[w[lz] & 0xffffu], gd = P[w[lz] >> 16];
-        const uint32_t nw = __byte_perm(gu, gd, 0x7610);  // up of gu, dn of gd
-        if (nw != w[lz]) {
-          w[lz] = nw;
-          P[ext_of(lx, ly, lz)] = nw;
-          changed = true;
+        for (int lz = 0; lz < kTZ; ++lz) {
+          if (__any_sync(0xffffffffu, (open >> lz) & 1u)) {
+            const uint32_t gu = P[w[lz] & 0xffffu], gd = P[w[lz] >> 16];
+            const uint32_t nw = __byte_perm(gu, gd, 0x7610);  // up of gu, dn of gd
+            if (nw != w[lz]) {
+              w[lz] = nw;
+              P[ext_of(lx, ly, lz)] = nw;
+              still |= 1u << lz;
+            }
+          }
         }
+        open = still;
+        if (!__any_sync(0xffffffffu, still)) break;
       }
-      if (!__any_sync(0xffffffffu, changed)) break;
     }
     __syncthreads();
 
