@@ -69,6 +69,8 @@ def lib():
                                             i64p, i32p, i32p]
             L.ms_oracle_segment.restype = ctypes.c_int
             L.ms_oracle_link_stats.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i32p, i64p]
+            L.ms_oracle_simplex_code.argtypes = [ctypes.c_int, i32p, ctypes.POINTER(ctypes.c_int)]
+            L.ms_oracle_simplex_index.argtypes = [i32p, i64p, ctypes.c_void_p, i64p, i64p]
             L.ms_oracle_link_stats.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -188,3 +190,39 @@ def link_stats(field: np.ndarray, with_links: bool = False):
     _check(lib().ms_oracle_link_stats(f.ctypes.data, dt, dims, _ptr32(out),
                                       links.ctypes.data_as(i64p) if with_links else None))
     return (out, links) if with_links else out
+
+
+def simplex_code(labels):
+    """(code, element count) of one triangle (3 labels) or tetrahedron (4),
+    the vertices in chain order (Sec. 4.3, Fig. 4, Tab. 1, Figs. 5-6)."""
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    cnt = ctypes.c_int(0)
+    code = lib().ms_oracle_simplex_code(int(lab.size), _ptr32(lab), ctypes.byref(cnt))
+    if code < 0:
+        raise ValueError("a simplex has 3 or 4 vertices")
+    return int(code), int(cnt.value)
+
+
+def simplex_cells(dims):
+    nx, ny, nz = (int(d) for d in dims)
+    if nz == 1:
+        return max(nx - 1, 0) * max(ny - 1, 0), 2
+    return max(nx - 1, 0) * max(ny - 1, 0) * max(nz - 1, 0), 6
+
+
+def simplex_index(labels: np.ndarray, dims):
+    """Index pass of the marching triangles / tetrahedra over a label grid:
+    {'codes': uint8 per simplex, 'cell_offsets': int64 per cell, 'total'}."""
+    lab = np.ascontiguousarray(labels, dtype=np.int32).reshape(-1)
+    nx, ny, nz = (int(d) for d in dims)
+    if lab.size != nx * ny * nz:
+        raise ValueError("labels do not match dims")
+    cells, per = simplex_cells(dims)
+    codes = np.zeros(cells * per, dtype=np.uint8)
+    offs = np.zeros(max(cells, 1), dtype=np.int64)
+    total = ctypes.c_int64(0)
+    d = (ctypes.c_int64 * 3)(nx, ny, nz)
+    _check(lib().ms_oracle_simplex_index(_ptr32(lab), d, codes.ctypes.data,
+                                         offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         ctypes.byref(total)))
+    return {"codes": codes, "cell_offsets": offs[:cells], "total": int(total.value)}

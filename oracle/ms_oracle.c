@@ -461,3 +461,138 @@ int ms_oracle_link_stats(const void *field, int dtype, const int64_t dims[3], in
   }
   return OR_OK;
 }
+
+/* ---- the index pass of the multi-label marching triangles / tetrahedra --
+ *
+ * Sec. 4.3 (region-separating geometry).  Every simplex of the triangulation
+ * whose vertices carry more than one label is split; the pass that precedes
+ * the geometry computes, per simplex, a binary code of its label
+ * configuration and the number of separating elements it produces, and the
+ * exclusive prefix sum of those numbers (where each cell's output starts).
+ *
+ * Simplices: the Freudenthal cells are cut along the (0,..,0)->(1,..,1)
+ * diagonal into one simplex per order in which the axes are stepped.
+ *   2D: cell (x, y), x < nx-1, y < ny-1, index c = x + (nx-1) y, triangles
+ *       t = 2c + p, p = 0: x then y, p = 1: y then x.
+ *   3D: cell (x, y, z), index c = x + (nx-1)(y + (ny-1) z), tetrahedra
+ *       t = 6c + p with axis orders p = 0: xyz, 1: xzy, 2: yxz, 3: yzx,
+ *       4: zxy, 5: zyx.
+ * The vertices a, b, c (, d) of a simplex are its chain in stepping order,
+ * which is also increasing vertex index.
+ *
+ * Code (Sec. 4.3, Fig. 4, Tab. 1): the first vertex gets local label 0; each
+ * later vertex gets the local label of the first earlier vertex with the same
+ * label, or its own position (1, 2, 3) if none has it.  Triangle code =
+ * b << 2 | c (3 bits); tetrahedron code = b << 4 | c << 2 | d (5 bits).
+ * Separating elements per code (Figs. 5 and 6): a triangle with two labels is
+ * cut by one segment, with three by three segments meeting at its centre; a
+ * tetrahedron whose labels split 1 + 3 is cut by one triangle, 2 + 2 by two,
+ * with three labels by five and with four labels by twelve.
+ */
+
+static int tri_code(int32_t la, int32_t lb, int32_t lc) {
+  const int b = lb == la ? 0 : 1;
+  const int c = lc == la ? 0 : (lc == lb ? b : 2);
+  return (b << 2) | c;
+}
+
+static int tri_count(int code) {
+  int32_t l[3] = {0, code >> 2, code & 3};
+  int distinct = 1;
+  if (l[1] != l[0]) ++distinct;
+  if (l[2] != l[0] && l[2] != l[1]) ++distinct;
+  return distinct == 1 ? 0 : distinct == 2 ? 1 : 3;
+}
+
+static int tet_code(const int32_t *lab) {
+  int loc[4];
+  for (int k = 0; k < 4; ++k) {
+    loc[k] = k;
+    for (int j = 0; j < k; ++j)
+      if (lab[j] == lab[k]) {
+        loc[k] = loc[j];
+        break;
+      }
+  }
+  return (loc[1] << 4) | (loc[2] << 2) | loc[3];
+}
+
+static int tet_count(int code) {
+  const int loc[4] = {0, code >> 4, (code >> 2) & 3, code & 3};
+  int size[4] = {0, 0, 0, 0};
+  for (int k = 0; k < 4; ++k) size[loc[k]]++;
+  int distinct = 0, largest = 0;
+  for (int k = 0; k < 4; ++k)
+    if (size[k]) {
+      ++distinct;
+      if (size[k] > largest) largest = size[k];
+    }
+  if (distinct == 1) return 0;
+  if (distinct == 2) return largest == 3 ? 1 : 2;
+  return distinct == 3 ? 5 : 12;
+}
+
+/* Code and element count of one label configuration (for the pins). */
+int ms_oracle_simplex_code(int nverts, const int32_t *labels, int *count) {
+  if (nverts == 3) {
+    const int code = tri_code(labels[0], labels[1], labels[2]);
+    *count = tri_count(code);
+    return code;
+  }
+  if (nverts == 4) {
+    const int code = tet_code(labels);
+    *count = tet_count(code);
+    return code;
+  }
+  return -1;
+}
+
+/* codes: one byte per simplex; cell_offsets: per cell, the exclusive prefix
+ * sum over cells of the cell's element count (sum over its simplices);
+ * *total: the sum over all cells.  Grids with a dimension of extent 1 other
+ * than nz (2D is nz == 1) have no cells. */
+int ms_oracle_simplex_index(const int32_t *labels, const int64_t dims[3], uint8_t *codes,
+                            int64_t *cell_offsets, int64_t *total) {
+  const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+  if (nx < 1 || ny < 1 || nz < 1) return OR_ERR_ARG;
+  const int two_d = nz == 1;
+  const int64_t cx = nx - 1, cy = ny - 1, cz = two_d ? 1 : nz - 1;
+  int64_t run = 0;
+  if (cx > 0 && cy > 0 && cz > 0) {
+    for (int64_t z = 0; z < cz; ++z)
+      for (int64_t y = 0; y < cy; ++y)
+        for (int64_t x = 0; x < cx; ++x) {
+          const int64_t c = x + cx * (y + cy * z);
+          const int64_t v0 = x + nx * (y + ny * z);
+          int cell_count = 0;
+          if (two_d) {
+            const int64_t step[2][2] = {{1, nx}, {nx, 1}};
+            for (int p = 0; p < 2; ++p) {
+              const int64_t va = v0, vb = va + step[p][0], vc = vb + step[p][1];
+              const int code = tri_code(labels[va], labels[vb], labels[vc]);
+              codes[2 * c + p] = (uint8_t)code;
+              cell_count += tri_count(code);
+            }
+          } else {
+            const int64_t ax[3] = {1, nx, nx * ny};
+            const int order[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+            for (int p = 0; p < 6; ++p) {
+              int32_t lab[4];
+              int64_t v = v0;
+              lab[0] = labels[v];
+              for (int k = 0; k < 3; ++k) {
+                v += ax[order[p][k]];
+                lab[k + 1] = labels[v];
+              }
+              const int code = tet_code(lab);
+              codes[6 * c + p] = (uint8_t)code;
+              cell_count += tet_count(code);
+            }
+          }
+          cell_offsets[c] = run;
+          run += cell_count;
+        }
+  }
+  *total = run;
+  return OR_OK;
+}
