@@ -188,6 +188,34 @@ ms_status ms_batch_autotune(ms_ctx *ctx, int n_fields, const void *const *fields
  * repeated batches on this context. */
 ms_status ms_batch_graphs(ms_ctx *ctx, int on);
 
+/* ---- after the segmentation: the marching triangles / tetrahedra index pass - */
+
+/* Sec. 4.3 (multi-label marching triangles and tetrahedra), the pass before
+ * the separating geometry: for every simplex of the triangulation the binary
+ * code of its label configuration (Fig. 4, Tab. 1) and, per cell, where the
+ * cell's separating elements start in the output.
+ *   Cells: (x, y[, z]) with x < nx-1, y < ny-1 (, z < nz-1), linear index
+ *   c = x + (nx-1)(y + (ny-1) z); a 2D grid (nz = 1) has (nx-1)(ny-1) cells.
+ *   Simplices: each cell is cut along its (0,..,0)->(1,..,1) diagonal into
+ *   one simplex per axis order -- 2D: 2c (x then y), 2c+1 (y then x); 3D:
+ *   6c + p with p = 0..5 for xyz, xzy, yxz, yzx, zxy, zyx.  The vertices
+ *   a, b, c(, d) of a simplex are its corners in stepping order.
+ *   Code: a gets local label 0; each later vertex takes the local label of
+ *   the first earlier vertex with an equal label, else its own position;
+ *   triangle code = b << 2 | c, tetrahedron code = b << 4 | c << 2 | d.
+ *   Elements (Figs. 5, 6): a triangle with 2 labels is cut by 1 segment, with
+ *   3 by 3; a tetrahedron whose labels split 3+1 by 1 triangle, 2+2 by 2,
+ *   2+1+1 by 5, 1+1+1+1 by 12.
+ * labels: int32[nx*ny*nz] (any segmentation: ms, asc or desc ids) on the
+ * device; codes: uint8[cells * (2 or 6)] on the device, 16-byte aligned;
+ * cell_offsets: int64[cells] on the device, the exclusive prefix sum of the
+ * cells' element counts; *total (host, may be NULL): the element total.
+ * Grids without cells (an extent of 1 other than nz) give *total = 0 and
+ * touch no output.  Errors: MS_ERR_INVALID_ARG, MS_ERR_TOO_LARGE,
+ * MS_ERR_OUT_OF_MEMORY, MS_ERR_CUDA. */
+ms_status ms_simplex_index(ms_ctx *ctx, const int32_t *labels, const int64_t dims[3],
+                           uint8_t *codes, int64_t *cell_offsets, int64_t *total);
+
 /* ---- serving ---------------------------------------------------------------- */
 
 /* A request loop for segmentations of mixed sizes.  The server owns n_slots

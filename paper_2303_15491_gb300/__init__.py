@@ -26,7 +26,7 @@ __all__ = [
     "ms_profile_read", "ms_profile_stage_name", "STAGES", "ms_segment_staged",
     "ms_pair_rank_noalloc", "MS_NOALLOC_MAX_N", "ms_segment_batch", "ms_server_create",
     "ms_server_submit", "ms_server_wait", "ms_server_stats", "ms_server_destroy",
-    "ms_batch_autotune", "ms_batch_graphs",
+    "ms_batch_autotune", "ms_batch_graphs", "ms_simplex_index", "simplex_cells",
 ]
 
 MS_F32, MS_F16 = 0, 1
@@ -40,7 +40,7 @@ EXPORTED_SYMBOLS = [
     "ms_profile_enable", "ms_profile_read", "ms_profile_stage_name", "ms_segment_staged",
     "ms_pair_rank_noalloc", "ms_segment_batch", "ms_server_create", "ms_server_submit",
     "ms_server_wait", "ms_server_stats", "ms_server_destroy", "ms_batch_autotune",
-    "ms_batch_graphs",
+    "ms_batch_graphs", "ms_simplex_index",
 ]
 MS_NOALLOC_MAX_N = 262144
 
@@ -98,6 +98,7 @@ def load(build: bool = True) -> ctypes.CDLL:
             L.ms_batch_autotune.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                             ctypes.POINTER(_Tuning)]
             L.ms_batch_graphs.argtypes = [c_vp, ctypes.c_int]
+            L.ms_simplex_index.argtypes = [c_vp, c_vp, c_i64p, c_vp, c_vp, c_i64p]
             L.ms_server_create.argtypes = [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_size_t,
                                            ctypes.c_int]
             L.ms_server_submit.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp,
@@ -220,6 +221,23 @@ def ms_batch_autotune(ctx, fields, dims_list, dtypes, ascs, descs, mss) -> dict:
                                     ctypes.cast(dts, c_vp), ptrs(ascs), ptrs(descs), ptrs(mss),
                                     ctypes.byref(t)), "ms_batch_autotune")
     return {f: getattr(t, f) for f, _ in _Tuning._fields_}
+
+
+def ms_simplex_index(ctx, labels, dims, codes, cell_offsets) -> int:
+    """Index pass of the marching triangles / tetrahedra (see ms.h); returns
+    the total number of separating elements."""
+    t = ctypes.c_int64(0)
+    _check(load().ms_simplex_index(ctx, _ptr(labels), _dims(dims), _ptr(codes), _ptr(cell_offsets),
+                                   ctypes.byref(t)), "ms_simplex_index")
+    return int(t.value)
+
+
+def simplex_cells(dims):
+    """(cells, simplices per cell) of a grid."""
+    nx, ny, nz = (int(d) for d in dims)
+    if nz == 1:
+        return max(nx - 1, 0) * max(ny - 1, 0), 2
+    return max(nx - 1, 0) * max(ny - 1, 0) * max(nz - 1, 0), 6
 
 
 def ms_batch_graphs(ctx, on: bool = True) -> None:

@@ -49,6 +49,8 @@ struct ms_ctx {
   size_t tscratch_bytes = 0;
   void *graph = nullptr;     // the face graph, built only for long exit chains
   size_t graph_bytes = 0;
+  void *sxscratch = nullptr;  // index-pass block totals and bases
+  size_t sxscratch_bytes = 0;
   unsigned long long *hcount = nullptr;  // pinned copy of the tiled pair count
   unsigned long long pool_hint = 0;      // pair-pool capacity that sufficed last time
   void *batch_dev = nullptr;             // field descriptors + tensor maps on the device
@@ -856,6 +858,7 @@ ms_status ms_destroy(ms_ctx *c) {
   if (c->io) cudaFree(c->io);
   if (c->tscratch) cudaFree(c->tscratch);
   if (c->graph) cudaFree(c->graph);
+  if (c->sxscratch) cudaFree(c->sxscratch);
   if (c->batch_dev) cudaFree(c->batch_dev);
   if (c->batch_host) cudaFreeHost(c->batch_host);
   if (c->hcount) cudaFreeHost(c->hcount);
@@ -950,6 +953,41 @@ ms_status ms_segment_batch(ms_ctx *c, int n_fields, const void *const *fields,
     finish_profile(c, l0);
   }
   return s;
+}
+
+ms_status ms_simplex_index(ms_ctx *c, const int32_t *labels, const int64_t dims[3],
+                           uint8_t *codes, int64_t *cell_offsets, int64_t *total) {
+  if (!c || !labels) return MS_ERR_INVALID_ARG;
+  int64_t n = 0;
+  ms_status s = check_dims(dims, &n);
+  if (s != MS_OK) return s;
+  DeviceGuard g(c->device);
+  const bool flat = dims[2] == 1;
+  const int64_t cz = flat ? 1 : dims[2] - 1;
+  const int64_t cells = (dims[0] > 1 && dims[1] > 1 && cz > 0) ? (dims[0] - 1) * (dims[1] - 1) * cz : 0;
+  if (cells == 0) {
+    if (total) *total = 0;
+    return MS_OK;
+  }
+  if (!is_device_pointer(labels) || !is_device_pointer(codes) || !is_device_pointer(cell_offsets))
+    return MS_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(codes) & 15) || (reinterpret_cast<uintptr_t>(cell_offsets) & 7))
+    return MS_ERR_INVALID_ARG;
+  s = ensure_buffer(c, &c->sxscratch, &c->sxscratch_bytes, simplex_scratch_bytes(cells));
+  if (s != MS_OK) return s;
+  const long long l0 = tl_launches;
+  unsigned long long *tot_dev = nullptr;
+  int64_t nc = 0;
+  StageTimer t0(c, MS_STAGE_TILE_LOCAL);
+  MS_TRY(launch_simplex_index(labels, dims, codes, cell_offsets, c->sxscratch, &tot_dev, &nc,
+                              c->stream));
+  t0.stop();
+  MS_TRY(cudaMemcpyAsync(c->hcount, tot_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                         c->stream));
+  MS_TRY(cudaStreamSynchronize(c->stream));
+  if (total) *total = (int64_t)*c->hcount;
+  finish_profile(c, l0);
+  return MS_OK;
 }
 
 ms_status ms_batch_graphs(ms_ctx *c, int on) {

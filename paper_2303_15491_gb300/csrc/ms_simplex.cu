@@ -1,0 +1,250 @@
+// Index pass of the multi-label marching triangles / tetrahedra (Sec. 4.3):
+// per simplex of the Freudenthal triangulation, the binary code of its label
+// configuration (Fig. 4, Tab. 1); per cell, where its separating elements
+// start in the output (exclusive prefix sum of the element counts drawn in
+// Figs. 5 and 6).
+//
+// Simplices: cell (x, y[, z]) is cut along its (0,..,0)->(1,..,1) diagonal
+// into one simplex per order in which the axes are stepped (2D: x-then-y,
+// y-then-x; 3D: xyz, xzy, yxz, yzx, zxy, zyx), numbered 2c + p / 6c + p with
+// c the cell's linear index (x fastest); a simplex's vertices in stepping
+// order are a, b, c(, d).
+//
+// Three launches: codes and per-block element totals (one thread per cell,
+// the block's codes staged in shared memory and stored as 16-byte vectors),
+// an exclusive scan of the block totals, and the per-cell offsets (counts
+// re-derived from the codes, block scan, plus the block's base).
+#include <stdint.h>
+
+#include "fastdiv.h"
+#include "ms_internal.cuh"
+
+namespace msseg {
+namespace {
+
+constexpr int kCellThreads = 256;
+
+struct SimplexGeom {
+  int64_t nx, ny;        // vertices per row / per plane row count
+  int64_t cx, cy;        // cells along x and y
+  int64_t ncells;
+  int per;               // simplices per cell: 2 (2D) or 6 (3D)
+  FastDivU32 div_cx, div_cy;
+};
+
+// Local label of position k given its equality to the earlier positions
+// (Sec. 4.3: the first earlier vertex with the same label lends its local
+// label, else the position itself).
+__device__ __forceinline__ int tri_code(int32_t a, int32_t b, int32_t c) {
+  const int lb = b != a;
+  const int lc = c == a ? 0 : (c == b ? 1 : 2);
+  return (lb << 2) | lc;
+}
+
+__device__ __forceinline__ int tet_code(int32_t a, int32_t b, int32_t c, int32_t d) {
+  const int lb = b == a ? 0 : 1;
+  const int lc = c == a ? 0 : (c == b ? lb : 2);
+  const int ld = d == a ? 0 : (d == b ? lb : (d == c ? lc : 3));
+  return (lb << 4) | (lc << 2) | ld;
+}
+
+// Separating elements of a configuration (Figs. 5, 6): by the sizes of its
+// label classes -- triangles: {3} 0, {2,1} 1, {1,1,1} 3 segments;
+// tetrahedra: {4} 0, {3,1} 1, {2,2} 2, {2,1,1} 5, {1,1,1,1} 12 triangles.
+__device__ __forceinline__ int tri_elements(int code) {
+  // codes: 0 = {3}; 2, 4, 5 = {2,1}; 6 = {1,1,1}
+  return code == 0 ? 0 : (code == 6 ? 3 : 1);
+}
+
+__device__ __forceinline__ int tet_elements(int code) {
+  const int b = code >> 4, c = (code >> 2) & 3, d = code & 3;
+  // class sizes of the local labels 0..3
+  const int n0 = 1 + (b == 0) + (c == 0) + (d == 0);
+  const int n1 = (b == 1) + (c == 1) + (d == 1);
+  const int n2 = (c == 2) + (d == 2);
+  const int n3 = d == 3;
+  const int classes = 1 + (n1 > 0) + (n2 > 0) + n3;
+  if (classes == 1) return 0;
+  if (classes == 2) return (n0 == 2 || n1 == 2 || n2 == 2) ? 2 : 1;
+  return classes == 3 ? 5 : 12;
+}
+
+__device__ __forceinline__ void cell_xyz(const SimplexGeom &g, uint32_t c, uint32_t *x, uint32_t *y,
+                                         uint32_t *z) {
+  uint32_t q;
+  g.div_cx.divmod(c, &q, x);
+  g.div_cy.divmod(q, z, y);
+}
+
+// Block-wide exclusive sum of one value per thread; also the block total.
+__device__ __forceinline__ unsigned int block_excl(unsigned int v, unsigned int *total,
+                                                   unsigned int *sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  unsigned int base = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kCellThreads / 32; ++w) {
+    const unsigned int s = sh[w];
+    if (w < warp) base += s;
+    tot += s;
+  }
+  *total = tot;
+  return base + incl - v;
+}
+
+__global__ void __launch_bounds__(kCellThreads) k_simplex_codes(const int32_t *__restrict__ lab,
+                                                                SimplexGeom g,
+                                                                uint8_t *__restrict__ codes,
+                                                                unsigned int *__restrict__ block_tot) {
+  __shared__ __align__(16) uint8_t sc[kCellThreads * 6];
+  __shared__ unsigned int sh[kCellThreads / 32];
+  const int64_t c0 = (int64_t)blockIdx.x * kCellThreads;
+  const int64_t c = c0 + threadIdx.x;
+  unsigned int count = 0;
+  if (c < g.ncells) {
+    uint32_t x, y, z;
+    cell_xyz(g, (uint32_t)c, &x, &y, &z);
+    const int64_t v = (int64_t)x + g.nx * ((int64_t)y + g.ny * z);
+    const int64_t sy = g.nx, sz = g.nx * g.ny;
+    if (g.per == 2) {
+      const int32_t l00 = __ldg(lab + v), l10 = __ldg(lab + v + 1), l01 = __ldg(lab + v + sy),
+                    l11 = __ldg(lab + v + sy + 1);
+      const int k0 = tri_code(l00, l10, l11), k1 = tri_code(l00, l01, l11);
+      sc[threadIdx.x * 2] = (uint8_t)k0;
+      sc[threadIdx.x * 2 + 1] = (uint8_t)k1;
+      count = tri_elements(k0) + tri_elements(k1);
+    } else {
+      // corners by offset bits (x = 1, y = 2, z = 4)
+      int32_t l[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        l[k] = __ldg(lab + v + ((k & 1) ? 1 : 0) + ((k & 2) ? sy : 0) + ((k & 4) ? sz : 0));
+      // axis orders xyz, xzy, yxz, yzx, zxy, zyx: b and c corners of each chain
+      const int kb[6] = {1, 1, 2, 2, 4, 4};
+      const int kc[6] = {3, 5, 3, 6, 5, 6};
+#pragma unroll
+      for (int p = 0; p < 6; ++p) {
+        const int code = tet_code(l[0], l[kb[p]], l[kc[p]], l[7]);
+        sc[threadIdx.x * 6 + p] = (uint8_t)code;
+        count += tet_elements(code);
+      }
+    }
+  }
+  __syncthreads();
+  // the block's codes are one contiguous byte range
+  const int64_t nvalid = min((int64_t)kCellThreads, g.ncells - c0);
+  const int64_t bytes = nvalid * g.per;
+  uint8_t *dst = codes + c0 * g.per;  // 16-byte aligned: c0 * per is a multiple of 512
+  const int vec = (int)(bytes / 16);
+  for (int i = threadIdx.x; i < vec; i += kCellThreads)
+    reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(sc)[i];
+  for (int64_t i = (int64_t)vec * 16 + threadIdx.x; i < bytes; i += kCellThreads) dst[i] = sc[i];
+  unsigned int tot = 0;
+  block_excl(count, &tot, sh);
+  if (threadIdx.x == 0) block_tot[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the per-block totals into 64-bit bases, by one block:
+// thread t sums its contiguous chunk, the chunk sums are scanned, and the
+// chunk is walked again writing bases.  *total receives the sum.
+__global__ void __launch_bounds__(1024) k_scan_blocks(const unsigned int *__restrict__ tot,
+                                                      int64_t nblocks,
+                                                      unsigned long long *__restrict__ base,
+                                                      unsigned long long *__restrict__ total) {
+  __shared__ unsigned long long sh[1024];
+  const int64_t chunk = (nblocks + 1023) / 1024;
+  const int64_t lo = (int64_t)threadIdx.x * chunk, hi = min(nblocks, lo + chunk);
+  unsigned long long s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += tot[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const unsigned long long t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0ull;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  unsigned long long run = sh[threadIdx.x] - s;
+  for (int64_t i = lo; i < hi; ++i) {
+    base[i] = run;
+    run += tot[i];
+  }
+  if (threadIdx.x == 1023) *total = sh[1023];
+}
+
+__global__ void __launch_bounds__(kCellThreads) k_simplex_offsets(const uint8_t *__restrict__ codes,
+                                                                  SimplexGeom g,
+                                                                  const unsigned long long *__restrict__ base,
+                                                                  int64_t *__restrict__ offsets) {
+  __shared__ unsigned int sh[kCellThreads / 32];
+  const int64_t c = (int64_t)blockIdx.x * kCellThreads + threadIdx.x;
+  unsigned int count = 0;
+  if (c < g.ncells) {
+    if (g.per == 2) {
+      const uint16_t two = __ldg(reinterpret_cast<const uint16_t *>(codes) + c);
+      count = tri_elements(two & 0xff) + tri_elements(two >> 8);
+    } else {
+      const uint16_t *p = reinterpret_cast<const uint16_t *>(codes + 6 * c);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const uint16_t two = __ldg(p + k);
+        count += tet_elements(two & 0xff) + tet_elements(two >> 8);
+      }
+    }
+  }
+  unsigned int tot = 0;
+  const unsigned int ex = block_excl(count, &tot, sh);
+  if (c < g.ncells) offsets[c] = (int64_t)(base[blockIdx.x] + ex);
+}
+
+}  // namespace
+
+size_t simplex_scratch_bytes(int64_t ncells) {
+  const int64_t nb = (ncells + kCellThreads - 1) / kCellThreads;
+  return 256 + (size_t)nb * 4 + (size_t)nb * 8 + 256;
+}
+
+// labels: int32[N]; codes: uint8[ncells * per]; offsets: int64[ncells];
+// scratch: simplex_scratch_bytes(ncells) bytes; *total_dev: the sum.
+cudaError_t launch_simplex_index(const int32_t *labels, const int64_t dims[3], uint8_t *codes,
+                                 int64_t *offsets, void *scratch, unsigned long long **total_dev,
+                                 int64_t *ncells_out, cudaStream_t s) {
+  SimplexGeom g;
+  g.nx = dims[0];
+  g.ny = dims[1];
+  const bool flat = dims[2] == 1;
+  g.cx = dims[0] - 1;
+  g.cy = dims[1] - 1;
+  const int64_t cz = flat ? 1 : dims[2] - 1;
+  g.ncells = (g.cx > 0 && g.cy > 0 && cz > 0) ? g.cx * g.cy * cz : 0;
+  g.per = flat ? 2 : 6;
+  *ncells_out = g.ncells;
+  unsigned long long *total = reinterpret_cast<unsigned long long *>(scratch);
+  *total_dev = total;
+  cudaError_t e = cudaMemsetAsync(total, 0, 8, s);
+  if (e != cudaSuccess || g.ncells == 0) return e;
+  g.div_cx = FastDivU32((uint32_t)g.cx);
+  g.div_cy = FastDivU32((uint32_t)g.cy);
+  const int64_t nb = (g.ncells + kCellThreads - 1) / kCellThreads;
+  unsigned int *btot = reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + 256);
+  unsigned long long *bbase = reinterpret_cast<unsigned long long *>(
+      static_cast<char *>(scratch) + 256 + (((size_t)nb * 4 + 255) & ~(size_t)255));
+  ++tl_launches;
+  k_simplex_codes<<<(unsigned)nb, kCellThreads, 0, s>>>(labels, g, codes, btot);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ++tl_launches;
+  k_scan_blocks<<<1, 1024, 0, s>>>(btot, nb, bbase, total);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ++tl_launches;
+  k_simplex_offsets<<<(unsigned)nb, kCellThreads, 0, s>>>(codes, g, bbase, offsets);
+  return cudaGetLastError();
+}
+
+}  // namespace msseg

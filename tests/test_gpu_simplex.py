@@ -1,0 +1,128 @@
+"""The marching triangles / tetrahedra index pass on the GPU (ms_simplex_index)
+against the oracle: every code and every cell offset, on label fields from
+real segmentations, random labels with many ties, and edge shapes."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2303_15491_gb300 as ms
+import synthfields as sf
+from gpu_util import gpu_segment
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    h = ms.ms_create(0)
+    yield h
+    ms.ms_destroy(h)
+
+
+def gpu_index(ctx, labels, dims):
+    cells, per = ms.simplex_cells(dims)
+    lab = torch.from_numpy(np.ascontiguousarray(labels, dtype=np.int32).reshape(-1)).cuda()
+    codes = torch.full((max(cells * per, 1),), 255, dtype=torch.uint8, device="cuda")
+    offs = torch.full((max(cells, 1),), -1, dtype=torch.int64, device="cuda")
+    total = ms.ms_simplex_index(ctx, lab, dims, codes, offs)
+    return codes[:cells * per].cpu().numpy(), offs[:cells].cpu().numpy(), total
+
+
+def check(ctx, labels, dims, what):
+    ref = oracle.simplex_index(labels, dims)
+    codes, offs, total = gpu_index(ctx, labels, dims)
+    assert total == ref["total"], f"{what}: total {total} != {ref['total']}"
+    for name, a, b in (("codes", codes, ref["codes"]), ("offsets", offs, ref["cell_offsets"])):
+        if not np.array_equal(a, b):
+            bad = np.flatnonzero(a != b)
+            raise AssertionError(f"{what}: {name} differ at {bad.size}, first {bad[:6]}: "
+                                 f"{a[bad[:6]]} vs {b[bad[:6]]}")
+
+
+@pytest.mark.parametrize("dims", [(40, 36, 30), (33, 17, 9), (2, 2, 2), (300, 200, 1), (2, 2, 1),
+                                  (257, 3, 1), (5, 70, 41)])
+def test_on_segmentation_labels(ctx, dims):
+    f = sf.smoothed_noise(dims, 17, sigma=2.0)
+    if dims[2] == 1:
+        f = f[0]
+    asc, desc, m, _ = gpu_segment(ctx, f)
+    for name, lab in (("ms", m), ("asc", asc), ("desc", desc)):
+        check(ctx, lab, dims, f"{dims} {name}")
+
+
+@pytest.mark.parametrize("dims", [(31, 29, 27), (129, 65, 1), (64, 64, 64)])
+@pytest.mark.parametrize("levels", [2, 4, 1 << 30])
+def test_random_labels(ctx, dims, levels):
+    g = np.random.default_rng(levels % 1000 + dims[0])
+    lab = g.integers(0, levels, size=int(np.prod(dims))).astype(np.int32)
+    check(ctx, lab, dims, f"{dims} levels {levels}")
+
+
+@pytest.mark.parametrize("dims", [(1, 5, 5), (5, 1, 5), (7, 1, 1), (1, 1, 1), (6, 6, 2)])
+def test_degenerate_shapes(ctx, dims):
+    lab = np.arange(int(np.prod(dims)), dtype=np.int32) % 3
+    check(ctx, lab, dims, f"degenerate {dims}")
+
+
+def test_constant_and_distinct_totals(ctx):
+    dims = (50, 40, 30)
+    n = 50 * 40 * 30
+    assert gpu_index(ctx, np.zeros(n, np.int32), dims)[2] == 0
+    cells = 49 * 39 * 29
+    assert gpu_index(ctx, np.arange(n, dtype=np.int32), dims)[2] == cells * 6 * 12
+
+
+def test_errors(ctx):
+    lab = torch.zeros(27, dtype=torch.int32, device="cuda")
+    codes = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    offs = torch.zeros(8, dtype=torch.int64, device="cuda")
+    with pytest.raises(ms.MSError) as e:  # codes not 16-byte aligned
+        ms.ms_simplex_index(ctx, lab, (3, 3, 3), codes[1:], offs)
+    assert e.value.name == "MS_ERR_INVALID_ARG"
+    with pytest.raises(ms.MSError) as e:  # host labels
+        ms.ms_simplex_index(ctx, np.zeros(27, np.int32), (3, 3, 3), codes, offs)
+    assert e.value.name == "MS_ERR_INVALID_ARG"
+    with pytest.raises(ms.MSError) as e:
+        ms.ms_simplex_index(ctx, lab, (0, 3, 3), codes, offs)
+    assert e.value.name == "MS_ERR_INVALID_ARG"
+
+
+@pytest.mark.slow
+def test_full_size_512(ctx):
+    """512^3 MS labels of the smoothed-noise workload: the codes of sampled
+    cells against the oracle (from their corner labels), and every offset
+    against the prefix-sum property with element counts per code taken from
+    the drawings of Figs. 5-6."""
+    import os
+    from test_gpu_fullsize import cached
+    f = cached("noise512", lambda: sf.smoothed_noise((512, 512, 512), 0, sigma=4.0, radius=16))
+    dims = (512, 512, 512)
+    asc, desc, m, k = ms.segment(ctx, torch.from_numpy(f).cuda())
+    del asc, desc
+    cells, per = ms.simplex_cells(dims)
+    codes = torch.empty(cells * per, dtype=torch.uint8, device="cuda")
+    offs = torch.empty(cells, dtype=torch.int64, device="cuda")
+    total = ms.ms_simplex_index(ctx, m, dims, codes, offs)
+    # sampled cells: codes from the oracle on the cell's own 2x2x2 corners
+    g = np.random.default_rng(5)
+    lab = m.view(512, 512, 512)
+    for c in g.integers(0, cells, size=3000):
+        x, y, z = c % 511, (c // 511) % 511, c // (511 * 511)
+        corner = lab[z:z + 2, y:y + 2, x:x + 2].cpu().numpy()
+        ref = oracle.simplex_index(corner, (2, 2, 2))
+        assert np.array_equal(codes[c * 6:(c + 1) * 6].cpu().numpy(), ref["codes"]), c
+    # offsets: exclusive prefix sums of per-cell counts
+    table = torch.zeros(32, dtype=torch.int64, device="cuda")
+    with open(os.path.join(os.path.dirname(__file__), "golden", "fig5_6_element_counts.txt")) as fh:
+        for ln in fh:
+            if ln.startswith("tet"):
+                _, code, cnt = ln.split()
+                table[int(code)] = int(cnt)
+    counts = table[codes.to(torch.int64)].view(cells, 6).sum(1)
+    assert int(offs[0]) == 0
+    assert bool(torch.equal(offs[1:] - offs[:-1], counts[:-1]))
+    assert total == int(offs[-1] + counts[-1])
