@@ -70,6 +70,9 @@ WORKLOADS = {
                        "side log-uniform 64-768, 50/50), fp32 sub-boxes of sigma=4 smoothed-noise "
                        "bases (16384^2 and 768^3, generated on the device), 120 GB budget; "
                        "saturation and Poisson arrivals vs the plain one-call-per-field path"),
+    "index512": dict(dims=(512, 512, 512), kind="index", dtype="i32",
+                     desc="marching tetrahedra index pass (codes + cell offsets) over the MS labels "
+                          "of the 512^3 sigma=4 noise field (6 x 511^3 tetrahedra)"),
     "batch256": dict(dims=None, kind="batch", dtype="mixed",
                      desc="256 fields, dims log-uniform in [32, 256] per axis, fp32/fp16 and smoothed "
                           "noise (sigma 2-6) / 8-Gaussian sums 50/50, seed 0; one ms_segment_batch call "
@@ -514,6 +517,74 @@ def run_serve_bench(args):
     return 0
 
 
+def run_index_bench(args):
+    """The index pass after the segmentation (ms_simplex_index) on the MS labels
+    of the 512^3 noise field: per cell, labels in (4 B, each vertex once),
+    6 tetrahedron codes (6 B) and one offset (8 B) out."""
+    import torch
+
+    import paper_2303_15491_gb300 as ms
+
+    torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    dims = (512, 512, 512)
+    field = torch.from_numpy(make_field("noise512")).to(dev)
+    stream = torch.cuda.Stream(device=dev)
+    ctx = ms.ms_create(dev, stream)
+    asc, desc, labels, _ = ms.segment(ctx, field)
+    del asc, desc, field
+    cells, per = ms.simplex_cells(dims)
+    codes = torch.empty(cells * per, dtype=torch.uint8, device=dev)
+    offs = torch.empty(cells, dtype=torch.int64, device=dev)
+    for _ in range(args.warmup):
+        total = ms.ms_simplex_index(ctx, labels, dims, codes, offs)
+    torch.cuda.synchronize()
+    ms.ms_profile_enable(ctx, True)
+    with ClockSampler(dev) as clk:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            total = ms.ms_simplex_index(ctx, labels, dims, codes, offs)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        host_ms = 1e3 * (time.perf_counter() - t)
+    prof = ms.ms_profile_read(ctx)
+    ms.ms_profile_enable(ctx, False)
+    ms_per = max(ev0.elapsed_time(ev1), host_ms) / args.steps
+    kern_ms = prof["stages"]["tile_local"]["ms"] / max(1, prof["calls"])
+    hbm, peak_kind = peaks()
+    alg = 18 * cells
+    # CPU baseline: the oracle on a z-slab of the labels
+    import oracle
+
+    slab = 17
+    lab_np = labels.view(512, 512, 512)[:slab].cpu().numpy()
+    t = time.perf_counter()
+    oracle.simplex_index(lab_np, (512, 512, slab))
+    cpu_s = time.perf_counter() - t
+    ms.ms_destroy(ctx)
+    line = {
+        "metric": "tetrahedra indexed/s (marching tetrahedra index pass)", "value": cells * per / (ms_per / 1e3),
+        "unit": "tetrahedra/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "i32", "data": "synthetic",
+        "config": {"workload": "index512", "desc": WORKLOADS["index512"]["desc"], "cells": cells,
+                   "tetrahedra": cells * per, "elements_total": total,
+                   "l2": "labels 512 MiB, codes 800 MB, offsets 1.07 GB: larger than L2"},
+        "roofline": {"bound": "hbm", "kernel": "index pass (3 launches)", "achieved": alg / (kern_ms / 1e3) / 1e9,
+                     "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": alg / (kern_ms / 1e3) / 1e9 / hbm, "traffic": None,
+                     "alg_bytes_per_cell": 18, "avg_launch_ms": kern_ms},
+        "gpu_launches": prof["launches"],
+        "cpu_baseline": {"value": 511 * 511 * (slab - 1) * per / cpu_s, "unit": "tetrahedra/s", "cores": 1,
+                         "kind": "oracle", "sample": f"512x512x{slab} slab ({cpu_s:.1f} s single-threaded)"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -533,6 +604,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "index512":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the index pass has no separate "
+                              "reference arm; its CPU baseline is in the line's cpu_baseline"}))
+            return 0
+        return run_index_bench(args)
     if args.workload == "serve":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the serving workload has no CPU "
