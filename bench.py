@@ -715,7 +715,7 @@ def main():
     launches = max(1, stages[dom]["launches"])
     per_launch_s = stages[dom]["ms"] / 1e3 / launches
     alg_bytes = STAGE_BYTES[dom][w["dtype"]] * n
-    achieved = alg_bytes / per_launch_s / 1e9
+    achieved = alg_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tpath):
@@ -738,7 +738,8 @@ def main():
                    "l2": "inputs larger than L2 (field 512 MiB, labels 3 x 512 MiB > 129 MB L2)",
                    "parallelism": f"replicas x{ws} (no data-path collective)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm,
+                     "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": None if achieved is None else achieved / hbm,
                      "traffic": traffic,
                      "alg_bytes_per_vertex": STAGE_BYTES[dom][w["dtype"]],
                      "avg_launch_ms": per_launch_s * 1e3},

@@ -85,6 +85,8 @@ ms_status ms_destroy(ms_ctx *ctx);
 /* Full segmentation (Sec. 4.2): order keys, steepest neighbours, path
  * compression, MS ids.  field: N values of `dtype`; out_asc, out_desc,
  * out_ms: int32[N] each (distinct, non-overlapping, 4-byte aligned).
+ * Repeated calls on the same buffers replay a captured CUDA graph (see
+ * ms_segment_batch); the results are the same either way.
  * Errors: MS_ERR_INVALID_ARG, MS_ERR_UNSUPPORTED_DTYPE, MS_ERR_TOO_LARGE,
  * MS_ERR_NAN_INPUT, MS_ERR_OUT_OF_MEMORY, MS_ERR_CUDA, MS_ERR_NOT_CONVERGED. */
 ms_status ms_segment(ms_ctx *ctx, const void *field, const int64_t dims[3], ms_dtype dtype,
@@ -99,10 +101,10 @@ ms_status ms_segment(ms_ctx *ctx, const void *field, const int64_t dims[3], ms_d
  * fields go through one launch per stage (tiles of all fields in one work
  * queue, one global pair set keyed by field); otherwise the fields are
  * segmented one after the other.
- * Repeats: the first call with a given set of fields (same pointers, dims and
- * dtypes) runs step by step and records the sizes it met; the context then
- * captures the whole pipeline (sized from them, with margins) in a CUDA graph,
- * and later calls with the same fields replay it with one host
+ * Repeats (here and in ms_segment): a call with the same fields as the call
+ * before (same pointers, dims and dtypes) runs step by step, records the sizes
+ * it met and captures the whole pipeline (sized from them, with margins) in a
+ * CUDA graph; later calls with the same fields replay it with one host
  * synchronisation.  A replay whose sizes no longer suffice (the fields'
  * contents changed) is detected on the device and the call runs step by step
  * again, so results never depend on the path taken.
@@ -185,7 +187,7 @@ ms_status ms_batch_autotune(ms_ctx *ctx, int n_fields, const void *const *fields
                             ms_tuning *out);
 
 /* Enable (on != 0, the default) or disable graph capture and replay of
- * repeated batches on this context. */
+ * repeated calls (ms_segment, ms_segment_batch) on this context. */
 ms_status ms_batch_graphs(ms_ctx *ctx, int on);
 
 /* ---- after the segmentation: the marching triangles / tetrahedra index pass - */
@@ -225,7 +227,9 @@ ms_status ms_simplex_index(ms_ctx *ctx, const int32_t *labels, const int64_t dim
  * memory -- its field and three label arrays plus about 10 bytes of scratch
  * per vertex -- fits in what budget_bytes has left; among waiting requests the
  * first that fits is admitted (one passed over 8 times is admitted next, once
- * it fits).  Results are exactly those of ms_segment. */
+ * it fits), except that requests of at least 2^25 vertices -- each fills the
+ * GPU by itself -- run one at a time.  Results are exactly those of
+ * ms_segment. */
 typedef struct ms_server ms_server;
 
 typedef struct {

@@ -33,6 +33,8 @@ struct BatchPlan {
   size_t host_desc_bytes = 0;
   uint32_t *hfstart = nullptr;  // pinned: first sorted pair of each descriptor
   size_t hfstart_count = 0;
+  int seen = 0;                   // consecutive calls with this signature
+  long long stage_launches[3] = {};  // kernels per replay: tile_local, resolve, write
 };
 
 struct ms_ctx {
@@ -528,12 +530,14 @@ ms_status segment_staged(ms_ctx *c, const void *field, const int64_t dims[3], in
 // the step-by-step path.
 bool tiled_shape(const int64_t dims[3]) { return dims[2] == 1 || dims[2] >= kTZ / 2; }
 
+ms_status run_batch(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out);
+
 ms_status segment_device(ms_ctx *c, const void *field, const int64_t dims[3], int dtype,
                          int64_t n, int32_t *asc, int32_t *desc, int32_t *ms) {
   if (tiled_shape(dims)) {
     const FieldArg fa{field, dims, dtype, n, asc, desc, ms};
     int64_t k = 0;
-    const ms_status s = segment_tiled(c, &fa, 1, &k, c->tune);
+    const ms_status s = run_batch(c, &fa, 1, &k);
     if (s == MS_OK) c->last_k = k;
     return s;
   }
@@ -651,6 +655,9 @@ ms_status capture_plan(ms_ctx *c, const FieldArg *fa, int nf) {
   RankScratch rs;
   rank_scratch_carve(c->scratch, hcap, &rs);
   if ((uint64_t)hcap < 2 * run.npairs + 2) rs.probe_limit = kEstimateProbeLimit;
+  // the sort and rank launches are sized for this many distinct pairs; more
+  // of them overflow the list on the device and the call runs step by step
+  rs.max_unique = (unsigned int)std::min<uint64_t>(rs.max_unique, run.m + run.m / 4 + 4096);
   // pinned copies the graph reads from and writes to
   if (P.host_desc_bytes < sf.bytes) {
     if (P.host_desc) cudaFreeHost(P.host_desc);
@@ -668,6 +675,9 @@ ms_status capture_plan(ms_ctx *c, const FieldArg *fa, int nf) {
     P.hfstart_count = (size_t)nf;
   }
   P.order = sf.order;
+  for (int i = 0; i < MS_STAGE_COUNT; ++i)  // the graph records the stage events
+    for (int j = 0; j < 2; ++j)
+      if (!c->ev[i][j]) MS_TRY(cudaEventCreate(&c->ev[i][j]));
   int raw = 0;
   const int kb = pair_key_bits(sf, &raw);
   const int rounds = std::max(3, run.rounds + 1);
@@ -682,7 +692,16 @@ ms_status capture_plan(ms_ctx *c, const FieldArg *fa, int nf) {
                              c->stream)) != cudaSuccess)
       return e;
     if ((e = cudaMemsetAsync(c->dst, 0, sizeof(DevStatus), c->stream)) != cudaSuccess) return e;
+    // stage events as record nodes of the graph (external records; a plain
+    // record during capture only orders the capture): a replay times its
+    // stages like a call
+    long long lc = tl_launches;
+    if ((e = cudaEventRecordWithFlags(c->ev[MS_STAGE_TILE_LOCAL][0], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = launch_tile_local(b, ts, c->dst, c->stream)) != cudaSuccess) return e;
+    if ((e = cudaEventRecordWithFlags(c->ev[MS_STAGE_TILE_LOCAL][1], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+    P.stage_launches[0] = tl_launches - lc;
+    lc = tl_launches;
+    if ((e = cudaEventRecordWithFlags(c->ev[MS_STAGE_RESOLVE][0], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
     if (run.use_graph) {
       if ((e = launch_face_graph_build(b, ts, graph, c->dst, c->stream)) != cudaSuccess) return e;
       if ((e = launch_face_graph_rounds(b, graph, 0, rounds, c->dst, c->stream)) != cudaSuccess)
@@ -706,7 +725,13 @@ ms_status capture_plan(ms_ctx *c, const FieldArg *fa, int nf) {
     if ((e = launch_field_starts(b, ts, rs, rs.max_unique, c->stream, &c->dst->n_unique)) !=
         cudaSuccess)
       return e;
+    if ((e = cudaEventRecordWithFlags(c->ev[MS_STAGE_RESOLVE][1], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+    P.stage_launches[1] = tl_launches - lc;
+    lc = tl_launches;
+    if ((e = cudaEventRecordWithFlags(c->ev[MS_STAGE_WRITE][0], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
     if ((e = launch_tile_write(b, ts, rs, c->dst, c->stream)) != cudaSuccess) return e;
+    if ((e = cudaEventRecordWithFlags(c->ev[MS_STAGE_WRITE][1], c->stream, cudaEventRecordExternal)) != cudaSuccess) return e;
+    P.stage_launches[2] = tl_launches - lc;
     if ((e = cudaMemcpyAsync(c->hst, c->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost,
                              c->stream)) != cudaSuccess)
       return e;
@@ -756,6 +781,11 @@ ms_status replay_plan(ms_ctx *c, int nf, int64_t *k_out, bool *fallback) {
     cudaEventRecord(c->ev[MS_STAGE_GRAPH][1], c->stream);
     c->ev_pending[MS_STAGE_GRAPH] = true;
     c->prof.stage_launches[MS_STAGE_GRAPH] += P.launches;
+    const int st3[3] = {MS_STAGE_TILE_LOCAL, MS_STAGE_RESOLVE, MS_STAGE_WRITE};
+    for (int i = 0; i < 3; ++i) {  // the graph recorded these stages' events
+      c->ev_pending[st3[i]] = true;
+      c->prof.stage_launches[st3[i]] += P.stage_launches[i];
+    }
   }
   tl_launches += P.launches;
   MS_TRY(cudaStreamSynchronize(c->stream));
@@ -788,6 +818,7 @@ ms_status run_batch(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
     reset_plan(&P);
     P.sig = std::move(sig);
   }
+  ++P.seen;
   if (c->graphs_on && P.exec && P.epoch == c->alloc_epoch) {
     bool fallback = false;
     const ms_status s = replay_plan(c, nf, k_out, &fallback);
@@ -796,7 +827,8 @@ ms_status run_batch(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
   }
   const ms_status s = segment_tiled(c, fa, nf, k_out, P.tuned ? P.tune : c->tune);
   if (s != MS_OK) return s;
-  if (c->graphs_on && !P.exec && capture_plan(c, fa, nf) != MS_OK) drop_graph(&P);
+  // capture once the same fields come a second time (one-off calls never pay for it)
+  if (c->graphs_on && !P.exec && P.seen >= 2 && capture_plan(c, fa, nf) != MS_OK) drop_graph(&P);
   return MS_OK;
 }
 

@@ -7,7 +7,8 @@
 // memory (its field and labels plus the scratch its segmentation needs) fits
 // in what the budget has left; among waiting requests the first that fits is
 // admitted (a request that has been passed over kMaxBypass times blocks
-// later ones until it fits, so large requests are not starved).
+// later ones until it fits, so large requests are not starved).  Requests of
+// at least kLargeVertices vertices run one at a time.
 #include <stdint.h>
 
 #include <chrono>
@@ -26,6 +27,10 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr int kMaxBypass = 8;
+// A request this large fills the GPU by itself: two of them side by side only
+// slow each other down, so at most one runs at a time (smaller requests still
+// run beside it).
+constexpr int64_t kLargeVertices = 1ll << 25;
 
 struct Request {
   uint64_t ticket = 0;
@@ -34,6 +39,7 @@ struct Request {
   ms_dtype dtype;
   int32_t *asc, *desc, *ms;
   size_t bytes;  // admission estimate
+  bool large = false;
   int bypassed = 0;
   Clock::time_point submitted;
 };
@@ -61,6 +67,7 @@ struct ms_server {
   size_t budget = 0;
   size_t in_use = 0;
   size_t peak = 0;
+  int large_running = 0;
   bool stopping = false;
   uint64_t next_ticket = 1;
   uint64_t admitted = 0, completed = 0;
@@ -78,12 +85,14 @@ namespace {
 // Pop the first admissible request (caller holds mu); false if none fits.
 bool take_admissible(ms_server *s, Request *out) {
   for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+    if (it->large && s->large_running > 0) continue;  // waits for the running large one
     if (s->in_use + it->bytes <= s->budget) {
       *out = *it;
       // everything ahead of it was passed over once more
       for (auto jt = s->queue.begin(); jt != it; ++jt) jt->bypassed++;
       s->queue.erase(it);
       s->in_use += out->bytes;
+      s->large_running += out->large ? 1 : 0;
       if (s->in_use > s->peak) s->peak = s->in_use;
       s->admitted++;
       return true;
@@ -116,6 +125,7 @@ void worker_main(ms_server *s, ms_ctx *ctx) {
       res.k = k;
       res.latency_ms = ms;
       s->in_use -= r.bytes;
+      s->large_running -= r.large ? 1 : 0;
       s->completed++;
       s->launches += (uint64_t)nl;
     }
@@ -163,6 +173,7 @@ ms_status ms_server_submit(ms_server *s, const void *field, const int64_t dims[3
   r.desc = out_desc;
   r.ms = out_ms;
   r.bytes = estimate_bytes(dims, dtype);
+  r.large = dims[0] * dims[1] * dims[2] >= kLargeVertices;
   r.submitted = Clock::now();
   {
     std::lock_guard<std::mutex> lock(s->mu);

@@ -10,10 +10,11 @@
 // c the cell's linear index (x fastest); a simplex's vertices in stepping
 // order are a, b, c(, d).
 //
-// Three launches: codes and per-block element totals (one thread per cell,
-// the block's codes staged in shared memory and stored as 16-byte vectors),
-// an exclusive scan of the block totals, and the per-cell offsets (counts
-// re-derived from the codes, block scan, plus the block's base).
+// Three launches: codes and per-block element totals (one thread per cell of
+// each of a block's kSub groups of 256 cells, a group's codes staged in
+// shared memory and stored as 16-byte vectors), an exclusive scan of the
+// block totals, and the per-cell offsets (counts re-derived from the codes,
+// block scans, plus the block's base).
 #include <stdint.h>
 
 #include "fastdiv.h"
@@ -23,6 +24,7 @@ namespace msseg {
 namespace {
 
 constexpr int kCellThreads = 256;
+constexpr int kSub = 8;  // groups of kCellThreads cells per block
 
 struct SimplexGeom {
   int64_t nx, ny;        // vertices per row / per plane row count
@@ -99,56 +101,74 @@ __device__ __forceinline__ unsigned int block_excl(unsigned int v, unsigned int 
   return base + incl - v;
 }
 
+// Element counts of all 32 codes (valid or not), one word per code so that
+// lookups of different codes hit different banks.
+__device__ __forceinline__ void fill_elements(unsigned int *lut, int per) {
+  if (threadIdx.x < 32)
+    lut[threadIdx.x] = per == 2 ? (unsigned int)tri_elements(threadIdx.x & 7)
+                                : (unsigned int)tet_elements(threadIdx.x);
+}
+
 __global__ void __launch_bounds__(kCellThreads) k_simplex_codes(const int32_t *__restrict__ lab,
                                                                 SimplexGeom g,
                                                                 uint8_t *__restrict__ codes,
                                                                 unsigned int *__restrict__ block_tot) {
   __shared__ __align__(16) uint8_t sc[kCellThreads * 6];
   __shared__ unsigned int sh[kCellThreads / 32];
-  const int64_t c0 = (int64_t)blockIdx.x * kCellThreads;
-  const int64_t c = c0 + threadIdx.x;
-  unsigned int count = 0;
-  if (c < g.ncells) {
-    uint32_t x, y, z;
-    cell_xyz(g, (uint32_t)c, &x, &y, &z);
-    const int64_t v = (int64_t)x + g.nx * ((int64_t)y + g.ny * z);
-    const int64_t sy = g.nx, sz = g.nx * g.ny;
-    if (g.per == 2) {
-      const int32_t l00 = __ldg(lab + v), l10 = __ldg(lab + v + 1), l01 = __ldg(lab + v + sy),
-                    l11 = __ldg(lab + v + sy + 1);
-      const int k0 = tri_code(l00, l10, l11), k1 = tri_code(l00, l01, l11);
-      sc[threadIdx.x * 2] = (uint8_t)k0;
-      sc[threadIdx.x * 2 + 1] = (uint8_t)k1;
-      count = tri_elements(k0) + tri_elements(k1);
-    } else {
-      // corners by offset bits (x = 1, y = 2, z = 4)
-      int32_t l[8];
+  __shared__ unsigned int lut[32];
+  fill_elements(lut, g.per);
+  __syncthreads();
+  unsigned int block_sum = 0;
+  // kSub consecutive groups of kCellThreads cells per block
+  for (int sub = 0; sub < kSub; ++sub) {
+    const int64_t c0 = ((int64_t)blockIdx.x * kSub + sub) * kCellThreads;
+    if (c0 >= g.ncells) break;  // block-uniform
+    const int64_t c = c0 + threadIdx.x;
+    unsigned int count = 0;
+    if (c < g.ncells) {
+      uint32_t x, y, z;
+      cell_xyz(g, (uint32_t)c, &x, &y, &z);
+      const int64_t v = (int64_t)x + g.nx * ((int64_t)y + g.ny * z);
+      const int64_t sy = g.nx, sz = g.nx * g.ny;
+      if (g.per == 2) {
+        const int32_t l00 = __ldg(lab + v), l10 = __ldg(lab + v + 1), l01 = __ldg(lab + v + sy),
+                      l11 = __ldg(lab + v + sy + 1);
+        const int k0 = tri_code(l00, l10, l11), k1 = tri_code(l00, l01, l11);
+        sc[threadIdx.x * 2] = (uint8_t)k0;
+        sc[threadIdx.x * 2 + 1] = (uint8_t)k1;
+        count = lut[k0] + lut[k1];
+      } else {
+        // corners by offset bits (x = 1, y = 2, z = 4)
+        int32_t l[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        l[k] = __ldg(lab + v + ((k & 1) ? 1 : 0) + ((k & 2) ? sy : 0) + ((k & 4) ? sz : 0));
-      // axis orders xyz, xzy, yxz, yzx, zxy, zyx: b and c corners of each chain
-      const int kb[6] = {1, 1, 2, 2, 4, 4};
-      const int kc[6] = {3, 5, 3, 6, 5, 6};
+        for (int k = 0; k < 8; ++k)
+          l[k] = __ldg(lab + v + ((k & 1) ? 1 : 0) + ((k & 2) ? sy : 0) + ((k & 4) ? sz : 0));
+        // axis orders xyz, xzy, yxz, yzx, zxy, zyx: b and c corners of each chain
+        const int kb[6] = {1, 1, 2, 2, 4, 4};
+        const int kc[6] = {3, 5, 3, 6, 5, 6};
 #pragma unroll
-      for (int p = 0; p < 6; ++p) {
-        const int code = tet_code(l[0], l[kb[p]], l[kc[p]], l[7]);
-        sc[threadIdx.x * 6 + p] = (uint8_t)code;
-        count += tet_elements(code);
+        for (int p = 0; p < 6; ++p) {
+          const int code = tet_code(l[0], l[kb[p]], l[kc[p]], l[7]);
+          sc[threadIdx.x * 6 + p] = (uint8_t)code;
+          count += lut[code];
+        }
       }
     }
+    __syncthreads();
+    // the group's codes are one contiguous byte range
+    const int64_t nvalid = min((int64_t)kCellThreads, g.ncells - c0);
+    const int64_t bytes = nvalid * g.per;
+    uint8_t *dst = codes + c0 * g.per;  // 16-byte aligned: c0 * per is a multiple of 512
+    const int vec = (int)(bytes / 16);
+    for (int i = threadIdx.x; i < vec; i += kCellThreads)
+      reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(sc)[i];
+    for (int64_t i = (int64_t)vec * 16 + threadIdx.x; i < bytes; i += kCellThreads) dst[i] = sc[i];
+    unsigned int tot = 0;
+    block_excl(count, &tot, sh);
+    block_sum += tot;
+    __syncthreads();  // sc and sh are reused by the next group
   }
-  __syncthreads();
-  // the block's codes are one contiguous byte range
-  const int64_t nvalid = min((int64_t)kCellThreads, g.ncells - c0);
-  const int64_t bytes = nvalid * g.per;
-  uint8_t *dst = codes + c0 * g.per;  // 16-byte aligned: c0 * per is a multiple of 512
-  const int vec = (int)(bytes / 16);
-  for (int i = threadIdx.x; i < vec; i += kCellThreads)
-    reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(sc)[i];
-  for (int64_t i = (int64_t)vec * 16 + threadIdx.x; i < bytes; i += kCellThreads) dst[i] = sc[i];
-  unsigned int tot = 0;
-  block_excl(count, &tot, sh);
-  if (threadIdx.x == 0) block_tot[blockIdx.x] = tot;
+  if (threadIdx.x == 0) block_tot[blockIdx.x] = block_sum;
 }
 
 // Exclusive scan of the per-block totals into 64-bit bases, by one block:
@@ -184,30 +204,40 @@ __global__ void __launch_bounds__(kCellThreads) k_simplex_offsets(const uint8_t 
                                                                   const unsigned long long *__restrict__ base,
                                                                   int64_t *__restrict__ offsets) {
   __shared__ unsigned int sh[kCellThreads / 32];
-  const int64_t c = (int64_t)blockIdx.x * kCellThreads + threadIdx.x;
-  unsigned int count = 0;
-  if (c < g.ncells) {
-    if (g.per == 2) {
-      const uint16_t two = __ldg(reinterpret_cast<const uint16_t *>(codes) + c);
-      count = tri_elements(two & 0xff) + tri_elements(two >> 8);
-    } else {
-      const uint16_t *p = reinterpret_cast<const uint16_t *>(codes + 6 * c);
+  __shared__ unsigned int lut[32];
+  fill_elements(lut, g.per);
+  __syncthreads();
+  unsigned long long running = base[blockIdx.x];
+  for (int sub = 0; sub < kSub; ++sub) {
+    const int64_t c0 = ((int64_t)blockIdx.x * kSub + sub) * kCellThreads;
+    if (c0 >= g.ncells) break;  // block-uniform
+    const int64_t c = c0 + threadIdx.x;
+    unsigned int count = 0;
+    if (c < g.ncells) {
+      if (g.per == 2) {
+        const uint16_t two = __ldg(reinterpret_cast<const uint16_t *>(codes) + c);
+        count = lut[two & 0x1f] + lut[(two >> 8) & 0x1f];
+      } else {
+        const uint16_t *p = reinterpret_cast<const uint16_t *>(codes + 6 * c);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const uint16_t two = __ldg(p + k);
-        count += tet_elements(two & 0xff) + tet_elements(two >> 8);
+        for (int k = 0; k < 3; ++k) {
+          const uint16_t two = __ldg(p + k);
+          count += lut[two & 0x1f] + lut[(two >> 8) & 0x1f];
+        }
       }
     }
+    unsigned int tot = 0;
+    const unsigned int ex = block_excl(count, &tot, sh);
+    if (c < g.ncells) offsets[c] = (int64_t)(running + ex);
+    running += tot;
+    __syncthreads();  // sh is reused by the next group
   }
-  unsigned int tot = 0;
-  const unsigned int ex = block_excl(count, &tot, sh);
-  if (c < g.ncells) offsets[c] = (int64_t)(base[blockIdx.x] + ex);
 }
 
 }  // namespace
 
 size_t simplex_scratch_bytes(int64_t ncells) {
-  const int64_t nb = (ncells + kCellThreads - 1) / kCellThreads;
+  const int64_t nb = (ncells + kCellThreads * kSub - 1) / (kCellThreads * kSub);
   return 256 + (size_t)nb * 4 + (size_t)nb * 8 + 256;
 }
 
@@ -232,7 +262,7 @@ cudaError_t launch_simplex_index(const int32_t *labels, const int64_t dims[3], u
   if (e != cudaSuccess || g.ncells == 0) return e;
   g.div_cx = FastDivU32((uint32_t)g.cx);
   g.div_cy = FastDivU32((uint32_t)g.cy);
-  const int64_t nb = (g.ncells + kCellThreads - 1) / kCellThreads;
+  const int64_t nb = (g.ncells + kCellThreads * kSub - 1) / (kCellThreads * kSub);
   unsigned int *btot = reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + 256);
   unsigned long long *bbase = reinterpret_cast<unsigned long long *>(
       static_cast<char *>(scratch) + 256 + (((size_t)nb * 4 + 255) & ~(size_t)255));

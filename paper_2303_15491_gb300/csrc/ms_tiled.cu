@@ -430,25 +430,34 @@ __device__ __forceinline__ void number_tile_pairs(uint32_t *K, uint32_t *P, cons
   uint32_t cidx[kRun / 2];  // two 16-bit candidate indices per word
   int ncand = 0;           // this warp's candidates so far
   {
+    // A run of equal pairs along the lanes takes the candidate of its first
+    // lane; that lane makes a new candidate unless its pair equals its own
+    // pair one step back along the run (then it reuses that candidate).
     const int seg = warp * (kRun * 32);
+    uint32_t prev_key = kEmpty32;  // this lane's pair at j - 1 (kEmpty32: none)
+    int prev_ci = 0;
 #pragma unroll
     for (int j = 0; j < kRun; ++j) {
       const bool valid = col_in && j < n_here;
       const uint32_t key = valid ? w[j] : kEmpty32;
-      const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-      const bool lead = valid && (lane == 0 || prev != key);
-      const unsigned lm = __ballot_sync(0xffffffffu, lead);
+      const uint32_t left = __shfl_up_sync(0xffffffffu, key, 1);
+      const bool start = valid && (lane == 0 || left != key);
+      const bool fresh = start && key != prev_key;
+      const unsigned lm = __ballot_sync(0xffffffffu, fresh);
       const int my = seg + ncand + __popc(lm & ((1u << lane) - 1u));
-      if (lead) CK[my] = key;
-      // the run's leader is the highest leader lane at or below this lane
-      const unsigned upto = lm & (0xffffffffu >> (31 - lane));
+      if (fresh) CK[my] = key;
+      // the run's first lane is the highest start lane at or below this lane
+      const unsigned sm = __ballot_sync(0xffffffffu, start);
+      const unsigned upto = sm & (0xffffffffu >> (31 - lane));
       const int src = upto ? 31 - __clz(upto) : lane;
-      const int ci = __shfl_sync(0xffffffffu, my, src);
+      const int ci = __shfl_sync(0xffffffffu, fresh ? my : prev_ci, src);
       const uint32_t c = valid ? (uint32_t)ci : 0u;
       if (j & 1)
         cidx[j / 2] |= c << 16;
       else
         cidx[j / 2] = c;
+      prev_key = key;
+      prev_ci = ci;
       ncand += __popc(lm);
     }
   }
@@ -1146,7 +1155,13 @@ __global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, int m
                                 const int2 *__restrict__ graph, unsigned long long stride,
                                 DevStatus *st) {
   const unsigned long long npairs = min(*ts.pool_count, ts.pool_cap);
-  const unsigned long long nwork = mode == kChaseProbe ? (npairs + stride - 1) / stride : npairs;
+  // the unbudgeted pass walks the pending list, or the whole pool if the
+  // list overflowed
+  const unsigned long long npend = mode == kChasePending ? *(volatile unsigned int *)&st->pending : 0;
+  const bool from_list = mode == kChasePending && npend <= ts.pending_cap;
+  const unsigned long long nwork = mode == kChaseProbe ? (npairs + stride - 1) / stride
+                                   : from_list         ? npend
+                                                       : npairs;
   const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
   const unsigned int mask = rs.capacity - 1u;
   // A set found too small stops the pass early (the host retries larger).
@@ -1156,8 +1171,8 @@ __global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, int m
   for (unsigned long long w = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < nwork;
        w += step) {
     if ((it++ & 31u) == 0) overflow = __ldcg(&st->hash_overflow);
-    const unsigned long long p = mode == kChaseProbe ? w * stride : w;
-    if (mode == kChasePending && ts.pool_slot[p] != kPendingSlot) continue;
+    const unsigned long long p = mode == kChaseProbe ? w * stride : from_list ? ts.pending_list[w] : w;
+    if (mode == kChasePending && !from_list && ts.pool_slot[p] != kPendingSlot) continue;
     const int2 r = ts.pool_roots[p];
     const uint32_t fi = kSingle ? 0u : ts.pool_field[p];
     const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
@@ -1186,7 +1201,8 @@ __global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, int m
       }
       if (a < 0 || d < 0) {  // only with the budget: resolved by a later pass
         ts.pool_slot[p] = kPendingSlot;
-        atomicAdd(&st->pending, 1u);
+        const unsigned int at = atomicAdd(&st->pending, 1u);
+        if (at < ts.pending_cap) ts.pending_list[at] = (uint32_t)p;
         continue;
       }
     }
@@ -1361,11 +1377,16 @@ TileGeom tile_geom(const int64_t dims[3]) {
   return g;
 }
 
+// Room for pending pairs: an eighth of the pool (more pending pairs make the
+// unbudgeted pass scan the whole pool instead).
+unsigned long long pending_cap_of(unsigned long long pool_cap) { return pool_cap / 8 + 1024; }
+
 size_t tiled_scratch_bytes(long long total_tiles, int n_fields, unsigned long long pool_cap) {
   const size_t pid = (size_t)total_tiles * kTileV * 2;
   const size_t face = (size_t)total_tiles * kFace * 4;
   const size_t meta = (size_t)total_tiles * (8 + 4);
-  return 16 * 256 + pid + face + meta + (size_t)pool_cap * (8 + 4 + 4) + (size_t)n_fields * 4;
+  return 16 * 256 + pid + face + meta + (size_t)pool_cap * (8 + 4 + 4) + (size_t)n_fields * 4 +
+         (size_t)pending_cap_of(pool_cap) * 4;
 }
 
 void tiled_scratch_carve(void *base, long long total_tiles, int n_fields,
@@ -1379,6 +1400,8 @@ void tiled_scratch_carve(void *base, long long total_tiles, int n_fields,
   ts->pool_count = reinterpret_cast<unsigned long long *>(take(256));
   ts->queue = reinterpret_cast<unsigned int *>(ts->pool_count + 1);
   ts->pool_slot = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
+  ts->pending_cap = pending_cap_of(pool_cap);
+  ts->pending_list = reinterpret_cast<uint32_t *>(take((size_t)ts->pending_cap * 4));
   ts->pool_roots = reinterpret_cast<int2 *>(take((size_t)pool_cap * 8));
   ts->pool_field = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
   ts->tile_base = reinterpret_cast<long long *>(take((size_t)total_tiles * 8));

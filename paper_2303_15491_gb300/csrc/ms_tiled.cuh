@@ -103,6 +103,8 @@ struct TiledScratch {
   uint32_t *pool_field;  // per tile pair: its field
   uint32_t *fstart;      // per field: index of its first pair in the sorted pair list
   uint32_t *pool_slot;  // per tile pair: slot of its (asc, desc) pair in the global pair set
+  uint32_t *pending_list;  // tile pairs left by the budgeted chase (up to pending_cap)
+  unsigned long long pending_cap;
   long long *tile_base;
   int32_t *tile_count;
   uint32_t *face;     // per tile kFace words: up-root | dn-root << 16 (extended-box indices)

@@ -425,3 +425,24 @@ def test_flat_tiles_equal_staged_path(ctx):
     for a, b in zip(tiled[:3], outs):
         assert torch.equal(a, b)
     assert tiled[3] == ms.ms_last_region_count(ctx)
+
+
+def test_repeated_calls_replay_and_follow_new_contents(ctx):
+    """ms_segment on the same buffers: the third call replays the captured
+    graph; changing the field's contents in place (many more regions) is
+    caught and the call runs step by step; results always match the oracle."""
+    dims = (70, 60, 50)
+    smooth = sf.broad_gaussians_ramp(dims, 91, sigma=25.0)
+    noisy = sf.smoothed_noise(dims, 92, sigma=1.0)
+    dev = to_dev(smooth)
+    outs = [torch.empty(smooth.size, dtype=torch.int32, device="cuda") for _ in range(3)]
+    ms.ms_profile_enable(ctx, True)
+    for f in (smooth, smooth, smooth, noisy, noisy, noisy, smooth):
+        dev.copy_(torch.from_numpy(np.ascontiguousarray(f)))
+        torch.cuda.synchronize()
+        ms.ms_segment(ctx, dev, dims, ms.MS_F32, *outs)
+        got = tuple(o.cpu().numpy() for o in outs) + (ms.ms_last_region_count(ctx),)
+        assert_same_labels(got, oracle.segment(f), "repeated call")
+    prof = ms.ms_profile_read(ctx)
+    ms.ms_profile_enable(ctx, False)
+    assert prof["stages"]["graph"]["launches"] > 0

@@ -180,3 +180,29 @@ def test_wait_with_timeout_then_release(ctx):
         assert e.value.name == "MS_ERR_INVALID_ARG"
     finally:
         ms.ms_server_destroy(srv)
+
+
+def test_large_requests_run_one_at_a_time_with_small_ones_beside(ctx):
+    """Two requests of at least 2^25 vertices (run one at a time) among small
+    ones: every result equals the request run alone."""
+    big = [torch.randn(6000 * 6000, device="cuda").view(6000, 6000) for _ in range(2)]
+    small = [torch.from_numpy(sf.smoothed_noise((40, 30, 20), 300 + i, sigma=2.0)).cuda()
+             for i in range(6)]
+    fields = [big[0], small[0], small[1], big[1]] + small[2:]
+    outs = [[torch.full((f.numel(),), -3, dtype=torch.int32, device="cuda") for _ in range(3)]
+            for f in fields]
+    torch.cuda.synchronize()
+    srv = ms.ms_server_create(0, 64 << 30, 4)
+    try:
+        tickets = [ms.ms_server_submit(srv, f, ms.dims_of(f), 0, *o) for f, o in zip(fields, outs)]
+        res = [ms.ms_server_wait(srv, t, 120000) for t in tickets]
+        stats = ms.ms_server_stats(srv)
+    finally:
+        ms.ms_server_destroy(srv)
+    assert stats["completed"] == len(fields)
+    for f, o, (st, k, _) in zip(fields, outs, res):
+        assert st == 0
+        alone = ms.segment(ctx, f)
+        for a, b in zip(o, alone[:3]):
+            assert torch.equal(a, b)
+        assert k == alone[3]
