@@ -10,11 +10,11 @@
 // c the cell's linear index (x fastest); a simplex's vertices in stepping
 // order are a, b, c(, d).
 //
-// Three launches: codes and per-block element totals (one thread per cell of
-// each of a block's kSub groups of 256 cells, a group's codes staged in
-// shared memory and stored as 16-byte vectors), an exclusive scan of the
-// block totals, and the per-cell offsets (counts re-derived from the codes,
-// block scans, plus the block's base).
+// Three launches: codes, per-cell element counts (one byte) and per-block
+// totals (one thread per cell of each of a block's kSub groups of 256 cells,
+// a group's codes staged in shared memory and stored as 16-byte vectors), an
+// exclusive scan of the block totals, and the per-cell offsets (block scans
+// of the counts, plus the block's base).
 #include <stdint.h>
 
 #include "fastdiv.h"
@@ -112,6 +112,7 @@ __device__ __forceinline__ void fill_elements(unsigned int *lut, int per) {
 __global__ void __launch_bounds__(kCellThreads) k_simplex_codes(const int32_t *__restrict__ lab,
                                                                 SimplexGeom g,
                                                                 uint8_t *__restrict__ codes,
+                                                                uint8_t *__restrict__ counts,
                                                                 unsigned int *__restrict__ block_tot) {
   __shared__ __align__(16) uint8_t sc[kCellThreads * 6];
   __shared__ unsigned int sh[kCellThreads / 32];
@@ -154,6 +155,7 @@ __global__ void __launch_bounds__(kCellThreads) k_simplex_codes(const int32_t *_
         }
       }
     }
+    if (c < g.ncells) counts[c] = (uint8_t)count;  // at most 6 x 12
     __syncthreads();
     // the group's codes are one contiguous byte range
     const int64_t nvalid = min((int64_t)kCellThreads, g.ncells - c0);
@@ -199,33 +201,17 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(const unsigned int *__rest
   if (threadIdx.x == 1023) *total = sh[1023];
 }
 
-__global__ void __launch_bounds__(kCellThreads) k_simplex_offsets(const uint8_t *__restrict__ codes,
+__global__ void __launch_bounds__(kCellThreads) k_simplex_offsets(const uint8_t *__restrict__ counts,
                                                                   SimplexGeom g,
                                                                   const unsigned long long *__restrict__ base,
                                                                   int64_t *__restrict__ offsets) {
   __shared__ unsigned int sh[kCellThreads / 32];
-  __shared__ unsigned int lut[32];
-  fill_elements(lut, g.per);
-  __syncthreads();
   unsigned long long running = base[blockIdx.x];
   for (int sub = 0; sub < kSub; ++sub) {
     const int64_t c0 = ((int64_t)blockIdx.x * kSub + sub) * kCellThreads;
     if (c0 >= g.ncells) break;  // block-uniform
     const int64_t c = c0 + threadIdx.x;
-    unsigned int count = 0;
-    if (c < g.ncells) {
-      if (g.per == 2) {
-        const uint16_t two = __ldg(reinterpret_cast<const uint16_t *>(codes) + c);
-        count = lut[two & 0x1f] + lut[(two >> 8) & 0x1f];
-      } else {
-        const uint16_t *p = reinterpret_cast<const uint16_t *>(codes + 6 * c);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const uint16_t two = __ldg(p + k);
-          count += lut[two & 0x1f] + lut[(two >> 8) & 0x1f];
-        }
-      }
-    }
+    const unsigned int count = c < g.ncells ? __ldg(counts + c) : 0u;
     unsigned int tot = 0;
     const unsigned int ex = block_excl(count, &tot, sh);
     if (c < g.ncells) offsets[c] = (int64_t)(running + ex);
@@ -238,7 +224,7 @@ __global__ void __launch_bounds__(kCellThreads) k_simplex_offsets(const uint8_t 
 
 size_t simplex_scratch_bytes(int64_t ncells) {
   const int64_t nb = (ncells + kCellThreads * kSub - 1) / (kCellThreads * kSub);
-  return 256 + (size_t)nb * 4 + (size_t)nb * 8 + 256;
+  return 256 + (size_t)nb * 4 + (size_t)nb * 8 + 256 + 256 + (size_t)ncells;
 }
 
 // labels: int32[N]; codes: uint8[ncells * per]; offsets: int64[ncells];
@@ -264,16 +250,19 @@ cudaError_t launch_simplex_index(const int32_t *labels, const int64_t dims[3], u
   g.div_cy = FastDivU32((uint32_t)g.cy);
   const int64_t nb = (g.ncells + kCellThreads * kSub - 1) / (kCellThreads * kSub);
   unsigned int *btot = reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + 256);
-  unsigned long long *bbase = reinterpret_cast<unsigned long long *>(
-      static_cast<char *>(scratch) + 256 + (((size_t)nb * 4 + 255) & ~(size_t)255));
+  const size_t tot_bytes = ((size_t)nb * 4 + 255) & ~(size_t)255;
+  unsigned long long *bbase =
+      reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + 256 + tot_bytes);
+  uint8_t *counts = static_cast<uint8_t *>(scratch) + 256 + tot_bytes +
+                    (((size_t)nb * 8 + 255) & ~(size_t)255);
   ++tl_launches;
-  k_simplex_codes<<<(unsigned)nb, kCellThreads, 0, s>>>(labels, g, codes, btot);
+  k_simplex_codes<<<(unsigned)nb, kCellThreads, 0, s>>>(labels, g, codes, counts, btot);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ++tl_launches;
   k_scan_blocks<<<1, 1024, 0, s>>>(btot, nb, bbase, total);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ++tl_launches;
-  k_simplex_offsets<<<(unsigned)nb, kCellThreads, 0, s>>>(codes, g, bbase, offsets);
+  k_simplex_offsets<<<(unsigned)nb, kCellThreads, 0, s>>>(counts, g, bbase, offsets);
   return cudaGetLastError();
 }
 
