@@ -65,11 +65,15 @@ struct RankScratch {
   int32_t *table_vals;             // capacity entries
   unsigned long long *list;        // unique keys, up to max_unique
   unsigned long long *tmp;         // sort ping-pong, up to max_unique
-  unsigned int *hist;              // 256 * kSortBlocks
+  unsigned int *hist;              // 256 * sort_blocks_cap
   unsigned int capacity;           // power of two
   unsigned int max_unique;         // capacity / 2
   unsigned int probe_limit;        // longest insert probe before the set counts as full
+  unsigned int sort_blocks_cap;    // most blocks a sort pass may use
 };
+// Sort passes over up to kSortBlocks * 4096 keys use at most kSortBlocks
+// blocks, each computing its digit offsets from the raw histogram; larger
+// sorts use more blocks and a separate scan of the histogram.
 constexpr int kSortBlocks = 240;
 // Insert probes allowed when the set was sized from an estimate: at a load
 // factor of at most one half such a run essentially never happens, and a

@@ -120,6 +120,32 @@ __global__ void k_radix_hist(const unsigned long long *__restrict__ in, unsigned
   hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
 }
 
+// Exclusive scan, in place, of the digit-major histogram hist[d * B + j]:
+// afterwards entry (d, j) is where block j's keys of digit d start.  One
+// block; thread t owns a contiguous chunk.
+__global__ void __launch_bounds__(1024) k_radix_scan(unsigned int *__restrict__ hist,
+                                                     unsigned int n) {
+  __shared__ unsigned int sh[1024];
+  const unsigned int chunk = (n + 1023) / 1024;
+  const unsigned int lo = min(n, threadIdx.x * chunk), hi = min(n, lo + chunk);
+  unsigned int s = 0;
+  for (unsigned int i = lo; i < hi; ++i) s += hist[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const unsigned int t = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0u;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  unsigned int run = sh[threadIdx.x] - s;
+  for (unsigned int i = lo; i < hi; ++i) {
+    const unsigned int v = hist[i];
+    hist[i] = run;
+    run += v;
+  }
+}
+
 // Stable scatter: block j re-reads the chunk it histogrammed, 256 keys at a
 // time; a key's destination is its digit's start (all keys of lower digits)
 // plus the keys of the same digit in earlier blocks, in earlier warps of the
@@ -129,12 +155,17 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const unsigned long long 
                                                        unsigned long long *__restrict__ out,
                                                        unsigned int m, const unsigned int *m_dev,
                                                        int b, int shift,
-                                                       const unsigned int *__restrict__ hist) {
+                                                       const unsigned int *__restrict__ hist,
+                                                       int scanned) {
   m = count_of(m, m_dev);
   __shared__ unsigned int run[256];
   __shared__ unsigned int wcnt[8][256];
   const unsigned int warp = threadIdx.x >> 5, lane = lane_id();
-  {
+  if (scanned) {
+    // k_radix_scan left each (digit, block) its first output position
+    run[threadIdx.x] = hist[threadIdx.x * gridDim.x + blockIdx.x];
+    __syncthreads();
+  } else {
     // digit d = threadIdx.x: total over all blocks, and over blocks before this one
     const unsigned int *row = hist + threadIdx.x * gridDim.x;
     unsigned int tot = 0, before = 0;
@@ -231,10 +262,14 @@ unsigned int grid_n(int64_t n, int per_sm) {
 
 }  // namespace
 
+unsigned int sort_blocks_cap_of(unsigned int capacity) {
+  return std::max<unsigned int>(kSortBlocks, capacity / 2 / 4096);
+}
+
 size_t rank_scratch_bytes(unsigned int capacity) {
   const size_t maxu = capacity / 2;
   return (size_t)capacity * 8 + (size_t)capacity * 4 + maxu * 8 * 2 +
-         256 * (size_t)kSortBlocks * 4 + 4 * 256;
+         256 * (size_t)sort_blocks_cap_of(capacity) * 4 + 4 * 256;
 }
 
 void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs) {
@@ -251,6 +286,7 @@ void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs) {
   rs->table_vals = reinterpret_cast<int32_t *>(p);
   p += (size_t)capacity * 4;
   rs->hist = reinterpret_cast<unsigned int *>(p);
+  rs->sort_blocks_cap = sort_blocks_cap_of(capacity);
 }
 
 cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t n,
@@ -269,14 +305,23 @@ cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bit
   unsigned long long *src = rs.list, *dst = rs.tmp;
   const int b = raw_bits > 0 ? -1 : key_bits;  // bit width of one label, or raw keys
   const int total = raw_bits > 0 ? raw_bits : 2 * key_bits;
-  // enough blocks to spread the keys, few enough that each block's offset
-  // computation (a pass over its digit's row) stays small
-  const unsigned int blocks = std::max(1u, std::min((unsigned)kSortBlocks, (m + 4095) / 4096));
+  // small sorts: enough blocks to spread the keys, few enough that each
+  // block's offset computation (a pass over its digit's row) stays small;
+  // large ones: 2048 keys a block (up to 8 blocks an SM) and a scan launch
+  unsigned int blocks = std::max(1u, std::min((unsigned)kSortBlocks, (m + 4095) / 4096));
+  const bool large = (m + 4095) / 4096 > (unsigned)kSortBlocks;
+  if (large)
+    blocks = std::max(1u, std::min({rs.sort_blocks_cap, (m + 2047) / 2048,
+                                    (unsigned)sm_count() * 8}));
   for (int shift = 0; shift < total; shift += 8) {
     ++tl_launches;
     k_radix_hist<<<blocks, 256, 0, s>>>(src, m, m_dev, b, shift, rs.hist);
+    if (large) {
+      ++tl_launches;
+      k_radix_scan<<<1, 1024, 0, s>>>(rs.hist, 256 * blocks);
+    }
     ++tl_launches;
-    k_radix_scatter<<<blocks, 256, 0, s>>>(src, dst, m, m_dev, b, shift, rs.hist);
+    k_radix_scatter<<<blocks, 256, 0, s>>>(src, dst, m, m_dev, b, shift, rs.hist, large ? 1 : 0);
     unsigned long long *t = src;
     src = dst;
     dst = t;

@@ -156,7 +156,7 @@ def test_compress_cycle_is_not_converged(ctx):
 
 # ------------------------------------------------------------- step 4: MS ids
 @pytest.mark.parametrize("n,levels", [(1, 1), (5000, 3), (300000, 50), (300000, 300000),
-                                      (2000000, 40000)])
+                                      (2000000, 40000), (6000000, 6000000)])
 def test_pair_rank_matches_oracle(ctx, n, levels):
     g = sf.rng_for(n + levels)
     a = g.integers(0, min(levels, n), n).astype(np.int32)
