@@ -437,7 +437,7 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
   // in O(log) rounds over all face slots.
   StageTimer t2(c, MS_STAGE_RESOLVE);
   const uint64_t exact = 2 * npairs + 2;
-  uint64_t want = c->last_k ? 4 * (uint64_t)c->last_k : npairs / 4;
+  uint64_t want = c->last_k ? 2 * (uint64_t)c->last_k + 4096 : npairs / 4;
   if (want < (1u << 16)) want = 1u << 16;
   if (want > exact) want = exact;
   const long long slots = face_graph_slots(b);
@@ -637,7 +637,7 @@ ms_status capture_plan(ms_ctx *c, const FieldArg *fa, int nf) {
   // capacities: the sizes met, with margins; overflow is detected on the device
   unsigned long long pool_cap = run.npairs + run.npairs / 8 + 4096;
   if (pool_cap > (unsigned long long)sf.total_n) pool_cap = (unsigned long long)sf.total_n;
-  const unsigned int hcap = pow2_at_least(4ull * run.m + 4096);
+  const unsigned int hcap = pow2_at_least(2ull * run.m + 4096);
   s = ensure_buffer(c, &c->tscratch, &c->tscratch_bytes,
                     tiled_scratch_bytes(b.total_tiles, nf, pool_cap));
   if (s != MS_OK) return s;

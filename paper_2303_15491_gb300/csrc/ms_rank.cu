@@ -129,6 +129,7 @@ __global__ void __launch_bounds__(1024) k_radix_scan(unsigned int *__restrict__ 
   const unsigned int chunk = (n + 1023) / 1024;
   const unsigned int lo = min(n, threadIdx.x * chunk), hi = min(n, lo + chunk);
   unsigned int s = 0;
+#pragma unroll 8
   for (unsigned int i = lo; i < hi; ++i) s += hist[i];
   sh[threadIdx.x] = s;
   __syncthreads();
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(1024) k_radix_scan(unsigned int *__restrict__ 
     __syncthreads();
   }
   unsigned int run = sh[threadIdx.x] - s;
+#pragma unroll 8
   for (unsigned int i = lo; i < hi; ++i) {
     const unsigned int v = hist[i];
     hist[i] = run;
@@ -309,7 +311,8 @@ cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bit
   // block's offset computation (a pass over its digit's row) stays small;
   // large ones: 2048 keys a block (up to 8 blocks an SM) and a scan launch
   unsigned int blocks = std::max(1u, std::min((unsigned)kSortBlocks, (m + 4095) / 4096));
-  const bool large = (m + 4095) / 4096 > (unsigned)kSortBlocks;
+  // (the scan launch pays off only when there are many more keys than 240 blocks hold)
+  const bool large = m > (1u << 22) && rs.sort_blocks_cap > (unsigned)kSortBlocks;
   if (large)
     blocks = std::max(1u, std::min({rs.sort_blocks_cap, (m + 2047) / 2048,
                                     (unsigned)sm_count() * 8}));
