@@ -185,6 +185,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest x of all ranks (replicas are timed by the slowest one);
+    x itself without a process group.  gloo groups reduce on the CPU."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    if dist.get_backend() == "gloo":
+        device = "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world_size: int, seconds: float) -> float:
+    """Units all ranks processed per second of the slowest rank (weak
+    scaling: every rank processes the same units)."""
+    return world_size * units_per_rank / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -695,13 +715,9 @@ def main():
     ms.ms_profile_enable(ctx, False)
     barrier()
     torch.cuda.synchronize()
-    elapsed_ms = max(ev0.elapsed_time(ev1), 1e3 * t_host)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(max(ev0.elapsed_time(ev1), 1e3 * t_host), dist, dev)
     ms_per_step = elapsed_ms / args.steps
-    value = ws * n * args.steps / (elapsed_ms / 1e3)
+    value = whole_job_rate(n * args.steps, ws, elapsed_ms / 1e3)
 
     # ---- end to end through ms_segment_host (pinned host memory)
     esz = 2 if w["dtype"] == "f16" else 4
@@ -716,12 +732,8 @@ def main():
         t = time.perf_counter()
         for _ in range(args.e2e_steps):
             ms.ms_segment_host(ctx, h_field, dims, dtype, h_asc, h_desc, h_ms)
-        e2e_s = time.perf_counter() - t
-        if dist is not None:
-            tt = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
-        e2e_value = ws * n * args.e2e_steps / e2e_s
+        e2e_s = max_over_ranks(time.perf_counter() - t, dist, dev)
+        e2e_value = whole_job_rate(n * args.e2e_steps, ws, e2e_s)
 
     # ---- roofline of the dominant kernel and of the whole path
     hbm, peak_kind = peaks()
