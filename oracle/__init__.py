@@ -71,6 +71,10 @@ def lib():
             L.ms_oracle_link_stats.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i32p, i64p]
             L.ms_oracle_simplex_code.argtypes = [ctypes.c_int, i32p, ctypes.POINTER(ctypes.c_int)]
             L.ms_oracle_simplex_index.argtypes = [i32p, i64p, ctypes.c_void_p, i64p, i64p]
+            L.ms_oracle_simplex_index_mode.argtypes = [i32p, i64p, ctypes.c_int, ctypes.c_void_p,
+                                                       i64p, i64p]
+            L.ms_oracle_simplex_geometry.argtypes = [i32p, i64p, ctypes.c_int, ctypes.c_void_p,
+                                                     ctypes.c_void_p, i64p]
             L.ms_oracle_link_stats.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -210,9 +214,10 @@ def simplex_cells(dims):
     return max(nx - 1, 0) * max(ny - 1, 0) * max(nz - 1, 0), 6
 
 
-def simplex_index(labels: np.ndarray, dims):
+def simplex_index(labels: np.ndarray, dims, mode: int = 0):
     """Index pass of the marching triangles / tetrahedra over a label grid:
-    {'codes': uint8 per simplex, 'cell_offsets': int64 per cell, 'total'}."""
+    {'codes': uint8 per simplex, 'cell_offsets': int64 per cell, 'total'};
+    mode 0 counts region separators, mode 1 region boundaries."""
     lab = np.ascontiguousarray(labels, dtype=np.int32).reshape(-1)
     nx, ny, nz = (int(d) for d in dims)
     if lab.size != nx * ny * nz:
@@ -222,7 +227,29 @@ def simplex_index(labels: np.ndarray, dims):
     offs = np.zeros(max(cells, 1), dtype=np.int64)
     total = ctypes.c_int64(0)
     d = (ctypes.c_int64 * 3)(nx, ny, nz)
-    _check(lib().ms_oracle_simplex_index(_ptr32(lab), d, codes.ctypes.data,
-                                         offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                                         ctypes.byref(total)))
+    _check(lib().ms_oracle_simplex_index_mode(_ptr32(lab), d, int(mode), codes.ctypes.data,
+                                              offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                              ctypes.byref(total)))
     return {"codes": codes, "cell_offsets": offs[:cells], "total": int(total.value)}
+
+
+def simplex_geometry(labels: np.ndarray, dims, mode: int = 0):
+    """Geometry pass (Sec. 4.3): mode 0 region separators, mode 1 region
+    boundaries.  {'pos': float32 (total, points, dim), 'pairs': int32
+    (total, 2), 'total'}."""
+    lab = np.ascontiguousarray(labels, dtype=np.int32).reshape(-1)
+    nx, ny, nz = (int(d) for d in dims)
+    d = (ctypes.c_int64 * 3)(nx, ny, nz)
+    total = ctypes.c_int64(0)
+    _check(lib().ms_oracle_simplex_geometry(_ptr32(lab), d, int(mode), None, None,
+                                            ctypes.byref(total)))
+    dim = 2 if nz == 1 else 3
+    npts = 2 if nz == 1 else 3
+    n = int(total.value)
+    pos = np.zeros((max(n, 1), npts, dim), dtype=np.float32)
+    pairs = np.zeros((max(n, 1), 2), dtype=np.int32)
+    _check(lib().ms_oracle_simplex_geometry(_ptr32(lab), d, int(mode), pos.ctypes.data,
+                                            pairs.ctypes.data, ctypes.byref(total)))
+    assert int(total.value) == n
+    return {"pos": pos[:n], "pairs": pairs[:n], "total": n}
+

@@ -551,8 +551,21 @@ int ms_oracle_simplex_code(int nverts, const int32_t *labels, int *count) {
  * sum over cells of the cell's element count (sum over its simplices);
  * *total: the sum over all cells.  Grids with a dimension of extent 1 other
  * than nz (2D is nz == 1) have no cells. */
+int ms_oracle_simplex_count_mode(int nverts, const int32_t *labels, int mode);
+static int count_of_mode(int nverts, const int32_t *labels, int mode);
+
+int ms_oracle_simplex_index_mode(const int32_t *labels, const int64_t dims[3], int mode,
+                                 uint8_t *codes, int64_t *cell_offsets, int64_t *total);
+
 int ms_oracle_simplex_index(const int32_t *labels, const int64_t dims[3], uint8_t *codes,
                             int64_t *cell_offsets, int64_t *total) {
+  return ms_oracle_simplex_index_mode(labels, dims, 0, codes, cell_offsets, total);
+}
+
+/* mode 0: separator elements per cell; mode 1: boundary elements */
+int ms_oracle_simplex_index_mode(const int32_t *labels, const int64_t dims[3], int mode,
+                                 uint8_t *codes, int64_t *cell_offsets, int64_t *total) {
+  if (mode != 0 && mode != 1) return OR_ERR_ARG;
   const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
   if (nx < 1 || ny < 1 || nz < 1) return OR_ERR_ARG;
   const int two_d = nz == 1;
@@ -571,7 +584,8 @@ int ms_oracle_simplex_index(const int32_t *labels, const int64_t dims[3], uint8_
               const int64_t va = v0, vb = va + step[p][0], vc = vb + step[p][1];
               const int code = tri_code(labels[va], labels[vb], labels[vc]);
               codes[2 * c + p] = (uint8_t)code;
-              cell_count += tri_count(code);
+              const int32_t lab3[3] = {labels[va], labels[vb], labels[vc]};
+              cell_count += mode == 0 ? tri_count(code) : count_of_mode(3, lab3, 1);
             }
           } else {
             const int64_t ax[3] = {1, nx, nx * ny};
@@ -586,7 +600,7 @@ int ms_oracle_simplex_index(const int32_t *labels, const int64_t dims[3], uint8_
               }
               const int code = tet_code(lab);
               codes[6 * c + p] = (uint8_t)code;
-              cell_count += tet_count(code);
+              cell_count += mode == 0 ? tet_count(code) : count_of_mode(4, lab, 1);
             }
           }
           cell_offsets[c] = run;
@@ -594,5 +608,265 @@ int ms_oracle_simplex_index(const int32_t *labels, const int64_t dims[3], uint8_
         }
   }
   *total = run;
+  return OR_OK;
+}
+
+/* ---- the geometry pass of the multi-label marching triangles / tetrahedra --
+ *
+ * Sec. 4.3 ("Region Separating Geometries"), after the index pass:
+ *
+ *  mode 0, region separators (Figs. 5, 6): in a simplex with several labels,
+ *   triangle, labels 2+1: one segment joining the midpoints of the two edges at
+ *     the lone vertex; 3 labels: three segments from the triangle's centre to
+ *     its edge midpoints (ab, bc, ac);
+ *   tetrahedron, 3+1: the triangle of the midpoints of the three edges at the
+ *     lone vertex; 2+2 (pairs {p1,p2}, {q1,q2}): the quad of the midpoints of
+ *     the four edges between the pairs, as triangles (p1q1, p1q2, p2q1),
+ *     (p1q2, p2q1, p2q2); 2+1+1 (pair P < Q, singles R < S): with T1, T2 the
+ *     centres of the faces PRS, QRS: (T1,T2,PR), (T2,PR,QR), (T1,T2,RS),
+ *     (T1,T2,PS), (T2,PS,QS); four labels: from the tetrahedron's centre C,
+ *     for each face (abc, abd, acd, bcd) with centre T and each of its edges
+ *     e (in the order ab, ac, ad, bc, bd, cd): (C, T, e).
+ *   Each element separates the labels at the two ends of its first edge
+ *   midpoint's edge; the pair is stored smaller label first.
+ *  mode 1, region boundaries: a tetrahedron with exactly three vertices of one
+ *   label gives the triangle of those three vertices (stored in chain order),
+ *   separating (that label, the fourth vertex's label), smaller first; a
+ *   triangle (2D) with exactly two vertices of one label gives that edge.
+ *
+ * Element order: cells in index order, simplices in chain order p, elements
+ * in the order above.  Points are grid coordinates (x, y[, z]) in float32:
+ * a midpoint is (u + v) / 2, a face centre (u + v + w) / 3, the tetrahedron
+ * centre the sum of its corners / 4, each coordinate's sum formed exactly
+ * before one rounded division.
+ */
+
+typedef struct {
+  float *pos;      /* dim floats per point */
+  int32_t *pairs;  /* 2 per element (may be NULL) */
+  int dim, npts;   /* coordinates per point, points per element */
+  int64_t at;      /* next element */
+} geo_out;
+
+static void geo_point(geo_out *o, int k, const int64_t (*c)[3], const int *ids, int nids) {
+  for (int d = 0; d < o->dim; ++d) {
+    int64_t sum = 0;
+    for (int i = 0; i < nids; ++i) sum += c[ids[i]][d];
+    o->pos[(o->at * o->npts + k) * o->dim + d] = (float)sum / (float)nids;
+  }
+}
+
+static void geo_pair(geo_out *o, int32_t l1, int32_t l2) {
+  if (o->pairs) {
+    o->pairs[2 * o->at] = l1 < l2 ? l1 : l2;
+    o->pairs[2 * o->at + 1] = l1 < l2 ? l2 : l1;
+  }
+}
+
+/* one element whose points are the centroids of the index sets ids[k] */
+static void geo_elem(geo_out *o, const int64_t (*c)[3], const int (*ids)[4], const int *nids,
+                     int32_t l1, int32_t l2) {
+  for (int k = 0; k < o->npts; ++k) geo_point(o, k, c, ids[k], nids[k]);
+  geo_pair(o, l1, l2);
+  o->at++;
+}
+
+static void tri_separators(geo_out *o, const int64_t (*c)[3], const int32_t *lab) {
+  const int code = tri_code(lab[0], lab[1], lab[2]);
+  const int b = code >> 2, cc = code & 3;
+  if (code == 0) return;
+  if (code == 6) {
+    const int e[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+    for (int k = 0; k < 3; ++k) {
+      const int ids[2][4] = {{0, 1, 2}, {e[k][0], e[k][1]}};
+      const int n[2] = {3, 2};
+      geo_elem(o, c, ids, n, lab[e[k][0]], lab[e[k][1]]);
+    }
+    return;
+  }
+  /* two labels: the lone vertex */
+  const int loc[3] = {0, b, cc};
+  int lone = -1;
+  for (int k = 0; k < 3; ++k) {
+    int same = 0;
+    for (int j = 0; j < 3; ++j) same += loc[j] == loc[k];
+    if (same == 1) lone = k;
+  }
+  int oth[2], no = 0;
+  for (int k = 0; k < 3; ++k)
+    if (k != lone) oth[no++] = k;
+  const int ids[2][4] = {{lone, oth[0]}, {lone, oth[1]}};
+  const int n[2] = {2, 2};
+  geo_elem(o, c, ids, n, lab[lone], lab[oth[0]]);
+}
+
+static void tet_separators(geo_out *o, const int64_t (*c)[3], const int32_t *lab) {
+  const int code = tet_code(lab);
+  const int loc[4] = {0, code >> 4, (code >> 2) & 3, code & 3};
+  int size[4] = {0, 0, 0, 0};
+  for (int k = 0; k < 4; ++k) size[loc[k]]++;
+  int classes = 0;
+  for (int k = 0; k < 4; ++k) classes += size[k] > 0;
+  const int n3[3] = {2, 2, 2};
+  if (classes == 1) return;
+  if (classes == 2) {
+    int big = 0;
+    for (int k = 0; k < 4; ++k)
+      if (size[k] > size[big]) big = k;
+    if (size[big] == 3) {
+      int lone = 0, oth[3], no = 0;
+      for (int k = 0; k < 4; ++k) {
+        if (loc[k] != big) lone = k;
+        else oth[no++] = k;
+      }
+      const int ids[3][4] = {{lone, oth[0]}, {lone, oth[1]}, {lone, oth[2]}};
+      geo_elem(o, c, ids, n3, lab[lone], lab[oth[0]]);
+    } else {
+      int p[2], q[2], np = 0, nq = 0;
+      for (int k = 0; k < 4; ++k) {
+        if (loc[k] == 0) p[np++] = k;
+        else q[nq++] = k;
+      }
+      const int t1[3][4] = {{p[0], q[0]}, {p[0], q[1]}, {p[1], q[0]}};
+      const int t2[3][4] = {{p[0], q[1]}, {p[1], q[0]}, {p[1], q[1]}};
+      geo_elem(o, c, t1, n3, lab[p[0]], lab[q[0]]);
+      geo_elem(o, c, t2, n3, lab[p[0]], lab[q[1]]);
+    }
+    return;
+  }
+  if (classes == 3) {
+    int P = -1, Q = -1, R = -1, S = -1;
+    for (int k = 0; k < 4; ++k) {
+      if (size[loc[k]] == 2) {
+        if (P < 0) P = k;
+        else Q = k;
+      } else {
+        if (R < 0) R = k;
+        else S = k;
+      }
+    }
+    const int n[3] = {3, 3, 2}, nb[3] = {3, 2, 2};
+    {
+      const int ids[3][4] = {{P, R, S}, {Q, R, S}, {P, R}};  /* T1, T2, PR */
+      geo_elem(o, c, ids, n, lab[P], lab[R]);
+    }
+    {
+      const int ids[3][4] = {{Q, R, S}, {P, R}, {Q, R}};  /* T2, PR, QR */
+      geo_elem(o, c, ids, nb, lab[P], lab[R]);
+    }
+    {
+      const int ids[3][4] = {{P, R, S}, {Q, R, S}, {R, S}};  /* T1, T2, RS */
+      geo_elem(o, c, ids, n, lab[R], lab[S]);
+    }
+    {
+      const int ids[3][4] = {{P, R, S}, {Q, R, S}, {P, S}};  /* T1, T2, PS */
+      geo_elem(o, c, ids, n, lab[P], lab[S]);
+    }
+    {
+      const int ids[3][4] = {{Q, R, S}, {P, S}, {Q, S}};  /* T2, PS, QS */
+      geo_elem(o, c, ids, nb, lab[P], lab[S]);
+    }
+    return;
+  }
+  /* four labels */
+  const int faces[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+  for (int f = 0; f < 4; ++f) {
+    const int e[3][2] = {{faces[f][0], faces[f][1]}, {faces[f][0], faces[f][2]},
+                         {faces[f][1], faces[f][2]}};
+    for (int k = 0; k < 3; ++k) {
+      const int ids[3][4] = {{0, 1, 2, 3}, {faces[f][0], faces[f][1], faces[f][2]}, {e[k][0], e[k][1]}};
+      const int n[3] = {4, 3, 2};
+      geo_elem(o, c, ids, n, lab[e[k][0]], lab[e[k][1]]);
+    }
+  }
+}
+
+static void boundaries(geo_out *o, const int64_t (*c)[3], const int32_t *lab, int nv) {
+  /* the vertices sharing a label that exactly nv - 1 of them carry */
+  for (int lone = 0; lone < nv; ++lone) {
+    int same = 0;
+    for (int k = 0; k < nv; ++k)
+      if (k != lone && lab[k] == lab[(lone + 1) % nv]) ++same;
+    int all_same = same == nv - 1, lone_differs = lab[lone] != lab[(lone + 1) % nv];
+    if (all_same && lone_differs) {
+      int ids[3][4], n[3], m = 0;
+      for (int k = 0; k < nv; ++k)
+        if (k != lone) {
+          ids[m][0] = k;
+          n[m++] = 1;
+        }
+      geo_elem(o, c, ids, n, lab[(lone + 1) % nv], lab[lone]);
+      return;
+    }
+  }
+}
+
+static int count_of_mode(int nverts, const int32_t *labels, int mode) {
+  return ms_oracle_simplex_count_mode(nverts, labels, mode);
+}
+
+int ms_oracle_simplex_count_mode(int nverts, const int32_t *labels, int mode) {
+  int cnt = 0;
+  if (mode == 0) {
+    ms_oracle_simplex_code(nverts, labels, &cnt);
+    return cnt;
+  }
+  for (int lone = 0; lone < nverts; ++lone) {
+    int same = 0;
+    for (int k = 0; k < nverts; ++k)
+      if (k != lone && labels[k] == labels[(lone + 1) % nverts]) ++same;
+    if (same == nverts - 1 && labels[lone] != labels[(lone + 1) % nverts]) return 1;
+  }
+  return 0;
+}
+
+/* Elements of every simplex in order (see above); pos: total * npts * dim
+ * floats, pairs: total * 2 int32 (may be NULL).  *total receives the count;
+ * with pos == NULL only the count is computed. */
+int ms_oracle_simplex_geometry(const int32_t *labels, const int64_t dims[3], int mode, float *pos,
+                               int32_t *pairs, int64_t *total) {
+  const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+  if (nx < 1 || ny < 1 || nz < 1 || (mode != 0 && mode != 1)) return OR_ERR_ARG;
+  const int two_d = nz == 1;
+  const int64_t cx = nx - 1, cy = ny - 1, cz = two_d ? 1 : nz - 1;
+  geo_out o;
+  o.pos = pos;
+  o.pairs = pairs;
+  o.dim = two_d ? 2 : 3;
+  o.npts = two_d ? 2 : 3;
+  o.at = 0;
+  int64_t count = 0;
+  if (cx > 0 && cy > 0 && cz > 0) {
+    for (int64_t z = 0; z < cz; ++z)
+      for (int64_t y = 0; y < cy; ++y)
+        for (int64_t x = 0; x < cx; ++x) {
+          const int nv = two_d ? 3 : 4;
+          const int np = two_d ? 2 : 6;
+          const int order[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+          for (int p = 0; p < np; ++p) {
+            int64_t c[4][3];
+            int32_t lab[4];
+            int64_t pt[3] = {x, y, z};
+            for (int k = 0; k < nv; ++k) {
+              if (k > 0) pt[two_d ? (p == 0 ? k - 1 : 2 - k) : order[p][k - 1]] += 1;
+              c[k][0] = pt[0];
+              c[k][1] = pt[1];
+              c[k][2] = pt[2];
+              lab[k] = labels[pt[0] + nx * (pt[1] + ny * pt[2])];
+            }
+            if (!pos) {
+              count += ms_oracle_simplex_count_mode(nv, lab, mode);
+              continue;
+            }
+            if (mode == 1)
+              boundaries(&o, (const int64_t(*)[3])c, lab, nv);
+            else if (two_d)
+              tri_separators(&o, (const int64_t(*)[3])c, lab);
+            else
+              tet_separators(&o, (const int64_t(*)[3])c, lab);
+          }
+        }
+  }
+  *total = pos ? o.at : count;
   return OR_OK;
 }
