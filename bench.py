@@ -590,6 +590,21 @@ def run_index_bench(args):
     kern_ms = prof["stages"]["tile_local"]["ms"] / max(1, prof["calls"])
     hbm, peak_kind = peaks()
     alg = 18 * cells
+    # the geometry pass (region separators) into the slots the index pass made:
+    # labels and offsets in, 9 floats + 2 labels out per triangle
+    pts = torch.empty((total, 3, 3), dtype=torch.float32, device=dev)
+    prs = torch.empty((total, 2), dtype=torch.int32, device=dev)
+    for _ in range(2):
+        ms.ms_simplex_geometry(ctx, labels, dims, offs, total, pts, prs)
+    ms.ms_profile_enable(ctx, True)
+    geo_steps = max(1, args.steps // 4)
+    for _ in range(geo_steps):
+        ms.ms_simplex_geometry(ctx, labels, dims, offs, total, pts, prs)
+    gprof = ms.ms_profile_read(ctx)
+    ms.ms_profile_enable(ctx, False)
+    geo_ms = gprof["stages"]["write"]["ms"] / max(1, gprof["calls"])
+    geo_bytes = 12 * cells + 44 * total
+    del pts, prs
     # CPU baseline: the oracle on a z-slab of the labels
     import oracle
 
@@ -612,6 +627,11 @@ def run_index_bench(args):
                      "frac": alg / (kern_ms / 1e3) / 1e9 / hbm, "traffic": None,
                      "alg_bytes_per_cell": 18, "avg_launch_ms": kern_ms},
         "gpu_launches": prof["launches"],
+        "geometry": {"kernel": "region separators", "ms": geo_ms, "triangles": total,
+                     "alg_bytes": geo_bytes, "achieved_gbs": geo_bytes / (geo_ms / 1e3) / 1e9,
+                     "frac": geo_bytes / (geo_ms / 1e3) / 1e9 / hbm,
+                     "note": "labels 4 B + offset 8 B per cell in, 36 B of points + 8 B of labels "
+                             "per triangle out"},
         "cpu_baseline": {"value": 511 * 511 * (slab - 1) * per / cpu_s, "unit": "tetrahedra/s", "cores": 1,
                          "kind": "oracle", "sample": f"512x512x{slab} slab ({cpu_s:.1f} s single-threaded)"},
         "clocks": clk.summary(),

@@ -209,14 +209,44 @@ ms_status ms_batch_graphs(ms_ctx *ctx, int on);
  *   3 by 3; a tetrahedron whose labels split 3+1 by 1 triangle, 2+2 by 2,
  *   2+1+1 by 5, 1+1+1+1 by 12.
  * labels: int32[nx*ny*nz] (any segmentation: ms, asc or desc ids) on the
- * device; codes: uint8[cells * (2 or 6)] on the device, 16-byte aligned;
- * cell_offsets: int64[cells] on the device, the exclusive prefix sum of the
- * cells' element counts; *total (host, may be NULL): the element total.
- * Grids without cells (an extent of 1 other than nz) give *total = 0 and
- * touch no output.  Errors: MS_ERR_INVALID_ARG, MS_ERR_TOO_LARGE,
- * MS_ERR_OUT_OF_MEMORY, MS_ERR_CUDA. */
-ms_status ms_simplex_index(ms_ctx *ctx, const int32_t *labels, const int64_t dims[3],
+ * device; mode: which elements are counted -- 0 region separators (the counts
+ * above), 1 region boundaries (one per simplex whose labels split 3+1, 2D:
+ * 2+1; see ms_simplex_geometry); codes: uint8[cells * (2 or 6)] on the
+ * device, 16-byte aligned; cell_offsets: int64[cells] on the device, the
+ * exclusive prefix sum of the cells' element counts; *total (host, may be
+ * NULL): the element total.  Grids without cells (an extent of 1 other than
+ * nz) give *total = 0 and touch no output.  Errors: MS_ERR_INVALID_ARG,
+ * MS_ERR_TOO_LARGE, MS_ERR_OUT_OF_MEMORY, MS_ERR_CUDA. */
+ms_status ms_simplex_index(ms_ctx *ctx, const int32_t *labels, const int64_t dims[3], int mode,
                            uint8_t *codes, int64_t *cell_offsets, int64_t *total);
+
+/* Sec. 4.3, the region-separating geometry, written where ms_simplex_index
+ * (same labels, dims and mode) put each cell's elements.
+ *   mode 0, region separators (Figs. 5, 6): triangle, 2 labels: the segment
+ *   joining the midpoints of the lone corner's edges; 3 labels: segments from
+ *   the centre to the midpoints of ab, bc, ac.  Tetrahedron, 3+1: the
+ *   triangle of the midpoints of the lone corner's edges; 2+2 ({p0,p1} holds
+ *   corner a, {q0,q1} the rest): (p0q0, p0q1, p1q0), (p0q1, p1q0, p1q1);
+ *   2+1+1 (pair P < Q, singles R < S, T1 / T2 the centres of faces PRS /
+ *   QRS): (T1,T2,PR), (T2,PR,QR), (T1,T2,RS), (T1,T2,PS), (T2,PS,QS); four
+ *   labels: (centre, face centre, edge midpoint) for the faces abc, abd,
+ *   acd, bcd and each face's edges in the order first-second, first-third,
+ *   second-third.  An element separates the labels at the ends of its
+ *   midpoint's edge (the first midpoint's, for 3+1 / 2+2 / 2+1 elements).
+ *   mode 1, region boundaries: the triangle (2D: edge) of the corners that
+ *   share the label all but one corner carry, in chain order; it separates
+ *   that label from the remaining corner's.
+ * Points are grid coordinates, float32: a midpoint is (u+v)/2, a face
+ * centre (u+v+w)/3, the centre the corners' sum / 4, each coordinate's sum
+ * formed exactly and divided once, rounded to nearest.
+ * points: float[total * 3 * 3] (3D: three xyz points per triangle) or
+ * float[total * 2 * 2] (2D: two xy points per segment), device; pairs:
+ * int32[total * 2] (smaller label first), device, or NULL.  total: the value
+ * ms_simplex_index returned.  MS_ERR_INVALID_ARG also when the offsets or
+ * total do not match the labels (nothing is written outside the ranges). */
+ms_status ms_simplex_geometry(ms_ctx *ctx, const int32_t *labels, const int64_t dims[3], int mode,
+                              const int64_t *cell_offsets, int64_t total, float *points,
+                              int32_t *pairs);
 
 /* ---- serving ---------------------------------------------------------------- */
 

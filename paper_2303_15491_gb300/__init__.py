@@ -26,7 +26,8 @@ __all__ = [
     "ms_profile_read", "ms_profile_stage_name", "STAGES", "ms_segment_staged",
     "ms_pair_rank_noalloc", "MS_NOALLOC_MAX_N", "ms_segment_batch", "ms_server_create",
     "ms_server_submit", "ms_server_wait", "ms_server_stats", "ms_server_destroy",
-    "ms_batch_autotune", "ms_batch_graphs", "ms_simplex_index", "simplex_cells",
+    "ms_batch_autotune", "ms_batch_graphs", "ms_simplex_index", "ms_simplex_geometry",
+    "simplex_cells",
 ]
 
 MS_F32, MS_F16 = 0, 1
@@ -40,7 +41,7 @@ EXPORTED_SYMBOLS = [
     "ms_profile_enable", "ms_profile_read", "ms_profile_stage_name", "ms_segment_staged",
     "ms_pair_rank_noalloc", "ms_segment_batch", "ms_server_create", "ms_server_submit",
     "ms_server_wait", "ms_server_stats", "ms_server_destroy", "ms_batch_autotune",
-    "ms_batch_graphs", "ms_simplex_index",
+    "ms_batch_graphs", "ms_simplex_index", "ms_simplex_geometry",
 ]
 MS_NOALLOC_MAX_N = 262144
 
@@ -98,7 +99,9 @@ def load(build: bool = True) -> ctypes.CDLL:
             L.ms_batch_autotune.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                             ctypes.POINTER(_Tuning)]
             L.ms_batch_graphs.argtypes = [c_vp, ctypes.c_int]
-            L.ms_simplex_index.argtypes = [c_vp, c_vp, c_i64p, c_vp, c_vp, c_i64p]
+            L.ms_simplex_index.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_i64p]
+            L.ms_simplex_geometry.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, ctypes.c_int64,
+                                              c_vp, c_vp]
             L.ms_server_create.argtypes = [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_size_t,
                                            ctypes.c_int]
             L.ms_server_submit.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp,
@@ -223,13 +226,20 @@ def ms_batch_autotune(ctx, fields, dims_list, dtypes, ascs, descs, mss) -> dict:
     return {f: getattr(t, f) for f, _ in _Tuning._fields_}
 
 
-def ms_simplex_index(ctx, labels, dims, codes, cell_offsets) -> int:
+def ms_simplex_index(ctx, labels, dims, codes, cell_offsets, mode: int = 0) -> int:
     """Index pass of the marching triangles / tetrahedra (see ms.h); returns
-    the total number of separating elements."""
+    the total number of elements (mode 0 separators, 1 boundaries)."""
     t = ctypes.c_int64(0)
-    _check(load().ms_simplex_index(ctx, _ptr(labels), _dims(dims), _ptr(codes), _ptr(cell_offsets),
-                                   ctypes.byref(t)), "ms_simplex_index")
+    _check(load().ms_simplex_index(ctx, _ptr(labels), _dims(dims), int(mode), _ptr(codes),
+                                   _ptr(cell_offsets), ctypes.byref(t)), "ms_simplex_index")
     return int(t.value)
+
+
+def ms_simplex_geometry(ctx, labels, dims, cell_offsets, total, points, pairs=None,
+                        mode: int = 0) -> None:
+    """Geometry pass (see ms.h) into points (and pairs, optional)."""
+    _check(load().ms_simplex_geometry(ctx, _ptr(labels), _dims(dims), int(mode), _ptr(cell_offsets),
+                                      int(total), _ptr(points), _ptr(pairs)), "ms_simplex_geometry")
 
 
 def simplex_cells(dims):

@@ -987,9 +987,9 @@ ms_status ms_segment_batch(ms_ctx *c, int n_fields, const void *const *fields,
   return s;
 }
 
-ms_status ms_simplex_index(ms_ctx *c, const int32_t *labels, const int64_t dims[3],
+ms_status ms_simplex_index(ms_ctx *c, const int32_t *labels, const int64_t dims[3], int mode,
                            uint8_t *codes, int64_t *cell_offsets, int64_t *total) {
-  if (!c || !labels) return MS_ERR_INVALID_ARG;
+  if (!c || !labels || (mode != 0 && mode != 1)) return MS_ERR_INVALID_ARG;
   int64_t n = 0;
   ms_status s = check_dims(dims, &n);
   if (s != MS_OK) return s;
@@ -1011,13 +1011,45 @@ ms_status ms_simplex_index(ms_ctx *c, const int32_t *labels, const int64_t dims[
   unsigned long long *tot_dev = nullptr;
   int64_t nc = 0;
   StageTimer t0(c, MS_STAGE_TILE_LOCAL);
-  MS_TRY(launch_simplex_index(labels, dims, codes, cell_offsets, c->sxscratch, &tot_dev, &nc,
+  MS_TRY(launch_simplex_index(labels, dims, mode, codes, cell_offsets, c->sxscratch, &tot_dev, &nc,
                               c->stream));
   t0.stop();
   MS_TRY(cudaMemcpyAsync(c->hcount, tot_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                          c->stream));
   MS_TRY(cudaStreamSynchronize(c->stream));
   if (total) *total = (int64_t)*c->hcount;
+  finish_profile(c, l0);
+  return MS_OK;
+}
+
+ms_status ms_simplex_geometry(ms_ctx *c, const int32_t *labels, const int64_t dims[3], int mode,
+                              const int64_t *cell_offsets, int64_t total, float *points,
+                              int32_t *pairs) {
+  if (!c || !labels || (mode != 0 && mode != 1) || total < 0) return MS_ERR_INVALID_ARG;
+  int64_t n = 0;
+  ms_status s = check_dims(dims, &n);
+  if (s != MS_OK) return s;
+  DeviceGuard g(c->device);
+  const bool flat = dims[2] == 1;
+  const int64_t cz = flat ? 1 : dims[2] - 1;
+  const int64_t cells = (dims[0] > 1 && dims[1] > 1 && cz > 0) ? (dims[0] - 1) * (dims[1] - 1) * cz : 0;
+  if (cells == 0) return total == 0 ? MS_OK : MS_ERR_INVALID_ARG;
+  if (!is_device_pointer(labels) || !is_device_pointer(cell_offsets) ||
+      (total > 0 && !is_device_pointer(points)) || (pairs && !is_device_pointer(pairs)))
+    return MS_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(points) & 3) || (reinterpret_cast<uintptr_t>(pairs) & 3) ||
+      (reinterpret_cast<uintptr_t>(cell_offsets) & 7))
+    return MS_ERR_INVALID_ARG;
+  const long long l0 = tl_launches;
+  s = reset_status(c);
+  if (s != MS_OK) return s;
+  StageTimer t0(c, MS_STAGE_WRITE);
+  MS_TRY(launch_simplex_geometry(labels, dims, mode, cell_offsets, total, points, pairs, c->dst,
+                                 c->stream));
+  t0.stop();
+  s = read_status(c);
+  if (s != MS_OK) return s;
+  if (c->hst->bad_index) return MS_ERR_INVALID_ARG;  // offsets or total do not match the labels
   finish_profile(c, l0);
   return MS_OK;
 }

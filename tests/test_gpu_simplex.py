@@ -126,3 +126,49 @@ def test_full_size_512(ctx):
     assert int(offs[0]) == 0
     assert bool(torch.equal(offs[1:] - offs[:-1], counts[:-1]))
     assert total == int(offs[-1] + counts[-1])
+
+
+# ---------------------------------------------------------------- geometry
+def gpu_geometry(ctx, labels, dims, mode):
+    cells, per = ms.simplex_cells(dims)
+    lab = torch.from_numpy(np.ascontiguousarray(labels, dtype=np.int32).reshape(-1)).cuda()
+    codes = torch.empty(max(cells * per, 1), dtype=torch.uint8, device="cuda")
+    offs = torch.empty(max(cells, 1), dtype=torch.int64, device="cuda")
+    total = ms.ms_simplex_index(ctx, lab, dims, codes, offs, mode)
+    dim = 2 if dims[2] == 1 else 3
+    pts = torch.full((max(total, 1), dim, dim), float("nan"), dtype=torch.float32, device="cuda")
+    pairs = torch.full((max(total, 1), 2), -1, dtype=torch.int32, device="cuda")
+    ms.ms_simplex_geometry(ctx, lab, dims, offs, total, pts, pairs, mode)
+    return total, pts[:total].cpu().numpy(), pairs[:total].cpu().numpy(), offs[:cells].cpu().numpy()
+
+
+@pytest.mark.parametrize("dims", [(30, 26, 22), (2, 2, 2), (140, 90, 1), (33, 17, 9)])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_geometry_matches_oracle(ctx, dims, mode):
+    f = sf.smoothed_noise(dims, 23, sigma=2.0)
+    if dims[2] == 1:
+        f = f[0]
+    _, _, m, _ = gpu_segment(ctx, f)
+    for name, lab in (("ms", m), ("random 4", np.random.default_rng(1).integers(0, 4, m.size))):
+        ref = oracle.simplex_geometry(lab, dims, mode)
+        iref = oracle.simplex_index(lab, dims, mode)
+        total, pts, pairs, offs = gpu_geometry(ctx, lab, dims, mode)
+        assert total == ref["total"] == iref["total"]
+        assert np.array_equal(offs, iref["cell_offsets"])
+        assert np.array_equal(pts, ref["pos"]), f"{dims} {name} mode {mode}: points differ"
+        assert np.array_equal(pairs, ref["pairs"]), f"{dims} {name} mode {mode}: pairs differ"
+
+
+def test_geometry_rejects_a_wrong_total(ctx):
+    dims = (10, 9, 8)
+    lab = np.random.default_rng(2).integers(0, 3, 720).astype(np.int32)
+    cells, per = ms.simplex_cells(dims)
+    dl = torch.from_numpy(lab).cuda()
+    codes = torch.empty(cells * per, dtype=torch.uint8, device="cuda")
+    offs = torch.empty(cells, dtype=torch.int64, device="cuda")
+    total = ms.ms_simplex_index(ctx, dl, dims, codes, offs)
+    pts = torch.empty((total, 3, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(ms.MSError) as e:
+        ms.ms_simplex_geometry(ctx, dl, dims, offs, total - 1, pts)
+    assert e.value.name == "MS_ERR_INVALID_ARG"
+    ms.ms_simplex_geometry(ctx, dl, dims, offs, total, pts)  # without pairs
