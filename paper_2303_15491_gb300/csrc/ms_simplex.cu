@@ -239,43 +239,40 @@ __global__ void __launch_bounds__(kCellThreads) k_simplex_offsets(const uint8_t 
 
 // ---- geometry pass ---------------------------------------------------------
 //
-// Points of an element are subsets of its simplex's corners, as bit masks
-// (bit k = corner k in chain order): a midpoint has two bits, a face centre
-// three, the tetrahedron centre four; the point is the subset's mean, each
-// coordinate's sum formed exactly and divided once with IEEE rounding.
-struct GeoOut {
-  float *pos;
-  int32_t *pairs;
-  int64_t at, end;  // next element, end of this cell's range
-  int npts, dim;
-  bool overrun;
-};
+// A simplex's elements depend on its code only.  Each block first tabulates,
+// for all 32 codes, the elements as corner subsets: a point of an element is
+// the mean of a subset of the simplex's corners (bit k = corner k in chain
+// order: a midpoint has two bits, a face centre three, the tetrahedron centre
+// four), and an element names the two corners whose labels it separates.
+// Each coordinate's sum is formed exactly and divided once with IEEE rounding.
+//
+// The pass then takes chunks of 32 cells per warp.  A chunk's elements are one
+// contiguous range of the output (the index pass's offsets); they are handed
+// out 32 at a time, one per lane, so that the lanes do equal work whatever the
+// cells' element counts.  A lane finds its element's cell by a binary search
+// over the chunk's running counts and the simplex by the cell's per-simplex
+// counts, writes the points to a shared-memory window, and the warp stores
+// the window as consecutive words.
+constexpr int kMaxElems = 12;  // four labels in a tetrahedron
+constexpr int kGeoThreads = 256;
 
-__device__ __forceinline__ void put(GeoOut &o, const int (*cc)[3], const unsigned (&m)[3],
-                                    int32_t l1, int32_t l2) {
-  if (o.at >= o.end) {
-    o.overrun = true;
-    return;
+// Element descriptor: point masks m0 | m1 << 4 | m2 << 8, separated corners
+// i << 12 | j << 14 (m2 = 0 for a segment).
+struct ElemRecorder {
+  uint32_t *desc;  // kMaxElems per code
+  int code;
+  int n;
+  __device__ void put(const unsigned (&m)[3], int i, int j) {
+    if (n < kMaxElems)
+      desc[code * kMaxElems + n] =
+          m[0] | m[1] << 4 | m[2] << 8 | (unsigned)i << 12 | (unsigned)j << 14;
+    ++n;
   }
-  for (int k = 0; k < o.npts; ++k) {
-    const int cnt = __popc(m[k]);
-    for (int d = 0; d < o.dim; ++d) {
-      int sum = 0;
-      for (int j = 0; j < 4; ++j)
-        if (m[k] >> j & 1u) sum += cc[j][d];
-      o.pos[(o.at * o.npts + k) * o.dim + d] = __fdiv_rn((float)sum, (float)cnt);
-    }
-  }
-  if (o.pairs) {
-    o.pairs[2 * o.at] = min(l1, l2);
-    o.pairs[2 * o.at + 1] = max(l1, l2);
-  }
-  ++o.at;
-}
+};
 
 // Separators of a triangle (Fig. 5) or tetrahedron (Fig. 6), n = 3 or 4
 // corners with labels L in chain order.
-__device__ void separators(GeoOut &o, const int (*cc)[3], const int32_t *L, int n) {
+__device__ void separators(ElemRecorder &o, const int32_t *L, int n) {
   // classes of equal labels: cls[k] = first corner with L[k]
   int cls[4], size[4] = {0, 0, 0, 0};
   for (int k = 0; k < n; ++k) {
@@ -295,8 +292,7 @@ __device__ void separators(GeoOut &o, const int (*cc)[3], const int32_t *L, int 
       const unsigned e[3] = {3u, 6u, 5u};
       for (int k = 0; k < 3; ++k) {
         const unsigned m[3] = {7u, e[k], 0u};
-        const int i = __ffs(e[k]) - 1, j = 31 - __clz(e[k]);
-        put(o, cc, m, L[i], L[j]);
+        o.put(m, __ffs(e[k]) - 1, 31 - __clz(e[k]));
       }
       return;
     }
@@ -305,7 +301,7 @@ __device__ void separators(GeoOut &o, const int (*cc)[3], const int32_t *L, int 
       if (size[cls[k]] == 1) lone = k;
     const int o1 = lone == 0 ? 1 : 0, o2 = lone == 2 ? 1 : 2;
     const unsigned m[3] = {(1u << lone) | (1u << o1), (1u << lone) | (1u << o2), 0u};
-    put(o, cc, m, L[lone], L[o1]);
+    o.put(m, lone, o1);
     return;
   }
   if (classes == 2) {
@@ -320,7 +316,7 @@ __device__ void separators(GeoOut &o, const int (*cc)[3], const int32_t *L, int 
           m[t++] = (1u << lone) | (1u << k);
           if (first < 0) first = k;
         }
-      put(o, cc, m, L[lone], L[first]);
+      o.put(m, lone, first);
       return;
     }
     // 2 + 2: the quad between {p0, p1} (the class of corner 0) and {q0, q1}
@@ -334,8 +330,8 @@ __device__ void separators(GeoOut &o, const int (*cc)[3], const int32_t *L, int 
     const unsigned p0q0 = (1u << p[0]) | (1u << q[0]), p0q1 = (1u << p[0]) | (1u << q[1]),
                    p1q0 = (1u << p[1]) | (1u << q[0]), p1q1 = (1u << p[1]) | (1u << q[1]);
     const unsigned m1[3] = {p0q0, p0q1, p1q0}, m2[3] = {p0q1, p1q0, p1q1};
-    put(o, cc, m1, L[p[0]], L[q[0]]);
-    put(o, cc, m2, L[p[0]], L[q[1]]);
+    o.put(m1, p[0], q[0]);
+    o.put(m2, p[0], q[1]);
     return;
   }
   if (classes == 3) {
@@ -357,11 +353,11 @@ __device__ void separators(GeoOut &o, const int (*cc)[3], const int32_t *L, int 
     const unsigned e1[3] = {T1, T2, bP | bR}, e2[3] = {T2, bP | bR, bQ | bR},
                    e3[3] = {T1, T2, bR | bS}, e4[3] = {T1, T2, bP | bS},
                    e5[3] = {T2, bP | bS, bQ | bS};
-    put(o, cc, e1, L[P], L[R]);
-    put(o, cc, e2, L[P], L[R]);
-    put(o, cc, e3, L[R], L[S]);
-    put(o, cc, e4, L[P], L[S]);
-    put(o, cc, e5, L[P], L[S]);
+    o.put(e1, P, R);
+    o.put(e2, P, R);
+    o.put(e3, R, S);
+    o.put(e4, P, S);
+    o.put(e5, P, S);
     return;
   }
   // four labels: centre, face centre, edge midpoint for each face's edges
@@ -373,13 +369,13 @@ __device__ void separators(GeoOut &o, const int (*cc)[3], const int32_t *L, int 
     const int ea[3] = {v[0], v[0], v[1]}, eb[3] = {v[1], v[2], v[2]};
     for (int k = 0; k < 3; ++k) {
       const unsigned m[3] = {0xFu, faces[f], (1u << ea[k]) | (1u << eb[k])};
-      put(o, cc, m, L[ea[k]], L[eb[k]]);
+      o.put(m, ea[k], eb[k]);
     }
   }
 }
 
 // Boundaries: the corners that share a label held by all but one of them.
-__device__ __forceinline__ void boundaries(GeoOut &o, const int (*cc)[3], const int32_t *L, int n) {
+__device__ void boundaries(ElemRecorder &o, const int32_t *L, int n) {
   for (int lone = 0; lone < n; ++lone) {
     const int ref = lone == 0 ? 1 : 0;
     bool same = L[lone] != L[ref];
@@ -390,80 +386,215 @@ __device__ __forceinline__ void boundaries(GeoOut &o, const int (*cc)[3], const 
       int t = 0;
       for (int k = 0; k < n; ++k)
         if (k != lone) m[t++] = 1u << k;
-      put(o, cc, m, L[ref], L[lone]);
+      o.put(m, ref, lone);
       return;
     }
   }
 }
 
-// One thread per cell, writing its cell's elements where the index pass put
-// them (a store-staged variant that regenerated the elements per window of
-// shared memory measured twice as slow).
-__global__ void __launch_bounds__(kCellThreads) k_simplex_geometry(const int32_t *__restrict__ lab,
-                                                                   SimplexGeom g,
-                                                                   const int64_t *__restrict__ offsets,
-                                                                   int64_t total, float *pos,
-                                                                   int32_t *pairs, DevStatus *st) {
-  const int64_t c = (int64_t)blockIdx.x * kCellThreads + threadIdx.x;
-  if (c >= g.ncells) return;
-  uint32_t x, y, z;
-  cell_xyz(g, (uint32_t)c, &x, &y, &z);
-  GeoOut o;
-  o.pos = pos;
-  o.pairs = pairs;
-  o.at = offsets[c];
-  o.end = c + 1 < g.ncells ? offsets[c + 1] : total;
-  o.dim = g.per == 2 ? 2 : 3;
-  o.npts = o.dim;
-  o.overrun = o.at > o.end || o.end > total;
-  if (o.overrun) {
-    atomicOr(&st->bad_index, 1u);
-    return;
+// Per-block tables: the elements of every code (mode 0: separators, mode 1:
+// boundaries), and per chain p the offset bits of its corners (x = 1, y = 2,
+// z = 4; corner k in bits 3k..3k+2) and the corners past each axis's step
+// (axis a: bit 4a + k set when corner k has +1 along a).
+struct GeoTables {
+  uint32_t desc[32 * kMaxElems];
+  uint32_t count[32];
+  uint32_t corners[6];
+  uint32_t above[6];
+};
+
+__device__ void fill_geo_tables(GeoTables &t, int per, int mode) {
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    // labels with the equality pattern the code describes (local labels)
+    const int code = per == 2 ? (tid & 7) : tid;
+    int32_t L[4];
+    L[0] = 0;
+    if (per == 2) {
+      L[1] = (code >> 2) & 1;
+      L[2] = code & 3;
+      L[3] = 0;
+    } else {
+      L[1] = code >> 4;
+      L[2] = (code >> 2) & 3;
+      L[3] = code & 3;
+    }
+    ElemRecorder r{t.desc, tid, 0};
+    if (mode)
+      boundaries(r, L, per == 2 ? 3 : 4);
+    else
+      separators(r, L, per == 2 ? 3 : 4);
+    t.count[tid] = (uint32_t)min(r.n, kMaxElems);
+  } else if (tid < 32 + per) {
+    const int p = tid - 32;
+    // axis stepped before corner k: 2D x,y / y,x; 3D xyz, xzy, yxz, yzx, zxy, zyx
+    // (axis a stepped k-th in bits 4(k-1)..4(k-1)+3)
+    const uint32_t orders3[6] = {0x210u, 0x120u, 0x201u, 0x021u, 0x102u, 0x012u};
+    const uint32_t order = per == 2 ? (p == 0 ? 0x10u : 0x01u) : orders3[p];
+    const int steps = per == 2 ? 2 : 3;
+    uint32_t bits = 0, corners = 0, above = 0;
+    for (int k = 1; k <= steps; ++k) {
+      const int a = (order >> (4 * (k - 1))) & 15;
+      bits |= 1u << a;
+      corners |= bits << (3 * k);
+      for (int kk = k; kk <= steps; ++kk) above |= 1u << (4 * a + kk);
+    }
+    t.corners[p] = corners;
+    t.above[p] = above;
   }
-  const int64_t v = (int64_t)x + g.nx * ((int64_t)y + g.ny * z);
+}
+
+// Mean of cnt corners whose coordinates sum to s (cnt * base + k, k <= cnt):
+// halves and quarters are exact scalings, thirds take the rounded division.
+__device__ __forceinline__ float mean_of(int64_t s, int cnt) {
+  const float f = (float)s;
+  return cnt == 3 ? __fdiv_rn(f, 3.0f) : (cnt == 1 ? f : (cnt == 2 ? f * 0.5f : f * 0.25f));
+}
+
+template <int kPer>
+__global__ void __launch_bounds__(kGeoThreads) k_simplex_geometry(
+    const int32_t *__restrict__ lab, SimplexGeom g, const int64_t *__restrict__ offsets,
+    int64_t total, float *__restrict__ pos, int32_t *__restrict__ pairs, int pairs8, DevStatus *st) {
+  constexpr int kDim = kPer == 2 ? 2 : 3;  // coordinates per point = points per element
+  constexpr int kF = kDim * kDim;          // floats per element
+  constexpr int kS = kF | 1;               // window stride per element (odd: no bank conflicts)
+  constexpr int kWarps = kGeoThreads / 32;
+  constexpr unsigned kAll = 0xffffffffu;
+  __shared__ GeoTables tab;
+  __shared__ float window[kWarps][32 * kS];
+  fill_geo_tables(tab, kPer, g.mode);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  float *win = window[threadIdx.x >> 5];
   const int64_t sy = g.nx, sz = g.nx * g.ny;
-  if (g.per == 2) {
-    int cc[3][3];
-    int32_t L[3];
-    for (int p = 0; p < 2; ++p) {
-      // chains (0,0) -> (1,0) -> (1,1) and (0,0) -> (0,1) -> (1,1)
-      const int dx[3] = {0, p == 0 ? 1 : 0, 1}, dy[3] = {0, p == 0 ? 0 : 1, 1};
-      for (int k = 0; k < 3; ++k) {
-        cc[k][0] = (int)x + dx[k];
-        cc[k][1] = (int)y + dy[k];
-        cc[k][2] = 0;
-        L[k] = __ldg(lab + v + dx[k] + sy * dy[k]);
-      }
-      if (g.mode)
-        boundaries(o, cc, L, 3);
-      else
-        separators(o, cc, L, 3);
-    }
-  } else {
-    const int ax[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
-    for (int p = 0; p < 6; ++p) {
-      int cc[4][3];
-      int32_t L[4];
-      int pt[3] = {(int)x, (int)y, (int)z};
-      int64_t vv = v;
-      for (int k = 0; k < 4; ++k) {
-        if (k > 0) {
-          const int a = ax[p][k - 1];
-          pt[a] += 1;
-          vv += a == 0 ? 1 : (a == 1 ? sy : sz);
+  const int64_t nchunks = (g.ncells + 31) / 32;
+  for (int64_t ch = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); ch < nchunks;
+       ch += (int64_t)gridDim.x * kWarps) {
+    const int64_t c = ch * 32 + lane;
+    uint32_t x = 0, y = 0, z = 0, codes = 0, counts = 0, n = 0;
+    int64_t off = 0;
+    if (c < g.ncells) {
+      cell_xyz(g, (uint32_t)c, &x, &y, &z);
+      const int64_t v = (int64_t)x + g.nx * ((int64_t)y + g.ny * z);
+      if (kPer == 2) {
+        const int32_t l00 = __ldg(lab + v), l10 = __ldg(lab + v + 1), l01 = __ldg(lab + v + sy),
+                      l11 = __ldg(lab + v + sy + 1);
+        const int k0 = tri_code(l00, l10, l11), k1 = tri_code(l00, l01, l11);
+        const uint32_t n0 = tab.count[k0], n1 = tab.count[k1];
+        codes = (uint32_t)k0 | (uint32_t)k1 << 5;
+        counts = n0 | n1 << 4;
+        n = n0 + n1;
+      } else {
+        int32_t l[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          l[k] = __ldg(lab + v + ((k & 1) ? 1 : 0) + ((k & 2) ? sy : 0) + ((k & 4) ? sz : 0));
+        const int kb[6] = {1, 1, 2, 2, 4, 4};
+        const int kc[6] = {3, 5, 3, 6, 5, 6};
+#pragma unroll
+        for (int p = 0; p < 6; ++p) {
+          const int code = tet_code(l[0], l[kb[p]], l[kc[p]], l[7]);
+          const uint32_t np = tab.count[code];
+          codes |= (uint32_t)code << (5 * p);
+          counts |= np << (4 * p);
+          n += np;
         }
-        cc[k][0] = pt[0];
-        cc[k][1] = pt[1];
-        cc[k][2] = pt[2];
-        L[k] = __ldg(lab + vv);
       }
-      if (g.mode)
-        boundaries(o, cc, L, 4);
-      else
-        separators(o, cc, L, 4);
+      off = offsets[c];
+    }
+    // running element counts over the chunk's cells
+    uint32_t incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(kAll, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const uint32_t nw = __shfl_sync(kAll, incl, 31);
+    const int64_t base = __shfl_sync(kAll, off, 0);
+    int64_t end = 0;
+    if (lane == 0) end = ch * 32 + 32 < g.ncells ? offsets[ch * 32 + 32] : total;
+    end = __shfl_sync(kAll, end, 0);
+    // the offsets must be the running counts: then every write below stays
+    // inside [offsets[first cell], end) and end <= total
+    const bool bad = c < g.ncells && off != base + (int64_t)(incl - n);
+    if (__any_sync(kAll, bad) || base < 0 || end != base + (int64_t)nw || end > total) {
+      if (lane == 0) atomicOr(&st->bad_index, 1u);
+      continue;
+    }
+    const uint32_t excl = incl - n;
+    for (uint32_t e0 = 0; e0 < nw; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      // the element's cell: the first lane whose running count exceeds e
+      int owner = 0;
+#pragma unroll
+      for (int s = 16; s > 0; s >>= 1) {
+        const uint32_t t = __shfl_sync(kAll, incl, owner + s - 1);
+        if (t <= e) owner += s;
+      }
+      const uint32_t oc = __shfl_sync(kAll, codes, owner), on = __shfl_sync(kAll, counts, owner);
+      const uint32_t ox = __shfl_sync(kAll, x, owner), oy = __shfl_sync(kAll, y, owner),
+                     oz = __shfl_sync(kAll, z, owner), oe = __shfl_sync(kAll, excl, owner);
+      if (e < nw) {
+        // the simplex within the cell, and the element within the simplex
+        uint32_t r = e - oe;
+        int p = 0;
+#pragma unroll
+        for (int q = 0; q < kPer - 1; ++q) {
+          const uint32_t cq = (on >> (4 * q)) & 15u;
+          if (p == q && r >= cq) {
+            r -= cq;
+            p = q + 1;
+          }
+        }
+        const int code = (int)((oc >> (5 * p)) & 31u);
+        const uint32_t d = tab.desc[code * kMaxElems + r];
+        const uint32_t above = tab.above[p];
+        const uint32_t o3[3] = {ox, oy, oz};
+#pragma unroll
+        for (int k = 0; k < kDim; ++k) {
+          const uint32_t m = (d >> (4 * k)) & 15u;
+          const int cnt = __popc(m);
+#pragma unroll
+          for (int a = 0; a < kDim; ++a) {
+            const int64_t s = (int64_t)cnt * o3[a] + __popc(m & (above >> (4 * a)) & 15u);
+            win[lane * kS + k * kDim + a] = mean_of(s, cnt);
+          }
+        }
+        if (pairs) {
+          const uint32_t cb = tab.corners[p];
+          const uint32_t bi = (cb >> (3 * ((d >> 12) & 3u))) & 7u, bj = (cb >> (3 * ((d >> 14) & 3u))) & 7u;
+          const int64_t v = (int64_t)ox + g.nx * ((int64_t)oy + g.ny * oz);
+          const int32_t li = __ldg(lab + v + (bi & 1u) + ((bi & 2u) ? sy : 0) + ((bi & 4u) ? sz : 0));
+          const int32_t lj = __ldg(lab + v + (bj & 1u) + ((bj & 2u) ? sy : 0) + ((bj & 4u) ? sz : 0));
+          const int64_t at = base + e;
+          if (pairs8) {
+            *reinterpret_cast<int2 *>(pairs + 2 * at) = make_int2(min(li, lj), max(li, lj));
+          } else {
+            pairs[2 * at] = min(li, lj);
+            pairs[2 * at + 1] = max(li, lj);
+          }
+        }
+      }
+      __syncwarp();
+      const int nf = (int)min(32u, nw - e0) * kF;
+      float *dst = pos + (base + e0) * kF;
+      for (int i = lane; i < nf; i += 32) {
+        const int el = i / kF;
+        dst[i] = win[el * kS + (i - el * kF)];
+      }
+      __syncwarp();  // the window is refilled by the next round
     }
   }
-  if (o.overrun || o.at != o.end) atomicOr(&st->bad_index, 1u);
+}
+
+int geometry_grid(int64_t nchunks, const void *kernel) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kGeoThreads, 0);
+  const int64_t want = (nchunks + kGeoThreads / 32 - 1) / (kGeoThreads / 32);
+  const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  return (int)(want < cap ? want : cap);
 }
 
 }  // namespace
@@ -500,9 +631,16 @@ cudaError_t launch_simplex_geometry(const int32_t *labels, const int64_t dims[3]
                                     int32_t *pairs, DevStatus *st, cudaStream_t s) {
   const SimplexGeom g = simplex_geom(dims, mode);
   if (g.ncells == 0) return cudaSuccess;
+  const int64_t nchunks = (g.ncells + 31) / 32;
+  const int pairs8 = (reinterpret_cast<uintptr_t>(pairs) & 7) == 0;
   ++tl_launches;
-  k_simplex_geometry<<<(unsigned)((g.ncells + kCellThreads - 1) / kCellThreads), kCellThreads, 0, s>>>(
-      labels, g, offsets, total, points, pairs, st);
+  if (g.per == 2) {
+    k_simplex_geometry<2><<<geometry_grid(nchunks, (const void *)k_simplex_geometry<2>), kGeoThreads, 0,
+                            s>>>(labels, g, offsets, total, points, pairs, pairs8, st);
+  } else {
+    k_simplex_geometry<6><<<geometry_grid(nchunks, (const void *)k_simplex_geometry<6>), kGeoThreads, 0,
+                            s>>>(labels, g, offsets, total, points, pairs, pairs8, st);
+  }
   return cudaGetLastError();
 }
 
