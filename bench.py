@@ -73,6 +73,9 @@ WORKLOADS = {
     "index512": dict(dims=(512, 512, 512), kind="index", dtype="i32",
                      desc="marching tetrahedra index pass (codes + cell offsets) over the MS labels "
                           "of the 512^3 sigma=4 noise field (6 x 511^3 tetrahedra)"),
+    "index256": dict(dims=(256, 256, 256), kind="index", dtype="i32",
+                     desc="the index and geometry passes over the MS labels of the 256^3 sigma=4 noise "
+                          "field (profiling size)"),
     "batch256": dict(dims=None, kind="batch", dtype="mixed",
                      desc="256 fields, dims log-uniform in [32, 256] per axis, fp32/fp16 and smoothed "
                           "noise (sigma 2-6) / 8-Gaussian sums 50/50, seed 0; one ms_segment_batch call "
@@ -554,16 +557,17 @@ def run_serve_bench(args):
 
 def run_index_bench(args):
     """The index pass after the segmentation (ms_simplex_index) on the MS labels
-    of the 512^3 noise field: per cell, labels in (4 B, each vertex once),
-    6 tetrahedron codes (6 B) and one offset (8 B) out."""
+    of the 512^3 (index256: 256^3) noise field: per cell, labels in (4 B, each
+    vertex once), 6 tetrahedron codes (6 B) and one offset (8 B) out; then the
+    geometry pass (region separators) into the slots it made."""
     import torch
 
     import paper_2303_15491_gb300 as ms
 
     torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
-    dims = (512, 512, 512)
-    field = torch.from_numpy(make_field("noise512")).to(dev)
+    dims = WORKLOADS[args.workload]["dims"]
+    field = torch.from_numpy(make_field("noise512" if dims[0] == 512 else "noise256")).to(dev)
     stream = torch.cuda.Stream(device=dev)
     ctx = ms.ms_create(dev, stream)
     asc, desc, labels, _ = ms.segment(ctx, field)
@@ -609,9 +613,9 @@ def run_index_bench(args):
     import oracle
 
     slab = 17
-    lab_np = labels.view(512, 512, 512)[:slab].cpu().numpy()
+    lab_np = labels.view(dims[2], dims[1], dims[0])[:slab].cpu().numpy()
     t = time.perf_counter()
-    oracle.simplex_index(lab_np, (512, 512, slab))
+    oracle.simplex_index(lab_np, (dims[0], dims[1], slab))
     cpu_s = time.perf_counter() - t
     ms.ms_destroy(ctx)
     line = {
@@ -619,10 +623,11 @@ def run_index_bench(args):
         "unit": "tetrahedra/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "i32", "data": "synthetic",
-        "config": {"workload": "index512", "desc": WORKLOADS["index512"]["desc"], "cells": cells,
+        "config": {"workload": args.workload, "desc": WORKLOADS[args.workload]["desc"], "cells": cells,
                    "tetrahedra": cells * per, "elements_total": total,
-                   "l2": "labels 512 MiB, codes 800 MB, offsets 1.07 GB: larger than L2"},
-        "roofline": {"bound": "hbm", "kernel": "index pass (3 launches)", "achieved": alg / (kern_ms / 1e3) / 1e9,
+                   "l2": ("labels 512 MiB, codes 800 MB, offsets 1.07 GB: larger than L2" if dims[0] == 512
+                          else "labels 64 MiB (L2-resident), codes 100 MB, offsets 134 MB")},
+        "roofline": {"bound": "hbm", "kernel": "index pass (k_simplex_index, one launch)", "achieved": alg / (kern_ms / 1e3) / 1e9,
                      "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": alg / (kern_ms / 1e3) / 1e9 / hbm, "traffic": None,
                      "alg_bytes_per_cell": 18, "avg_launch_ms": kern_ms},
@@ -632,8 +637,9 @@ def run_index_bench(args):
                      "frac": geo_bytes / (geo_ms / 1e3) / 1e9 / hbm,
                      "note": "labels 4 B + offset 8 B per cell in, 36 B of points + 8 B of labels "
                              "per triangle out"},
-        "cpu_baseline": {"value": 511 * 511 * (slab - 1) * per / cpu_s, "unit": "tetrahedra/s", "cores": 1,
-                         "kind": "oracle", "sample": f"512x512x{slab} slab ({cpu_s:.1f} s single-threaded)"},
+        "cpu_baseline": {"value": (dims[0] - 1) * (dims[1] - 1) * (slab - 1) * per / cpu_s,
+                         "unit": "tetrahedra/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{dims[0]}x{dims[1]}x{slab} slab ({cpu_s:.1f} s single-threaded)"},
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -659,7 +665,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.workload == "index512":
+    if args.workload in ("index512", "index256"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the index pass has no separate "
                               "reference arm; its CPU baseline is in the line's cpu_baseline"}))

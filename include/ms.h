@@ -215,8 +215,10 @@ ms_status ms_batch_graphs(ms_ctx *ctx, int on);
  * device, 16-byte aligned; cell_offsets: int64[cells] on the device, the
  * exclusive prefix sum of the cells' element counts; *total (host, may be
  * NULL): the element total.  Grids without cells (an extent of 1 other than
- * nz) give *total = 0 and touch no output.  Errors: MS_ERR_INVALID_ARG,
- * MS_ERR_TOO_LARGE, MS_ERR_OUT_OF_MEMORY, MS_ERR_CUDA. */
+ * nz) give *total = 0 and touch no output.  One kernel launch: tiles of
+ * cells find their offset bases from the earlier tiles' totals (a bounded
+ * wait; MS_ERR_TIMEOUT if it runs out).  Errors: MS_ERR_INVALID_ARG,
+ * MS_ERR_TOO_LARGE, MS_ERR_OUT_OF_MEMORY, MS_ERR_TIMEOUT, MS_ERR_CUDA. */
 ms_status ms_simplex_index(ms_ctx *ctx, const int32_t *labels, const int64_t dims[3], int mode,
                            uint8_t *codes, int64_t *cell_offsets, int64_t *total);
 

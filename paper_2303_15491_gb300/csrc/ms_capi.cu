@@ -1010,13 +1010,17 @@ ms_status ms_simplex_index(ms_ctx *c, const int32_t *labels, const int64_t dims[
   const long long l0 = tl_launches;
   unsigned long long *tot_dev = nullptr;
   int64_t nc = 0;
+  s = reset_status(c);
+  if (s != MS_OK) return s;
   StageTimer t0(c, MS_STAGE_TILE_LOCAL);
   MS_TRY(launch_simplex_index(labels, dims, mode, codes, cell_offsets, c->sxscratch, &tot_dev, &nc,
-                              c->stream));
+                              c->dst, c->stream));
   t0.stop();
   MS_TRY(cudaMemcpyAsync(c->hcount, tot_dev, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                          c->stream));
-  MS_TRY(cudaStreamSynchronize(c->stream));
+  s = read_status(c);  // synchronises the stream
+  if (s != MS_OK) return s;
+  if (c->hst->timeout) return MS_ERR_TIMEOUT;
   if (total) *total = (int64_t)*c->hcount;
   finish_profile(c, l0);
   return MS_OK;

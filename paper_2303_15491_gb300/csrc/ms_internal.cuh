@@ -102,7 +102,7 @@ cudaError_t launch_fill_u64(unsigned long long *p, size_t count, unsigned long l
 size_t simplex_scratch_bytes(int64_t ncells);
 cudaError_t launch_simplex_index(const int32_t *labels, const int64_t dims[3], int mode,
                                  uint8_t *codes, int64_t *offsets, void *scratch,
-                                 unsigned long long **total_dev, int64_t *ncells_out,
+                                 unsigned long long **total_dev, int64_t *ncells_out, DevStatus *st,
                                  cudaStream_t s);
 cudaError_t launch_simplex_geometry(const int32_t *labels, const int64_t dims[3], int mode,
                                     const int64_t *offsets, int64_t total, float *points,

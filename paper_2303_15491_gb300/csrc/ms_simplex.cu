@@ -10,11 +10,9 @@
 // c the cell's linear index (x fastest); a simplex's vertices in stepping
 // order are a, b, c(, d).
 //
-// Three launches: codes, per-cell element counts (one byte) and per-block
-// totals (one thread per cell of each of a block's kSub groups of 256 cells,
-// a group's codes staged in shared memory and stored as 16-byte vectors), an
-// exclusive scan of the block totals, and the per-cell offsets (block scans
-// of the counts, plus the block's base).
+// One launch computes the codes and the offsets (k_simplex_index); a second
+// kernel writes the separating elements into those slots
+// (k_simplex_geometry).
 #include <stdint.h>
 
 #include "fastdiv.h"
@@ -24,7 +22,6 @@ namespace msseg {
 namespace {
 
 constexpr int kCellThreads = 256;
-constexpr int kSub = 8;  // groups of kCellThreads cells per block
 
 struct SimplexGeom {
   int64_t nx, ny;        // vertices per row / per plane row count
@@ -126,114 +123,204 @@ __device__ __forceinline__ void fill_elements(unsigned int *lut, int per, int mo
   }
 }
 
-__global__ void __launch_bounds__(kCellThreads) k_simplex_codes(const int32_t *__restrict__ lab,
-                                                                SimplexGeom g,
-                                                                uint8_t *__restrict__ codes,
-                                                                uint8_t *__restrict__ counts,
-                                                                unsigned int *__restrict__ block_tot) {
-  __shared__ __align__(16) uint8_t sc[kCellThreads * 6];
-  __shared__ unsigned int sh[kCellThreads / 32];
+// Codes of the six tetrahedra of a cell from its corner labels (corner
+// bits x = 1, y = 2, z = 4; axis orders xyz, xzy, yxz, yzx, zxy, zyx give the
+// b and c corners 1,3 / 1,5 / 2,3 / 2,6 / 4,5 / 4,6), packed into the byte
+// lanes of w starting at byte `at` (a constant once the caller's loop is
+// unrolled); returns the cell's element count.
+__device__ __forceinline__ uint32_t cell_codes3(const int32_t (&l)[8], int at, uint32_t *w,
+                                                const unsigned int *lut) {
+  constexpr int kb[6] = {1, 1, 2, 2, 4, 4};
+  constexpr int kc[6] = {3, 5, 3, 6, 5, 6};
+  uint32_t n = 0;
+#pragma unroll
+  for (int p = 0; p < 6; ++p) {
+    const uint32_t code = (uint32_t)tet_code(l[0], l[kb[p]], l[kc[p]], l[7]);
+    w[(at + p) / 4] |= code << (8 * ((at + p) % 4));
+    n += lut[code];
+  }
+  return n;
+}
+
+__device__ __forceinline__ uint32_t cell_codes2(int32_t l00, int32_t l10, int32_t l01, int32_t l11,
+                                                int at, uint32_t *w, const unsigned int *lut) {
+  const uint32_t k0 = (uint32_t)tri_code(l00, l10, l11), k1 = (uint32_t)tri_code(l00, l01, l11);
+  w[at / 4] |= k0 << (8 * (at % 4));
+  w[(at + 1) / 4] |= k1 << (8 * ((at + 1) % 4));
+  return lut[k0] + lut[k1];
+}
+
+// One launch.  Each block takes the next tile of kTileCells cells (tile ids
+// from an atomic counter, so every earlier tile's block has started and will
+// publish without waiting), each thread kRunCells consecutive cells of it:
+// along a row the thread slides a window of corner labels (4 new labels a
+// cell in 3D, 2 in 2D), codes go out as 16-byte vectors.  The tile's element
+// total is published at once; the tile's base is found by decoupled
+// look-back over the earlier tiles' published words (flag and value in one
+// 64-bit word: the tile's own total, or its inclusive prefix), and then
+// every cell's offset is written.
+constexpr int kRunCells = 8;
+constexpr int kTileCells = kCellThreads * kRunCells;
+constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPrefix = 2ull << 62,
+                             kValueMask = (1ull << 62) - 1;
+// Look-back waits are bounded: past this many polls the call reports a
+// timeout (and the waiting tiles take base 0, so nothing waits on them).
+constexpr int kLookbackPolls = 1 << 22;
+
+template <int kPer>
+__global__ void __launch_bounds__(kCellThreads) k_simplex_index(
+    const int32_t *__restrict__ lab, SimplexGeom g, uint8_t *__restrict__ codes,
+    int64_t *__restrict__ offsets, int vec_offsets, unsigned long long *hdr,
+    unsigned long long *status, DevStatus *st) {
+  constexpr int kWords = kPer * kRunCells / 4;  // code bytes of a run, 4 a word
   __shared__ unsigned int lut[32];
-  fill_elements(lut, g.per, g.mode);
+  __shared__ unsigned int sh[kCellThreads / 32];
+  __shared__ unsigned long long s_base;
+  __shared__ unsigned int s_tile;
+  fill_elements(lut, kPer, g.mode);
+  if (threadIdx.x == 0) s_tile = atomicAdd(reinterpret_cast<unsigned int *>(hdr + 1), 1u);
   __syncthreads();
-  unsigned int block_sum = 0;
-  // kSub consecutive groups of kCellThreads cells per block
-  for (int sub = 0; sub < kSub; ++sub) {
-    const int64_t c0 = ((int64_t)blockIdx.x * kSub + sub) * kCellThreads;
-    if (c0 >= g.ncells) break;  // block-uniform
-    const int64_t c = c0 + threadIdx.x;
-    unsigned int count = 0;
-    if (c < g.ncells) {
-      uint32_t x, y, z;
-      cell_xyz(g, (uint32_t)c, &x, &y, &z);
-      const int64_t v = (int64_t)x + g.nx * ((int64_t)y + g.ny * z);
-      const int64_t sy = g.nx, sz = g.nx * g.ny;
-      if (g.per == 2) {
-        const int32_t l00 = __ldg(lab + v), l10 = __ldg(lab + v + 1), l01 = __ldg(lab + v + sy),
-                      l11 = __ldg(lab + v + sy + 1);
-        const int k0 = tri_code(l00, l10, l11), k1 = tri_code(l00, l01, l11);
-        sc[threadIdx.x * 2] = (uint8_t)k0;
-        sc[threadIdx.x * 2 + 1] = (uint8_t)k1;
-        count = lut[k0] + lut[k1];
+  const unsigned int tile = s_tile;
+  const int64_t c0 = (int64_t)tile * kTileCells + (int64_t)threadIdx.x * kRunCells;
+  const int64_t sy = g.nx, sz = g.nx * g.ny;
+  uint32_t w[kWords];
+#pragma unroll
+  for (int i = 0; i < kWords; ++i) w[i] = 0;
+  uint32_t n[kRunCells];
+#pragma unroll
+  for (int j = 0; j < kRunCells; ++j) n[j] = 0;
+  const bool full = c0 + kRunCells <= g.ncells;
+  if (c0 < g.ncells) {
+    uint32_t x, y, z;
+    cell_xyz(g, (uint32_t)c0, &x, &y, &z);
+    const int32_t *r0 = lab + ((int64_t)x + g.nx * ((int64_t)y + g.ny * z));
+    if (full && x + kRunCells <= g.cx) {  // the run stays in one row
+      if (kPer == 2) {
+        const int32_t *r1 = r0 + sy;
+        int32_t a0 = __ldg(r0), a1 = __ldg(r1);
+#pragma unroll
+        for (int j = 0; j < kRunCells; ++j) {
+          const int32_t b0 = __ldg(r0 + j + 1), b1 = __ldg(r1 + j + 1);
+          n[j] = cell_codes2(a0, b0, a1, b1, 2 * j, w, lut);
+          a0 = b0;
+          a1 = b1;
+        }
       } else {
-        // corners by offset bits (x = 1, y = 2, z = 4)
-        int32_t l[8];
+        const int32_t *r1 = r0 + sy, *r2 = r0 + sz, *r3 = r0 + sy + sz;
+        int32_t a0 = __ldg(r0), a1 = __ldg(r1), a2 = __ldg(r2), a3 = __ldg(r3);
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
-          l[k] = __ldg(lab + v + ((k & 1) ? 1 : 0) + ((k & 2) ? sy : 0) + ((k & 4) ? sz : 0));
-        // axis orders xyz, xzy, yxz, yzx, zxy, zyx: b and c corners of each chain
-        const int kb[6] = {1, 1, 2, 2, 4, 4};
-        const int kc[6] = {3, 5, 3, 6, 5, 6};
+        for (int j = 0; j < kRunCells; ++j) {
+          const int32_t b0 = __ldg(r0 + j + 1), b1 = __ldg(r1 + j + 1), b2 = __ldg(r2 + j + 1),
+                        b3 = __ldg(r3 + j + 1);
+          const int32_t l[8] = {a0, b0, a1, b1, a2, b2, a3, b3};
+          n[j] = cell_codes3(l, 6 * j, w, lut);
+          a0 = b0;
+          a1 = b1;
+          a2 = b2;
+          a3 = b3;
+        }
+      }
+    } else {  // the run wraps a row or ends the grid: cell by cell
 #pragma unroll
-        for (int p = 0; p < 6; ++p) {
-          const int code = tet_code(l[0], l[kb[p]], l[kc[p]], l[7]);
-          sc[threadIdx.x * 6 + p] = (uint8_t)code;
-          count += lut[code];
+      for (int j = 0; j < kRunCells; ++j) {
+        const int64_t c = c0 + j;
+        if (c < g.ncells) {
+          cell_xyz(g, (uint32_t)c, &x, &y, &z);
+          const int32_t *q = lab + ((int64_t)x + g.nx * ((int64_t)y + g.ny * z));
+          if (kPer == 2) {
+            n[j] = cell_codes2(__ldg(q), __ldg(q + 1), __ldg(q + sy), __ldg(q + sy + 1), 2 * j, w, lut);
+          } else {
+            int32_t l[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              l[k] = __ldg(q + ((k & 1) ? 1 : 0) + ((k & 2) ? sy : 0) + ((k & 4) ? sz : 0));
+            n[j] = cell_codes3(l, 6 * j, w, lut);
+          }
         }
       }
     }
-    if (c < g.ncells) counts[c] = (uint8_t)count;  // at most 6 x 12
-    __syncthreads();
-    // the group's codes are one contiguous byte range
-    const int64_t nvalid = min((int64_t)kCellThreads, g.ncells - c0);
-    const int64_t bytes = nvalid * g.per;
-    uint8_t *dst = codes + c0 * g.per;  // 16-byte aligned: c0 * per is a multiple of 512
-    const int vec = (int)(bytes / 16);
-    for (int i = threadIdx.x; i < vec; i += kCellThreads)
-      reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(sc)[i];
-    for (int64_t i = (int64_t)vec * 16 + threadIdx.x; i < bytes; i += kCellThreads) dst[i] = sc[i];
-    unsigned int tot = 0;
-    block_excl(count, &tot, sh);
-    block_sum += tot;
-    __syncthreads();  // sc and sh are reused by the next group
+    if (full) {  // c0 * kPer is a multiple of 16 bytes
+      uint4 *dst = reinterpret_cast<uint4 *>(codes + c0 * kPer);
+#pragma unroll
+      for (int i = 0; i < kWords / 4; ++i) dst[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kPer * kRunCells; ++i)
+        if (c0 + i / kPer < g.ncells) codes[c0 * kPer + i] = (uint8_t)(w[i / 4] >> (8 * (i % 4)));
+    }
   }
-  if (threadIdx.x == 0) block_tot[blockIdx.x] = block_sum;
-}
-
-// Exclusive scan of the per-block totals into 64-bit bases, by one block:
-// thread t sums its contiguous chunk, the chunk sums are scanned, and the
-// chunk is walked again writing bases.  *total receives the sum.
-__global__ void __launch_bounds__(1024) k_scan_blocks(const unsigned int *__restrict__ tot,
-                                                      int64_t nblocks,
-                                                      unsigned long long *__restrict__ base,
-                                                      unsigned long long *__restrict__ total) {
-  __shared__ unsigned long long sh[1024];
-  const int64_t chunk = (nblocks + 1023) / 1024;
-  const int64_t lo = (int64_t)threadIdx.x * chunk, hi = min(nblocks, lo + chunk);
-  unsigned long long s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += tot[i];
-  sh[threadIdx.x] = s;
+  uint32_t mine = 0;
+#pragma unroll
+  for (int j = 0; j < kRunCells; ++j) mine += n[j];
+  unsigned int tot = 0;
+  const unsigned int ex = block_excl(mine, &tot, sh);
+  // the tile's base: look back over the earlier tiles (warp 0)
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    unsigned long long base = 0;
+    if (tile == 0) {
+      if (lane == 0) *(volatile unsigned long long *)&status[0] = kFlagPrefix | tot;
+    } else {
+      if (lane == 0) *(volatile unsigned long long *)&status[tile] = kFlagAgg | tot;
+      long long j = (long long)tile - 1;  // newest tile not yet summed
+      int polls = 0;
+      bool timed_out = false;
+      for (;;) {
+        const long long idx = j - lane;
+        unsigned long long word = kFlagPrefix;  // before tile 0: a prefix of 0
+        if (idx >= 0) word = *(volatile unsigned long long *)&status[idx];
+        unsigned int pm;
+        for (;;) {  // until every lane before the nearest prefix has published
+          pm = __ballot_sync(0xffffffffu, (word >> 62) == 2);
+          const unsigned int em = __ballot_sync(0xffffffffu, (word >> 62) == 0);
+          const unsigned int need = pm ? em & ((pm & (~pm + 1u)) - 1u) : em;
+          if (!need) break;
+          if (__any_sync(0xffffffffu, ++polls > kLookbackPolls ||
+                                          *(volatile unsigned int *)&st->timeout != 0)) {
+            timed_out = true;
+            break;
+          }
+          __nanosleep(32);
+          if (need >> lane & 1u) word = *(volatile unsigned long long *)&status[idx];
+        }
+        if (timed_out) break;
+        const int stop = pm ? __ffs(pm) - 1 : 31;  // lanes 0..stop are summed
+        unsigned long long v = lane <= stop ? (word & kValueMask) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        base += v;
+        if (pm) break;
+        j -= 32;
+      }
+      if (timed_out) {
+        if (lane == 0) atomicOr(&st->timeout, 1u);
+        base = 0;
+      }
+      if (lane == 0) *(volatile unsigned long long *)&status[tile] = kFlagPrefix | ((base + tot) & kValueMask);
+    }
+    if (lane == 0) {
+      s_base = base;
+      if ((int64_t)(tile + 1) * kTileCells >= g.ncells) hdr[0] = base + tot;  // the last tile
+    }
+  }
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const unsigned long long t = threadIdx.x >= o ? sh[threadIdx.x - o] : 0ull;
-    __syncthreads();
-    sh[threadIdx.x] += t;
-    __syncthreads();
-  }
-  unsigned long long run = sh[threadIdx.x] - s;
-  for (int64_t i = lo; i < hi; ++i) {
-    base[i] = run;
-    run += tot[i];
-  }
-  if (threadIdx.x == 1023) *total = sh[1023];
-}
-
-__global__ void __launch_bounds__(kCellThreads) k_simplex_offsets(const uint8_t *__restrict__ counts,
-                                                                  SimplexGeom g,
-                                                                  const unsigned long long *__restrict__ base,
-                                                                  int64_t *__restrict__ offsets) {
-  __shared__ unsigned int sh[kCellThreads / 32];
-  unsigned long long running = base[blockIdx.x];
-  for (int sub = 0; sub < kSub; ++sub) {
-    const int64_t c0 = ((int64_t)blockIdx.x * kSub + sub) * kCellThreads;
-    if (c0 >= g.ncells) break;  // block-uniform
-    const int64_t c = c0 + threadIdx.x;
-    const unsigned int count = c < g.ncells ? __ldg(counts + c) : 0u;
-    unsigned int tot = 0;
-    const unsigned int ex = block_excl(count, &tot, sh);
-    if (c < g.ncells) offsets[c] = (int64_t)(running + ex);
-    running += tot;
-    __syncthreads();  // sh is reused by the next group
+  if (c0 < g.ncells) {
+    long long o[kRunCells];
+    unsigned long long run = s_base + ex;
+#pragma unroll
+    for (int j = 0; j < kRunCells; ++j) {
+      o[j] = (long long)run;
+      run += n[j];
+    }
+    if (full && vec_offsets) {
+      longlong2 *dst = reinterpret_cast<longlong2 *>(offsets + c0);
+#pragma unroll
+      for (int i = 0; i < kRunCells / 2; ++i) dst[i] = make_longlong2(o[2 * i], o[2 * i + 1]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kRunCells; ++j)
+        if (c0 + j < g.ncells) offsets[c0 + j] = o[j];
+    }
   }
 }
 
@@ -393,14 +480,15 @@ __device__ void boundaries(ElemRecorder &o, const int32_t *L, int n) {
 }
 
 // Per-block tables: the elements of every code (mode 0: separators, mode 1:
-// boundaries), and per chain p the offset bits of its corners (x = 1, y = 2,
-// z = 4; corner k in bits 3k..3k+2) and the corners past each axis's step
-// (axis a: bit 4a + k set when corner k has +1 along a).
+// boundaries); per chain p the offset bits of its corners (x = 1, y = 2,
+// z = 4; corner k in bits 3k..3k+2); and per chain p and corner subset m,
+// |m| | k_x << 3 | k_y << 6 | k_z << 9 with k_a the corners of m past axis
+// a's step (their coordinate along a is the cell's plus one).
 struct GeoTables {
   uint32_t desc[32 * kMaxElems];
   uint32_t count[32];
   uint32_t corners[6];
-  uint32_t above[6];
+  uint32_t subset[6 * 16];
 };
 
 __device__ void fill_geo_tables(GeoTables &t, int per, int mode) {
@@ -440,18 +528,34 @@ __device__ void fill_geo_tables(GeoTables &t, int per, int mode) {
       for (int kk = k; kk <= steps; ++kk) above |= 1u << (4 * a + kk);
     }
     t.corners[p] = corners;
-    t.above[p] = above;
+    for (unsigned m = 0; m < 16; ++m)
+      t.subset[p * 16 + m] = (uint32_t)__popc(m) | (uint32_t)__popc(m & above & 15u) << 3 |
+                             (uint32_t)__popc(m & (above >> 4) & 15u) << 6 |
+                             (uint32_t)__popc(m & (above >> 8) & 15u) << 9;
   }
 }
 
-// Mean of cnt corners whose coordinates sum to s (cnt * base + k, k <= cnt):
-// halves and quarters are exact scalings, thirds take the rounded division.
-__device__ __forceinline__ float mean_of(int64_t s, int cnt) {
-  const float f = (float)s;
-  return cnt == 3 ? __fdiv_rn(f, 3.0f) : (cnt == 1 ? f : (cnt == 2 ? f * 0.5f : f * 0.25f));
+// Largest vertex coordinate for which mean_of's sums stay below 2^23.
+constexpr int64_t kNarrowCoord = (1 << 21) - 1;
+
+// Mean of cnt corners (1..4) whose coordinate along an axis is o for cnt - k
+// of them and o + 1 for k: (cnt * o + k) / cnt rounded to nearest even.
+// Narrow: the sum is below 2^23, so it converts exactly by placing it in the
+// mantissa of 2^23; with R = 1/cnt rounded, q = s R is exact for cnt = 1, 2,
+// 4 (the residual is then zero), and for cnt = 3 one FMA residual step
+// (Markstein's correction) makes it the correctly rounded quotient -- checked
+// for every s below 2^23 against the exact quotient.  Wide: an IEEE division.
+template <bool kWide>
+__device__ __forceinline__ float mean_of(uint32_t o, uint32_t k, uint32_t cnt) {
+  if (kWide) return __fdiv_rn((float)((uint64_t)cnt * o + k), (float)cnt);
+  const float f = __uint_as_float(0x4B000000u | (cnt * o + k)) - 8388608.0f;
+  const float c = __uint_as_float(0x4B000000u | cnt) - 8388608.0f;
+  const float R = cnt == 3 ? 1.0f / 3.0f : (cnt == 4 ? 0.25f : (cnt == 2 ? 0.5f : 1.0f));
+  const float q = f * R;
+  return fmaf(fmaf(-q, c, f), R, q);
 }
 
-template <int kPer>
+template <int kPer, bool kWide>
 __global__ void __launch_bounds__(kGeoThreads) k_simplex_geometry(
     const int32_t *__restrict__ lab, SimplexGeom g, const int64_t *__restrict__ offsets,
     int64_t total, float *__restrict__ pos, int32_t *__restrict__ pairs, int pairs8, DevStatus *st) {
@@ -548,17 +652,14 @@ __global__ void __launch_bounds__(kGeoThreads) k_simplex_geometry(
         }
         const int code = (int)((oc >> (5 * p)) & 31u);
         const uint32_t d = tab.desc[code * kMaxElems + r];
-        const uint32_t above = tab.above[p];
-        const uint32_t o3[3] = {ox, oy, oz};
+        const uint32_t *sub = tab.subset + p * 16;
 #pragma unroll
         for (int k = 0; k < kDim; ++k) {
-          const uint32_t m = (d >> (4 * k)) & 15u;
-          const int cnt = __popc(m);
-#pragma unroll
-          for (int a = 0; a < kDim; ++a) {
-            const int64_t s = (int64_t)cnt * o3[a] + __popc(m & (above >> (4 * a)) & 15u);
-            win[lane * kS + k * kDim + a] = mean_of(s, cnt);
-          }
+          const uint32_t q = sub[(d >> (4 * k)) & 15u];
+          const uint32_t cnt = q & 7u;
+          win[lane * kS + k * kDim] = mean_of<kWide>(ox, (q >> 3) & 7u, cnt);
+          win[lane * kS + k * kDim + 1] = mean_of<kWide>(oy, (q >> 6) & 7u, cnt);
+          if (kDim == 3) win[lane * kS + k * kDim + 2] = mean_of<kWide>(oz, (q >> 9) & 7u, cnt);
         }
         if (pairs) {
           const uint32_t cb = tab.corners[p];
@@ -600,12 +701,10 @@ int geometry_grid(int64_t nchunks, const void *kernel) {
 }  // namespace
 
 size_t simplex_scratch_bytes(int64_t ncells) {
-  const int64_t nb = (ncells + kCellThreads * kSub - 1) / (kCellThreads * kSub);
-  return 256 + (size_t)nb * 4 + (size_t)nb * 8 + 256 + 256 + (size_t)ncells;
+  const int64_t nb = (ncells + kTileCells - 1) / kTileCells;
+  return 256 + (size_t)nb * 8;
 }
 
-// labels: int32[N]; codes: uint8[ncells * per]; offsets: int64[ncells];
-// scratch: simplex_scratch_bytes(ncells) bytes; *total_dev: the sum.
 namespace {
 SimplexGeom simplex_geom(const int64_t dims[3], int mode) {
   SimplexGeom g;
@@ -633,53 +732,48 @@ cudaError_t launch_simplex_geometry(const int32_t *labels, const int64_t dims[3]
   if (g.ncells == 0) return cudaSuccess;
   const int64_t nchunks = (g.ncells + 31) / 32;
   const int pairs8 = (reinterpret_cast<uintptr_t>(pairs) & 7) == 0;
+  const bool wide = dims[0] > kNarrowCoord || dims[1] > kNarrowCoord || dims[2] > kNarrowCoord;
   ++tl_launches;
+#define MS_GEO_LAUNCH(per, w)                                                                   \
+  k_simplex_geometry<per, w><<<geometry_grid(nchunks, (const void *)k_simplex_geometry<per, w>), \
+                               kGeoThreads, 0, s>>>(labels, g, offsets, total, points, pairs, pairs8, st)
   if (g.per == 2) {
-    k_simplex_geometry<2><<<geometry_grid(nchunks, (const void *)k_simplex_geometry<2>), kGeoThreads, 0,
-                            s>>>(labels, g, offsets, total, points, pairs, pairs8, st);
+    if (wide)
+      MS_GEO_LAUNCH(2, true);
+    else
+      MS_GEO_LAUNCH(2, false);
   } else {
-    k_simplex_geometry<6><<<geometry_grid(nchunks, (const void *)k_simplex_geometry<6>), kGeoThreads, 0,
-                            s>>>(labels, g, offsets, total, points, pairs, pairs8, st);
+    if (wide)
+      MS_GEO_LAUNCH(6, true);
+    else
+      MS_GEO_LAUNCH(6, false);
   }
+#undef MS_GEO_LAUNCH
   return cudaGetLastError();
 }
 
+// labels: int32[N]; codes: uint8[ncells * per] (16-byte aligned); offsets:
+// int64[ncells]; scratch: simplex_scratch_bytes(ncells) bytes; *total_dev:
+// the sum; a look-back that waited too long sets st->timeout.
 cudaError_t launch_simplex_index(const int32_t *labels, const int64_t dims[3], int mode,
                                  uint8_t *codes, int64_t *offsets, void *scratch,
-                                 unsigned long long **total_dev, int64_t *ncells_out,
+                                 unsigned long long **total_dev, int64_t *ncells_out, DevStatus *st,
                                  cudaStream_t s) {
-  SimplexGeom g;
-  g.nx = dims[0];
-  g.ny = dims[1];
-  const bool flat = dims[2] == 1;
-  g.cx = dims[0] - 1;
-  g.cy = dims[1] - 1;
-  const int64_t cz = flat ? 1 : dims[2] - 1;
-  g.ncells = (g.cx > 0 && g.cy > 0 && cz > 0) ? g.cx * g.cy * cz : 0;
-  g.per = flat ? 2 : 6;
-  g.mode = mode;
+  const SimplexGeom g = simplex_geom(dims, mode);
   *ncells_out = g.ncells;
-  unsigned long long *total = reinterpret_cast<unsigned long long *>(scratch);
-  *total_dev = total;
-  cudaError_t e = cudaMemsetAsync(total, 0, 8, s);
+  // scratch: the total (8 bytes) and the tile counter, then one word per tile
+  unsigned long long *hdr = reinterpret_cast<unsigned long long *>(scratch);
+  *total_dev = hdr;
+  const int64_t nb = (g.ncells + kTileCells - 1) / kTileCells;
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 256 + (size_t)nb * 8, s);
   if (e != cudaSuccess || g.ncells == 0) return e;
-  g.div_cx = FastDivU32((uint32_t)g.cx);
-  g.div_cy = FastDivU32((uint32_t)g.cy);
-  const int64_t nb = (g.ncells + kCellThreads * kSub - 1) / (kCellThreads * kSub);
-  unsigned int *btot = reinterpret_cast<unsigned int *>(static_cast<char *>(scratch) + 256);
-  const size_t tot_bytes = ((size_t)nb * 4 + 255) & ~(size_t)255;
-  unsigned long long *bbase =
-      reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + 256 + tot_bytes);
-  uint8_t *counts = static_cast<uint8_t *>(scratch) + 256 + tot_bytes +
-                    (((size_t)nb * 8 + 255) & ~(size_t)255);
+  unsigned long long *status = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + 256);
+  const int vec = (reinterpret_cast<uintptr_t>(offsets) & 15) == 0;
   ++tl_launches;
-  k_simplex_codes<<<(unsigned)nb, kCellThreads, 0, s>>>(labels, g, codes, counts, btot);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  ++tl_launches;
-  k_scan_blocks<<<1, 1024, 0, s>>>(btot, nb, bbase, total);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  ++tl_launches;
-  k_simplex_offsets<<<(unsigned)nb, kCellThreads, 0, s>>>(counts, g, bbase, offsets);
+  if (g.per == 2)
+    k_simplex_index<2><<<(unsigned)nb, kCellThreads, 0, s>>>(labels, g, codes, offsets, vec, hdr, status, st);
+  else
+    k_simplex_index<6><<<(unsigned)nb, kCellThreads, 0, s>>>(labels, g, codes, offsets, vec, hdr, status, st);
   return cudaGetLastError();
 }
 

@@ -91,6 +91,24 @@ def test_errors(ctx):
     assert e.value.name == "MS_ERR_INVALID_ARG"
 
 
+def test_offsets_only_8_byte_aligned(ctx):
+    """Offsets at an address that is 8- but not 16-byte aligned take the
+    scalar stores; every offset still equals the oracle's and nothing before
+    the array is touched."""
+    dims = (37, 23, 19)
+    lab = np.random.default_rng(4).integers(0, 3, int(np.prod(dims))).astype(np.int32)
+    ref = oracle.simplex_index(lab, dims)
+    cells, per = ms.simplex_cells(dims)
+    codes = torch.empty(cells * per, dtype=torch.uint8, device="cuda")
+    offs = torch.full((cells + 1,), -1, dtype=torch.int64, device="cuda")
+    total = ms.ms_simplex_index(ctx, torch.from_numpy(lab).cuda(), dims, codes, offs[1:])
+    assert offs[1:].data_ptr() % 16 == 8
+    assert total == ref["total"]
+    assert np.array_equal(offs[1:].cpu().numpy(), ref["cell_offsets"])
+    assert int(offs[0]) == -1
+    assert np.array_equal(codes.cpu().numpy(), ref["codes"])
+
+
 @pytest.mark.slow
 def test_full_size_512(ctx):
     """512^3 MS labels of the smoothed-noise workload: the codes of sampled
@@ -172,3 +190,64 @@ def test_geometry_rejects_a_wrong_total(ctx):
         ms.ms_simplex_geometry(ctx, dl, dims, offs, total - 1, pts)
     assert e.value.name == "MS_ERR_INVALID_ARG"
     ms.ms_simplex_geometry(ctx, dl, dims, offs, total, pts)  # without pairs
+
+
+@pytest.mark.parametrize("dims", [((1 << 21) - 3, 2, 1), ((1 << 21) + 5, 2, 1), ((1 << 21) - 3, 2, 2)])
+def test_geometry_far_coordinates(ctx, dims):
+    """Coordinates up to 2^21 - 3 (the largest whose corner sums the kernel
+    converts without a division) and past 2^21 (the division path): points
+    bit-exact with the oracle.  Sparse labels keep the element count small;
+    triples of labels give the face and triangle centres (thirds)."""
+    g = np.random.default_rng(dims[0] % 97 + dims[2])
+    n = int(np.prod(dims))
+    lab = np.zeros(n, np.int32)
+    hit = g.random(n) < 0.03
+    lab[hit] = g.integers(1, 4, int(hit.sum()))
+    ref = oracle.simplex_geometry(lab, dims, 0)
+    total, pts, pairs, _ = gpu_geometry(ctx, lab, dims, 0)
+    assert total == ref["total"] > 0
+    far = pts.reshape(total, -1)[:, 0] > (1 << 20)
+    assert far.any()
+    assert np.array_equal(pts, ref["pos"]), f"{dims}: points differ"
+    assert np.array_equal(pairs, ref["pairs"]), f"{dims}: pairs differ"
+
+
+@pytest.mark.slow
+def test_geometry_full_size_512(ctx):
+    """Region separators of the 512^3 MS labels, in the launch the index512
+    bench times: for sampled cells, the elements at the cell's offsets equal
+    the oracle's on the cell's own 2x2x2 corners, shifted to the cell (each
+    local coordinate k/n becomes (n o + k)/n rounded, from the exact fraction)."""
+    from test_gpu_fullsize import cached
+    f = cached("noise512", lambda: sf.smoothed_noise((512, 512, 512), 0, sigma=4.0, radius=16))
+    dims = (512, 512, 512)
+    _, _, m, _ = ms.segment(ctx, torch.from_numpy(f).cuda())
+    cells, per = ms.simplex_cells(dims)
+    codes = torch.empty(cells * per, dtype=torch.uint8, device="cuda")
+    offs = torch.empty(cells, dtype=torch.int64, device="cuda")
+    total = ms.ms_simplex_index(ctx, m, dims, codes, offs)
+    del codes
+    pts = torch.empty((total, 3, 3), dtype=torch.float32, device="cuda")
+    pairs = torch.empty((total, 2), dtype=torch.int32, device="cuda")
+    ms.ms_simplex_geometry(ctx, m, dims, offs, total, pts, pairs)
+    frac = {float(np.float32(k / n)): (k, n) for n in (1, 2, 3, 4) for k in range(n + 1)}
+    lab = m.view(512, 512, 512)
+    g = np.random.default_rng(8)
+    seen = 0
+    for c in g.integers(0, cells, size=2000):
+        x, y, z = c % 511, (c // 511) % 511, c // (511 * 511)
+        ref = oracle.simplex_geometry(lab[z:z + 2, y:y + 2, x:x + 2].cpu().numpy(), (2, 2, 2), 0)
+        a = int(offs[c])
+        b = int(offs[c + 1]) if c + 1 < cells else total
+        assert b - a == ref["total"], c
+        if a == b:
+            continue
+        seen += 1
+        assert np.array_equal(pairs[a:b].cpu().numpy(), ref["pairs"]), c
+        want = np.empty_like(ref["pos"])
+        base = np.array([x, y, z], np.int64)
+        for idx in np.ndindex(*ref["pos"].shape):
+            k, n = frac[float(ref["pos"][idx])]
+            want[idx] = np.float32((n * int(base[idx[-1]]) + k) / n)
+        assert np.array_equal(pts[a:b].cpu().numpy(), want), c
+    assert seen > 500
