@@ -13,3 +13,14 @@ def test_fastdiv_matches_hardware_division():
         subprocess.check_call(["g++", "-O2", "-std=c++17", src, "-o", exe])
         out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
+
+
+def test_point_mean_rounding_is_exact():
+    """The geometry kernel's narrow coordinate path: exact conversion and a
+    correctly rounded quotient for every corner sum below 2^23."""
+    src = os.path.join(ROOT, "tests", "native", "mean_rounding_check.c")
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "mean_rounding_check")
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", src, "-o", exe, "-lm"])
+        out = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
