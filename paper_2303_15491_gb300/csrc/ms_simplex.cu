@@ -21,7 +21,7 @@
 namespace msseg {
 namespace {
 
-constexpr int kCellThreads = 256;
+constexpr int kCellThreads = 512;
 
 struct SimplexGeom {
   int64_t nx, ny;        // vertices per row / per plane row count
@@ -193,49 +193,42 @@ __global__ void __launch_bounds__(kCellThreads) k_simplex_index(
   if (c0 < g.ncells) {
     uint32_t x, y, z;
     cell_xyz(g, (uint32_t)c0, &x, &y, &z);
-    const int32_t *r0 = lab + ((int64_t)x + g.nx * ((int64_t)y + g.ny * z));
-    if (full && x + kRunCells <= g.cx) {  // the run stays in one row
-      if (kPer == 2) {
-        const int32_t *r1 = r0 + sy;
-        int32_t a0 = __ldg(r0), a1 = __ldg(r1);
+    // a window of corner labels slides along the row: the column at the
+    // cell's x (rows y, y+1 of planes z, z+1) and the one at x + 1; at the end
+    // of a row the window restarts at the next row's first column
+    const int32_t *r = lab + ((int64_t)x + g.nx * ((int64_t)y + g.ny * z));
+    const bool three = kPer == 6;
+    int32_t a0 = __ldg(r), a1 = __ldg(r + sy), a2 = three ? __ldg(r + sz) : 0,
+            a3 = three ? __ldg(r + sy + sz) : 0;
 #pragma unroll
-        for (int j = 0; j < kRunCells; ++j) {
-          const int32_t b0 = __ldg(r0 + j + 1), b1 = __ldg(r1 + j + 1);
-          n[j] = cell_codes2(a0, b0, a1, b1, 2 * j, w, lut);
-          a0 = b0;
-          a1 = b1;
-        }
-      } else {
-        const int32_t *r1 = r0 + sy, *r2 = r0 + sz, *r3 = r0 + sy + sz;
-        int32_t a0 = __ldg(r0), a1 = __ldg(r1), a2 = __ldg(r2), a3 = __ldg(r3);
-#pragma unroll
-        for (int j = 0; j < kRunCells; ++j) {
-          const int32_t b0 = __ldg(r0 + j + 1), b1 = __ldg(r1 + j + 1), b2 = __ldg(r2 + j + 1),
-                        b3 = __ldg(r3 + j + 1);
+    for (int j = 0; j < kRunCells; ++j) {
+      if (full || c0 + j < g.ncells) {
+        const int32_t b0 = __ldg(r + 1), b1 = __ldg(r + sy + 1), b2 = three ? __ldg(r + sz + 1) : 0,
+                      b3 = three ? __ldg(r + sy + sz + 1) : 0;
+        if (three) {
           const int32_t l[8] = {a0, b0, a1, b1, a2, b2, a3, b3};
           n[j] = cell_codes3(l, 6 * j, w, lut);
-          a0 = b0;
-          a1 = b1;
-          a2 = b2;
-          a3 = b3;
+        } else {
+          n[j] = cell_codes2(a0, b0, a1, b1, 2 * j, w, lut);
         }
-      }
-    } else {  // the run wraps a row or ends the grid: cell by cell
-#pragma unroll
-      for (int j = 0; j < kRunCells; ++j) {
-        const int64_t c = c0 + j;
-        if (c < g.ncells) {
-          cell_xyz(g, (uint32_t)c, &x, &y, &z);
-          const int32_t *q = lab + ((int64_t)x + g.nx * ((int64_t)y + g.ny * z));
-          if (kPer == 2) {
-            n[j] = cell_codes2(__ldg(q), __ldg(q + 1), __ldg(q + sy), __ldg(q + sy + 1), 2 * j, w, lut);
-          } else {
-            int32_t l[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k)
-              l[k] = __ldg(q + ((k & 1) ? 1 : 0) + ((k & 2) ? sy : 0) + ((k & 4) ? sz : 0));
-            n[j] = cell_codes3(l, 6 * j, w, lut);
+        a0 = b0;
+        a1 = b1;
+        a2 = b2;
+        a3 = b3;
+        ++r;
+        if (++x == (uint32_t)g.cx && j + 1 < kRunCells && c0 + j + 1 < g.ncells) {
+          // r is at vertex x = nx - 1: one more is the next row's first vertex,
+          // and past the last row of cells skip the plane's last vertex row
+          x = 0;
+          ++r;
+          if (++y == (uint32_t)g.cy) {
+            y = 0;
+            r += g.nx;
           }
+          a0 = __ldg(r);
+          a1 = __ldg(r + sy);
+          a2 = three ? __ldg(r + sz) : 0;
+          a3 = three ? __ldg(r + sy + sz) : 0;
         }
       }
     }
