@@ -192,6 +192,27 @@ def test_geometry_rejects_a_wrong_total(ctx):
     ms.ms_simplex_geometry(ctx, dl, dims, offs, total, pts)  # without pairs
 
 
+@pytest.mark.parametrize("dims", [(140, 90, 1), (30, 26, 22)])
+def test_geometry_points_not_16_byte_aligned(ctx, dims):
+    """Points at an address 4 bytes past a 16-byte boundary (the stores then
+    go through the window word by word at the ends): bit-exact all the same,
+    and the word before the array untouched."""
+    lab = np.random.default_rng(6).integers(0, 4, int(np.prod(dims))).astype(np.int32)
+    ref = oracle.simplex_geometry(lab, dims, 0)
+    cells, per = ms.simplex_cells(dims)
+    dl = torch.from_numpy(lab).cuda()
+    codes = torch.empty(cells * per, dtype=torch.uint8, device="cuda")
+    offs = torch.empty(cells, dtype=torch.int64, device="cuda")
+    total = ms.ms_simplex_index(ctx, dl, dims, codes, offs)
+    dim = 2 if dims[2] == 1 else 3
+    buf = torch.full((total * dim * dim + 4,), float("nan"), dtype=torch.float32, device="cuda")
+    pts = buf[1:1 + total * dim * dim].view(total, dim, dim)
+    assert pts.data_ptr() % 16 == 4
+    ms.ms_simplex_geometry(ctx, dl, dims, offs, total, pts)
+    assert np.array_equal(pts.cpu().numpy(), ref["pos"])
+    assert torch.isnan(buf[0]) and bool(torch.isnan(buf[1 + total * dim * dim:]).all())
+
+
 @pytest.mark.parametrize("dims", [((1 << 21) - 3, 2, 1), ((1 << 21) + 5, 2, 1), ((1 << 21) - 3, 2, 2)])
 def test_geometry_far_coordinates(ctx, dims):
     """Coordinates up to 2^21 - 3 (the largest whose corner sums the kernel
