@@ -76,29 +76,6 @@ __device__ __forceinline__ void cell_xyz(const SimplexGeom &g, uint32_t c, uint3
   g.div_cy.divmod(q, z, y);
 }
 
-// Block-wide exclusive sum of one value per thread; also the block total.
-__device__ __forceinline__ unsigned int block_excl(unsigned int v, unsigned int *total,
-                                                   unsigned int *sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned int incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) sh[warp] = incl;
-  __syncthreads();
-  unsigned int base = 0, tot = 0;
-#pragma unroll
-  for (int w = 0; w < kCellThreads / 32; ++w) {
-    const unsigned int s = sh[w];
-    if (w < warp) base += s;
-    tot += s;
-  }
-  *total = tot;
-  return base + incl - v;
-}
-
 // Region boundaries (Sec. 4.3): a tetrahedron with exactly three vertices of
 // one label gives the triangle of those three, a triangle with exactly two
 // the edge between them: one element for the splits 3+1 / 2+1.
@@ -150,170 +127,278 @@ __device__ __forceinline__ uint32_t cell_codes2(int32_t l00, int32_t l10, int32_
   return lut[k0] + lut[k1];
 }
 
-// One launch.  Each block takes the next tile of kTileCells cells (tile ids
-// from an atomic counter, so every earlier tile's block has started and will
-// publish without waiting), each thread kRunCells consecutive cells of it:
-// along a row the thread slides a window of corner labels (4 new labels a
-// cell in 3D, 2 in 2D), codes go out as 16-byte vectors.  The tile's element
-// total is published at once; the tile's base is found by decoupled
-// look-back over the earlier tiles' published words (flag and value in one
-// 64-bit word: the tile's own total, or its inclusive prefix), and then
-// every cell's offset is written.
+// One persistent launch.  A block's warps split into kComputeWarps that
+// compute and one look-back warp.  The compute warps take tiles of
+// kTileCells cells in turn (tile ids from an atomic counter), each thread
+// kRunCells consecutive cells: along a row the thread slides a window of
+// corner labels (4 new labels a cell in 3D, 2 in 2D, restarting at the next
+// row's first column when the run reaches a row's end), codes go out as
+// 16-byte vectors, and the tile's element total is published at once.  The
+// look-back warp then finds the tile's base by decoupled look-back over the
+// earlier tiles' published words (flag and value in one 64-bit word: the
+// tile's own total, or its inclusive prefix), while the compute warps go on
+// with their next tile; they write a tile's offsets one tile later, when its
+// base is known.  So no warp computing codes waits for a look-back.
+//
+// Hand-offs within the block are named barriers with fixed counts: compute
+// warps arrive on kBarTile + (i & 1) when tile i is counted, the look-back
+// warp arrives on kBarBase + (i & 1) when its base is in s_base; alternating
+// by parity keeps a fast side from arriving twice on one barrier before the
+// other side has waited on it (each side's arrival for tile i + 2 comes after
+// its wait for the other side's arrival for tile i + 1).
 constexpr int kRunCells = 8;
-constexpr int kTileCells = kCellThreads * kRunCells;
+constexpr int kComputeWarps = kCellThreads / 32 - 1;
+constexpr int kComputeThreads = kComputeWarps * 32;
+constexpr int kTileCells = kComputeThreads * kRunCells;
 constexpr unsigned long long kFlagAgg = 1ull << 62, kFlagPrefix = 2ull << 62,
                              kValueMask = (1ull << 62) - 1;
 // Look-back waits are bounded: past this many polls the call reports a
-// timeout (and the waiting tiles take base 0, so nothing waits on them).
+// timeout (and the waiting tile takes base 0, so nothing waits on it).
 constexpr int kLookbackPolls = 1 << 22;
+constexpr unsigned int kNoTile = 0xffffffffu;
+constexpr int kBarCompute = 1, kBarTile = 2, kBarBase = 4;  // 2, 3 and 4, 5 by parity
 
+template <int kId>
+__device__ __forceinline__ void named_sync(int count) {
+  asm volatile("bar.sync %0, %1;" ::"n"(kId), "r"(count) : "memory");
+}
+template <int kId>
+__device__ __forceinline__ void named_arrive(int count) {
+  asm volatile("bar.arrive %0, %1;" ::"n"(kId), "r"(count) : "memory");
+}
+// the barrier of parity b (ids fixed at compile time)
+template <int kId>
+__device__ __forceinline__ void named_sync_by(int b, int count) {
+  if (b)
+    named_sync<kId + 1>(count);
+  else
+    named_sync<kId>(count);
+}
+template <int kId>
+__device__ __forceinline__ void named_arrive_by(int b, int count) {
+  if (b)
+    named_arrive<kId + 1>(count);
+  else
+    named_arrive<kId>(count);
+}
+
+// Codes and element counts of the run of kRunCells cells at c0 (c0 <
+// ncells); the codes are stored.
 template <int kPer>
-__global__ void __launch_bounds__(kCellThreads) k_simplex_index(
-    const int32_t *__restrict__ lab, SimplexGeom g, uint8_t *__restrict__ codes,
-    int64_t *__restrict__ offsets, int vec_offsets, unsigned long long *hdr,
-    unsigned long long *status, DevStatus *st) {
+__device__ __forceinline__ void run_codes(const int32_t *__restrict__ lab, const SimplexGeom &g,
+                                          int64_t c0, uint8_t *__restrict__ codes,
+                                          const unsigned int *lut, uint32_t (&n)[kRunCells]) {
   constexpr int kWords = kPer * kRunCells / 4;  // code bytes of a run, 4 a word
-  __shared__ unsigned int lut[32];
-  __shared__ unsigned int sh[kCellThreads / 32];
-  __shared__ unsigned long long s_base;
-  __shared__ unsigned int s_tile;
-  fill_elements(lut, kPer, g.mode);
-  if (threadIdx.x == 0) s_tile = atomicAdd(reinterpret_cast<unsigned int *>(hdr + 1), 1u);
-  __syncthreads();
-  const unsigned int tile = s_tile;
-  const int64_t c0 = (int64_t)tile * kTileCells + (int64_t)threadIdx.x * kRunCells;
   const int64_t sy = g.nx, sz = g.nx * g.ny;
   uint32_t w[kWords];
 #pragma unroll
   for (int i = 0; i < kWords; ++i) w[i] = 0;
-  uint32_t n[kRunCells];
 #pragma unroll
   for (int j = 0; j < kRunCells; ++j) n[j] = 0;
   const bool full = c0 + kRunCells <= g.ncells;
-  if (c0 < g.ncells) {
-    uint32_t x, y, z;
-    cell_xyz(g, (uint32_t)c0, &x, &y, &z);
-    // a window of corner labels slides along the row: the column at the
-    // cell's x (rows y, y+1 of planes z, z+1) and the one at x + 1; at the end
-    // of a row the window restarts at the next row's first column
-    const int32_t *r = lab + ((int64_t)x + g.nx * ((int64_t)y + g.ny * z));
-    const bool three = kPer == 6;
-    int32_t a0 = __ldg(r), a1 = __ldg(r + sy), a2 = three ? __ldg(r + sz) : 0,
-            a3 = three ? __ldg(r + sy + sz) : 0;
-#pragma unroll
-    for (int j = 0; j < kRunCells; ++j) {
-      if (full || c0 + j < g.ncells) {
-        const int32_t b0 = __ldg(r + 1), b1 = __ldg(r + sy + 1), b2 = three ? __ldg(r + sz + 1) : 0,
-                      b3 = three ? __ldg(r + sy + sz + 1) : 0;
-        if (three) {
-          const int32_t l[8] = {a0, b0, a1, b1, a2, b2, a3, b3};
-          n[j] = cell_codes3(l, 6 * j, w, lut);
-        } else {
-          n[j] = cell_codes2(a0, b0, a1, b1, 2 * j, w, lut);
-        }
-        a0 = b0;
-        a1 = b1;
-        a2 = b2;
-        a3 = b3;
-        ++r;
-        if (++x == (uint32_t)g.cx && j + 1 < kRunCells && c0 + j + 1 < g.ncells) {
-          // r is at vertex x = nx - 1: one more is the next row's first vertex,
-          // and past the last row of cells skip the plane's last vertex row
-          x = 0;
-          ++r;
-          if (++y == (uint32_t)g.cy) {
-            y = 0;
-            r += g.nx;
-          }
-          a0 = __ldg(r);
-          a1 = __ldg(r + sy);
-          a2 = three ? __ldg(r + sz) : 0;
+  uint32_t x, y, z;
+  cell_xyz(g, (uint32_t)c0, &x, &y, &z);
+  // the window: the column at the cell's x (rows y, y+1 of planes z, z+1)
+  // and the one at x + 1
+  const int32_t *r = lab + ((int64_t)x + g.nx * ((int64_t)y + g.ny * z));
+  const bool three = kPer == 6;
+  int32_t a0 = __ldg(r), a1 = __ldg(r + sy), a2 = three ? __ldg(r + sz) : 0,
           a3 = three ? __ldg(r + sy + sz) : 0;
-        }
+#pragma unroll
+  for (int j = 0; j < kRunCells; ++j) {
+    if (full || c0 + j < g.ncells) {
+      const int32_t b0 = __ldg(r + 1), b1 = __ldg(r + sy + 1), b2 = three ? __ldg(r + sz + 1) : 0,
+                    b3 = three ? __ldg(r + sy + sz + 1) : 0;
+      if (three) {
+        const int32_t l[8] = {a0, b0, a1, b1, a2, b2, a3, b3};
+        n[j] = cell_codes3(l, 6 * j, w, lut);
+      } else {
+        n[j] = cell_codes2(a0, b0, a1, b1, 2 * j, w, lut);
       }
-    }
-    if (full) {  // c0 * kPer is a multiple of 16 bytes
-      uint4 *dst = reinterpret_cast<uint4 *>(codes + c0 * kPer);
-#pragma unroll
-      for (int i = 0; i < kWords / 4; ++i) dst[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
-    } else {
-#pragma unroll
-      for (int i = 0; i < kPer * kRunCells; ++i)
-        if (c0 + i / kPer < g.ncells) codes[c0 * kPer + i] = (uint8_t)(w[i / 4] >> (8 * (i % 4)));
+      a0 = b0;
+      a1 = b1;
+      a2 = b2;
+      a3 = b3;
+      ++r;
+      if (++x == (uint32_t)g.cx && j + 1 < kRunCells && c0 + j + 1 < g.ncells) {
+        // r is at vertex x = nx - 1: one more is the next row's first vertex,
+        // and past the last row of cells skip the plane's last vertex row
+        x = 0;
+        ++r;
+        if (++y == (uint32_t)g.cy) {
+          y = 0;
+          r += g.nx;
+        }
+        a0 = __ldg(r);
+        a1 = __ldg(r + sy);
+        a2 = three ? __ldg(r + sz) : 0;
+        a3 = three ? __ldg(r + sy + sz) : 0;
+      }
     }
   }
-  uint32_t mine = 0;
+  if (full) {  // c0 * kPer is a multiple of 16 bytes
+    uint4 *dst = reinterpret_cast<uint4 *>(codes + c0 * kPer);
 #pragma unroll
-  for (int j = 0; j < kRunCells; ++j) mine += n[j];
-  unsigned int tot = 0;
-  const unsigned int ex = block_excl(mine, &tot, sh);
-  // the tile's base: look back over the earlier tiles (warp 0)
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    unsigned long long base = 0;
-    if (tile == 0) {
-      if (lane == 0) *(volatile unsigned long long *)&status[0] = kFlagPrefix | tot;
-    } else {
-      if (lane == 0) *(volatile unsigned long long *)&status[tile] = kFlagAgg | tot;
-      long long j = (long long)tile - 1;  // newest tile not yet summed
-      int polls = 0;
-      bool timed_out = false;
-      for (;;) {
-        const long long idx = j - lane;
-        unsigned long long word = kFlagPrefix;  // before tile 0: a prefix of 0
-        if (idx >= 0) word = *(volatile unsigned long long *)&status[idx];
-        unsigned int pm;
-        for (;;) {  // until every lane before the nearest prefix has published
-          pm = __ballot_sync(0xffffffffu, (word >> 62) == 2);
-          const unsigned int em = __ballot_sync(0xffffffffu, (word >> 62) == 0);
-          const unsigned int need = pm ? em & ((pm & (~pm + 1u)) - 1u) : em;
-          if (!need) break;
-          if (__any_sync(0xffffffffu, ++polls > kLookbackPolls ||
-                                          *(volatile unsigned int *)&st->timeout != 0)) {
-            timed_out = true;
-            break;
-          }
-          __nanosleep(32);
-          if (need >> lane & 1u) word = *(volatile unsigned long long *)&status[idx];
-        }
-        if (timed_out) break;
-        const int stop = pm ? __ffs(pm) - 1 : 31;  // lanes 0..stop are summed
-        unsigned long long v = lane <= stop ? (word & kValueMask) : 0ull;
+    for (int i = 0; i < kWords / 4; ++i) dst[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+  } else {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        base += v;
-        if (pm) break;
-        j -= 32;
-      }
-      if (timed_out) {
+    for (int i = 0; i < kPer * kRunCells; ++i)
+      if (c0 + i / kPer < g.ncells) codes[c0 * kPer + i] = (uint8_t)(w[i / 4] >> (8 * (i % 4)));
+  }
+}
+
+// Exclusive sum over the compute threads of one value each; also the total.
+__device__ __forceinline__ unsigned int compute_excl(unsigned int v, unsigned int *total,
+                                                     unsigned int *sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) sh[warp] = incl;
+  named_sync<kBarCompute>(kComputeThreads);
+  unsigned int base = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kComputeWarps; ++w) {
+    const unsigned int s = sh[w];
+    if (w < warp) base += s;
+    tot += s;
+  }
+  *total = tot;
+  return base + incl - v;
+}
+
+// Base of `tile` (whose own total is already published): the sum of the
+// earlier tiles' totals, read back 32 words at a time until one holds an
+// inclusive prefix.  Run by one whole warp; the result is in every lane.
+__device__ unsigned long long look_back(unsigned long long *status, unsigned int tile,
+                                        DevStatus *st) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  long long j = (long long)tile - 1;  // newest tile not yet summed
+  int polls = 0;
+  for (;;) {
+    const long long idx = j - lane;
+    unsigned long long word = kFlagPrefix;  // before tile 0: a prefix of 0
+    if (idx >= 0) word = *(volatile unsigned long long *)&status[idx];
+    unsigned int pm;
+    for (;;) {  // until every lane before the nearest prefix has published
+      pm = __ballot_sync(0xffffffffu, (word >> 62) == 2);
+      const unsigned int em = __ballot_sync(0xffffffffu, (word >> 62) == 0);
+      const unsigned int need = pm ? em & ((pm & (~pm + 1u)) - 1u) : em;
+      if (!need) break;
+      if (__any_sync(0xffffffffu, ++polls > kLookbackPolls ||
+                                      *(volatile unsigned int *)&st->timeout != 0)) {
         if (lane == 0) atomicOr(&st->timeout, 1u);
-        base = 0;
+        return 0;
       }
-      if (lane == 0) *(volatile unsigned long long *)&status[tile] = kFlagPrefix | ((base + tot) & kValueMask);
+      __nanosleep(32);
+      if (need >> lane & 1u) word = *(volatile unsigned long long *)&status[idx];
     }
-    if (lane == 0) {
-      s_base = base;
-      if ((int64_t)(tile + 1) * kTileCells >= g.ncells) hdr[0] = base + tot;  // the last tile
+    const int stop = pm ? __ffs(pm) - 1 : 31;  // lanes 0..stop are summed
+    unsigned long long v = lane <= stop ? (word & kValueMask) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    base += v;
+    if (pm) return base;
+    j -= 32;
+  }
+}
+
+template <int kPer>
+__global__ void __launch_bounds__(kCellThreads, 2) k_simplex_index(
+    const int32_t *__restrict__ lab, SimplexGeom g, uint8_t *__restrict__ codes,
+    int64_t *__restrict__ offsets, int vec_offsets, unsigned long long *hdr,
+    unsigned long long *status, unsigned int ntiles, DevStatus *st) {
+  __shared__ unsigned int lut[32];
+  __shared__ unsigned int sh[kComputeWarps];
+  __shared__ unsigned int s_fetch;
+  __shared__ unsigned int s_tile[2], s_tot[2];
+  __shared__ unsigned long long s_base[2];
+  fill_elements(lut, kPer, g.mode);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  if (warp == kComputeWarps) {
+    // ---- the look-back warp: tile i of this block, in the order computed
+    for (int i = 0;; ++i) {
+      const int b = i & 1;
+      named_sync_by<kBarTile>(b, kCellThreads);
+      const unsigned int t = s_tile[b];
+      if (t == kNoTile) return;  // the compute warps have finished
+      const unsigned int tot = s_tot[b];
+      const unsigned long long base = t == 0 ? 0ull : look_back(status, t, st);
+      if ((threadIdx.x & 31) == 0) {
+        if (t != 0) *(volatile unsigned long long *)&status[t] = kFlagPrefix | ((base + tot) & kValueMask);
+        if (t + 1 == ntiles) hdr[0] = base + tot;  // the element total
+        s_base[b] = base;
+      }
+      __threadfence_block();
+      named_arrive_by<kBarBase>(b, kCellThreads);
     }
   }
-  __syncthreads();
-  if (c0 < g.ncells) {
-    long long o[kRunCells];
-    unsigned long long run = s_base + ex;
+  // ---- the compute warps
+  uint32_t prev_n[kRunCells / 4];  // the previous tile's counts (a byte each), exclusive sum, run
+  unsigned int prev_ex = 0;
+  int64_t prev_c0 = -1;
+  for (int i = 0;; ++i) {
+    const int b = i & 1;
+    if (threadIdx.x == 0) s_fetch = atomicAdd(reinterpret_cast<unsigned int *>(hdr + 1), 1u);
+    named_sync<kBarCompute>(kComputeThreads);
+    const unsigned int t = s_fetch < ntiles ? s_fetch : kNoTile;
+    uint32_t n[kRunCells];
+    unsigned int ex = 0;
+    const int64_t c0 = t == kNoTile ? -1 : (int64_t)t * kTileCells + (int64_t)threadIdx.x * kRunCells;
+    if (t != kNoTile) {
+      if (c0 < g.ncells) {
+        run_codes<kPer>(lab, g, c0, codes, lut, n);
+      } else {
 #pragma unroll
-    for (int j = 0; j < kRunCells; ++j) {
-      o[j] = (long long)run;
-      run += n[j];
+        for (int j = 0; j < kRunCells; ++j) n[j] = 0;
+      }
+      uint32_t mine = 0;
+#pragma unroll
+      for (int j = 0; j < kRunCells; ++j) mine += n[j];
+      unsigned int tot = 0;
+      ex = compute_excl(mine, &tot, sh);  // also orders s_fetch's read before its next write
+      if (threadIdx.x == 0) {
+        // publish the tile's total (tile 0: its prefix) for later tiles' look-back
+        *(volatile unsigned long long *)&status[t] = (t == 0 ? kFlagPrefix : kFlagAgg) | tot;
+        s_tot[b] = tot;
+      }
     }
-    if (full && vec_offsets) {
-      longlong2 *dst = reinterpret_cast<longlong2 *>(offsets + c0);
+    if (threadIdx.x == 0) s_tile[b] = t;
+    __threadfence_block();
+    named_arrive_by<kBarTile>(b, kCellThreads);
+    // the previous tile's offsets, now that its base is known
+    if (i > 0) {  // tile i - 1 was a tile: the block stops at its first kNoTile
+      named_sync_by<kBarBase>(b ^ 1, kCellThreads);
+      if (prev_c0 >= 0 && prev_c0 < g.ncells) {
+        long long o[kRunCells];
+        unsigned long long run = s_base[b ^ 1] + prev_ex;
 #pragma unroll
-      for (int i = 0; i < kRunCells / 2; ++i) dst[i] = make_longlong2(o[2 * i], o[2 * i + 1]);
-    } else {
+        for (int j = 0; j < kRunCells; ++j) {
+          o[j] = (long long)run;
+          run += (prev_n[j / 4] >> (8 * (j % 4))) & 0xffu;
+        }
+        if (prev_c0 + kRunCells <= g.ncells && vec_offsets) {
+          longlong2 *dst = reinterpret_cast<longlong2 *>(offsets + prev_c0);
 #pragma unroll
-      for (int j = 0; j < kRunCells; ++j)
-        if (c0 + j < g.ncells) offsets[c0 + j] = o[j];
+          for (int j = 0; j < kRunCells / 2; ++j) dst[j] = make_longlong2(o[2 * j], o[2 * j + 1]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < kRunCells; ++j)
+            if (prev_c0 + j < g.ncells) offsets[prev_c0 + j] = o[j];
+        }
+      }
     }
+    if (t == kNoTile) return;
+#pragma unroll
+    for (int j = 0; j < kRunCells / 4; ++j)
+      prev_n[j] = n[4 * j] | n[4 * j + 1] << 8 | n[4 * j + 2] << 16 | n[4 * j + 3] << 24;  // each <= 72
+    prev_ex = ex;
+    prev_c0 = c0;
   }
 }
 
@@ -762,11 +847,21 @@ cudaError_t launch_simplex_index(const int32_t *labels, const int64_t dims[3], i
   if (e != cudaSuccess || g.ncells == 0) return e;
   unsigned long long *status = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + 256);
   const int vec = (reinterpret_cast<uintptr_t>(offsets) & 15) == 0;
+  // persistent: as many blocks as are resident at once, at most one a tile
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const void *kern = g.per == 2 ? (const void *)k_simplex_index<2> : (const void *)k_simplex_index<6>;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCellThreads, 0);
+  const int64_t cap = (int64_t)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+  const unsigned int grid = (unsigned)(nb < cap ? nb : cap);
   ++tl_launches;
   if (g.per == 2)
-    k_simplex_index<2><<<(unsigned)nb, kCellThreads, 0, s>>>(labels, g, codes, offsets, vec, hdr, status, st);
+    k_simplex_index<2><<<grid, kCellThreads, 0, s>>>(labels, g, codes, offsets, vec, hdr, status,
+                                                     (unsigned)nb, st);
   else
-    k_simplex_index<6><<<(unsigned)nb, kCellThreads, 0, s>>>(labels, g, codes, offsets, vec, hdr, status, st);
+    k_simplex_index<6><<<grid, kCellThreads, 0, s>>>(labels, g, codes, offsets, vec, hdr, status,
+                                                     (unsigned)nb, st);
   return cudaGetLastError();
 }
 
