@@ -66,6 +66,7 @@ struct RankScratch {
   unsigned long long *list;        // unique keys, up to max_unique
   unsigned long long *tmp;         // sort ping-pong, up to max_unique
   unsigned int *hist;              // 256 * sort_blocks_cap
+  unsigned int *scan_sums;         // 256 chunk sums of the histogram scan
   unsigned int capacity;           // power of two
   unsigned int max_unique;         // capacity / 2
   unsigned int probe_limit;        // longest insert probe before the set counts as full

@@ -121,30 +121,102 @@ __global__ void k_radix_hist(const unsigned long long *__restrict__ in, unsigned
 }
 
 // Exclusive scan, in place, of the digit-major histogram hist[d * B + j]:
-// afterwards entry (d, j) is where block j's keys of digit d start.  One
-// block; thread t owns a contiguous chunk.
-__global__ void __launch_bounds__(1024) k_radix_scan(unsigned int *__restrict__ hist,
-                                                     unsigned int n) {
-  __shared__ unsigned int sh[1024];
-  const unsigned int chunk = (n + 1023) / 1024;
-  const unsigned int lo = min(n, threadIdx.x * chunk), hi = min(n, lo + chunk);
-  unsigned int s = 0;
-#pragma unroll 8
-  for (unsigned int i = lo; i < hi; ++i) s += hist[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const unsigned int t = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0u;
-    __syncthreads();
-    sh[threadIdx.x] += t;
-    __syncthreads();
+// afterwards entry (d, j) is where block j's keys of digit d start.  Two
+// launches over chunks of kScanChunk entries (n is a multiple of 256, so
+// every chunk starts 16-byte aligned): the chunk sums, then each chunk's
+// scan from the sum of the chunks before it.  Every thread reads and writes
+// 8 consecutive entries as two 16-byte vectors.
+constexpr int kScanThreads = 1024;
+constexpr int kScanChunk = kScanThreads * 8;
+constexpr int kScanMaxChunks = 256;  // rank scratch keeps this many chunk sums
+
+__device__ __forceinline__ void load8(const unsigned int *p, unsigned int i0, unsigned int n,
+                                      unsigned int (&v)[8]) {
+  if (i0 + 8 <= n) {
+    const uint4 a = *reinterpret_cast<const uint4 *>(p + i0), b = *reinterpret_cast<const uint4 *>(p + i0 + 4);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = i0 + k < n ? p[i0 + k] : 0u;
   }
-  unsigned int run = sh[threadIdx.x] - s;
-#pragma unroll 8
-  for (unsigned int i = lo; i < hi; ++i) {
-    const unsigned int v = hist[i];
-    hist[i] = run;
-    run += v;
+}
+
+// Block-wide exclusive sum of one value per thread (kScanThreads threads);
+// also the total.
+__device__ __forceinline__ unsigned int scan_block_excl(unsigned int v, unsigned int *total,
+                                                        unsigned int *sh) {
+  const unsigned int lane = lane_id(), warp = threadIdx.x >> 5;
+  unsigned int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= (unsigned)o) incl += t;
+  }
+  if (lane == 31) sh[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned int w = sh[lane];
+    unsigned int wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int t = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= (unsigned)o) wi += t;
+    }
+    sh[lane] = wi - w;  // exclusive
+    if (lane == 31) sh[32] = wi;
+  }
+  __syncthreads();
+  *total = sh[32];
+  return sh[warp] + incl - v;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_sums(const unsigned int *__restrict__ hist,
+                                                            unsigned int n,
+                                                            unsigned int *__restrict__ sums) {
+  __shared__ unsigned int sh[33];
+  unsigned int v[8];
+  load8(hist, blockIdx.x * kScanChunk + threadIdx.x * 8, n, v);
+  unsigned int t = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += v[k];
+  unsigned int tot = 0;
+  scan_block_excl(t, &tot, sh);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(unsigned int *__restrict__ hist,
+                                                              unsigned int n,
+                                                              const unsigned int *__restrict__ sums) {
+  __shared__ unsigned int sh[33];
+  __shared__ unsigned int s_before;
+  if (threadIdx.x < 32) {  // the chunks before this one (at most kScanMaxChunks)
+    unsigned int b = 0;
+    for (unsigned int j = threadIdx.x; j < blockIdx.x; j += 32) b += sums[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    if (threadIdx.x == 0) s_before = b;
+  }
+  const unsigned int i0 = blockIdx.x * kScanChunk + threadIdx.x * 8;
+  unsigned int v[8];
+  load8(hist, i0, n, v);
+  unsigned int t = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += v[k];
+  unsigned int tot = 0;
+  unsigned int run = scan_block_excl(t, &tot, sh) + s_before;  // the scan's barriers order s_before
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const unsigned int x = v[k];
+    v[k] = run;
+    run += x;
+  }
+  if (i0 + 8 <= n) {
+    *reinterpret_cast<uint4 *>(hist + i0) = make_uint4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<uint4 *>(hist + i0 + 4) = make_uint4(v[4], v[5], v[6], v[7]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (i0 + k < n) hist[i0 + k] = v[k];
   }
 }
 
@@ -164,7 +236,7 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const unsigned long long 
   __shared__ unsigned int wcnt[8][256];
   const unsigned int warp = threadIdx.x >> 5, lane = lane_id();
   if (scanned) {
-    // k_radix_scan left each (digit, block) its first output position
+    // the histogram scan left each (digit, block) its first output position
     run[threadIdx.x] = hist[threadIdx.x * gridDim.x + blockIdx.x];
     __syncthreads();
   } else {
@@ -288,6 +360,8 @@ void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs) {
   rs->table_vals = reinterpret_cast<int32_t *>(p);
   p += (size_t)capacity * 4;
   rs->hist = reinterpret_cast<unsigned int *>(p);
+  p += 256 * (size_t)sort_blocks_cap_of(capacity) * 4;
+  rs->scan_sums = reinterpret_cast<unsigned int *>(p);  // the last 4 * 256 bytes
   rs->sort_blocks_cap = sort_blocks_cap_of(capacity);
 }
 
@@ -320,8 +394,11 @@ cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bit
     ++tl_launches;
     k_radix_hist<<<blocks, 256, 0, s>>>(src, m, m_dev, b, shift, rs.hist);
     if (large) {
-      ++tl_launches;
-      k_radix_scan<<<1, 1024, 0, s>>>(rs.hist, 256 * blocks);
+      const unsigned int n = 256 * blocks, chunks = (n + kScanChunk - 1) / kScanChunk;
+      if (chunks > (unsigned)kScanMaxChunks) return cudaErrorInvalidValue;  // blocks <= 8 an SM
+      tl_launches += 2;
+      k_scan_sums<<<chunks, kScanThreads, 0, s>>>(rs.hist, n, rs.scan_sums);
+      k_scan_chunks<<<chunks, kScanThreads, 0, s>>>(rs.hist, n, rs.scan_sums);
     }
     ++tl_launches;
     k_radix_scatter<<<blocks, 256, 0, s>>>(src, dst, m, m_dev, b, shift, rs.hist, large ? 1 : 0);
