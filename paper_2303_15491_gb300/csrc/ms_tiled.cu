@@ -1249,6 +1249,10 @@ __global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, int m
     }
     if (found == 0xffffffffu) atomicOr(&st->hash_overflow, 1u);
     ts.pool_slot[p] = found;
+    // with a set larger than L2 the resolved pair replaces the entry's roots,
+    // so that the write kernel reads it in order instead of from the set
+    // (resolving a resolved entry again gives the same pair)
+    if (rs.capacity > kSetInL2) ts.pool_roots[p] = make_int2(a, d);
   }
 }
 
@@ -1268,7 +1272,7 @@ __global__ void k_field_starts(const unsigned long long *__restrict__ sorted, un
 // kernel (3D: the z-column (x0 + lane, y0 + warp, .); 2D: the y-run at
 // x0 + lane + 32 (warp % 4)); its 16 pair numbers are one 32-byte vector.
 // kFlat selects the 2D tiles, which follow the 3D ones.
-template <bool kFlat, bool kSingle>
+template <bool kFlat, bool kSingle, bool kInPool>
 __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch ts, RankScratch rs,
                                                          const DevStatus *st) {
   // A replayed graph runs this kernel even when an earlier stage found its
@@ -1313,6 +1317,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch 
     const long long b = ts.tile_base[gt];
     const int cnt = ts.tile_count[gt];
     const uint32_t *src = ts.pool_slot + b;
+    const int2 *res = ts.pool_roots + b;  // resolved (asc, desc) of each tile pair
     const bool staged = cnt <= kStageCap;
     const bool batch = bt.key_mode == kKeyBatch;
     const int first = batch ? (int)ts.fstart[fi] : 0;
@@ -1323,14 +1328,21 @@ __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch 
       q0 = __ldcs(pid4);
       q1 = __ldcs(pid4 + 1);
     }
-    auto entry = [&](uint32_t sl) {
+    // kInPool (a set of more than kSetInL2 entries): k_resolve_pairs left
+    // each resolved pair in its pool entry
+    auto entry = [&](int i) {
+      const uint32_t sl = __ldcs(src + i);
+      if (kInPool) {
+        const int2 ad = __ldcs(res + i);
+        return make_int4(ad.x, ad.y, __ldg(&rs.table_vals[sl]) - first, 0);
+      }
       const unsigned long long key = __ldg(&rs.table_keys[sl]);
       const int r = __ldg(&rs.table_vals[sl]) - first;
       return batch ? make_int4((int)((key >> 24) & 0xffffffull), (int)(key & 0xffffffull), r, 0)
                    : make_int4((int)(key >> 32), (int)(uint32_t)key, r, 0);
     };
     if (staged)
-      for (int i = threadIdx.x; i < cnt; i += kThreads) T[i] = entry(__ldcs(src + i));
+      for (int i = threadIdx.x; i < cnt; i += kThreads) T[i] = entry(i);
     __syncthreads();
     if (col_in) {
       int32_t *__restrict__ asc = fd.asc, *__restrict__ desc = fd.desc, *__restrict__ ms = fd.ms;
@@ -1339,7 +1351,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch 
       for (int j = 0; j < kRun; ++j) {
         if (j >= n_here) break;
         const int id = (int)((w[j / 2] >> (16 * (j & 1))) & 0xffffu);
-        const int4 t = staged ? T[id] : entry(src[id]);
+        const int4 t = staged ? T[id] : entry(id);
         const int64_t v = v0 + stride * j;
         __stcs(asc + v, t.x);
         __stcs(desc + v, t.y);
@@ -1574,13 +1586,19 @@ cudaError_t launch_field_starts(const Batch &b, const TiledScratch &ts, const Ra
 cudaError_t launch_tile_write(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
                               const DevStatus *st, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
+  const bool in_pool = rs.capacity > kSetInL2;  // as k_resolve_pairs decides on the device
   if (b.tiles3 > 0) {
     const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * b.tune.write_ctas);
     ++tl_launches;
     if (b.n_fields == 1)
-      k_tile_write<false, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+      if (in_pool)
+        k_tile_write<false, true, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+      else
+        k_tile_write<false, true, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+    else if (in_pool)
+      k_tile_write<false, false, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
     else
-      k_tile_write<false, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+      k_tile_write<false, false, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -1588,9 +1606,14 @@ cudaError_t launch_tile_write(const Batch &b, const TiledScratch &ts, const Rank
     const int64_t grid = std::min<int64_t>(b.total_tiles - b.tiles3, (int64_t)sms() * b.tune.write_ctas);
     ++tl_launches;
     if (b.n_fields == 1)
-      k_tile_write<true, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+      if (in_pool)
+        k_tile_write<true, true, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+      else
+        k_tile_write<true, true, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+    else if (in_pool)
+      k_tile_write<true, false, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
     else
-      k_tile_write<true, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+      k_tile_write<true, false, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
     e = cudaGetLastError();
   }
   return e;

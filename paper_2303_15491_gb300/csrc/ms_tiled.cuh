@@ -99,7 +99,8 @@ struct TiledScratch {
   unsigned long long *pool_count;  // pairs reserved by all tiles
   unsigned int *queue;             // work-queue counters: tile 3D, tile 2D, write 3D, write 2D
   unsigned long long pool_cap;
-  int2 *pool_roots;   // per tile pair: (dn-root, up-root), global index | kExitFlag if an exit
+  int2 *pool_roots;   // per tile pair: (dn-root, up-root), global index | kExitFlag if an exit;
+                      // the resolved pair once resolved, if the set exceeds kSetInL2 entries
   uint32_t *pool_field;  // per tile pair: its field
   uint32_t *fstart;      // per field: index of its first pair in the sorted pair list
   uint32_t *pool_slot;  // per tile pair: slot of its (asc, desc) pair in the global pair set
@@ -130,6 +131,10 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
 // kChaseGraph resolves every pair through the jumped face graph
 // (launch_face_graph_*).  clear_table: reset the pair set first.
 enum { kChaseProbe = 0, kChaseBudget = 1, kChasePending = 2, kChaseGraph = 3 };
+// Pair sets of more entries than this (12 bytes each: beyond about a third of
+// L2) are read in random order from DRAM; then k_resolve_pairs stores each
+// resolved pair over its pool entry's roots and k_tile_write reads it there.
+constexpr unsigned int kSetInL2 = 1u << 22;
 constexpr int kProbeHops = 4;
 // The probe samples about kProbeSample pairs, when there are kProbeMinPairs.
 constexpr unsigned long long kProbeSample = 16384, kProbeMinPairs = 65536;

@@ -104,3 +104,26 @@ def test_broad_1024(ctx):
 def test_broad_32768_2d(ctx):
     f = cached("broad32768", lambda: sf.broad_gaussians_ramp((32768, 32768, 1), 0))
     check_full(ctx, f, n_walk=200, seed=3)
+
+
+@pytest.mark.parametrize("shape", [(4096, 4096), (224, 224, 224)])
+def test_pair_set_larger_than_l2(ctx, shape):
+    """White noise: millions of regions, so the pair set outgrows L2 and the
+    resolved pairs reach the write kernel through the pool entries -- labels
+    and region count equal to the oracle's, vertex for vertex."""
+    from gpu_util import assert_same_labels
+    f = np.random.default_rng(31).standard_normal(shape).astype(np.float32)
+    fresh = ms.ms_create(0)
+    try:
+        dev = torch.from_numpy(f).cuda()
+        outs = [torch.empty(f.size, dtype=torch.int32, device="cuda") for _ in range(3)]
+        ref = oracle.segment(f)
+        for call in range(3):  # step by step, then captured, then a graph replay
+            ms.ms_segment(fresh, dev, ms.dims_of(f), ms.dtype_code(f), *outs)
+            k = ms.ms_last_region_count(fresh)
+            # twice the regions, rounded up to a power of two: above 2^22 entries
+            assert k > (1 << 21), k
+            got = tuple(o.cpu().numpy() for o in outs) + (k,)
+            assert_same_labels(got, ref, f"white noise {shape}, call {call}")
+    finally:
+        ms.ms_destroy(fresh)
