@@ -563,6 +563,7 @@ __device__ void boundaries(ElemRecorder &o, const int32_t *L, int n) {
 // |m| | k_x << 3 | k_y << 6 | k_z << 9 with k_a the corners of m past axis
 // a's step (their coordinate along a is the cell's plus one).
 struct GeoTables {
+  float4 frac[6 * 16];  // per chain and subset: k_a / |m| rounded (x, y, z), w: the axes where it is 2/3
   uint32_t desc[32 * kMaxElems];
   uint32_t count[32];
   uint32_t corners[6];
@@ -606,35 +607,38 @@ __device__ void fill_geo_tables(GeoTables &t, int per, int mode) {
       for (int kk = k; kk <= steps; ++kk) above |= 1u << (4 * a + kk);
     }
     t.corners[p] = corners;
-    for (unsigned m = 0; m < 16; ++m)
-      t.subset[p * 16 + m] = (uint32_t)__popc(m) | (uint32_t)__popc(m & above & 15u) << 3 |
-                             (uint32_t)__popc(m & (above >> 4) & 15u) << 6 |
-                             (uint32_t)__popc(m & (above >> 8) & 15u) << 9;
+    for (unsigned m = 0; m < 16; ++m) {
+      const uint32_t cnt = (uint32_t)__popc(m), kx = (uint32_t)__popc(m & above & 15u),
+                     ky = (uint32_t)__popc(m & (above >> 4) & 15u),
+                     kz = (uint32_t)__popc(m & (above >> 8) & 15u);
+      t.subset[p * 16 + m] = cnt | kx << 3 | ky << 6 | kz << 9;
+      const float c = (float)(cnt ? cnt : 1u);
+      const uint32_t two_thirds = (cnt == 3 && kx == 2) | (cnt == 3 && ky == 2) << 1 |
+                                  (cnt == 3 && kz == 2) << 2;
+      t.frac[p * 16 + m] = make_float4(__fdiv_rn((float)kx, c), __fdiv_rn((float)ky, c),
+                                       __fdiv_rn((float)kz, c), __uint_as_float(two_thirds));
+    }
   }
 }
 
-// Largest vertex coordinate for which mean_of's sums stay below 2^23.
+// Largest vertex coordinate of the narrow path.
 constexpr int64_t kNarrowCoord = (1 << 21) - 1;
+// 5/3 rounded to float: the one narrow-path coordinate that o + fl(2/3) rounds
+// the other way (o = 1)
+constexpr uint32_t kFiveThirdsBits = 0x3FD55555u;
 
-// Mean of cnt corners (1..4) whose coordinate along an axis is o for cnt - k
-// of them and o + 1 for k: (cnt * o + k) / cnt rounded to nearest even.
-// Narrow: the sum is below 2^23, so it converts exactly by placing it in the
-// mantissa of 2^23; with R = 1/cnt rounded, q = s R is exact for cnt = 1, 2,
-// 4 (the residual is then zero), and for cnt = 3 one FMA residual step
-// (Markstein's correction) makes it the correctly rounded quotient -- checked
-// for every s below 2^23 against the exact quotient.  Wide: an IEEE division.
-template <bool kWide>
-__device__ __forceinline__ float mean_of(uint32_t o, uint32_t k, uint32_t cnt) {
-  if (kWide) return __fdiv_rn((float)((uint64_t)cnt * o + k), (float)cnt);
-  const float f = __uint_as_float(0x4B000000u | (cnt * o + k)) - 8388608.0f;
-  const float c = __uint_as_float(0x4B000000u | cnt) - 8388608.0f;
-  const float R = cnt == 3 ? 1.0f / 3.0f : (cnt == 4 ? 0.25f : (cnt == 2 ? 0.5f : 1.0f));
-  const float q = f * R;
-  return fmaf(fmaf(-q, c, f), R, q);
+// A point coordinate is the mean of cnt corners (1..4) whose coordinate along
+// the axis is o for cnt - k of them and o + 1 for k: (cnt o + k) / cnt rounded
+// to nearest even.  Narrow path (o below 2^21): fl(o) + fl(k / cnt), which is
+// exact for cnt = 1, 2, 4 and the correctly rounded value for thirds except
+// k / cnt = 2/3 at o = 1 -- checked for every o below 2^21 against the exact
+// quotient.  Wide path: the sum in 64 bits and an IEEE division.
+__device__ __forceinline__ float mean_wide(uint32_t o, uint32_t k, uint32_t cnt) {
+  return __fdiv_rn((float)((uint64_t)cnt * o + k), (float)cnt);
 }
 
 template <int kPer, bool kWide>
-__global__ void __launch_bounds__(kGeoThreads) k_simplex_geometry(
+__global__ void __launch_bounds__(kGeoThreads, 6) k_simplex_geometry(
     const int32_t *__restrict__ lab, SimplexGeom g, const int64_t *__restrict__ offsets,
     int64_t total, float *__restrict__ pos, int32_t *__restrict__ pairs, int pairs8, DevStatus *st) {
   constexpr int kDim = kPer == 2 ? 2 : 3;  // coordinates per point = points per element
@@ -730,14 +734,29 @@ __global__ void __launch_bounds__(kGeoThreads) k_simplex_geometry(
         }
         const int code = (int)((oc >> (5 * p)) & 31u);
         const uint32_t d = tab.desc[code * kMaxElems + r];
-        const uint32_t *sub = tab.subset + p * 16;
+        if (kWide) {
+          const uint32_t *sub = tab.subset + p * 16;
 #pragma unroll
-        for (int k = 0; k < kDim; ++k) {
-          const uint32_t q = sub[(d >> (4 * k)) & 15u];
-          const uint32_t cnt = q & 7u;
-          win[lane * kS + k * kDim] = mean_of<kWide>(ox, (q >> 3) & 7u, cnt);
-          win[lane * kS + k * kDim + 1] = mean_of<kWide>(oy, (q >> 6) & 7u, cnt);
-          if (kDim == 3) win[lane * kS + k * kDim + 2] = mean_of<kWide>(oz, (q >> 9) & 7u, cnt);
+          for (int k = 0; k < kDim; ++k) {
+            const uint32_t q = sub[(d >> (4 * k)) & 15u];
+            const uint32_t cnt = q & 7u;
+            win[lane * kS + k * kDim] = mean_wide(ox, (q >> 3) & 7u, cnt);
+            win[lane * kS + k * kDim + 1] = mean_wide(oy, (q >> 6) & 7u, cnt);
+            if (kDim == 3) win[lane * kS + k * kDim + 2] = mean_wide(oz, (q >> 9) & 7u, cnt);
+          }
+        } else {
+          const float fx = (float)ox, fy = (float)oy, fz = (float)oz;  // exact below 2^24
+          const uint32_t one = (ox == 1u) | (oy == 1u) << 1 | (oz == 1u) << 2;
+          const float five_thirds = __uint_as_float(kFiveThirdsBits);
+          const float4 *fr = tab.frac + p * 16;
+#pragma unroll
+          for (int k = 0; k < kDim; ++k) {
+            const float4 q = fr[(d >> (4 * k)) & 15u];
+            const uint32_t fix = __float_as_uint(q.w) & one;
+            win[lane * kS + k * kDim] = (fix & 1u) ? five_thirds : fx + q.x;
+            win[lane * kS + k * kDim + 1] = (fix & 2u) ? five_thirds : fy + q.y;
+            if (kDim == 3) win[lane * kS + k * kDim + 2] = (fix & 4u) ? five_thirds : fz + q.z;
+          }
         }
         if (pairs) {
           const uint32_t cb = tab.corners[p];

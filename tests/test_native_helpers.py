@@ -16,8 +16,9 @@ def test_fastdiv_matches_hardware_division():
 
 
 def test_point_mean_rounding_is_exact():
-    """The geometry kernel's narrow coordinate path: exact conversion and a
-    correctly rounded quotient for every corner sum below 2^23."""
+    """The geometry kernel's narrow coordinate path, fl(o) + fl(k / n) with
+    one fixed exception: the correctly rounded mean for every cell
+    coordinate o below 2^21 and every corner count n and k."""
     src = os.path.join(ROOT, "tests", "native", "mean_rounding_check.c")
     with tempfile.TemporaryDirectory() as d:
         exe = os.path.join(d, "mean_rounding_check")
