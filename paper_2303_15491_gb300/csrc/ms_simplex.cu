@@ -646,12 +646,16 @@ __global__ void __launch_bounds__(kGeoThreads, 6) k_simplex_geometry(
   constexpr int kS = kF | 1;               // window stride per element (odd: no bank conflicts)
   constexpr int kWarps = kGeoThreads / 32;
   constexpr unsigned kAll = 0xffffffffu;
+  constexpr int kCorners = kPer == 2 ? 4 : 8;  // a cell's corner labels, kept for the pairs
+  constexpr int kLS = kCorners + 1;             // their stride (odd: no bank conflicts)
   __shared__ GeoTables tab;
   __shared__ float window[kWarps][32 * kS];
+  __shared__ int32_t corner_labels[kWarps][32 * kLS];
   fill_geo_tables(tab, kPer, g.mode);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   float *win = window[threadIdx.x >> 5];
+  int32_t *cl = corner_labels[threadIdx.x >> 5];
   const int64_t sy = g.nx, sz = g.nx * g.ny;
   const int64_t nchunks = (g.ncells + 31) / 32;
   for (int64_t ch = (int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5); ch < nchunks;
@@ -665,6 +669,10 @@ __global__ void __launch_bounds__(kGeoThreads, 6) k_simplex_geometry(
       if (kPer == 2) {
         const int32_t l00 = __ldg(lab + v), l10 = __ldg(lab + v + 1), l01 = __ldg(lab + v + sy),
                       l11 = __ldg(lab + v + sy + 1);
+        cl[lane * kLS] = l00;  // corner bits x = 1, y = 2
+        cl[lane * kLS + 1] = l10;
+        cl[lane * kLS + 2] = l01;
+        cl[lane * kLS + 3] = l11;
         const int k0 = tri_code(l00, l10, l11), k1 = tri_code(l00, l01, l11);
         const uint32_t n0 = tab.count[k0], n1 = tab.count[k1];
         codes = (uint32_t)k0 | (uint32_t)k1 << 5;
@@ -673,8 +681,10 @@ __global__ void __launch_bounds__(kGeoThreads, 6) k_simplex_geometry(
       } else {
         int32_t l[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k)
+        for (int k = 0; k < 8; ++k) {
           l[k] = __ldg(lab + v + ((k & 1) ? 1 : 0) + ((k & 2) ? sy : 0) + ((k & 4) ? sz : 0));
+          cl[lane * kLS + k] = l[k];
+        }
         const int kb[6] = {1, 1, 2, 2, 4, 4};
         const int kc[6] = {3, 5, 3, 6, 5, 6};
 #pragma unroll
@@ -688,6 +698,7 @@ __global__ void __launch_bounds__(kGeoThreads, 6) k_simplex_geometry(
       }
       off = offsets[c];
     }
+    __syncwarp();  // the corner labels are read by other lanes below
     // running element counts over the chunk's cells
     uint32_t incl = n;
 #pragma unroll
@@ -761,9 +772,7 @@ __global__ void __launch_bounds__(kGeoThreads, 6) k_simplex_geometry(
         if (pairs) {
           const uint32_t cb = tab.corners[p];
           const uint32_t bi = (cb >> (3 * ((d >> 12) & 3u))) & 7u, bj = (cb >> (3 * ((d >> 14) & 3u))) & 7u;
-          const int64_t v = (int64_t)ox + g.nx * ((int64_t)oy + g.ny * oz);
-          const int32_t li = __ldg(lab + v + (bi & 1u) + ((bi & 2u) ? sy : 0) + ((bi & 4u) ? sz : 0));
-          const int32_t lj = __ldg(lab + v + (bj & 1u) + ((bj & 2u) ? sy : 0) + ((bj & 4u) ? sz : 0));
+          const int32_t li = cl[owner * kLS + bi], lj = cl[owner * kLS + bj];
           const int64_t at = base + e;
           if (pairs8) {
             *reinterpret_cast<int2 *>(pairs + 2 * at) = make_int2(min(li, lj), max(li, lj));
