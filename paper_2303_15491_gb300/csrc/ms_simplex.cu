@@ -247,29 +247,6 @@ __device__ __forceinline__ void run_codes(const int32_t *__restrict__ lab, const
   }
 }
 
-// Exclusive sum over the compute threads of one value each; also the total.
-__device__ __forceinline__ unsigned int compute_excl(unsigned int v, unsigned int *total,
-                                                     unsigned int *sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned int incl = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) sh[warp] = incl;
-  named_sync<kBarCompute>(kComputeThreads);
-  unsigned int base = 0, tot = 0;
-#pragma unroll
-  for (int w = 0; w < kComputeWarps; ++w) {
-    const unsigned int s = sh[w];
-    if (w < warp) base += s;
-    tot += s;
-  }
-  *total = tot;
-  return base + incl - v;
-}
-
 // Base of `tile` (whose own total is already published): the sum of the
 // earlier tiles' totals, read back 32 words at a time until one holds an
 // inclusive prefix.  Run by one whole warp; the result is in every lane.
@@ -313,26 +290,38 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_simplex_index(
     int64_t *__restrict__ offsets, int vec_offsets, unsigned long long *hdr,
     unsigned long long *status, unsigned int ntiles, DevStatus *st) {
   __shared__ unsigned int lut[32];
-  __shared__ unsigned int sh[kComputeWarps];
-  __shared__ unsigned int s_fetch;
-  __shared__ unsigned int s_tile[2], s_tot[2];
-  __shared__ unsigned long long s_base[2];
+  __shared__ unsigned int s_fetch[2];                       // tile ids, by parity
+  __shared__ unsigned int s_tile[2];
+  __shared__ unsigned int s_wtot[2][kComputeWarps];         // each compute warp's total
+  __shared__ unsigned long long s_wbase[2][kComputeWarps];  // each compute warp's base
   fill_elements(lut, kPer, g.mode);
+  if (threadIdx.x == 0) s_fetch[0] = atomicAdd(reinterpret_cast<unsigned int *>(hdr + 1), 1u);
   __syncthreads();
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == kComputeWarps) {
-    // ---- the look-back warp: tile i of this block, in the order computed
+    // ---- the look-back warp: tile i of this block, in the order computed.
+    // It sums the compute warps' totals, publishes the tile's total, looks
+    // back for the tile's base and hands each compute warp its base.
     for (int i = 0;; ++i) {
       const int b = i & 1;
       named_sync_by<kBarTile>(b, kCellThreads);
       const unsigned int t = s_tile[b];
       if (t == kNoTile) return;  // the compute warps have finished
-      const unsigned int tot = s_tot[b];
+      const unsigned int wv = lane < kComputeWarps ? s_wtot[b][lane] : 0u;
+      unsigned int wi = wv;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int u = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += u;
+      }
+      const unsigned int tot = __shfl_sync(0xffffffffu, wi, 31);
+      if (lane == 0)  // the tile's total (tile 0: its prefix) for later tiles' look-back
+        *(volatile unsigned long long *)&status[t] = (t == 0 ? kFlagPrefix : kFlagAgg) | tot;
       const unsigned long long base = t == 0 ? 0ull : look_back(status, t, st);
-      if ((threadIdx.x & 31) == 0) {
+      if (lane < kComputeWarps) s_wbase[b][lane] = base + (wi - wv);
+      if (lane == 0) {
         if (t != 0) *(volatile unsigned long long *)&status[t] = kFlagPrefix | ((base + tot) & kValueMask);
         if (t + 1 == ntiles) hdr[0] = base + tot;  // the element total
-        s_base[b] = base;
       }
       __threadfence_block();
       named_arrive_by<kBarBase>(b, kCellThreads);
@@ -344,9 +333,14 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_simplex_index(
   int64_t prev_c0 = -1;
   for (int i = 0;; ++i) {
     const int b = i & 1;
-    if (threadIdx.x == 0) s_fetch = atomicAdd(reinterpret_cast<unsigned int *>(hdr + 1), 1u);
-    named_sync<kBarCompute>(kComputeThreads);
-    const unsigned int t = s_fetch < ntiles ? s_fetch : kNoTile;
+    // tile i's id is in s_fetch[b] (tile 0's from before the role split);
+    // s_fetch[b] is written again for tile i + 2 only after every compute
+    // thread has passed the base barrier of tile i + 1, so after this read
+    if (i > 0) {
+      if (threadIdx.x == 0) s_fetch[b] = atomicAdd(reinterpret_cast<unsigned int *>(hdr + 1), 1u);
+      named_sync<kBarCompute>(kComputeThreads);
+    }
+    const unsigned int t = s_fetch[b] < ntiles ? s_fetch[b] : kNoTile;
     uint32_t n[kRunCells];
     unsigned int ex = 0;
     const int64_t c0 = t == kNoTile ? -1 : (int64_t)t * kTileCells + (int64_t)threadIdx.x * kRunCells;
@@ -360,13 +354,16 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_simplex_index(
       uint32_t mine = 0;
 #pragma unroll
       for (int j = 0; j < kRunCells; ++j) mine += n[j];
-      unsigned int tot = 0;
-      ex = compute_excl(mine, &tot, sh);  // also orders s_fetch's read before its next write
-      if (threadIdx.x == 0) {
-        // publish the tile's total (tile 0: its prefix) for later tiles' look-back
-        *(volatile unsigned long long *)&status[t] = (t == 0 ? kFlagPrefix : kFlagAgg) | tot;
-        s_tot[b] = tot;
+      // the exclusive sum within the warp; the warp's total goes to the
+      // look-back warp, which returns the warp's base
+      unsigned int incl = mine;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
       }
+      ex = incl - mine;
+      if (lane == 31) s_wtot[b][warp] = incl;
     }
     if (threadIdx.x == 0) s_tile[b] = t;
     __threadfence_block();
@@ -376,7 +373,7 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_simplex_index(
       named_sync_by<kBarBase>(b ^ 1, kCellThreads);
       if (prev_c0 >= 0 && prev_c0 < g.ncells) {
         long long o[kRunCells];
-        unsigned long long run = s_base[b ^ 1] + prev_ex;
+        unsigned long long run = s_wbase[b ^ 1][warp] + prev_ex;
 #pragma unroll
         for (int j = 0; j < kRunCells; ++j) {
           o[j] = (long long)run;
