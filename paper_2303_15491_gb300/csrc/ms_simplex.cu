@@ -406,7 +406,8 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_simplex_index(
 // the mean of a subset of the simplex's corners (bit k = corner k in chain
 // order: a midpoint has two bits, a face centre three, the tetrahedron centre
 // four), and an element names the two corners whose labels it separates.
-// Each coordinate's sum is formed exactly and divided once with IEEE rounding.
+// A coordinate is the subset's mean rounded once to nearest even (see
+// mean_wide and the narrow path's table of fractions below).
 //
 // The pass then takes chunks of 32 cells per warp.  A chunk's elements are one
 // contiguous range of the output (the index pass's offsets); they are handed
@@ -414,7 +415,8 @@ __global__ void __launch_bounds__(kCellThreads, 2) k_simplex_index(
 // cells' element counts.  A lane finds its element's cell by a binary search
 // over the chunk's running counts and the simplex by the cell's per-simplex
 // counts, writes the points to a shared-memory window, and the warp stores
-// the window as consecutive words.
+// the window as consecutive words; the separated labels come from the owner
+// cell's corner labels, which each lane leaves in shared memory.
 constexpr int kMaxElems = 12;  // four labels in a tetrahedron
 constexpr int kGeoThreads = 256;
 
