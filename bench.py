@@ -775,6 +775,7 @@ def main():
     alg_bytes = STAGE_BYTES[dom][w["dtype"]] * n
     achieved = alg_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
     traffic = None
+    warp_inst = None  # ncu's executed warp instructions per launch, for the issue roofline
     tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if os.path.exists(tpath):
         try:
@@ -782,9 +783,24 @@ def main():
             ent = tj.get(dom)
             if ent and ent.get("csrc_sha1") == source_hash() and ent.get("workload") == args.workload:
                 traffic = ent["dram_bytes_per_launch"]
+                warp_inst = ent.get("warp_inst_per_launch")
         except Exception:
             traffic = None
     path_gbs = PATH_BYTES[w["dtype"]] * n / (ms_per_step / 1e3) / 1e9
+    clocks = clk.summary()
+    # The tiled kernels are bound by instruction issue, not DRAM: beside the
+    # HBM roofline, the executed warp instructions (ncu) per launch time
+    # against the issue peak -- four schedulers an SM, one warp instruction a
+    # cycle each, at the SM clock sampled during the timed region.
+    issue = None
+    if warp_inst and per_launch_s > 0:
+        sm_mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_wi = sms * 4 * sm_mhz * 1e6
+        issue = {"kernel": dom, "warp_inst_per_launch": warp_inst,
+                 "achieved_warp_inst_per_s": warp_inst / per_launch_s, "peak_warp_inst_per_s": peak_wi,
+                 "frac": warp_inst / per_launch_s / peak_wi,
+                 "peak_from": f"{sms} SMs x 4 schedulers x 1 warp instruction a cycle x {sm_mhz:.0f} MHz"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "vertices/s", "n_gpus": ws,
@@ -803,13 +819,14 @@ def main():
                      "avg_launch_ms": per_launch_s * 1e3},
         "path_roofline": {"alg_bytes_per_vertex": PATH_BYTES[w["dtype"]], "achieved": path_gbs,
                           "peak": hbm, "unit": "GB/s", "frac": path_gbs / hbm},
+        "issue_roofline": issue,
         "stages_ms_per_step": {k: v["ms"] / max(1, prof["calls"]) for k, v in stages.items()
                                if v["launches"] or v["ms"]},
         "gpu_launches": prof["launches"],
         "e2e": None if e2e_value is None else {
             "value": e2e_value, "unit": "vertices/s", "h2d_bytes_per_step": n * esz,
             "d2h_bytes_per_step": 3 * n * 4, "api": "ms_segment_host, pinned host buffers"},
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     ms.ms_destroy(ctx)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
