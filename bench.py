@@ -734,11 +734,15 @@ def main():
     with ClockSampler(dev) as clk:
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
-        # events on the stream the library's kernels are launched on
+        # events on the stream the library's kernels are launched on; one more
+        # between steps for the per-step statistics
+        step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         ev0.record(stream)
         t_host = time.perf_counter()
-        for _ in range(args.steps):
+        for i in range(args.steps):
+            step_ev[i].record(stream)
             ms.ms_segment(ctx, field, dims, dtype, asc, desc, msid)
+        step_ev[args.steps].record(stream)
         ev1.record(stream)
         torch.cuda.synchronize()
         t_host = time.perf_counter() - t_host
@@ -749,6 +753,14 @@ def main():
     elapsed_ms = max_over_ranks(max(ev0.elapsed_time(ev1), 1e3 * t_host), dist, dev)
     ms_per_step = elapsed_ms / args.steps
     value = whole_job_rate(n * args.steps, ws, elapsed_ms / 1e3)
+    # per-step times: median, and the paper's protocol (10 runs, the best and
+    # the worst dropped, the mean of the other 8) over the last 10 steps
+    per_step = [step_ev[i].elapsed_time(step_ev[i + 1]) for i in range(args.steps)]
+    step_stats = {"median_ms": statistics.median(per_step), "min_ms": min(per_step),
+                  "max_ms": max(per_step)}
+    if len(per_step) >= 10:
+        last = sorted(per_step[-10:])
+        step_stats["paper_protocol_ms"] = sum(last[1:-1]) / 8
 
     # ---- end to end through ms_segment_host (pinned host memory)
     esz = 2 if w["dtype"] == "f16" else 4
@@ -820,6 +832,7 @@ def main():
         "path_roofline": {"alg_bytes_per_vertex": PATH_BYTES[w["dtype"]], "achieved": path_gbs,
                           "peak": hbm, "unit": "GB/s", "frac": path_gbs / hbm},
         "issue_roofline": issue,
+        "step_ms": step_stats,
         "stages_ms_per_step": {k: v["ms"] / max(1, prof["calls"]) for k, v in stages.items()
                                if v["launches"] or v["ms"]},
         "gpu_launches": prof["launches"],
