@@ -288,6 +288,42 @@ def cpu_baseline(args):
             "sample": f"first {shape} of {args.workload} ({n} vertices, {dt:.1f} s single-threaded)"}
 
 
+def cpu_parallel_baseline(args):
+    """The paper's CPU-parallel scheme (cpu_parallel: per-thread active lists,
+    OpenMP) on all host cores, on the same sample as the oracle's baseline:
+    one warm-up and 5 timed runs in a child process with a time limit, so
+    that it can neither hang nor break this line."""
+    w = WORKLOADS[args.workload]
+    nx, ny, nz = w["dims"]
+    if nz == 1:
+        rows = max(1, min(ny, args.cpu_slab * 512 * 512 // nx))
+        f = np.ascontiguousarray(make_field(args.workload)[0, :rows])
+        shape = f"{nx}x{rows} row block"
+    else:
+        slab = max(1, min(nz, args.cpu_slab))
+        f = make_field(args.workload, 0, slab)
+        shape = f"{nx}x{ny}x{slab} z-slab"
+    path = os.path.join(cache_dir(), f"cpu_parallel_sample_{os.getpid()}.npy")
+    try:
+        np.save(path, np.ascontiguousarray(f, dtype=np.float32))
+        r = subprocess.run([sys.executable, "-m", "cpu_parallel", path, "5"], cwd=ROOT,
+                           capture_output=True, text=True, timeout=240)
+        if r.returncode != 0:
+            return {"unavailable": (r.stderr.strip().splitlines() or ["failed"])[-1][:200]}
+        res = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": res["vertices"] / res["median_s"], "unit": "vertices/s",
+                "cores": res["threads"], "kind": "the paper's CPU-parallel scheme (OpenMP)",
+                "sample": f"first {shape} of {args.workload} ({res['vertices']} vertices): median of 5 "
+                          f"runs after one warm-up, {res['median_s'] * 1e3:.0f} ms"}
+    except Exception as e:  # includes the time limit
+        return {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+    finally:
+        try:
+            os.remove(path)
+        except OSError:
+            pass
+
+
 def batch_fields():
     specs = sf.batch_specs(256, seed=0)
     out = []
@@ -844,6 +880,7 @@ def main():
     ms.ms_destroy(ctx)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
+        line["cpu_parallel_baseline"] = cpu_parallel_baseline(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
