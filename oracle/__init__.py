@@ -49,6 +49,9 @@ def lib():
     with _lock:
         if _lib is None:
             L = ctypes.CDLL(build())
+            L.ms_oracle_persistence.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, ctypes.c_int,
+                                                i32p, i32p, ctypes.POINTER(ctypes.c_int64)]
+            L.ms_oracle_persistence.restype = ctypes.c_int
             L.ms_oracle_neighbors.argtypes = [i64p, ctypes.c_int64, i64p]
             L.ms_oracle_neighbors.restype = ctypes.c_int
             L.ms_oracle_steepest.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i32p, i32p]
@@ -253,3 +256,17 @@ def simplex_geometry(labels: np.ndarray, dims, mode: int = 0):
     assert int(total.value) == n
     return {"pos": pos[:n], "pairs": pairs[:n], "total": n}
 
+
+def persistence(field: np.ndarray, direction: int = -1):
+    """0-dimensional persistence pairs of the extrema (direction -1: minima of
+    the sublevel sets, +1: maxima of the superlevel sets): a dict with
+    ``extremum`` and ``death`` (int32, in increasing extremum index; death
+    -1 for the extremum that never dies)."""
+    f, dt, dims = _prep(field)
+    n = f.size
+    ext = np.empty(n, np.int32)
+    dth = np.empty(n, np.int32)
+    k = ctypes.c_int64(0)
+    _check(lib().ms_oracle_persistence(f.ctypes.data, dt, dims, int(direction), _ptr32(ext),
+                                       _ptr32(dth), ctypes.byref(k)))
+    return {"extremum": ext[:k.value].copy(), "death": dth[:k.value].copy()}

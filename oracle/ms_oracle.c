@@ -37,6 +37,10 @@
  *               characteristic and number of connected components
  *               (Banchoff's classification), from an explicit enumeration of
  *               the simplices of the triangulation.
+ *   persistence Sec. 4.1 (simplification by persistence) + Sec. 6
+ *               (thresholds): the 0-dimensional persistence pairs of the
+ *               extrema -- sublevel-set components for minima, superlevel-set
+ *               components for maxima, the elder rule at every merge.
  *
  * Vertex numbering: v = x + nx*(y + ny*z), x fastest (Fig. 1 numbers the
  * nodes of its grid along x first).
@@ -868,5 +872,129 @@ int ms_oracle_simplex_geometry(const int32_t *labels, const int64_t dims[3], int
         }
   }
   *total = pos ? o.at : count;
+  return OR_OK;
+}
+
+/* ---- 0-dimensional persistence of the extrema --------------------------------
+ *
+ * The paper removes non-persistent critical points by topological
+ * simplification before segmenting (Sec. 4.1) and quotes persistence
+ * thresholds for its runs (Sec. 6); the pairing that decides which extrema a
+ * threshold removes is the persistence pairing of the sublevel-set components
+ * (minima) or superlevel-set components (maxima), written out here from its
+ * textbook definition on the vertex-edge graph of the triangulation:
+ *
+ *   vertices enter one at a time in the order of Sec. 4.1 (increasing for
+ *   minima, decreasing for maxima); a vertex with no earlier neighbour starts
+ *   a component -- it is an extremum, born there; a vertex with earlier
+ *   neighbours joins their components, and where it joins several, every
+ *   component but the one whose extremum entered first ends there (the elder
+ *   rule): its extremum dies at that vertex.  The extremum that entered first
+ *   of a connected grid never dies.
+ *
+ * direction -1: minima, +1: maxima.  extremum / death: int32[n] (at most one
+ * pair per vertex); pair i = (extremum[i], death[i]), death -1 for the one
+ * that never dies, pairs in increasing extremum index; *npairs receives the
+ * count.  The persistence of a pair is |f(death) - f(extremum)|. */
+typedef struct {
+  double value;
+  int64_t index;
+} ordered_t;
+
+static int cmp_ordered(const void *a, const void *b) {
+  const ordered_t *x = (const ordered_t *)a, *y = (const ordered_t *)b;
+  if (x->value < y->value) return -1;
+  if (x->value > y->value) return 1;
+  return x->index < y->index ? -1 : (x->index > y->index);
+}
+
+/* root of v's component, compressing the path on the way */
+static int64_t uf_root(int64_t *parent, int64_t v) {
+  int64_t r = v;
+  while (parent[r] != r) r = parent[r];
+  while (parent[v] != r) {
+    const int64_t next = parent[v];
+    parent[v] = r;
+    v = next;
+  }
+  return r;
+}
+
+int ms_oracle_persistence(const void *field, int dtype, const int64_t dims[3], int direction,
+                          int32_t *extremum, int32_t *death, int64_t *npairs) {
+  field_t F;
+  int st = make_field(&F, field, dtype, dims);
+  if (st != OR_OK) return st;
+  if ((direction != 1 && direction != -1) || !extremum || !death || !npairs) return OR_ERR_ARG;
+  if (F.n > 2147483647LL) return OR_ERR_ARG;
+  if (has_nan(&F)) return OR_ERR_NAN;
+  const int64_t n = F.n;
+  ordered_t *ord = (ordered_t *)malloc(sizeof(ordered_t) * (size_t)n);
+  int64_t *pos = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);     /* entry step of a vertex */
+  int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t *eldest = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);  /* a root's first extremum */
+  int32_t *dies = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);    /* per extremum, or -2 */
+  if (!ord || !pos || !parent || !eldest || !dies) {
+    free(ord);
+    free(pos);
+    free(parent);
+    free(eldest);
+    free(dies);
+    return OR_ERR_NOMEM;
+  }
+  for (int64_t v = 0; v < n; ++v) {
+    ord[v].value = value_at(&F, v);
+    ord[v].index = v;
+    dies[v] = -2; /* not an extremum */
+  }
+  qsort(ord, (size_t)n, sizeof(ordered_t), cmp_ordered);
+  for (int64_t s = 0; s < n; ++s) {
+    const int64_t v = ord[direction < 0 ? s : n - 1 - s].index;
+    pos[v] = s;
+  }
+  for (int64_t v = 0; v < n; ++v) parent[v] = -1; /* not entered yet */
+  for (int64_t s = 0; s < n; ++s) {
+    const int64_t v = ord[direction < 0 ? s : n - 1 - s].index;
+    int64_t nb[14], roots[14];
+    const int c = neighbours_of(&F, v, nb);
+    int nr = 0;
+    for (int i = 0; i < c; ++i) {
+      if (parent[nb[i]] < 0) continue; /* enters later */
+      const int64_t r = uf_root(parent, nb[i]);
+      int seen = 0;
+      for (int j = 0; j < nr; ++j) seen |= roots[j] == r;
+      if (!seen) roots[nr++] = r;
+    }
+    if (nr == 0) { /* an extremum: a new component */
+      parent[v] = v;
+      eldest[v] = v;
+      dies[v] = -1;
+      continue;
+    }
+    /* the component whose extremum entered first survives */
+    int keep = 0;
+    for (int j = 1; j < nr; ++j)
+      if (pos[eldest[roots[j]]] < pos[eldest[roots[keep]]]) keep = j;
+    const int64_t root = roots[keep];
+    for (int j = 0; j < nr; ++j) {
+      if (j == keep) continue;
+      dies[eldest[roots[j]]] = (int32_t)v;
+      parent[roots[j]] = root;
+    }
+    parent[v] = root;
+  }
+  int64_t k = 0;
+  for (int64_t v = 0; v < n; ++v)
+    if (dies[v] != -2) {
+      extremum[k] = (int32_t)v;
+      death[k] = dies[v];
+      ++k;
+    }
+  *npairs = k;
+  free(ord);
+  free(pos);
+  free(parent);
+  free(eldest);
+  free(dies);
   return OR_OK;
 }
