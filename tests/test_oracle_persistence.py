@@ -108,3 +108,55 @@ def test_nan_rejected():
     f[1, 1, 1] = np.nan
     with pytest.raises(Exception):
         oracle.persistence(f, -1)
+
+
+def basin_graph_pairs(f, dims):
+    """The same pairing computed the way a data-parallel pass can: from the
+    ascending segmentation (every vertex's minimum), every edge of the
+    triangulation between two basins becomes active when its later endpoint
+    enters; taking the active edges in entry order and merging basins with
+    the elder rule gives each minimum's death vertex."""
+    _, pos = order_positions(f, -1)
+    asc = oracle.segment(f)["asc"]
+    n = f.size
+    best = {}  # (basin a, basin b) -> (activation step, entering vertex)
+    for v in range(n):
+        for u in oracle.neighbors(dims, v):
+            if u <= v or asc[u] == asc[v]:
+                continue
+            a, b = sorted((int(asc[u]), int(asc[v])))
+            w = max(pos[u], pos[v])
+            if (a, b) not in best or w < best[(a, b)][0]:
+                best[(a, b)] = (w, u if pos[u] > pos[v] else v)
+    parent = {m: m for m in set(asc.tolist())}
+
+    def root(x):
+        while parent[x] != x:
+            x = parent[x]
+        return x
+
+    death = {m: -1 for m in parent}
+    for (a, b), (w, v) in sorted(best.items(), key=lambda kv: kv[1][0]):
+        ra, rb = root(a), root(b)
+        if ra == rb:
+            continue
+        young, old = (ra, rb) if pos[ra] > pos[rb] else (rb, ra)  # a root is its component's eldest
+        death[young] = v
+        parent[young] = old
+    ext = np.array(sorted(death), np.int32)
+    return ext, np.array([death[m] for m in ext], np.int32)
+
+
+@pytest.mark.parametrize("dims", [(9, 8, 7), (20, 15, 1), (6, 5, 4)])
+@pytest.mark.parametrize("levels", [4, 1 << 20])
+def test_basin_graph_formulation_agrees(dims, levels):
+    """Sublevel-set components at any step are unions of (parts of) basins
+    joined by active basin-boundary edges -- every entered vertex reaches its
+    minimum by steepest descent inside the sublevel set -- so the merges
+    happen exactly when boundary edges become active.  Checked against the
+    oracle's pairing, with and without ties."""
+    f = np.random.default_rng(levels % 1000 + dims[0]).integers(0, levels, size=dims[::-1]).astype(np.float32)
+    p = oracle.persistence(f, -1)
+    ext, death = basin_graph_pairs(f, dims)
+    assert np.array_equal(p["extremum"], ext)
+    assert np.array_equal(p["death"], death)
