@@ -345,6 +345,11 @@ def batch_fields():
 
 
 def run_batch_bench(args):
+    print(json.dumps(batch_line(args)), flush=True)
+    return 0
+
+
+def batch_line(args, plain_steps=None):
     """Many uneven fields per step: one ms_segment_batch call against the same
     fields through one ms_segment call each."""
     import torch
@@ -394,9 +399,11 @@ def run_batch_bench(args):
           flush=True)
     prof = ms.ms_profile_read(ctx)
     ms.ms_profile_enable(ctx, False)
-    t_plain = timed(plain, max(1, args.steps // 4))
+    t_plain = timed(plain, plain_steps or max(1, args.steps // 4))
     ks = batched()
     ms.ms_destroy(ctx)
+    del fields, outs, asc, desc, mso
+    torch.cuda.empty_cache()
     line = {
         "metric": METRIC, "value": n / (t_batch / 1e3), "unit": "vertices/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True,
@@ -411,8 +418,7 @@ def run_batch_bench(args):
                                if v["launches"] or v["ms"]},
         "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 def device_smoothed_noise(shape, seed, dev, sigma=4.0, radius=16):
@@ -447,6 +453,11 @@ def device_smoothed_noise(shape, seed, dev, sigma=4.0, radius=16):
 
 
 def run_serve_bench(args):
+    print(json.dumps(serve_line(args)), flush=True)
+    return 0
+
+
+def serve_line(args):
     """The request loop (ms_server) against the plain path on the same requests:
     (1) saturation -- all requests submitted at once -- for throughput, and
     (2) a Poisson stream at a stated rate for p50 / p99 latency, through the
@@ -592,8 +603,9 @@ def run_serve_bench(args):
         "plain_gpu_launches": plain_launches,
         "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
-    return 0
+    del reqs
+    torch.cuda.empty_cache()
+    return line
 
 
 def run_index_bench(args):
@@ -687,6 +699,85 @@ def run_index_bench(args):
     return 0
 
 
+def extra(name, fn):
+    """One sub-measurement of the default run; a failure is reported in the
+    line instead of ending the run."""
+    t = time.perf_counter()
+    print(f"[bench] {name} ...", file=sys.stderr, flush=True)
+    try:
+        out = fn()
+    except Exception as e:  # reported, not hidden: the key says what failed
+        out = {"unavailable": f"{type(e).__name__}: {e}"[:300]}
+    out["wall_s"] = round(time.perf_counter() - t, 1)
+    return out
+
+
+def quantised_summary(args, f_np):
+    """The 512^3 field quantised to 256 levels (exact ties), one field per
+    call, timed like the main workload over fewer steps."""
+    import torch
+
+    import paper_2303_15491_gb300 as ms
+
+    fq = sf.quantize_levels(np.asarray(f_np))
+    dev = torch.cuda.current_device()
+    n = fq.size
+    field = torch.from_numpy(fq).to(dev)
+    outs = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(3)]
+    stream = torch.cuda.Stream(device=dev)
+    ctx = ms.ms_create(dev, stream)
+    dims = ms.dims_of(fq)
+    try:
+        for _ in range(args.warmup):
+            ms.ms_segment(ctx, field, dims, ms.MS_F32, *outs)
+        steps = 20
+        torch.cuda.synchronize()
+        ms.ms_profile_enable(ctx, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            ms.ms_segment(ctx, field, dims, ms.MS_F32, *outs)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        prof = ms.ms_profile_read(ctx)
+        t = ev0.elapsed_time(ev1) / steps
+        k = ms.ms_last_region_count(ctx)
+    finally:
+        ms.ms_destroy(ctx)
+        del field, outs
+        torch.cuda.empty_cache()
+    hbm, _ = peaks()
+    return {"workload": "noise512q", "desc": WORKLOADS["noise512q"]["desc"], "steps": steps,
+            "ms_per_step": t, "vertices_per_s": n / (t / 1e3), "regions_K": k,
+            "path_frac": PATH_BYTES["f32"] * n / (t / 1e3) / 1e9 / hbm,
+            "stages_ms_per_step": {kk: v["ms"] / max(1, prof["calls"])
+                                   for kk, v in prof["stages"].items() if v["launches"] or v["ms"]}}
+
+
+def batched_summary(args):
+    sub = argparse.Namespace(**vars(args))
+    sub.steps, sub.warmup = 10, 3
+    ln = batch_line(sub, plain_steps=2)
+    return {"workload": "batch256", "desc": WORKLOADS["batch256"]["desc"], "steps": sub.steps,
+            "ms_per_step": ln["ms_per_step"], "vertices_per_s": ln["value"],
+            "plain_ms_per_step": ln["plain_ms_per_step"], "speedup_vs_plain": ln["speedup_vs_plain"],
+            "fields": ln["config"]["fields"], "vertices": ln["config"]["vertices"],
+            "regions_K_total": ln["config"]["regions_K_total"], "tuning": ln["tuning"],
+            "graph_replay": ln["graph_replay"], "stages_ms_per_step": ln["stages_ms_per_step"],
+            "note": "10 timed batched steps, 2 timed rounds of 256 single calls (reduced counts)"}
+
+
+def served_summary(args):
+    sub = argparse.Namespace(**vars(args))
+    sub.serve_passes = 4
+    ln = serve_line(sub)
+    return {"workload": "serve", "desc": WORKLOADS["serve"]["desc"], "passes": sub.serve_passes,
+            "slots": ln["config"]["slots"], "budget_bytes": ln["config"]["budget_bytes"],
+            "saturated_vertices_per_s": ln["value"], "speedup_vs_plain": ln["speedup_vs_plain"],
+            "plain": ln["plain"], "saturated": ln["saturated"], "poisson": ln["poisson"],
+            "note": "4 passes of 64 requests (256 requests) per stream instead of 16 (reduced count)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -698,6 +789,8 @@ def main():
     ap.add_argument("--cpu-slab", type=int, default=48)
     ap.add_argument("--ref-slab", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the quantised, batched and served sub-measurements of the default run")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-passes", type=int, default=16)
@@ -814,14 +907,19 @@ def main():
         e2e_s = max_over_ranks(time.perf_counter() - t, dist, dev)
         e2e_value = whole_job_rate(n * args.e2e_steps, ws, e2e_s)
 
-    # ---- roofline of the dominant kernel and of the whole path
+    # ---- roofline of the dominant kernel and of the whole path.  The
+    # headline figure is the path's algorithmic bytes (field in, three labels
+    # out: 16 B a vertex) over one launch of the dominant kernel; the bytes the
+    # kernel itself must move (its stage figure) are reported beside it.
     hbm, peak_kind = peaks()
     stages = prof["stages"]
     dom = max(("tile_local", "write"), key=lambda s: stages[s]["ms"])
     launches = max(1, stages[dom]["launches"])
     per_launch_s = stages[dom]["ms"] / 1e3 / launches
-    alg_bytes = STAGE_BYTES[dom][w["dtype"]] * n
+    alg_bytes = PATH_BYTES[w["dtype"]] * n
     achieved = alg_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
+    stage_bytes = STAGE_BYTES[dom][w["dtype"]] * n
+    stage_gbs = stage_bytes / per_launch_s / 1e9 if per_launch_s > 0 else None
     traffic = None
     warp_inst = None  # ncu's executed warp instructions per launch, for the issue roofline
     tpath = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -850,6 +948,15 @@ def main():
                  "frac": warp_inst / per_launch_s / peak_wi,
                  "peak_from": f"{sms} SMs x 4 schedulers x 1 warp instruction a cycle x {sm_mhz:.0f} MHz"}
 
+    # what limits the dominant kernel: the larger of its DRAM fraction (the
+    # bytes it moves itself) and its instruction-issue fraction
+    hbm_frac = (traffic / per_launch_s / 1e9 / hbm) if (traffic and per_launch_s > 0) else (
+        stage_gbs / hbm if stage_gbs else 0.0)
+    if issue and issue["frac"] > hbm_frac:
+        limiter = (f"instruction issue: {issue['frac']:.0%} of the issue peak against "
+                   f"{hbm_frac:.0%} of HBM for the bytes the kernel moves")
+    else:
+        limiter = f"HBM: {hbm_frac:.0%} of the copy peak for the bytes the kernel moves"
     line = {
         "metric": METRIC, "value": value, "unit": "vertices/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -863,8 +970,12 @@ def main():
                      "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": None if achieved is None else achieved / hbm,
                      "traffic": traffic,
-                     "alg_bytes_per_vertex": STAGE_BYTES[dom][w["dtype"]],
-                     "avg_launch_ms": per_launch_s * 1e3},
+                     "alg_bytes_per_vertex": PATH_BYTES[w["dtype"]],
+                     "avg_launch_ms": per_launch_s * 1e3,
+                     "limiter": limiter},
+        "stage_roofline": {"kernel": dom, "alg_bytes_per_vertex": STAGE_BYTES[dom][w["dtype"]],
+                           "achieved": stage_gbs, "peak": hbm, "unit": "GB/s",
+                           "frac": None if stage_gbs is None else stage_gbs / hbm},
         "path_roofline": {"alg_bytes_per_vertex": PATH_BYTES[w["dtype"]], "achieved": path_gbs,
                           "peak": hbm, "unit": "GB/s", "frac": path_gbs / hbm},
         "issue_roofline": issue,
@@ -878,9 +989,17 @@ def main():
         "clocks": clocks,
     }
     ms.ms_destroy(ctx)
+    del field, asc, desc, msid
+    torch.cuda.empty_cache()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
         line["cpu_parallel_baseline"] = cpu_parallel_baseline(args)
+    if rank == 0 and ws == 1 and args.workload == "noise512" and not args.no_extras:
+        # the metric's other halves, measured in the same run: the quantised
+        # 512^3 variant, the 256-field batch and the request loop
+        line["quantised"] = extra("quantised", lambda: quantised_summary(args, f_np))
+        line["batched"] = extra("batched", lambda: batched_summary(args))
+        line["served"] = extra("served", lambda: served_summary(args))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -255,21 +255,26 @@ ms_status ms_simplex_geometry(ms_ctx *ctx, const int32_t *labels, const int64_t 
 /* A request loop for segmentations of mixed sizes.  The server owns n_slots
  * worker threads, each with its own context (stream and resident scratch) on
  * `device`, so requests run concurrently and their kernels overlap on the GPU.
- * A submitted request waits until a slot is idle and its estimated device
- * memory -- its field and three label arrays plus about 10 bytes of scratch
- * per vertex -- fits in what budget_bytes has left; among waiting requests the
- * first that fits is admitted (one passed over 8 times is admitted next, once
- * it fits), except that requests of at least 2^25 vertices -- each fills the
- * GPU by itself -- run one at a time.  Results are exactly those of
- * ms_segment. */
+ * budget_bytes bounds what the server's requests hold on the device: the
+ * scratch each slot keeps between requests (measured after every request)
+ * plus, for each running request, its field and three label arrays and the
+ * growth of its slot's scratch (estimated at 10 bytes per vertex).  A
+ * submitted request waits until a slot is idle and that much fits in what the
+ * budget has left; among waiting requests the first that fits is admitted (one
+ * passed over 8 times is admitted next, once it fits), except that requests of
+ * at least 2^25 vertices -- each fills the GPU by itself -- run one at a time.
+ * When a waiting request does not fit and no request is running, idle slots
+ * free their scratch; a slot whose scratch outgrew its estimate frees it after
+ * the request.  Results are exactly those of ms_segment. */
 typedef struct ms_server ms_server;
 
 typedef struct {
   uint64_t admitted, completed, queued; /* requests */
-  size_t bytes_in_use;                  /* estimated bytes of running requests */
+  size_t bytes_in_use;                  /* slots' resident scratch + running requests' charges */
   size_t peak_bytes;                    /* the largest bytes_in_use so far */
   size_t budget_bytes;
   uint64_t launches;                    /* kernel launches of completed requests */
+  size_t resident_bytes;                /* device bytes the slots' contexts hold now */
 } ms_server_info;
 
 /* n_slots in [1, 64], budget_bytes > 0.  *out is set only on MS_OK. */
@@ -320,8 +325,11 @@ ms_status ms_server_destroy(ms_server *srv);
  * loads the library holds until the process exits; the call itself performs
  * no cudaMalloc / cudaFree and calls no allocating routine.  The first call
  * on a device looks the array's device address up (cudaGetSymbolAddress) and
- * caches it, so make that first call before any stream capture on the
- * device.  Every call reuses the same array: the call clears what must start
+ * caches it for the device's current context, so make that first call before
+ * any stream capture on the device; the cache is keyed by the context's id
+ * (cuCtxGetId), and a call made in a new context (for example after
+ * cudaDeviceReset) looks the address up again, which again must happen
+ * outside a stream capture.  Every call reuses the same array: the call clears what must start
  * empty, but calls that overlap on the GPU (two streams, two threads) race on
  * it and must be serialised by the caller. */
 ms_status ms_pair_rank_noalloc(const int32_t *asc, const int32_t *desc, int64_t n, int32_t *ms,

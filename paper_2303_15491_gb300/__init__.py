@@ -57,7 +57,9 @@ class _ServerInfo(ctypes.Structure):
     _fields_ = [("admitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
                 ("queued", ctypes.c_uint64), ("bytes_in_use", ctypes.c_size_t),
                 ("peak_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
-                ("launches", ctypes.c_uint64)]
+                ("launches", ctypes.c_uint64), ("resident_bytes", ctypes.c_size_t)]
+
+
 STAGES = ["tile_local", "resolve", "write", "h2d", "d2h", "graph"]
 
 

@@ -834,6 +834,31 @@ ms_status run_batch(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
 
 }  // namespace
 
+namespace msseg {
+
+size_t ctx_resident_bytes(const ms_ctx *c) {
+  return c->scratch_bytes + c->io_bytes + c->tscratch_bytes + c->graph_bytes + c->sxscratch_bytes +
+         c->batch_dev_bytes + sizeof(DevStatus);
+}
+
+void ctx_release_scratch(ms_ctx *c) {
+  DeviceGuard g(c->device);
+  cudaStreamSynchronize(c->stream);
+  drop_graph(&c->plan);
+  void **bufs[] = {&c->scratch, &c->io, &c->tscratch, &c->graph, &c->sxscratch, &c->batch_dev};
+  size_t *sizes[] = {&c->scratch_bytes, &c->io_bytes, &c->tscratch_bytes, &c->graph_bytes,
+                     &c->sxscratch_bytes, &c->batch_dev_bytes};
+  for (int i = 0; i < 6; ++i) {
+    if (*bufs[i]) cudaFree(*bufs[i]);
+    *bufs[i] = nullptr;
+    *sizes[i] = 0;
+  }
+  ++c->alloc_epoch;
+  cudaGetLastError();
+}
+
+}  // namespace msseg
+
 extern "C" {
 
 const char *ms_status_string(ms_status s) {

@@ -50,6 +50,12 @@ __device__ __forceinline__ uint32_t load_bits(const void *field, int dtype, int6
 // Kernels launched by this host thread (read by the profiler).
 extern thread_local long long tl_launches;
 
+// Device bytes a context holds between calls (its scratch, staging and status
+// buffers), and the release of everything but its status block (the next call
+// allocates again).  Used by the request loop to keep its slots within budget.
+size_t ctx_resident_bytes(const ms_ctx *c);
+void ctx_release_scratch(ms_ctx *c);
+
 // ---- launchers (stream-ordered, no synchronisation) ----------------------
 cudaError_t launch_order_keys(const void *field, int64_t n, int dtype, uint32_t *keys,
                               DevStatus *st, cudaStream_t s);

@@ -3,6 +3,8 @@
 // memory is one file-scope device array, so the call itself never allocates:
 // the array is part of the library's device image and every GPU that loads
 // the library holds it until the process exits.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "ms_internal.cuh"
@@ -26,20 +28,62 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
+// Per device: the array's address and the id of the context it was looked up
+// in.  A module's device variables live in one context; after
+// cudaDeviceReset (or any other end of the primary context) the next context
+// loads the module again and the variable may sit elsewhere, so the address
+// is looked up again whenever the current context's id differs.
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;
+  void *ptr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
 
-// Device address of the array on the current device (set up once per device;
-// the first call on a device does this, so it must come before any stream
-// capture on that device).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Id of the calling thread's current context (0 if none or unavailable).
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+    cudaGetLastError();
+  });
+  CUcontext c = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c ||
+      get_id(c, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the array on the current device, for the current
+// context.  The first call on a device (and the first after its context
+// changed) looks it up, so it must come before any stream capture.
 cudaError_t scratch_address(int device, void **out) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[device]) {
+  ScratchAddr &a = g_scratch[device];
+  const unsigned long long id = current_ctx_id();
+  if (!a.ptr || id == 0 || id != a.ctx_id) {
     void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the context current
     if (e != cudaSuccess) return e;
-    g_scratch_ptr[device] = p;
+    a.ptr = p;
+    a.ctx_id = current_ctx_id();
   }
-  *out = g_scratch_ptr[device];
+  *out = a.ptr;
   return cudaSuccess;
 }
 

@@ -1,13 +1,15 @@
 """ms_pair_rank_noalloc -- the pair-ranking step for callers that cannot
 allocate device memory (its working memory is a static array inside the
-library) -- must give exactly what ms_pair_rank gives.  Two calls in a row on
-different inputs check that the shared array is cleared between calls.
+library) -- must give exactly the dense pair ranks of the oracle, and what
+ms_pair_rank gives.  Two calls in a row on different inputs check that the
+shared array is cleared between calls.
 
 This file sorts last so that a run stopping at the first failure has already
 run every other test; it also passes alone in a fresh process."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_2303_15491_gb300 as ms
 import synthfields as sf
 
@@ -23,7 +25,7 @@ def _labels(n, levels, seed):
     return torch.from_numpy(a).cuda(), torch.from_numpy(d).cuda()
 
 
-def test_noalloc_matches_pair_rank_two_calls():
+def test_noalloc_matches_oracle_two_calls():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     ctx = ms.ms_create(0)
@@ -36,8 +38,10 @@ def test_noalloc_matches_pair_rank_two_calls():
             out = torch.full((n,), -7, dtype=torch.int32, device="cuda")
             k = ms.ms_pair_rank_noalloc(a, d, n, out)
             torch.cuda.synchronize()
-            assert k == k_ref
-            assert torch.equal(out, ref)
+            want, k_want = oracle.ms_rank(a.cpu().numpy(), d.cpu().numpy())
+            assert k == k_want
+            assert np.array_equal(out.cpu().numpy(), want)
+            assert k_ref == k_want and torch.equal(out, ref)
     finally:
         ms.ms_destroy(ctx)
 
