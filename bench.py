@@ -402,13 +402,14 @@ def batch_line(args, plain_steps=None):
     t_plain = timed(plain, plain_steps or max(1, args.steps // 4))
     ks = batched()
     ms.ms_destroy(ctx)
+    n_fields = len(fields)
     del fields, outs, asc, desc, mso
     torch.cuda.empty_cache()
     line = {
         "metric": METRIC, "value": n / (t_batch / 1e3), "unit": "vertices/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": "batch256", "desc": WORKLOADS["batch256"]["desc"], "fields": len(fields),
+        "config": {"workload": "batch256", "desc": WORKLOADS["batch256"]["desc"], "fields": n_fields,
                    "vertices": n, "regions_K_total": int(sum(ks)),
                    "l2": "fields 1.1 GB + labels 3.6 GB, larger than L2"},
         "plain_ms_per_step": t_plain, "speedup_vs_plain": t_plain / t_batch,

@@ -48,7 +48,7 @@ MS_NOALLOC_MAX_N = 262144
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("tile_ctas", ctypes.c_int), ("write_ctas", ctypes.c_int),
-                ("resolve_blocks", ctypes.c_int), ("chase_hops", ctypes.c_int),
+                ("chase_blocks", ctypes.c_int), ("pair_blocks", ctypes.c_int),
                 ("dynamic", ctypes.c_int), ("default_ms", ctypes.c_double),
                 ("best_ms", ctypes.c_double)]
 

@@ -15,6 +15,7 @@ using namespace msseg;
 // Sizes a step-by-step tiled call met (they size a captured replay).
 struct RunInfo {
   unsigned long long npairs = 0;  // tile pairs
+  unsigned long long nroots = 0;  // tile roots
   unsigned int m = 0;             // distinct (asc, desc) pairs
   bool use_graph = false;         // exits resolved through the face graph
   int rounds = 0;                 // face-graph rounds it took
@@ -53,8 +54,9 @@ struct ms_ctx {
   size_t graph_bytes = 0;
   void *sxscratch = nullptr;  // index-pass block totals and bases
   size_t sxscratch_bytes = 0;
-  unsigned long long *hcount = nullptr;  // pinned copy of the tiled pair count
+  unsigned long long *hcount = nullptr;  // pinned copies of the tile pass's pair and root counts
   unsigned long long pool_hint = 0;      // pair-pool capacity that sufficed last time
+  unsigned long long root_hint = 0;      // root-list capacity that sufficed last time
   void *batch_dev = nullptr;             // field descriptors + tensor maps on the device
   size_t batch_dev_bytes = 0;
   void *batch_host = nullptr;            // their pinned staging copy
@@ -403,55 +405,54 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
   const std::vector<int> &order = sf.order;
   c->run = RunInfo{};
 
-  // ---- tile pass; the pair pool is sized from the last call, exact on overflow
-  unsigned long long cap = c->pool_hint;
-  if (cap == 0) cap = std::max<unsigned long long>(1ull << 16, (unsigned long long)total_n / 16);
-  if (cap > (unsigned long long)total_n) cap = (unsigned long long)total_n;
+  // ---- tile pass; the pair pool and root list are sized from the last call,
+  // exact on overflow
+  const unsigned long long vslots = (unsigned long long)total_tiles * kTileV;
+  unsigned long long cap = c->pool_hint, rcap = c->root_hint;
+  if (cap == 0) cap = std::max<unsigned long long>(1ull << 16, (unsigned long long)total_n / 4);
+  if (rcap == 0) rcap = std::max<unsigned long long>(1ull << 16, (unsigned long long)total_n / 4);
+  cap = std::min(cap, vslots);
+  rcap = std::min(rcap, 2 * (unsigned long long)total_tiles * kExt);
   TiledScratch ts;
-  unsigned long long npairs = 0;
+  unsigned long long npairs = 0, nroots = 0;
   for (;;) {
     s = reset_status(c);
     if (s != MS_OK) return s;
-    s = ensure_buffer(c, &c->tscratch, &c->tscratch_bytes, tiled_scratch_bytes(total_tiles, nf, cap));
+    s = ensure_buffer(c, &c->tscratch, &c->tscratch_bytes,
+                      tiled_scratch_bytes(total_tiles, nf, cap, rcap));
     if (s != MS_OK) return s;
-    tiled_scratch_carve(c->tscratch, total_tiles, nf, cap, &ts);
+    tiled_scratch_carve(c->tscratch, total_tiles, nf, cap, rcap, &ts);
     StageTimer t0(c, MS_STAGE_TILE_LOCAL);
     MS_TRY(launch_tile_local(b, ts, c->dst, c->stream));
     t0.stop();
-    MS_TRY(cudaMemcpyAsync(c->hcount, ts.pool_count, sizeof(unsigned long long),
+    MS_TRY(cudaMemcpyAsync(c->hcount, ts.counters, 2 * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, c->stream));
     s = read_status(c);
     if (s != MS_OK) return s;
     if (c->hst->nan_flag) return MS_ERR_NAN_INPUT;
     if (c->hst->timeout) return MS_ERR_TIMEOUT;
-    npairs = *c->hcount;
+    npairs = c->hcount[0];
+    nroots = c->hcount[1];
     if (!c->hst->pool_overflow) break;
-    cap = npairs;  // exact now
+    cap = std::max(cap, npairs);  // exact now
+    rcap = std::max(rcap, nroots);
   }
   c->pool_hint = std::max(c->pool_hint, cap);
+  c->root_hint = std::max(c->root_hint, rcap);
 
-  // ---- exits followed, pairs deduplicated; the set is sized from the last
-  // call's region count (or a quarter of the tile pairs), exact on overflow.
-  // Exits are chased face to face; where a sample of the pairs shows long
-  // chains (smooth fields), through the face graph instead, pointer-jumped
-  // in O(log) rounds over all face slots.
+  // ---- every tile root followed to its extremum: face to face, or, where a
+  // sample of the tiles shows long chains (smooth fields), through the face
+  // graph, pointer-jumped in O(log) rounds over all face slots
   StageTimer t2(c, MS_STAGE_RESOLVE);
-  const uint64_t exact = 2 * npairs + 2;
-  uint64_t want = c->last_k ? 2 * (uint64_t)c->last_k + 4096 : npairs / 4;
-  if (want < (1u << 16)) want = 1u << 16;
-  if (want > exact) want = exact;
   const long long slots = face_graph_slots(b);
   bool use_graph = false;
-  if (npairs >= kProbeMinPairs && slots < (1ll << 31)) {
-    const unsigned long long stride = npairs / kProbeSample;
-    MS_TRY(cudaMemsetAsync(&c->dst->pending, 0, sizeof(unsigned int), c->stream));
-    MS_TRY(launch_resolve_pairs(b, ts, RankScratch{}, npairs, kChaseProbe, nullptr, stride, false,
-                                c->dst, c->stream));
+  if (nroots >= kProbeMinRoots && slots < (1ll << 31)) {
+    const long long stride = std::max<long long>(1, total_tiles / kProbeTiles);
+    MS_TRY(cudaMemsetAsync(&c->dst->pending, 0, 2 * sizeof(unsigned int), c->stream));
+    MS_TRY(launch_chase_roots(b, ts, nullptr, stride, c->dst, c->stream));
     s = read_status(c);
     if (s != MS_OK) return s;
-    if (c->hst->not_converged) return MS_ERR_NOT_CONVERGED;
-    const unsigned long long sampled = (npairs + stride - 1) / stride;
-    use_graph = (unsigned long long)c->hst->pending * 8 > sampled;
+    use_graph = (unsigned long long)c->hst->pending * 8 > c->hst->sampled;
   }
   int2 *graph = nullptr;
   if (use_graph) {
@@ -463,6 +464,14 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
     if (s != MS_OK) return s;
     if (c->hst->bad_index) return MS_ERR_CUDA;  // an ill-formed face graph: cannot happen
   }
+  MS_TRY(launch_chase_roots(b, ts, graph, 0, c->dst, c->stream));
+
+  // ---- tile pairs into the global pair set, sized from the last call's
+  // region count (or an eighth of the tile pairs), exact on overflow
+  const uint64_t exact = 2 * npairs + 2;
+  uint64_t want = c->last_k ? 2 * (uint64_t)c->last_k + 4096 : npairs / 8;
+  if (want < (1u << 16)) want = 1u << 16;
+  if (want > exact) want = exact;
   RankScratch rs;
   for (;;) {
     const unsigned int hcap = pow2_at_least(want);
@@ -472,26 +481,17 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
     if (want < exact) rs.probe_limit = kEstimateProbeLimit;
     MS_TRY(cudaMemsetAsync(&c->dst->n_unique, 0, sizeof(unsigned int), c->stream));
     MS_TRY(cudaMemsetAsync(&c->dst->hash_overflow, 0, sizeof(unsigned int), c->stream));
-    MS_TRY(cudaMemsetAsync(&c->dst->pending, 0, sizeof(unsigned int), c->stream));
-    MS_TRY(launch_resolve_pairs(b, ts, rs, npairs, use_graph ? kChaseGraph : kChaseBudget, graph, 1,
-                                true, c->dst, c->stream));
+    MS_TRY(launch_tile_pairs(b, ts, rs, true, c->dst, c->stream));
     s = read_status(c);
     if (s != MS_OK) return s;
     if (c->hst->not_converged) return MS_ERR_NOT_CONVERGED;
-    if (!c->hst->hash_overflow && c->hst->pending) {
-      // the few pairs whose exits lead through more than kChaseHops tiles
-      MS_TRY(launch_resolve_pairs(b, ts, rs, npairs, kChasePending, nullptr, 1, false, c->dst,
-                                  c->stream));
-      s = read_status(c);
-      if (s != MS_OK) return s;
-      if (c->hst->not_converged) return MS_ERR_NOT_CONVERGED;
-    }
     if (!c->hst->hash_overflow) break;
     if (want >= exact) return MS_ERR_CUDA;  // cannot happen: the exact bound always fits
     want = exact;
   }
   const unsigned int m = c->hst->n_unique;
   c->run.npairs = npairs;
+  c->run.nroots = nroots;
   c->run.m = m;
   c->run.use_graph = use_graph;
   {
@@ -636,10 +636,12 @@ ms_status capture_plan(ms_ctx *c, const FieldArg *fa, int nf) {
   const RunInfo run = c->run;
   // capacities: the sizes met, with margins; overflow is detected on the device
   unsigned long long pool_cap = run.npairs + run.npairs / 8 + 4096;
-  if (pool_cap > (unsigned long long)sf.total_n) pool_cap = (unsigned long long)sf.total_n;
+  pool_cap = std::min(pool_cap, (unsigned long long)b.total_tiles * kTileV);
+  unsigned long long root_cap = run.nroots + run.nroots / 8 + 4096;
+  root_cap = std::min(root_cap, 2 * (unsigned long long)b.total_tiles * kExt);
   const unsigned int hcap = pow2_at_least(2ull * run.m + 4096);
   s = ensure_buffer(c, &c->tscratch, &c->tscratch_bytes,
-                    tiled_scratch_bytes(b.total_tiles, nf, pool_cap));
+                    tiled_scratch_bytes(b.total_tiles, nf, pool_cap, root_cap));
   if (s != MS_OK) return s;
   s = ensure_scratch(c, rank_scratch_bytes(hcap));
   if (s != MS_OK) return s;
@@ -651,7 +653,7 @@ ms_status capture_plan(ms_ctx *c, const FieldArg *fa, int nf) {
     graph = static_cast<int2 *>(c->graph);
   }
   TiledScratch ts;
-  tiled_scratch_carve(c->tscratch, b.total_tiles, nf, pool_cap, &ts);
+  tiled_scratch_carve(c->tscratch, b.total_tiles, nf, pool_cap, root_cap, &ts);
   RankScratch rs;
   rank_scratch_carve(c->scratch, hcap, &rs);
   if ((uint64_t)hcap < 2 * run.npairs + 2) rs.probe_limit = kEstimateProbeLimit;
@@ -706,17 +708,9 @@ ms_status capture_plan(ms_ctx *c, const FieldArg *fa, int nf) {
       if ((e = launch_face_graph_build(b, ts, graph, c->dst, c->stream)) != cudaSuccess) return e;
       if ((e = launch_face_graph_rounds(b, graph, 0, rounds, c->dst, c->stream)) != cudaSuccess)
         return e;
-      if ((e = launch_resolve_pairs(b, ts, rs, pool_cap, kChaseGraph, graph, 1, true, c->dst,
-                                    c->stream)) != cudaSuccess)
-        return e;
-    } else {
-      if ((e = launch_resolve_pairs(b, ts, rs, pool_cap, kChaseBudget, nullptr, 1, true, c->dst,
-                                    c->stream)) != cudaSuccess)
-        return e;
-      if ((e = launch_resolve_pairs(b, ts, rs, pool_cap, kChasePending, nullptr, 1, false, c->dst,
-                                    c->stream)) != cudaSuccess)
-        return e;
     }
+    if ((e = launch_chase_roots(b, ts, graph, 0, c->dst, c->stream)) != cudaSuccess) return e;
+    if ((e = launch_tile_pairs(b, ts, rs, true, c->dst, c->stream)) != cudaSuccess) return e;
     if ((e = launch_pairs_sort(rs, rs.max_unique, kb, c->stream, raw, &c->dst->n_unique)) !=
         cudaSuccess)
       return e;
@@ -898,7 +892,7 @@ ms_status ms_create(ms_ctx **out, int device, void *cuda_stream) {
   }
   if (s == MS_OK) s = cuda_status(cudaMalloc(&c->dst, sizeof(DevStatus)));
   if (s == MS_OK) s = cuda_status(cudaMallocHost(&c->hst, sizeof(DevStatus)));
-  if (s == MS_OK) s = cuda_status(cudaMallocHost(&c->hcount, sizeof(unsigned long long)));
+  if (s == MS_OK) s = cuda_status(cudaMallocHost(&c->hcount, 2 * sizeof(unsigned long long)));
   if (s != MS_OK) {
     ms_destroy(c);
     return s;
@@ -1145,8 +1139,8 @@ ms_status ms_batch_autotune(ms_ctx *c, int n_fields, const void *const *fields,
   const Knob knobs[] = {{&Tuning::dynamic, {1, 0}},
                         {&Tuning::tile_ctas, {2, 1}},
                         {&Tuning::write_ctas, {2, 4, 8}},
-                        {&Tuning::resolve_blocks, {8, 16, 32}},
-                        {&Tuning::chase_hops, {8, 16, 32}}};
+                        {&Tuning::chase_blocks, {8, 4, 16}},
+                        {&Tuning::pair_blocks, {6, 3, 8}}};
   for (const Knob &kn : knobs) {
     if (s != MS_OK) break;
     const int start = best.*(kn.field);
@@ -1175,8 +1169,8 @@ ms_status ms_batch_autotune(ms_ctx *c, int n_fields, const void *const *fields,
   if (out) {
     out->tile_ctas = best.tile_ctas;
     out->write_ctas = best.write_ctas;
-    out->resolve_blocks = best.resolve_blocks;
-    out->chase_hops = best.chase_hops;
+    out->chase_blocks = best.chase_blocks;
+    out->pair_blocks = best.pair_blocks;
     out->dynamic = best.dynamic;
     out->default_ms = t_default;
     out->best_ms = t_best;

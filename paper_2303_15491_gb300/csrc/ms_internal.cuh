@@ -20,8 +20,9 @@ struct DevStatus {
   unsigned int n_min;          // minima found by the steepest step
   unsigned int pool_overflow;  // the tiled path's pair pool ran out of room
   unsigned int timeout;        // a bounded wait in a kernel gave up
-  unsigned int pending;         // tile pairs whose exit chase ran out of its hop budget
-  unsigned int pad[2];
+  unsigned int pending;         // probe: sampled tile roots whose chase needs more hops
+  unsigned int sampled;         // probe: tile roots sampled
+  unsigned int pad;
   unsigned int round_open[64];  // round_open[r] != 0: round r left work for round r+1
 };
 

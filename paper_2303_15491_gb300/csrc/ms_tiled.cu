@@ -248,6 +248,30 @@ __device__ __forceinline__ void tma_load_box2(void *dst, const CUtensorMap *map,
 
 constexpr long long kWaitPolls = 1ll << 26;  // about a second of polling: a TMA never takes that
 
+// Bounded wait for the tile's box load (thread 0).  Past the bound the call
+// is flagged MS_ERR_TIMEOUT and the block stops; before it leaves, it polls up
+// to four times longer still, so that a copy still in flight does not land in
+// shared memory that another block (of this or another call) owns next.
+__device__ __forceinline__ void wait_box(uint64_t *bar, uint32_t parity, DevStatus *st, int *s_abort) {
+  long long polls = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if (++polls > kWaitPolls) {
+      atomicOr(&st->timeout, 1u);
+      *s_abort = 1;
+      for (long long q = 0; q < 4 * kWaitPolls && !mbar_try_wait(bar, parity); ++q) __nanosleep(64);
+      break;
+    }
+    __nanosleep(64);
+  }
+}
+
+// Two pointer jumps of a packed (up | dn << 16) entry through the pointer
+// area: up of up's up, dn of dn's dn (Sec. 4.2.1 second step).
+__device__ __forceinline__ uint32_t jump2(const uint32_t *P, uint32_t x) {
+  const uint32_t g1 = __byte_perm(P[x & 0xffffu], P[x >> 16], 0x7610);  // up of up, dn of dn
+  return __byte_perm(P[g1 & 0xffffu], P[g1 >> 16], 0x7610);
+}
+
 // Comparisons of staged values.  Interior tiles (tile and halo inside the
 // field) compare the raw float32 values: IEEE ">=" is the real order, equal
 // reals (including -0 and +0) tie and fall to the index rule, and nvcc does
@@ -401,134 +425,175 @@ __device__ __forceinline__ uint32_t pairset_insert(uint32_t *H, uint32_t key, ui
     if (cur == kEmpty32 || cur == key) return s;
     s = (s + 1) & (kHash - 1);
   }
-  return kEmpty32;  // unreachable: the set holds one slot per vertex
+  return 0;  // unreachable: the set holds one slot per vertex
 }
 
-// The distinct (up-root, dn-root) pairs of a tile whose final pointers are
-// in w[] (one run of kRun per thread, both tile shapes), with uniform work:
-// (1) in each warp row, the first lane of every run of equal pairs is the
-//     run's leader and appends the pair to its warp's candidate list; every
-//     vertex remembers its run's candidate index;
-// (2) each warp inserts its candidates into an open-addressing set H;
-// (3) the used slots of H are numbered by a block scan, which is also the
-//     order of the tile's pair list; candidates take their slot's number.
-// Writes the pair list to the pool (roots through `ref`, exits flagged) and
-// the per-vertex pair numbers; K and P are free scratch here.  Valid run
-// entries are those of a column with col_in, below n_here.
-template <class RootRef>
-__device__ __forceinline__ void number_tile_pairs(uint32_t *K, uint32_t *P, const uint32_t (&w)[kRun],
-                                                  bool col_in, int n_here, int64_t gt, int fi,
-                                                  int n_fields,
+static_assert(2 * kBmW3 <= 2 * kThreads && 2 * kBmW2 <= 2 * kThreads,
+              "two bitmap words per thread cover both root bitmaps");
+static_assert(kHash == kThreads * 16, "each thread numbers 16 consecutive set slots");
+
+// The distinct (dn-root, up-root) pairs and the distinct roots of a tile whose
+// final pointers are in w[] (one run of kRun per thread, both tile shapes).
+//   (1) every run entry whose pair differs from the entry before it inserts
+//       the pair into the open-addressing set H (first fit);
+//   (2) the used slots of H get dense numbers by a block scan (thread t owns
+//       slots 16t .. 16t + 15), in which order they form the pair list PL;
+//       each listed pair marks its dn root and its up root in two bitmaps
+//       over the extended box;
+//   (3) a block scan of the bitmap words' popcounts ranks the roots: the
+//       tile's root list holds its dn roots in box order, then its up roots;
+//   (4) the pair pool gets each pair as (dn-root index, up-root index) in the
+//       root list, the root list gets each root's box index, and every
+//       vertex its pair's dense number.
+// A (kHash + kHash / 2 words) and B (kTileV + 4 kBmW words) are free
+// shared-memory areas; valid run entries are those of a column with col_in,
+// below n_here.
+template <int kBmW>
+__device__ __forceinline__ void number_tile_pairs(uint32_t *A, uint32_t *B, const uint32_t (&w)[kRun],
+                                                  bool col_in, int n_here, int64_t gt,
                                                   const TiledScratch &ts, DevStatus *st,
-                                                  long long *s_base, int (*s_scan2)[kThreads / 32],
-                                                  RootRef ref) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t *H = K;                                           // kHash words
-  uint32_t *CK = P;                                          // kTileV candidate pairs, then the pair list
-  uint16_t *CS = reinterpret_cast<uint16_t *>(P + kTileV);   // candidate slot, then number
-  for (int i = threadIdx.x; i < kHash; i += kThreads) H[i] = kEmpty32;
-  uint32_t cidx[kRun / 2];  // two 16-bit candidate indices per word
-  int ncand = 0;           // this warp's candidates so far
+                                                  int (*s_scan2)[kThreads / 32],
+                                                  unsigned long long *s_base) {
+  const int t = threadIdx.x;
+  uint32_t *H = A;
+  uint16_t *D = reinterpret_cast<uint16_t *>(A + kHash);
+  uint32_t *PL = B;
+  uint32_t *BW = B + kTileV;
+  uint32_t *PW = BW + 2 * kBmW;
+  for (int i = t; i < kHash / 4; i += kThreads)
+    reinterpret_cast<uint4 *>(H)[i] = make_uint4(kEmpty32, kEmpty32, kEmpty32, kEmpty32);
+  for (int i = t; i < 2 * kBmW; i += kThreads) BW[i] = 0u;
+  __syncthreads();
+  // (1) inserts: one per change of pair along the run
+  uint32_t slot2[kRun / 2];  // two 16-bit set slots per word
   {
-    // A run of equal pairs along the lanes takes the candidate of its first
-    // lane; that lane makes a new candidate unless its pair equals its own
-    // pair one step back along the run (then it reuses that candidate).
-    const int seg = warp * (kRun * 32);
-    uint32_t prev_key = kEmpty32;  // this lane's pair at j - 1 (kEmpty32: none)
-    int prev_ci = 0;
+    uint32_t prev = kEmpty32, ps = 0;
 #pragma unroll
     for (int j = 0; j < kRun; ++j) {
-      const bool valid = col_in && j < n_here;
-      const uint32_t key = valid ? w[j] : kEmpty32;
-      const uint32_t left = __shfl_up_sync(0xffffffffu, key, 1);
-      const bool start = valid && (lane == 0 || left != key);
-      const bool fresh = start && key != prev_key;
-      const unsigned lm = __ballot_sync(0xffffffffu, fresh);
-      const int my = seg + ncand + __popc(lm & ((1u << lane) - 1u));
-      if (fresh) CK[my] = key;
-      // the run's first lane is the highest start lane at or below this lane
-      const unsigned sm = __ballot_sync(0xffffffffu, start);
-      const unsigned upto = sm & (0xffffffffu >> (31 - lane));
-      const int src = upto ? 31 - __clz(upto) : lane;
-      const int ci = __shfl_sync(0xffffffffu, fresh ? my : prev_ci, src);
-      const uint32_t c = valid ? (uint32_t)ci : 0u;
+      const uint32_t key = w[j];
+      if (col_in && j < n_here && key != prev) {
+        ps = pairset_insert(H, key, hash32(key));
+        prev = key;
+      }
       if (j & 1)
-        cidx[j / 2] |= c << 16;
+        slot2[j / 2] |= ps << 16;
       else
-        cidx[j / 2] = c;
-      prev_key = key;
-      prev_ci = ci;
-      ncand += __popc(lm);
+        slot2[j / 2] = ps;
     }
   }
-  __syncthreads();  // H cleared, candidates written
-  {
-    const int seg = warp * (kRun * 32);
-    for (int i = lane; i < ncand; i += 32) CS[seg + i] = (uint16_t)pairset_insert(H, CK[seg + i], hash32(CK[seg + i]));
-  }
   __syncthreads();
-  // number the used slots: thread t owns slots t, t + 512, ...
-  constexpr int kPer = kHash / kThreads;
-  int cnt = 0;
-#pragma unroll
-  for (int j = 0; j < kPer; ++j) cnt += H[threadIdx.x + kThreads * j] != kEmpty32;
-  int ex, dummy_e, npairs, dummy_t;
-  block_scan2(cnt, 0, &ex, &dummy_e, &npairs, &dummy_t, s_scan2);
+  // (2) dense numbers of the used slots; the pair list; roots marked
+  int npairs;
   {
+    uint32_t hk[16];
+    const uint4 *h4 = reinterpret_cast<const uint4 *>(H + 16 * t);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint4 v = h4[q];
+      hk[4 * q] = v.x, hk[4 * q + 1] = v.y, hk[4 * q + 2] = v.z, hk[4 * q + 3] = v.w;
+    }
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) cnt += hk[k] != kEmpty32;
+    int ex, e2, t2;
+    block_scan2(cnt, 0, &ex, &e2, &npairs, &t2, s_scan2);
     int id = ex;
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const int sl = threadIdx.x + kThreads * j;
-      const uint32_t key = H[sl];
+    for (int k = 0; k < 16; ++k) {
+      const uint32_t key = hk[k];
       if (key != kEmpty32) {
-        CK[id] = key;  // the pair list replaces the (inserted) candidates
-        H[sl] = (uint32_t)id;
+        D[16 * t + k] = (uint16_t)id;
+        PL[id] = key;
+        const uint32_t dn = key >> 16, up = key & 0xffffu;
+        atomicOr(&BW[dn >> 5], 1u << (dn & 31u));
+        atomicOr(&BW[kBmW + (up >> 5)], 1u << (up & 31u));
         ++id;
       }
     }
   }
-  if (threadIdx.x == 0) {
-    const long long b = (long long)atomicAdd(ts.pool_count, (unsigned long long)npairs);
-    *s_base = b;
-    ts.tile_base[gt] = b;
-    ts.tile_count[gt] = npairs;
+  __syncthreads();
+  // (3) root ranks: exclusive prefix popcounts over the dn words, then the up words
+  int nroots;
+  {
+    const int w0 = t, w1 = t + kThreads;
+    const int a = w0 < 2 * kBmW ? __popc(BW[w0]) : 0;
+    const int b = w1 < 2 * kBmW ? __popc(BW[w1]) : 0;
+    int ea, eb, ta, tb;
+    block_scan2(a, b, &ea, &eb, &ta, &tb, s_scan2);  // ends with a barrier
+    if (w0 < 2 * kBmW) PW[w0] = (uint32_t)ea;
+    if (w1 < 2 * kBmW) PW[w1] = (uint32_t)(ta + eb);
+    nroots = ta + tb;
+    if (t == 0) s_base[0] = atomicAdd(&ts.counters[0], (unsigned long long)npairs);
+    if (t == 32) s_base[1] = atomicAdd(&ts.counters[1], (unsigned long long)nroots);
   }
   __syncthreads();
-  {
-    const int seg = warp * (kRun * 32);
-    for (int i = lane; i < ncand; i += 32) CS[seg + i] = (uint16_t)H[CS[seg + i]];
+  const unsigned long long pbase = s_base[0], rbase = s_base[1];
+  const int nd = (int)PW[kBmW];
+  if (t == 0) {
+    TileMeta m;
+    m.pbase = pbase;
+    m.rbase = rbase;
+    m.npairs = npairs;
+    m.nd = nd;
+    m.nu = nroots - nd;
+    m.pad = 0;
+    ts.meta[gt] = m;
+    if (pbase + (unsigned long long)npairs > ts.pool_cap) atomicOr(&st->pool_overflow, 1u);
+    if (rbase + (unsigned long long)nroots > ts.root_cap) atomicOr(&st->pool_overflow, 1u);
   }
-  {
-    // the tile's pair list to the pool: global root indices, exits flagged
-    const long long base = *s_base;
-    const uint32_t *PL = CK;
-    for (int i = threadIdx.x; i < npairs; i += kThreads) {
-      const long long at = base + i;
-      if (at >= (long long)ts.pool_cap) {
-        atomicOr(&st->pool_overflow, 1u);
-        break;
-      }
+  // (4) pool entries, root list, per-vertex numbers
+  if (pbase + (unsigned long long)npairs <= ts.pool_cap) {
+    for (int i = t; i < npairs; i += kThreads) {
       const uint32_t key = PL[i];
-      const int u = (int)(key & 0xffffu), d = (int)(key >> 16);
-      ts.pool_roots[at] = make_int2(ref(d), ref(u));
-      if (n_fields > 1) ts.pool_field[at] = (uint32_t)fi;
+      const uint32_t dn = key >> 16, up = key & 0xffffu;
+      const uint32_t wd = dn >> 5, wu = kBmW + (up >> 5);
+      const uint32_t di = PW[wd] + __popc(BW[wd] & ((1u << (dn & 31u)) - 1u));
+      const uint32_t ui = PW[wu] + __popc(BW[wu] & ((1u << (up & 31u)) - 1u));
+      ts.pool_pair[pbase + i] = di | (ui << 16);
     }
   }
-  __syncthreads();
-  uint32_t cell[kRun];
+  if (rbase + (unsigned long long)nroots <= ts.root_cap) {
 #pragma unroll
-  for (int j = 0; j < kRun; ++j) cell[j] = CS[(cidx[j / 2] >> (16 * (j & 1))) & 0xffffu];
-  // per-vertex pair numbers: the column's 16 numbers are one 32-byte vector
+    for (int q = 0; q < 2; ++q) {
+      const int wi = t + q * kThreads;
+      if (wi < 2 * kBmW) {
+        uint32_t bits = BW[wi];
+        uint32_t r = PW[wi];
+        const uint32_t box0 = 32u * (uint32_t)(wi < kBmW ? wi : wi - kBmW);
+        while (bits) {
+          const uint32_t b = (uint32_t)(__ffs(bits) - 1);
+          bits &= bits - 1u;
+          ts.root_box[rbase + r] = (uint16_t)(box0 + b);
+          ++r;
+        }
+      }
+    }
+  }
   if (col_in) {
     uint32_t packed[kRun / 2];
 #pragma unroll
-    for (int j = 0; j < kRun; j += 2) packed[j / 2] = (cell[j] & 0xffffu) | (cell[j + 1] << 16);
+    for (int j = 0; j < kRun; j += 2)
+      packed[j / 2] = (uint32_t)D[slot2[j / 2] & 0xffffu] | ((uint32_t)D[slot2[j / 2] >> 16] << 16);
     uint4 *pid4 = reinterpret_cast<uint4 *>(ts.pid + gt * (int64_t)kTileV +
                                             (int64_t)threadIdx.x * kRun);
     pid4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
     pid4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
   }
-  __syncthreads();
+  __syncthreads();  // A and B are reused by the next tile
+}
+
+// An empty tile record (a tile skipped for a NaN): no pairs, no roots.
+__device__ __forceinline__ void empty_tile(const TiledScratch &ts, int64_t gt) {
+  if (threadIdx.x == 0) {
+    TileMeta m;
+    m.pbase = 0;
+    m.rbase = 0;
+    m.npairs = 0;
+    m.nd = 0;
+    m.nu = 0;
+    m.pad = 0;
+    ts.meta[gt] = m;
+  }
 }
 
 // Tile scheduling of the persistent kernels: a static stride over the tile
@@ -574,7 +639,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
   uint32_t *K = dsmem;         // kExt words: values / keys, then pair-numbering scratch
   uint32_t *P = dsmem + kExt;  // kExt words: up | dn << 16, box indices
   __shared__ __align__(8) uint64_t s_bar;
-  __shared__ long long s_base;
+  __shared__ unsigned long long s_base[2];
   __shared__ int s_abort;
   __shared__ int s_scan2[2][kThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -587,9 +652,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
 
   __shared__ long long s_next;
   const bool dyn = bt.tune.dynamic != 0;
-  for (long long k = queue_first(dyn, ts.queue + 0, &s_next); k < bt.tiles3;
+  for (long long k = queue_first(dyn, ts.queue + kQTile3, &s_next); k < bt.tiles3;
        k = queue_next(dyn, k, &s_next)) {
-    queue_prefetch(dyn, ts.queue + 0, &s_next);
+    queue_prefetch(dyn, ts.queue + kQTile3, &s_next);
     const int64_t gt = k;
     const int fi = kSingle ? 0 : field_of(bt, gt);
     const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
@@ -612,17 +677,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
         mbar_expect_tx(&s_bar, (uint32_t)(kExt * 4));
         tma_load_box(K, &bt.tmaps[fi], &s_bar, (int)(x0 - kXO), (int)(y0 - 1), (int)(z0 - 1));
       }
-      if (threadIdx.x == 0) {
-        long long polls = 0;
-        while (!mbar_try_wait(&s_bar, parity)) {
-          if (++polls > kWaitPolls) {
-            atomicOr(&st->timeout, 1u);
-            s_abort = 1;
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
+      if (threadIdx.x == 0) wait_box(&s_bar, parity, st, &s_abort);
       __syncthreads();
       if (s_abort) return;  // block-uniform
       parity ^= 1u;
@@ -670,7 +725,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
       steepest_tile<false>(K, P, lx, ly, col_in, nz_here, w, &nan);
     if (__syncthreads_or(nan)) {
       // the call fails with MS_ERR_NAN_INPUT; skip the rest of this tile
-      if (threadIdx.x == 0) ts.tile_count[gt] = 0;
+      empty_tile(ts, gt);
       __syncthreads();
       continue;
     }
@@ -721,8 +776,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
 #pragma unroll
         for (int lz = 0; lz < kTZ; ++lz) {
           if (__any_sync(0xffffffffu, (open >> lz) & 1u)) {
-            const uint32_t gu = P[w[lz] & 0xffffu], gd = P[w[lz] >> 16];
-            const uint32_t nw = __byte_perm(gu, gd, 0x7610);  // up of gu, dn of gd
+            const uint32_t nw = jump2(P, w[lz]);
             if (nw != w[lz]) {
               w[lz] = nw;
               P[ext_of(lx, ly, lz)] = nw;
@@ -748,8 +802,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
     }
     __syncthreads();
 
-    number_tile_pairs(K, P, w, col_in, nz_here, gt, fi, bt.n_fields, ts, st, &s_base, s_scan2,
-                      [&](int e) { return root_ref(g, x0, y0, z0, e); });
+    number_tile_pairs<kBmW3>(K, P, w, col_in, nz_here, gt, ts, st, s_scan2, s_base);
   }
   if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&st->nan_flag, 1u);
 }
@@ -813,10 +866,10 @@ __device__ __forceinline__ void steepest_run2(const uint32_t *__restrict__ K, in
 template <bool kSingle>
 __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScratch ts, DevStatus *st) {
   extern __shared__ __align__(128) uint32_t dsmem[];
-  uint32_t *K = dsmem;          // k2Ext words: values / keys, then the pair set
-  uint32_t *P = dsmem + k2Ext;  // k2PArea words: up | dn << 16, then candidates
+  uint32_t *K = dsmem;            // k2KArea words: values / keys, then the pair list and bitmaps
+  uint32_t *P = dsmem + k2KArea;  // k2PArea words: up | dn << 16, then the pair set
   __shared__ __align__(8) uint64_t s_bar;
-  __shared__ long long s_base;
+  __shared__ unsigned long long s_base[2];
   __shared__ int s_abort;
   __shared__ int s_scan2[2][kThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -829,9 +882,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScra
 
   __shared__ long long s_next;
   const bool dyn = bt.tune.dynamic != 0;
-  for (long long k = queue_first(dyn, ts.queue + 1, &s_next); k < bt.total_tiles - bt.tiles3;
+  for (long long k = queue_first(dyn, ts.queue + kQTile2, &s_next); k < bt.total_tiles - bt.tiles3;
        k = queue_next(dyn, k, &s_next)) {
-    queue_prefetch(dyn, ts.queue + 1, &s_next);
+    queue_prefetch(dyn, ts.queue + kQTile2, &s_next);
     const int64_t gt = bt.tiles3 + k;
     const int fi = kSingle ? 0 : field_of(bt, gt);
     const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
@@ -848,15 +901,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScra
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(&s_bar, (uint32_t)(k2Ext * 4));
         tma_load_box2(K, &bt.tmaps[fi], &s_bar, (int)(x0 - kXO), (int)(y0 - 1));
-        long long polls = 0;
-        while (!mbar_try_wait(&s_bar, parity)) {
-          if (++polls > kWaitPolls) {
-            atomicOr(&st->timeout, 1u);
-            s_abort = 1;
-            break;
-          }
-          __nanosleep(64);
-        }
+        wait_box(&s_bar, parity, st, &s_abort);
       }
       __syncthreads();
       if (s_abort) return;  // block-uniform
@@ -889,7 +934,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScra
     else
       steepest_run2<false>(K, cx, cy0, col_in, n_here, w, &nan);
     if (__syncthreads_or(nan)) {
-      if (threadIdx.x == 0) ts.tile_count[gt] = 0;
+      empty_tile(ts, gt);
       __syncthreads();
       continue;
     }
@@ -915,8 +960,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScra
       bool changed = false;
 #pragma unroll
       for (int j = 0; j < kRun; ++j) {
-        const uint32_t gu = P[w[j] & 0xffffu], gd = P[w[j] >> 16];
-        const uint32_t nw = __byte_perm(gu, gd, 0x7610);
+        const uint32_t nw = jump2(P, w[j]);
         if (nw != w[j]) {
           w[j] = nw;
           P[ext2_of(cx, cy0 + j)] = nw;
@@ -937,77 +981,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScra
     }
     __syncthreads();
 
-    number_tile_pairs(K, P, w, col_in, n_here, gt, fi, bt.n_fields, ts, st, &s_base, s_scan2,
-                      [&](int e) { return root_ref2(g, x0, y0, e); });
+    number_tile_pairs<kBmW2>(P, K, w, col_in, n_here, gt, ts, st, s_scan2, s_base);
   }
   if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&st->nan_flag, 1u);
-}
-
-// Follow an exit (a vertex on another tile's face) through the face roots
-// until an extremum; `up` selects the direction.  All indices fit 31 bits
-// (N < 2^31), so the hops use 32-bit arithmetic.  A path may leave and
-// re-enter the same tile many times, so the number of hops is not bounded by
-// the tile count; but every hop lands on a different halo vertex of the same
-// strictly monotone path, so it is bounded by the number of face slots and by
-// N.  The cap only guards against a corrupted face array.
-// Returns the extremum, or -1 once `budget` hops have not reached one (the
-// caller defers the pair).
-__device__ int32_t chase(const TileGeom &g, const uint32_t *__restrict__ face, int32_t r, bool up,
-                         int64_t budget, DevStatus *st) {
-  const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny, gtx = (uint32_t)g.tx,
-                 gty = (uint32_t)g.ty;
-  const int64_t n = g.nx * g.ny * g.nz, slots = g.ntiles * kFace;
-  const int64_t max_hops = n < slots ? n : slots;
-  const int64_t lim = budget < max_hops ? budget : max_hops;
-  for (int64_t hop = 0; hop <= lim; ++hop) {
-    if (!(r & kExitFlag)) return r;
-    uint32_t q, x, y, z;
-    g.div_nx.divmod((uint32_t)(r & ~kExitFlag), &q, &x);
-    g.div_ny.divmod(q, &z, &y);
-    const uint32_t tx = x / kTX, ty = y / kTY, tz = z / kTZ;
-    const uint32_t tile = tx + gtx * (ty + gty * tz);
-    const int fs = face_slot((int)(x - tx * kTX), (int)(y - ty * kTY), (int)(z - tz * kTZ));
-    if (fs < 0) break;
-    const uint32_t w = __ldg(&face[(size_t)tile * kFace + fs]);
-    const uint32_t loc = up ? (w & 0xffffu) : (w >> 16);
-    const uint32_t ez = loc / (kEX * kEY), rr = loc - ez * (kEX * kEY);
-    const uint32_t ey = rr / kEX, ex = rr - ey * kEX;
-    const bool halo = ex == kXO - 1 || ex == kXO + kTX || ey == 0 || ez == 0 || ey == kEY - 1 ||
-                      ez == kEZ - 1;
-    const uint32_t gx = tx * kTX + ex - kXO, gy = ty * kTY + ey - 1, gz = tz * kTZ + ez - 1;
-    r = (int32_t)(gx + nx * (gy + ny * gz)) | (halo ? kExitFlag : 0);
-  }
-  if (!(r & kExitFlag)) return r;  // reached on the last hop
-  if (lim < max_hops) return -1;
-  atomicOr(&st->not_converged, 1u);
-  return 0;
-}
-
-// chase for 2D fields (k2TX x k2TY tiles).
-__device__ int32_t chase2(const TileGeom &g, const uint32_t *__restrict__ face, int32_t r, bool up,
-                          int64_t budget, DevStatus *st) {
-  const uint32_t nx = (uint32_t)g.nx, gtx = (uint32_t)g.tx;
-  const int64_t n = g.nx * g.ny, slots = g.ntiles * k2Face;
-  const int64_t max_hops = n < slots ? n : slots;
-  const int64_t lim = budget < max_hops ? budget : max_hops;
-  for (int64_t hop = 0; hop <= lim; ++hop) {
-    if (!(r & kExitFlag)) return r;
-    uint32_t x, y;
-    g.div_nx.divmod((uint32_t)(r & ~kExitFlag), &y, &x);
-    const uint32_t tx = x / k2TX, ty = y / k2TY;
-    const int fs = face_slot2((int)(x - tx * k2TX), (int)(y - ty * k2TY));
-    if (fs < 0) break;
-    const uint32_t w = __ldg(&face[(size_t)(tx + gtx * ty) * kFace + fs]);
-    const uint32_t loc = up ? (w & 0xffffu) : (w >> 16);
-    const uint32_t ey = loc / k2EX, ex = loc - ey * k2EX;
-    const bool halo = ex == kXO - 1 || ex == kXO + k2TX || ey == 0 || ey == k2EY - 1;
-    const uint32_t gx = tx * k2TX + ex - kXO, gy = ty * k2TY + ey - 1;
-    r = (int32_t)(gx + nx * gy) | (halo ? kExitFlag : 0);
-  }
-  if (!(r & kExitFlag)) return r;  // reached on the last hop
-  if (lim < max_hops) return -1;
-  atomicOr(&st->not_converged, 1u);
-  return 0;
 }
 
 // Global face-graph slot of a face vertex v (a tile exit) of a field whose
@@ -1147,112 +1123,336 @@ __device__ __forceinline__ unsigned long long mix64t(unsigned long long k) {
   return k;
 }
 
-constexpr uint32_t kPendingSlot = 0xfffffffeu;
+// Returns true (block-uniform) when an earlier stage of the call found its
+// buffers too small or the input bad: the tile records are then not valid to
+// read (a replayed graph runs every stage regardless; the host runs the call
+// again step by step or reports the error).
+__device__ __forceinline__ bool call_failed(const DevStatus *st) {
+  return (st->pool_overflow | st->nan_flag | st->timeout | st->bad_index) != 0u;
+}
 
-// kSingle: one field, whose descriptor is bt.f0 (kernel parameters).
+// One step of a root's chase.  The chase stands at box index e of tile
+// (tx, ty, tz) of its field, following dn pointers (asc, toward a minimum) or
+// up pointers.  If e lies inside the tile it is the extremum: *label is set
+// and true returned.  Otherwise e is a vertex of a neighbouring tile, on that
+// tile's face; the chase moves there and reads that vertex's tile root from
+// the face array (one dependent load).  Every hop lands on a later vertex of
+// the same strictly monotone integral line, so a chase ends.
+struct Chase {
+  uint32_t e;
+  int tx, ty, tz;
+};
+
+__device__ __forceinline__ bool chase_step3(const TileGeom &g, const uint32_t *__restrict__ face,
+                                            bool up, Chase *c, int32_t *label) {
+  const uint32_t ez = c->e / (uint32_t)(kEX * kEY), r = c->e - ez * (uint32_t)(kEX * kEY);
+  const uint32_t ey = r / (uint32_t)kEX, ex = r - ey * (uint32_t)kEX;
+  int lx = (int)ex - kXO, ly = (int)ey - 1, lz = (int)ez - 1;
+  const int dx = lx < 0 ? -1 : (lx >= kTX ? 1 : 0);
+  const int dy = ly < 0 ? -1 : (ly >= kTY ? 1 : 0);
+  const int dz = lz < 0 ? -1 : (lz >= kTZ ? 1 : 0);
+  if ((dx | dy | dz) == 0) {
+    *label = (int32_t)((uint32_t)(c->tx * kTX + lx) +
+                       (uint32_t)g.nx * ((uint32_t)(c->ty * kTY + ly) + (uint32_t)g.ny * (uint32_t)(c->tz * kTZ + lz)));
+    return true;
+  }
+  c->tx += dx, c->ty += dy, c->tz += dz;
+  lx -= dx * kTX, ly -= dy * kTY, lz -= dz * kTZ;
+  const uint32_t tile = (uint32_t)c->tx + (uint32_t)g.tx * ((uint32_t)c->ty + (uint32_t)g.ty * (uint32_t)c->tz);
+  const uint32_t w = __ldg(&face[(size_t)tile * kFace + face_slot(lx, ly, lz)]);
+  c->e = up ? (w & 0xffffu) : (w >> 16);
+  return false;
+}
+
+__device__ __forceinline__ bool chase_step2(const TileGeom &g, const uint32_t *__restrict__ face,
+                                            bool up, Chase *c, int32_t *label) {
+  const uint32_t ey = c->e / (uint32_t)k2EX, ex = c->e - ey * (uint32_t)k2EX;
+  int lx = (int)ex - kXO, ly = (int)ey - 1;
+  const int dx = lx < 0 ? -1 : (lx >= k2TX ? 1 : 0);
+  const int dy = ly < 0 ? -1 : (ly >= k2TY ? 1 : 0);
+  if ((dx | dy) == 0) {
+    *label = (int32_t)((uint32_t)(c->tx * k2TX + lx) + (uint32_t)g.nx * (uint32_t)(c->ty * k2TY + ly));
+    return true;
+  }
+  c->tx += dx, c->ty += dy;
+  lx -= dx * k2TX, ly -= dy * k2TY;
+  const uint32_t tile = (uint32_t)c->tx + (uint32_t)g.tx * (uint32_t)c->ty;
+  const uint32_t w = __ldg(&face[(size_t)tile * kFace + face_slot2(lx, ly)]);
+  c->e = up ? (w & 0xffffu) : (w >> 16);
+  return false;
+}
+
+// The label of a chase standing inside its tile (an extremum), if it does.
+__device__ __forceinline__ bool interior_label(const TileGeom &g, const Chase &c, int32_t *label) {
+  if (g.flat) {
+    const uint32_t ey = c.e / (uint32_t)k2EX, ex = c.e - ey * (uint32_t)k2EX;
+    const int lx = (int)ex - kXO, ly = (int)ey - 1;
+    if (lx < 0 || lx >= k2TX || ly < 0 || ly >= k2TY) return false;
+    *label = (int32_t)((uint32_t)(c.tx * k2TX + lx) + (uint32_t)g.nx * (uint32_t)(c.ty * k2TY + ly));
+    return true;
+  }
+  const uint32_t ez = c.e / (uint32_t)(kEX * kEY), r = c.e - ez * (uint32_t)(kEX * kEY);
+  const uint32_t ey = r / (uint32_t)kEX, ex = r - ey * (uint32_t)kEX;
+  const int lx = (int)ex - kXO, ly = (int)ey - 1, lz = (int)ez - 1;
+  if (lx < 0 || lx >= kTX || ly < 0 || ly >= kTY || lz < 0 || lz >= kTZ) return false;
+  *label = (int32_t)((uint32_t)(c.tx * kTX + lx) +
+                     (uint32_t)g.nx * ((uint32_t)(c.ty * kTY + ly) + (uint32_t)g.ny * (uint32_t)(c.tz * kTZ + lz)));
+  return true;
+}
+
+// The jumped face graph's answer for a chase standing on a halo vertex: the
+// extremum the neighbouring tile's face vertex leads to.
+__device__ __forceinline__ int32_t graph_label(const TileGeom &g, long long tile_base,
+                                               const int2 *__restrict__ graph, bool up, const Chase &c,
+                                               DevStatus *st) {
+  int tx = c.tx, ty = c.ty, tz = c.tz, fs;
+  if (g.flat) {
+    const uint32_t ey = c.e / (uint32_t)k2EX, ex = c.e - ey * (uint32_t)k2EX;
+    int lx = (int)ex - kXO, ly = (int)ey - 1;
+    const int dx = lx < 0 ? -1 : (lx >= k2TX ? 1 : 0), dy = ly < 0 ? -1 : (ly >= k2TY ? 1 : 0);
+    tx += dx, ty += dy;
+    fs = face_slot2(lx - dx * k2TX, ly - dy * k2TY);
+  } else {
+    const uint32_t ez = c.e / (uint32_t)(kEX * kEY), r = c.e - ez * (uint32_t)(kEX * kEY);
+    const uint32_t ey = r / (uint32_t)kEX, ex = r - ey * (uint32_t)kEX;
+    int lx = (int)ex - kXO, ly = (int)ey - 1, lz = (int)ez - 1;
+    const int dx = lx < 0 ? -1 : (lx >= kTX ? 1 : 0), dy = ly < 0 ? -1 : (ly >= kTY ? 1 : 0),
+              dz = lz < 0 ? -1 : (lz >= kTZ ? 1 : 0);
+    tx += dx, ty += dy, tz += dz;
+    fs = face_slot(lx - dx * kTX, ly - dy * kTY, lz - dz * kTZ);
+  }
+  const long long tile = tile_base + tx + g.tx * (ty + g.ty * (long long)tz);
+  const int2 e = graph[tile * kFace + fs];
+  const uint32_t f = (uint32_t)(up ? e.x : e.y);
+  if (!(f & kSlotFinal)) atomicOr(&st->not_converged, 1u);
+  return (int32_t)(f & ~kSlotFinal);
+}
+
+// Root chase (see launch_chase_roots).  A warp takes one tile at a time from
+// a work queue; its lanes take the tile's roots in turn (lane l roots l,
+// l + 32, ...) and each lane moves on to its next root as soon as one ends,
+// so one long chain holds up no other lane.
+constexpr int kChaseThreads = 256;
+
 template <bool kSingle>
-__global__ void k_resolve_pairs(Batch bt, TiledScratch ts, RankScratch rs, int mode,
-                                const int2 *__restrict__ graph, unsigned long long stride,
-                                DevStatus *st) {
-  const unsigned long long npairs = min(*ts.pool_count, ts.pool_cap);
-  // the unbudgeted pass walks the pending list, or the whole pool if the
-  // list overflowed
-  const unsigned long long npend = mode == kChasePending ? *(volatile unsigned int *)&st->pending : 0;
-  const bool from_list = mode == kChasePending && npend <= ts.pending_cap;
-  const unsigned long long nwork = mode == kChaseProbe ? (npairs + stride - 1) / stride
-                                   : from_list         ? npend
-                                                       : npairs;
-  const unsigned long long step = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned int mask = rs.capacity - 1u;
-  // A set found too small stops the pass early (the host retries larger).
-  // The flag is one word that every warp would read: it is read on every
-  // 32nd iteration only, or that word's L2 line serialises the pass.
-  unsigned int overflow = 0, it = 0;
-  for (unsigned long long w = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; w < nwork;
-       w += step) {
-    if ((it++ & 31u) == 0) overflow = __ldcg(&st->hash_overflow);
-    const unsigned long long p = mode == kChaseProbe ? w * stride : from_list ? ts.pending_list[w] : w;
-    if (mode == kChasePending && !from_list && ts.pool_slot[p] != kPendingSlot) continue;
-    const int2 r = ts.pool_roots[p];
-    const uint32_t fi = kSingle ? 0u : ts.pool_field[p];
+__global__ void __launch_bounds__(kChaseThreads) k_chase_roots(Batch bt, TiledScratch ts,
+                                                               const int2 *__restrict__ graph,
+                                                               long long probe_stride,
+                                                               DevStatus *st) {
+  if (call_failed(st)) return;
+  const int lane = threadIdx.x & 31;
+  const bool probe = probe_stride > 0;
+  const long long nwork = probe ? (bt.total_tiles + probe_stride - 1) / probe_stride : bt.total_tiles;
+  unsigned int sampled = 0, pending = 0;
+  for (;;) {
+    long long k = 0;
+    if (lane == 0) k = (long long)atomicAdd(ts.queue + kQChase, 1u);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= nwork) break;
+    const int64_t gt = probe ? k * probe_stride : k;
+    const TileMeta m = ts.meta[gt];
+    const int fi = kSingle ? 0 : field_of(bt, gt);
     const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
-    int32_t a, d;
-    if (mode == kChaseGraph) {
-      auto final_of = [&](int32_t x, bool up) -> int32_t {
-        if (!(x & kExitFlag)) return x;
-        const int2 e = graph[slot_of_vertex(fd.g, fd.tile_base, (uint32_t)(x & ~kExitFlag))];
-        const uint32_t f = (uint32_t)(up ? e.x : e.y);
-        if (!(f & kSlotFinal)) atomicOr(&st->not_converged, 1u);
-        return (int32_t)(f & ~kSlotFinal);
-      };
-      a = final_of(r.x, false);
-      d = final_of(r.y, true);
-    } else {
-      const int64_t budget =
-          mode == kChaseProbe ? kProbeHops : mode == kChaseBudget ? bt.tune.chase_hops : (1ll << 40);
-      const uint32_t *face = ts.face + fd.tile_base * (long long)kFace;
-      a = fd.g.flat ? chase2(fd.g, face, r.x, false, budget, st)
-                    : chase(fd.g, face, r.x, false, budget, st);
-      d = fd.g.flat ? chase2(fd.g, face, r.y, true, budget, st)
-                    : chase(fd.g, face, r.y, true, budget, st);
-      if (mode == kChaseProbe) {
-        if (a < 0 || d < 0) atomicAdd(&st->pending, 1u);
-        continue;
+    const TileGeom &g = fd.g;
+    const uint32_t *__restrict__ face = ts.face + fd.tile_base * (long long)kFace;
+    int tx0, ty0, tz0 = 0;
+    {
+      const int64_t tile = gt - fd.tile_base;
+      uint32_t r, tx, ty, tz = 0;
+      if (g.flat) {
+        g.div_tx.divmod((uint32_t)tile, &ty, &tx);
+      } else {
+        g.div_tx.divmod((uint32_t)tile, &r, &tx);
+        g.div_ty.divmod(r, &tz, &ty);
       }
-      if (a < 0 || d < 0) {  // only with the budget: resolved by a later pass
-        ts.pool_slot[p] = kPendingSlot;
-        const unsigned int at = atomicAdd(&st->pending, 1u);
-        if (at < ts.pending_cap) ts.pending_list[at] = (uint32_t)p;
-        continue;
-      }
+      tx0 = (int)tx, ty0 = (int)ty, tz0 = (int)tz;
     }
-    const unsigned long long key =
-        bt.key_mode == kKeyBatch
-            ? (((unsigned long long)fi << 48) | ((unsigned long long)(uint32_t)a << 24) | (uint32_t)d)
-            : (((unsigned long long)(uint32_t)a << 32) | (uint32_t)d);
-    // insert into the global pair set (first fit, open addressing); stop as
-    // soon as the set is known to be too small (the host retries larger)
-    unsigned int slot = (unsigned int)mix64t(key) & mask, found = 0xffffffffu;
-    if (overflow) continue;
-    bool fresh = false;  // this thread's CAS placed the key
-    for (unsigned int probe = 0; probe < rs.probe_limit; ++probe) {
-      unsigned long long cur = __ldcg(&rs.table_keys[slot]);
-      if (cur == ~0ull) {
-        cur = atomicCAS(&rs.table_keys[slot], ~0ull, key);
-        if (cur == ~0ull) {
-          fresh = true;
-          found = slot;
-          break;
+    const int nr = m.nd + m.nu;
+    const int64_t n = g.nx * g.ny * g.nz;
+    const int64_t slots = g.ntiles * (int64_t)kFace;
+    const int64_t max_hops = probe ? kProbeHops : (n < slots ? n : slots);
+    int i = lane;
+    bool have = i < nr;
+    Chase c{0u, tx0, ty0, tz0};
+    int64_t hops = 0;
+    if (have) c.e = ts.root_box[m.rbase + i];
+    while (__any_sync(0xffffffffu, have)) {
+      if (have) {
+        const bool up = i >= m.nd;
+        int32_t label = 0;
+        bool done;
+        if (graph) {  // an exit: the graph knows where its path ends
+          done = interior_label(g, c, &label);
+          if (!done) {
+            label = graph_label(g, fd.tile_base, graph, up, c, st);
+            done = true;
+          }
+        } else {
+          done = g.flat ? chase_step2(g, face, up, &c, &label) : chase_step3(g, face, up, &c, &label);
+          if (!done && ++hops > max_hops) {
+            if (probe)
+              ++pending;
+            else
+              atomicOr(&st->not_converged, 1u);
+            done = true;
+            label = 0;
+          }
+        }
+        if (done) {
+          if (probe)
+            ++sampled;
+          else
+            ts.root_label[m.rbase + i] = label;
+          i += 32;
+          have = i < nr;
+          hops = 0;
+          c = Chase{0u, tx0, ty0, tz0};
+          if (have) c.e = ts.root_box[m.rbase + i];
         }
       }
-      if (cur == key) {
-        found = slot;
-        break;
-      }
-      slot = (slot + 1u) & mask;
     }
-    // new keys join the list with one counter update per warp
-    const unsigned int am = __activemask();
-    const unsigned int nm = __ballot_sync(am, fresh);
-    if (nm) {
-      const int lane = threadIdx.x & 31, leader = __ffs(nm) - 1;
-      unsigned int base = 0;
-      if (lane == leader) base = atomicAdd(&st->n_unique, (unsigned int)__popc(nm));
-      base = __shfl_sync(am, base, leader);
-      if (fresh) {
-        const unsigned int at = base + __popc(nm & ((1u << lane) - 1u));
-        if (at < rs.max_unique)
-          rs.list[at] = key;
-        else
-          atomicOr(&st->hash_overflow, 1u);
+  }
+  if (probe) {
+    if (sampled) atomicAdd(&st->sampled, sampled);
+    if (pending) atomicAdd(&st->pending, pending);
+  }
+}
+
+// First-fit insert into the global pair set; returns the key's slot (and
+// *fresh when this call placed it), or 0xffffffff when the probe limit ran
+// out (the set is too small: the host retries with a larger one).
+__device__ __forceinline__ uint32_t global_insert(const RankScratch &rs, unsigned long long key,
+                                                  bool *fresh) {
+  const unsigned int mask = rs.capacity - 1u;
+  unsigned int slot = (unsigned int)mix64t(key) & mask;
+  for (unsigned int probe = 0; probe < rs.probe_limit; ++probe) {
+    unsigned long long cur = __ldcg(&rs.table_keys[slot]);
+    if (cur == ~0ull) {
+      cur = atomicCAS(&rs.table_keys[slot], ~0ull, key);
+      if (cur == ~0ull) {
+        *fresh = true;
+        return slot;
       }
     }
-    if (found == 0xffffffffu) atomicOr(&st->hash_overflow, 1u);
-    ts.pool_slot[p] = found;
-    // with a set larger than L2 the resolved pair replaces the entry's roots,
-    // so that the write kernel reads it in order instead of from the set
-    // (resolving a resolved entry again gives the same pair)
-    if (rs.capacity > kSetInL2) ts.pool_roots[p] = make_int2(a, d);
+    if (cur == key) return slot;
+    slot = (slot + 1u) & mask;
+  }
+  return 0xffffffffu;
+}
+
+// New keys join the sorted-list input with one counter update per warp.
+__device__ __forceinline__ void list_append(const RankScratch &rs, unsigned long long key, bool fresh,
+                                            uint32_t slot, DevStatus *st) {
+  const unsigned int am = __activemask();
+  const unsigned int nm = __ballot_sync(am, fresh);
+  if (nm) {
+    const int lane = threadIdx.x & 31, leader = __ffs(nm) - 1;
+    unsigned int base = 0;
+    if (lane == leader) base = atomicAdd(&st->n_unique, (unsigned int)__popc(nm));
+    base = __shfl_sync(am, base, leader);
+    if (fresh) {
+      const unsigned int at = base + __popc(nm & ((1u << lane) - 1u));
+      if (at < rs.max_unique)
+        rs.list[at] = key;
+      else
+        atomicOr(&st->hash_overflow, 1u);
+    }
+  }
+  if (slot == 0xffffffffu) atomicOr(&st->hash_overflow, 1u);
+}
+
+// Tile pairs (see launch_tile_pairs).  Per tile: each pair's (asc, desc) from
+// its two roots' labels; the tile's distinct pairs -- a few dozen where the
+// tile has about a thousand root pairs -- are found in a shared-memory set and
+// only they are inserted into the global set.  A tile with more distinct pairs
+// than the shared set holds inserts the rest directly.
+constexpr int kPairThreads = 256;
+constexpr int kPairHash = 2048;
+constexpr int kPairProbes = 64;
+
+__device__ __forceinline__ unsigned long long final_key(int key_mode, uint32_t fi, int32_t a, int32_t d) {
+  return key_mode == kKeyBatch
+             ? (((unsigned long long)fi << 48) | ((unsigned long long)(uint32_t)a << 24) | (uint32_t)d)
+             : (((unsigned long long)(uint32_t)a << 32) | (uint32_t)d);
+}
+
+__device__ __forceinline__ uint32_t smem_slot_of(unsigned long long key) {
+  return (uint32_t)(mix64t(key) & (kPairHash - 1));
+}
+
+template <bool kSingle>
+__global__ void __launch_bounds__(kPairThreads) k_tile_pairs(Batch bt, TiledScratch ts, RankScratch rs,
+                                                             DevStatus *st) {
+  if (call_failed(st) || st->not_converged) return;
+  __shared__ unsigned long long HK[kPairHash];
+  __shared__ uint32_t HS[kPairHash];
+  __shared__ long long s_next;
+  const bool keep_ad = rs.capacity > kSetInL2;
+  for (long long k = queue_first(true, ts.queue + kQPairs, &s_next); k < bt.total_tiles;
+       k = queue_next(true, k, &s_next)) {
+    queue_prefetch(true, ts.queue + kQPairs, &s_next);
+    const int64_t gt = k;
+    const TileMeta m = ts.meta[gt];
+    const uint32_t fi = kSingle ? 0u : (uint32_t)field_of(bt, gt);
+    for (int i = threadIdx.x; i < kPairHash; i += kPairThreads) HK[i] = ~0ull;
+    __syncthreads();
+    // the pair's final key, and its slot in the tile's shared set (kPairHash:
+    // not there -- inserted straight into the global set)
+    auto key_of_pair = [&](int i, int32_t *a, int32_t *d) {
+      const uint32_t pp = ts.pool_pair[m.pbase + i];
+      *a = __ldcg(&ts.root_label[m.rbase + (pp & 0xffffu)]);
+      *d = __ldcg(&ts.root_label[m.rbase + (pp >> 16)]);
+      return final_key(bt.key_mode, fi, *a, *d);
+    };
+    for (int i = threadIdx.x; i < m.npairs; i += kPairThreads) {
+      int32_t a, d;
+      const unsigned long long key = key_of_pair(i, &a, &d);
+      uint32_t s = smem_slot_of(key);
+      bool placed = false;
+      for (int probe = 0; probe < kPairProbes; ++probe) {
+        unsigned long long cur = HK[s];
+        if (cur == ~0ull) cur = atomicCAS(&HK[s], ~0ull, key);
+        if (cur == ~0ull || cur == key) {
+          placed = true;
+          break;
+        }
+        s = (s + 1) & (kPairHash - 1);
+      }
+      if (!placed) {  // the shared set is full: straight into the global set
+        bool fresh = false;
+        const uint32_t gs = global_insert(rs, key, &fresh);
+        list_append(rs, key, fresh, gs, st);
+        ts.pool_slot[m.pbase + i] = gs;
+        if (keep_ad) ts.pool_ad[m.pbase + i] = make_int2(a, d);
+      }
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < kPairHash; s += kPairThreads) {
+      const unsigned long long key = HK[s];
+      if (key != ~0ull) {
+        bool fresh = false;
+        const uint32_t gs = global_insert(rs, key, &fresh);
+        list_append(rs, key, fresh, gs, st);
+        HS[s] = gs;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m.npairs; i += kPairThreads) {
+      int32_t a, d;
+      const unsigned long long key = key_of_pair(i, &a, &d);
+      uint32_t s = smem_slot_of(key);
+      for (int probe = 0; probe < kPairProbes; ++probe) {
+        const unsigned long long cur = HK[s];
+        if (cur == key) {
+          ts.pool_slot[m.pbase + i] = HS[s];
+          if (keep_ad) ts.pool_ad[m.pbase + i] = make_int2(a, d);
+          break;
+        }
+        if (cur == ~0ull) break;  // inserted straight into the global set above
+        s = (s + 1) & (kPairHash - 1);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -1285,7 +1485,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t base = kFlat ? bt.tiles3 : 0;
   const long long count = kFlat ? bt.total_tiles - bt.tiles3 : bt.tiles3;
-  unsigned int *ctr = ts.queue + (kFlat ? 3 : 2);
+  unsigned int *ctr = ts.queue + (kFlat ? kQWrite2 : kQWrite3);
   __shared__ long long s_next;
   const bool dyn = bt.tune.dynamic != 0;
   for (long long k = queue_first(dyn, ctr, &s_next); k < count; k = queue_next(dyn, k, &s_next)) {
@@ -1314,10 +1514,11 @@ __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch 
       stride = g.nx * g.ny;
       v0 = x + g.nx * y + stride * z0;
     }
-    const long long b = ts.tile_base[gt];
-    const int cnt = ts.tile_count[gt];
+    const TileMeta &m = ts.meta[gt];
+    const unsigned long long b = m.pbase;
+    const int cnt = m.npairs;
     const uint32_t *src = ts.pool_slot + b;
-    const int2 *res = ts.pool_roots + b;  // resolved (asc, desc) of each tile pair
+    const int2 *res = ts.pool_ad + b;  // resolved (asc, desc) of each tile pair
     const bool staged = cnt <= kStageCap;
     const bool batch = bt.key_mode == kKeyBatch;
     const int first = batch ? (int)ts.fstart[fi] : 0;
@@ -1328,8 +1529,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch 
       q0 = __ldcs(pid4);
       q1 = __ldcs(pid4 + 1);
     }
-    // kInPool (a set of more than kSetInL2 entries): k_resolve_pairs left
-    // each resolved pair in its pool entry
+    // kInPool (a set of more than kSetInL2 entries): k_tile_pairs left each
+    // resolved pair in its pool entry
     auto entry = [&](int i) {
       const uint32_t sl = __ldcs(src + i);
       if (kInPool) {
@@ -1389,39 +1590,36 @@ TileGeom tile_geom(const int64_t dims[3]) {
   return g;
 }
 
-// Room for pending pairs: an eighth of the pool (more pending pairs make the
-// unbudgeted pass scan the whole pool instead).
-unsigned long long pending_cap_of(unsigned long long pool_cap) { return pool_cap / 8 + 1024; }
-
-size_t tiled_scratch_bytes(long long total_tiles, int n_fields, unsigned long long pool_cap) {
-  const size_t pid = (size_t)total_tiles * kTileV * 2;
-  const size_t face = (size_t)total_tiles * kFace * 4;
-  const size_t meta = (size_t)total_tiles * (8 + 4);
-  return 16 * 256 + pid + face + meta + (size_t)pool_cap * (8 + 4 + 4) + (size_t)n_fields * 4 +
-         (size_t)pending_cap_of(pool_cap) * 4;
+size_t tiled_scratch_bytes(long long total_tiles, int n_fields, unsigned long long pool_cap,
+                           unsigned long long root_cap) {
+  auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  return r(256) + r((size_t)pool_cap * 4) * 2 + r((size_t)pool_cap * 8) + r((size_t)root_cap * 2) +
+         r((size_t)root_cap * 4) + r((size_t)total_tiles * sizeof(TileMeta)) + r((size_t)n_fields * 4) +
+         r((size_t)total_tiles * kFace * 4) + r((size_t)total_tiles * kTileV * 2);
 }
 
 void tiled_scratch_carve(void *base, long long total_tiles, int n_fields,
-                         unsigned long long pool_cap, TiledScratch *ts) {
+                         unsigned long long pool_cap, unsigned long long root_cap,
+                         TiledScratch *ts) {
   char *p = static_cast<char *>(base);
   auto take = [&](size_t bytes) {
-    char *r = p;
+    char *q = p;
     p += (bytes + 255) & ~(size_t)255;
-    return r;
+    return q;
   };
-  ts->pool_count = reinterpret_cast<unsigned long long *>(take(256));
-  ts->queue = reinterpret_cast<unsigned int *>(ts->pool_count + 1);
+  ts->counters = reinterpret_cast<unsigned long long *>(take(256));
+  ts->queue = reinterpret_cast<unsigned int *>(ts->counters + 2);
+  ts->pool_pair = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
   ts->pool_slot = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
-  ts->pending_cap = pending_cap_of(pool_cap);
-  ts->pending_list = reinterpret_cast<uint32_t *>(take((size_t)ts->pending_cap * 4));
-  ts->pool_roots = reinterpret_cast<int2 *>(take((size_t)pool_cap * 8));
-  ts->pool_field = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
-  ts->tile_base = reinterpret_cast<long long *>(take((size_t)total_tiles * 8));
-  ts->tile_count = reinterpret_cast<int32_t *>(take((size_t)total_tiles * 4));
+  ts->pool_ad = reinterpret_cast<int2 *>(take((size_t)pool_cap * 8));
+  ts->root_box = reinterpret_cast<uint16_t *>(take((size_t)root_cap * 2));
+  ts->root_label = reinterpret_cast<int32_t *>(take((size_t)root_cap * 4));
+  ts->meta = reinterpret_cast<TileMeta *>(take((size_t)total_tiles * sizeof(TileMeta)));
+  ts->fstart = reinterpret_cast<uint32_t *>(take((size_t)n_fields * 4));
   ts->face = reinterpret_cast<uint32_t *>(take((size_t)total_tiles * kFace * 4));
   ts->pid = reinterpret_cast<uint16_t *>(take((size_t)total_tiles * kTileV * 2));
-  ts->fstart = reinterpret_cast<uint32_t *>(take((size_t)n_fields * 4));
   ts->pool_cap = pool_cap;
+  ts->root_cap = root_cap;
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -1495,10 +1693,9 @@ bool capturing(cudaStream_t s) {
 
 cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus *st,
                               cudaStream_t s) {
-  // the pool counter and the four work-queue counters after it
-  cudaError_t e = cudaMemsetAsync(ts.pool_count, 0, sizeof(unsigned long long) + 4 * sizeof(unsigned int), s);
+  // the pool and root counters and the work-queue counters after them
+  cudaError_t e = cudaMemsetAsync(ts.counters, 0, 2 * sizeof(unsigned long long) + kQueues * sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  static_assert(kHash <= kExt, "the pair set reuses the key area");
   if (b.tiles3 > 0) {
     constexpr int kSmem = 2 * kExt * 4;
     auto kern = b.n_fields == 1 ? k_tile_local<true> : k_tile_local<false>;
@@ -1513,7 +1710,7 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
     if (e != cudaSuccess) return e;
   }
   if (b.total_tiles > b.tiles3) {
-    constexpr int kSmem2 = (k2Ext + k2PArea) * 4;
+    constexpr int kSmem2 = (k2KArea + k2PArea) * 4;
     auto kern = b.n_fields == 1 ? k_tile_local2<true> : k_tile_local2<false>;
     if (!capturing(s)) {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem2);
@@ -1527,23 +1724,36 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
   return e;
 }
 
-cudaError_t launch_resolve_pairs(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
-                                 unsigned long long npairs, int mode, const int2 *graph,
-                                 unsigned long long stride, bool clear_table, DevStatus *st,
-                                 cudaStream_t s) {
-  cudaError_t e = cudaSuccess;
-  if (clear_table) e = cudaMemsetAsync(rs.table_keys, 0xff, (size_t)rs.capacity * 8, s);
-  if (e != cudaSuccess || npairs == 0) return e;
-  if (stride == 0) stride = 1;
-  const unsigned long long work = mode == kChaseProbe ? (npairs + stride - 1) / stride : npairs;
-  unsigned long long blocks = (work + 255) / 256;
-  const unsigned long long cap = (unsigned long long)sms() * b.tune.resolve_blocks;
-  if (blocks > cap) blocks = cap;
+cudaError_t launch_chase_roots(const Batch &b, const TiledScratch &ts, const int2 *graph,
+                               long long probe_stride, DevStatus *st, cudaStream_t s) {
+  const long long tiles = probe_stride > 0 ? (b.total_tiles + probe_stride - 1) / probe_stride
+                                           : b.total_tiles;
+  if (tiles == 0) return cudaSuccess;
+  const cudaError_t e = cudaMemsetAsync(ts.queue + kQChase, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  constexpr int kWarps = kChaseThreads / 32;
+  const long long blocks =
+      std::min<long long>((long long)sms() * b.tune.chase_blocks, (tiles + kWarps - 1) / kWarps);
   ++tl_launches;
   if (b.n_fields == 1)
-    k_resolve_pairs<true><<<(unsigned)blocks, 256, 0, s>>>(b, ts, rs, mode, graph, stride, st);
+    k_chase_roots<true><<<(unsigned)blocks, kChaseThreads, 0, s>>>(b, ts, graph, probe_stride, st);
   else
-    k_resolve_pairs<false><<<(unsigned)blocks, 256, 0, s>>>(b, ts, rs, mode, graph, stride, st);
+    k_chase_roots<false><<<(unsigned)blocks, kChaseThreads, 0, s>>>(b, ts, graph, probe_stride, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_pairs(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
+                              bool clear_table, DevStatus *st, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (clear_table) e = cudaMemsetAsync(rs.table_keys, 0xff, (size_t)rs.capacity * 8, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ts.queue + kQPairs, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess || b.total_tiles == 0) return e;
+  const long long blocks = std::min<long long>(b.total_tiles, (long long)sms() * b.tune.pair_blocks);
+  ++tl_launches;
+  if (b.n_fields == 1)
+    k_tile_pairs<true><<<(unsigned)blocks, kPairThreads, 0, s>>>(b, ts, rs, st);
+  else
+    k_tile_pairs<false><<<(unsigned)blocks, kPairThreads, 0, s>>>(b, ts, rs, st);
   return cudaGetLastError();
 }
 

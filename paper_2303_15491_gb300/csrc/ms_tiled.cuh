@@ -37,19 +37,26 @@ constexpr int k2EX = k2TX + 2 * kXO, k2EY = k2TY + 2;    // 136 x 66
 constexpr int k2Ext = k2EX * k2EY;                       // 8976
 constexpr int k2Face = 2 * (k2TX + k2TY);                // face-root slots of a 2D tile
 constexpr int kRun = 16;                                 // vertices per thread, both shapes
-// The pointer area holds the extended box and, later, the candidate list and
-// its 16-bit slots.
-constexpr int k2PArea = k2Ext > kTileV + kTileV / 2 ? k2Ext : kTileV + kTileV / 2;
+// Words of the root bitmaps over a tile shape's extended box.
+constexpr int kBmW3 = (kExt + 31) / 32;
+constexpr int kBmW2 = (k2Ext + 31) / 32;
+// Shared-memory areas of a 2D tile: the value area holds the extended box
+// and, once the steepest step is done, the pair list and the root bitmaps;
+// the pointer area holds the pointers and, once they are final, the pair set
+// and its dense numbers.
+constexpr int k2KArea = k2Ext > kTileV + 4 * kBmW2 ? k2Ext : kTileV + 4 * kBmW2;
+constexpr int k2PArea = k2Ext > kHash + kHash / 2 ? k2Ext : kHash + kHash / 2;
 
 static_assert(k2TX * k2TY == kTileV, "2D tiles hold as many vertices as 3D tiles");
 static_assert(k2TX * k2TY == kThreads * kRun && kTZ == kRun, "one run of 16 per thread");
 static_assert(k2Face <= kFace, "the face array has kFace slots per tile");
-static_assert(kHash <= k2Ext, "the 2D pair set fits the key area");
 static_assert(kExt < 65536, "extended-box indices must fit 16 bits");
+static_assert(2 * kExt < 65536, "root-list indices (dn roots, then up roots) fit 16 bits");
 static_assert(kHash >= kTileV, "pair table must hold one pair per vertex");
-static_assert(kHash <= kExt, "the pair set fits the key area");
 static_assert((kTX + 1) * (kTY + 1) * (kTZ + 1) <= kExt, "cube extrema fit the pointer area");
-static_assert(kTileV + kTileV / 2 <= kExt, "candidates (later the pair list) and their 16-bit slots fit the pointer area");
+static_assert(kHash + kHash / 2 <= kExt, "pair set and dense numbers fit the 3D value area");
+static_assert(kTileV + 4 * kBmW3 <= kExt, "pair list and root bitmaps fit the 3D pointer area");
+static_assert((k2KArea * 4) % 16 == 0, "the 2D pointer area starts 16-byte aligned");
 
 struct TileGeom {
   int64_t nx, ny, nz;
@@ -77,11 +84,11 @@ constexpr int kBatchMaxFields = 1 << 16;
 // Launch choices that change only scheduling, never results (picked by the
 // batch autotuner; the defaults are the single-field choices).
 struct Tuning {
-  int tile_ctas = 2;       // tile kernels: CTAs per SM (2 fit an SM)
-  int write_ctas = 4;      // write kernels: CTAs per SM
-  int resolve_blocks = 16;  // resolve: 256-thread blocks per SM
-  int chase_hops = 16;     // budget of the first exit-chasing pass
-  int dynamic = 1;         // tiles from a work queue (1) or a static stride (0)
+  int tile_ctas = 2;     // tile kernels: CTAs per SM (2 fit an SM)
+  int write_ctas = 4;    // write kernels: CTAs per SM
+  int chase_blocks = 8;  // root chase: 256-thread blocks (8 warps) per SM
+  int pair_blocks = 6;   // tile pairs: 256-thread blocks per SM
+  int dynamic = 1;       // tile and write kernels: a work queue (1) or a static stride (0)
 };
 
 struct Batch {
@@ -95,53 +102,69 @@ struct Batch {
   Tuning tune;
 };
 
-struct TiledScratch {
-  unsigned long long *pool_count;  // pairs reserved by all tiles
-  unsigned int *queue;             // work-queue counters: tile 3D, tile 2D, write 3D, write 2D
-  unsigned long long pool_cap;
-  int2 *pool_roots;   // per tile pair: (dn-root, up-root), global index | kExitFlag if an exit;
-                      // the resolved pair once resolved, if the set exceeds kSetInL2 entries
-  uint32_t *pool_field;  // per tile pair: its field
-  uint32_t *fstart;      // per field: index of its first pair in the sorted pair list
-  uint32_t *pool_slot;  // per tile pair: slot of its (asc, desc) pair in the global pair set
-  uint32_t *pending_list;  // tile pairs left by the budgeted chase (up to pending_cap)
-  unsigned long long pending_cap;
-  long long *tile_base;
-  int32_t *tile_count;
-  uint32_t *face;     // per tile kFace words: up-root | dn-root << 16 (extended-box indices)
-  uint16_t *pid;      // per tile kTileV pair numbers; the 16 of column (lx, ly) are contiguous
+// Per-tile record of the tile pass: where the tile's pairs and roots start in
+// the pair pool and the root list, and how many there are.
+struct TileMeta {
+  unsigned long long pbase;  // first pair-pool entry
+  unsigned long long rbase;  // first root-list entry
+  int npairs;                // distinct (dn-root, up-root) pairs of the tile
+  int nd, nu;                // distinct dn roots, up roots (the root list holds dn, then up)
+  int pad;
 };
 
+struct TiledScratch {
+  unsigned long long *counters;  // [0] pairs reserved by all tiles, [1] roots
+  unsigned int *queue;           // work-queue counters (kQueues)
+  unsigned long long pool_cap;   // pair-pool entries
+  unsigned long long root_cap;   // root-list entries
+  uint32_t *pool_pair;  // per tile pair: dn-root index | up-root index << 16 (in the tile's root list)
+  uint32_t *pool_slot;  // per tile pair: slot of its (asc, desc) pair in the global pair set
+  int2 *pool_ad;        // per tile pair: its (asc, desc), kept when the set exceeds kSetInL2 entries
+  uint16_t *root_box;   // per tile root: its extended-box index
+  int32_t *root_label;  // per tile root: the extremum its path reaches
+  TileMeta *meta;       // per tile
+  uint32_t *fstart;     // per field: index of its first pair in the sorted pair list
+  uint32_t *face;       // per tile kFace words: up-root | dn-root << 16 (extended-box indices)
+  uint16_t *pid;        // per tile kTileV pair numbers; the 16 of a thread's run are contiguous
+};
+// Work-queue counters: tile pass 3D / 2D, write 3D / 2D, root chase, tile pairs.
+enum { kQTile3 = 0, kQTile2 = 1, kQWrite3 = 2, kQWrite2 = 3, kQChase = 4, kQPairs = 5, kQueues = 8 };
+
 TileGeom tile_geom(const int64_t dims[3]);
-size_t tiled_scratch_bytes(long long total_tiles, int n_fields, unsigned long long pool_cap);
+size_t tiled_scratch_bytes(long long total_tiles, int n_fields, unsigned long long pool_cap,
+                           unsigned long long root_cap);
 void tiled_scratch_carve(void *base, long long total_tiles, int n_fields,
-                         unsigned long long pool_cap, TiledScratch *ts);
+                         unsigned long long pool_cap, unsigned long long root_cap,
+                         TiledScratch *ts);
 // Host side of a field descriptor (and its tensor map when TMA applies).
 void make_field_desc(const void *field, int dtype, const int64_t dims[3], long long tile_base,
                      int32_t *asc, int32_t *desc, int32_t *ms, bool allow_tma, FieldDesc *fd,
                      CUtensorMap *map);
+// Tile pass: steepest neighbours, in-tile compression, the tile's distinct
+// roots and pairs (counters[0] / [1] hold the pool and root-list totals).
 cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus *st,
                               cudaStream_t s);
-// Exit resolution.  kChaseProbe chases the exits of a strided sample of the
-// tile pairs (every `stride`-th) for at most kProbeHops face hops and only
-// counts, in st->pending, the sampled pairs that need more: it decides
-// between the two ways below.  kChaseBudget follows every pair's exits for at
-// most Tuning::chase_hops hops, inserts the finished pairs and marks the others
-// pending; kChasePending follows the pending pairs without a budget.
-// kChaseGraph resolves every pair through the jumped face graph
-// (launch_face_graph_*).  clear_table: reset the pair set first.
-enum { kChaseProbe = 0, kChaseBudget = 1, kChasePending = 2, kChaseGraph = 3 };
-// Pair sets of more entries than this (12 bytes each: beyond about a third of
-// L2) are read in random order from DRAM; then k_resolve_pairs stores each
-// resolved pair over its pool entry's roots and k_tile_write reads it there.
-constexpr unsigned int kSetInL2 = 1u << 22;
+// Root chase: every tile root is followed from face to face (or looked up in
+// the jumped face graph when `graph` is given) to the extremum it leads to.
+// Probe form (probe_stride > 0): only every probe_stride-th tile, at most
+// kProbeHops hops a root, counting in st->pending the roots that need more
+// and in st->n_max the roots sampled; no labels are stored.
 constexpr int kProbeHops = 4;
-// The probe samples about kProbeSample pairs, when there are kProbeMinPairs.
-constexpr unsigned long long kProbeSample = 16384, kProbeMinPairs = 65536;
-cudaError_t launch_resolve_pairs(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
-                                 unsigned long long npairs, int mode, const int2 *graph,
-                                 unsigned long long stride, bool clear_table, DevStatus *st,
-                                 cudaStream_t s);
+// The probe runs when a call has at least kProbeMinRoots roots, on about
+// kProbeTiles tiles.
+constexpr unsigned long long kProbeMinRoots = 65536;
+constexpr long long kProbeTiles = 512;
+cudaError_t launch_chase_roots(const Batch &b, const TiledScratch &ts, const int2 *graph,
+                               long long probe_stride, DevStatus *st, cudaStream_t s);
+// Tile pairs: each tile pair's (asc, desc) from its roots' labels, the tile's
+// distinct pairs inserted into the global pair set (clear_table: reset it
+// first), each tile pair's set slot stored.
+// Pair sets of more entries than this (12 bytes each: beyond about a third of
+// L2) are read in random order from DRAM; then the tile pairs also keep their
+// (asc, desc) for the write kernel to read in order.
+constexpr unsigned int kSetInL2 = 1u << 22;
+cudaError_t launch_tile_pairs(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
+                              bool clear_table, DevStatus *st, cudaStream_t s);
 
 // The face graph: per face slot of every tile (kFace slots per tile, 3D
 // tiles first) the up and dn successor -- the global slot of the next face
