@@ -168,8 +168,8 @@ ms_status ms_pair_rank(ms_ctx *ctx, const int32_t *asc, const int32_t *desc, int
 typedef struct {
   int tile_ctas;      /* tile kernels: CTAs per SM (1 or 2) */
   int write_ctas;     /* label-writing kernels: CTAs per SM */
-  int chase_blocks;   /* root chase: 256-thread blocks (warps take tiles) per SM */
-  int pair_blocks;    /* tile pairs: 256-thread blocks (one tile each) per SM */
+  int chase_blocks;   /* root chase: 512-thread blocks (warps take tiles) per SM */
+  int pair_blocks;    /* tile pairs: 256-thread blocks (one tile a warp) per SM */
   int dynamic;        /* 1: tiles taken from a work queue; 0: static stride */
   double default_ms;  /* ms_batch_autotune: time of the default choices */
   double best_ms;     /* ms_batch_autotune: time of the chosen ones */

@@ -485,6 +485,7 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
     s = read_status(c);
     if (s != MS_OK) return s;
     if (c->hst->not_converged) return MS_ERR_NOT_CONVERGED;
+    if (c->hst->bad_index) return MS_ERR_CUDA;  // a chase or a pair out of its tile: cannot happen
     if (!c->hst->hash_overflow) break;
     if (want >= exact) return MS_ERR_CUDA;  // cannot happen: the exact bound always fits
     want = exact;
@@ -1139,8 +1140,8 @@ ms_status ms_batch_autotune(ms_ctx *c, int n_fields, const void *const *fields,
   const Knob knobs[] = {{&Tuning::dynamic, {1, 0}},
                         {&Tuning::tile_ctas, {2, 1}},
                         {&Tuning::write_ctas, {2, 4, 8}},
-                        {&Tuning::chase_blocks, {8, 4, 16}},
-                        {&Tuning::pair_blocks, {6, 3, 8}}};
+                        {&Tuning::chase_blocks, {3, 2}},
+                        {&Tuning::pair_blocks, {4, 3}}};
   for (const Knob &kn : knobs) {
     if (s != MS_OK) break;
     const int start = best.*(kn.field);

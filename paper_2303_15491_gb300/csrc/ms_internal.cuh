@@ -79,9 +79,9 @@ struct RankScratch {
   unsigned int probe_limit;        // longest insert probe before the set counts as full
   unsigned int sort_blocks_cap;    // most blocks a sort pass may use
 };
-// Sort passes over up to 2^22 keys use at most kSortBlocks blocks, each
-// computing its digit offsets from the raw histogram; larger sorts use more
-// blocks and a separate scan of the histogram.
+// Sort passes over up to 2^16 keys use at most kSortBlocks blocks, each
+// computing its digit offsets from the raw histogram; larger sorts use
+// 2048-key blocks and a separate scan of the histogram.
 constexpr int kSortBlocks = 240;
 // Insert probes allowed when the set was sized from an estimate: at a load
 // factor of at most one half such a run essentially never happens, and a

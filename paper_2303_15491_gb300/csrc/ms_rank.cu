@@ -129,6 +129,8 @@ __global__ void k_radix_hist(const unsigned long long *__restrict__ in, unsigned
 constexpr int kScanThreads = 1024;
 constexpr int kScanChunk = kScanThreads * 8;
 constexpr int kScanMaxChunks = 256;  // rank scratch keeps this many chunk sums
+// Sorts of more keys than this use 2048-key blocks and the scan launches.
+constexpr unsigned int kSortScanFrom = 1u << 16;
 
 __device__ __forceinline__ void load8(const unsigned int *p, unsigned int i0, unsigned int n,
                                       unsigned int (&v)[8]) {
@@ -383,10 +385,11 @@ cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bit
   const int total = raw_bits > 0 ? raw_bits : 2 * key_bits;
   // small sorts: enough blocks to spread the keys, few enough that each
   // block's offset computation (a pass over its digit's row) stays small;
-  // large ones: 2048 keys a block (up to 8 blocks an SM) and a scan launch
+  // larger ones: 2048 keys a block (up to 8 blocks an SM) and the histogram
+  // scanned by two launches (a block with 4096 or more keys walks them 256 at
+  // a time, three barriers each: at 350K keys, 85 blocks took 33 us a pass)
   unsigned int blocks = std::max(1u, std::min((unsigned)kSortBlocks, (m + 4095) / 4096));
-  // (the scan launch pays off only when there are many more keys than 240 blocks hold)
-  const bool large = m > (1u << 22) && rs.sort_blocks_cap > (unsigned)kSortBlocks;
+  const bool large = m > kSortScanFrom;
   if (large)
     blocks = std::max(1u, std::min({rs.sort_blocks_cap, (m + 2047) / 2048,
                                     (unsigned)sm_count() * 8}));

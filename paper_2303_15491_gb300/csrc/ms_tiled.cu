@@ -265,11 +265,10 @@ __device__ __forceinline__ void wait_box(uint64_t *bar, uint32_t parity, DevStat
   }
 }
 
-// Two pointer jumps of a packed (up | dn << 16) entry through the pointer
-// area: up of up's up, dn of dn's dn (Sec. 4.2.1 second step).
-__device__ __forceinline__ uint32_t jump2(const uint32_t *P, uint32_t x) {
-  const uint32_t g1 = __byte_perm(P[x & 0xffffu], P[x >> 16], 0x7610);  // up of up, dn of dn
-  return __byte_perm(P[g1 & 0xffffu], P[g1 >> 16], 0x7610);
+// One pointer jump of a packed (up | dn << 16) entry through the pointer
+// area: up of its up, dn of its dn (Sec. 4.2.1 second step).
+__device__ __forceinline__ uint32_t jump1(const uint32_t *P, uint32_t x) {
+  return __byte_perm(P[x & 0xffffu], P[x >> 16], 0x7610);
 }
 
 // Comparisons of staged values.  Interior tiles (tile and halo inside the
@@ -772,11 +771,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
     {
       uint32_t open = 0xffffu;
       for (int it = 0; it < kExt; ++it) {
+        // the entries still open in some lane of the warp (one reduction a pass)
+        const uint32_t rows = __reduce_or_sync(0xffffffffu, open);
+        if (!rows) break;
         uint32_t still = 0;
 #pragma unroll
         for (int lz = 0; lz < kTZ; ++lz) {
-          if (__any_sync(0xffffffffu, (open >> lz) & 1u)) {
-            const uint32_t nw = jump2(P, w[lz]);
+          if ((rows >> lz) & 1u) {
+            const uint32_t nw = jump1(P, w[lz]);
             if (nw != w[lz]) {
               w[lz] = nw;
               P[ext_of(lx, ly, lz)] = nw;
@@ -785,7 +787,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
           }
         }
         open = still;
-        if (!__any_sync(0xffffffffu, still)) break;
       }
     }
     __syncthreads();
@@ -956,18 +957,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScra
     __syncthreads();
 
     // in-place pointer jumping, as in the 3D tiles
-    for (int it = 0; it < k2Ext; ++it) {
-      bool changed = false;
+    {
+      uint32_t open = 0xffffu;
+      for (int it = 0; it < k2Ext; ++it) {
+        const uint32_t rows = __reduce_or_sync(0xffffffffu, open);
+        if (!rows) break;
+        uint32_t still = 0;
 #pragma unroll
-      for (int j = 0; j < kRun; ++j) {
-        const uint32_t nw = jump2(P, w[j]);
-        if (nw != w[j]) {
-          w[j] = nw;
-          P[ext2_of(cx, cy0 + j)] = nw;
-          changed = true;
+        for (int j = 0; j < kRun; ++j) {
+          if ((rows >> j) & 1u) {
+            const uint32_t nw = jump1(P, w[j]);
+            if (nw != w[j]) {
+              w[j] = nw;
+              P[ext2_of(cx, cy0 + j)] = nw;
+              still |= 1u << j;
+            }
+          }
         }
+        open = still;
       }
-      if (!__any_sync(0xffffffffu, changed)) break;
     }
     __syncthreads();
 
@@ -1131,135 +1139,83 @@ __device__ __forceinline__ bool call_failed(const DevStatus *st) {
   return (st->pool_overflow | st->nan_flag | st->timeout | st->bad_index) != 0u;
 }
 
-// One step of a root's chase.  The chase stands at box index e of tile
-// (tx, ty, tz) of its field, following dn pointers (asc, toward a minimum) or
-// up pointers.  If e lies inside the tile it is the extremum: *label is set
-// and true returned.  Otherwise e is a vertex of a neighbouring tile, on that
-// tile's face; the chase moves there and reads that vertex's tile root from
-// the face array (one dependent load).  Every hop lands on a later vertex of
-// the same strictly monotone integral line, so a chase ends.
-struct Chase {
-  uint32_t e;
-  int tx, ty, tz;
-};
+// Decoding table of the root chase: for every extended-box index of a tile
+// shape, either its tile coordinates (a vertex inside the tile: the chase
+// ends there) or, for a halo vertex, the direction of the neighbouring tile
+// that holds it and its slot in that tile's face array.  Built once per
+// block; a hop is then one table read and one face read.
+//   inside:  bits 0-6 lx, 7-12 ly, 13-17 lz
+//   halo:    bit 31, bits 0-11 face slot, 12-13 dx + 1, 14-15 dy + 1, 16-17 dz + 1
+constexpr uint32_t kHaloBit = 0x80000000u;
 
-__device__ __forceinline__ bool chase_step3(const TileGeom &g, const uint32_t *__restrict__ face,
-                                            bool up, Chase *c, int32_t *label) {
-  const uint32_t ez = c->e / (uint32_t)(kEX * kEY), r = c->e - ez * (uint32_t)(kEX * kEY);
-  const uint32_t ey = r / (uint32_t)kEX, ex = r - ey * (uint32_t)kEX;
-  int lx = (int)ex - kXO, ly = (int)ey - 1, lz = (int)ez - 1;
-  const int dx = lx < 0 ? -1 : (lx >= kTX ? 1 : 0);
-  const int dy = ly < 0 ? -1 : (ly >= kTY ? 1 : 0);
-  const int dz = lz < 0 ? -1 : (lz >= kTZ ? 1 : 0);
-  if ((dx | dy | dz) == 0) {
-    *label = (int32_t)((uint32_t)(c->tx * kTX + lx) +
-                       (uint32_t)g.nx * ((uint32_t)(c->ty * kTY + ly) + (uint32_t)g.ny * (uint32_t)(c->tz * kTZ + lz)));
-    return true;
-  }
-  c->tx += dx, c->ty += dy, c->tz += dz;
-  lx -= dx * kTX, ly -= dy * kTY, lz -= dz * kTZ;
-  const uint32_t tile = (uint32_t)c->tx + (uint32_t)g.tx * ((uint32_t)c->ty + (uint32_t)g.ty * (uint32_t)c->tz);
-  const uint32_t w = __ldg(&face[(size_t)tile * kFace + face_slot(lx, ly, lz)]);
-  c->e = up ? (w & 0xffffu) : (w >> 16);
-  return false;
-}
-
-__device__ __forceinline__ bool chase_step2(const TileGeom &g, const uint32_t *__restrict__ face,
-                                            bool up, Chase *c, int32_t *label) {
-  const uint32_t ey = c->e / (uint32_t)k2EX, ex = c->e - ey * (uint32_t)k2EX;
-  int lx = (int)ex - kXO, ly = (int)ey - 1;
-  const int dx = lx < 0 ? -1 : (lx >= k2TX ? 1 : 0);
-  const int dy = ly < 0 ? -1 : (ly >= k2TY ? 1 : 0);
-  if ((dx | dy) == 0) {
-    *label = (int32_t)((uint32_t)(c->tx * k2TX + lx) + (uint32_t)g.nx * (uint32_t)(c->ty * k2TY + ly));
-    return true;
-  }
-  c->tx += dx, c->ty += dy;
-  lx -= dx * k2TX, ly -= dy * k2TY;
-  const uint32_t tile = (uint32_t)c->tx + (uint32_t)g.tx * (uint32_t)c->ty;
-  const uint32_t w = __ldg(&face[(size_t)tile * kFace + face_slot2(lx, ly)]);
-  c->e = up ? (w & 0xffffu) : (w >> 16);
-  return false;
-}
-
-// The label of a chase standing inside its tile (an extremum), if it does.
-__device__ __forceinline__ bool interior_label(const TileGeom &g, const Chase &c, int32_t *label) {
-  if (g.flat) {
-    const uint32_t ey = c.e / (uint32_t)k2EX, ex = c.e - ey * (uint32_t)k2EX;
-    const int lx = (int)ex - kXO, ly = (int)ey - 1;
-    if (lx < 0 || lx >= k2TX || ly < 0 || ly >= k2TY) return false;
-    *label = (int32_t)((uint32_t)(c.tx * k2TX + lx) + (uint32_t)g.nx * (uint32_t)(c.ty * k2TY + ly));
-    return true;
-  }
-  const uint32_t ez = c.e / (uint32_t)(kEX * kEY), r = c.e - ez * (uint32_t)(kEX * kEY);
-  const uint32_t ey = r / (uint32_t)kEX, ex = r - ey * (uint32_t)kEX;
-  const int lx = (int)ex - kXO, ly = (int)ey - 1, lz = (int)ez - 1;
-  if (lx < 0 || lx >= kTX || ly < 0 || ly >= kTY || lz < 0 || lz >= kTZ) return false;
-  *label = (int32_t)((uint32_t)(c.tx * kTX + lx) +
-                     (uint32_t)g.nx * ((uint32_t)(c.ty * kTY + ly) + (uint32_t)g.ny * (uint32_t)(c.tz * kTZ + lz)));
-  return true;
-}
-
-// The jumped face graph's answer for a chase standing on a halo vertex: the
-// extremum the neighbouring tile's face vertex leads to.
-__device__ __forceinline__ int32_t graph_label(const TileGeom &g, long long tile_base,
-                                               const int2 *__restrict__ graph, bool up, const Chase &c,
-                                               DevStatus *st) {
-  int tx = c.tx, ty = c.ty, tz = c.tz, fs;
-  if (g.flat) {
-    const uint32_t ey = c.e / (uint32_t)k2EX, ex = c.e - ey * (uint32_t)k2EX;
-    int lx = (int)ex - kXO, ly = (int)ey - 1;
-    const int dx = lx < 0 ? -1 : (lx >= k2TX ? 1 : 0), dy = ly < 0 ? -1 : (ly >= k2TY ? 1 : 0);
-    tx += dx, ty += dy;
-    fs = face_slot2(lx - dx * k2TX, ly - dy * k2TY);
+template <bool kFlat>
+__device__ __forceinline__ uint32_t chase_code(int e) {
+  int lx, ly, lz = 0;
+  if (kFlat) {
+    const int ey = e / k2EX;
+    lx = e - ey * k2EX - kXO, ly = ey - 1;
   } else {
-    const uint32_t ez = c.e / (uint32_t)(kEX * kEY), r = c.e - ez * (uint32_t)(kEX * kEY);
-    const uint32_t ey = r / (uint32_t)kEX, ex = r - ey * (uint32_t)kEX;
-    int lx = (int)ex - kXO, ly = (int)ey - 1, lz = (int)ez - 1;
-    const int dx = lx < 0 ? -1 : (lx >= kTX ? 1 : 0), dy = ly < 0 ? -1 : (ly >= kTY ? 1 : 0),
-              dz = lz < 0 ? -1 : (lz >= kTZ ? 1 : 0);
-    tx += dx, ty += dy, tz += dz;
-    fs = face_slot(lx - dx * kTX, ly - dy * kTY, lz - dz * kTZ);
+    const int ez = e / (kEX * kEY), r = e - ez * (kEX * kEY), ey = r / kEX;
+    lx = r - ey * kEX - kXO, ly = ey - 1, lz = ez - 1;
   }
-  const long long tile = tile_base + tx + g.tx * (ty + g.ty * (long long)tz);
-  const int2 e = graph[tile * kFace + fs];
-  const uint32_t f = (uint32_t)(up ? e.x : e.y);
-  if (!(f & kSlotFinal)) atomicOr(&st->not_converged, 1u);
-  return (int32_t)(f & ~kSlotFinal);
+  constexpr int TX = kFlat ? k2TX : kTX, TY = kFlat ? k2TY : kTY, TZ = kFlat ? 1 : kTZ;
+  const int dx = lx < 0 ? -1 : (lx >= TX ? 1 : 0);
+  const int dy = ly < 0 ? -1 : (ly >= TY ? 1 : 0);
+  const int dz = kFlat ? 0 : (lz < 0 ? -1 : (lz >= TZ ? 1 : 0));
+  if ((dx | dy | dz) == 0) return (uint32_t)lx | ((uint32_t)ly << 7) | ((uint32_t)lz << 13);
+  if (lx < -1 || lx > TX) return kHaloBit;  // a padding column: never a root
+  const int fs = kFlat ? face_slot2(lx - dx * TX, ly - dy * TY)
+                       : face_slot(lx - dx * TX, ly - dy * TY, lz - dz * TZ);
+  return kHaloBit | (uint32_t)fs | ((uint32_t)(dx + 1) << 12) | ((uint32_t)(dy + 1) << 14) |
+         ((uint32_t)(dz + 1) << 16);
 }
 
 // Root chase (see launch_chase_roots).  A warp takes one tile at a time from
 // a work queue; its lanes take the tile's roots in turn (lane l roots l,
-// l + 32, ...) and each lane moves on to its next root as soon as one ends,
-// so one long chain holds up no other lane.
-constexpr int kChaseThreads = 256;
+// l + 32, ...).  Each hop of a chase is one dependent load, so every lane
+// keeps kInFlight chases going at once, and a lane whose chase ends starts
+// its next root in that place: one long chain holds up no other chase.
+// kFlat: the 2D tiles (which follow the 3D ones).
+constexpr int kChaseThreads = 512;
+constexpr int kInFlight = 4;
 
-template <bool kSingle>
+template <bool kFlat, bool kSingle>
 __global__ void __launch_bounds__(kChaseThreads) k_chase_roots(Batch bt, TiledScratch ts,
                                                                const int2 *__restrict__ graph,
                                                                long long probe_stride,
                                                                DevStatus *st) {
   if (call_failed(st)) return;
+  extern __shared__ uint32_t LUT[];
+  constexpr int kE = kFlat ? k2Ext : kExt;
+  constexpr int TX = kFlat ? k2TX : kTX, TY = kFlat ? k2TY : kTY, TZ = kFlat ? 1 : kTZ;
+  constexpr int kFaceN = kFlat ? k2Face : kFace;
+  for (int e = threadIdx.x; e < kE; e += kChaseThreads) LUT[e] = chase_code<kFlat>(e);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const bool probe = probe_stride > 0;
-  const long long nwork = probe ? (bt.total_tiles + probe_stride - 1) / probe_stride : bt.total_tiles;
-  unsigned int sampled = 0, pending = 0;
+  const long long t0 = kFlat ? bt.tiles3 : 0;
+  const long long ntiles = kFlat ? bt.total_tiles - bt.tiles3 : bt.tiles3;
+  const long long nwork = probe ? (ntiles + probe_stride - 1) / probe_stride : ntiles;
+  unsigned int *ctr = ts.queue + (kFlat ? kQChase2 : kQChase);
+  unsigned int sampled = 0, pending = 0, bad = 0;
   for (;;) {
     long long k = 0;
-    if (lane == 0) k = (long long)atomicAdd(ts.queue + kQChase, 1u);
+    if (lane == 0) k = (long long)atomicAdd(ctr, 1u);
     k = __shfl_sync(0xffffffffu, k, 0);
     if (k >= nwork) break;
-    const int64_t gt = probe ? k * probe_stride : k;
+    const int64_t gt = t0 + (probe ? k * probe_stride : k);
     const TileMeta m = ts.meta[gt];
     const int fi = kSingle ? 0 : field_of(bt, gt);
     const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
     const TileGeom &g = fd.g;
     const uint32_t *__restrict__ face = ts.face + fd.tile_base * (long long)kFace;
+    const int gtx = (int)g.tx, gty = (int)g.ty, gtz = (int)g.tz;
+    const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
     int tx0, ty0, tz0 = 0;
     {
       const int64_t tile = gt - fd.tile_base;
       uint32_t r, tx, ty, tz = 0;
-      if (g.flat) {
+      if (kFlat) {
         g.div_tx.divmod((uint32_t)tile, &ty, &tx);
       } else {
         g.div_tx.divmod((uint32_t)tile, &r, &tx);
@@ -1269,49 +1225,84 @@ __global__ void __launch_bounds__(kChaseThreads) k_chase_roots(Batch bt, TiledSc
     }
     const int nr = m.nd + m.nu;
     const int64_t n = g.nx * g.ny * g.nz;
-    const int64_t slots = g.ntiles * (int64_t)kFace;
-    const int64_t max_hops = probe ? kProbeHops : (n < slots ? n : slots);
-    int i = lane;
-    bool have = i < nr;
-    Chase c{0u, tx0, ty0, tz0};
-    int64_t hops = 0;
-    if (have) c.e = ts.root_box[m.rbase + i];
-    while (__any_sync(0xffffffffu, have)) {
-      if (have) {
-        const bool up = i >= m.nd;
+    const int64_t slots = g.ntiles * (int64_t)kFaceN;
+    const int max_hops = probe ? kProbeHops : (int)(n < slots ? n : slots);
+    const uint16_t *__restrict__ rb = ts.root_box + m.rbase;
+    int32_t *__restrict__ rl = ts.root_label + m.rbase;
+    uint32_t e[kInFlight];
+    int tx[kInFlight], ty[kInFlight], tz[kInFlight], idx[kInFlight], hops[kInFlight];
+    int next = lane + 32 * kInFlight;  // this lane's next root to start
+    uint32_t nb = next < nr ? (uint32_t)rb[next] : 0u;  // its box index, loaded ahead
+#pragma unroll
+    for (int q = 0; q < kInFlight; ++q) {
+      idx[q] = lane + 32 * q;
+      hops[q] = 0;
+      tx[q] = tx0, ty[q] = ty0, tz[q] = tz0;
+      e[q] = idx[q] < nr ? (uint32_t)rb[idx[q]] : 0u;
+    }
+    for (;;) {
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < kInFlight; ++q) {
+        if (idx[q] >= nr) continue;
+        any = true;
+        const bool up = idx[q] >= m.nd;
+        const uint32_t code = LUT[e[q]];
         int32_t label = 0;
-        bool done;
-        if (graph) {  // an exit: the graph knows where its path ends
-          done = interior_label(g, c, &label);
-          if (!done) {
-            label = graph_label(g, fd.tile_base, graph, up, c, st);
-            done = true;
-          }
+        bool done = false;
+        if (!(code & kHaloBit)) {  // inside its tile: the extremum
+          const uint32_t lx = code & 127u, ly = (code >> 7) & 63u, lz = (code >> 13) & 31u;
+          label = (int32_t)((uint32_t)(tx[q] * TX) + lx +
+                            nx * ((uint32_t)(ty[q] * TY) + ly + ny * ((uint32_t)(tz[q] * TZ) + lz)));
+          done = true;
         } else {
-          done = g.flat ? chase_step2(g, face, up, &c, &label) : chase_step3(g, face, up, &c, &label);
-          if (!done && ++hops > max_hops) {
-            if (probe)
-              ++pending;
-            else
-              atomicOr(&st->not_converged, 1u);
+          const int ntx = tx[q] + (int)((code >> 12) & 3u) - 1;
+          const int nty = ty[q] + (int)((code >> 14) & 3u) - 1;
+          const int ntz = tz[q] + (int)((code >> 16) & 3u) - 1;
+          if ((unsigned)ntx >= (unsigned)gtx || (unsigned)nty >= (unsigned)gty ||
+              (unsigned)ntz >= (unsigned)gtz) {  // cannot happen: every root lies in the field
+            ++bad;
             done = true;
-            label = 0;
+          } else {
+            const long long slot =
+                ((long long)ntx + (long long)gtx * (nty + (long long)gty * ntz)) * kFace +
+                (code & 0xfffu);
+            if (graph) {  // the jumped face graph knows where the path ends
+              const int2 gv = graph[fd.tile_base * (long long)kFace + slot];
+              const uint32_t f = (uint32_t)(up ? gv.x : gv.y);
+              if (!(f & kSlotFinal)) atomicOr(&st->not_converged, 1u);
+              label = (int32_t)(f & ~kSlotFinal);
+              done = true;
+            } else if (++hops[q] > max_hops) {
+              if (probe)
+                ++pending;
+              else
+                atomicOr(&st->not_converged, 1u);
+              done = true;
+            } else {
+              const uint32_t wv = __ldg(&face[slot]);
+              e[q] = up ? (wv & 0xffffu) : (wv >> 16);
+              tx[q] = ntx, ty[q] = nty, tz[q] = ntz;
+            }
           }
         }
         if (done) {
           if (probe)
             ++sampled;
           else
-            ts.root_label[m.rbase + i] = label;
-          i += 32;
-          have = i < nr;
-          hops = 0;
-          c = Chase{0u, tx0, ty0, tz0};
-          if (have) c.e = ts.root_box[m.rbase + i];
+            rl[idx[q]] = label;
+          idx[q] = next;
+          e[q] = nb;
+          next += 32;
+          nb = next < nr ? (uint32_t)rb[next] : 0u;
+          hops[q] = 0;
+          tx[q] = tx0, ty[q] = ty0, tz[q] = tz0;
         }
       }
+      if (!__any_sync(0xffffffffu, any)) break;
     }
   }
+  if (bad) atomicOr(&st->bad_index, 1u);
   if (probe) {
     if (sampled) atomicAdd(&st->sampled, sampled);
     if (pending) atomicAdd(&st->pending, pending);
@@ -1361,14 +1352,17 @@ __device__ __forceinline__ void list_append(const RankScratch &rs, unsigned long
   if (slot == 0xffffffffu) atomicOr(&st->hash_overflow, 1u);
 }
 
-// Tile pairs (see launch_tile_pairs).  Per tile: each pair's (asc, desc) from
-// its two roots' labels; the tile's distinct pairs -- a few dozen where the
-// tile has about a thousand root pairs -- are found in a shared-memory set and
-// only they are inserted into the global set.  A tile with more distinct pairs
-// than the shared set holds inserts the rest directly.
+// Tile pairs (see launch_tile_pairs).  One warp per tile, taken from a work
+// queue: each tile pair's (asc, desc) from its two roots' labels; the tile's
+// distinct pairs -- a few dozen where the tile has about a thousand root
+// pairs -- are found in the warp's shared-memory set and only they are
+// inserted into the global set.  Lanes work on kPairBatch pairs at once, so
+// their loads overlap.  A tile with more distinct pairs than the warp's set
+// holds inserts the rest directly.
 constexpr int kPairThreads = 256;
-constexpr int kPairHash = 2048;
-constexpr int kPairProbes = 64;
+constexpr int kWarpHash = 512;
+constexpr int kWarpProbes = 32;
+constexpr int kPairBatch = 4;
 
 __device__ __forceinline__ unsigned long long final_key(int key_mode, uint32_t fi, int32_t a, int32_t d) {
   return key_mode == kKeyBatch
@@ -1376,83 +1370,121 @@ __device__ __forceinline__ unsigned long long final_key(int key_mode, uint32_t f
              : (((unsigned long long)(uint32_t)a << 32) | (uint32_t)d);
 }
 
-__device__ __forceinline__ uint32_t smem_slot_of(unsigned long long key) {
-  return (uint32_t)(mix64t(key) & (kPairHash - 1));
+__device__ __forceinline__ uint32_t warp_slot_of(unsigned long long key) {
+  uint32_t h = ((uint32_t)key * 0x9E3779B1u) ^ ((uint32_t)(key >> 32) * 0x85EBCA77u);
+  h ^= h >> 15;
+  return h & (kWarpHash - 1);
 }
 
 template <bool kSingle>
 __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(Batch bt, TiledScratch ts, RankScratch rs,
                                                              DevStatus *st) {
   if (call_failed(st) || st->not_converged) return;
-  __shared__ unsigned long long HK[kPairHash];
-  __shared__ uint32_t HS[kPairHash];
-  __shared__ long long s_next;
+  __shared__ unsigned long long HKs[kPairThreads / 32][kWarpHash];
+  __shared__ uint32_t HSs[kPairThreads / 32][kWarpHash];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long *HK = HKs[wid];
+  uint32_t *HS = HSs[wid];
   const bool keep_ad = rs.capacity > kSetInL2;
-  for (long long k = queue_first(true, ts.queue + kQPairs, &s_next); k < bt.total_tiles;
-       k = queue_next(true, k, &s_next)) {
-    queue_prefetch(true, ts.queue + kQPairs, &s_next);
+  for (;;) {
+    long long k = 0;
+    if (lane == 0) k = (long long)atomicAdd(ts.queue + kQPairs, 1u);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= bt.total_tiles) break;
     const int64_t gt = k;
     const TileMeta m = ts.meta[gt];
     const uint32_t fi = kSingle ? 0u : (uint32_t)field_of(bt, gt);
-    for (int i = threadIdx.x; i < kPairHash; i += kPairThreads) HK[i] = ~0ull;
-    __syncthreads();
-    // the pair's final key, and its slot in the tile's shared set (kPairHash:
-    // not there -- inserted straight into the global set)
-    auto key_of_pair = [&](int i, int32_t *a, int32_t *d) {
-      const uint32_t pp = ts.pool_pair[m.pbase + i];
-      *a = __ldcg(&ts.root_label[m.rbase + (pp & 0xffffu)]);
-      *d = __ldcg(&ts.root_label[m.rbase + (pp >> 16)]);
-      return final_key(bt.key_mode, fi, *a, *d);
-    };
-    for (int i = threadIdx.x; i < m.npairs; i += kPairThreads) {
-      int32_t a, d;
-      const unsigned long long key = key_of_pair(i, &a, &d);
-      uint32_t s = smem_slot_of(key);
-      bool placed = false;
-      for (int probe = 0; probe < kPairProbes; ++probe) {
-        unsigned long long cur = HK[s];
-        if (cur == ~0ull) cur = atomicCAS(&HK[s], ~0ull, key);
-        if (cur == ~0ull || cur == key) {
-          placed = true;
-          break;
-        }
-        s = (s + 1) & (kPairHash - 1);
+    const uint32_t nr = (uint32_t)(m.nd + m.nu);
+    const int np = m.npairs;
+    const uint32_t *__restrict__ pp_src = ts.pool_pair + m.pbase;
+    const int32_t *__restrict__ labels = ts.root_label + m.rbase;
+    for (int i = lane; i < kWarpHash; i += 32) HK[i] = ~0ull;
+    __syncwarp();
+    auto label_of = [&](uint32_t r) -> int32_t {
+      if (r >= nr) {  // cannot happen for a pair the tile pass listed
+        atomicOr(&st->bad_index, 1u);
+        return 0;
       }
-      if (!placed) {  // the shared set is full: straight into the global set
-        bool fresh = false;
-        const uint32_t gs = global_insert(rs, key, &fresh);
-        list_append(rs, key, fresh, gs, st);
-        ts.pool_slot[m.pbase + i] = gs;
-        if (keep_ad) ts.pool_ad[m.pbase + i] = make_int2(a, d);
+      return __ldcg(&labels[r]);
+    };
+    // pass 1: every pair into the warp's set (or, past it, the global set)
+    for (int i0 = lane; i0 < np; i0 += 32 * kPairBatch) {
+      uint32_t pp[kPairBatch];
+      int32_t a[kPairBatch], d[kPairBatch];
+#pragma unroll
+      for (int u = 0; u < kPairBatch; ++u) pp[u] = i0 + 32 * u < np ? __ldcs(&pp_src[i0 + 32 * u]) : 0u;
+#pragma unroll
+      for (int u = 0; u < kPairBatch; ++u) {
+        a[u] = i0 + 32 * u < np ? label_of(pp[u] & 0xffffu) : 0;
+        d[u] = i0 + 32 * u < np ? label_of(pp[u] >> 16) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kPairBatch; ++u) {
+        const int i = i0 + 32 * u;
+        if (i >= np) continue;
+        const unsigned long long key = final_key(bt.key_mode, fi, a[u], d[u]);
+        uint32_t sl = warp_slot_of(key);
+        bool placed = false;
+        for (int probe = 0; probe < kWarpProbes; ++probe) {
+          unsigned long long cur = HK[sl];
+          if (cur == ~0ull) cur = atomicCAS(&HK[sl], ~0ull, key);
+          if (cur == ~0ull || cur == key) {
+            placed = true;
+            break;
+          }
+          sl = (sl + 1) & (kWarpHash - 1);
+        }
+        if (!placed) {  // the warp's set is full: straight into the global set
+          bool fresh = false;
+          const uint32_t gs = global_insert(rs, key, &fresh);
+          list_append(rs, key, fresh, gs, st);
+          ts.pool_slot[m.pbase + i] = gs;
+          if (keep_ad) ts.pool_ad[m.pbase + i] = make_int2(a[u], d[u]);
+        }
       }
     }
-    __syncthreads();
-    for (int s = threadIdx.x; s < kPairHash; s += kPairThreads) {
-      const unsigned long long key = HK[s];
+    __syncwarp();
+    // the tile's distinct pairs into the global set
+    for (int sl = lane; sl < kWarpHash; sl += 32) {
+      const unsigned long long key = HK[sl];
       if (key != ~0ull) {
         bool fresh = false;
         const uint32_t gs = global_insert(rs, key, &fresh);
         list_append(rs, key, fresh, gs, st);
-        HS[s] = gs;
+        HS[sl] = gs;
       }
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < m.npairs; i += kPairThreads) {
-      int32_t a, d;
-      const unsigned long long key = key_of_pair(i, &a, &d);
-      uint32_t s = smem_slot_of(key);
-      for (int probe = 0; probe < kPairProbes; ++probe) {
-        const unsigned long long cur = HK[s];
-        if (cur == key) {
-          ts.pool_slot[m.pbase + i] = HS[s];
-          if (keep_ad) ts.pool_ad[m.pbase + i] = make_int2(a, d);
-          break;
+    __syncwarp();
+    // pass 2: every pair's set slot
+    for (int i0 = lane; i0 < np; i0 += 32 * kPairBatch) {
+      uint32_t pp[kPairBatch];
+      int32_t a[kPairBatch], d[kPairBatch];
+#pragma unroll
+      for (int u = 0; u < kPairBatch; ++u) pp[u] = i0 + 32 * u < np ? __ldcs(&pp_src[i0 + 32 * u]) : 0u;
+#pragma unroll
+      for (int u = 0; u < kPairBatch; ++u) {
+        a[u] = i0 + 32 * u < np ? label_of(pp[u] & 0xffffu) : 0;
+        d[u] = i0 + 32 * u < np ? label_of(pp[u] >> 16) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kPairBatch; ++u) {
+        const int i = i0 + 32 * u;
+        if (i >= np) continue;
+        const unsigned long long key = final_key(bt.key_mode, fi, a[u], d[u]);
+        uint32_t sl = warp_slot_of(key);
+        for (int probe = 0; probe < kWarpProbes; ++probe) {
+          const unsigned long long cur = HK[sl];
+          if (cur == key) {
+            ts.pool_slot[m.pbase + i] = HS[sl];
+            if (keep_ad) ts.pool_ad[m.pbase + i] = make_int2(a[u], d[u]);
+            break;
+          }
+          if (cur == ~0ull) break;  // inserted straight into the global set in pass 1
+          sl = (sl + 1) & (kWarpHash - 1);
         }
-        if (cur == ~0ull) break;  // inserted straight into the global set above
-        s = (s + 1) & (kPairHash - 1);
       }
     }
-    __syncthreads();
+    __syncwarp();  // the warp's set is reused by its next tile
   }
 }
 
@@ -1551,7 +1583,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch 
 #pragma unroll
       for (int j = 0; j < kRun; ++j) {
         if (j >= n_here) break;
-        const int id = (int)((w[j / 2] >> (16 * (j & 1))) & 0xffffu);
+        int id = (int)((w[j / 2] >> (16 * (j & 1))) & 0xffffu);
+        if (id >= cnt) id = 0;  // cannot happen: every vertex's number is one of its tile's pairs
         const int4 t = staged ? T[id] : entry(id);
         const int64_t v = v0 + stride * j;
         __stcs(asc + v, t.x);
@@ -1726,20 +1759,36 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
 
 cudaError_t launch_chase_roots(const Batch &b, const TiledScratch &ts, const int2 *graph,
                                long long probe_stride, DevStatus *st, cudaStream_t s) {
-  const long long tiles = probe_stride > 0 ? (b.total_tiles + probe_stride - 1) / probe_stride
-                                           : b.total_tiles;
-  if (tiles == 0) return cudaSuccess;
-  const cudaError_t e = cudaMemsetAsync(ts.queue + kQChase, 0, sizeof(unsigned int), s);
+  cudaError_t e = cudaMemsetAsync(ts.queue + kQChase, 0, 2 * sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   constexpr int kWarps = kChaseThreads / 32;
-  const long long blocks =
-      std::min<long long>((long long)sms() * b.tune.chase_blocks, (tiles + kWarps - 1) / kWarps);
-  ++tl_launches;
-  if (b.n_fields == 1)
-    k_chase_roots<true><<<(unsigned)blocks, kChaseThreads, 0, s>>>(b, ts, graph, probe_stride, st);
-  else
-    k_chase_roots<false><<<(unsigned)blocks, kChaseThreads, 0, s>>>(b, ts, graph, probe_stride, st);
-  return cudaGetLastError();
+  for (int flat = 0; flat < 2; ++flat) {
+    const long long n = flat ? b.total_tiles - b.tiles3 : b.tiles3;
+    if (n == 0) continue;
+    const long long tiles = probe_stride > 0 ? (n + probe_stride - 1) / probe_stride : n;
+    const long long blocks =
+        std::min<long long>((long long)sms() * b.tune.chase_blocks, (tiles + kWarps - 1) / kWarps);
+    const size_t smem = (size_t)(flat ? k2Ext : kExt) * 4;
+    ++tl_launches;
+    if (flat) {
+      auto kern = b.n_fields == 1 ? k_chase_roots<true, true> : k_chase_roots<true, false>;
+      if (!capturing(s)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      kern<<<(unsigned)blocks, kChaseThreads, smem, s>>>(b, ts, graph, probe_stride, st);
+    } else {
+      auto kern = b.n_fields == 1 ? k_chase_roots<false, true> : k_chase_roots<false, false>;
+      if (!capturing(s)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+      }
+      kern<<<(unsigned)blocks, kChaseThreads, smem, s>>>(b, ts, graph, probe_stride, st);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 cudaError_t launch_tile_pairs(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
@@ -1748,7 +1797,9 @@ cudaError_t launch_tile_pairs(const Batch &b, const TiledScratch &ts, const Rank
   if (clear_table) e = cudaMemsetAsync(rs.table_keys, 0xff, (size_t)rs.capacity * 8, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ts.queue + kQPairs, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess || b.total_tiles == 0) return e;
-  const long long blocks = std::min<long long>(b.total_tiles, (long long)sms() * b.tune.pair_blocks);
+  constexpr int kWarps = kPairThreads / 32;
+  const long long blocks = std::min<long long>((b.total_tiles + kWarps - 1) / kWarps,
+                                               (long long)sms() * b.tune.pair_blocks);
   ++tl_launches;
   if (b.n_fields == 1)
     k_tile_pairs<true><<<(unsigned)blocks, kPairThreads, 0, s>>>(b, ts, rs, st);

@@ -86,8 +86,8 @@ constexpr int kBatchMaxFields = 1 << 16;
 struct Tuning {
   int tile_ctas = 2;     // tile kernels: CTAs per SM (2 fit an SM)
   int write_ctas = 4;    // write kernels: CTAs per SM
-  int chase_blocks = 8;  // root chase: 256-thread blocks (8 warps) per SM
-  int pair_blocks = 6;   // tile pairs: 256-thread blocks per SM
+  int chase_blocks = 3;  // root chase: 512-thread blocks (16 warps) per SM
+  int pair_blocks = 4;   // tile pairs: 256-thread blocks (a tile a warp) per SM
   int dynamic = 1;       // tile and write kernels: a work queue (1) or a static stride (0)
 };
 
@@ -127,8 +127,9 @@ struct TiledScratch {
   uint32_t *face;       // per tile kFace words: up-root | dn-root << 16 (extended-box indices)
   uint16_t *pid;        // per tile kTileV pair numbers; the 16 of a thread's run are contiguous
 };
-// Work-queue counters: tile pass 3D / 2D, write 3D / 2D, root chase, tile pairs.
-enum { kQTile3 = 0, kQTile2 = 1, kQWrite3 = 2, kQWrite2 = 3, kQChase = 4, kQPairs = 5, kQueues = 8 };
+// Work-queue counters: tile pass 3D / 2D, write 3D / 2D, root chase 3D / 2D, tile pairs.
+enum { kQTile3 = 0, kQTile2 = 1, kQWrite3 = 2, kQWrite2 = 3, kQChase = 4, kQChase2 = 5, kQPairs = 6,
+       kQueues = 8 };
 
 TileGeom tile_geom(const int64_t dims[3]);
 size_t tiled_scratch_bytes(long long total_tiles, int n_fields, unsigned long long pool_cap,
