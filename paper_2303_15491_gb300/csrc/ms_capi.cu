@@ -1141,7 +1141,7 @@ ms_status ms_batch_autotune(ms_ctx *c, int n_fields, const void *const *fields,
                         {&Tuning::tile_ctas, {2, 1}},
                         {&Tuning::write_ctas, {2, 4, 8}},
                         {&Tuning::chase_blocks, {3, 2}},
-                        {&Tuning::pair_blocks, {4, 3}}};
+                        {&Tuning::pair_blocks, {7, 5}}};
   for (const Knob &kn : knobs) {
     if (s != MS_OK) break;
     const int start = best.*(kn.field);

@@ -431,6 +431,20 @@ static_assert(2 * kBmW3 <= 2 * kThreads && 2 * kBmW2 <= 2 * kThreads,
               "two bitmap words per thread cover both root bitmaps");
 static_assert(kHash == kThreads * 16, "each thread numbers 16 consecutive set slots");
 
+// An empty tile record (a tile skipped for a NaN): no pairs, no roots.
+__device__ __forceinline__ void empty_tile(const TiledScratch &ts, int64_t gt) {
+  if (threadIdx.x == 0) {
+    TileMeta m;
+    m.pbase = 0;
+    m.rbase = 0;
+    m.npairs = 0;
+    m.nd = 0;
+    m.nu = 0;
+    m.pad = 0;
+    ts.meta[gt] = m;
+  }
+}
+
 // The distinct (dn-root, up-root) pairs and the distinct roots of a tile whose
 // final pointers are in w[] (one run of kRun per thread, both tile shapes).
 //   (1) every run entry whose pair differs from the entry before it inserts
@@ -579,20 +593,6 @@ __device__ __forceinline__ void number_tile_pairs(uint32_t *A, uint32_t *B, cons
     pid4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
   }
   __syncthreads();  // A and B are reused by the next tile
-}
-
-// An empty tile record (a tile skipped for a NaN): no pairs, no roots.
-__device__ __forceinline__ void empty_tile(const TiledScratch &ts, int64_t gt) {
-  if (threadIdx.x == 0) {
-    TileMeta m;
-    m.pbase = 0;
-    m.rbase = 0;
-    m.npairs = 0;
-    m.nd = 0;
-    m.nu = 0;
-    m.pad = 0;
-    ts.meta[gt] = m;
-  }
 }
 
 // Tile scheduling of the persistent kernels: a static stride over the tile
@@ -1360,9 +1360,9 @@ __device__ __forceinline__ void list_append(const RankScratch &rs, unsigned long
 // their loads overlap.  A tile with more distinct pairs than the warp's set
 // holds inserts the rest directly.
 constexpr int kPairThreads = 256;
-constexpr int kWarpHash = 512;
+constexpr int kWarpHash = 256;
 constexpr int kWarpProbes = 32;
-constexpr int kPairBatch = 4;
+constexpr int kPairBatch = 8;
 
 __device__ __forceinline__ unsigned long long final_key(int key_mode, uint32_t fi, int32_t a, int32_t d) {
   return key_mode == kKeyBatch
@@ -1405,14 +1405,14 @@ __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(Batch bt, TiledScra
         atomicOr(&st->bad_index, 1u);
         return 0;
       }
-      return __ldcg(&labels[r]);
+      return __ldg(&labels[r]);  // written by the previous launch
     };
     // pass 1: every pair into the warp's set (or, past it, the global set)
     for (int i0 = lane; i0 < np; i0 += 32 * kPairBatch) {
       uint32_t pp[kPairBatch];
       int32_t a[kPairBatch], d[kPairBatch];
 #pragma unroll
-      for (int u = 0; u < kPairBatch; ++u) pp[u] = i0 + 32 * u < np ? __ldcs(&pp_src[i0 + 32 * u]) : 0u;
+      for (int u = 0; u < kPairBatch; ++u) pp[u] = i0 + 32 * u < np ? __ldg(&pp_src[i0 + 32 * u]) : 0u;
 #pragma unroll
       for (int u = 0; u < kPairBatch; ++u) {
         a[u] = i0 + 32 * u < np ? label_of(pp[u] & 0xffffu) : 0;
@@ -1460,7 +1460,7 @@ __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(Batch bt, TiledScra
       uint32_t pp[kPairBatch];
       int32_t a[kPairBatch], d[kPairBatch];
 #pragma unroll
-      for (int u = 0; u < kPairBatch; ++u) pp[u] = i0 + 32 * u < np ? __ldcs(&pp_src[i0 + 32 * u]) : 0u;
+      for (int u = 0; u < kPairBatch; ++u) pp[u] = i0 + 32 * u < np ? __ldg(&pp_src[i0 + 32 * u]) : 0u;
 #pragma unroll
       for (int u = 0; u < kPairBatch; ++u) {
         a[u] = i0 + 32 * u < np ? label_of(pp[u] & 0xffffu) : 0;

@@ -87,7 +87,7 @@ struct Tuning {
   int tile_ctas = 2;     // tile kernels: CTAs per SM (2 fit an SM)
   int write_ctas = 4;    // write kernels: CTAs per SM
   int chase_blocks = 3;  // root chase: 512-thread blocks (16 warps) per SM
-  int pair_blocks = 4;   // tile pairs: 256-thread blocks (a tile a warp) per SM
+  int pair_blocks = 7;   // tile pairs: 256-thread blocks (a tile a warp) per SM
   int dynamic = 1;       // tile and write kernels: a work queue (1) or a static stride (0)
 };
 
