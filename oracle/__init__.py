@@ -79,6 +79,8 @@ def lib():
             L.ms_oracle_simplex_geometry.argtypes = [i32p, i64p, ctypes.c_int, ctypes.c_void_p,
                                                      ctypes.c_void_p, i64p]
             L.ms_oracle_link_stats.restype = ctypes.c_int
+            L.ms_oracle_coord_mean.argtypes = [ctypes.c_int64, ctypes.c_int]
+            L.ms_oracle_coord_mean.restype = ctypes.c_float
             _lib = L
     return _lib
 
@@ -234,6 +236,12 @@ def simplex_index(labels: np.ndarray, dims, mode: int = 0):
                                               offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                               ctypes.byref(total)))
     return {"codes": codes, "cell_offsets": offs[:cells], "total": int(total.value)}
+
+
+def coord_mean(total: int, n: int) -> float:
+    """The geometry pass's point coordinate: the mean of n corner coordinates
+    whose exact sum is total, as a float32."""
+    return float(np.float32(lib().ms_oracle_coord_mean(int(total), int(n))))
 
 
 def simplex_geometry(labels: np.ndarray, dims, mode: int = 0):

@@ -641,8 +641,14 @@ int ms_oracle_simplex_index_mode(const int32_t *labels, const int64_t dims[3], i
  * Element order: cells in index order, simplices in chain order p, elements
  * in the order above.  Points are grid coordinates (x, y[, z]) in float32:
  * a midpoint is (u + v) / 2, a face centre (u + v + w) / 3, the tetrahedron
- * centre the sum of its corners / 4, each coordinate's sum formed exactly
- * before one rounded division.
+ * centre the sum of its corners / 4: each coordinate is the exact sum S of
+ * the corners' integer coordinates divided by the corner count n, rounded
+ * once to the nearest float32 (ties to even).  It is computed as
+ * (float)((double)S / n): for n = 1, 2, 4 the double quotient is exact; for
+ * n = 3, S / 3 is an integer (exact) or differs from every float32 rounding
+ * midpoint m by at least 2^(E-25) / 3 (S and 3m are both multiples of
+ * 2^(E-25), E the exponent of S / 3), far more than the double rounding
+ * error 2^(E-53), so rounding the double to float32 rounds S / 3 itself.
  */
 
 typedef struct {
@@ -652,11 +658,15 @@ typedef struct {
   int64_t at;      /* next element */
 } geo_out;
 
+/* The mean of n corner coordinates whose exact sum is sum (n in 1..4),
+ * rounded once to float32 (see above). */
+float ms_oracle_coord_mean(int64_t sum, int n) { return (float)((double)sum / (double)n); }
+
 static void geo_point(geo_out *o, int k, const int64_t (*c)[3], const int *ids, int nids) {
   for (int d = 0; d < o->dim; ++d) {
     int64_t sum = 0;
     for (int i = 0; i < nids; ++i) sum += c[ids[i]][d];
-    o->pos[(o->at * o->npts + k) * o->dim + d] = (float)sum / (float)nids;
+    o->pos[(o->at * o->npts + k) * o->dim + d] = ms_oracle_coord_mean(sum, nids);
   }
 }
 

@@ -631,9 +631,12 @@ constexpr uint32_t kFiveThirdsBits = 0x3FD55555u;
 // to nearest even.  Narrow path (o below 2^21): fl(o) + fl(k / cnt), which is
 // exact for cnt = 1, 2, 4 and the correctly rounded value for thirds except
 // k / cnt = 2/3 at o = 1 -- checked for every o below 2^21 against the exact
-// quotient.  Wide path: the sum in 64 bits and an IEEE division.
+// quotient.  Wide path: the exact sum in 64 bits, divided in double and
+// rounded to float -- one correct rounding of the exact quotient, as the
+// double quotient is exact for cnt = 1, 2, 4 and for thirds never within a
+// double rounding error of a float rounding midpoint.
 __device__ __forceinline__ float mean_wide(uint32_t o, uint32_t k, uint32_t cnt) {
-  return __fdiv_rn((float)((uint64_t)cnt * o + k), (float)cnt);
+  return __double2float_rn(__ddiv_rn((double)((uint64_t)cnt * o + k), (double)cnt));
 }
 
 template <int kPer, bool kWide>

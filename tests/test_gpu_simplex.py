@@ -213,12 +213,16 @@ def test_geometry_points_not_16_byte_aligned(ctx, dims):
     assert torch.isnan(buf[0]) and bool(torch.isnan(buf[1 + total * dim * dim:]).all())
 
 
-@pytest.mark.parametrize("dims", [((1 << 21) - 3, 2, 1), ((1 << 21) + 5, 2, 1), ((1 << 21) - 3, 2, 2)])
+@pytest.mark.parametrize("dims", [((1 << 21) - 3, 2, 1), ((1 << 21) + 5, 2, 1), ((1 << 21) - 3, 2, 2),
+                                  ((6 << 20) + 3, 2, 1)])
 def test_geometry_far_coordinates(ctx, dims):
     """Coordinates up to 2^21 - 3 (the largest whose corner sums the kernel
-    converts without a division) and past 2^21 (the division path): points
-    bit-exact with the oracle.  Sparse labels keep the element count small;
-    triples of labels give the face and triangle centres (thirds)."""
+    converts without a division), past 2^21 (the division path) and past
+    2^24 / 3 (sums of three corners beyond 2^24, where rounding the sum before
+    dividing would round twice): points bit-exact with the oracle, whose
+    coordinate rounding is pinned to exact rational arithmetic.  Sparse labels
+    keep the element count small; triples of labels give the face and
+    triangle centres (thirds)."""
     g = np.random.default_rng(dims[0] % 97 + dims[2])
     n = int(np.prod(dims))
     lab = np.zeros(n, np.int32)

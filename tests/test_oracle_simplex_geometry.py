@@ -129,3 +129,42 @@ def test_separators_are_closed(levels):
             assert n == 2, (a, b, n)
         else:
             assert n >= 2, (a, b, n)
+
+
+def _f32_nearest(q):
+    """The float32 nearest to the positive rational q, ties to even, by
+    integer arithmetic (no floating-point step)."""
+    from fractions import Fraction
+    q = Fraction(q)
+    e = q.numerator.bit_length() - q.denominator.bit_length()
+    if Fraction(2) ** e > q:
+        e -= 1
+    m = q / Fraction(2) ** (e - 23)  # in [2^23, 2^24)
+    r = m.numerator // m.denominator
+    rem = m - r
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and r % 2 == 1):
+        r += 1
+    return float(r) * 2.0 ** (e - 23)
+
+
+def test_coordinate_mean_is_one_rounding_of_the_exact_quotient():
+    """Sec. 4.3 centres and midpoints: a point coordinate is the exact mean of
+    its corners' integer coordinates rounded once to float32.  Checked against
+    rational arithmetic for sums past 2^24, where rounding the sum to float
+    first would round twice (it does so for some of these cases)."""
+    from fractions import Fraction
+    g = np.random.default_rng(2024)
+    cases = [(s, n) for n in (1, 2, 3, 4) for s in g.integers(1, 1 << 33, 400, dtype=np.int64)]
+    # sums just past powers of two and odd sums near 2^24..2^26 (thirds land
+    # between float32 neighbours there)
+    for b in (24, 25, 26, 30, 33):
+        for d in range(-7, 8):
+            for n in (2, 3, 4):
+                cases.append((int((1 << b) + d), n))
+    twice = 0
+    for s, n in cases:
+        s = int(s)
+        want = _f32_nearest(Fraction(s, n))
+        assert oracle.coord_mean(s, n) == want, (s, n)
+        twice += float(np.float32(np.float32(s) / np.float32(n))) != want
+    assert twice > 0  # the cases include ones where two roundings differ
