@@ -786,7 +786,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="noise512", choices=sorted(WORKLOADS))
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-slab", type=int, default=48)
     ap.add_argument("--ref-slab", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -894,7 +894,7 @@ def main():
 
     # ---- end to end through ms_segment_host (pinned host memory)
     esz = 2 if w["dtype"] == "f16" else 4
-    e2e_value = None
+    e2e_value = e2e_single = None
     if args.e2e_steps > 0:
         h_field = torch.from_numpy(f_np).pin_memory()
         h_asc = torch.empty(n, dtype=torch.int32).pin_memory()
@@ -905,8 +905,20 @@ def main():
         t = time.perf_counter()
         for _ in range(args.e2e_steps):
             ms.ms_segment_host(ctx, h_field, dims, dtype, h_asc, h_desc, h_ms)
+        single_s = max_over_ranks(time.perf_counter() - t, dist, dev)
+        e2e_single = whole_job_rate(n * args.e2e_steps, ws, single_s)
+        # the pipelined host path: step s+1's upload and step s-1's download
+        # overlap step s's segmentation (every step's copies are in the region)
+        k_steps = args.e2e_steps
+        many = lambda: ms.ms_segment_host_many(ctx, [h_field] * k_steps, [dims] * k_steps,
+                                               [dtype] * k_steps, [h_asc] * k_steps,
+                                               [h_desc] * k_steps, [h_ms] * k_steps)
+        many()  # warm the second buffer set and its captured plan
+        barrier()
+        t = time.perf_counter()
+        many()
         e2e_s = max_over_ranks(time.perf_counter() - t, dist, dev)
-        e2e_value = whole_job_rate(n * args.e2e_steps, ws, e2e_s)
+        e2e_value = whole_job_rate(n * k_steps, ws, e2e_s)
 
     # ---- roofline of the dominant kernel and of the whole path.  The
     # headline figure is the path's algorithmic bytes (field in, three labels
@@ -986,7 +998,11 @@ def main():
         "gpu_launches": prof["launches"],
         "e2e": None if e2e_value is None else {
             "value": e2e_value, "unit": "vertices/s", "h2d_bytes_per_step": n * esz,
-            "d2h_bytes_per_step": 3 * n * 4, "api": "ms_segment_host, pinned host buffers"},
+            "d2h_bytes_per_step": 3 * n * 4,
+            "api": f"ms_segment_host_many over {args.e2e_steps} steps, pinned host buffers (each step's "
+                   "upload and label download overlap the neighbouring steps' work)",
+            "single_call": {"value": e2e_single, "unit": "vertices/s",
+                            "api": "ms_segment_host, one synchronous call a step"}},
         "clocks": clocks,
     }
     ms.ms_destroy(ctx)

@@ -129,6 +129,20 @@ ms_status ms_segment_host(ms_ctx *ctx, const void *host_field, const int64_t dim
                           ms_dtype dtype, int32_t *host_asc, int32_t *host_desc,
                           int32_t *host_ms);
 
+/* Many segmentations from and to HOST memory, pipelined: field f is copied
+ * to the device while field f - 1 is segmented and field f - 2's labels are
+ * copied back, so the host link carries uploads and downloads at once (two
+ * device buffer sets, one upload and one download stream besides the
+ * context's).  Arguments per field as ms_segment_host; k_out[f] (may be NULL)
+ * receives each field's region count.  Returns after every field's labels
+ * are in host memory, or at the first failing field (later fields' outputs
+ * are then undefined).  Host buffers should be pinned: pageable memory makes
+ * the copies synchronous and removes the overlap. */
+ms_status ms_segment_host_many(ms_ctx *ctx, int n_fields, const void *const *host_fields,
+                               const int64_t (*dims)[3], const ms_dtype *dtypes,
+                               int32_t *const *host_asc, int32_t *const *host_desc,
+                               int32_t *const *host_ms, int64_t *k_out);
+
 /* K, the number of MS regions found by the last successful ms_segment /
  * ms_segment_host / ms_pair_rank on this context (0 before any). */
 ms_status ms_last_region_count(const ms_ctx *ctx, int64_t *k);
@@ -169,8 +183,9 @@ typedef struct {
   int tile_ctas;      /* tile kernels: CTAs per SM (1 or 2) */
   int write_ctas;     /* label-writing kernels: CTAs per SM */
   int chase_blocks;   /* root chase: 512-thread blocks (warps take tiles) per SM */
-  int pair_blocks;    /* tile pairs: 256-thread blocks (one tile a warp) per SM */
+  int pair_blocks;    /* tile pairs: 256-thread blocks per SM */
   int dynamic;        /* 1: tiles taken from a work queue; 0: static stride */
+  int resolve_mode;   /* exits and pairs: -1 by tile count, 0 a tile a warp, 1 flat */
   double default_ms;  /* ms_batch_autotune: time of the default choices */
   double best_ms;     /* ms_batch_autotune: time of the chosen ones */
 } ms_tuning;

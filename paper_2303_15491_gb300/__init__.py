@@ -27,7 +27,7 @@ __all__ = [
     "ms_pair_rank_noalloc", "MS_NOALLOC_MAX_N", "ms_segment_batch", "ms_server_create",
     "ms_server_submit", "ms_server_wait", "ms_server_stats", "ms_server_destroy",
     "ms_batch_autotune", "ms_batch_graphs", "ms_simplex_index", "ms_simplex_geometry",
-    "simplex_cells",
+    "simplex_cells", "ms_segment_host_many",
 ]
 
 MS_F32, MS_F16 = 0, 1
@@ -41,7 +41,7 @@ EXPORTED_SYMBOLS = [
     "ms_profile_enable", "ms_profile_read", "ms_profile_stage_name", "ms_segment_staged",
     "ms_pair_rank_noalloc", "ms_segment_batch", "ms_server_create", "ms_server_submit",
     "ms_server_wait", "ms_server_stats", "ms_server_destroy", "ms_batch_autotune",
-    "ms_batch_graphs", "ms_simplex_index", "ms_simplex_geometry",
+    "ms_batch_graphs", "ms_simplex_index", "ms_simplex_geometry", "ms_segment_host_many",
 ]
 MS_NOALLOC_MAX_N = 262144
 
@@ -49,7 +49,7 @@ MS_NOALLOC_MAX_N = 262144
 class _Tuning(ctypes.Structure):
     _fields_ = [("tile_ctas", ctypes.c_int), ("write_ctas", ctypes.c_int),
                 ("chase_blocks", ctypes.c_int), ("pair_blocks", ctypes.c_int),
-                ("dynamic", ctypes.c_int), ("default_ms", ctypes.c_double),
+                ("dynamic", ctypes.c_int), ("resolve_mode", ctypes.c_int), ("default_ms", ctypes.c_double),
                 ("best_ms", ctypes.c_double)]
 
 
@@ -115,6 +115,8 @@ def load(build: bool = True) -> ctypes.CDLL:
             L.ms_server_destroy.argtypes = [c_vp]
             L.ms_segment_staged.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
             L.ms_segment_host.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp]
+            L.ms_segment_host_many.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                               c_i64p]
             L.ms_last_region_count.argtypes = [c_vp, c_i64p]
             L.ms_order_keys.argtypes = [c_vp, c_vp, ctypes.c_int64, ctypes.c_int, c_vp]
             L.ms_steepest.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp]
@@ -291,6 +293,20 @@ def ms_server_destroy(srv) -> None:
 def ms_segment_staged(ctx, field, dims, dtype, out_asc, out_desc, out_ms) -> None:
     _check(load().ms_segment_staged(ctx, _ptr(field), _dims(dims), int(dtype), _ptr(out_asc),
                                     _ptr(out_desc), _ptr(out_ms)), "ms_segment_staged")
+
+
+def ms_segment_host_many(ctx, host_fields, dims, dtypes, host_asc, host_desc, host_ms) -> list:
+    """Many host fields through the pipelined host path; returns the region
+    counts."""
+    n = len(host_fields)
+    ptrs = lambda xs: (c_vp * n)(*[_ptr(x) for x in xs])
+    d = (ctypes.c_int64 * (3 * n))(*[int(v) for dd in dims for v in dd])
+    t = (ctypes.c_int * n)(*[int(x) for x in dtypes])
+    k = (ctypes.c_int64 * n)()
+    _check(load().ms_segment_host_many(ctx, n, ptrs(host_fields), ctypes.cast(d, c_vp),
+                                       ctypes.cast(t, c_vp), ptrs(host_asc), ptrs(host_desc),
+                                       ptrs(host_ms), k), "ms_segment_host_many")
+    return [int(x) for x in k]
 
 
 def ms_segment_host(ctx, host_field, dims, dtype, host_asc, host_desc, host_ms) -> None:

@@ -46,8 +46,12 @@ struct ms_ctx {
   DevStatus *hst = nullptr;  // pinned host copy
   void *scratch = nullptr;   // pair-rank working memory
   size_t scratch_bytes = 0;
-  void *io = nullptr;        // device buffers of ms_segment_host
-  size_t io_bytes = 0;
+  void *io = nullptr;        // device buffers of ms_segment_host (and the first set of
+  size_t io_bytes = 0;       // ms_segment_host_many)
+  void *io2 = nullptr;       // the second buffer set of ms_segment_host_many
+  size_t io2_bytes = 0;
+  cudaStream_t up = nullptr, down = nullptr;  // ms_segment_host_many: upload / download streams
+  cudaEvent_t ev_up[2] = {}, ev_comp[2] = {}, ev_down[2] = {};
   void *tscratch = nullptr;  // tiled path working memory
   size_t tscratch_bytes = 0;
   void *graph = nullptr;     // the face graph, built only for long exit chains
@@ -65,7 +69,8 @@ struct ms_ctx {
   long long alloc_epoch = 0;  // bumped whenever a device buffer is reallocated
   Tuning tune;                // launch choices without a tuned entry
   RunInfo run;                // sizes met by the last step-by-step tiled call
-  BatchPlan plan;             // the last batch: its tuning and captured graph
+  BatchPlan plans[2];         // the last two batches: their tuning and captured graphs
+  int plan_next = 0;          // the plan slot a new signature takes
   bool graphs_on = true;
   // profiler
   bool prof_on = false;
@@ -422,6 +427,7 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
                       tiled_scratch_bytes(total_tiles, nf, cap, rcap));
     if (s != MS_OK) return s;
     tiled_scratch_carve(c->tscratch, total_tiles, nf, cap, rcap, &ts);
+    if (tile_mode(b)) ts.root_tile = nullptr;  // only the flat resolution reads it
     StageTimer t0(c, MS_STAGE_TILE_LOCAL);
     MS_TRY(launch_tile_local(b, ts, c->dst, c->stream));
     t0.stop();
@@ -447,7 +453,7 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
   const long long slots = face_graph_slots(b);
   bool use_graph = false;
   if (nroots >= kProbeMinRoots && slots < (1ll << 31)) {
-    const long long stride = std::max<long long>(1, total_tiles / kProbeTiles);
+    const long long stride = std::max<long long>(1, (long long)(nroots / kProbeRoots));
     MS_TRY(cudaMemsetAsync(&c->dst->pending, 0, 2 * sizeof(unsigned int), c->stream));
     MS_TRY(launch_chase_roots(b, ts, nullptr, stride, c->dst, c->stream));
     s = read_status(c);
@@ -626,8 +632,7 @@ void reset_plan(BatchPlan *p) {
 // Capture the whole tiled pipeline for these fields as one CUDA graph, sized
 // from the step-by-step call that just ran (c->run) with margins; nothing in
 // it reads back to the host but the final status block and field starts.
-ms_status capture_plan(ms_ctx *c, const FieldArg *fa, int nf) {
-  BatchPlan &P = c->plan;
+ms_status capture_plan(ms_ctx *c, BatchPlan &P, const FieldArg *fa, int nf) {
   drop_graph(&P);
   Staged sf;
   ms_status s = stage_fields(c, fa, nf, &sf);  // also leaves the descriptors on the device
@@ -655,6 +660,7 @@ ms_status capture_plan(ms_ctx *c, const FieldArg *fa, int nf) {
   }
   TiledScratch ts;
   tiled_scratch_carve(c->tscratch, b.total_tiles, nf, pool_cap, root_cap, &ts);
+  if (tile_mode(b)) ts.root_tile = nullptr;
   RankScratch rs;
   rank_scratch_carve(c->scratch, hcap, &rs);
   if ((uint64_t)hcap < 2 * run.npairs + 2) rs.probe_limit = kEstimateProbeLimit;
@@ -767,8 +773,7 @@ ms_status capture_plan(ms_ctx *c, const FieldArg *fa, int nf) {
 
 // Replay the captured pipeline.  *fallback: the sizes it was captured with no
 // longer suffice (the caller runs the call step by step).
-ms_status replay_plan(ms_ctx *c, int nf, int64_t *k_out, bool *fallback) {
-  BatchPlan &P = c->plan;
+ms_status replay_plan(ms_ctx *c, BatchPlan &P, int nf, int64_t *k_out, bool *fallback) {
   *fallback = false;
   if (c->prof_on) cudaEventRecord(c->ev[MS_STAGE_GRAPH][0], c->stream);
   MS_TRY(cudaGraphLaunch(P.exec, c->stream));
@@ -806,24 +811,32 @@ ms_status replay_plan(ms_ctx *c, int nf, int64_t *k_out, bool *fallback) {
 
 // A batch through the tiled path: replayed from its graph when the same fields
 // come again, else step by step (then captured for the next time).
+// The plan of these fields: the slot holding their signature, else the older
+// slot, reset for them (two buffer sets alternating -- ms_segment_host_many --
+// keep both captured).
+BatchPlan &plan_of(ms_ctx *c, std::vector<int64_t> sig) {
+  for (BatchPlan &P : c->plans)
+    if (P.sig == sig) return P;
+  BatchPlan &P = c->plans[c->plan_next];
+  c->plan_next ^= 1;
+  reset_plan(&P);
+  P.sig = std::move(sig);
+  return P;
+}
+
 ms_status run_batch(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
-  BatchPlan &P = c->plan;
-  std::vector<int64_t> sig = batch_signature(fa, nf);
-  if (P.sig != sig) {
-    reset_plan(&P);
-    P.sig = std::move(sig);
-  }
+  BatchPlan &P = plan_of(c, batch_signature(fa, nf));
   ++P.seen;
   if (c->graphs_on && P.exec && P.epoch == c->alloc_epoch) {
     bool fallback = false;
-    const ms_status s = replay_plan(c, nf, k_out, &fallback);
+    const ms_status s = replay_plan(c, P, nf, k_out, &fallback);
     if (s != MS_OK || !fallback) return s;
     drop_graph(&P);
   }
   const ms_status s = segment_tiled(c, fa, nf, k_out, P.tuned ? P.tune : c->tune);
   if (s != MS_OK) return s;
   // capture once the same fields come a second time (one-off calls never pay for it)
-  if (c->graphs_on && !P.exec && P.seen >= 2 && capture_plan(c, fa, nf) != MS_OK) drop_graph(&P);
+  if (c->graphs_on && !P.exec && P.seen >= 2 && capture_plan(c, P, fa, nf) != MS_OK) drop_graph(&P);
   return MS_OK;
 }
 
@@ -832,18 +845,19 @@ ms_status run_batch(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out) {
 namespace msseg {
 
 size_t ctx_resident_bytes(const ms_ctx *c) {
-  return c->scratch_bytes + c->io_bytes + c->tscratch_bytes + c->graph_bytes + c->sxscratch_bytes +
-         c->batch_dev_bytes + sizeof(DevStatus);
+  return c->scratch_bytes + c->io_bytes + c->io2_bytes + c->tscratch_bytes + c->graph_bytes +
+         c->sxscratch_bytes + c->batch_dev_bytes + sizeof(DevStatus);
 }
 
 void ctx_release_scratch(ms_ctx *c) {
   DeviceGuard g(c->device);
   cudaStreamSynchronize(c->stream);
-  drop_graph(&c->plan);
-  void **bufs[] = {&c->scratch, &c->io, &c->tscratch, &c->graph, &c->sxscratch, &c->batch_dev};
-  size_t *sizes[] = {&c->scratch_bytes, &c->io_bytes, &c->tscratch_bytes, &c->graph_bytes,
-                     &c->sxscratch_bytes, &c->batch_dev_bytes};
-  for (int i = 0; i < 6; ++i) {
+  for (BatchPlan &P : c->plans) drop_graph(&P);
+  void **bufs[] = {&c->scratch, &c->io, &c->io2, &c->tscratch, &c->graph, &c->sxscratch,
+                   &c->batch_dev};
+  size_t *sizes[] = {&c->scratch_bytes, &c->io_bytes, &c->io2_bytes, &c->tscratch_bytes,
+                     &c->graph_bytes, &c->sxscratch_bytes, &c->batch_dev_bytes};
+  for (int i = 0; i < 7; ++i) {
     if (*bufs[i]) cudaFree(*bufs[i]);
     *bufs[i] = nullptr;
     *sizes[i] = 0;
@@ -919,6 +933,15 @@ ms_status ms_destroy(ms_ctx *c) {
   for (int i = 0; i < MS_STAGE_COUNT; ++i)
     for (int j = 0; j < 2; ++j)
       if (c->ev[i][j]) cudaEventDestroy(c->ev[i][j]);
+  for (int i = 0; i < 2; ++i) {
+    if (c->ev_up[i]) cudaEventDestroy(c->ev_up[i]);
+    if (c->ev_comp[i]) cudaEventDestroy(c->ev_comp[i]);
+    if (c->ev_down[i]) cudaEventDestroy(c->ev_down[i]);
+  }
+  if (c->up) cudaStreamDestroy(c->up);
+  if (c->down) cudaStreamDestroy(c->down);
+  if (c->io2) cudaFree(c->io2);
+  for (BatchPlan &P : c->plans) reset_plan(&P);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return MS_OK;
@@ -1082,7 +1105,8 @@ ms_status ms_batch_graphs(ms_ctx *c, int on) {
   if (!c) return MS_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
   c->graphs_on = on != 0;
-  if (!c->graphs_on) drop_graph(&c->plan);
+  if (!c->graphs_on)
+    for (BatchPlan &P : c->plans) drop_graph(&P);
   return MS_OK;
 }
 
@@ -1096,12 +1120,7 @@ ms_status ms_batch_autotune(ms_ctx *c, int n_fields, const void *const *fields,
   ms_status s = batch_args(n_fields, fields, dims, dtypes, asc, desc, ms, &fa, &batchable);
   if (s != MS_OK) return s;
   if (!batchable) return MS_ERR_INVALID_ARG;
-  BatchPlan &P = c->plan;
-  std::vector<int64_t> sig = batch_signature(fa.data(), n_fields);
-  if (P.sig != sig) {
-    reset_plan(&P);
-    P.sig = std::move(sig);
-  }
+  BatchPlan &P = plan_of(c, batch_signature(fa.data(), n_fields));
   drop_graph(&P);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   MS_TRY(cudaEventCreate(&e0));
@@ -1141,7 +1160,8 @@ ms_status ms_batch_autotune(ms_ctx *c, int n_fields, const void *const *fields,
                         {&Tuning::tile_ctas, {2, 1}},
                         {&Tuning::write_ctas, {2, 4, 8}},
                         {&Tuning::chase_blocks, {3, 2}},
-                        {&Tuning::pair_blocks, {7, 5}}};
+                        {&Tuning::pair_blocks, {8, 4}},
+                        {&Tuning::resolve_mode, {-1, 0, 1}}};
   for (const Knob &kn : knobs) {
     if (s != MS_OK) break;
     const int start = best.*(kn.field);
@@ -1172,6 +1192,7 @@ ms_status ms_batch_autotune(ms_ctx *c, int n_fields, const void *const *fields,
     out->write_ctas = best.write_ctas;
     out->chase_blocks = best.chase_blocks;
     out->pair_blocks = best.pair_blocks;
+    out->resolve_mode = best.resolve_mode;
     out->dynamic = best.dynamic;
     out->default_ms = t_default;
     out->best_ms = t_best;
@@ -1226,6 +1247,101 @@ ms_status ms_segment_host(ms_ctx *c, const void *host_field, const int64_t dims[
   MS_TRY(cudaMemcpyAsync(host_ms, dms, (size_t)n * 4, cudaMemcpyDeviceToHost, c->stream));
   td.stop();
   MS_TRY(cudaStreamSynchronize(c->stream));
+  finish_profile(c, l0);
+  return MS_OK;
+}
+
+ms_status ms_segment_host_many(ms_ctx *c, int n_fields, const void *const *host_fields,
+                               const int64_t (*dims)[3], const ms_dtype *dtypes,
+                               int32_t *const *host_asc, int32_t *const *host_desc,
+                               int32_t *const *host_ms, int64_t *k_out) {
+  if (!c || n_fields < 0) return MS_ERR_INVALID_ARG;
+  if (n_fields == 0) return MS_OK;
+  if (!host_fields || !dims || !dtypes || !host_asc || !host_desc || !host_ms)
+    return MS_ERR_INVALID_ARG;
+  std::vector<int64_t> nv((size_t)n_fields);
+  size_t need = 0;
+  for (int f = 0; f < n_fields; ++f) {
+    ms_status s = check_dims(dims[f], &nv[f]);
+    if (s != MS_OK) return s;
+    s = check_dtype(dtypes[f]);
+    if (s != MS_OK) return s;
+    if (!host_fields[f] || !host_asc[f] || !host_desc[f] || !host_ms[f]) return MS_ERR_INVALID_ARG;
+    const size_t esz = dtypes[f] == MS_F16 ? 2 : 4;
+    const size_t fb = ((size_t)nv[f] * esz + 255) & ~(size_t)255;
+    const size_t lb = ((size_t)nv[f] * 4 + 255) & ~(size_t)255;
+    need = std::max(need, fb + 3 * lb);
+  }
+  DeviceGuard g(c->device);
+  ms_status s = ensure_buffer(c, &c->io, &c->io_bytes, need);
+  if (s == MS_OK && n_fields > 1) s = ensure_buffer(c, &c->io2, &c->io2_bytes, need);
+  if (s != MS_OK) return s;
+  if (!c->up) MS_TRY(cudaStreamCreateWithFlags(&c->up, cudaStreamNonBlocking));
+  if (!c->down) MS_TRY(cudaStreamCreateWithFlags(&c->down, cudaStreamNonBlocking));
+  for (int i = 0; i < 2; ++i) {
+    if (!c->ev_up[i]) MS_TRY(cudaEventCreateWithFlags(&c->ev_up[i], cudaEventDisableTiming));
+    if (!c->ev_comp[i]) MS_TRY(cudaEventCreateWithFlags(&c->ev_comp[i], cudaEventDisableTiming));
+    if (!c->ev_down[i]) MS_TRY(cudaEventCreateWithFlags(&c->ev_down[i], cudaEventDisableTiming));
+  }
+  // the buffers of set `slot` for field f
+  struct Io {
+    void *field;
+    int32_t *asc, *desc, *ms;
+  };
+  auto io_of = [&](int slot, int f) {
+    const size_t esz = dtypes[f] == MS_F16 ? 2 : 4;
+    const size_t fb = ((size_t)nv[f] * esz + 255) & ~(size_t)255;
+    const size_t lb = ((size_t)nv[f] * 4 + 255) & ~(size_t)255;
+    char *base = static_cast<char *>(slot ? c->io2 : c->io);
+    return Io{base, reinterpret_cast<int32_t *>(base + fb), reinterpret_cast<int32_t *>(base + fb + lb),
+              reinterpret_cast<int32_t *>(base + fb + 2 * lb)};
+  };
+  // field f's upload into set f % 2, once field f - 2 (the set's last user) is downloaded
+  auto upload = [&](int f) -> cudaError_t {
+    const int slot = f & 1;
+    cudaError_t e = cudaSuccess;
+    if (f >= 2) e = cudaStreamWaitEvent(c->up, c->ev_down[slot], 0);
+    const size_t esz = dtypes[f] == MS_F16 ? 2 : 4;
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(io_of(slot, f).field, host_fields[f], (size_t)nv[f] * esz,
+                          cudaMemcpyHostToDevice, c->up);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_up[slot], c->up);
+    return e;
+  };
+  auto drain = [&]() {
+    cudaStreamSynchronize(c->up);
+    cudaStreamSynchronize(c->down);
+    cudaStreamSynchronize(c->stream);
+  };
+  // the streams of a previous call on this context are idle: each call drains them
+  const long long l0 = tl_launches;
+  cudaError_t e = upload(0);
+  for (int f = 0; f < n_fields && e == cudaSuccess; ++f) {
+    if (f + 1 < n_fields) e = upload(f + 1);  // overlaps field f's segmentation and downloads
+    if (e != cudaSuccess) break;
+    const int slot = f & 1;
+    const Io io = io_of(slot, f);
+    e = cudaStreamWaitEvent(c->stream, c->ev_up[slot], 0);
+    if (e != cudaSuccess) break;
+    s = segment_device(c, io.field, dims[f], (int)dtypes[f], nv[f], io.asc, io.desc, io.ms);
+    if (s != MS_OK) {
+      drain();
+      return s;
+    }
+    if (k_out) k_out[f] = c->last_k;
+    e = cudaEventRecord(c->ev_comp[slot], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->down, c->ev_comp[slot], 0);
+    const size_t lbytes = (size_t)nv[f] * 4;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_asc[f], io.asc, lbytes, cudaMemcpyDeviceToHost, c->down);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_desc[f], io.desc, lbytes, cudaMemcpyDeviceToHost, c->down);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_ms[f], io.ms, lbytes, cudaMemcpyDeviceToHost, c->down);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_down[slot], c->down);
+  }
+  drain();
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_status(e);
+  }
   finish_profile(c, l0);
   return MS_OK;
 }

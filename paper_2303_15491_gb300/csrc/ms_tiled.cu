@@ -562,7 +562,8 @@ __device__ __forceinline__ void number_tile_pairs(uint32_t *A, uint32_t *B, cons
       const uint32_t wd = dn >> 5, wu = kBmW + (up >> 5);
       const uint32_t di = PW[wd] + __popc(BW[wd] & ((1u << (dn & 31u)) - 1u));
       const uint32_t ui = PW[wu] + __popc(BW[wu] & ((1u << (up & 31u)) - 1u));
-      ts.pool_pair[pbase + i] = di | (ui << 16);
+      // the pair's two roots as indices into the global root list
+      ts.pool_pair[pbase + i] = make_uint2((uint32_t)(rbase + di), (uint32_t)(rbase + ui));
     }
   }
   if (rbase + (unsigned long long)nroots <= ts.root_cap) {
@@ -576,7 +577,8 @@ __device__ __forceinline__ void number_tile_pairs(uint32_t *A, uint32_t *B, cons
         while (bits) {
           const uint32_t b = (uint32_t)(__ffs(bits) - 1);
           bits &= bits - 1u;
-          ts.root_box[rbase + r] = (uint16_t)(box0 + b);
+          ts.root_box[rbase + r] = (uint16_t)(box0 + b) | (wi < kBmW ? (uint16_t)0 : kUpRoot);
+          if (ts.root_tile) ts.root_tile[rbase + r] = (uint32_t)gt;
           ++r;
         }
       }
@@ -1170,17 +1172,146 @@ __device__ __forceinline__ uint32_t chase_code(int e) {
          ((uint32_t)(dz + 1) << 16);
 }
 
-// Root chase (see launch_chase_roots).  A warp takes one tile at a time from
+// Root chase, flat over the root list (see launch_chase_roots; calls with
+// few tiles): a lane takes
+// roots r, r + T, r + 2T, ... (T threads in all) and keeps kInFlight chases
+// going at once, starting the next root in a chase's place as soon as it ends,
+// so that neither a long chain nor a tile with many roots holds up others.
+// A root knows its tile; its field is found from the tile.  kFlat: the 2D
+// tiles' roots, which follow the 3D tiles' in the list.
+constexpr int kChaseThreads = 512;
+constexpr int kInFlight = 4;
+
+template <bool kFlat, bool kSingle>
+__global__ void __launch_bounds__(kChaseThreads, 2) k_chase_flat(Batch bt, TiledScratch ts,
+                                                                  const int2 *__restrict__ graph,
+                                                                  long long probe_stride,
+                                                                  DevStatus *st) {
+  if (call_failed(st)) return;
+  extern __shared__ uint32_t LUT[];
+  constexpr int kE = kFlat ? k2Ext : kExt;
+  constexpr int TX = kFlat ? k2TX : kTX, TY = kFlat ? k2TY : kTY, TZ = kFlat ? 1 : kTZ;
+  constexpr int kFaceN = kFlat ? k2Face : kFace;
+  for (int e = threadIdx.x; e < kE; e += kChaseThreads) LUT[e] = chase_code<kFlat>(e);
+  __syncthreads();
+  const bool probe = probe_stride > 0;
+  const unsigned long long cap = ts.root_cap;
+  const unsigned long long r0 = kFlat ? min(ts.counters[2], cap) : 0ull;
+  const unsigned long long r1 = min(kFlat ? ts.counters[1] : ts.counters[2], cap);
+  const unsigned long long nroots = r1 > r0 ? r1 - r0 : 0ull;
+  const unsigned long long nwork =
+      probe ? (nroots + (unsigned long long)probe_stride - 1) / (unsigned long long)probe_stride : nroots;
+  const unsigned long long T = (unsigned long long)gridDim.x * kChaseThreads;
+  unsigned int sampled = 0, pending = 0, bad = 0;
+  // per chase in flight: its work item, root, field, tile, box index, hops
+  unsigned long long w[kInFlight];
+  uint32_t e[kInFlight];
+  int fi[kInFlight], tx[kInFlight], ty[kInFlight], tz[kInFlight], hops[kInFlight];
+  bool up[kInFlight];
+  unsigned long long next = (unsigned long long)blockIdx.x * kChaseThreads + threadIdx.x;
+  auto start = [&](int q) {
+    w[q] = next;
+    next += T;
+    if (w[q] >= nwork) return;
+    const unsigned long long r = r0 + (probe ? w[q] * (unsigned long long)probe_stride : w[q]);
+    const uint32_t b = ts.root_box[r];
+    const int64_t gt = ts.root_tile[r];
+    const int f = kSingle ? 0 : field_of(bt, gt);
+    const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[f];
+    uint32_t rr, x, y, z = 0;
+    if (kFlat) {
+      fd.g.div_tx.divmod((uint32_t)(gt - fd.tile_base), &y, &x);
+    } else {
+      fd.g.div_tx.divmod((uint32_t)(gt - fd.tile_base), &rr, &x);
+      fd.g.div_ty.divmod(rr, &z, &y);
+    }
+    fi[q] = f, tx[q] = (int)x, ty[q] = (int)y, tz[q] = (int)z;
+    e[q] = b & (uint32_t)(kUpRoot - 1);
+    up[q] = (b & kUpRoot) != 0;
+    hops[q] = 0;
+  };
+#pragma unroll
+  for (int q = 0; q < kInFlight; ++q) start(q);
+  for (;;) {
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < kInFlight; ++q) {
+      if (w[q] >= nwork) continue;
+      any = true;
+      const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi[q]];
+      const uint32_t code = LUT[e[q]];
+      int32_t label = 0;
+      bool done = false;
+      if (!(code & kHaloBit)) {  // inside its tile: the extremum
+        const uint32_t lx = code & 127u, ly = (code >> 7) & 63u, lz = (code >> 13) & 31u;
+        label = (int32_t)((uint32_t)(tx[q] * TX) + lx +
+                          (uint32_t)fd.g.nx * ((uint32_t)(ty[q] * TY) + ly +
+                                               (uint32_t)fd.g.ny * ((uint32_t)(tz[q] * TZ) + lz)));
+        done = true;
+      } else {
+        const int gtx = (int)fd.g.tx, gty = (int)fd.g.ty, gtz = (int)fd.g.tz;
+        const int ntx = tx[q] + (int)((code >> 12) & 3u) - 1;
+        const int nty = ty[q] + (int)((code >> 14) & 3u) - 1;
+        const int ntz = tz[q] + (int)((code >> 16) & 3u) - 1;
+        if ((unsigned)ntx >= (unsigned)gtx || (unsigned)nty >= (unsigned)gty ||
+            (unsigned)ntz >= (unsigned)gtz) {  // cannot happen: every root lies in the field
+          ++bad;
+          done = true;
+        } else {
+          const long long slot =
+              (fd.tile_base + (long long)ntx + (long long)gtx * (nty + (long long)gty * ntz)) * kFace +
+              (code & 0xfffu);
+          if (graph) {  // the jumped face graph knows where the path ends
+            const int2 gv = graph[slot];
+            const uint32_t f = (uint32_t)(up[q] ? gv.x : gv.y);
+            if (!(f & kSlotFinal)) atomicOr(&st->not_converged, 1u);
+            label = (int32_t)(f & ~kSlotFinal);
+            done = true;
+          } else {
+            const int64_t n = fd.g.nx * fd.g.ny * fd.g.nz;
+            const int64_t slots = fd.g.ntiles * (int64_t)kFaceN;
+            const int64_t max_hops = probe ? kProbeHops : (n < slots ? n : slots);
+            if (++hops[q] > max_hops) {
+              if (probe)
+                ++pending;
+              else
+                atomicOr(&st->not_converged, 1u);
+              done = true;
+            } else {
+              const uint32_t wv = __ldg(&ts.face[slot]);
+              e[q] = up[q] ? (wv & 0xffffu) : (wv >> 16);
+              tx[q] = ntx, ty[q] = nty, tz[q] = ntz;
+            }
+          }
+        }
+      }
+      if (done) {
+        if (probe)
+          ++sampled;
+        else
+          ts.root_label[r0 + w[q]] = label;
+        start(q);
+      }
+    }
+    if (!__any_sync(0xffffffffu, any)) break;
+  }
+  if (bad) atomicOr(&st->bad_index, 1u);
+  if (probe) {
+    if (sampled) atomicAdd(&st->sampled, sampled);
+    if (pending) atomicAdd(&st->pending, pending);
+  }
+}
+
+// Root chase, a tile a warp (see launch_chase_roots; calls with many tiles).
+// A warp takes one tile at a time from
 // a work queue; its lanes take the tile's roots in turn (lane l roots l,
 // l + 32, ...).  Each hop of a chase is one dependent load, so every lane
 // keeps kInFlight chases going at once, and a lane whose chase ends starts
 // its next root in that place: one long chain holds up no other chase.
 // kFlat: the 2D tiles (which follow the 3D ones).
-constexpr int kChaseThreads = 512;
-constexpr int kInFlight = 4;
 
 template <bool kFlat, bool kSingle>
-__global__ void __launch_bounds__(kChaseThreads) k_chase_roots(Batch bt, TiledScratch ts,
+__global__ void __launch_bounds__(kChaseThreads) k_chase_tiles(Batch bt, TiledScratch ts,
                                                                const int2 *__restrict__ graph,
                                                                long long probe_stride,
                                                                DevStatus *st) {
@@ -1232,13 +1363,13 @@ __global__ void __launch_bounds__(kChaseThreads) k_chase_roots(Batch bt, TiledSc
     uint32_t e[kInFlight];
     int tx[kInFlight], ty[kInFlight], tz[kInFlight], idx[kInFlight], hops[kInFlight];
     int next = lane + 32 * kInFlight;  // this lane's next root to start
-    uint32_t nb = next < nr ? (uint32_t)rb[next] : 0u;  // its box index, loaded ahead
+    uint32_t nb = next < nr ? ((uint32_t)rb[next] & (uint32_t)(kUpRoot - 1)) : 0u;  // its box index, loaded ahead
 #pragma unroll
     for (int q = 0; q < kInFlight; ++q) {
       idx[q] = lane + 32 * q;
       hops[q] = 0;
       tx[q] = tx0, ty[q] = ty0, tz[q] = tz0;
-      e[q] = idx[q] < nr ? (uint32_t)rb[idx[q]] : 0u;
+      e[q] = idx[q] < nr ? ((uint32_t)rb[idx[q]] & (uint32_t)(kUpRoot - 1)) : 0u;
     }
     for (;;) {
       bool any = false;
@@ -1294,7 +1425,7 @@ __global__ void __launch_bounds__(kChaseThreads) k_chase_roots(Batch bt, TiledSc
           idx[q] = next;
           e[q] = nb;
           next += 32;
-          nb = next < nr ? (uint32_t)rb[next] : 0u;
+          nb = next < nr ? ((uint32_t)rb[next] & (uint32_t)(kUpRoot - 1)) : 0u;
           hops[q] = 0;
           tx[q] = tx0, ty[q] = ty0, tz[q] = tz0;
         }
@@ -1352,16 +1483,37 @@ __device__ __forceinline__ void list_append(const RankScratch &rs, unsigned long
   if (slot == 0xffffffffu) atomicOr(&st->hash_overflow, 1u);
 }
 
-// Tile pairs (see launch_tile_pairs).  One warp per tile, taken from a work
-// queue: each tile pair's (asc, desc) from its two roots' labels; the tile's
-// distinct pairs -- a few dozen where the tile has about a thousand root
-// pairs -- are found in the warp's shared-memory set and only they are
-// inserted into the global set.  Lanes work on kPairBatch pairs at once, so
-// their loads overlap.  A tile with more distinct pairs than the warp's set
-// holds inserts the rest directly.
+// list_append for a converged warp: the lanes with inserted set true are
+// the ones that inserted (fresh: placed a new key); a failed insert (slot
+// 0xffffffff) flags the set as too small.
+__device__ __forceinline__ void list_append_warp(const RankScratch &rs, unsigned long long key, bool fresh,
+                                                 bool inserted, uint32_t slot, DevStatus *st) {
+  const unsigned int nm = __ballot_sync(0xffffffffu, fresh);
+  const int lane = threadIdx.x & 31;
+  if (nm) {
+    const int leader = __ffs(nm) - 1;
+    unsigned int base = 0;
+    if (lane == leader) base = atomicAdd(&st->n_unique, (unsigned int)__popc(nm));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (fresh) {
+      const unsigned int at = base + __popc(nm & ((1u << lane) - 1u));
+      if (at < rs.max_unique)
+        rs.list[at] = key;
+      else
+        atomicOr(&st->hash_overflow, 1u);
+    }
+  }
+  if (inserted && slot == 0xffffffffu) atomicOr(&st->hash_overflow, 1u);
+}
+
+// Tile pairs, flat over the pair pool (see launch_tile_pairs; calls with few
+// tiles): every tile
+// pair's (asc, desc) from its two roots' labels into the global set.  A lane
+// handles kPairBatch pairs at once (their loads overlap); lanes of a warp
+// holding the same pair -- mostly the same tile's pairs reaching the same
+// extrema -- insert it once (__match_any_sync), and every lane stores the
+// slot.  An overflowing set stops the pass early (the host retries larger).
 constexpr int kPairThreads = 256;
-constexpr int kWarpHash = 256;
-constexpr int kWarpProbes = 32;
 constexpr int kPairBatch = 8;
 
 __device__ __forceinline__ unsigned long long final_key(int key_mode, uint32_t fi, int32_t a, int32_t d) {
@@ -1370,6 +1522,68 @@ __device__ __forceinline__ unsigned long long final_key(int key_mode, uint32_t f
              : (((unsigned long long)(uint32_t)a << 32) | (uint32_t)d);
 }
 
+template <bool kSingle>
+__global__ void __launch_bounds__(kPairThreads) k_pairs_flat(Batch bt, TiledScratch ts, RankScratch rs,
+                                                             DevStatus *st) {
+  if (call_failed(st) || st->not_converged) return;
+  const int lane = threadIdx.x & 31;
+  const bool keep_ad = rs.capacity > kSetInL2;
+  const unsigned long long npairs = min(ts.counters[0], ts.pool_cap);
+  const unsigned long long nroots = min(ts.counters[1], ts.root_cap);
+  const unsigned long long step = (unsigned long long)gridDim.x * kPairThreads * kPairBatch;
+  unsigned int it = 0;
+  // the loop bound is the warp's first pair, so the whole warp iterates together
+  for (unsigned long long wb = (unsigned long long)blockIdx.x * kPairThreads * kPairBatch +
+                               (threadIdx.x & ~31u) * kPairBatch;
+       wb < npairs; wb += step) {
+    const unsigned long long p0 = wb + lane;
+    // a set found too small ends the pass; the flag is one word every warp
+    // would read, so it is read on every 8th iteration only
+    if ((it++ & 7u) == 0 && __shfl_sync(0xffffffffu, __ldcg(&st->hash_overflow), 0)) break;
+    uint2 pp[kPairBatch];
+#pragma unroll
+    for (int u = 0; u < kPairBatch; ++u)
+      pp[u] = p0 + 32 * u < npairs ? __ldcs(&ts.pool_pair[p0 + 32 * u]) : make_uint2(0u, 0u);
+    int32_t a[kPairBatch], d[kPairBatch];
+#pragma unroll
+    for (int u = 0; u < kPairBatch; ++u) {
+      const bool ok = p0 + 32 * u < npairs && pp[u].x < nroots && pp[u].y < nroots;
+      if (p0 + 32 * u < npairs && !ok) atomicOr(&st->bad_index, 1u);  // cannot happen
+      a[u] = ok ? __ldg(&ts.root_label[pp[u].x]) : 0;
+      d[u] = ok ? __ldg(&ts.root_label[pp[u].y]) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kPairBatch; ++u) {
+      const unsigned long long p = p0 + 32 * u;
+      const bool valid = p < npairs;
+      const uint32_t fi = (kSingle || !valid) ? 0u : (uint32_t)field_of(bt, ts.root_tile[pp[u].x]);
+      const unsigned long long key = valid ? final_key(bt.key_mode, fi, a[u], d[u]) : ~0ull;
+      const unsigned int peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      bool fresh = false;
+      uint32_t gs = 0;
+      if (valid && lane == leader) gs = global_insert(rs, key, &fresh);
+      list_append_warp(rs, key, fresh, valid && lane == leader, gs, st);
+      gs = __shfl_sync(0xffffffffu, gs, leader);
+      if (valid) {
+        ts.pool_slot[p] = gs;
+        if (keep_ad) ts.pool_ad[p] = make_int2(a[u], d[u]);
+      }
+    }
+  }
+}
+
+// Tile pairs, a tile a warp (see launch_tile_pairs; calls with many tiles),
+// taken from a work queue: each tile pair's (asc, desc) from its two roots' labels; the tile's
+// distinct pairs -- a few dozen where the tile has about a thousand root
+// pairs -- are found in the warp's shared-memory set and only they are
+// inserted into the global set.  Lanes work on kPairBatch pairs at once, so
+// their loads overlap.  A tile with more distinct pairs than the warp's set
+// holds inserts the rest directly.
+constexpr int kWarpHash = 256;
+constexpr int kWarpProbes = 8;
+constexpr int kWarpFill = kWarpHash * 3 / 4;  // entries past which the set takes no new keys
+
 __device__ __forceinline__ uint32_t warp_slot_of(unsigned long long key) {
   uint32_t h = ((uint32_t)key * 0x9E3779B1u) ^ ((uint32_t)(key >> 32) * 0x85EBCA77u);
   h ^= h >> 15;
@@ -1377,11 +1591,12 @@ __device__ __forceinline__ uint32_t warp_slot_of(unsigned long long key) {
 }
 
 template <bool kSingle>
-__global__ void __launch_bounds__(kPairThreads) k_tile_pairs(Batch bt, TiledScratch ts, RankScratch rs,
+__global__ void __launch_bounds__(kPairThreads) k_pairs_tiles(Batch bt, TiledScratch ts, RankScratch rs,
                                                              DevStatus *st) {
   if (call_failed(st) || st->not_converged) return;
   __shared__ unsigned long long HKs[kPairThreads / 32][kWarpHash];
   __shared__ uint32_t HSs[kPairThreads / 32][kWarpHash];
+  __shared__ int s_fill[kPairThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned long long *HK = HKs[wid];
   uint32_t *HS = HSs[wid];
@@ -1391,32 +1606,34 @@ __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(Batch bt, TiledScra
     if (lane == 0) k = (long long)atomicAdd(ts.queue + kQPairs, 1u);
     k = __shfl_sync(0xffffffffu, k, 0);
     if (k >= bt.total_tiles) break;
+    // a set found too small ends the pass (the host retries larger)
+    if (__shfl_sync(0xffffffffu, lane == 0 ? __ldcg(&st->hash_overflow) : 0u, 0)) break;
     const int64_t gt = k;
     const TileMeta m = ts.meta[gt];
     const uint32_t fi = kSingle ? 0u : (uint32_t)field_of(bt, gt);
     const uint32_t nr = (uint32_t)(m.nd + m.nu);
     const int np = m.npairs;
-    const uint32_t *__restrict__ pp_src = ts.pool_pair + m.pbase;
-    const int32_t *__restrict__ labels = ts.root_label + m.rbase;
+    const uint2 *__restrict__ pp_src = ts.pool_pair + m.pbase;
     for (int i = lane; i < kWarpHash; i += 32) HK[i] = ~0ull;
+    if (lane == 0) s_fill[wid] = 0;
     __syncwarp();
     auto label_of = [&](uint32_t r) -> int32_t {
-      if (r >= nr) {  // cannot happen for a pair the tile pass listed
+      if (r < m.rbase || r >= m.rbase + nr) {  // cannot happen for a pair the tile pass listed
         atomicOr(&st->bad_index, 1u);
         return 0;
       }
-      return __ldg(&labels[r]);  // written by the previous launch
+      return __ldg(&ts.root_label[r]);  // written by the previous launch
     };
     // pass 1: every pair into the warp's set (or, past it, the global set)
     for (int i0 = lane; i0 < np; i0 += 32 * kPairBatch) {
-      uint32_t pp[kPairBatch];
+      uint2 pp[kPairBatch];
       int32_t a[kPairBatch], d[kPairBatch];
 #pragma unroll
-      for (int u = 0; u < kPairBatch; ++u) pp[u] = i0 + 32 * u < np ? __ldg(&pp_src[i0 + 32 * u]) : 0u;
+      for (int u = 0; u < kPairBatch; ++u) pp[u] = i0 + 32 * u < np ? __ldg(&pp_src[i0 + 32 * u]) : make_uint2(0u, 0u);
 #pragma unroll
       for (int u = 0; u < kPairBatch; ++u) {
-        a[u] = i0 + 32 * u < np ? label_of(pp[u] & 0xffffu) : 0;
-        d[u] = i0 + 32 * u < np ? label_of(pp[u] >> 16) : 0;
+        a[u] = i0 + 32 * u < np ? label_of(pp[u].x) : 0;
+        d[u] = i0 + 32 * u < np ? label_of(pp[u].y) : 0;
       }
 #pragma unroll
       for (int u = 0; u < kPairBatch; ++u) {
@@ -1427,10 +1644,19 @@ __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(Batch bt, TiledScra
         bool placed = false;
         for (int probe = 0; probe < kWarpProbes; ++probe) {
           unsigned long long cur = HK[sl];
-          if (cur == ~0ull) cur = atomicCAS(&HK[sl], ~0ull, key);
-          if (cur == ~0ull || cur == key) {
+          if (cur == key) {
             placed = true;
             break;
+          }
+          if (cur == ~0ull) {
+            // a full set takes no new keys: its probe chains stay short
+            if (*(volatile int *)&s_fill[wid] >= kWarpFill) break;
+            cur = atomicCAS(&HK[sl], ~0ull, key);
+            if (cur == ~0ull) atomicAdd(&s_fill[wid], 1);
+            if (cur == ~0ull || cur == key) {
+              placed = true;
+              break;
+            }
           }
           sl = (sl + 1) & (kWarpHash - 1);
         }
@@ -1457,14 +1683,14 @@ __global__ void __launch_bounds__(kPairThreads) k_tile_pairs(Batch bt, TiledScra
     __syncwarp();
     // pass 2: every pair's set slot
     for (int i0 = lane; i0 < np; i0 += 32 * kPairBatch) {
-      uint32_t pp[kPairBatch];
+      uint2 pp[kPairBatch];
       int32_t a[kPairBatch], d[kPairBatch];
 #pragma unroll
-      for (int u = 0; u < kPairBatch; ++u) pp[u] = i0 + 32 * u < np ? __ldg(&pp_src[i0 + 32 * u]) : 0u;
+      for (int u = 0; u < kPairBatch; ++u) pp[u] = i0 + 32 * u < np ? __ldg(&pp_src[i0 + 32 * u]) : make_uint2(0u, 0u);
 #pragma unroll
       for (int u = 0; u < kPairBatch; ++u) {
-        a[u] = i0 + 32 * u < np ? label_of(pp[u] & 0xffffu) : 0;
-        d[u] = i0 + 32 * u < np ? label_of(pp[u] >> 16) : 0;
+        a[u] = i0 + 32 * u < np ? label_of(pp[u].x) : 0;
+        d[u] = i0 + 32 * u < np ? label_of(pp[u].y) : 0;
       }
 #pragma unroll
       for (int u = 0; u < kPairBatch; ++u) {
@@ -1596,6 +1822,14 @@ __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch 
   }
 }
 
+}  // namespace
+
+bool tile_mode(const Batch &b) {
+  return b.tune.resolve_mode == 0 || (b.tune.resolve_mode < 0 && b.total_tiles >= kTileModeMin);
+}
+
+namespace {
+
 int sms() {
   int dev = 0, n = 152;
   cudaGetDevice(&dev);
@@ -1626,7 +1860,9 @@ TileGeom tile_geom(const int64_t dims[3]) {
 size_t tiled_scratch_bytes(long long total_tiles, int n_fields, unsigned long long pool_cap,
                            unsigned long long root_cap) {
   auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  return r(256) + r((size_t)pool_cap * 4) * 2 + r((size_t)pool_cap * 8) + r((size_t)root_cap * 2) +
+  return r(256) + r((size_t)pool_cap * 8) + r((size_t)pool_cap * 4) + r((size_t)pool_cap * 8) +
+         r((size_t)root_cap * 2) +
+         r((size_t)root_cap * 4) +
          r((size_t)root_cap * 4) + r((size_t)total_tiles * sizeof(TileMeta)) + r((size_t)n_fields * 4) +
          r((size_t)total_tiles * kFace * 4) + r((size_t)total_tiles * kTileV * 2);
 }
@@ -1641,11 +1877,12 @@ void tiled_scratch_carve(void *base, long long total_tiles, int n_fields,
     return q;
   };
   ts->counters = reinterpret_cast<unsigned long long *>(take(256));
-  ts->queue = reinterpret_cast<unsigned int *>(ts->counters + 2);
-  ts->pool_pair = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
+  ts->queue = reinterpret_cast<unsigned int *>(ts->counters + 3);
+  ts->pool_pair = reinterpret_cast<uint2 *>(take((size_t)pool_cap * 8));
   ts->pool_slot = reinterpret_cast<uint32_t *>(take((size_t)pool_cap * 4));
   ts->pool_ad = reinterpret_cast<int2 *>(take((size_t)pool_cap * 8));
   ts->root_box = reinterpret_cast<uint16_t *>(take((size_t)root_cap * 2));
+  ts->root_tile = reinterpret_cast<uint32_t *>(take((size_t)root_cap * 4));
   ts->root_label = reinterpret_cast<int32_t *>(take((size_t)root_cap * 4));
   ts->meta = reinterpret_cast<TileMeta *>(take((size_t)total_tiles * sizeof(TileMeta)));
   ts->fstart = reinterpret_cast<uint32_t *>(take((size_t)n_fields * 4));
@@ -1727,7 +1964,7 @@ bool capturing(cudaStream_t s) {
 cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus *st,
                               cudaStream_t s) {
   // the pool and root counters and the work-queue counters after them
-  cudaError_t e = cudaMemsetAsync(ts.counters, 0, 2 * sizeof(unsigned long long) + kQueues * sizeof(unsigned int), s);
+  cudaError_t e = cudaMemsetAsync(ts.counters, 0, 3 * sizeof(unsigned long long) + kQueues * sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   if (b.tiles3 > 0) {
     constexpr int kSmem = 2 * kExt * 4;
@@ -1740,6 +1977,10 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
     ++tl_launches;
     kern<<<(unsigned)grid, kThreads, kSmem, s>>>(b, ts, st);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the 3D tiles' roots come first in the root list
+    e = cudaMemcpyAsync(ts.counters + 2, ts.counters + 1, sizeof(unsigned long long),
+                        cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return e;
   }
   if (b.total_tiles > b.tiles3) {
@@ -1759,33 +2000,50 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
 
 cudaError_t launch_chase_roots(const Batch &b, const TiledScratch &ts, const int2 *graph,
                                long long probe_stride, DevStatus *st, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(ts.queue + kQChase, 0, 2 * sizeof(unsigned int), s);
+  const bool tiles = tile_mode(b);
+  cudaError_t e = cudaSuccess;
+  if (tiles) e = cudaMemsetAsync(ts.queue + kQChase, 0, 2 * sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
-  constexpr int kWarps = kChaseThreads / 32;
   for (int flat = 0; flat < 2; ++flat) {
     const long long n = flat ? b.total_tiles - b.tiles3 : b.tiles3;
     if (n == 0) continue;
-    const long long tiles = probe_stride > 0 ? (n + probe_stride - 1) / probe_stride : n;
-    const long long blocks =
-        std::min<long long>((long long)sms() * b.tune.chase_blocks, (tiles + kWarps - 1) / kWarps);
     const size_t smem = (size_t)(flat ? k2Ext : kExt) * 4;
+    // the probe samples every probe_stride-th root (flat) or tile (a tile a
+    // warp): either way about kProbeRoots roots, as a tile holds about
+    // nroots / tiles of them
+    const long long stride = probe_stride;
+    const long long work = tiles ? (stride > 0 ? (n + stride - 1) / stride : n) : 0;
     ++tl_launches;
-    if (flat) {
-      auto kern = b.n_fields == 1 ? k_chase_roots<true, true> : k_chase_roots<true, false>;
+    auto go = [&](auto kern) -> cudaError_t {
       if (!capturing(s)) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        const cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (r != cudaSuccess) return r;
       }
-      kern<<<(unsigned)blocks, kChaseThreads, smem, s>>>(b, ts, graph, probe_stride, st);
-    } else {
-      auto kern = b.n_fields == 1 ? k_chase_roots<false, true> : k_chase_roots<false, false>;
-      if (!capturing(s)) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+      // a tile a warp: up to chase_blocks blocks an SM, no more warps than
+      // tiles; flat: every thread strides over the roots, so exactly the
+      // blocks that are resident at once
+      long long blocks;
+      if (tiles) {
+        blocks = std::max<long long>(1, std::min<long long>((long long)sms() * b.tune.chase_blocks,
+                                                            (work + kChaseThreads / 32 - 1) / (kChaseThreads / 32)));
+      } else {
+        int per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kChaseThreads, smem) != cudaSuccess ||
+            per_sm < 1)
+          per_sm = 1;
+        cudaGetLastError();
+        blocks = (long long)sms() * std::min(per_sm, b.tune.chase_blocks);
       }
-      kern<<<(unsigned)blocks, kChaseThreads, smem, s>>>(b, ts, graph, probe_stride, st);
-    }
-    e = cudaGetLastError();
+      kern<<<(unsigned)blocks, kChaseThreads, smem, s>>>(b, ts, graph, stride, st);
+      return cudaGetLastError();
+    };
+    const bool one = b.n_fields == 1;
+    if (tiles)
+      e = flat ? (one ? go(k_chase_tiles<true, true>) : go(k_chase_tiles<true, false>))
+               : (one ? go(k_chase_tiles<false, true>) : go(k_chase_tiles<false, false>));
+    else
+      e = flat ? (one ? go(k_chase_flat<true, true>) : go(k_chase_flat<true, false>))
+               : (one ? go(k_chase_flat<false, true>) : go(k_chase_flat<false, false>));
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -1797,14 +2055,29 @@ cudaError_t launch_tile_pairs(const Batch &b, const TiledScratch &ts, const Rank
   if (clear_table) e = cudaMemsetAsync(rs.table_keys, 0xff, (size_t)rs.capacity * 8, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(ts.queue + kQPairs, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess || b.total_tiles == 0) return e;
-  constexpr int kWarps = kPairThreads / 32;
-  const long long blocks = std::min<long long>((b.total_tiles + kWarps - 1) / kWarps,
-                                               (long long)sms() * b.tune.pair_blocks);
   ++tl_launches;
-  if (b.n_fields == 1)
-    k_tile_pairs<true><<<(unsigned)blocks, kPairThreads, 0, s>>>(b, ts, rs, st);
-  else
-    k_tile_pairs<false><<<(unsigned)blocks, kPairThreads, 0, s>>>(b, ts, rs, st);
+  if (tile_mode(b)) {
+    constexpr int kWarps = kPairThreads / 32;
+    const long long blocks = std::min<long long>((b.total_tiles + kWarps - 1) / kWarps,
+                                                 (long long)sms() * b.tune.pair_blocks);
+    if (b.n_fields == 1)
+      k_pairs_tiles<true><<<(unsigned)blocks, kPairThreads, 0, s>>>(b, ts, rs, st);
+    else
+      k_pairs_tiles<false><<<(unsigned)blocks, kPairThreads, 0, s>>>(b, ts, rs, st);
+  } else {
+    // every thread strides over the pool: the blocks resident at once
+    auto kern = b.n_fields == 1 ? k_pairs_flat<true> : k_pairs_flat<false>;
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPairThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    cudaGetLastError();
+    const unsigned long long per_block = (unsigned long long)kPairThreads * kPairBatch;
+    const long long blocks = (long long)std::max<unsigned long long>(
+        1, std::min<unsigned long long>((ts.pool_cap + per_block - 1) / per_block,
+                                        (unsigned long long)sms() * std::min(per_sm, b.tune.pair_blocks)));
+    kern<<<(unsigned)blocks, kPairThreads, 0, s>>>(b, ts, rs, st);
+  }
   return cudaGetLastError();
 }
 

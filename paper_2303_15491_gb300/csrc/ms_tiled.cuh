@@ -87,9 +87,19 @@ struct Tuning {
   int tile_ctas = 2;     // tile kernels: CTAs per SM (2 fit an SM)
   int write_ctas = 4;    // write kernels: CTAs per SM
   int chase_blocks = 3;  // root chase: 512-thread blocks (16 warps) per SM
-  int pair_blocks = 7;   // tile pairs: 256-thread blocks (a tile a warp) per SM
+  int pair_blocks = 8;   // tile pairs: 256-thread blocks per SM
   int dynamic = 1;       // tile and write kernels: a work queue (1) or a static stride (0)
+  int resolve_mode = -1;  // root chase and tile pairs: a tile a warp (0), flat over the root
+                          // list and pair pool (1), or by tile count (-1, see tile_mode)
 };
+// Calls with at least this many tiles resolve a tile a warp when the mode is
+// left to the tile count: enough tiles keep every warp busy, and a warp then
+// deduplicates its tile's pairs before the global set.  Fewer tiles resolve
+// flat, which spreads a tile's roots and pairs over many warps.
+constexpr long long kTileModeMin = 2048;
+
+struct Batch;
+bool tile_mode(const Batch &b);
 
 struct Batch {
   const FieldDesc *fields;    // n_fields descriptors
@@ -113,20 +123,25 @@ struct TileMeta {
 };
 
 struct TiledScratch {
-  unsigned long long *counters;  // [0] pairs reserved by all tiles, [1] roots
+  unsigned long long *counters;  // [0] pairs reserved by all tiles, [1] roots, [2] roots of
+                                 // the 3D tiles (which come first in the root list)
   unsigned int *queue;           // work-queue counters (kQueues)
   unsigned long long pool_cap;   // pair-pool entries
   unsigned long long root_cap;   // root-list entries
-  uint32_t *pool_pair;  // per tile pair: dn-root index | up-root index << 16 (in the tile's root list)
+  uint2 *pool_pair;     // per tile pair: its dn root and up root (indices into the root list)
   uint32_t *pool_slot;  // per tile pair: slot of its (asc, desc) pair in the global pair set
   int2 *pool_ad;        // per tile pair: its (asc, desc), kept when the set exceeds kSetInL2 entries
-  uint16_t *root_box;   // per tile root: its extended-box index
+  uint16_t *root_box;   // per tile root: its extended-box index | kUpRoot if an up root
+  uint32_t *root_tile;  // per tile root: its tile (global index)
   int32_t *root_label;  // per tile root: the extremum its path reaches
   TileMeta *meta;       // per tile
   uint32_t *fstart;     // per field: index of its first pair in the sorted pair list
   uint32_t *face;       // per tile kFace words: up-root | dn-root << 16 (extended-box indices)
   uint16_t *pid;        // per tile kTileV pair numbers; the 16 of a thread's run are contiguous
 };
+// The root list: dn and up roots of a tile, the latter flagged.
+constexpr uint16_t kUpRoot = 0x8000u;
+static_assert(kExt < kUpRoot, "box indices leave the top bit free");
 // Work-queue counters: tile pass 3D / 2D, write 3D / 2D, root chase 3D / 2D, tile pairs.
 enum { kQTile3 = 0, kQTile2 = 1, kQWrite3 = 2, kQWrite2 = 3, kQChase = 4, kQChase2 = 5, kQPairs = 6,
        kQueues = 8 };
@@ -147,14 +162,14 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
                               cudaStream_t s);
 // Root chase: every tile root is followed from face to face (or looked up in
 // the jumped face graph when `graph` is given) to the extremum it leads to.
-// Probe form (probe_stride > 0): only every probe_stride-th tile, at most
+// Probe form (probe_stride > 0): only every probe_stride-th root, at most
 // kProbeHops hops a root, counting in st->pending the roots that need more
-// and in st->n_max the roots sampled; no labels are stored.
+// and in st->sampled the roots sampled; no labels are stored.
 constexpr int kProbeHops = 4;
 // The probe runs when a call has at least kProbeMinRoots roots, on about
-// kProbeTiles tiles.
+// kProbeRoots of them (every probe_stride-th root of the list).
 constexpr unsigned long long kProbeMinRoots = 65536;
-constexpr long long kProbeTiles = 512;
+constexpr unsigned long long kProbeRoots = 16384;
 cudaError_t launch_chase_roots(const Batch &b, const TiledScratch &ts, const int2 *graph,
                                long long probe_stride, DevStatus *st, cudaStream_t s);
 // Tile pairs: each tile pair's (asc, desc) from its roots' labels, the tile's
