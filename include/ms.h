@@ -265,6 +265,42 @@ ms_status ms_simplex_geometry(ms_ctx *ctx, const int32_t *labels, const int64_t 
                               const int64_t *cell_offsets, int64_t total, float *points,
                               int32_t *pairs);
 
+/* ---- after the segmentation: persistence pairs of the extrema ----------------- */
+
+/* Sec. 4.1 (topological simplification by persistence, with the thresholds of
+ * Sec. 6): the 0-dimensional persistence pairs of the minima (direction -1)
+ * or maxima (+1), computed from the basins of a segmentation of the same
+ * field -- the ascending labels (out_asc of ms_segment) for minima, the
+ * descending ones (out_desc) for maxima.
+ *   Vertices enter in increasing (value, index) order for minima, decreasing
+ *   for maxima (Sec. 4.1's total order); a vertex with no earlier neighbour
+ *   starts a component, its extremum; a vertex joining several components
+ *   ends all but the one whose extremum entered first (the elder rule), and
+ *   each ended extremum dies at that vertex.  The extremum that enters first
+ *   never dies.  Its persistence is |f(death) - f(extremum)|.
+ * field, dims, dtype: as ms_segment (device).  labels: int32[n], device; every
+ * label must be an extremum's own label (labels[labels[v]] == labels[v]),
+ * else MS_ERR_INVALID_ARG.  extremum, death: int32[capacity], device; pair i
+ * is (extremum[i], death[i]) with the extrema in increasing vertex index and
+ * death -1 for the one that never dies.  *info (host, may be NULL) receives
+ * the counts; n_extrema is set also when it exceeds capacity
+ * (MS_ERR_TOO_LARGE, nothing written), so capacity 0 asks for the count.
+ * The labels are trusted to be the segmentation of this field: other labels
+ * give other pairs, never an out-of-range access.  Errors: MS_ERR_INVALID_ARG,
+ * MS_ERR_UNSUPPORTED_DTYPE, MS_ERR_TOO_LARGE (also more than 2^30 distinct
+ * basin pairs), MS_ERR_NAN_INPUT, MS_ERR_OUT_OF_MEMORY, MS_ERR_CUDA. */
+typedef struct {
+  int64_t n_extrema;    /* pairs (extrema) */
+  int64_t basin_edges;  /* distinct pairs of adjacent basins */
+  int32_t rounds;       /* parallel merge rounds that ran */
+  int32_t pad;
+  int64_t finish_edges; /* edges left to the one-thread finish in entry order (0: none) */
+} ms_persistence_info;
+
+ms_status ms_persistence(ms_ctx *ctx, const void *field, const int64_t dims[3], ms_dtype dtype,
+                         const int32_t *labels, int direction, int32_t *extremum, int32_t *death,
+                         int64_t capacity, ms_persistence_info *info);
+
 /* ---- serving ---------------------------------------------------------------- */
 
 /* A request loop for segmentations of mixed sizes.  The server owns n_slots

@@ -27,7 +27,7 @@ __all__ = [
     "ms_pair_rank_noalloc", "MS_NOALLOC_MAX_N", "ms_segment_batch", "ms_server_create",
     "ms_server_submit", "ms_server_wait", "ms_server_stats", "ms_server_destroy",
     "ms_batch_autotune", "ms_batch_graphs", "ms_simplex_index", "ms_simplex_geometry",
-    "simplex_cells", "ms_segment_host_many",
+    "simplex_cells", "ms_segment_host_many", "ms_persistence", "persistence",
 ]
 
 MS_F32, MS_F16 = 0, 1
@@ -42,6 +42,7 @@ EXPORTED_SYMBOLS = [
     "ms_pair_rank_noalloc", "ms_segment_batch", "ms_server_create", "ms_server_submit",
     "ms_server_wait", "ms_server_stats", "ms_server_destroy", "ms_batch_autotune",
     "ms_batch_graphs", "ms_simplex_index", "ms_simplex_geometry", "ms_segment_host_many",
+    "ms_persistence",
 ]
 MS_NOALLOC_MAX_N = 262144
 
@@ -51,6 +52,11 @@ class _Tuning(ctypes.Structure):
                 ("chase_blocks", ctypes.c_int), ("pair_blocks", ctypes.c_int),
                 ("dynamic", ctypes.c_int), ("resolve_mode", ctypes.c_int), ("default_ms", ctypes.c_double),
                 ("best_ms", ctypes.c_double)]
+
+
+class _PersistenceInfo(ctypes.Structure):
+    _fields_ = [("n_extrema", ctypes.c_int64), ("basin_edges", ctypes.c_int64),
+                ("rounds", ctypes.c_int32), ("pad", ctypes.c_int32), ("finish_edges", ctypes.c_int64)]
 
 
 class _ServerInfo(ctypes.Structure):
@@ -104,6 +110,8 @@ def load(build: bool = True) -> ctypes.CDLL:
             L.ms_simplex_index.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_i64p]
             L.ms_simplex_geometry.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, ctypes.c_int64,
                                               c_vp, c_vp]
+            L.ms_persistence.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, ctypes.c_int, c_vp,
+                                         c_vp, ctypes.c_int64, ctypes.POINTER(_PersistenceInfo)]
             L.ms_server_create.argtypes = [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_size_t,
                                            ctypes.c_int]
             L.ms_server_submit.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp,
@@ -252,6 +260,42 @@ def simplex_cells(dims):
     if nz == 1:
         return max(nx - 1, 0) * max(ny - 1, 0), 2
     return max(nx - 1, 0) * max(ny - 1, 0) * max(nz - 1, 0), 6
+
+
+def ms_persistence(ctx, field, dims, dtype, labels, direction, extremum, death, capacity) -> dict:
+    """Persistence pairs of the minima (direction -1, labels = asc) or maxima
+    (+1, labels = desc) into ``extremum`` / ``death`` (int32 device buffers of
+    ``capacity`` entries).  Returns the info counts; raises MSError
+    (MS_ERR_TOO_LARGE with ``.info`` set) when capacity is too small."""
+    info = _PersistenceInfo()
+    st = load().ms_persistence(ctx, _ptr(field), _dims(dims), int(dtype), _ptr(labels), int(direction),
+                               _ptr(extremum), _ptr(death), int(capacity), ctypes.byref(info))
+    out = {k: int(getattr(info, k)) for k in ("n_extrema", "basin_edges", "rounds", "finish_edges")}
+    if st != 0:
+        err = MSError(st, "ms_persistence")
+        err.info = out
+        raise err
+    return out
+
+
+def persistence(ctx, field, labels, direction: int = -1):
+    """(extremum, death, info) of a device field and its asc (minima) or desc
+    (maxima) labels; extremum and death are int32 device tensors."""
+    import torch
+    dims, dt = dims_of(field), dtype_code(field)
+    cap = min(field.numel(), 1 << 20)
+    for _ in range(2):
+        ext = torch.empty(max(cap, 1), dtype=torch.int32, device=field.device)
+        dth = torch.empty_like(ext)
+        try:
+            info = ms_persistence(ctx, field, dims, dt, labels, direction, ext, dth, cap)
+        except MSError as e:
+            if e.status != 3 or not getattr(e, "info", None) or e.info["n_extrema"] <= cap:
+                raise
+            cap = e.info["n_extrema"]
+            continue
+        return ext[:info["n_extrema"]], dth[:info["n_extrema"]], info
+    raise RuntimeError("ms_persistence: extremum count changed between calls")
 
 
 def ms_batch_graphs(ctx, on: bool = True) -> None:

@@ -58,6 +58,11 @@ struct ms_ctx {
   size_t graph_bytes = 0;
   void *sxscratch = nullptr;  // index-pass block totals and bases
   size_t sxscratch_bytes = 0;
+  void *pscratch = nullptr;   // persistence pairing working memory
+  size_t pscratch_bytes = 0;
+  void *pcount = nullptr;     // its pinned counter copy
+  uint64_t pers_pairs_hint = 0;   // basin-pair capacity that sufficed last time
+  uint64_t pers_minima_hint = 0;  // extremum capacity that sufficed last time
   unsigned long long *hcount = nullptr;  // pinned copies of the tile pass's pair and root counts
   unsigned long long pool_hint = 0;      // pair-pool capacity that sufficed last time
   unsigned long long root_hint = 0;      // root-list capacity that sufficed last time
@@ -846,7 +851,7 @@ namespace msseg {
 
 size_t ctx_resident_bytes(const ms_ctx *c) {
   return c->scratch_bytes + c->io_bytes + c->io2_bytes + c->tscratch_bytes + c->graph_bytes +
-         c->sxscratch_bytes + c->batch_dev_bytes + sizeof(DevStatus);
+         c->sxscratch_bytes + c->pscratch_bytes + c->batch_dev_bytes + sizeof(DevStatus);
 }
 
 void ctx_release_scratch(ms_ctx *c) {
@@ -854,10 +859,11 @@ void ctx_release_scratch(ms_ctx *c) {
   cudaStreamSynchronize(c->stream);
   for (BatchPlan &P : c->plans) drop_graph(&P);
   void **bufs[] = {&c->scratch, &c->io, &c->io2, &c->tscratch, &c->graph, &c->sxscratch,
-                   &c->batch_dev};
+                   &c->pscratch, &c->batch_dev};
   size_t *sizes[] = {&c->scratch_bytes, &c->io_bytes, &c->io2_bytes, &c->tscratch_bytes,
-                     &c->graph_bytes, &c->sxscratch_bytes, &c->batch_dev_bytes};
-  for (int i = 0; i < 7; ++i) {
+                     &c->graph_bytes, &c->sxscratch_bytes, &c->pscratch_bytes,
+                     &c->batch_dev_bytes};
+  for (int i = 0; i < 8; ++i) {
     if (*bufs[i]) cudaFree(*bufs[i]);
     *bufs[i] = nullptr;
     *sizes[i] = 0;
@@ -925,6 +931,8 @@ ms_status ms_destroy(ms_ctx *c) {
   if (c->tscratch) cudaFree(c->tscratch);
   if (c->graph) cudaFree(c->graph);
   if (c->sxscratch) cudaFree(c->sxscratch);
+  if (c->pscratch) cudaFree(c->pscratch);
+  if (c->pcount) cudaFreeHost(c->pcount);
   if (c->batch_dev) cudaFree(c->batch_dev);
   if (c->batch_host) cudaFreeHost(c->batch_host);
   if (c->hcount) cudaFreeHost(c->hcount);
@@ -1099,6 +1107,95 @@ ms_status ms_simplex_geometry(ms_ctx *c, const int32_t *labels, const int64_t di
   if (c->hst->bad_index) return MS_ERR_INVALID_ARG;  // offsets or total do not match the labels
   finish_profile(c, l0);
   return MS_OK;
+}
+
+ms_status ms_persistence(ms_ctx *c, const void *field, const int64_t dims[3], ms_dtype dtype,
+                         const int32_t *labels, int direction, int32_t *extremum, int32_t *death,
+                         int64_t capacity, ms_persistence_info *info) {
+  if (!c || !field || !labels || (direction != 1 && direction != -1) || capacity < 0)
+    return MS_ERR_INVALID_ARG;
+  int64_t n = 0;
+  ms_status s = check_dims(dims, &n);
+  if (s != MS_OK) return s;
+  s = check_dtype(dtype);
+  if (s != MS_OK) return s;
+  DeviceGuard g(c->device);
+  if (!is_device_pointer(field) || !is_device_pointer(labels)) return MS_ERR_INVALID_ARG;
+  if (capacity > 0 && (!is_device_pointer(extremum) || !is_device_pointer(death)))
+    return MS_ERR_INVALID_ARG;
+  const uintptr_t align = dtype == MS_F16 ? 1 : 3;
+  if ((reinterpret_cast<uintptr_t>(field) & align) || (reinterpret_cast<uintptr_t>(labels) & 3) ||
+      (reinterpret_cast<uintptr_t>(extremum) & 3) || (reinterpret_cast<uintptr_t>(death) & 3))
+    return MS_ERR_INVALID_ARG;
+  if (!c->pcount) {
+    if (cudaMallocHost(&c->pcount, persist_counters_bytes()) != cudaSuccess) {
+      cudaGetLastError();
+      return MS_ERR_OUT_OF_MEMORY;
+    }
+  }
+  // capacities: first from the last call (within this field's bounds), else
+  // from the field's size; grown by 4x while a pass reports them full
+  const uint64_t pair_bound = std::min<uint64_t>(1ull << 30, (uint64_t)n * (dims[2] > 1 ? 7 : 3));
+  const uint64_t min_bound = (uint64_t)n;
+  uint64_t pairs = std::max<uint64_t>(c->pers_pairs_hint, std::max<int64_t>(4096, n / 32));
+  uint64_t minima = std::max<uint64_t>(c->pers_minima_hint, std::max<int64_t>(1024, n / 32));
+  pairs = std::max<uint64_t>(1, std::min(pairs, pair_bound));
+  minima = std::max<uint64_t>(1, std::min(minima, min_bound));
+  const long long l0 = tl_launches;
+  for (;;) {
+    s = ensure_buffer(c, &c->pscratch, &c->pscratch_bytes, persist_scratch_bytes(pairs, minima));
+    if (s != MS_OK) return s;
+    PersistCall P{};
+    P.field = field;
+    P.dtype = dtype;
+    P.labels = labels;
+    for (int i = 0; i < 3; ++i) P.dims[i] = dims[i];
+    P.n = n;
+    P.direction = direction;
+    P.extremum = extremum;
+    P.death = death;
+    P.capacity = capacity;
+    P.max_pairs = pairs;
+    P.max_minima = minima;
+    P.min_rounds = 4;
+    PersistOutcome o;
+    StageTimer t0(c, MS_STAGE_RESOLVE);
+    MS_TRY(persist_run(P, c->pscratch, c->pcount, c->stream, &o));
+    t0.stop();
+    switch (o.kind) {
+      case PersistOutcome::kNan:
+        return MS_ERR_NAN_INPUT;
+      case PersistOutcome::kBadLabels:
+        return MS_ERR_INVALID_ARG;
+      case PersistOutcome::kGrow:
+        if (o.n_minima > minima) minima = std::min(min_bound, std::max(minima * 4, o.n_minima));
+        if (o.pairs_full) {
+          if (pairs >= pair_bound) return MS_ERR_TOO_LARGE;
+          pairs = std::min(pair_bound, std::max(pairs * 4, o.n_pairs));
+        }
+        continue;
+      case PersistOutcome::kTooSmall:
+        if (info) {
+          *info = ms_persistence_info{};
+          info->n_extrema = (int64_t)o.n_minima;
+          info->basin_edges = (int64_t)o.n_pairs;
+        }
+        return MS_ERR_TOO_LARGE;
+      case PersistOutcome::kDone:
+        break;
+    }
+    c->pers_pairs_hint = pairs;
+    c->pers_minima_hint = minima;
+    if (info) {
+      *info = ms_persistence_info{};
+      info->n_extrema = (int64_t)o.n_minima;
+      info->basin_edges = (int64_t)o.n_pairs;
+      info->rounds = o.rounds;
+      info->finish_edges = (int64_t)o.finish_edges;
+    }
+    finish_profile(c, l0);
+    return MS_OK;
+  }
 }
 
 ms_status ms_batch_graphs(ms_ctx *c, int on) {

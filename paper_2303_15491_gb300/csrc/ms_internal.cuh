@@ -36,6 +36,17 @@ __host__ __device__ __forceinline__ uint32_t order_key_bits(uint32_t b) {
   return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
+// 64-bit finaliser of MurmurHash3 (Appleby): spreads a packed key over an
+// open-addressing table.
+__device__ __forceinline__ unsigned long long hash_mix64(unsigned long long k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return k;
+}
+
 __host__ __device__ __forceinline__ bool is_nan_bits(uint32_t b) {
   return (b & 0x7fffffffu) > 0x7f800000u;
 }
@@ -89,6 +100,8 @@ constexpr int kSortBlocks = 240;
 // size.  Sets sized from an exact bound probe up to their capacity.
 constexpr unsigned int kEstimateProbeLimit = 256;
 size_t rank_scratch_bytes(unsigned int capacity);
+// Most blocks a sort pass over up to capacity / 2 keys uses.
+unsigned int sort_blocks_cap_of(unsigned int capacity);
 void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs);
 cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t n,
                                 const RankScratch &rs, DevStatus *st, cudaStream_t s);
@@ -115,5 +128,36 @@ cudaError_t launch_simplex_index(const int32_t *labels, const int64_t dims[3], i
 cudaError_t launch_simplex_geometry(const int32_t *labels, const int64_t dims[3], int mode,
                                     const int64_t *offsets, int64_t total, float *points,
                                     int32_t *pairs, DevStatus *st, cudaStream_t s);
+
+// 0-dimensional persistence pairing from the basin graph (ms_persist.cu).
+struct PersistCall {
+  const void *field;
+  int dtype;
+  const int32_t *labels;
+  int64_t dims[3];
+  int64_t n;
+  int direction;          // -1 minima, +1 maxima
+  int32_t *extremum;      // capacity entries, device
+  int32_t *death;         // capacity entries, device
+  int64_t capacity;
+  uint64_t max_pairs;     // basin pairs the scratch holds
+  uint64_t max_minima;    // extrema the scratch holds
+  int min_rounds;         // parallel rounds before a stalled call finishes in order
+};
+struct PersistOutcome {
+  enum Kind { kDone, kGrow, kTooSmall, kBadLabels, kNan };
+  Kind kind = kDone;
+  uint64_t n_minima = 0;  // extrema found (a lower bound after kGrow)
+  uint64_t n_pairs = 0;   // basin pairs found (a lower bound after kGrow)
+  bool pairs_full = false;
+  int rounds = 0;
+  uint64_t finish_edges = 0;  // edges left to the in-order finish (0: none)
+};
+size_t persist_scratch_bytes(uint64_t max_pairs, uint64_t max_minima);
+size_t persist_counters_bytes();
+// Runs the pairing on stream s (synchronising it between steps);
+// host_counters: pinned, persist_counters_bytes() long.
+cudaError_t persist_run(const PersistCall &P, void *scratch, void *host_counters, cudaStream_t s,
+                        PersistOutcome *out);
 
 }  // namespace msseg

@@ -22,22 +22,12 @@ __device__ __forceinline__ unsigned long long pack_pair(int32_t a, int32_t d) {
   return ((unsigned long long)(uint32_t)a << 32) | (uint32_t)d;
 }
 
-// 64-bit finaliser of MurmurHash3 (Appleby): spreads the pair over the table.
-__device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
-  k ^= k >> 33;
-  k *= 0xff51afd7ed558ccdull;
-  k ^= k >> 33;
-  k *= 0xc4ceb9fe1a85ec53ull;
-  k ^= k >> 33;
-  return k;
-}
-
 __device__ __forceinline__ unsigned int lane_id() { return threadIdx.x & 31u; }
 
 __device__ void table_insert(const RankScratch &rs, unsigned long long key, DevStatus *st) {
   if (*(volatile unsigned int *)&st->hash_overflow) return;  // the caller retries larger
   const unsigned int mask = rs.capacity - 1u;
-  unsigned int slot = (unsigned int)mix64(key) & mask;
+  unsigned int slot = (unsigned int)hash_mix64(key) & mask;
   for (unsigned int probe = 0; probe < rs.probe_limit; ++probe) {
     unsigned long long cur = *(volatile unsigned long long *)&rs.table_keys[slot];
     if (cur == key) return;
@@ -60,7 +50,7 @@ __device__ void table_insert(const RankScratch &rs, unsigned long long key, DevS
 
 __device__ __forceinline__ int table_find(const RankScratch &rs, unsigned long long key) {
   const unsigned int mask = rs.capacity - 1u;
-  unsigned int slot = (unsigned int)mix64(key) & mask;
+  unsigned int slot = (unsigned int)hash_mix64(key) & mask;
   for (unsigned int probe = 0; probe < rs.capacity; ++probe) {
     const unsigned long long cur = __ldg(&rs.table_keys[slot]);
     if (cur == key) return (int)slot;

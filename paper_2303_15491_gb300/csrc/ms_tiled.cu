@@ -1123,16 +1123,6 @@ __global__ void k_face_graph_round(Batch bt, int2 *__restrict__ graph, int round
 
 
 
-// 64-bit finaliser of MurmurHash3 (Appleby).
-__device__ __forceinline__ unsigned long long mix64t(unsigned long long k) {
-  k ^= k >> 33;
-  k *= 0xff51afd7ed558ccdull;
-  k ^= k >> 33;
-  k *= 0xc4ceb9fe1a85ec53ull;
-  k ^= k >> 33;
-  return k;
-}
-
 // Returns true (block-uniform) when an earlier stage of the call found its
 // buffers too small or the input bad: the tile records are then not valid to
 // read (a replayed graph runs every stage regardless; the host runs the call
@@ -1446,7 +1436,7 @@ __global__ void __launch_bounds__(kChaseThreads) k_chase_tiles(Batch bt, TiledSc
 __device__ __forceinline__ uint32_t global_insert(const RankScratch &rs, unsigned long long key,
                                                   bool *fresh) {
   const unsigned int mask = rs.capacity - 1u;
-  unsigned int slot = (unsigned int)mix64t(key) & mask;
+  unsigned int slot = (unsigned int)hash_mix64(key) & mask;
   for (unsigned int probe = 0; probe < rs.probe_limit; ++probe) {
     unsigned long long cur = __ldcg(&rs.table_keys[slot]);
     if (cur == ~0ull) {

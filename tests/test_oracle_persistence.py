@@ -160,3 +160,25 @@ def test_basin_graph_formulation_agrees(dims, levels):
     ext, death = basin_graph_pairs(f, dims)
     assert np.array_equal(p["extremum"], ext)
     assert np.array_equal(p["death"], death)
+
+
+def staircase(k_steps, wall=10000.0):
+    f = np.empty(2 * k_steps + 1, np.float32)
+    f[0::2] = np.arange(k_steps + 1)
+    f[1::2] = wall - np.arange(k_steps)
+    return f.reshape(1, -1)
+
+
+@pytest.mark.parametrize("steps", [1, 2, 5, 50])
+def test_staircase_closed_form(steps):
+    """Minima at x = 2k with value k, walls at x = 2k + 1 with value W - k.
+    Walls enter lowest first, i.e. from the right: the wall at 2k - 1 joins
+    minimum k to minimum k - 1's component, so minimum k dies there.  For
+    maxima the valleys enter highest first, from the right: the valley at 2k
+    joins wall k to wall k - 1's component, so wall k dies at 2k."""
+    f = staircase(steps)
+    mn, mx = oracle.persistence(f, -1), oracle.persistence(f, 1)
+    assert mn["extremum"].tolist() == list(range(0, 2 * steps + 1, 2))
+    assert mn["death"].tolist() == [-1] + [2 * k - 1 for k in range(1, steps + 1)]
+    assert mx["extremum"].tolist() == list(range(1, 2 * steps, 2))
+    assert mx["death"].tolist() == [-1] + [2 * k for k in range(1, steps)]
