@@ -301,6 +301,59 @@ ms_status ms_persistence(ms_ctx *ctx, const void *field, const int64_t dims[3], 
                          const int32_t *labels, int direction, int32_t *extremum, int32_t *death,
                          int64_t capacity, ms_persistence_info *info);
 
+/* ---- one field over several processes: z-slabs ------------------------------- */
+
+/* The paper leaves computing one field on many nodes to future work (Sec. 8).
+ * These four calls split Sec. 4.2's steps by z-slab so that each process (one
+ * GPU each) segments its slab and the processes exchange two small messages:
+ *   1. ms_slab_local on every slab; each publishes the asc / desc labels of
+ *      its first and last owned planes (those another slab's lines can
+ *      enter) -- planes z0 (if z0 > 0) and z1 - 1 (if z1 < nz);
+ *   2. all-gather of those rows; ms_slab_resolve on every slab;
+ *   3. ms_slab_pairs on every slab; all-gather of the pair lists;
+ *      ms_slab_rank on every slab.
+ * Labels and MS ids then equal ms_segment's on the whole field, vertex for
+ * vertex.  Every buffer is in the calling process's device memory: gathered
+ * data is copied in before a call reads it. */
+
+/* Steepest steps and pointer jumping inside one slab (Sec. 4.2.1).
+ * dims: the whole field's (nx, ny, nz); the slab owns planes [z0, z1).
+ * field: the slab's planes plus one halo plane on each side that exists --
+ * planes [z0 - (z0 > 0), z1 + (z1 < nz)) -- device.  out_asc, out_desc:
+ * int32[(z1 - z0) nx ny], device: for each owned vertex the global index of
+ * the extremum its line reaches inside the slab, or -(h + 1) where the line
+ * leaves the slab at global vertex h (a halo vertex).  Errors as
+ * ms_segment. */
+ms_status ms_slab_local(ms_ctx *ctx, const void *field, const int64_t dims[3], ms_dtype dtype,
+                        int64_t z0, int64_t z1, int32_t *out_asc, int32_t *out_desc);
+
+/* Resolves exits.  rows: int32[n_planes][2][nx ny] on the device, the
+ * published rows of all slabs ([plane][0] asc, [plane][1] desc), rewritten in
+ * place; plane_z: int64[n_planes] on the host, each row's global z (distinct).
+ * asc, desc: int32[n_owned] on the device, this slab's ms_slab_local output,
+ * rewritten with every exit replaced by the extremum its line reaches.
+ * MS_ERR_INVALID_ARG if an exit points into a plane that is not among the
+ * rows (or the rows hold an index out of range); MS_ERR_NOT_CONVERGED if the
+ * rows hold a cycle. */
+ms_status ms_slab_resolve(ms_ctx *ctx, const int64_t dims[3], int32_t *rows, const int64_t *plane_z,
+                          int n_planes, int32_t *asc, int32_t *desc, int64_t n_owned);
+
+/* The distinct (asc, desc) pairs of n resolved vertices, as keys
+ * (asc << 32) | desc in increasing order, into keys (uint64[capacity],
+ * device); *m receives the count (also on MS_ERR_TOO_LARGE, when it exceeds
+ * capacity and nothing is written).  Labels must lie in [0, n_labels). */
+ms_status ms_slab_pairs(ms_ctx *ctx, const int32_t *asc, const int32_t *desc, int64_t n,
+                        int64_t n_labels, uint64_t *keys, int64_t capacity, int64_t *m);
+
+/* MS ids (Sec. 4.2.2) of n resolved vertices: the rank of each vertex's pair
+ * among the distinct keys of all slabs (keys: every slab's ms_slab_pairs
+ * output, concatenated, n_keys <= 2^30, device).  ms: int32[n], device; *k
+ * (may be NULL): the number of distinct pairs of the whole field.
+ * MS_ERR_INVALID_ARG if a vertex's pair is missing from the keys. */
+ms_status ms_slab_rank(ms_ctx *ctx, const int32_t *asc, const int32_t *desc, int64_t n,
+                       int64_t n_labels, const uint64_t *keys, int64_t n_keys, int32_t *ms,
+                       int64_t *k);
+
 /* ---- serving ---------------------------------------------------------------- */
 
 /* A request loop for segmentations of mixed sizes.  The server owns n_slots

@@ -27,7 +27,8 @@ __all__ = [
     "ms_pair_rank_noalloc", "MS_NOALLOC_MAX_N", "ms_segment_batch", "ms_server_create",
     "ms_server_submit", "ms_server_wait", "ms_server_stats", "ms_server_destroy",
     "ms_batch_autotune", "ms_batch_graphs", "ms_simplex_index", "ms_simplex_geometry",
-    "simplex_cells", "ms_segment_host_many", "ms_persistence", "persistence",
+    "simplex_cells", "ms_segment_host_many", "ms_persistence", "persistence", "ms_slab_local",
+    "ms_slab_resolve", "ms_slab_pairs", "ms_slab_rank",
 ]
 
 MS_F32, MS_F16 = 0, 1
@@ -42,7 +43,7 @@ EXPORTED_SYMBOLS = [
     "ms_pair_rank_noalloc", "ms_segment_batch", "ms_server_create", "ms_server_submit",
     "ms_server_wait", "ms_server_stats", "ms_server_destroy", "ms_batch_autotune",
     "ms_batch_graphs", "ms_simplex_index", "ms_simplex_geometry", "ms_segment_host_many",
-    "ms_persistence",
+    "ms_persistence", "ms_slab_local", "ms_slab_resolve", "ms_slab_pairs", "ms_slab_rank",
 ]
 MS_NOALLOC_MAX_N = 262144
 
@@ -112,6 +113,14 @@ def load(build: bool = True) -> ctypes.CDLL:
                                               c_vp, c_vp]
             L.ms_persistence.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, ctypes.c_int, c_vp,
                                          c_vp, ctypes.c_int64, ctypes.POINTER(_PersistenceInfo)]
+            L.ms_slab_local.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, ctypes.c_int64,
+                                        ctypes.c_int64, c_vp, c_vp]
+            L.ms_slab_resolve.argtypes = [c_vp, c_i64p, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp,
+                                          ctypes.c_int64]
+            L.ms_slab_pairs.argtypes = [c_vp, c_vp, c_vp, ctypes.c_int64, ctypes.c_int64, c_vp,
+                                        ctypes.c_int64, c_i64p]
+            L.ms_slab_rank.argtypes = [c_vp, c_vp, c_vp, ctypes.c_int64, ctypes.c_int64, c_vp,
+                                       ctypes.c_int64, c_vp, c_i64p]
             L.ms_server_create.argtypes = [ctypes.POINTER(c_vp), ctypes.c_int, ctypes.c_size_t,
                                            ctypes.c_int]
             L.ms_server_submit.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_vp,
@@ -296,6 +305,37 @@ def persistence(ctx, field, labels, direction: int = -1):
             continue
         return ext[:info["n_extrema"]], dth[:info["n_extrema"]], info
     raise RuntimeError("ms_persistence: extremum count changed between calls")
+
+
+def ms_slab_local(ctx, field, dims, dtype, z0, z1, out_asc, out_desc) -> None:
+    _check(load().ms_slab_local(ctx, _ptr(field), _dims(dims), int(dtype), int(z0), int(z1),
+                                _ptr(out_asc), _ptr(out_desc)), "ms_slab_local")
+
+
+def ms_slab_resolve(ctx, dims, rows, plane_z, asc, desc, n_owned) -> None:
+    zs = (ctypes.c_int64 * max(1, len(plane_z)))(*[int(z) for z in plane_z])
+    _check(load().ms_slab_resolve(ctx, _dims(dims), _ptr(rows), zs, len(plane_z), _ptr(asc),
+                                  _ptr(desc), int(n_owned)), "ms_slab_resolve")
+
+
+def ms_slab_pairs(ctx, asc, desc, n, n_labels, keys, capacity) -> int:
+    """Count of distinct pairs; raises MSError (with ``.count``) when it
+    exceeds capacity."""
+    m = ctypes.c_int64(0)
+    st = load().ms_slab_pairs(ctx, _ptr(asc), _ptr(desc), int(n), int(n_labels), _ptr(keys),
+                              int(capacity), ctypes.byref(m))
+    if st != 0:
+        err = MSError(st, "ms_slab_pairs")
+        err.count = m.value
+        raise err
+    return m.value
+
+
+def ms_slab_rank(ctx, asc, desc, n, n_labels, keys, n_keys, ms) -> int:
+    k = ctypes.c_int64(0)
+    _check(load().ms_slab_rank(ctx, _ptr(asc), _ptr(desc), int(n), int(n_labels), _ptr(keys),
+                               int(n_keys), _ptr(ms), ctypes.byref(k)), "ms_slab_rank")
+    return k.value
 
 
 def ms_batch_graphs(ctx, on: bool = True) -> None:

@@ -58,6 +58,10 @@ struct ms_ctx {
   size_t graph_bytes = 0;
   void *sxscratch = nullptr;  // index-pass block totals and bases
   size_t sxscratch_bytes = 0;
+  void *slscratch = nullptr;  // z-slab pointer arrays (slab and its halo planes)
+  size_t slscratch_bytes = 0;
+  void *slmap = nullptr;      // published planes: their z and row, sorted by z
+  size_t slmap_bytes = 0;
   void *pscratch = nullptr;   // persistence pairing working memory
   size_t pscratch_bytes = 0;
   void *pcount = nullptr;     // its pinned counter copy
@@ -851,19 +855,21 @@ namespace msseg {
 
 size_t ctx_resident_bytes(const ms_ctx *c) {
   return c->scratch_bytes + c->io_bytes + c->io2_bytes + c->tscratch_bytes + c->graph_bytes +
-         c->sxscratch_bytes + c->pscratch_bytes + c->batch_dev_bytes + sizeof(DevStatus);
+         c->sxscratch_bytes + c->pscratch_bytes + c->slscratch_bytes + c->slmap_bytes +
+         c->batch_dev_bytes + sizeof(DevStatus);
 }
 
 void ctx_release_scratch(ms_ctx *c) {
   DeviceGuard g(c->device);
   cudaStreamSynchronize(c->stream);
   for (BatchPlan &P : c->plans) drop_graph(&P);
-  void **bufs[] = {&c->scratch, &c->io, &c->io2, &c->tscratch, &c->graph, &c->sxscratch,
-                   &c->pscratch, &c->batch_dev};
-  size_t *sizes[] = {&c->scratch_bytes, &c->io_bytes, &c->io2_bytes, &c->tscratch_bytes,
-                     &c->graph_bytes, &c->sxscratch_bytes, &c->pscratch_bytes,
+  void **bufs[] = {&c->scratch, &c->io,       &c->io2,    &c->tscratch, &c->graph,
+                   &c->sxscratch, &c->pscratch, &c->slscratch, &c->slmap, &c->batch_dev};
+  size_t *sizes[] = {&c->scratch_bytes,   &c->io_bytes,        &c->io2_bytes,
+                     &c->tscratch_bytes,  &c->graph_bytes,     &c->sxscratch_bytes,
+                     &c->pscratch_bytes,  &c->slscratch_bytes, &c->slmap_bytes,
                      &c->batch_dev_bytes};
-  for (int i = 0; i < 8; ++i) {
+  for (int i = 0; i < 10; ++i) {
     if (*bufs[i]) cudaFree(*bufs[i]);
     *bufs[i] = nullptr;
     *sizes[i] = 0;
@@ -932,6 +938,8 @@ ms_status ms_destroy(ms_ctx *c) {
   if (c->graph) cudaFree(c->graph);
   if (c->sxscratch) cudaFree(c->sxscratch);
   if (c->pscratch) cudaFree(c->pscratch);
+  if (c->slscratch) cudaFree(c->slscratch);
+  if (c->slmap) cudaFree(c->slmap);
   if (c->pcount) cudaFreeHost(c->pcount);
   if (c->batch_dev) cudaFree(c->batch_dev);
   if (c->batch_host) cudaFreeHost(c->batch_host);
@@ -1196,6 +1204,182 @@ ms_status ms_persistence(ms_ctx *c, const void *field, const int64_t dims[3], ms
     finish_profile(c, l0);
     return MS_OK;
   }
+}
+
+ms_status ms_slab_local(ms_ctx *c, const void *field, const int64_t dims[3], ms_dtype dtype,
+                        int64_t z0, int64_t z1, int32_t *out_asc, int32_t *out_desc) {
+  if (!c || !field || !out_asc || !out_desc || out_asc == out_desc) return MS_ERR_INVALID_ARG;
+  int64_t n = 0;
+  ms_status s = check_dims(dims, &n);
+  if (s != MS_OK) return s;
+  s = check_dtype(dtype);
+  if (s != MS_OK) return s;
+  if (z0 < 0 || z1 <= z0 || z1 > dims[2]) return MS_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (!is_device_pointer(field) || !is_device_pointer(out_asc) || !is_device_pointer(out_desc))
+    return MS_ERR_INVALID_ARG;
+  const int64_t nxy = dims[0] * dims[1];
+  const int64_t lo = z0 > 0 ? 1 : 0, hi = z1 < dims[2] ? 1 : 0, owned = z1 - z0;
+  const int64_t ext_dims[3] = {dims[0], dims[1], owned + lo + hi};
+  const int64_t n_ext = ext_dims[2] * nxy;
+  s = ensure_buffer(c, &c->slscratch, &c->slscratch_bytes, (size_t)n_ext * 8);
+  if (s != MS_OK) return s;
+  int32_t *up = static_cast<int32_t *>(c->slscratch), *dn = up + n_ext;
+  const long long l0 = tl_launches;
+  s = reset_status(c);
+  if (s != MS_OK) return s;
+  StageTimer t0(c, MS_STAGE_TILE_LOCAL);
+  MS_TRY(launch_steepest_simple(field, ext_dims, dtype, up, dn, c->dst, c->stream));
+  MS_TRY(launch_slab_halo_self(up, dn, nxy, lo, owned, hi, c->stream));
+  t0.stop();
+  StageTimer t1(c, MS_STAGE_RESOLVE);
+  s = compress_pair(c, up, dn, n_ext);  // also reads the status block back
+  t1.stop();
+  if (c->hst->nan_flag) return MS_ERR_NAN_INPUT;
+  if (s != MS_OK) return s;
+  MS_TRY(launch_slab_encode(up, dn, nxy, lo, owned, (z0 - lo) * nxy, out_asc, out_desc, c->stream));
+  MS_TRY(cudaStreamSynchronize(c->stream));
+  finish_profile(c, l0);
+  return MS_OK;
+}
+
+ms_status ms_slab_resolve(ms_ctx *c, const int64_t dims[3], int32_t *rows, const int64_t *plane_z,
+                          int n_planes, int32_t *asc, int32_t *desc, int64_t n_owned) {
+  if (!c || n_planes < 0 || n_owned < 0 || (n_planes > 0 && (!rows || !plane_z)) ||
+      (n_owned > 0 && (!asc || !desc)))
+    return MS_ERR_INVALID_ARG;
+  int64_t n = 0;
+  ms_status s = check_dims(dims, &n);
+  if (s != MS_OK) return s;
+  DeviceGuard g(c->device);
+  if ((n_planes > 0 && !is_device_pointer(rows)) ||
+      (n_owned > 0 && (!is_device_pointer(asc) || !is_device_pointer(desc))))
+    return MS_ERR_INVALID_ARG;
+  const int64_t nxy = dims[0] * dims[1];
+  if ((int64_t)n_planes * 2 * nxy > kMaxVertices) return MS_ERR_TOO_LARGE;
+  // the planes' z, sorted, each with its row
+  std::vector<std::pair<long long, int>> zr((size_t)n_planes);
+  for (int i = 0; i < n_planes; ++i) {
+    if (plane_z[i] < 0 || plane_z[i] >= dims[2]) return MS_ERR_INVALID_ARG;
+    zr[(size_t)i] = {(long long)plane_z[i], i};
+  }
+  std::sort(zr.begin(), zr.end());
+  for (int i = 1; i < n_planes; ++i)
+    if (zr[(size_t)i].first == zr[(size_t)i - 1].first) return MS_ERR_INVALID_ARG;
+  const size_t zbytes = (size_t)n_planes * 8;
+  s = ensure_buffer(c, &c->slmap, &c->slmap_bytes, zbytes + (size_t)n_planes * 4 + 16);
+  if (s != MS_OK) return s;
+  long long *zs = static_cast<long long *>(c->slmap);
+  int *slot = reinterpret_cast<int *>(static_cast<char *>(c->slmap) + zbytes);
+  if (n_planes > 0) {
+    std::vector<long long> hz((size_t)n_planes);
+    std::vector<int> hs((size_t)n_planes);
+    for (int i = 0; i < n_planes; ++i) {
+      hz[(size_t)i] = zr[(size_t)i].first;
+      hs[(size_t)i] = zr[(size_t)i].second;
+    }
+    MS_TRY(cudaMemcpyAsync(zs, hz.data(), zbytes, cudaMemcpyHostToDevice, c->stream));
+    MS_TRY(cudaMemcpyAsync(slot, hs.data(), (size_t)n_planes * 4, cudaMemcpyHostToDevice, c->stream));
+  }
+  const long long l0 = tl_launches;
+  s = reset_status(c);
+  if (s != MS_OK) return s;
+  StageTimer t0(c, MS_STAGE_RESOLVE);
+  // an exit chain visits each row entry at most once: jumping with doubling
+  // ends within ceil(log2(entries)) + 2 rounds
+  const int cap = n_planes > 0 ? round_cap((int64_t)n_planes * 2 * nxy) : 0;
+  for (int r = 0; r < cap; ++r)
+    MS_TRY(launch_slab_rows_round(rows, n_planes, nxy, n, zs, slot, c->dst, r, c->stream));
+  MS_TRY(launch_slab_apply(asc, desc, n_owned, rows, nxy, n, zs, slot, n_planes, c->dst, c->stream));
+  t0.stop();
+  s = read_status(c);
+  if (s != MS_OK) return s;
+  if (c->hst->bad_index) return MS_ERR_INVALID_ARG;
+  if (cap > 0 && c->hst->round_open[cap - 1]) return MS_ERR_NOT_CONVERGED;
+  finish_profile(c, l0);
+  return MS_OK;
+}
+
+ms_status ms_slab_pairs(ms_ctx *c, const int32_t *asc, const int32_t *desc, int64_t n,
+                        int64_t n_labels, uint64_t *keys, int64_t capacity, int64_t *m) {
+  if (!c || n < 0 || capacity < 0 || n_labels < 1 || n_labels > kMaxVertices || n > kMaxVertices ||
+      (n > 0 && (!asc || !desc)))
+    return MS_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if (n == 0) {
+    if (m) *m = 0;
+    return MS_OK;
+  }
+  if (!is_device_pointer(asc) || !is_device_pointer(desc) || (capacity > 0 && !is_device_pointer(keys)))
+    return MS_ERR_INVALID_ARG;
+  const long long l0 = tl_launches;
+  uint64_t guess = std::min<uint64_t>((uint64_t)n, (uint64_t)n / 16 + 1024);
+  for (;;) {
+    const unsigned int cap = pow2_at_least(2 * guess + 2);
+    ms_status s = ensure_scratch(c, rank_scratch_bytes(cap));
+    if (s != MS_OK) return s;
+    RankScratch rs;
+    rank_scratch_carve(c->scratch, cap, &rs);
+    if (guess < (uint64_t)n) rs.probe_limit = kEstimateProbeLimit;
+    s = reset_status(c);
+    if (s != MS_OK) return s;
+    MS_TRY(launch_pairs_insert(asc, desc, n, rs, c->dst, c->stream, n_labels));
+    s = read_status(c);
+    if (s != MS_OK) return s;
+    if (c->hst->bad_index) return MS_ERR_INVALID_ARG;
+    if (c->hst->hash_overflow) {
+      if (guess >= (uint64_t)n) return MS_ERR_CUDA;  // cannot happen: n is a bound
+      guess = std::min<uint64_t>((uint64_t)n, guess * 4);
+      continue;
+    }
+    const unsigned int mu = c->hst->n_unique;
+    if (m) *m = mu;
+    if ((int64_t)mu > capacity) return MS_ERR_TOO_LARGE;
+    MS_TRY(launch_pairs_sort(rs, mu, bit_width(n_labels - 1), c->stream));
+    MS_TRY(cudaMemcpyAsync(keys, rs.list, (size_t)mu * 8, cudaMemcpyDeviceToDevice, c->stream));
+    MS_TRY(cudaStreamSynchronize(c->stream));
+    finish_profile(c, l0);
+    return MS_OK;
+  }
+}
+
+ms_status ms_slab_rank(ms_ctx *c, const int32_t *asc, const int32_t *desc, int64_t n,
+                       int64_t n_labels, const uint64_t *keys, int64_t n_keys, int32_t *ms,
+                       int64_t *k) {
+  if (!c || n < 0 || n_keys < 0 || n_labels < 1 || n_labels > kMaxVertices || n > kMaxVertices ||
+      n_keys > (1ll << 30) || (n > 0 && (!asc || !desc || !ms)) || (n_keys > 0 && !keys))
+    return MS_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  if ((n > 0 && (!is_device_pointer(asc) || !is_device_pointer(desc) || !is_device_pointer(ms))) ||
+      (n_keys > 0 && !is_device_pointer(keys)))
+    return MS_ERR_INVALID_ARG;
+  if (n > 0 && n_keys == 0) return MS_ERR_INVALID_ARG;  // the slab's own pairs are missing
+  const long long l0 = tl_launches;
+  const unsigned int cap = pow2_at_least(2 * (uint64_t)n_keys + 2);
+  ms_status s = ensure_scratch(c, rank_scratch_bytes(cap));
+  if (s != MS_OK) return s;
+  RankScratch rs;
+  rank_scratch_carve(c->scratch, cap, &rs);
+  s = reset_status(c);
+  if (s != MS_OK) return s;
+  MS_TRY(launch_keys_insert(reinterpret_cast<const unsigned long long *>(keys), n_keys, n_labels, rs,
+                            c->dst, c->stream));
+  s = read_status(c);
+  if (s != MS_OK) return s;
+  if (c->hst->bad_index) return MS_ERR_INVALID_ARG;
+  if (c->hst->hash_overflow) return MS_ERR_CUDA;  // cannot happen: sized from n_keys
+  const unsigned int mu = c->hst->n_unique;
+  MS_TRY(launch_pairs_sort(rs, mu, bit_width(n_labels - 1), c->stream));
+  MS_TRY(launch_pairs_assign(rs, mu, c->stream));
+  MS_TRY(launch_pairs_lookup(asc, desc, n, rs, ms, c->stream));
+  MS_TRY(launch_check_nonneg(ms, n, c->dst, c->stream));
+  s = read_status(c);
+  if (s != MS_OK) return s;
+  if (c->hst->bad_index) return MS_ERR_INVALID_ARG;  // a pair missing from the keys
+  c->last_k = mu;
+  if (k) *k = mu;
+  finish_profile(c, l0);
+  return MS_OK;
 }
 
 ms_status ms_batch_graphs(ms_ctx *c, int on) {

@@ -103,8 +103,14 @@ size_t rank_scratch_bytes(unsigned int capacity);
 // Most blocks a sort pass over up to capacity / 2 keys uses.
 unsigned int sort_blocks_cap_of(unsigned int capacity);
 void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs);
+// Labels must lie in [0, label_bound) (label_bound <= 0: [0, n)).
 cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t n,
-                                const RankScratch &rs, DevStatus *st, cudaStream_t s);
+                                const RankScratch &rs, DevStatus *st, cudaStream_t s,
+                                int64_t label_bound = 0);
+// Inserts packed (asc << 32) | desc keys (repeats allowed), labels in
+// [0, label_bound).
+cudaError_t launch_keys_insert(const unsigned long long *keys, int64_t n, int64_t label_bound,
+                               const RankScratch &rs, DevStatus *st, cudaStream_t s);
 // Sorts the pair list: (asc << 32) | desc keys with labels below 2^key_bits,
 // or (raw_bits > 0) keys compared on their low raw_bits bits as they are.
 // With m_dev, n_unique is a capacity that sizes the launches and the kernels
@@ -128,6 +134,20 @@ cudaError_t launch_simplex_index(const int32_t *labels, const int64_t dims[3], i
 cudaError_t launch_simplex_geometry(const int32_t *labels, const int64_t dims[3], int mode,
                                     const int64_t *offsets, int64_t total, float *points,
                                     int32_t *pairs, DevStatus *st, cudaStream_t s);
+
+// z-slab sharding (ms_slab.cu).
+cudaError_t launch_slab_halo_self(int32_t *up, int32_t *dn, int64_t nxy, int64_t lo_planes,
+                                  int64_t owned_planes, int64_t hi_planes, cudaStream_t s);
+cudaError_t launch_slab_encode(const int32_t *up, const int32_t *dn, int64_t nxy, int64_t lo_planes,
+                               int64_t owned_planes, int64_t base, int32_t *out_asc,
+                               int32_t *out_desc, cudaStream_t s);
+cudaError_t launch_slab_rows_round(int32_t *rows, int n_planes, int64_t nxy, int64_t n_global,
+                                   const long long *zs, const int *slot, DevStatus *st, int round,
+                                   cudaStream_t s);
+cudaError_t launch_slab_apply(int32_t *asc, int32_t *desc, int64_t n, const int32_t *rows,
+                              int64_t nxy, int64_t n_global, const long long *zs, const int *slot,
+                              int n_planes, DevStatus *st, cudaStream_t s);
+cudaError_t launch_check_nonneg(const int32_t *p, int64_t n, DevStatus *st, cudaStream_t s);
 
 // 0-dimensional persistence pairing from the basin graph (ms_persist.cu).
 struct PersistCall {

@@ -60,8 +60,9 @@ __device__ __forceinline__ int table_find(const RankScratch &rs, unsigned long l
   return -1;
 }
 
+// Labels must lie in [0, bound).
 __global__ void k_pairs_insert(const int32_t *__restrict__ asc, const int32_t *__restrict__ desc,
-                               int64_t n, RankScratch rs, DevStatus *st) {
+                               int64_t n, int64_t bound, RankScratch rs, DevStatus *st) {
   bool bad = false;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   // the loop bound keeps whole warps together for __match_any_sync
@@ -70,10 +71,32 @@ __global__ void k_pairs_insert(const int32_t *__restrict__ asc, const int32_t *_
     unsigned long long key = kEmpty;
     if (v < n) {
       const int32_t a = asc[v], d = desc[v];
-      if (a < 0 || d < 0 || (int64_t)a >= n || (int64_t)d >= n)
+      if (a < 0 || d < 0 || (int64_t)a >= bound || (int64_t)d >= bound)
         bad = true;
       else
         key = pack_pair(a, d);
+    }
+    const unsigned int peers = __match_any_sync(0xffffffffu, key);
+    if (key != kEmpty && (__ffs(peers) - 1) == (int)lane_id()) table_insert(rs, key, st);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane_id() == 0) atomicOr(&st->bad_index, 1u);
+}
+
+// Packed (asc << 32) | desc keys, labels in [0, bound); keys may repeat.
+__global__ void k_keys_insert(const unsigned long long *__restrict__ keys, int64_t n, int64_t bound,
+                              RankScratch rs, DevStatus *st) {
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    unsigned long long key = kEmpty;
+    if (i < n) {
+      key = keys[i];
+      const int64_t a = (int64_t)(key >> 32), d = (int64_t)(key & 0xffffffffull);
+      if (a >= bound || d >= bound) {
+        bad = true;
+        key = kEmpty;
+      }
     }
     const unsigned int peers = __match_any_sync(0xffffffffu, key);
     if (key != kEmpty && (__ffs(peers) - 1) == (int)lane_id()) table_insert(rs, key, st);
@@ -358,11 +381,22 @@ void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs) {
 }
 
 cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t n,
-                                const RankScratch &rs, DevStatus *st, cudaStream_t s) {
+                                const RankScratch &rs, DevStatus *st, cudaStream_t s,
+                                int64_t label_bound) {
   cudaError_t e = cudaMemsetAsync(rs.table_keys, 0xff, (size_t)rs.capacity * 8, s);
   if (e != cudaSuccess || n <= 0) return e;
   ++tl_launches;
-  k_pairs_insert<<<grid_n(n, 8), 256, 0, s>>>(asc, desc, n, rs, st);
+  k_pairs_insert<<<grid_n(n, 8), 256, 0, s>>>(asc, desc, n, label_bound > 0 ? label_bound : n, rs,
+                                              st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_keys_insert(const unsigned long long *keys, int64_t n, int64_t label_bound,
+                               const RankScratch &rs, DevStatus *st, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(rs.table_keys, 0xff, (size_t)rs.capacity * 8, s);
+  if (e != cudaSuccess || n <= 0) return e;
+  ++tl_launches;
+  k_keys_insert<<<grid_n(n, 8), 256, 0, s>>>(keys, n, label_bound, rs, st);
   return cudaGetLastError();
 }
 
