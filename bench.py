@@ -413,7 +413,8 @@ def batch_line(args, plain_steps=None):
                    "vertices": n, "regions_K_total": int(sum(ks)),
                    "l2": "fields 1.1 GB + labels 3.6 GB, larger than L2"},
         "plain_ms_per_step": t_plain, "speedup_vs_plain": t_plain / t_batch,
-        "tuning": tuning, "graph_replay": prof["stages"]["graph"]["launches"] > 0,
+        "tuning": tuning, "tile_shape": "x".join(map(str, ms.TILE_SHAPES[tuning["shape3"]])),
+        "graph_replay": prof["stages"]["graph"]["launches"] > 0,
         "gpu_launches": prof["launches"],
         "stages_ms_per_step": {k: v["ms"] / max(1, prof["calls"]) for k, v in prof["stages"].items()
                                if v["launches"] or v["ms"]},
@@ -755,6 +756,40 @@ def quantised_summary(args, f_np):
                                    for kk, v in prof["stages"].items() if v["launches"] or v["ms"]}}
 
 
+def persistence_summary(args, f_np):
+    """Persistence pairs of the 512^3 field's minima and maxima from its
+    segmentation (ms_persistence, Sec. 4.1), wall time per call (the call
+    reads counts back between its steps), median of 5 after one untimed."""
+    import torch
+
+    import paper_2303_15491_gb300 as ms
+
+    dev = torch.cuda.current_device()
+    field = torch.from_numpy(np.asarray(f_np)).to(dev)
+    ctx = ms.ms_create(dev, torch.cuda.Stream(device=dev))
+    out = {"workload": "noise512", "reps": 5}
+    try:
+        asc, desc, _, _ = ms.segment(ctx, field)
+        dims, dt = ms.dims_of(field), ms.dtype_code(field)
+        for name, direction, lab in (("minima", -1, asc), ("maxima", 1, desc)):
+            ext, death, info = ms.persistence(ctx, field, lab, direction)
+            cap = info["n_extrema"]
+            times = []
+            for _ in range(5):
+                torch.cuda.synchronize()
+                t = time.perf_counter()
+                info = ms.ms_persistence(ctx, field, dims, dt, lab, direction, ext, death, cap)
+                times.append(1e3 * (time.perf_counter() - t))
+            out[name] = {"ms": float(np.median(times)), "extrema": info["n_extrema"],
+                         "basin_edges": info["basin_edges"], "rounds": info["rounds"],
+                         "finish_edges": info["finish_edges"]}
+    finally:
+        ms.ms_destroy(ctx)
+        del field
+        torch.cuda.empty_cache()
+    return out
+
+
 def batched_summary(args):
     sub = argparse.Namespace(**vars(args))
     sub.steps, sub.warmup = 10, 3
@@ -764,6 +799,7 @@ def batched_summary(args):
             "plain_ms_per_step": ln["plain_ms_per_step"], "speedup_vs_plain": ln["speedup_vs_plain"],
             "fields": ln["config"]["fields"], "vertices": ln["config"]["vertices"],
             "regions_K_total": ln["config"]["regions_K_total"], "tuning": ln["tuning"],
+            "tile_shape": ln["tile_shape"],
             "graph_replay": ln["graph_replay"], "stages_ms_per_step": ln["stages_ms_per_step"],
             "note": "10 timed batched steps, 2 timed rounds of 256 single calls (reduced counts)"}
 
@@ -791,7 +827,8 @@ def main():
     ap.add_argument("--ref-slab", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the quantised, batched and served sub-measurements of the default run")
+                    help="skip the quantised, batched, served and persistence sub-measurements of "
+                         "the default run")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-passes", type=int, default=16)
@@ -1017,6 +1054,7 @@ def main():
         line["quantised"] = extra("quantised", lambda: quantised_summary(args, f_np))
         line["batched"] = extra("batched", lambda: batched_summary(args))
         line["served"] = extra("served", lambda: served_summary(args))
+        line["persistence"] = extra("persistence", lambda: persistence_summary(args, f_np))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -186,20 +186,31 @@ typedef struct {
   int pair_blocks;    /* tile pairs: 256-thread blocks per SM */
   int dynamic;        /* 1: tiles taken from a work queue; 0: static stride */
   int resolve_mode;   /* exits and pairs: -1 by tile count, 0 a tile a warp, 1 flat */
+  int shape3;         /* 3D tile shape (x * y * z vertices): 0 32x16x16 (the default),
+                         1 64x8x16, 2 16x32x16, 3 16x16x16 */
   double default_ms;  /* ms_batch_autotune: time of the default choices */
   double best_ms;     /* ms_batch_autotune: time of the chosen ones */
 } ms_tuning;
 
 /* Time the batched path on these fields (arguments as ms_segment_batch; the
- * outputs are written) under candidate launch choices -- one knob at a time,
- * keeping a change only if it is at least 2 % faster -- and keep the fastest
- * for later ms_segment_batch calls with the same fields.  *out (may be NULL)
+ * outputs are written) under candidate launch choices -- the tile shape
+ * first, then one knob at a time, keeping a change only if it is at least
+ * 2 % faster -- and keep the fastest for later calls with the same fields
+ * (ms_segment_batch, or ms_segment for one field).  *out (may be NULL)
  * receives the choice.  MS_ERR_INVALID_ARG if the fields do not take the
  * batched path. */
 ms_status ms_batch_autotune(ms_ctx *ctx, int n_fields, const void *const *fields,
                             const int64_t (*dims)[3], const ms_dtype *dtypes,
                             int32_t *const *asc, int32_t *const *desc, int32_t *const *ms,
                             ms_tuning *out);
+
+/* The choices calls on this context take when no ms_batch_autotune entry
+ * covers their fields (the timing fields are ignored / zero).  Setting them
+ * drops captured graphs of untuned calls.  MS_ERR_INVALID_ARG for a choice
+ * out of range (tile_ctas 1..4, write_ctas 1..16, chase_blocks 1..4,
+ * pair_blocks 1..16, dynamic 0..1, resolve_mode -1..1, shape3 0..3). */
+ms_status ms_set_tuning(ms_ctx *ctx, const ms_tuning *t);
+ms_status ms_get_tuning(const ms_ctx *ctx, ms_tuning *t);
 
 /* Enable (on != 0, the default) or disable graph capture and replay of
  * repeated calls (ms_segment, ms_segment_batch) on this context. */

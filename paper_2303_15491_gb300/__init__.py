@@ -28,7 +28,8 @@ __all__ = [
     "ms_server_submit", "ms_server_wait", "ms_server_stats", "ms_server_destroy",
     "ms_batch_autotune", "ms_batch_graphs", "ms_simplex_index", "ms_simplex_geometry",
     "simplex_cells", "ms_segment_host_many", "ms_persistence", "persistence", "ms_slab_local",
-    "ms_slab_resolve", "ms_slab_pairs", "ms_slab_rank",
+    "ms_slab_resolve", "ms_slab_pairs", "ms_slab_rank", "ms_set_tuning", "ms_get_tuning",
+    "TILE_SHAPES",
 ]
 
 MS_F32, MS_F16 = 0, 1
@@ -44,15 +45,18 @@ EXPORTED_SYMBOLS = [
     "ms_server_wait", "ms_server_stats", "ms_server_destroy", "ms_batch_autotune",
     "ms_batch_graphs", "ms_simplex_index", "ms_simplex_geometry", "ms_segment_host_many",
     "ms_persistence", "ms_slab_local", "ms_slab_resolve", "ms_slab_pairs", "ms_slab_rank",
+    "ms_set_tuning", "ms_get_tuning",
 ]
 MS_NOALLOC_MAX_N = 262144
+# 3D tile shapes by ms_tuning.shape3 id: (x, y, z) vertices
+TILE_SHAPES = {0: (32, 16, 16), 1: (64, 8, 16), 2: (16, 32, 16), 3: (16, 16, 16)}
 
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("tile_ctas", ctypes.c_int), ("write_ctas", ctypes.c_int),
                 ("chase_blocks", ctypes.c_int), ("pair_blocks", ctypes.c_int),
-                ("dynamic", ctypes.c_int), ("resolve_mode", ctypes.c_int), ("default_ms", ctypes.c_double),
-                ("best_ms", ctypes.c_double)]
+                ("dynamic", ctypes.c_int), ("resolve_mode", ctypes.c_int), ("shape3", ctypes.c_int),
+                ("default_ms", ctypes.c_double), ("best_ms", ctypes.c_double)]
 
 
 class _PersistenceInfo(ctypes.Structure):
@@ -108,6 +112,8 @@ def load(build: bool = True) -> ctypes.CDLL:
             L.ms_batch_autotune.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                             ctypes.POINTER(_Tuning)]
             L.ms_batch_graphs.argtypes = [c_vp, ctypes.c_int]
+            L.ms_set_tuning.argtypes = [c_vp, ctypes.POINTER(_Tuning)]
+            L.ms_get_tuning.argtypes = [c_vp, ctypes.POINTER(_Tuning)]
             L.ms_simplex_index.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, c_vp, c_i64p]
             L.ms_simplex_geometry.argtypes = [c_vp, c_vp, c_i64p, ctypes.c_int, c_vp, ctypes.c_int64,
                                               c_vp, c_vp]
@@ -336,6 +342,21 @@ def ms_slab_rank(ctx, asc, desc, n, n_labels, keys, n_keys, ms) -> int:
     _check(load().ms_slab_rank(ctx, _ptr(asc), _ptr(desc), int(n), int(n_labels), _ptr(keys),
                                int(n_keys), _ptr(ms), ctypes.byref(k)), "ms_slab_rank")
     return k.value
+
+
+def ms_get_tuning(ctx) -> dict:
+    t = _Tuning()
+    _check(load().ms_get_tuning(ctx, ctypes.byref(t)), "ms_get_tuning")
+    return {f: getattr(t, f) for f, _ in _Tuning._fields_ if not f.endswith("_ms")}
+
+
+def ms_set_tuning(ctx, **choices) -> dict:
+    """Set some of the context's default launch choices (see ms.h); returns
+    the previous ones."""
+    prev = ms_get_tuning(ctx)
+    t = _Tuning(**{**prev, **choices})
+    _check(load().ms_set_tuning(ctx, ctypes.byref(t)), "ms_set_tuning")
+    return prev
 
 
 def ms_batch_graphs(ctx, on: bool = True) -> None:

@@ -342,7 +342,7 @@ struct Staged {
   size_t bytes = 0;  // descriptor bytes on the device
 };
 
-ms_status stage_fields(ms_ctx *c, const FieldArg *fa, int nf, Staged *out) {
+ms_status stage_fields(ms_ctx *c, const FieldArg *fa, int nf, int shape3, Staged *out) {
   const int key_mode = nf > 1 ? kKeyBatch : kKeyOne;
   const size_t desc_bytes = ((size_t)nf * sizeof(FieldDesc) + 127) & ~(size_t)127;
   const size_t bytes = desc_bytes + (size_t)nf * sizeof(CUtensorMap);
@@ -376,8 +376,8 @@ ms_status stage_fields(ms_ctx *c, const FieldArg *fa, int nf, Staged *out) {
   int64_t total_n = 0, max_n = 0;
   for (int j = 0; j < nf; ++j) {
     const FieldArg &a = fa[order[j]];
-    make_field_desc(a.field, a.dtype, a.dims, total_tiles, a.asc, a.desc, a.ms, true, &hd[j],
-                    &hm[j]);
+    make_field_desc(a.field, a.dtype, a.dims, total_tiles, a.asc, a.desc, a.ms, true, shape3,
+                    &hd[j], &hm[j]);
     total_tiles += hd[j].g.ntiles;
     if (!hd[j].g.flat) tiles3 = total_tiles;
     total_n += a.n;
@@ -392,6 +392,8 @@ ms_status stage_fields(ms_ctx *c, const FieldArg *fa, int nf, Staged *out) {
   b.total_tiles = total_tiles;
   b.tiles3 = tiles3;
   b.f0 = hd[0];
+  b.shape3 = shape3;
+  b.face_stride = shape_info(shape3).face;
   out->b = b;
   out->order = std::move(order);
   out->total_n = total_n;
@@ -409,7 +411,7 @@ int pair_key_bits(const Staged &sf, int *raw_bits) {
 ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
                         const Tuning &tune) {
   Staged sf;
-  ms_status s = stage_fields(c, fa, nf, &sf);
+  ms_status s = stage_fields(c, fa, nf, tune.shape3, &sf);
   if (s != MS_OK) return s;
   Batch b = sf.b;
   b.tune = tune;
@@ -421,21 +423,21 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
 
   // ---- tile pass; the pair pool and root list are sized from the last call,
   // exact on overflow
-  const unsigned long long vslots = (unsigned long long)total_tiles * kTileV;
+  const unsigned long long vslots = (unsigned long long)total_tiles * kPidStride;
   unsigned long long cap = c->pool_hint, rcap = c->root_hint;
   if (cap == 0) cap = std::max<unsigned long long>(1ull << 16, (unsigned long long)total_n / 4);
   if (rcap == 0) rcap = std::max<unsigned long long>(1ull << 16, (unsigned long long)total_n / 4);
   cap = std::min(cap, vslots);
-  rcap = std::min(rcap, 2 * (unsigned long long)total_tiles * kExt);
+  rcap = std::min(rcap, 2 * (unsigned long long)total_tiles * kExtMax);
   TiledScratch ts;
   unsigned long long npairs = 0, nroots = 0;
   for (;;) {
     s = reset_status(c);
     if (s != MS_OK) return s;
     s = ensure_buffer(c, &c->tscratch, &c->tscratch_bytes,
-                      tiled_scratch_bytes(total_tiles, nf, cap, rcap));
+                      tiled_scratch_bytes(total_tiles, nf, cap, rcap, b.face_stride));
     if (s != MS_OK) return s;
-    tiled_scratch_carve(c->tscratch, total_tiles, nf, cap, rcap, &ts);
+    tiled_scratch_carve(c->tscratch, total_tiles, nf, cap, rcap, b.face_stride, &ts);
     if (tile_mode(b)) ts.root_tile = nullptr;  // only the flat resolution reads it
     StageTimer t0(c, MS_STAGE_TILE_LOCAL);
     MS_TRY(launch_tile_local(b, ts, c->dst, c->stream));
@@ -644,19 +646,20 @@ void reset_plan(BatchPlan *p) {
 ms_status capture_plan(ms_ctx *c, BatchPlan &P, const FieldArg *fa, int nf) {
   drop_graph(&P);
   Staged sf;
-  ms_status s = stage_fields(c, fa, nf, &sf);  // also leaves the descriptors on the device
+  const Tuning tune = P.tuned ? P.tune : c->tune;
+  ms_status s = stage_fields(c, fa, nf, tune.shape3, &sf);  // also leaves the descriptors on the device
   if (s != MS_OK) return s;
   Batch b = sf.b;
-  b.tune = P.tuned ? P.tune : c->tune;
+  b.tune = tune;
   const RunInfo run = c->run;
   // capacities: the sizes met, with margins; overflow is detected on the device
   unsigned long long pool_cap = run.npairs + run.npairs / 8 + 4096;
-  pool_cap = std::min(pool_cap, (unsigned long long)b.total_tiles * kTileV);
+  pool_cap = std::min(pool_cap, (unsigned long long)b.total_tiles * kPidStride);
   unsigned long long root_cap = run.nroots + run.nroots / 8 + 4096;
-  root_cap = std::min(root_cap, 2 * (unsigned long long)b.total_tiles * kExt);
+  root_cap = std::min(root_cap, 2 * (unsigned long long)b.total_tiles * kExtMax);
   const unsigned int hcap = pow2_at_least(2ull * run.m + 4096);
   s = ensure_buffer(c, &c->tscratch, &c->tscratch_bytes,
-                    tiled_scratch_bytes(b.total_tiles, nf, pool_cap, root_cap));
+                    tiled_scratch_bytes(b.total_tiles, nf, pool_cap, root_cap, b.face_stride));
   if (s != MS_OK) return s;
   s = ensure_scratch(c, rank_scratch_bytes(hcap));
   if (s != MS_OK) return s;
@@ -668,7 +671,7 @@ ms_status capture_plan(ms_ctx *c, BatchPlan &P, const FieldArg *fa, int nf) {
     graph = static_cast<int2 *>(c->graph);
   }
   TiledScratch ts;
-  tiled_scratch_carve(c->tscratch, b.total_tiles, nf, pool_cap, root_cap, &ts);
+  tiled_scratch_carve(c->tscratch, b.total_tiles, nf, pool_cap, root_cap, b.face_stride, &ts);
   if (tile_mode(b)) ts.root_tile = nullptr;
   RankScratch rs;
   rank_scratch_carve(c->scratch, hcap, &rs);
@@ -1382,6 +1385,41 @@ ms_status ms_slab_rank(ms_ctx *c, const int32_t *asc, const int32_t *desc, int64
   return MS_OK;
 }
 
+ms_status ms_set_tuning(ms_ctx *c, const ms_tuning *t) {
+  if (!c || !t) return MS_ERR_INVALID_ARG;
+  if (t->tile_ctas < 1 || t->tile_ctas > 4 || t->write_ctas < 1 || t->write_ctas > 16 ||
+      t->chase_blocks < 1 || t->chase_blocks > 4 || t->pair_blocks < 1 || t->pair_blocks > 16 ||
+      t->dynamic < 0 || t->dynamic > 1 || t->resolve_mode < -1 || t->resolve_mode > 1 ||
+      t->shape3 < 0 || t->shape3 >= kShapeCount)
+    return MS_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  Tuning u;
+  u.tile_ctas = t->tile_ctas;
+  u.write_ctas = t->write_ctas;
+  u.chase_blocks = t->chase_blocks;
+  u.pair_blocks = t->pair_blocks;
+  u.dynamic = t->dynamic;
+  u.resolve_mode = t->resolve_mode;
+  u.shape3 = t->shape3;
+  c->tune = u;
+  for (BatchPlan &P : c->plans)
+    if (!P.tuned) drop_graph(&P);
+  return MS_OK;
+}
+
+ms_status ms_get_tuning(const ms_ctx *c, ms_tuning *t) {
+  if (!c || !t) return MS_ERR_INVALID_ARG;
+  *t = ms_tuning{};
+  t->tile_ctas = c->tune.tile_ctas;
+  t->write_ctas = c->tune.write_ctas;
+  t->chase_blocks = c->tune.chase_blocks;
+  t->pair_blocks = c->tune.pair_blocks;
+  t->dynamic = c->tune.dynamic;
+  t->resolve_mode = c->tune.resolve_mode;
+  t->shape3 = c->tune.shape3;
+  return MS_OK;
+}
+
 ms_status ms_batch_graphs(ms_ctx *c, int on) {
   if (!c) return MS_ERR_INVALID_ARG;
   DeviceGuard g(c->device);
@@ -1437,7 +1475,8 @@ ms_status ms_batch_autotune(ms_ctx *c, int n_fields, const void *const *fields,
     int Tuning::*field;
     std::vector<int> values;
   };
-  const Knob knobs[] = {{&Tuning::dynamic, {1, 0}},
+  const Knob knobs[] = {{&Tuning::shape3, {kShape32x16, kShape64x8, kShape16x32, kShape16x16}},
+                        {&Tuning::dynamic, {1, 0}},
                         {&Tuning::tile_ctas, {2, 1}},
                         {&Tuning::write_ctas, {2, 4, 8}},
                         {&Tuning::chase_blocks, {3, 2}},
@@ -1475,6 +1514,7 @@ ms_status ms_batch_autotune(ms_ctx *c, int n_fields, const void *const *fields,
     out->pair_blocks = best.pair_blocks;
     out->resolve_mode = best.resolve_mode;
     out->dynamic = best.dynamic;
+    out->shape3 = best.shape3;
     out->default_ms = t_default;
     out->best_ms = t_best;
   }

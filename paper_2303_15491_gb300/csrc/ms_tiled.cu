@@ -44,66 +44,74 @@ struct Cand {
   uint32_t i;  // extended-box index of the candidate
 };
 
+template <class S>
 __device__ __forceinline__ int ext_of(int lx, int ly, int lz) {
-  return (lx + kXO) + kEX * ((ly + 1) + kEY * (lz + 1));
+  return (lx + kXO) + S::EX * ((ly + 1) + S::EY * (lz + 1));
 }
 
+template <class S>
 __device__ __forceinline__ void tile_origin(const TileGeom &g, int64_t t, int64_t *x0, int64_t *y0,
                                             int64_t *z0) {
   uint32_t r, tx, ty, tz;
   g.div_tx.divmod((uint32_t)t, &r, &tx);
   g.div_ty.divmod(r, &tz, &ty);
-  *x0 = (int64_t)tx * kTX;
-  *y0 = (int64_t)ty * kTY;
-  *z0 = (int64_t)tz * kTZ;
+  *x0 = (int64_t)tx * S::TX;
+  *y0 = (int64_t)ty * S::TY;
+  *z0 = (int64_t)tz * S::TZ;
 }
 
 // Slot of a face vertex in its tile's face-root array (first face that
 // contains it, in the order z-low, z-high, y-low, y-high, x-low, x-high), or
 // -1 for an interior vertex.
+template <class S>
 __device__ __forceinline__ int face_slot(int lx, int ly, int lz) {
-  if (lz == 0) return lx + kTX * ly;
-  if (lz == kTZ - 1) return kTX * kTY + lx + kTX * ly;
-  if (ly == 0) return 2 * kTX * kTY + lx + kTX * lz;
-  if (ly == kTY - 1) return 2 * kTX * kTY + kTX * kTZ + lx + kTX * lz;
-  if (lx == 0) return 2 * kTX * kTY + 2 * kTX * kTZ + ly + kTY * lz;
-  if (lx == kTX - 1) return 2 * kTX * kTY + 2 * kTX * kTZ + kTY * kTZ + ly + kTY * lz;
+  constexpr int TX = S::TX, TY = S::TY, TZ = S::TZ;
+  if (lz == 0) return lx + TX * ly;
+  if (lz == TZ - 1) return TX * TY + lx + TX * ly;
+  if (ly == 0) return 2 * TX * TY + lx + TX * lz;
+  if (ly == TY - 1) return 2 * TX * TY + TX * TZ + lx + TX * lz;
+  if (lx == 0) return 2 * TX * TY + 2 * TX * TZ + ly + TY * lz;
+  if (lx == TX - 1) return 2 * TX * TY + 2 * TX * TZ + TY * TZ + ly + TY * lz;
   return -1;
 }
 
 // Reference to a tile root at box index e: its global vertex index, with
 // kExitFlag set when e lies in the halo (the path continues in another tile).
+template <class S>
 __device__ __forceinline__ int32_t root_ref(const TileGeom &g, int64_t x0, int64_t y0, int64_t z0,
                                             int e) {
+  constexpr int EX = S::EX, EY = S::EY, EZ = S::EZ;
   const uint32_t ue = (uint32_t)e;
-  const uint32_t ez = ue / (kEX * kEY), r = ue - ez * (kEX * kEY);
-  const uint32_t ey = r / kEX, ex = r - ey * kEX;
-  const bool halo = ex == kXO - 1 || ex == kXO + kTX || ey == 0 || ez == 0 || ey == kEY - 1 ||
-                    ez == kEZ - 1;
+  const uint32_t ez = ue / (EX * EY), r = ue - ez * (EX * EY);
+  const uint32_t ey = r / EX, ex = r - ey * EX;
+  const bool halo = ex == kXO - 1 || ex == kXO + S::TX || ey == 0 || ez == 0 || ey == EY - 1 ||
+                    ez == EZ - 1;
   const int64_t v = (x0 + (int)ex - kXO) + g.nx * ((y0 + (int)ey - 1) + g.ny * (z0 + (int)ez - 1));
   return (int32_t)v | (halo ? kExitFlag : 0);
 }
 
 // Inverse of face_slot's layout: the vertex a face slot describes.
+template <class S>
 __device__ __forceinline__ void face_coords(int fs, int *lx, int *ly, int *lz) {
-  constexpr int kZ = kTX * kTY, kY = kTX * kTZ, kX = kTY * kTZ;
+  constexpr int TX = S::TX, TY = S::TY, TZ = S::TZ;
+  constexpr int kZ = TX * TY, kY = TX * TZ, kX = TY * TZ;
   if (fs < 2 * kZ) {
-    *lz = fs < kZ ? 0 : kTZ - 1;
+    *lz = fs < kZ ? 0 : TZ - 1;
     const int r = fs % kZ;
-    *lx = r % kTX;
-    *ly = r / kTX;
+    *lx = r % TX;
+    *ly = r / TX;
   } else if (fs < 2 * kZ + 2 * kY) {
     const int q = fs - 2 * kZ;
-    *ly = q < kY ? 0 : kTY - 1;
+    *ly = q < kY ? 0 : TY - 1;
     const int r = q % kY;
-    *lx = r % kTX;
-    *lz = r / kTX;
+    *lx = r % TX;
+    *lz = r / TX;
   } else {
     const int q = fs - 2 * kZ - 2 * kY;
-    *lx = q < kX ? 0 : kTX - 1;
+    *lx = q < kX ? 0 : TX - 1;
     const int r = q % kX;
-    *ly = r % kTY;
-    *lz = r / kTY;
+    *ly = r % TY;
+    *lz = r / TY;
   }
 }
 
@@ -147,10 +155,11 @@ __device__ __forceinline__ int32_t root_ref2(const TileGeom &g, int64_t x0, int6
   return (int32_t)v | (halo ? kExitFlag : 0);
 }
 
-// Exclusive block scan of two values per thread (kThreads threads); also
-// returns both totals.  Uses scratch[2][kThreads / 32]; ends with a barrier.
+// Exclusive block scan of two values per thread (kWarps warps); also returns
+// both totals.  Uses scratch[2][kWarps]; ends with a barrier.
+template <int kWarps>
 __device__ __forceinline__ void block_scan2(int a, int b, int *ea, int *eb, int *ta, int *tb,
-                                            int (*scratch)[kThreads / 32]) {
+                                            int (*scratch)[kWarps]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int ia = a, ib = b;
 #pragma unroll
@@ -169,7 +178,7 @@ __device__ __forceinline__ void block_scan2(int a, int b, int *ea, int *eb, int 
   __syncthreads();
   int pa = 0, pb = 0, sa = 0, sb = 0;
 #pragma unroll
-  for (int k = 0; k < kThreads / 32; ++k) {
+  for (int k = 0; k < kWarps; ++k) {
     const int va = scratch[0][k], vb = scratch[1][k];
     if (k < warp) {
       pa += va;
@@ -185,7 +194,8 @@ __device__ __forceinline__ void block_scan2(int a, int b, int *ea, int *eb, int 
   __syncthreads();
 }
 
-__device__ __forceinline__ uint32_t hash32(uint32_t k) { return (k * 0x9E3779B1u) >> (32 - kHashBits); }
+template <int kBits>
+__device__ __forceinline__ uint32_t hash32(uint32_t k) { return (k * 0x9E3779B1u) >> (32 - kBits); }
 
 // Order key of one field value (Sec. 4.1): see order_key_bits; written
 // branch-free.  Out-of-box positions get the sentinel 0, which no real value
@@ -311,9 +321,9 @@ __device__ __forceinline__ Cand omin(Cand a, Cand b) {
 // Cube extrema.  A unit cube with minimum corner c = (cx, cy, cz), cx in
 // [-1, TX-1], cy in [-1, TY-1], cz in [-1, TZ-1] (tile coordinates), has its
 // (max, min) winners' box indices at C[cube_of(c)] as max | min << 16.
-constexpr int kCX = kTX + 1, kCY = kTY + 1;
+template <class S>
 __device__ __forceinline__ int cube_of(int cx, int cy, int cz) {
-  return (cx + 1) + kCX * ((cy + 1) + kCY * (cz + 1));
+  return (cx + 1) + S::CX * ((cy + 1) + S::CY * (cz + 1));
 }
 
 // Max and min of two candidates in one step (b at higher indices); the
@@ -326,7 +336,7 @@ __device__ __forceinline__ void mm2(Cand a_max, Cand a_min, Cand b_max, Cand b_m
 }
 
 // The extremum pair of one cube from 8 box loads, x pairs, then y, then z.
-template <bool kRaw>
+template <class S, bool kRaw>
 __device__ __forceinline__ uint32_t cube_extrema(const uint32_t *__restrict__ K, int cx, int cy,
                                                  int cz) {
   typedef Ord<kRaw> O;
@@ -336,7 +346,7 @@ __device__ __forceinline__ uint32_t cube_extrema(const uint32_t *__restrict__ K,
     Cand ymax[2], ymin[2];
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy) {
-      const uint32_t e = (uint32_t)((cx + kXO) + kEX * ((cy + dy + 1) + kEY * (cz + dz + 1)));
+      const uint32_t e = (uint32_t)((cx + kXO) + S::EX * ((cy + dy + 1) + S::EY * (cz + dz + 1)));
       const uint32_t k0 = K[e], k1 = K[e + 1];
       ymax[dy] = omax<kRaw>(Cand{k0, e}, Cand{k1, e + 1});
       ymin[dy] = omin<kRaw>(Cand{O::mk(k0), e}, Cand{O::mk(k1), e + 1});
@@ -355,15 +365,16 @@ __device__ __forceinline__ uint32_t cube_extrema(const uint32_t *__restrict__ K,
 // computed once: the cubes with c = (lx, ly, .) by thread (lx, ly) streaming
 // z, the remaining cubes (some coordinate -1) spread over the block.  The
 // results go to w[] in registers; C lives in P's area until then.
-template <bool kRaw>
+template <class S, bool kRaw>
 __device__ __forceinline__ void steepest_tile(const uint32_t *__restrict__ K, uint32_t *C, int lx,
                                               int ly, bool col_in, int nz_here, uint32_t *w,
                                               bool *nan) {
   typedef Ord<kRaw> O;
+  constexpr int kEX = S::EX, kEY = S::EY, kTZ_ = S::TZ;
   {
     Cand h2max{}, h2min{};
 #pragma unroll 2
-    for (int p = 0; p <= kTZ; ++p) {
+    for (int p = 0; p <= kTZ_; ++p) {
       const uint32_t e = (uint32_t)((lx + kXO) + kEX * ((ly + 1) + kEY * (p + 1)));
       const uint32_t k00 = K[e], k10 = K[e + 1], k01 = K[e + kEX], k11 = K[e + kEX + 1];
       if (kRaw && p < nz_here && col_in) *nan |= is_nan_bits(k00);
@@ -374,16 +385,17 @@ __device__ __forceinline__ void steepest_tile(const uint32_t *__restrict__ K, ui
       const Cand pmax = omax<kRaw>(a_max, b_max), pmin = omin<kRaw>(a_min, b_min);
       if (p >= 1) {
         const Cand m = omax<kRaw>(h2max, pmax), n = omin<kRaw>(h2min, pmin);
-        C[cube_of(lx, ly, p - 1)] = m.i | (n.i << 16);
+        C[cube_of<S>(lx, ly, p - 1)] = m.i | (n.i << 16);
       }
       h2max = pmax;
       h2min = pmin;
     }
   }
-  // cubes with a coordinate at -1: cz = -1 (kCX x kCY), then cy = -1 with cz
-  // >= 0 (kCX x kTZ), then cx = -1 with cy, cz >= 0 (kTY x kTZ)
-  constexpr int kA = kCX * kCY, kB = kCX * kTZ, kCn = kTY * kTZ;
-  for (int j = threadIdx.x; j < kA + kB + kCn; j += kThreads) {
+  // cubes with a coordinate at -1: cz = -1 (CX x CY), then cy = -1 with cz
+  // >= 0 (CX x TZ), then cx = -1 with cy, cz >= 0 (TY x TZ)
+  constexpr int kCX = S::CX, kCY = S::CY, kTY = S::TY;
+  constexpr int kA = kCX * kCY, kB = kCX * kTZ_, kCn = kTY * kTZ_;
+  for (int j = threadIdx.x; j < kA + kB + kCn; j += S::Threads) {
     int cx, cy, cz;
     if (j < kA) {
       cz = -1;
@@ -400,13 +412,13 @@ __device__ __forceinline__ void steepest_tile(const uint32_t *__restrict__ K, ui
       cy = q % kTY;
       cz = q / kTY;
     }
-    C[cube_of(cx, cy, cz)] = cube_extrema<kRaw>(K, cx, cy, cz);
+    C[cube_of<S>(cx, cy, cz)] = cube_extrema<S, kRaw>(K, cx, cy, cz);
   }
   __syncthreads();
 #pragma unroll
-  for (int lz = 0; lz < kTZ; ++lz) {
-    const uint32_t ev = (uint32_t)ext_of(lx, ly, lz);
-    const uint32_t hi = C[cube_of(lx, ly, lz)], lo = C[cube_of(lx - 1, ly - 1, lz - 1)];
+  for (int lz = 0; lz < kTZ_; ++lz) {
+    const uint32_t ev = (uint32_t)ext_of<S>(lx, ly, lz);
+    const uint32_t hi = C[cube_of<S>(lx, ly, lz)], lo = C[cube_of<S>(lx - 1, ly - 1, lz - 1)];
     const uint32_t ua = lo & 0xffffu, ub = hi & 0xffffu, da = lo >> 16, db = hi >> 16;
     const uint32_t up = O::ge(K[ub], K[ua]) ? ub : ua;  // the upper cube lies at higher indices
     const uint32_t dn = O::lt(O::mk(K[db]), O::mk(K[da])) ? db : da;
@@ -415,21 +427,18 @@ __device__ __forceinline__ void steepest_tile(const uint32_t *__restrict__ K, ui
   __syncthreads();  // C is dead; P may be written
 }
 
-// First-fit insert of key into the open-addressing pair set H, starting at
-// slot s; returns the key's slot.
+// First-fit insert of key into the open-addressing pair set H of kHashN
+// slots, starting at slot s; returns the key's slot.
+template <int kHashN>
 __device__ __forceinline__ uint32_t pairset_insert(uint32_t *H, uint32_t key, uint32_t s) {
-  for (int probe = 0; probe < kHash; ++probe) {
+  for (int probe = 0; probe < kHashN; ++probe) {
     uint32_t cur = H[s];
     if (cur == kEmpty32) cur = atomicCAS(&H[s], kEmpty32, key);
     if (cur == kEmpty32 || cur == key) return s;
-    s = (s + 1) & (kHash - 1);
+    s = (s + 1) & (kHashN - 1);
   }
   return 0;  // unreachable: the set holds one slot per vertex
 }
-
-static_assert(2 * kBmW3 <= 2 * kThreads && 2 * kBmW2 <= 2 * kThreads,
-              "two bitmap words per thread cover both root bitmaps");
-static_assert(kHash == kThreads * 16, "each thread numbers 16 consecutive set slots");
 
 // An empty tile record (a tile skipped for a NaN): no pairs, no roots.
 __device__ __forceinline__ void empty_tile(const TiledScratch &ts, int64_t gt) {
@@ -460,13 +469,19 @@ __device__ __forceinline__ void empty_tile(const TiledScratch &ts, int64_t gt) {
 //       vertex its pair's dense number.
 // A (kHash + kHash / 2 words) and B (kTileV + 4 kBmW words) are free
 // shared-memory areas; valid run entries are those of a column with col_in,
-// below n_here.
-template <int kBmW>
+// below n_here.  A tile of kThreads threads holds kTileV = 16 kThreads
+// vertices, and its set kHash = kTileV slots (thread t numbers slots
+// 16t .. 16t + 15).
+template <int kThreads, int kBmW>
 __device__ __forceinline__ void number_tile_pairs(uint32_t *A, uint32_t *B, const uint32_t (&w)[kRun],
                                                   bool col_in, int n_here, int64_t gt,
                                                   const TiledScratch &ts, DevStatus *st,
                                                   int (*s_scan2)[kThreads / 32],
                                                   unsigned long long *s_base) {
+  constexpr int kTileV = kThreads * kRun;
+  constexpr int kHash = kTileV;
+  constexpr int kHashBits = ilog2(kHash);
+  static_assert(kBmW <= kThreads, "two bitmap words per thread cover both root bitmaps");
   const int t = threadIdx.x;
   uint32_t *H = A;
   uint16_t *D = reinterpret_cast<uint16_t *>(A + kHash);
@@ -485,7 +500,7 @@ __device__ __forceinline__ void number_tile_pairs(uint32_t *A, uint32_t *B, cons
     for (int j = 0; j < kRun; ++j) {
       const uint32_t key = w[j];
       if (col_in && j < n_here && key != prev) {
-        ps = pairset_insert(H, key, hash32(key));
+        ps = pairset_insert<kHash>(H, key, hash32<kHashBits>(key));
         prev = key;
       }
       if (j & 1)
@@ -509,7 +524,7 @@ __device__ __forceinline__ void number_tile_pairs(uint32_t *A, uint32_t *B, cons
 #pragma unroll
     for (int k = 0; k < 16; ++k) cnt += hk[k] != kEmpty32;
     int ex, e2, t2;
-    block_scan2(cnt, 0, &ex, &e2, &npairs, &t2, s_scan2);
+    block_scan2<kThreads / 32>(cnt, 0, &ex, &e2, &npairs, &t2, s_scan2);
     int id = ex;
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
@@ -532,7 +547,7 @@ __device__ __forceinline__ void number_tile_pairs(uint32_t *A, uint32_t *B, cons
     const int a = w0 < 2 * kBmW ? __popc(BW[w0]) : 0;
     const int b = w1 < 2 * kBmW ? __popc(BW[w1]) : 0;
     int ea, eb, ta, tb;
-    block_scan2(a, b, &ea, &eb, &ta, &tb, s_scan2);  // ends with a barrier
+    block_scan2<kThreads / 32>(a, b, &ea, &eb, &ta, &tb, s_scan2);  // ends with a barrier
     if (w0 < 2 * kBmW) PW[w0] = (uint32_t)ea;
     if (w1 < 2 * kBmW) PW[w1] = (uint32_t)(ta + eb);
     nroots = ta + tb;
@@ -589,7 +604,7 @@ __device__ __forceinline__ void number_tile_pairs(uint32_t *A, uint32_t *B, cons
 #pragma unroll
     for (int j = 0; j < kRun; j += 2)
       packed[j / 2] = (uint32_t)D[slot2[j / 2] & 0xffffu] | ((uint32_t)D[slot2[j / 2] >> 16] << 16);
-    uint4 *pid4 = reinterpret_cast<uint4 *>(ts.pid + gt * (int64_t)kTileV +
+    uint4 *pid4 = reinterpret_cast<uint4 *>(ts.pid + gt * (int64_t)kPidStride +
                                             (int64_t)threadIdx.x * kRun);
     pid4[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
     pid4[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
@@ -615,8 +630,8 @@ __device__ __forceinline__ long long queue_next(bool dyn, long long k, const lon
   return dyn ? *s_next : k + gridDim.x;
 }
 
-// One CTA per tile (persistent).  Thread (lane, warp) owns the z-column of
-// vertices (x0 + lane, y0 + warp, z0 .. z0 + TZ - 1).
+// One CTA per tile (persistent).  Thread t owns the z-column of vertices
+// (x0 + t % TX, y0 + t / TX, z0 .. z0 + TZ - 1).
 //
 // Shared memory (dynamic): K, the staged field values of the tile and its
 // halo in box order (reused for the pair set once the steepest step is
@@ -634,8 +649,11 @@ __device__ __forceinline__ int field_of(const Batch &b, int64_t gt) {
   return lo;
 }
 
-template <bool kSingle>
-__global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScratch ts, DevStatus *st) {
+template <bool kSingle, class S>
+__global__ void __launch_bounds__(S::Threads, 1024 / S::Threads) k_tile_local(Batch bt, TiledScratch ts,
+                                                                             DevStatus *st) {
+  constexpr int kTX = S::TX, kTY = S::TY, kTZ_ = S::TZ, kEX = S::EX, kEY = S::EY, kEZ = S::EZ;
+  constexpr int kExt = S::Ext, kThreads = S::Threads, kFace = S::Face;
   extern __shared__ __align__(128) uint32_t dsmem[];
   uint32_t *K = dsmem;         // kExt words: values / keys, then pair-numbering scratch
   uint32_t *P = dsmem + kExt;  // kExt words: up | dn << 16, box indices
@@ -643,8 +661,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
   __shared__ unsigned long long s_base[2];
   __shared__ int s_abort;
   __shared__ int s_scan2[2][kThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int lx = lane, ly = warp;
+  const int lane = threadIdx.x & 31;
+  const int lx = threadIdx.x % kTX, ly = threadIdx.x / kTX;
   bool nan = false;
   uint32_t parity = 0;
   if (threadIdx.x == 0) s_abort = 0;
@@ -665,10 +683,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
     const bool tma = fd.tma != 0;
     const int64_t tile = gt - fd.tile_base;  // within the field
     int64_t x0, y0, z0;
-    tile_origin(g, tile, &x0, &y0, &z0);
+    tile_origin<S>(g, tile, &x0, &y0, &z0);
     // tile and halo entirely inside the field: raw float comparisons
     const bool raw = tma && x0 >= 1 && y0 >= 1 && z0 >= 1 && x0 + kTX < g.nx &&
-                     y0 + kTY < g.ny && z0 + kTZ < g.nz;
+                     y0 + kTY < g.ny && z0 + kTZ_ < g.nz;
 
     // ---- field values of the tile + halo into K
     if (tma) {
@@ -684,15 +702,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
       parity ^= 1u;
     }
     // ---- boundary tiles: order keys in place (sentinel 0 outside the
-    // field).  All tiles: halo pointers are self-loops.
+    // field).  All tiles: halo pointers are self-loops.  The kTX threads of
+    // a row group (one y of the tile) take one box row at a time; the first
+    // two also take the row's halo columns.
     if (!raw) {
-      const int exe = lane == 0 ? kXO - 1 : kXO + kTX;  // lanes 0, 1: the halo columns
+      const int exe = lx == 0 ? kXO - 1 : kXO + kTX;  // threads lx = 0, 1: the halo columns
       const int64_t xl = x0 + lx, xe = x0 + exe - kXO;
       const bool x_in = xl < g.nx, xe_in = xe >= 0 && xe < g.nx;
 #pragma unroll 4
-      for (int r = warp; r < kEY * kEZ; r += kThreads / 32) {
+      for (int r = ly; r < kEY * kEZ; r += kTY) {
         const int ey = r % kEY, ez = r / kEY;
-        const bool interior = ey >= 1 && ey <= kTY && ez >= 1 && ez <= kTZ;
+        const bool interior = ey >= 1 && ey <= kTY && ez >= 1 && ez <= kTZ_;
         const int eb = kEX * r;
         {
           const int64_t y = y0 + ey - 1, z = z0 + ez - 1;
@@ -700,15 +720,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
           uint32_t b, be = 0;
           if (tma) {
             b = K[eb + kXO + lx];
-            if (lane < 2) be = K[eb + exe];
+            if (lx < 2) be = K[eb + exe];
           } else {
             const int64_t row = y * g.nx + z * g.nx * g.ny;
             b = (row_in && x_in) ? raw_bits(field, dtype, row + xl) : 0u;
-            if (lane < 2 && row_in && xe_in) be = raw_bits(field, dtype, row + xe);
+            if (lx < 2 && row_in && xe_in) be = raw_bits(field, dtype, row + xe);
           }
           if (row_in && x_in && interior) nan |= is_nan_bits(b);
           K[eb + kXO + lx] = (row_in && x_in) ? key_of(b) : 0u;
-          if (lane < 2) K[eb + exe] = (row_in && xe_in) ? key_of(be) : 0u;
+          if (lx < 2) K[eb + exe] = (row_in && xe_in) ? key_of(be) : 0u;
         }
       }
     }
@@ -718,12 +738,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
     // vertices need, once each, into C (in P's area); then per vertex the
     // better of its two cubes; then P = pointers, halo = self-loops
     const bool col_in = x0 + lx < g.nx && y0 + ly < g.ny;
-    const int nz_here = (int)min((int64_t)kTZ, g.nz - z0);
-    uint32_t w[kTZ];
+    const int nz_here = (int)min((int64_t)kTZ_, g.nz - z0);
+    uint32_t w[kRun];
     if (raw)
-      steepest_tile<true>(K, P, lx, ly, col_in, nz_here, w, &nan);
+      steepest_tile<S, true>(K, P, lx, ly, col_in, nz_here, w, &nan);
     else
-      steepest_tile<false>(K, P, lx, ly, col_in, nz_here, w, &nan);
+      steepest_tile<S, false>(K, P, lx, ly, col_in, nz_here, w, &nan);
     if (__syncthreads_or(nan)) {
       // the call fails with MS_ERR_NAN_INPUT; skip the rest of this tile
       empty_tile(ts, gt);
@@ -731,11 +751,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
       continue;
     }
 #pragma unroll
-    for (int lz = 0; lz < kTZ; ++lz) P[ext_of(lx, ly, lz)] = w[lz];
+    for (int lz = 0; lz < kTZ_; ++lz) P[ext_of<S>(lx, ly, lz)] = w[lz];
     // the halo points at itself: the 2 kEZ + 2 kTY box rows with ey or ez on
-    // the halo (one warp per row), then the two halo columns of the kTY x kTZ
-    // inner rows (one thread each)
-    for (int j = warp; j < 2 * kEZ + 2 * kTY; j += kThreads / 32) {
+    // the halo (one row group per row), then the two halo columns of the
+    // kTY x kTZ inner rows
+    for (int j = ly; j < 2 * kEZ + 2 * kTY; j += kTY) {
       int ey, ez;
       if (j < 2 * kEZ) {
         ey = (j & 1) ? kEY - 1 : 0;
@@ -747,16 +767,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
       }
       const int eb = kEX * (ey + kEY * ez);
       P[eb + kXO + lx] = (uint32_t)(eb + kXO + lx) * 0x10001u;
-      if (lane < 2) {
-        const int e = eb + (lane == 0 ? kXO - 1 : kXO + kTX);
+      if (lx < 2) {
+        const int e = eb + (lx == 0 ? kXO - 1 : kXO + kTX);
         P[e] = (uint32_t)e * 0x10001u;
       }
     }
-    static_assert(kThreads == 2 * kTY * kTZ, "one thread per inner-row halo column");
-    {
-      const int row = threadIdx.x >> 1;
+    for (int i = threadIdx.x; i < 2 * kTY * kTZ_; i += kThreads) {
+      const int row = i >> 1;
       const int e = kEX * ((1 + (row % kTY)) + kEY * (1 + row / kTY)) +
-                    ((threadIdx.x & 1) ? kXO + kTX : kXO - 1);
+                    ((i & 1) ? kXO + kTX : kXO - 1);
       P[e] = (uint32_t)e * 0x10001u;
     }
     __syncthreads();
@@ -778,12 +797,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
         if (!rows) break;
         uint32_t still = 0;
 #pragma unroll
-        for (int lz = 0; lz < kTZ; ++lz) {
+        for (int lz = 0; lz < kTZ_; ++lz) {
           if ((rows >> lz) & 1u) {
             const uint32_t nw = jump1(P, w[lz]);
             if (nw != w[lz]) {
               w[lz] = nw;
-              P[ext_of(lx, ly, lz)] = nw;
+              P[ext_of<S>(lx, ly, lz)] = nw;
               still |= 1u << lz;
             }
           }
@@ -796,16 +815,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local(Batch bt, TiledScrat
     // ---- face roots (final pointers of the tile's face vertices), written
     // cooperatively from P: other tiles' paths enter through these vertices
     {
-      uint32_t *face = ts.face + gt * (int64_t)kFace;
+      uint32_t *face = ts.face + gt * (int64_t)bt.face_stride;
       for (int fs = threadIdx.x; fs < kFace; fs += kThreads) {
         int fx, fy, fz;
-        face_coords(fs, &fx, &fy, &fz);
-        if (x0 + fx < g.nx && y0 + fy < g.ny && fz < nz_here) face[fs] = P[ext_of(fx, fy, fz)];
+        face_coords<S>(fs, &fx, &fy, &fz);
+        if (x0 + fx < g.nx && y0 + fy < g.ny && fz < nz_here) face[fs] = P[ext_of<S>(fx, fy, fz)];
       }
     }
     __syncthreads();
 
-    number_tile_pairs<kBmW3>(K, P, w, col_in, nz_here, gt, ts, st, s_scan2, s_base);
+    number_tile_pairs<kThreads, S::BmW>(K, P, w, col_in, nz_here, gt, ts, st, s_scan2, s_base);
   }
   if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&st->nan_flag, 1u);
 }
@@ -867,14 +886,14 @@ __device__ __forceinline__ void steepest_run2(const uint32_t *__restrict__ K, in
 // 3D fields' in a batch).  Thread (lane, warp) owns the run of kRun vertices
 // at x = lane + 32 (warp % 4), y = kRun (warp / 4) + 0 .. kRun - 1.
 template <bool kSingle>
-__global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScratch ts, DevStatus *st) {
+__global__ void __launch_bounds__(k2Threads, 2) k_tile_local2(Batch bt, TiledScratch ts, DevStatus *st) {
   extern __shared__ __align__(128) uint32_t dsmem[];
   uint32_t *K = dsmem;            // k2KArea words: values / keys, then the pair list and bitmaps
   uint32_t *P = dsmem + k2KArea;  // k2PArea words: up | dn << 16, then the pair set
   __shared__ __align__(8) uint64_t s_bar;
   __shared__ unsigned long long s_base[2];
   __shared__ int s_abort;
-  __shared__ int s_scan2[2][kThreads / 32];
+  __shared__ int s_scan2[2][k2Threads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cx = lane + 32 * (warp & 3), cy0 = kRun * (warp >> 2);
   bool nan = false;
@@ -913,7 +932,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScra
     // boundary tiles: order keys in place, sentinel 0 outside the field
     if (!raw) {
       constexpr int kCols = k2TX + 2;  // the tile's columns and the two halo columns
-      for (int i = threadIdx.x; i < k2EY * kCols; i += kThreads) {
+      for (int i = threadIdx.x; i < k2EY * kCols; i += k2Threads) {
         const int r = i / kCols, c = i - r * kCols + kXO - 1;
         const int e = r * k2EX + c;
         const int64_t x = x0 + c - kXO, y = y0 + r - 1;
@@ -944,7 +963,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScra
 #pragma unroll
     for (int j = 0; j < kRun; ++j) P[ext2_of(cx, cy0 + j)] = w[j];
     // the halo ring points at itself
-    for (int i = threadIdx.x; i < 2 * (k2TX + 2) + 2 * k2TY; i += kThreads) {
+    for (int i = threadIdx.x; i < 2 * (k2TX + 2) + 2 * k2TY; i += k2Threads) {
       int e;
       if (i < k2TX + 2)
         e = kXO - 1 + i;
@@ -982,8 +1001,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScra
     __syncthreads();
 
     {
-      uint32_t *face = ts.face + gt * (int64_t)kFace;
-      for (int fs = threadIdx.x; fs < k2Face; fs += kThreads) {
+      uint32_t *face = ts.face + gt * (int64_t)bt.face_stride;
+      for (int fs = threadIdx.x; fs < k2Face; fs += k2Threads) {
         int fx, fy;
         face_coords2(fs, &fx, &fy);
         if (x0 + fx < g.nx && y0 + fy < g.ny) face[fs] = P[ext2_of(fx, fy)];
@@ -991,37 +1010,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_tile_local2(Batch bt, TiledScra
     }
     __syncthreads();
 
-    number_tile_pairs<kBmW2>(P, K, w, col_in, n_here, gt, ts, st, s_scan2, s_base);
+    number_tile_pairs<k2Threads, kBmW2>(P, K, w, col_in, n_here, gt, ts, st, s_scan2, s_base);
   }
   if (__any_sync(0xffffffffu, nan) && lane == 0) atomicOr(&st->nan_flag, 1u);
 }
 
 // Global face-graph slot of a face vertex v (a tile exit) of a field whose
-// first tile is tile_base.
+// first tile is tile_base (fstride slots a tile).
+template <class S>
 __device__ __forceinline__ uint32_t slot_of_vertex(const TileGeom &g, long long tile_base,
-                                                   uint32_t v) {
+                                                   uint32_t v, int fstride) {
   if (g.flat) {
     uint32_t x, y;
     g.div_nx.divmod(v, &y, &x);
     const uint32_t tx = x / k2TX, ty = y / k2TY;
     const int fs = face_slot2((int)(x - tx * k2TX), (int)(y - ty * k2TY));
-    return (uint32_t)((tile_base + tx + (long long)g.tx * ty) * kFace + fs);
+    return (uint32_t)((tile_base + tx + (long long)g.tx * ty) * fstride + fs);
   }
   uint32_t q, x, y, z;
   g.div_nx.divmod(v, &q, &x);
   g.div_ny.divmod(q, &z, &y);
-  const uint32_t tx = x / kTX, ty = y / kTY, tz = z / kTZ;
-  const int fs = face_slot((int)(x - tx * kTX), (int)(y - ty * kTY), (int)(z - tz * kTZ));
-  return (uint32_t)((tile_base + tx + (long long)g.tx * (ty + (long long)g.ty * tz)) * kFace + fs);
+  const uint32_t tx = x / S::TX, ty = y / S::TY, tz = z / S::TZ;
+  const int fs = face_slot<S>((int)(x - tx * S::TX), (int)(y - ty * S::TY), (int)(z - tz * S::TZ));
+  return (uint32_t)((tile_base + tx + (long long)g.tx * (ty + (long long)g.ty * tz)) * fstride + fs);
 }
 
-// Face-graph slots are numbered kFace per tile; 2D tiles use the first
-// k2Face.  Valid slot i (of face_graph_valid(b)) -> (tile, face slot).
+// Face-graph slots are numbered face_stride per tile (the 3D shape's face
+// count); 2D tiles use the first k2Face.  Valid slot i (of
+// face_graph_valid(b)) -> (tile, face slot).
 __device__ __forceinline__ void valid_slot(const Batch &b, long long i, long long *gt, int *fs) {
-  const long long n3 = b.tiles3 * (long long)kFace;
+  const long long f3 = b.face_stride;
+  const long long n3 = b.tiles3 * f3;
   if (i < n3) {
-    *gt = i / kFace;
-    *fs = (int)(i - *gt * kFace);
+    *gt = i / f3;
+    *fs = (int)(i - *gt * f3);
   } else {
     const long long j = i - n3;
     *gt = b.tiles3 + j / k2Face;
@@ -1030,12 +1052,13 @@ __device__ __forceinline__ void valid_slot(const Batch &b, long long i, long lon
 }
 
 __host__ __device__ __forceinline__ long long face_graph_valid(const Batch &b) {
-  return b.tiles3 * (long long)kFace + (b.total_tiles - b.tiles3) * (long long)k2Face;
+  return b.tiles3 * (long long)b.face_stride + (b.total_tiles - b.tiles3) * (long long)k2Face;
 }
 
 // The face graph from the tiles' face roots (local box indices): exits
 // become the global slot of the exit vertex, extrema their vertex index |
 // kSlotFinal.  Slots of vertices outside their field get a final dummy.
+template <class S>
 __global__ void k_face_graph_build(Batch bt, TiledScratch ts, int2 *__restrict__ graph) {
   const long long nvalid = face_graph_valid(bt);
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nvalid;
@@ -1047,7 +1070,7 @@ __global__ void k_face_graph_build(Batch bt, TiledScratch ts, int2 *__restrict__
     const FieldDesc &fd = bt.fields[fi];
     const TileGeom &g = fd.g;
     const long long tile = gt - fd.tile_base;
-    const long long slot = gt * kFace + fs;
+    const long long slot = gt * (long long)bt.face_stride + fs;
     int32_t ru, rd;
     bool in;
     const uint32_t w = ts.face[slot];
@@ -1061,16 +1084,16 @@ __global__ void k_face_graph_build(Batch bt, TiledScratch ts, int2 *__restrict__
       rd = in ? root_ref2(g, x0, y0, (int)(w >> 16)) : 0;
     } else {
       int64_t x0, y0, z0;
-      tile_origin(g, tile, &x0, &y0, &z0);
+      tile_origin<S>(g, tile, &x0, &y0, &z0);
       int fx, fy, fz;
-      face_coords(fs, &fx, &fy, &fz);
+      face_coords<S>(fs, &fx, &fy, &fz);
       in = x0 + fx < g.nx && y0 + fy < g.ny && z0 + fz < g.nz;
-      ru = in ? root_ref(g, x0, y0, z0, (int)(w & 0xffffu)) : 0;
-      rd = in ? root_ref(g, x0, y0, z0, (int)(w >> 16)) : 0;
+      ru = in ? root_ref<S>(g, x0, y0, z0, (int)(w & 0xffffu)) : 0;
+      rd = in ? root_ref<S>(g, x0, y0, z0, (int)(w >> 16)) : 0;
     }
     auto enc = [&](int32_t r) -> int32_t {
       if (!(r & kExitFlag)) return (int32_t)((uint32_t)r | kSlotFinal);
-      return (int32_t)slot_of_vertex(g, fd.tile_base, (uint32_t)(r & ~kExitFlag));
+      return (int32_t)slot_of_vertex<S>(g, fd.tile_base, (uint32_t)(r & ~kExitFlag), bt.face_stride);
     };
     graph[slot] = in ? make_int2(enc(ru), enc(rd)) : make_int2((int32_t)kSlotFinal, (int32_t)kSlotFinal);
   }
@@ -1081,14 +1104,14 @@ __global__ void k_face_graph_build(Batch bt, TiledScratch ts, int2 *__restrict__
 // Sets st->round_open[round] if any entry is still not final.
 __global__ void k_face_graph_round(Batch bt, int2 *__restrict__ graph, int round, DevStatus *st) {
   const long long nvalid = face_graph_valid(bt);
-  const long long nslots = bt.total_tiles * (long long)kFace;
+  const long long nslots = bt.total_tiles * (long long)bt.face_stride;
   bool open = false;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nvalid;
        i += (long long)gridDim.x * blockDim.x) {
     long long gt;
     int fs;
     valid_slot(bt, i, &gt, &fs);
-    const long long slot = gt * kFace + fs;
+    const long long slot = gt * (long long)bt.face_stride + fs;
     int2 a = graph[slot];
     bool ch = false;
     // two jumps per round: an entry then points (more than) three times as far
@@ -1140,24 +1163,24 @@ __device__ __forceinline__ bool call_failed(const DevStatus *st) {
 //   halo:    bit 31, bits 0-11 face slot, 12-13 dx + 1, 14-15 dy + 1, 16-17 dz + 1
 constexpr uint32_t kHaloBit = 0x80000000u;
 
-template <bool kFlat>
+template <bool kFlat, class S>
 __device__ __forceinline__ uint32_t chase_code(int e) {
   int lx, ly, lz = 0;
   if (kFlat) {
     const int ey = e / k2EX;
     lx = e - ey * k2EX - kXO, ly = ey - 1;
   } else {
-    const int ez = e / (kEX * kEY), r = e - ez * (kEX * kEY), ey = r / kEX;
-    lx = r - ey * kEX - kXO, ly = ey - 1, lz = ez - 1;
+    const int ez = e / (S::EX * S::EY), r = e - ez * (S::EX * S::EY), ey = r / S::EX;
+    lx = r - ey * S::EX - kXO, ly = ey - 1, lz = ez - 1;
   }
-  constexpr int TX = kFlat ? k2TX : kTX, TY = kFlat ? k2TY : kTY, TZ = kFlat ? 1 : kTZ;
+  constexpr int TX = kFlat ? k2TX : S::TX, TY = kFlat ? k2TY : S::TY, TZ = kFlat ? 1 : S::TZ;
   const int dx = lx < 0 ? -1 : (lx >= TX ? 1 : 0);
   const int dy = ly < 0 ? -1 : (ly >= TY ? 1 : 0);
   const int dz = kFlat ? 0 : (lz < 0 ? -1 : (lz >= TZ ? 1 : 0));
   if ((dx | dy | dz) == 0) return (uint32_t)lx | ((uint32_t)ly << 7) | ((uint32_t)lz << 13);
   if (lx < -1 || lx > TX) return kHaloBit;  // a padding column: never a root
   const int fs = kFlat ? face_slot2(lx - dx * TX, ly - dy * TY)
-                       : face_slot(lx - dx * TX, ly - dy * TY, lz - dz * TZ);
+                       : face_slot<S>(lx - dx * TX, ly - dy * TY, lz - dz * TZ);
   return kHaloBit | (uint32_t)fs | ((uint32_t)(dx + 1) << 12) | ((uint32_t)(dy + 1) << 14) |
          ((uint32_t)(dz + 1) << 16);
 }
@@ -1172,17 +1195,18 @@ __device__ __forceinline__ uint32_t chase_code(int e) {
 constexpr int kChaseThreads = 512;
 constexpr int kInFlight = 4;
 
-template <bool kFlat, bool kSingle>
+template <bool kFlat, bool kSingle, class S>
 __global__ void __launch_bounds__(kChaseThreads, 2) k_chase_flat(Batch bt, TiledScratch ts,
                                                                   const int2 *__restrict__ graph,
                                                                   long long probe_stride,
                                                                   DevStatus *st) {
   if (call_failed(st)) return;
   extern __shared__ uint32_t LUT[];
-  constexpr int kE = kFlat ? k2Ext : kExt;
-  constexpr int TX = kFlat ? k2TX : kTX, TY = kFlat ? k2TY : kTY, TZ = kFlat ? 1 : kTZ;
-  constexpr int kFaceN = kFlat ? k2Face : kFace;
-  for (int e = threadIdx.x; e < kE; e += kChaseThreads) LUT[e] = chase_code<kFlat>(e);
+  constexpr int kE = kFlat ? k2Ext : S::Ext;
+  constexpr int TX = kFlat ? k2TX : S::TX, TY = kFlat ? k2TY : S::TY, TZ = kFlat ? 1 : S::TZ;
+  constexpr int kFaceN = kFlat ? k2Face : S::Face;
+  const long long fstride = bt.face_stride;
+  for (int e = threadIdx.x; e < kE; e += kChaseThreads) LUT[e] = chase_code<kFlat, S>(e);
   __syncthreads();
   const bool probe = probe_stride > 0;
   const unsigned long long cap = ts.root_cap;
@@ -1249,7 +1273,7 @@ __global__ void __launch_bounds__(kChaseThreads, 2) k_chase_flat(Batch bt, Tiled
           done = true;
         } else {
           const long long slot =
-              (fd.tile_base + (long long)ntx + (long long)gtx * (nty + (long long)gty * ntz)) * kFace +
+              (fd.tile_base + (long long)ntx + (long long)gtx * (nty + (long long)gty * ntz)) * fstride +
               (code & 0xfffu);
           if (graph) {  // the jumped face graph knows where the path ends
             const int2 gv = graph[slot];
@@ -1300,17 +1324,18 @@ __global__ void __launch_bounds__(kChaseThreads, 2) k_chase_flat(Batch bt, Tiled
 // its next root in that place: one long chain holds up no other chase.
 // kFlat: the 2D tiles (which follow the 3D ones).
 
-template <bool kFlat, bool kSingle>
+template <bool kFlat, bool kSingle, class S>
 __global__ void __launch_bounds__(kChaseThreads) k_chase_tiles(Batch bt, TiledScratch ts,
                                                                const int2 *__restrict__ graph,
                                                                long long probe_stride,
                                                                DevStatus *st) {
   if (call_failed(st)) return;
   extern __shared__ uint32_t LUT[];
-  constexpr int kE = kFlat ? k2Ext : kExt;
-  constexpr int TX = kFlat ? k2TX : kTX, TY = kFlat ? k2TY : kTY, TZ = kFlat ? 1 : kTZ;
-  constexpr int kFaceN = kFlat ? k2Face : kFace;
-  for (int e = threadIdx.x; e < kE; e += kChaseThreads) LUT[e] = chase_code<kFlat>(e);
+  constexpr int kE = kFlat ? k2Ext : S::Ext;
+  constexpr int TX = kFlat ? k2TX : S::TX, TY = kFlat ? k2TY : S::TY, TZ = kFlat ? 1 : S::TZ;
+  constexpr int kFaceN = kFlat ? k2Face : S::Face;
+  const long long fstride = bt.face_stride;
+  for (int e = threadIdx.x; e < kE; e += kChaseThreads) LUT[e] = chase_code<kFlat, S>(e);
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const bool probe = probe_stride > 0;
@@ -1329,7 +1354,7 @@ __global__ void __launch_bounds__(kChaseThreads) k_chase_tiles(Batch bt, TiledSc
     const int fi = kSingle ? 0 : field_of(bt, gt);
     const FieldDesc &fd = kSingle ? bt.f0 : bt.fields[fi];
     const TileGeom &g = fd.g;
-    const uint32_t *__restrict__ face = ts.face + fd.tile_base * (long long)kFace;
+    const uint32_t *__restrict__ face = ts.face + fd.tile_base * fstride;
     const int gtx = (int)g.tx, gty = (int)g.ty, gtz = (int)g.tz;
     const uint32_t nx = (uint32_t)g.nx, ny = (uint32_t)g.ny;
     int tx0, ty0, tz0 = 0;
@@ -1386,10 +1411,10 @@ __global__ void __launch_bounds__(kChaseThreads) k_chase_tiles(Batch bt, TiledSc
             done = true;
           } else {
             const long long slot =
-                ((long long)ntx + (long long)gtx * (nty + (long long)gty * ntz)) * kFace +
+                ((long long)ntx + (long long)gtx * (nty + (long long)gty * ntz)) * fstride +
                 (code & 0xfffu);
             if (graph) {  // the jumped face graph knows where the path ends
-              const int2 gv = graph[fd.tile_base * (long long)kFace + slot];
+              const int2 gv = graph[fd.tile_base * fstride + slot];
               const uint32_t f = (uint32_t)(up ? gv.x : gv.y);
               if (!(f & kSlotFinal)) atomicOr(&st->not_converged, 1u);
               label = (int32_t)(f & ~kSlotFinal);
@@ -1717,12 +1742,13 @@ __global__ void k_field_starts(const unsigned long long *__restrict__ sorted, un
 // Per tile: stage the pair table -- each tile pair's (asc, desc) and MS id,
 // read from the global pair set at the pair's slot -- and stream the labels
 // out.  Each thread writes the run of kRun vertices it owned in the tile
-// kernel (3D: the z-column (x0 + lane, y0 + warp, .); 2D: the y-run at
+// kernel (3D: the z-column (x0 + t % TX, y0 + t / TX, .); 2D: the y-run at
 // x0 + lane + 32 (warp % 4)); its 16 pair numbers are one 32-byte vector.
-// kFlat selects the 2D tiles, which follow the 3D ones.
-template <bool kFlat, bool kSingle, bool kInPool>
-__global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch ts, RankScratch rs,
-                                                         const DevStatus *st) {
+// kFlat selects the 2D tiles, which follow the 3D ones (S: the 3D shape).
+template <bool kFlat, bool kSingle, bool kInPool, class S>
+__global__ void __launch_bounds__(kFlat ? k2Threads : S::Threads)
+    k_tile_write(Batch bt, TiledScratch ts, RankScratch rs, const DevStatus *st) {
+  constexpr int kThreads = kFlat ? k2Threads : S::Threads;
   // A replayed graph runs this kernel even when an earlier stage found its
   // buffers too small; the tile ranges and set slots are then not valid to
   // read, and the host runs the call again step by step.
@@ -1755,10 +1781,10 @@ __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch 
       stride = g.nx;
     } else {
       int64_t x0, y0, z0;
-      tile_origin(g, gt - fd.tile_base, &x0, &y0, &z0);
-      const int64_t x = x0 + lane, y = y0 + warp;
+      tile_origin<S>(g, gt - fd.tile_base, &x0, &y0, &z0);
+      const int64_t x = x0 + threadIdx.x % S::TX, y = y0 + threadIdx.x / S::TX;
       col_in = x < g.nx && y < g.ny;
-      n_here = (int)std::min<int64_t>(kTZ, g.nz - z0);
+      n_here = (int)std::min<int64_t>(S::TZ, g.nz - z0);
       stride = g.nx * g.ny;
       v0 = x + g.nx * y + stride * z0;
     }
@@ -1772,7 +1798,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_write(Batch bt, TiledScratch 
     const int first = batch ? (int)ts.fstart[fi] : 0;
     uint4 q0 = make_uint4(0, 0, 0, 0), q1 = q0;
     if (col_in) {
-      const uint4 *pid4 = reinterpret_cast<const uint4 *>(ts.pid + gt * (int64_t)kTileV +
+      const uint4 *pid4 = reinterpret_cast<const uint4 *>(ts.pid + gt * (int64_t)kPidStride +
                                                           (int64_t)threadIdx.x * kRun);
       q0 = __ldcs(pid4);
       q1 = __ldcs(pid4 + 1);
@@ -1829,16 +1855,17 @@ int sms() {
 
 }  // namespace
 
-TileGeom tile_geom(const int64_t dims[3]) {
+TileGeom tile_geom(const int64_t dims[3], int shape3) {
   TileGeom g;
   g.nx = dims[0];
   g.ny = dims[1];
   g.nz = dims[2];
   g.flat = g.nz == 1 ? 1 : 0;
-  const int64_t tx = g.flat ? k2TX : kTX, ty = g.flat ? k2TY : kTY;
+  const ShapeInfo si = shape_info(shape3);
+  const int64_t tx = g.flat ? k2TX : si.tx, ty = g.flat ? k2TY : si.ty;
   g.tx = (g.nx + tx - 1) / tx;
   g.ty = (g.ny + ty - 1) / ty;
-  g.tz = g.flat ? 1 : (g.nz + kTZ - 1) / kTZ;
+  g.tz = g.flat ? 1 : (g.nz + si.tz - 1) / si.tz;
   g.ntiles = g.tx * g.ty * g.tz;
   g.div_nx = FastDivU32((uint32_t)g.nx);
   g.div_ny = FastDivU32((uint32_t)g.ny);
@@ -1848,17 +1875,17 @@ TileGeom tile_geom(const int64_t dims[3]) {
 }
 
 size_t tiled_scratch_bytes(long long total_tiles, int n_fields, unsigned long long pool_cap,
-                           unsigned long long root_cap) {
+                           unsigned long long root_cap, int face_stride) {
   auto r = [](size_t b) { return (b + 255) & ~(size_t)255; };
   return r(256) + r((size_t)pool_cap * 8) + r((size_t)pool_cap * 4) + r((size_t)pool_cap * 8) +
          r((size_t)root_cap * 2) +
          r((size_t)root_cap * 4) +
          r((size_t)root_cap * 4) + r((size_t)total_tiles * sizeof(TileMeta)) + r((size_t)n_fields * 4) +
-         r((size_t)total_tiles * kFace * 4) + r((size_t)total_tiles * kTileV * 2);
+         r((size_t)total_tiles * face_stride * 4) + r((size_t)total_tiles * kPidStride * 2);
 }
 
 void tiled_scratch_carve(void *base, long long total_tiles, int n_fields,
-                         unsigned long long pool_cap, unsigned long long root_cap,
+                         unsigned long long pool_cap, unsigned long long root_cap, int face_stride,
                          TiledScratch *ts) {
   char *p = static_cast<char *>(base);
   auto take = [&](size_t bytes) {
@@ -1876,8 +1903,8 @@ void tiled_scratch_carve(void *base, long long total_tiles, int n_fields,
   ts->root_label = reinterpret_cast<int32_t *>(take((size_t)root_cap * 4));
   ts->meta = reinterpret_cast<TileMeta *>(take((size_t)total_tiles * sizeof(TileMeta)));
   ts->fstart = reinterpret_cast<uint32_t *>(take((size_t)n_fields * 4));
-  ts->face = reinterpret_cast<uint32_t *>(take((size_t)total_tiles * kFace * 4));
-  ts->pid = reinterpret_cast<uint16_t *>(take((size_t)total_tiles * kTileV * 2));
+  ts->face = reinterpret_cast<uint32_t *>(take((size_t)total_tiles * face_stride * 4));
+  ts->pid = reinterpret_cast<uint16_t *>(take((size_t)total_tiles * kPidStride * 2));
   ts->pool_cap = pool_cap;
   ts->root_cap = root_cap;
 }
@@ -1904,7 +1931,7 @@ EncodeTiledFn encode_tiled_fn() {
 // load; false when the
 // field's layout does not meet TMA's rules (16-byte aligned base and row /
 // plane strides) or the driver entry point is missing.
-bool make_box_map(const void *field, int dtype, const TileGeom &g, CUtensorMap *map) {
+bool make_box_map(const void *field, int dtype, const TileGeom &g, int shape3, CUtensorMap *map) {
   if (dtype != MS_F32) return false;
   if ((reinterpret_cast<uintptr_t>(field) & 15) != 0) return false;
   if ((g.nx * 4) % 16 != 0) return false;
@@ -1923,7 +1950,9 @@ bool make_box_map(const void *field, int dtype, const TileGeom &g, CUtensorMap *
   }
   const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
   const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)(g.nx * g.ny) * 4};
-  const cuuint32_t box[3] = {kEX, kEY, kEZ};
+  const ShapeInfo si = shape_info(shape3);
+  const cuuint32_t box[3] = {(cuuint32_t)(si.tx + 2 * kXO), (cuuint32_t)(si.ty + 2),
+                             (cuuint32_t)(si.tz + 2)};
   const cuuint32_t estr[3] = {1, 1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<void *>(field), dims, strides, box,
             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1931,17 +1960,29 @@ bool make_box_map(const void *field, int dtype, const TileGeom &g, CUtensorMap *
 }
 
 void make_field_desc(const void *field, int dtype, const int64_t dims[3], long long tile_base,
-                     int32_t *asc, int32_t *desc, int32_t *ms, bool allow_tma, FieldDesc *fd,
-                     CUtensorMap *map) {
+                     int32_t *asc, int32_t *desc, int32_t *ms, bool allow_tma, int shape3,
+                     FieldDesc *fd, CUtensorMap *map) {
   fd->field = field;
   fd->asc = asc;
   fd->desc = desc;
   fd->ms = ms;
-  fd->g = tile_geom(dims);
+  fd->g = tile_geom(dims, shape3);
   fd->tile_base = tile_base;
   fd->dtype = dtype;
   memset(map, 0, sizeof(*map));
-  fd->tma = (allow_tma && make_box_map(field, dtype, fd->g, map)) ? 1 : 0;
+  fd->tma = (allow_tma && make_box_map(field, dtype, fd->g, shape3, map)) ? 1 : 0;
+}
+
+// Calls f with a value of the 3D shape type of id (the kernels' template
+// argument).
+template <class F>
+cudaError_t with_shape(int id, F &&f) {
+  switch (id) {
+    case kShape64x8: return f(Shape64x8{});
+    case kShape16x32: return f(Shape16x32{});
+    case kShape16x16: return f(Shape16x16{});
+    default: return f(Shape32x16{});
+  }
 }
 
 namespace {
@@ -1957,16 +1998,21 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
   cudaError_t e = cudaMemsetAsync(ts.counters, 0, 3 * sizeof(unsigned long long) + kQueues * sizeof(unsigned int), s);
   if (e != cudaSuccess) return e;
   if (b.tiles3 > 0) {
-    constexpr int kSmem = 2 * kExt * 4;
-    auto kern = b.n_fields == 1 ? k_tile_local<true> : k_tile_local<false>;
-    if (!capturing(s)) {  // set by the step-by-step call that precedes every capture
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-      if (e != cudaSuccess) return e;
-    }
-    const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * b.tune.tile_ctas);
-    ++tl_launches;
-    kern<<<(unsigned)grid, kThreads, kSmem, s>>>(b, ts, st);
-    e = cudaGetLastError();
+    e = with_shape(b.shape3, [&](auto shape) -> cudaError_t {
+      using S = decltype(shape);
+      constexpr int kSmem = 2 * S::Ext * 4;
+      auto kern = b.n_fields == 1 ? k_tile_local<true, S> : k_tile_local<false, S>;
+      if (!capturing(s)) {  // set by the step-by-step call that precedes every capture
+        const cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (r != cudaSuccess) return r;
+      }
+      // 512-thread shapes fit 2 CTAs an SM, 256-thread ones twice as many
+      const int64_t per_sm = (int64_t)b.tune.tile_ctas * (512 / S::Threads);
+      const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * per_sm);
+      ++tl_launches;
+      kern<<<(unsigned)grid, S::Threads, kSmem, s>>>(b, ts, st);
+      return cudaGetLastError();
+    });
     if (e != cudaSuccess) return e;
     // the 3D tiles' roots come first in the root list
     e = cudaMemcpyAsync(ts.counters + 2, ts.counters + 1, sizeof(unsigned long long),
@@ -1982,7 +2028,7 @@ cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus 
     }
     const int64_t grid = std::min<int64_t>(b.total_tiles - b.tiles3, (int64_t)sms() * b.tune.tile_ctas);
     ++tl_launches;
-    kern<<<(unsigned)grid, kThreads, kSmem2, s>>>(b, ts, st);
+    kern<<<(unsigned)grid, k2Threads, kSmem2, s>>>(b, ts, st);
     e = cudaGetLastError();
   }
   return e;
@@ -1997,7 +2043,7 @@ cudaError_t launch_chase_roots(const Batch &b, const TiledScratch &ts, const int
   for (int flat = 0; flat < 2; ++flat) {
     const long long n = flat ? b.total_tiles - b.tiles3 : b.tiles3;
     if (n == 0) continue;
-    const size_t smem = (size_t)(flat ? k2Ext : kExt) * 4;
+    const size_t smem = (size_t)(flat ? k2Ext : shape_info(b.shape3).ext) * 4;
     // the probe samples every probe_stride-th root (flat) or tile (a tile a
     // warp): either way about kProbeRoots roots, as a tile holds about
     // nroots / tiles of them
@@ -2028,12 +2074,20 @@ cudaError_t launch_chase_roots(const Batch &b, const TiledScratch &ts, const int
       return cudaGetLastError();
     };
     const bool one = b.n_fields == 1;
-    if (tiles)
-      e = flat ? (one ? go(k_chase_tiles<true, true>) : go(k_chase_tiles<true, false>))
-               : (one ? go(k_chase_tiles<false, true>) : go(k_chase_tiles<false, false>));
-    else
-      e = flat ? (one ? go(k_chase_flat<true, true>) : go(k_chase_flat<true, false>))
-               : (one ? go(k_chase_flat<false, true>) : go(k_chase_flat<false, false>));
+    if (flat) {  // the 2D tiles' kernels do not depend on the 3D shape
+      using S = Shape32x16;
+      if (tiles)
+        e = one ? go(k_chase_tiles<true, true, S>) : go(k_chase_tiles<true, false, S>);
+      else
+        e = one ? go(k_chase_flat<true, true, S>) : go(k_chase_flat<true, false, S>);
+    } else {
+      e = with_shape(b.shape3, [&](auto shape) -> cudaError_t {
+        using S = decltype(shape);
+        if (tiles)
+          return one ? go(k_chase_tiles<false, true, S>) : go(k_chase_tiles<false, false, S>);
+        return one ? go(k_chase_flat<false, true, S>) : go(k_chase_flat<false, false, S>);
+      });
+    }
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -2084,8 +2138,10 @@ cudaError_t launch_face_graph_build(const Batch &b, const TiledScratch &ts, int2
                                     DevStatus *st, cudaStream_t s) {
   (void)st;
   ++tl_launches;
-  k_face_graph_build<<<graph_blocks(b), 256, 0, s>>>(b, ts, graph);
-  return cudaGetLastError();
+  return with_shape(b.shape3, [&](auto shape) -> cudaError_t {
+    k_face_graph_build<decltype(shape)><<<graph_blocks(b), 256, 0, s>>>(b, ts, graph);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_face_graph_rounds(const Batch &b, int2 *graph, int r0, int r1, DevStatus *st,
@@ -2112,32 +2168,38 @@ cudaError_t launch_tile_write(const Batch &b, const TiledScratch &ts, const Rank
   cudaError_t e = cudaSuccess;
   const bool in_pool = rs.capacity > kSetInL2;  // as k_resolve_pairs decides on the device
   if (b.tiles3 > 0) {
-    const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * b.tune.write_ctas);
-    ++tl_launches;
-    if (b.n_fields == 1)
-      if (in_pool)
-        k_tile_write<false, true, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+    e = with_shape(b.shape3, [&](auto shape) -> cudaError_t {
+      using S = decltype(shape);
+      const int64_t per_sm = (int64_t)b.tune.write_ctas * (512 / S::Threads);
+      const int64_t grid = std::min<int64_t>(b.tiles3, (int64_t)sms() * per_sm);
+      const unsigned g = (unsigned)grid;
+      ++tl_launches;
+      if (b.n_fields == 1)
+        if (in_pool)
+          k_tile_write<false, true, true, S><<<g, S::Threads, 0, s>>>(b, ts, rs, st);
+        else
+          k_tile_write<false, true, false, S><<<g, S::Threads, 0, s>>>(b, ts, rs, st);
+      else if (in_pool)
+        k_tile_write<false, false, true, S><<<g, S::Threads, 0, s>>>(b, ts, rs, st);
       else
-        k_tile_write<false, true, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
-    else if (in_pool)
-      k_tile_write<false, false, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
-    else
-      k_tile_write<false, false, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
-    e = cudaGetLastError();
+        k_tile_write<false, false, false, S><<<g, S::Threads, 0, s>>>(b, ts, rs, st);
+      return cudaGetLastError();
+    });
     if (e != cudaSuccess) return e;
   }
   if (b.total_tiles > b.tiles3) {
     const int64_t grid = std::min<int64_t>(b.total_tiles - b.tiles3, (int64_t)sms() * b.tune.write_ctas);
     ++tl_launches;
+    using S = Shape32x16;  // unused by the 2D tiles
     if (b.n_fields == 1)
       if (in_pool)
-        k_tile_write<true, true, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+        k_tile_write<true, true, true, S><<<(unsigned)grid, k2Threads, 0, s>>>(b, ts, rs, st);
       else
-        k_tile_write<true, true, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+        k_tile_write<true, true, false, S><<<(unsigned)grid, k2Threads, 0, s>>>(b, ts, rs, st);
     else if (in_pool)
-      k_tile_write<true, false, true><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+      k_tile_write<true, false, true, S><<<(unsigned)grid, k2Threads, 0, s>>>(b, ts, rs, st);
     else
-      k_tile_write<true, false, false><<<(unsigned)grid, kThreads, 0, s>>>(b, ts, rs, st);
+      k_tile_write<true, false, false, S><<<(unsigned)grid, k2Threads, 0, s>>>(b, ts, rs, st);
     e = cudaGetLastError();
   }
   return e;

@@ -12,50 +12,94 @@
 
 namespace msseg {
 
-constexpr int kTX = 32, kTY = 16, kTZ = 16;               // tile, x fastest
-constexpr int kThreads = kTX * kTY;                      // one thread per (x, y) column
-// The tile plus a one-vertex halo is staged in a box of kEX x kEY x kEZ
-// values whose x range starts 4 values left of the tile (x0 - 4, a 16-byte
-// boundary for float32 rows), so the tile's column lx sits at box column
-// lx + kXO and the halo columns at kXO - 1 and kXO + kTX.
+constexpr int kTZ = 16;   // tile depth: every 3D tile shape is TX x TY x kTZ
+constexpr int kRun = 16;  // vertices per thread: a 3D tile's z-column, a 2D tile's y-run
+// The staged box of a tile starts kXO values left of the tile (x0 - 4, a
+// 16-byte boundary for float32 rows), so the tile's column lx sits at box
+// column lx + kXO and the halo columns at kXO - 1 and kXO + TX.
 constexpr int kXO = 4;
-constexpr int kEX = kTX + 2 * kXO, kEY = kTY + 2, kEZ = kTZ + 2;  // 40 x 18 x 18
-constexpr int kExt = kEX * kEY * kEZ;                    // 12960 < 2^16
-constexpr int kTileV = kTX * kTY * kTZ;                  // 8192
-constexpr int kFace = 2 * (kTX * kTY + kTX * kTZ + kTY * kTZ);  // face-root slots per tile
-constexpr int kHashBits = 13;
-constexpr int kHash = 1 << kHashBits;                    // >= kTileV: never overflows
-constexpr int kStageCap = 2048;                          // pair-table entries staged in smem
 constexpr int32_t kExitFlag = (int32_t)0x80000000u;
+constexpr int kStageCap = 2048;  // pair-table entries staged in smem
 
-// 2D fields (nz = 1) use tiles of k2TX x k2TY vertices with the same 512
-// threads: thread (lane, warp) owns the y-run of 16 vertices at
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+
+// A 3D tile shape: TX x TY x kTZ vertices and one thread per (x, y) column
+// (thread t owns x = t % TX, y = t / TX, all kTZ planes).  The tile plus a
+// one-vertex halo is staged in a box of EX x EY x EZ values.
+template <int TX_, int TY_>
+struct Shape3 {
+  static constexpr int TX = TX_, TY = TY_, TZ = kTZ;
+  static constexpr int Threads = TX * TY;
+  static constexpr int EX = TX + 2 * kXO, EY = TY + 2, EZ = TZ + 2;
+  static constexpr int Ext = EX * EY * EZ;
+  static constexpr int TileV = TX * TY * TZ;
+  static constexpr int Face = 2 * (TX * TY + TX * TZ + TY * TZ);  // face-root slots per tile
+  static constexpr int Hash = TileV;  // the tile's pair set: a slot per vertex, never full
+  static constexpr int HashBits = ilog2(Hash);
+  static constexpr int BmW = (Ext + 31) / 32;  // words of a root bitmap over the box
+  static constexpr int CX = TX + 1, CY = TY + 1;  // unit cubes along x and y
+  static_assert(Threads % 32 == 0 && Threads <= 512, "whole warps, at most 512 threads");
+  static_assert((1 << HashBits) == Hash, "tiles of a power-of-two size");
+  static_assert(Threads * kRun == TileV, "one run of kRun per thread");
+  static_assert(TX % 4 == 0, "box rows of whole 16-byte units");
+  static_assert(2 * Ext < 65536 && Ext < 0x8000, "box indices (and root-list indices) fit");
+  static_assert(CX * CY * (TZ + 1) <= Ext, "cube extrema fit the pointer area");
+  static_assert(Hash + Hash / 2 <= Ext, "pair set and dense numbers fit the value area");
+  static_assert(TileV + 4 * BmW <= Ext, "pair list and root bitmaps fit the pointer area");
+  static_assert(BmW <= Threads, "two bitmap words per thread cover both root bitmaps");
+  static_assert(Face < 4096 && TX < 128 && TY < 64, "the root-chase table's field widths");
+};
+// The shapes a call can take (Tuning::shape3); the first is the default.
+using Shape32x16 = Shape3<32, 16>;
+using Shape64x8 = Shape3<64, 8>;
+using Shape16x32 = Shape3<16, 32>;
+using Shape16x16 = Shape3<16, 16>;  // 4096 vertices: small fields
+enum { kShape32x16 = 0, kShape64x8 = 1, kShape16x32 = 2, kShape16x16 = 3, kShapeCount = 4 };
+struct ShapeInfo {
+  int tx, ty, tz, threads, ext, face, tilev;
+};
+template <class S>
+constexpr ShapeInfo info_of() {
+  return ShapeInfo{S::TX, S::TY, S::TZ, S::Threads, S::Ext, S::Face, S::TileV};
+}
+inline ShapeInfo shape_info(int id) {
+  switch (id) {
+    case kShape64x8: return info_of<Shape64x8>();
+    case kShape16x32: return info_of<Shape16x32>();
+    case kShape16x16: return info_of<Shape16x16>();
+    default: return info_of<Shape32x16>();
+  }
+}
+constexpr int kExtMax = Shape16x32::Ext;  // the largest staged box of any shape
+static_assert(kExtMax >= Shape32x16::Ext && kExtMax >= Shape64x8::Ext && kExtMax >= Shape16x16::Ext,
+              "kExtMax bounds every shape");
+constexpr int kPidStride = 8192;  // pair numbers stored per tile (the largest tile)
+
+// 2D fields (nz = 1) use tiles of k2TX x k2TY vertices with 512 threads:
+// thread (lane, warp) owns the y-run of 16 vertices at
 // x = lane + 32 (warp % 4), y = 16 (warp / 4) + 0..15.  The staged box is the
 // tile plus a one-vertex halo, x again from 4 values left of the tile.
 constexpr int k2TX = 128, k2TY = 64;
+constexpr int k2Threads = 512;
 constexpr int k2EX = k2TX + 2 * kXO, k2EY = k2TY + 2;    // 136 x 66
 constexpr int k2Ext = k2EX * k2EY;                       // 8976
+constexpr int k2TileV = k2TX * k2TY;                     // 8192
 constexpr int k2Face = 2 * (k2TX + k2TY);                // face-root slots of a 2D tile
-constexpr int kRun = 16;                                 // vertices per thread, both shapes
-// Words of the root bitmaps over a tile shape's extended box.
-constexpr int kBmW3 = (kExt + 31) / 32;
-constexpr int kBmW2 = (k2Ext + 31) / 32;
+constexpr int k2Hash = k2TileV;
+constexpr int k2HashBits = ilog2(k2Hash);
+constexpr int kBmW2 = (k2Ext + 31) / 32;  // words of a root bitmap over the 2D box
 // Shared-memory areas of a 2D tile: the value area holds the extended box
 // and, once the steepest step is done, the pair list and the root bitmaps;
 // the pointer area holds the pointers and, once they are final, the pair set
 // and its dense numbers.
-constexpr int k2KArea = k2Ext > kTileV + 4 * kBmW2 ? k2Ext : kTileV + 4 * kBmW2;
-constexpr int k2PArea = k2Ext > kHash + kHash / 2 ? k2Ext : kHash + kHash / 2;
+constexpr int k2KArea = k2Ext > k2TileV + 4 * kBmW2 ? k2Ext : k2TileV + 4 * kBmW2;
+constexpr int k2PArea = k2Ext > k2Hash + k2Hash / 2 ? k2Ext : k2Hash + k2Hash / 2;
 
-static_assert(k2TX * k2TY == kTileV, "2D tiles hold as many vertices as 3D tiles");
-static_assert(k2TX * k2TY == kThreads * kRun && kTZ == kRun, "one run of 16 per thread");
-static_assert(k2Face <= kFace, "the face array has kFace slots per tile");
-static_assert(kExt < 65536, "extended-box indices must fit 16 bits");
-static_assert(2 * kExt < 65536, "root-list indices (dn roots, then up roots) fit 16 bits");
-static_assert(kHash >= kTileV, "pair table must hold one pair per vertex");
-static_assert((kTX + 1) * (kTY + 1) * (kTZ + 1) <= kExt, "cube extrema fit the pointer area");
-static_assert(kHash + kHash / 2 <= kExt, "pair set and dense numbers fit the 3D value area");
-static_assert(kTileV + 4 * kBmW3 <= kExt, "pair list and root bitmaps fit the 3D pointer area");
+static_assert(k2TileV == k2Threads * kRun, "one run of 16 per thread");
+static_assert(k2TileV <= kPidStride, "a 2D tile's pair numbers fit its stride");
+static_assert(k2Face <= Shape16x16::Face, "a 2D tile's face slots fit any shape's stride");
+static_assert(2 * k2Ext < 65536, "root-list indices (dn roots, then up roots) fit 16 bits");
+static_assert(kBmW2 <= k2Threads, "two bitmap words per thread cover both root bitmaps");
 static_assert((k2KArea * 4) % 16 == 0, "the 2D pointer area starts 16-byte aligned");
 
 struct TileGeom {
@@ -91,6 +135,7 @@ struct Tuning {
   int dynamic = 1;       // tile and write kernels: a work queue (1) or a static stride (0)
   int resolve_mode = -1;  // root chase and tile pairs: a tile a warp (0), flat over the root
                           // list and pair pool (1), or by tile count (-1, see tile_mode)
+  int shape3 = kShape32x16;  // the 3D tiles' shape (a kShape* id)
 };
 // Calls with at least this many tiles resolve a tile a warp when the mode is
 // left to the tile count: enough tiles keep every warp busy, and a warp then
@@ -110,6 +155,8 @@ struct Batch {
   long long tiles3;  // tiles of the 3D fields, which come first; the rest are 2D
   FieldDesc f0;      // n_fields == 1: the descriptor itself, read from kernel parameters
   Tuning tune;
+  int shape3;        // the 3D tiles' shape (the one their geometry was computed for)
+  int face_stride;   // face slots per tile, 3D and 2D alike (the 3D shape's face count)
 };
 
 // Per-tile record of the tile pass: where the tile's pairs and roots start in
@@ -136,26 +183,27 @@ struct TiledScratch {
   int32_t *root_label;  // per tile root: the extremum its path reaches
   TileMeta *meta;       // per tile
   uint32_t *fstart;     // per field: index of its first pair in the sorted pair list
-  uint32_t *face;       // per tile kFace words: up-root | dn-root << 16 (extended-box indices)
-  uint16_t *pid;        // per tile kTileV pair numbers; the 16 of a thread's run are contiguous
+  uint32_t *face;       // per tile face_stride words: up-root | dn-root << 16 (box indices)
+  uint16_t *pid;        // per tile kPidStride pair numbers; a thread's run of 16 is contiguous
 };
 // The root list: dn and up roots of a tile, the latter flagged.
 constexpr uint16_t kUpRoot = 0x8000u;
-static_assert(kExt < kUpRoot, "box indices leave the top bit free");
+static_assert(kExtMax < kUpRoot, "box indices leave the top bit free");
 // Work-queue counters: tile pass 3D / 2D, write 3D / 2D, root chase 3D / 2D, tile pairs.
 enum { kQTile3 = 0, kQTile2 = 1, kQWrite3 = 2, kQWrite2 = 3, kQChase = 4, kQChase2 = 5, kQPairs = 6,
        kQueues = 8 };
 
-TileGeom tile_geom(const int64_t dims[3]);
+// Tile geometry of a field for the 3D shape shape3 (2D fields: 2D tiles).
+TileGeom tile_geom(const int64_t dims[3], int shape3);
 size_t tiled_scratch_bytes(long long total_tiles, int n_fields, unsigned long long pool_cap,
-                           unsigned long long root_cap);
+                           unsigned long long root_cap, int face_stride);
 void tiled_scratch_carve(void *base, long long total_tiles, int n_fields,
-                         unsigned long long pool_cap, unsigned long long root_cap,
+                         unsigned long long pool_cap, unsigned long long root_cap, int face_stride,
                          TiledScratch *ts);
 // Host side of a field descriptor (and its tensor map when TMA applies).
 void make_field_desc(const void *field, int dtype, const int64_t dims[3], long long tile_base,
-                     int32_t *asc, int32_t *desc, int32_t *ms, bool allow_tma, FieldDesc *fd,
-                     CUtensorMap *map);
+                     int32_t *asc, int32_t *desc, int32_t *ms, bool allow_tma, int shape3,
+                     FieldDesc *fd, CUtensorMap *map);
 // Tile pass: steepest neighbours, in-tile compression, the tile's distinct
 // roots and pairs (counters[0] / [1] hold the pool and root-list totals).
 cudaError_t launch_tile_local(const Batch &b, const TiledScratch &ts, DevStatus *st,
@@ -182,11 +230,11 @@ constexpr unsigned int kSetInL2 = 1u << 22;
 cudaError_t launch_tile_pairs(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
                               bool clear_table, DevStatus *st, cudaStream_t s);
 
-// The face graph: per face slot of every tile (kFace slots per tile, 3D
-// tiles first) the up and dn successor -- the global slot of the next face
-// vertex on the path, or the extremum's vertex index | kSlotFinal.
+// The face graph: per face slot of every tile (face_stride slots per tile,
+// 3D tiles first) the up and dn successor -- the global slot of the next
+// face vertex on the path, or the extremum's vertex index | kSlotFinal.
 constexpr uint32_t kSlotFinal = 0x80000000u;
-inline long long face_graph_slots(const Batch &b) { return b.total_tiles * (long long)kFace; }
+inline long long face_graph_slots(const Batch &b) { return b.total_tiles * (long long)b.face_stride; }
 // Builds the graph from the tiles' face roots, then pointer-jumps it in place
 // until every entry is final (at most `rounds` rounds; rounds r use
 // st->round_open[r]).  queue_rounds queues rounds [r0, r1).

@@ -207,6 +207,7 @@ def test_graphs_off_and_autotune(ctx):
                              [o[1] for o in outs], [o[2] for o in outs])
     assert t["tile_ctas"] in (1, 2) and t["write_ctas"] in (2, 4, 8) and t["dynamic"] in (0, 1)
     assert t["chase_blocks"] in (2, 3) and t["pair_blocks"] in (4, 8) and t["resolve_mode"] in (-1, 0, 1)
+    assert t["shape3"] in ms.TILE_SHAPES
     assert 0 < t["best_ms"] <= t["default_ms"]
     for call in range(3):  # tuned, then captured and replayed with the tuning
         for i, (g, r) in enumerate(zip(_call(ctx, fields, devs, outs), refs)):
