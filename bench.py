@@ -822,7 +822,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="noise512", choices=sorted(WORKLOADS))
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--cpu-slab", type=int, default=48)
     ap.add_argument("--ref-slab", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -466,7 +466,7 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
   if (nroots >= kProbeMinRoots && slots < (1ll << 31)) {
     const long long stride = std::max<long long>(1, (long long)(nroots / kProbeRoots));
     MS_TRY(cudaMemsetAsync(&c->dst->pending, 0, 2 * sizeof(unsigned int), c->stream));
-    MS_TRY(launch_chase_roots(b, ts, nullptr, stride, c->dst, c->stream));
+    MS_TRY(launch_chase_roots(b, ts, nullptr, stride, c->dst, c->stream, nroots));
     s = read_status(c);
     if (s != MS_OK) return s;
     use_graph = (unsigned long long)c->hst->pending * 8 > c->hst->sampled;
@@ -481,7 +481,7 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
     if (s != MS_OK) return s;
     if (c->hst->bad_index) return MS_ERR_CUDA;  // an ill-formed face graph: cannot happen
   }
-  MS_TRY(launch_chase_roots(b, ts, graph, 0, c->dst, c->stream));
+  MS_TRY(launch_chase_roots(b, ts, graph, 0, c->dst, c->stream, nroots));
 
   // ---- tile pairs into the global pair set, sized from the last call's
   // region count (or an eighth of the tile pairs), exact on overflow
@@ -498,7 +498,7 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
     if (want < exact) rs.probe_limit = kEstimateProbeLimit;
     MS_TRY(cudaMemsetAsync(&c->dst->n_unique, 0, sizeof(unsigned int), c->stream));
     MS_TRY(cudaMemsetAsync(&c->dst->hash_overflow, 0, sizeof(unsigned int), c->stream));
-    MS_TRY(launch_tile_pairs(b, ts, rs, true, c->dst, c->stream));
+    MS_TRY(launch_tile_pairs(b, ts, rs, true, c->dst, c->stream, npairs));
     s = read_status(c);
     if (s != MS_OK) return s;
     if (c->hst->not_converged) return MS_ERR_NOT_CONVERGED;

@@ -218,8 +218,11 @@ constexpr int kProbeHops = 4;
 // kProbeRoots of them (every probe_stride-th root of the list).
 constexpr unsigned long long kProbeMinRoots = 65536;
 constexpr unsigned long long kProbeRoots = 16384;
+// roots: an upper bound on the call's tile roots (0: the root list's capacity),
+// which sizes the flat form's grid.
 cudaError_t launch_chase_roots(const Batch &b, const TiledScratch &ts, const int2 *graph,
-                               long long probe_stride, DevStatus *st, cudaStream_t s);
+                               long long probe_stride, DevStatus *st, cudaStream_t s,
+                               unsigned long long roots = 0);
 // Tile pairs: each tile pair's (asc, desc) from its roots' labels, the tile's
 // distinct pairs inserted into the global pair set (clear_table: reset it
 // first), each tile pair's set slot stored.
@@ -227,8 +230,11 @@ cudaError_t launch_chase_roots(const Batch &b, const TiledScratch &ts, const int
 // L2) are read in random order from DRAM; then the tile pairs also keep their
 // (asc, desc) for the write kernel to read in order.
 constexpr unsigned int kSetInL2 = 1u << 22;
+// pairs: an upper bound on the call's tile pairs (0: the pool's capacity),
+// which sizes the flat form's grid.
 cudaError_t launch_tile_pairs(const Batch &b, const TiledScratch &ts, const RankScratch &rs,
-                              bool clear_table, DevStatus *st, cudaStream_t s);
+                              bool clear_table, DevStatus *st, cudaStream_t s,
+                              unsigned long long pairs = 0);
 
 // The face graph: per face slot of every tile (face_stride slots per tile,
 // 3D tiles first) the up and dn successor -- the global slot of the next
