@@ -389,8 +389,11 @@ def batch_line(args, plain_steps=None):
         torch.cuda.synchronize()
         return max(ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t)) / steps
 
-    print("[bench] fields on device; autotuning the batched call", file=sys.stderr, flush=True)
-    tuning = ms.ms_batch_autotune(ctx, fields, dims, dts, asc, desc, mso)
+    if getattr(args, "no_autotune", False):  # default choices (profiling runs)
+        tuning = {**ms.ms_get_tuning(ctx), "default_ms": None, "best_ms": None}
+    else:
+        print("[bench] fields on device; autotuning the batched call", file=sys.stderr, flush=True)
+        tuning = ms.ms_batch_autotune(ctx, fields, dims, dts, asc, desc, mso)
     print(f"[bench] tuning {tuning}; timing the batched call", file=sys.stderr, flush=True)
     ms.ms_profile_enable(ctx, True)
     with ClockSampler(dev) as clk:
@@ -829,6 +832,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the quantised, batched, served and persistence sub-measurements of "
                          "the default run")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batch256: time the default launch choices (no autotuning run first)")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-passes", type=int, default=16)

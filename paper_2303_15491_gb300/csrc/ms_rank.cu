@@ -258,6 +258,7 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const unsigned long long 
     // digit d = threadIdx.x: total over all blocks, and over blocks before this one
     const unsigned int *row = hist + threadIdx.x * gridDim.x;
     unsigned int tot = 0, before = 0;
+#pragma unroll 8
     for (unsigned int j = 0; j < gridDim.x; ++j) {
       const unsigned int v = row[j];
       tot += v;
@@ -407,12 +408,13 @@ cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bit
   unsigned long long *src = rs.list, *dst = rs.tmp;
   const int b = raw_bits > 0 ? -1 : key_bits;  // bit width of one label, or raw keys
   const int total = raw_bits > 0 ? raw_bits : 2 * key_bits;
-  // small sorts: enough blocks to spread the keys, few enough that each
-  // block's offset computation (a pass over its digit's row) stays small;
+  // small sorts: 1024 keys a block (at most 64 blocks up to 2^16 keys, so each
+  // block's offset computation, a pass over its digit's row, stays short;
+  // 4096-key blocks made 13.5K keys a 4-block pass of 26 us);
   // larger ones: 2048 keys a block (up to 8 blocks an SM) and the histogram
   // scanned by two launches (a block with 4096 or more keys walks them 256 at
   // a time, three barriers each: at 350K keys, 85 blocks took 33 us a pass)
-  unsigned int blocks = std::max(1u, std::min((unsigned)kSortBlocks, (m + 4095) / 4096));
+  unsigned int blocks = std::max(1u, std::min((unsigned)kSortBlocks, (m + 1023) / 1024));
   const bool large = m > kSortScanFrom;
   if (large)
     blocks = std::max(1u, std::min({rs.sort_blocks_cap, (m + 2047) / 2048,
