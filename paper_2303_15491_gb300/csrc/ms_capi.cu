@@ -183,6 +183,17 @@ ms_status ensure_scratch(ms_ctx *c, size_t bytes) {
   return MS_OK;
 }
 
+// The pair-rank working memory of a set of this capacity, with the state of
+// the one-launch-a-pass sort after it (its waits report to the status block).
+ms_status rank_scratch_ready(ms_ctx *c, unsigned int cap, RankScratch *rs) {
+  const size_t base = rank_scratch_bytes(cap);
+  ms_status s = ensure_scratch(c, base + rank_sweep_bytes(cap));
+  if (s != MS_OK) return s;
+  rank_scratch_carve(c->scratch, cap, rs);
+  rank_sweep_carve(static_cast<char *>(c->scratch) + base, cap, rs, &c->dst->timeout);
+  return MS_OK;
+}
+
 unsigned int pow2_at_least(uint64_t x) {
   uint64_t p = 1024;
   while (p < x && p < (1ull << 31)) p <<= 1;
@@ -217,10 +228,9 @@ ms_status rank_pairs(ms_ctx *c, const int32_t *asc, const int32_t *desc, int64_t
   if (guess < 1) guess = 1;
   for (;;) {
     const unsigned int cap = pow2_at_least(2 * guess + 2);
-    ms_status s = ensure_scratch(c, rank_scratch_bytes(cap));
-    if (s != MS_OK) return s;
     RankScratch rs;
-    rank_scratch_carve(c->scratch, cap, &rs);
+    ms_status s = rank_scratch_ready(c, cap, &rs);
+    if (s != MS_OK) return s;
     if (guess < bound) rs.probe_limit = kEstimateProbeLimit;
     MS_TRY(cudaMemsetAsync(&c->dst->n_unique, 0, sizeof(unsigned int), c->stream));
     MS_TRY(cudaMemsetAsync(&c->dst->hash_overflow, 0, sizeof(unsigned int), c->stream));
@@ -237,7 +247,9 @@ ms_status rank_pairs(ms_ctx *c, const int32_t *asc, const int32_t *desc, int64_t
     MS_TRY(launch_pairs_sort(rs, m, bit_width(n - 1), c->stream));
     MS_TRY(launch_pairs_assign(rs, m, c->stream));
     MS_TRY(launch_pairs_lookup(asc, desc, n, rs, ms, c->stream));
-    MS_TRY(cudaStreamSynchronize(c->stream));
+    s = read_status(c);
+    if (s != MS_OK) return s;
+    if (c->hst->timeout) return MS_ERR_TIMEOUT;
     c->last_k = m;
     return MS_OK;
   }
@@ -492,9 +504,8 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
   RankScratch rs;
   for (;;) {
     const unsigned int hcap = pow2_at_least(want);
-    s = ensure_scratch(c, rank_scratch_bytes(hcap));
+    s = rank_scratch_ready(c, hcap, &rs);
     if (s != MS_OK) return s;
-    rank_scratch_carve(c->scratch, hcap, &rs);
     if (want < exact) rs.probe_limit = kEstimateProbeLimit;
     MS_TRY(cudaMemsetAsync(&c->dst->n_unique, 0, sizeof(unsigned int), c->stream));
     MS_TRY(cudaMemsetAsync(&c->dst->hash_overflow, 0, sizeof(unsigned int), c->stream));
@@ -532,9 +543,11 @@ ms_status segment_tiled(ms_ctx *c, const FieldArg *fa, int nf, int64_t *k_out,
       if (k_out) k_out[order[j]] = (int64_t)(end - hf[j]);
     }
   } else {
-    MS_TRY(cudaStreamSynchronize(c->stream));
     if (k_out) k_out[0] = m;
   }
+  s = read_status(c);  // synchronises; a sort wait that gave up left the labels unwritten
+  if (s != MS_OK) return s;
+  if (c->hst->timeout) return MS_ERR_TIMEOUT;
   c->last_k = m;
   return MS_OK;
 }
@@ -661,7 +674,8 @@ ms_status capture_plan(ms_ctx *c, BatchPlan &P, const FieldArg *fa, int nf) {
   s = ensure_buffer(c, &c->tscratch, &c->tscratch_bytes,
                     tiled_scratch_bytes(b.total_tiles, nf, pool_cap, root_cap, b.face_stride));
   if (s != MS_OK) return s;
-  s = ensure_scratch(c, rank_scratch_bytes(hcap));
+  RankScratch rs;
+  s = rank_scratch_ready(c, hcap, &rs);
   if (s != MS_OK) return s;
   const long long slots = face_graph_slots(b);
   int2 *graph = nullptr;
@@ -673,8 +687,6 @@ ms_status capture_plan(ms_ctx *c, BatchPlan &P, const FieldArg *fa, int nf) {
   TiledScratch ts;
   tiled_scratch_carve(c->tscratch, b.total_tiles, nf, pool_cap, root_cap, b.face_stride, &ts);
   if (tile_mode(b)) ts.root_tile = nullptr;
-  RankScratch rs;
-  rank_scratch_carve(c->scratch, hcap, &rs);
   if ((uint64_t)hcap < 2 * run.npairs + 2) rs.probe_limit = kEstimateProbeLimit;
   // the sort and rank launches are sized for this many distinct pairs; more
   // of them overflow the list on the device and the call runs step by step
@@ -1319,10 +1331,9 @@ ms_status ms_slab_pairs(ms_ctx *c, const int32_t *asc, const int32_t *desc, int6
   uint64_t guess = std::min<uint64_t>((uint64_t)n, (uint64_t)n / 16 + 1024);
   for (;;) {
     const unsigned int cap = pow2_at_least(2 * guess + 2);
-    ms_status s = ensure_scratch(c, rank_scratch_bytes(cap));
-    if (s != MS_OK) return s;
     RankScratch rs;
-    rank_scratch_carve(c->scratch, cap, &rs);
+    ms_status s = rank_scratch_ready(c, cap, &rs);
+    if (s != MS_OK) return s;
     if (guess < (uint64_t)n) rs.probe_limit = kEstimateProbeLimit;
     s = reset_status(c);
     if (s != MS_OK) return s;
@@ -1340,7 +1351,9 @@ ms_status ms_slab_pairs(ms_ctx *c, const int32_t *asc, const int32_t *desc, int6
     if ((int64_t)mu > capacity) return MS_ERR_TOO_LARGE;
     MS_TRY(launch_pairs_sort(rs, mu, bit_width(n_labels - 1), c->stream));
     MS_TRY(cudaMemcpyAsync(keys, rs.list, (size_t)mu * 8, cudaMemcpyDeviceToDevice, c->stream));
-    MS_TRY(cudaStreamSynchronize(c->stream));
+    s = read_status(c);
+    if (s != MS_OK) return s;
+    if (c->hst->timeout) return MS_ERR_TIMEOUT;
     finish_profile(c, l0);
     return MS_OK;
   }
@@ -1359,10 +1372,9 @@ ms_status ms_slab_rank(ms_ctx *c, const int32_t *asc, const int32_t *desc, int64
   if (n > 0 && n_keys == 0) return MS_ERR_INVALID_ARG;  // the slab's own pairs are missing
   const long long l0 = tl_launches;
   const unsigned int cap = pow2_at_least(2 * (uint64_t)n_keys + 2);
-  ms_status s = ensure_scratch(c, rank_scratch_bytes(cap));
-  if (s != MS_OK) return s;
   RankScratch rs;
-  rank_scratch_carve(c->scratch, cap, &rs);
+  ms_status s = rank_scratch_ready(c, cap, &rs);
+  if (s != MS_OK) return s;
   s = reset_status(c);
   if (s != MS_OK) return s;
   MS_TRY(launch_keys_insert(reinterpret_cast<const unsigned long long *>(keys), n_keys, n_labels, rs,
@@ -1379,6 +1391,7 @@ ms_status ms_slab_rank(ms_ctx *c, const int32_t *asc, const int32_t *desc, int64
   s = read_status(c);
   if (s != MS_OK) return s;
   if (c->hst->bad_index) return MS_ERR_INVALID_ARG;  // a pair missing from the keys
+  if (c->hst->timeout) return MS_ERR_TIMEOUT;
   c->last_k = mu;
   if (k) *k = mu;
   finish_profile(c, l0);
