@@ -206,6 +206,11 @@ __device__ __forceinline__ uint32_t key_of(uint32_t b) {
   return b ^ (m | 0x80000000u);
 }
 
+// float16 bits widened exactly to float32 bits.
+__device__ __forceinline__ uint32_t half_bits_to_float(uint16_t h) {
+  return __float_as_uint(__half2float(__ushort_as_half(h)));
+}
+
 __device__ __forceinline__ uint32_t raw_bits(const void *__restrict__ field, int dtype, int64_t i) {
   if (dtype == MS_F16)
     return __float_as_uint(__half2float(reinterpret_cast<const __half *>(field)[i]));
@@ -654,6 +659,10 @@ __global__ void __launch_bounds__(S::Threads, 1024 / S::Threads) k_tile_local(Ba
                                                                              DevStatus *st) {
   constexpr int kTX = S::TX, kTY = S::TY, kTZ_ = S::TZ, kEX = S::EX, kEY = S::EY, kEZ = S::EZ;
   constexpr int kExt = S::Ext, kThreads = S::Threads, kFace = S::Face;
+  // float16 boxes start kXO16 values left of the tile (16 bytes) and are kE16X wide
+  constexpr int kXO16 = 8, kE16X = S::TX + 2 * kXO16;
+  static_assert(kE16X * S::EY * S::EZ * 2 <= kExt * 4, "a float16 box fits the pointer area");
+  static_assert((kExt * 4) % 128 == 0, "the pointer area starts 128-byte aligned");
   extern __shared__ __align__(128) uint32_t dsmem[];
   uint32_t *K = dsmem;         // kExt words: values / keys, then pair-numbering scratch
   uint32_t *P = dsmem + kExt;  // kExt words: up | dn << 16, box indices
@@ -681,20 +690,27 @@ __global__ void __launch_bounds__(S::Threads, 1024 / S::Threads) k_tile_local(Ba
     const void *__restrict__ field = fd.field;
     const int dtype = fd.dtype;
     const bool tma = fd.tma != 0;
+    const bool f16 = dtype == MS_F16;
     const int64_t tile = gt - fd.tile_base;  // within the field
     int64_t x0, y0, z0;
     tile_origin<S>(g, tile, &x0, &y0, &z0);
-    // tile and halo entirely inside the field: raw float comparisons
-    const bool raw = tma && x0 >= 1 && y0 >= 1 && z0 >= 1 && x0 + kTX < g.nx &&
+    // float32 tile and halo entirely inside the field: raw float comparisons
+    const bool raw = tma && !f16 && x0 >= 1 && y0 >= 1 && z0 >= 1 && x0 + kTX < g.nx &&
                      y0 + kTY < g.ny && z0 + kTZ_ < g.nz;
 
-    // ---- field values of the tile + halo into K
+    // ---- field values of the tile + halo into K (float16: a 16-bit box from
+    // x0 - 8, the nearest 16-byte boundary, into P's area, widened below)
     if (tma) {
       if (threadIdx.x == 0) {
-        // K was last written by ordinary stores; order them before the copy
+        // K and P were last written by ordinary stores; order them before the copy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&s_bar, (uint32_t)(kExt * 4));
-        tma_load_box(K, &bt.tmaps[fi], &s_bar, (int)(x0 - kXO), (int)(y0 - 1), (int)(z0 - 1));
+        if (f16) {
+          mbar_expect_tx(&s_bar, (uint32_t)(kE16X * kEY * kEZ * 2));
+          tma_load_box(P, &bt.tmaps[fi], &s_bar, (int)(x0 - kXO16), (int)(y0 - 1), (int)(z0 - 1));
+        } else {
+          mbar_expect_tx(&s_bar, (uint32_t)(kExt * 4));
+          tma_load_box(K, &bt.tmaps[fi], &s_bar, (int)(x0 - kXO), (int)(y0 - 1), (int)(z0 - 1));
+        }
       }
       if (threadIdx.x == 0) wait_box(&s_bar, parity, st, &s_abort);
       __syncthreads();
@@ -718,7 +734,11 @@ __global__ void __launch_bounds__(S::Threads, 1024 / S::Threads) k_tile_local(Ba
           const int64_t y = y0 + ey - 1, z = z0 + ez - 1;
           const bool row_in = y >= 0 && y < g.ny && z >= 0 && z < g.nz;
           uint32_t b, be = 0;
-          if (tma) {
+          if (tma && f16) {  // the staged 16-bit row: box column c is staged column c + kXO16 - kXO
+            const uint16_t *row16 = reinterpret_cast<const uint16_t *>(P) + kE16X * r + (kXO16 - kXO);
+            b = half_bits_to_float(row16[kXO + lx]);
+            if (lx < 2) be = half_bits_to_float(row16[exe]);
+          } else if (tma) {
             b = K[eb + kXO + lx];
             if (lx < 2) be = K[eb + exe];
           } else {
@@ -885,6 +905,12 @@ __device__ __forceinline__ void steepest_run2(const uint32_t *__restrict__ K, in
 // The 2D form of k_tile_local, for fields with nz = 1 (the tiles after the
 // 3D fields' in a batch).  Thread (lane, warp) owns the run of kRun vertices
 // at x = lane + 32 (warp % 4), y = kRun (warp / 4) + 0 .. kRun - 1.
+// float16 2D boxes: k2E16X values from x0 - k2XO16 (16-byte aligned), staged
+// in P's area from its first 128-byte boundary (word k2StageOff).
+constexpr int k2XO16 = 8, k2E16X = k2TX + 2 * k2XO16;
+constexpr int k2StageOff = ((k2KArea * 4 + 127) / 128 * 128 - k2KArea * 4) / 4;
+static_assert(k2StageOff * 4 + k2E16X * k2EY * 2 <= k2PArea * 4, "a float16 2D box fits P's area");
+
 template <bool kSingle>
 __global__ void __launch_bounds__(k2Threads, 2) k_tile_local2(Batch bt, TiledScratch ts, DevStatus *st) {
   extern __shared__ __align__(128) uint32_t dsmem[];
@@ -914,15 +940,23 @@ __global__ void __launch_bounds__(k2Threads, 2) k_tile_local2(Batch bt, TiledScr
     const void *__restrict__ field = fd.field;
     const int dtype = fd.dtype;
     const bool tma = fd.tma != 0;
+    const bool f16 = dtype == MS_F16;
     int64_t x0, y0;
     tile_origin2(g, gt - fd.tile_base, &x0, &y0);
-    const bool raw = tma && x0 >= 1 && y0 >= 1 && x0 + k2TX < g.nx && y0 + k2TY < g.ny;
+    const bool raw = tma && !f16 && x0 >= 1 && y0 >= 1 && x0 + k2TX < g.nx && y0 + k2TY < g.ny;
+    // float16: a 16-bit box from x0 - 8 staged at a 128-byte boundary in P's area
+    const uint16_t *S16 = reinterpret_cast<const uint16_t *>(P + k2StageOff);
 
     if (tma) {
       if (threadIdx.x == 0) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&s_bar, (uint32_t)(k2Ext * 4));
-        tma_load_box2(K, &bt.tmaps[fi], &s_bar, (int)(x0 - kXO), (int)(y0 - 1));
+        if (f16) {
+          mbar_expect_tx(&s_bar, (uint32_t)(k2E16X * k2EY * 2));
+          tma_load_box2(P + k2StageOff, &bt.tmaps[fi], &s_bar, (int)(x0 - k2XO16), (int)(y0 - 1));
+        } else {
+          mbar_expect_tx(&s_bar, (uint32_t)(k2Ext * 4));
+          tma_load_box2(K, &bt.tmaps[fi], &s_bar, (int)(x0 - kXO), (int)(y0 - 1));
+        }
         wait_box(&s_bar, parity, st, &s_abort);
       }
       __syncthreads();
@@ -938,7 +972,9 @@ __global__ void __launch_bounds__(k2Threads, 2) k_tile_local2(Batch bt, TiledScr
         const int64_t x = x0 + c - kXO, y = y0 + r - 1;
         const bool in = x >= 0 && x < g.nx && y >= 0 && y < g.ny;
         uint32_t b = 0;
-        if (tma)
+        if (tma && f16)
+          b = half_bits_to_float(S16[r * k2E16X + c + (k2XO16 - kXO)]);
+        else if (tma)
           b = K[e];
         else if (in)
           b = raw_bits(field, dtype, y * g.nx + x);
@@ -1949,30 +1985,35 @@ EncodeTiledFn encode_tiled_fn() {
 // field's layout does not meet TMA's rules (16-byte aligned base and row /
 // plane strides) or the driver entry point is missing.
 bool make_box_map(const void *field, int dtype, const TileGeom &g, int shape3, CUtensorMap *map) {
-  if (dtype != MS_F32) return false;
+  // float32 boxes start 4 values left of the tile, float16 boxes 8 (both 16 bytes)
+  if (dtype != MS_F32 && dtype != MS_F16) return false;
+  const cuuint64_t esz = dtype == MS_F16 ? 2 : 4;
+  const int xo = dtype == MS_F16 ? 8 : kXO;
+  const CUtensorMapDataType type =
+      dtype == MS_F16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
   if ((reinterpret_cast<uintptr_t>(field) & 15) != 0) return false;
-  if ((g.nx * 4) % 16 != 0) return false;
+  if ((g.nx * esz) % 16 != 0) return false;
   if (g.nx > (1ll << 31) || g.ny > (1ll << 31) || g.nz > (1ll << 31)) return false;
   EncodeTiledFn fn = encode_tiled_fn();
   if (!fn) return false;
   if (g.flat) {
     const cuuint64_t dims2[2] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny};
-    const cuuint64_t strides2[1] = {(cuuint64_t)g.nx * 4};
-    const cuuint32_t box2[2] = {k2EX, k2EY};
+    const cuuint64_t strides2[1] = {(cuuint64_t)g.nx * esz};
+    const cuuint32_t box2[2] = {(cuuint32_t)(k2TX + 2 * xo), k2EY};
     const cuuint32_t estr2[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<void *>(field), dims2, strides2,
-              box2, estr2, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+    return fn(map, type, 2, const_cast<void *>(field), dims2, strides2, box2, estr2,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   }
   const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz};
-  const cuuint64_t strides[2] = {(cuuint64_t)g.nx * 4, (cuuint64_t)(g.nx * g.ny) * 4};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.nx * esz, (cuuint64_t)(g.nx * g.ny) * esz};
   const ShapeInfo si = shape_info(shape3);
-  const cuuint32_t box[3] = {(cuuint32_t)(si.tx + 2 * kXO), (cuuint32_t)(si.ty + 2),
+  const cuuint32_t box[3] = {(cuuint32_t)(si.tx + 2 * xo), (cuuint32_t)(si.ty + 2),
                              (cuuint32_t)(si.tz + 2)};
   const cuuint32_t estr[3] = {1, 1, 1};
-  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<void *>(field), dims, strides, box,
-            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+  return fn(map, type, 3, const_cast<void *>(field), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
