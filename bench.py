@@ -389,7 +389,9 @@ def batch_line(args, plain_steps=None):
         torch.cuda.synchronize()
         return max(ev0.elapsed_time(ev1), 1e3 * (time.perf_counter() - t)) / steps
 
-    if getattr(args, "no_autotune", False):  # default choices (profiling runs)
+    if getattr(args, "no_autotune", False):  # fixed choices (profiling runs)
+        if getattr(args, "resolve_mode", None) is not None:
+            ms.ms_set_tuning(ctx, resolve_mode=args.resolve_mode)
         tuning = {**ms.ms_get_tuning(ctx), "default_ms": None, "best_ms": None}
     else:
         print("[bench] fields on device; autotuning the batched call", file=sys.stderr, flush=True)
@@ -834,6 +836,8 @@ def main():
                          "the default run")
     ap.add_argument("--no-autotune", action="store_true",
                     help="batch256: time the default launch choices (no autotuning run first)")
+    ap.add_argument("--resolve-mode", type=int, choices=[-1, 0, 1], default=None,
+                    help="batch256 with --no-autotune: resolve by tile (0), flat (1) or by tile count (-1)")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-passes", type=int, default=16)

@@ -183,14 +183,11 @@ ms_status ensure_scratch(ms_ctx *c, size_t bytes) {
   return MS_OK;
 }
 
-// The pair-rank working memory of a set of this capacity, with the state of
-// the one-launch-a-pass sort after it (its waits report to the status block).
+// The pair-rank working memory of a set of this capacity, carved.
 ms_status rank_scratch_ready(ms_ctx *c, unsigned int cap, RankScratch *rs) {
-  const size_t base = rank_scratch_bytes(cap);
-  ms_status s = ensure_scratch(c, base + rank_sweep_bytes(cap));
+  ms_status s = ensure_scratch(c, rank_scratch_bytes(cap));
   if (s != MS_OK) return s;
   rank_scratch_carve(c->scratch, cap, rs);
-  rank_sweep_carve(static_cast<char *>(c->scratch) + base, cap, rs, &c->dst->timeout);
   return MS_OK;
 }
 

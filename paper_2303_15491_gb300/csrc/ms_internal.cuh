@@ -89,13 +89,6 @@ struct RankScratch {
   unsigned int max_unique;         // capacity / 2
   unsigned int probe_limit;        // longest insert probe before the set counts as full
   unsigned int sort_blocks_cap;    // most blocks a sort pass may use
-  // Optional (rank_sweep_carve): state of the one-launch-a-pass sort of large
-  // key counts.  Null: large sorts take the histogram-scan-scatter launches.
-  unsigned long long *sweep_state;  // per key tile, per digit: tagged count or prefix
-  unsigned int *sweep_hist;         // per pass, per digit: key count
-  unsigned int *sweep_ctr;          // per pass: tiles claimed
-  unsigned int *sweep_timeout;      // set when a look-back wait gives up
-  unsigned int sweep_tiles;         // tiles the state holds
 };
 // Sort passes over up to 2^16 keys use at most kSortBlocks blocks, each
 // computing its digit offsets from the raw histogram; larger sorts use
@@ -109,11 +102,7 @@ constexpr unsigned int kEstimateProbeLimit = 256;
 size_t rank_scratch_bytes(unsigned int capacity);
 // Most blocks a sort pass over up to capacity / 2 keys uses.
 unsigned int sort_blocks_cap_of(unsigned int capacity);
-// Working memory of the one-launch-a-pass sort for a set of this capacity,
-// and its carving (after rank_scratch_carve); timeout_flag: a status word set
-// when a wait of the sort gives up.
-size_t rank_sweep_bytes(unsigned int capacity);
-void rank_sweep_carve(void *base, unsigned int capacity, RankScratch *rs, unsigned int *timeout_flag);
+
 void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs);
 // Labels must lie in [0, label_bound) (label_bound <= 0: [0, n)).
 cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t n,

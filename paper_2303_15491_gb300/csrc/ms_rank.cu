@@ -17,14 +17,6 @@ namespace msseg {
 namespace {
 
 constexpr unsigned long long kEmpty = ~0ull;
-}  // namespace
-
-constexpr int kSweepTile = 2048;       // keys a block sorts in one pass
-constexpr int kSweepMaxPasses = 8;     // 8-bit digits of up to 64-bit keys
-constexpr long long kSweepPolls = 1ll << 22;  // look-back polls before a wait gives up
-constexpr int kSweepWindow = 16;       // earlier tiles' words a look-back step loads
-
-namespace {
 
 __device__ __forceinline__ unsigned long long pack_pair(int32_t a, int32_t d) {
   return ((unsigned long long)(uint32_t)a << 32) | (uint32_t)d;
@@ -150,8 +142,7 @@ __global__ void k_radix_hist(const unsigned long long *__restrict__ in, unsigned
 constexpr int kScanThreads = 1024;
 constexpr int kScanChunk = kScanThreads * 8;
 constexpr int kScanMaxChunks = 256;  // rank scratch keeps this many chunk sums
-// Sorts of more keys than this use 2048-key blocks and the scan launches
-// (or, with sweep state, the one-launch-a-pass sort).
+// Sorts of more keys than this use 2048-key blocks and the scan launches.
 constexpr unsigned int kSortScanFrom = 1u << 16;
 
 __device__ __forceinline__ void load8(const unsigned int *p, unsigned int i0, unsigned int n,
@@ -345,153 +336,6 @@ __global__ void k_pairs_lookup(const int32_t *__restrict__ asc, const int32_t *_
   }
 }
 
-// ---- the one-launch-a-pass sort of large key counts ---------------------
-// All passes' digit counts come from one read of the keys (k_sweep_hist).
-// Each pass is then one launch (k_sweep_pass): a block claims the next tile
-// of kSweepTile keys from a counter, counts its digits, publishes the counts,
-// and finds how many keys of each digit the earlier tiles hold by walking
-// back over their published words until one holds a prefix (each tile
-// publishes its prefix as soon as it knows it).  Tiles are claimed in order,
-// so an earlier tile's block is already running: no wait depends on a block
-// that has not started.  Words carry their pass, so one clear per sort
-// suffices; every wait is bounded.
-//   word: bits 60-63 pass + 1, bits 58-59 kind (1 count, 2 prefix), bits 0-31 value
-__device__ __forceinline__ unsigned long long sweep_word(int pass, unsigned long long kind,
-                                                         unsigned int v) {
-  return ((unsigned long long)(pass + 1) << 60) | (kind << 58) | v;
-}
-
-__global__ void __launch_bounds__(256) k_sweep_hist(const unsigned long long *__restrict__ in,
-                                                    unsigned int m, const unsigned int *m_dev, int b,
-                                                    int passes, unsigned int *__restrict__ hist) {
-  m = count_of(m, m_dev);
-  __shared__ unsigned int h[kSweepMaxPasses][256];
-  for (int p = 0; p < kSweepMaxPasses; ++p) h[p][threadIdx.x] = 0;
-  __syncthreads();
-  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-    const unsigned long long key = in[i];
-    for (int p = 0; p < passes; ++p) atomicAdd(&h[p][sort_digit(key, b, 8 * p)], 1u);
-  }
-  __syncthreads();
-  for (int p = 0; p < passes; ++p) {
-    const unsigned int v = h[p][threadIdx.x];
-    if (v) atomicAdd(&hist[p * 256 + threadIdx.x], v);
-  }
-}
-
-__global__ void __launch_bounds__(256) k_sweep_pass(const unsigned long long *__restrict__ in,
-                                                    unsigned long long *__restrict__ out,
-                                                    unsigned int m, const unsigned int *m_dev, int b,
-                                                    int pass, RankScratch rs) {
-  m = count_of(m, m_dev);
-  __shared__ unsigned long long keys[kSweepTile];
-  __shared__ unsigned int cnt[256], run[256], wsum[8];
-  __shared__ unsigned int wcnt[8][256];
-  __shared__ unsigned int s_tile;
-  const unsigned int d = threadIdx.x, warp = threadIdx.x >> 5, lane = lane_id();
-  const int shift = 8 * pass;
-  if (threadIdx.x == 0) s_tile = atomicAdd(&rs.sweep_ctr[pass], 1u);
-  cnt[d] = 0;
-  __syncthreads();
-  const unsigned int t = s_tile;
-  const unsigned int ntiles = (m + kSweepTile - 1) / kSweepTile;
-  if (t >= ntiles || t >= rs.sweep_tiles) return;  // block-uniform
-  const unsigned int lo = t * kSweepTile, n = min(m - lo, (unsigned int)kSweepTile);
-  for (unsigned int i = threadIdx.x; i < n; i += 256) {
-    const unsigned long long key = in[lo + i];
-    keys[i] = key;
-    atomicAdd(&cnt[sort_digit(key, b, shift)], 1u);
-  }
-  __syncthreads();
-  // publish this tile's count of digit d, then find the keys of digit d in
-  // the tiles before it
-  const unsigned int c = cnt[d];
-  volatile unsigned long long *state = rs.sweep_state;
-  state[(size_t)t * 256 + d] = sweep_word(pass, t == 0 ? 2ull : 1ull, c);
-  unsigned int before = 0;
-  if (t > 0) {
-    // walk back kSweepWindow tiles at a time (their words loaded together):
-    // published counts are added and passed, a prefix ends the walk, and an
-    // unpublished word is waited for
-    long long j = (long long)t - 1;
-    long long polls = 0;
-    const unsigned long long tag = (unsigned long long)(pass + 1);
-    while (j >= 0) {
-      const int wn = (int)min(j + 1, (long long)kSweepWindow);
-      unsigned long long w[kSweepWindow];
-#pragma unroll
-      for (int k = 0; k < kSweepWindow; ++k) w[k] = k < wn ? state[(size_t)(j - k) * 256 + d] : 0ull;
-      unsigned int add = 0;
-      int k = 0;
-      bool prefix = false;
-#pragma unroll
-      for (int q = 0; q < kSweepWindow; ++q) {
-        if (q != k || k >= wn) continue;  // stopped earlier
-        if ((w[q] >> 60) != tag) continue;  // not published in this pass yet: stop here
-        add += (unsigned int)w[q];
-        if (((w[q] >> 58) & 3ull) == 2ull) {
-          prefix = true;
-        } else {
-          k = q + 1;
-        }
-      }
-      before += add;
-      if (prefix) break;
-      j -= k;  // the counts taken
-      if (k < wn) {  // word j is not published yet
-        if (++polls > kSweepPolls) {
-          if (rs.sweep_timeout) atomicOr(rs.sweep_timeout, 1u);
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    state[(size_t)t * 256 + d] = sweep_word(pass, 2ull, before + c);
-  }
-  // where the keys of digit d start: all keys of lower digits, then the
-  // earlier tiles' keys of digit d
-  const unsigned int g = rs.sweep_hist[pass * 256 + d];
-  unsigned int incl = g;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned int x = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= (unsigned)o) incl += x;
-  }
-  if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
-  unsigned int wbase = 0;
-  for (unsigned int w = 0; w < warp; ++w) wbase += wsum[w];
-  run[d] = wbase + incl - g + before;
-  __syncthreads();
-  // stable scatter, 256 keys at a time (as k_radix_scatter)
-  for (unsigned int t0 = 0; t0 < n; t0 += 256) {
-    for (int w = 0; w < 8; ++w) wcnt[w][threadIdx.x] = 0;
-    __syncthreads();
-    const unsigned int i = t0 + threadIdx.x;
-    const bool valid = i < n;
-    unsigned long long key = 0;
-    unsigned int dg = 0x100u + lane;  // invalid lanes get distinct private digits
-    if (valid) {
-      key = keys[i];
-      dg = sort_digit(key, b, shift);
-    }
-    const unsigned int peers = __match_any_sync(0xffffffffu, dg);
-    const unsigned int below = __popc(peers & ((1u << lane) - 1u));
-    if (valid && below == 0) wcnt[warp][dg] = __popc(peers);
-    __syncthreads();
-    if (valid) {
-      unsigned int pre = 0;
-      for (unsigned int w = 0; w < warp; ++w) pre += wcnt[w][dg];
-      out[run[dg] + pre + below] = key;
-    }
-    __syncthreads();
-    unsigned int tot = 0;
-    for (int w = 0; w < 8; ++w) tot += wcnt[w][threadIdx.x];
-    run[threadIdx.x] += tot;
-    __syncthreads();
-  }
-}
-
 int sm_count() {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
@@ -535,29 +379,6 @@ void rank_scratch_carve(void *base, unsigned int capacity, RankScratch *rs) {
   p += 256 * (size_t)sort_blocks_cap_of(capacity) * 4;
   rs->scan_sums = reinterpret_cast<unsigned int *>(p);  // the last 4 * 256 bytes
   rs->sort_blocks_cap = sort_blocks_cap_of(capacity);
-  rs->sweep_state = nullptr;
-  rs->sweep_hist = nullptr;
-  rs->sweep_ctr = nullptr;
-  rs->sweep_timeout = nullptr;
-  rs->sweep_tiles = 0;
-}
-
-size_t rank_sweep_bytes(unsigned int capacity) {
-  const size_t tiles = ((size_t)capacity / 2 + kSweepTile - 1) / kSweepTile;
-  return 256 + tiles * 256 * 8 + (size_t)kSweepMaxPasses * 256 * 4 + 256;
-}
-
-void rank_sweep_carve(void *base, unsigned int capacity, RankScratch *rs, unsigned int *timeout_flag) {
-  char *p = static_cast<char *>(base);
-  p += (256 - (reinterpret_cast<uintptr_t>(p) & 255)) & 255;  // 256-byte aligned start
-  const size_t tiles = ((size_t)capacity / 2 + kSweepTile - 1) / kSweepTile;
-  rs->sweep_state = reinterpret_cast<unsigned long long *>(p);
-  p += tiles * 256 * 8;
-  rs->sweep_hist = reinterpret_cast<unsigned int *>(p);
-  p += (size_t)kSweepMaxPasses * 256 * 4;
-  rs->sweep_ctr = reinterpret_cast<unsigned int *>(p);
-  rs->sweep_tiles = (unsigned int)tiles;
-  rs->sweep_timeout = timeout_flag;
 }
 
 cudaError_t launch_pairs_insert(const int32_t *asc, const int32_t *desc, int64_t n,
@@ -595,28 +416,6 @@ cudaError_t launch_pairs_sort(const RankScratch &rs, unsigned int m, int key_bit
   // a time, three barriers each: at 350K keys, 85 blocks took 33 us a pass)
   unsigned int blocks = std::max(1u, std::min((unsigned)kSortBlocks, (m + 1023) / 1024));
   const bool large = m > kSortScanFrom;
-  const int passes = (total + 7) / 8;
-  const unsigned int tiles = (m + kSweepTile - 1) / kSweepTile;
-  if (large && rs.sweep_state && passes <= kSweepMaxPasses && tiles <= rs.sweep_tiles) {
-    // one launch for all passes' digit counts, then one launch a pass
-    cudaError_t e = cudaMemsetAsync(rs.sweep_state, 0, (size_t)tiles * 256 * 8, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(rs.sweep_hist, 0, (size_t)passes * 256 * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(rs.sweep_ctr, 0, kSweepMaxPasses * 4, s);
-    if (e != cudaSuccess) return e;
-    const unsigned int hblocks = std::max(1u, std::min((unsigned)sm_count() * 4, (m + 4095) / 4096));
-    ++tl_launches;
-    k_sweep_hist<<<hblocks, 256, 0, s>>>(src, m, m_dev, b, passes, rs.sweep_hist);
-    for (int pass = 0; pass < passes; ++pass) {
-      ++tl_launches;
-      k_sweep_pass<<<tiles, 256, 0, s>>>(src, dst, m, m_dev, b, pass, rs);
-      unsigned long long *t = src;
-      src = dst;
-      dst = t;
-    }
-    if (src != rs.list)
-      return cudaMemcpyAsync(rs.list, src, (size_t)m * 8, cudaMemcpyDeviceToDevice, s);
-    return cudaGetLastError();
-  }
   if (large)
     blocks = std::max(1u, std::min({rs.sort_blocks_cap, (m + 2047) / 2048,
                                     (unsigned)sm_count() * 8}));

@@ -194,7 +194,9 @@ def test_segment_shapes_and_kinds(ctx, dims, kind):
     run_and_compare(ctx, f, f"{kind} {dims}")
 
 
-@pytest.mark.parametrize("dims", [(48, 40, 36), (513, 300, 1)])
+# rows of whole 16-byte units (nx a multiple of 8) take TMA boxes, the others plain loads
+@pytest.mark.parametrize("dims", [(48, 40, 36), (513, 300, 1), (520, 300, 1), (52, 33, 20),
+                                  (136, 70, 40)])
 def test_segment_fp16(ctx, dims):
     f = sf.smoothed_noise(dims, 9, sigma=2.0, radius=8).astype(np.float16)
     run_and_compare(ctx, f, f"fp16 {dims}")
