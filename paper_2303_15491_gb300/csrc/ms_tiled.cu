@@ -1634,9 +1634,6 @@ __global__ void __launch_bounds__(kPairThreads) k_pairs_flat(Batch bt, TiledScra
 constexpr int kWarpHash = 256;
 constexpr int kWarpProbes = 8;
 constexpr int kWarpFill = kWarpHash * 3 / 4;  // entries past which the set takes no new keys
-constexpr int kWarpSlotCache = 2048;             // pairs of a tile whose set slots pass 1 keeps
-constexpr uint16_t kNoWarpSlot = 0xffffu;        // a pair inserted straight into the global set
-constexpr int kPairTileThreads = 128;            // a warp a tile: 4 warps a block (28 KB of sets)
 
 __device__ __forceinline__ uint32_t warp_slot_of(unsigned long long key) {
   uint32_t h = ((uint32_t)key * 0x9E3779B1u) ^ ((uint32_t)(key >> 32) * 0x85EBCA77u);
@@ -1645,17 +1642,15 @@ __device__ __forceinline__ uint32_t warp_slot_of(unsigned long long key) {
 }
 
 template <bool kSingle>
-__global__ void __launch_bounds__(kPairTileThreads, 8) k_pairs_tiles(Batch bt, TiledScratch ts, RankScratch rs,
+__global__ void __launch_bounds__(kPairThreads) k_pairs_tiles(Batch bt, TiledScratch ts, RankScratch rs,
                                                              DevStatus *st) {
   if (call_failed(st) || st->not_converged) return;
-  __shared__ unsigned long long HKs[kPairTileThreads / 32][kWarpHash];
-  __shared__ uint32_t HSs[kPairTileThreads / 32][kWarpHash];
-  __shared__ uint16_t WSs[kPairTileThreads / 32][kWarpSlotCache];  // pass 1's set slot of each pair
-  __shared__ int s_fill[kPairTileThreads / 32];
+  __shared__ unsigned long long HKs[kPairThreads / 32][kWarpHash];
+  __shared__ uint32_t HSs[kPairThreads / 32][kWarpHash];
+  __shared__ int s_fill[kPairThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned long long *HK = HKs[wid];
   uint32_t *HS = HSs[wid];
-  uint16_t *WS = WSs[wid];
   const bool keep_ad = rs.capacity > kSetInL2;
   for (;;) {
     long long k = 0;
@@ -1670,9 +1665,6 @@ __global__ void __launch_bounds__(kPairTileThreads, 8) k_pairs_tiles(Batch bt, T
     const uint32_t nr = (uint32_t)(m.nd + m.nu);
     const int np = m.npairs;
     const uint2 *__restrict__ pp_src = ts.pool_pair + m.pbase;
-    // pass 2 reads each pair's set slot back from WS when the tile's pairs fit
-    // it (and no pair needs its resolved (asc, desc) kept)
-    const bool cached = np <= kWarpSlotCache && !keep_ad;
     for (int i = lane; i < kWarpHash; i += 32) HK[i] = ~0ull;
     if (lane == 0) s_fill[wid] = 0;
     __syncwarp();
@@ -1719,7 +1711,6 @@ __global__ void __launch_bounds__(kPairTileThreads, 8) k_pairs_tiles(Batch bt, T
           }
           sl = (sl + 1) & (kWarpHash - 1);
         }
-        if (cached) WS[i] = placed ? (uint16_t)sl : kNoWarpSlot;
         if (!placed) {  // the warp's set is full: straight into the global set
           bool fresh = false;
           const uint32_t gs = global_insert(rs, key, &fresh);
@@ -1742,14 +1733,6 @@ __global__ void __launch_bounds__(kPairTileThreads, 8) k_pairs_tiles(Batch bt, T
     }
     __syncwarp();
     // pass 2: every pair's set slot
-    if (cached) {
-      for (int i = lane; i < np; i += 32) {
-        const uint32_t sl = WS[i];
-        if (sl != kNoWarpSlot) ts.pool_slot[m.pbase + i] = HS[sl];
-      }
-      __syncwarp();  // the warp's set is reused by its next tile
-      continue;
-    }
     for (int i0 = lane; i0 < np; i0 += 32 * kPairBatch) {
       uint2 pp[kPairBatch];
       int32_t a[kPairBatch], d[kPairBatch];
@@ -2168,13 +2151,13 @@ cudaError_t launch_tile_pairs(const Batch &b, const TiledScratch &ts, const Rank
   if (e != cudaSuccess || b.total_tiles == 0) return e;
   ++tl_launches;
   if (tile_mode(b)) {
-    constexpr int kWarps = kPairTileThreads / 32;
+    constexpr int kWarps = kPairThreads / 32;
     const long long blocks = std::min<long long>((b.total_tiles + kWarps - 1) / kWarps,
                                                  (long long)sms() * b.tune.pair_blocks);
     if (b.n_fields == 1)
-      k_pairs_tiles<true><<<(unsigned)blocks, kPairTileThreads, 0, s>>>(b, ts, rs, st);
+      k_pairs_tiles<true><<<(unsigned)blocks, kPairThreads, 0, s>>>(b, ts, rs, st);
     else
-      k_pairs_tiles<false><<<(unsigned)blocks, kPairTileThreads, 0, s>>>(b, ts, rs, st);
+      k_pairs_tiles<false><<<(unsigned)blocks, kPairThreads, 0, s>>>(b, ts, rs, st);
   } else {
     // every thread strides over the pool: the blocks resident at once
     auto kern = b.n_fields == 1 ? k_pairs_flat<true> : k_pairs_flat<false>;
