@@ -173,7 +173,9 @@ __device__ void pair_insert(const ScanArgs &A, unsigned long long key, unsigned 
       }
     }
     if (cur == key) {
-      atomicMin(&A.S.vals[slot], when);
+      // most edges of a basin pair enter after the earliest one: read first,
+      // so that only an earlier entry pays for the atomic
+      if (when < *(volatile unsigned long long *)&A.S.vals[slot]) atomicMin(&A.S.vals[slot], when);
       return;
     }
     slot = (slot + 1u) & mask;
@@ -181,13 +183,41 @@ __device__ void pair_insert(const ScanArgs &A, unsigned long long key, unsigned 
   atomicOr(&cnt->pairs_overflow, 1u);
 }
 
+// A block's own table of basin pairs.  A block scans kChunk consecutive
+// vertices at a time (a sheet of rows of one or two planes), which meet a
+// few hundred basin pairs but cross basin boundaries tens of thousands of
+// times: the crossings meet in shared memory, and only each pair's earliest
+// entry goes to the global table when the chunk ends.
+constexpr uint32_t kChunk = 8192;
+constexpr uint32_t kBlockSlots = 1024;  // about four times the pairs of a chunk of a 3D field
+
+struct BlockTable {
+  unsigned long long keys[kBlockSlots], vals[kBlockSlots];
+};
+
+__device__ __forceinline__ void block_insert(BlockTable &T, const ScanArgs &A, unsigned long long key,
+                                             unsigned long long when) {
+  uint32_t slot = (uint32_t)hash_mix64(key) & (kBlockSlots - 1u);
+  for (uint32_t probe = 0; probe < kBlockSlots; ++probe) {
+    unsigned long long cur = *(volatile unsigned long long *)&T.keys[slot];
+    if (cur == kEmptyKey) cur = atomicCAS(&T.keys[slot], kEmptyKey, key);
+    if (cur == kEmptyKey || cur == key) {
+      if (when < *(volatile unsigned long long *)&T.vals[slot]) atomicMin(&T.vals[slot], when);
+      return;
+    }
+    slot = (slot + 1u) & (kBlockSlots - 1u);
+  }
+  pair_insert(A, key, when);  // the block's table is full: straight to the global one
+}
+
 // Step 1 over every vertex v: checks its label (in range and an extremum's
 // own label), lists v if it is an extremum, and for each of its forward
 // stencil neighbours w in another basin records the basin pair with the
 // entry key of the later of v, w.  Lanes of a warp holding the same pair
-// reduce their keys first and insert once.
+// reduce their keys first and insert once into the block's table.
 template <bool kFlat>
 __global__ void __launch_bounds__(256) k_basin_edges(ScanArgs A) {
+  __shared__ BlockTable T;
   // forward half of the Freudenthal stencil (the other half is its negation)
   constexpr int kNb = kFlat ? 3 : 7;
   constexpr int8_t kOx[7] = {1, 0, 1, 0, 1, 0, 1};
@@ -195,70 +225,101 @@ __global__ void __launch_bounds__(256) k_basin_edges(ScanArgs A) {
   constexpr int8_t kOz[7] = {0, 0, 0, 1, 1, 1, 1};
   const uint32_t lane = threadIdx.x & 31u;
   bool bad = false, nan = false;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  // the loop bound is the same for a whole warp (ballots and matches below)
-  for (uint32_t base = blockIdx.x * blockDim.x; base < A.n; base += stride) {
-    const uint32_t v = base + threadIdx.x;
-    const bool in = v < A.n;
-    int32_t lv = -1;
-    unsigned long long kv = 0;
-    uint32_t x = 0, y = 0, z = 0;
-    if (in) {
-      lv = A.labels[v];
-      if (lv < 0 || (uint32_t)lv >= A.n) {
-        bad = true;
-        lv = -1;
-      } else if (A.labels[lv] != lv) {
-        bad = true;
-      }
-      const uint32_t bits = load_bits(A.field, A.dtype, v);
-      nan |= is_nan_bits(bits);
-      kv = entry_key(bits, v, A.maxima);
-      uint32_t q;
-      A.div_x.divmod(v, &q, &x);
-      if (kFlat)
-        y = q;
-      else
-        A.div_y.divmod(q, &z, &y);
-    }
-    const bool own = in && lv == (int32_t)v;
-    const uint32_t mine = __ballot_sync(kFull, own);
-    if (mine) {
-      const int leader = __ffs(mine) - 1;
-      uint32_t at = 0;
-      if ((int)lane == leader) at = atomicAdd(&A.S.cnt->n_minima, (unsigned)__popc(mine));
-      at = __shfl_sync(kFull, at, leader) + __popc(mine & ((1u << lane) - 1u));
-      if (own) {
-        if (at < A.S.max_minima)
-          A.S.minima[at] = v;
+  for (uint32_t i = threadIdx.x; i < kBlockSlots; i += blockDim.x) {
+    T.keys[i] = kEmptyKey;
+    T.vals[i] = kEmptyKey;
+  }
+  __syncthreads();
+  const uint32_t chunks = (uint32_t)(((uint64_t)A.n + kChunk - 1) / kChunk);
+  for (uint32_t c = blockIdx.x; c < chunks; c += gridDim.x) {
+    const uint32_t end = (uint32_t)min((uint64_t)A.n, (uint64_t)(c + 1) * kChunk);
+    // the loop bound is the same for the whole block (ballots, matches, barriers)
+    for (uint32_t base = c * kChunk; base < end; base += blockDim.x) {
+      const uint32_t v = base + threadIdx.x;
+      int32_t lv = -1;
+      unsigned long long kv = 0;
+      uint32_t x = 0, y = 0, z = 0;
+      if (v < end) {
+        lv = __ldg(&A.labels[v]);
+        if (lv < 0 || (uint32_t)lv >= A.n) {
+          bad = true;
+          lv = -1;
+        } else if (__ldg(&A.labels[lv]) != lv) {
+          bad = true;
+        }
+        const uint32_t bits = load_bits(A.field, A.dtype, v);
+        nan |= is_nan_bits(bits);
+        kv = entry_key(bits, v, A.maxima);
+        uint32_t q;
+        A.div_x.divmod(v, &q, &x);
+        if (kFlat)
+          y = q;
         else
-          atomicOr(&A.S.cnt->minima_overflow, 1u);
+          A.div_y.divmod(q, &z, &y);
       }
-    }
-#pragma unroll
-    for (int j = 0; j < kNb; ++j) {
-      unsigned long long key = kEmptyKey, when = kEmptyKey;
-      if (lv >= 0 && x + kOx[j] < A.nx && y + kOy[j] < A.ny && (kFlat || z + kOz[j] < A.nz)) {
-        const uint32_t w = v + kOx[j] + kOy[j] * A.nx + (kFlat ? 0u : kOz[j] * A.nxy);
-        const int32_t lw = A.labels[w];
-        if (lw != lv) {
-          const unsigned long long kw = entry_key(load_bits(A.field, A.dtype, w), w, A.maxima);
-          when = kv > kw ? kv : kw;
-          const uint32_t lo = min((uint32_t)lv, (uint32_t)lw), hi = max((uint32_t)lv, (uint32_t)lw);
-          key = ((unsigned long long)lo << 32) | hi;  // lo != hi, so never the empty key
+      const bool own = lv == (int32_t)v;
+      const uint32_t mine = __ballot_sync(kFull, own);
+      if (mine) {
+        const int leader = __ffs(mine) - 1;
+        uint32_t at = 0;
+        if ((int)lane == leader) at = atomicAdd(&A.S.cnt->n_minima, (unsigned)__popc(mine));
+        at = __shfl_sync(kFull, at, leader) + __popc(mine & ((1u << lane) - 1u));
+        if (own) {
+          if (at < A.S.max_minima)
+            A.S.minima[at] = v;
+          else
+            atomicOr(&A.S.cnt->minima_overflow, 1u);
         }
       }
-      const uint32_t peers = __match_any_sync(kFull, key);
-      if (key != kEmptyKey) {
-        // 64-bit minimum over the lanes of the group: high words, then the
-        // low words of the lanes that hold the high minimum
-        const uint32_t hi = (uint32_t)(when >> 32);
-        const uint32_t hmin = __reduce_min_sync(peers, hi);
-        const uint32_t lmin = __reduce_min_sync(peers, hi == hmin ? (uint32_t)when : kFull);
-        if ((int)lane == __ffs(peers) - 1)
-          pair_insert(A, key, ((unsigned long long)hmin << 32) | lmin);
+      // every neighbour's label first, then the values of those across a
+      // boundary: the loads of a vertex are in flight together
+      int32_t lw[kNb];
+      uint32_t bw[kNb];
+#pragma unroll
+      for (int j = 0; j < kNb; ++j) {
+        lw[j] = lv;
+        if (lv >= 0 && x + kOx[j] < A.nx && y + kOy[j] < A.ny && (kFlat || z + kOz[j] < A.nz))
+          lw[j] = __ldg(&A.labels[v + kOx[j] + kOy[j] * A.nx + (kFlat ? 0u : kOz[j] * A.nxy)]);
+      }
+#pragma unroll
+      for (int j = 0; j < kNb; ++j) {
+        bw[j] = 0;
+        if (lw[j] != lv)
+          bw[j] = load_bits(A.field, A.dtype, v + kOx[j] + kOy[j] * A.nx + (kFlat ? 0u : kOz[j] * A.nxy));
+      }
+#pragma unroll
+      for (int j = 0; j < kNb; ++j) {
+        unsigned long long key = kEmptyKey, when = kEmptyKey;
+        if (lw[j] != lv) {
+          const uint32_t w = v + kOx[j] + kOy[j] * A.nx + (kFlat ? 0u : kOz[j] * A.nxy);
+          const unsigned long long kw = entry_key(bw[j], w, A.maxima);
+          when = kv > kw ? kv : kw;
+          const uint32_t lo = min((uint32_t)lv, (uint32_t)lw[j]), hi = max((uint32_t)lv, (uint32_t)lw[j]);
+          key = ((unsigned long long)lo << 32) | hi;  // lo != hi, so never the empty key
+        }
+        if (!__any_sync(kFull, key != kEmptyKey)) continue;  // no lane of the warp on a basin boundary
+        const uint32_t peers = __match_any_sync(kFull, key);
+        if (key != kEmptyKey) {
+          // 64-bit minimum over the lanes of the group: high words, then the
+          // low words of the lanes that hold the high minimum
+          const uint32_t hi = (uint32_t)(when >> 32);
+          const uint32_t hmin = __reduce_min_sync(peers, hi);
+          const uint32_t lmin = __reduce_min_sync(peers, hi == hmin ? (uint32_t)when : kFull);
+          if ((int)lane == __ffs(peers) - 1) block_insert(T, A, key, ((unsigned long long)hmin << 32) | lmin);
+        }
       }
     }
+    // the chunk's pairs to the global table; the block's table empties
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < kBlockSlots; i += blockDim.x) {
+      const unsigned long long key = T.keys[i];
+      if (key != kEmptyKey) {
+        pair_insert(A, key, T.vals[i]);
+        T.keys[i] = kEmptyKey;
+        T.vals[i] = kEmptyKey;
+      }
+    }
+    __syncthreads();
   }
   if (__any_sync(kFull, bad) && lane == 0) atomicOr(&A.S.cnt->bad_label, 1u);
   if (__any_sync(kFull, nan) && lane == 0) atomicOr(&A.S.cnt->nan_flag, 1u);
@@ -460,6 +521,18 @@ unsigned int grid_for(uint64_t n, int per_sm = 8) {
   return (unsigned int)(b ? b : 1);
 }
 
+// One resident wave of the basin-edge scan (a block takes chunks in turn).
+template <bool kFlat>
+unsigned int edges_grid(uint64_t n) {
+  static int per_sm = 0;
+  if (!per_sm && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_basin_edges<kFlat>, 256, 0) !=
+                      cudaSuccess ||
+                  per_sm < 1))
+    per_sm = 1;
+  const uint64_t chunks = (n + kChunk - 1) / kChunk;
+  return (unsigned int)std::max<uint64_t>(1, std::min<uint64_t>(chunks, (uint64_t)sms() * per_sm));
+}
+
 int bits_of(uint64_t x) {
   int b = 0;
   while (x) {
@@ -512,9 +585,9 @@ cudaError_t persist_run(const PersistCall &P, void *scratch, void *host_counters
   A.S = S;
   ++tl_launches;
   if (A.nz == 1)
-    k_basin_edges<true><<<grid_for(n), 256, 0, s>>>(A);
+    k_basin_edges<true><<<edges_grid<true>(n), 256, 0, s>>>(A);
   else
-    k_basin_edges<false><<<grid_for(n), 256, 0, s>>>(A);
+    k_basin_edges<false><<<edges_grid<false>(n), 256, 0, s>>>(A);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = read_counters(S, h, s)) != cudaSuccess) return e;
   if (h->nan_flag) {
