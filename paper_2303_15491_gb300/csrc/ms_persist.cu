@@ -213,8 +213,8 @@ __device__ __forceinline__ void block_insert(BlockTable &T, const ScanArgs &A, u
 // Step 1 over every vertex v: checks its label (in range and an extremum's
 // own label), lists v if it is an extremum, and for each of its forward
 // stencil neighbours w in another basin records the basin pair with the
-// entry key of the later of v, w.  Lanes of a warp holding the same pair
-// reduce their keys first and insert once into the block's table.
+// entry key of the later of v, w.  A lane merges its own crossings of one
+// pair first and inserts each pair once into the block's table.
 template <bool kFlat>
 __global__ void __launch_bounds__(256) k_basin_edges(ScanArgs A) {
   __shared__ BlockTable T;
@@ -287,26 +287,42 @@ __global__ void __launch_bounds__(256) k_basin_edges(ScanArgs A) {
         if (lw[j] != lv)
           bw[j] = load_bits(A.field, A.dtype, v + kOx[j] + kOy[j] * A.nx + (kFlat ? 0u : kOz[j] * A.nxy));
       }
+      // the lane's basin pairs, one entry a pair with its earliest entry
+      unsigned long long key[kNb], when[kNb];
+      uint32_t pending = 0;
 #pragma unroll
       for (int j = 0; j < kNb; ++j) {
-        unsigned long long key = kEmptyKey, when = kEmptyKey;
+        key[j] = kEmptyKey;
+        when[j] = kEmptyKey;
         if (lw[j] != lv) {
           const uint32_t w = v + kOx[j] + kOy[j] * A.nx + (kFlat ? 0u : kOz[j] * A.nxy);
           const unsigned long long kw = entry_key(bw[j], w, A.maxima);
-          when = kv > kw ? kv : kw;
           const uint32_t lo = min((uint32_t)lv, (uint32_t)lw[j]), hi = max((uint32_t)lv, (uint32_t)lw[j]);
-          key = ((unsigned long long)lo << 32) | hi;  // lo != hi, so never the empty key
+          key[j] = ((unsigned long long)lo << 32) | hi;  // lo != hi, so never the empty key
+          when[j] = kv > kw ? kv : kw;
+          bool seen = false;
+#pragma unroll
+          for (int i = 0; i < j; ++i) {
+            if (!seen && key[i] == key[j]) {
+              when[i] = min(when[i], when[j]);
+              seen = true;
+            }
+          }
+          if (!seen) pending |= 1u << j;
         }
-        if (!__any_sync(kFull, key != kEmptyKey)) continue;  // no lane of the warp on a basin boundary
-        const uint32_t peers = __match_any_sync(kFull, key);
-        if (key != kEmptyKey) {
-          // 64-bit minimum over the lanes of the group: high words, then the
-          // low words of the lanes that hold the high minimum
-          const uint32_t hi = (uint32_t)(when >> 32);
-          const uint32_t hmin = __reduce_min_sync(peers, hi);
-          const uint32_t lmin = __reduce_min_sync(peers, hi == hmin ? (uint32_t)when : kFull);
-          if ((int)lane == __ffs(peers) - 1) block_insert(T, A, key, ((unsigned long long)hmin << 32) | lmin);
+      }
+      while (pending) {
+        const int j = __ffs(pending) - 1;
+        pending &= pending - 1u;
+        unsigned long long k = key[0], t = when[0];
+#pragma unroll
+        for (int i = 1; i < kNb; ++i) {
+          if (j == i) {
+            k = key[i];
+            t = when[i];
+          }
         }
+        block_insert(T, A, k, t);
       }
     }
     // the chunk's pairs to the global table; the block's table empties
