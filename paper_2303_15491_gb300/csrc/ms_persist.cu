@@ -195,9 +195,17 @@ struct BlockTable {
   unsigned long long keys[kBlockSlots], vals[kBlockSlots];
 };
 
-__device__ __forceinline__ void block_insert(BlockTable &T, const ScanArgs &A, unsigned long long key,
+// Slot of basin pair (lo, hi) in the block's table: multiplicative hashing
+// (Knuth, TAOCP vol. 3, Sec. 6.4) of both halves, the top bits kept.
+__device__ __forceinline__ uint32_t block_slot(uint32_t lo, uint32_t hi) {
+  static_assert((kBlockSlots & (kBlockSlots - 1u)) == 0 && kBlockSlots >= 2, "a power of two");
+  return (lo * 0x9e3779b1u ^ hi * 0x85ebca77u) >> (32 - __builtin_ctz(kBlockSlots));
+}
+
+__device__ __forceinline__ void block_insert(BlockTable &T, const ScanArgs &A, uint32_t lo, uint32_t hi,
                                              unsigned long long when) {
-  uint32_t slot = (uint32_t)hash_mix64(key) & (kBlockSlots - 1u);
+  const unsigned long long key = ((unsigned long long)lo << 32) | hi;  // lo != hi: never the empty key
+  uint32_t slot = block_slot(lo, hi);
   for (uint32_t probe = 0; probe < kBlockSlots; ++probe) {
     unsigned long long cur = *(volatile unsigned long long *)&T.keys[slot];
     if (cur == kEmptyKey) cur = atomicCAS(&T.keys[slot], kEmptyKey, key);
@@ -213,8 +221,9 @@ __device__ __forceinline__ void block_insert(BlockTable &T, const ScanArgs &A, u
 // Step 1 over every vertex v: checks its label (in range and an extremum's
 // own label), lists v if it is an extremum, and for each of its forward
 // stencil neighbours w in another basin records the basin pair with the
-// entry key of the later of v, w.  A lane merges its own crossings of one
-// pair first and inserts each pair once into the block's table.
+// entry key of the later of v, w, in the block's table.  (Merging a lane's
+// or a warp's crossings of one pair first costs more instructions than the
+// shared-memory inserts it saves.)
 template <bool kFlat>
 __global__ void __launch_bounds__(256) k_basin_edges(ScanArgs A) {
   __shared__ BlockTable T;
@@ -273,12 +282,13 @@ __global__ void __launch_bounds__(256) k_basin_edges(ScanArgs A) {
       }
       // every neighbour's label first, then the values of those across a
       // boundary: the loads of a vertex are in flight together
+      const bool hx = x + 1u < A.nx, hy = y + 1u < A.ny, hz = !kFlat && z + 1u < A.nz;
       int32_t lw[kNb];
       uint32_t bw[kNb];
 #pragma unroll
       for (int j = 0; j < kNb; ++j) {
         lw[j] = lv;
-        if (lv >= 0 && x + kOx[j] < A.nx && y + kOy[j] < A.ny && (kFlat || z + kOz[j] < A.nz))
+        if (lv >= 0 && (!kOx[j] || hx) && (!kOy[j] || hy) && (!kOz[j] || hz))
           lw[j] = __ldg(&A.labels[v + kOx[j] + kOy[j] * A.nx + (kFlat ? 0u : kOz[j] * A.nxy)]);
       }
 #pragma unroll
@@ -287,42 +297,14 @@ __global__ void __launch_bounds__(256) k_basin_edges(ScanArgs A) {
         if (lw[j] != lv)
           bw[j] = load_bits(A.field, A.dtype, v + kOx[j] + kOy[j] * A.nx + (kFlat ? 0u : kOz[j] * A.nxy));
       }
-      // the lane's basin pairs, one entry a pair with its earliest entry
-      unsigned long long key[kNb], when[kNb];
-      uint32_t pending = 0;
 #pragma unroll
       for (int j = 0; j < kNb; ++j) {
-        key[j] = kEmptyKey;
-        when[j] = kEmptyKey;
         if (lw[j] != lv) {
-          const uint32_t w = v + kOx[j] + kOy[j] * A.nx + (kFlat ? 0u : kOz[j] * A.nxy);
-          const unsigned long long kw = entry_key(bw[j], w, A.maxima);
-          const uint32_t lo = min((uint32_t)lv, (uint32_t)lw[j]), hi = max((uint32_t)lv, (uint32_t)lw[j]);
-          key[j] = ((unsigned long long)lo << 32) | hi;  // lo != hi, so never the empty key
-          when[j] = kv > kw ? kv : kw;
-          bool seen = false;
-#pragma unroll
-          for (int i = 0; i < j; ++i) {
-            if (!seen && key[i] == key[j]) {
-              when[i] = min(when[i], when[j]);
-              seen = true;
-            }
-          }
-          if (!seen) pending |= 1u << j;
+          const unsigned long long k =
+              entry_key(bw[j], v + kOx[j] + kOy[j] * A.nx + (kFlat ? 0u : kOz[j] * A.nxy), A.maxima);
+          const uint32_t a = (uint32_t)lv, b = (uint32_t)lw[j];
+          block_insert(T, A, min(a, b), max(a, b), kv > k ? kv : k);
         }
-      }
-      while (pending) {
-        const int j = __ffs(pending) - 1;
-        pending &= pending - 1u;
-        unsigned long long k = key[0], t = when[0];
-#pragma unroll
-        for (int i = 1; i < kNb; ++i) {
-          if (j == i) {
-            k = key[i];
-            t = when[i];
-          }
-        }
-        block_insert(T, A, k, t);
       }
     }
     // the chunk's pairs to the global table; the block's table empties
