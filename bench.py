@@ -762,7 +762,7 @@ def quantised_summary(args, f_np):
 
 
 def persistence_summary(args, f_np):
-    """Persistence pairs of the 512^3 field's minima and maxima from its
+    """Persistence pairs of the workload field's minima and maxima from its
     segmentation (ms_persistence, Sec. 4.1), wall time per call (the call
     reads counts back between its steps), median of 5 after one untimed."""
     import torch
@@ -772,7 +772,7 @@ def persistence_summary(args, f_np):
     dev = torch.cuda.current_device()
     field = torch.from_numpy(np.asarray(f_np)).to(dev)
     ctx = ms.ms_create(dev, torch.cuda.Stream(device=dev))
-    out = {"workload": "noise512", "reps": 5}
+    out = {"workload": args.workload, "reps": 5}
     try:
         asc, desc, _, _ = ms.segment(ctx, field)
         dims, dt = ms.dims_of(field), ms.dtype_code(field)
@@ -838,6 +838,8 @@ def main():
                     help="batch256: time the default launch choices (no autotuning run first)")
     ap.add_argument("--resolve-mode", type=int, choices=[-1, 0, 1], default=None,
                     help="batch256 with --no-autotune: resolve by tile (0), flat (1) or by tile count (-1)")
+    ap.add_argument("--persistence-only", action="store_true",
+                    help="time only the persistence pairing of the workload's field (a profiling aid)")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-passes", type=int, default=16)
@@ -858,6 +860,16 @@ def main():
                               "reference arm; the oracle arm runs on the 512^3 workload"}))
             return 0
         return run_serve_bench(args)
+    if args.persistence_only:
+        if args.impl == "reference" or WORKLOADS[args.workload]["kind"] not in ("noise", "noiseq", "gauss", "broad"):
+            print(json.dumps({"impl": args.impl, "unavailable": "--persistence-only times the GPU pairing of "
+                              "one field workload"}))
+            return 0
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps({"persistence": persistence_summary(args, make_field(args.workload))}))
+        return 0
     if args.impl == "reference" and args.workload != "batch256":
         return run_reference(args)
     if args.workload == "batch256":
