@@ -848,6 +848,16 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.persistence_only:
+        if args.impl == "reference" or WORKLOADS[args.workload]["kind"] not in ("noise", "noiseq", "gauss", "broad"):
+            print(json.dumps({"impl": args.impl, "unavailable": "--persistence-only times the GPU pairing of "
+                              "one field workload"}))
+            return 0
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps({"persistence": persistence_summary(args, make_field(args.workload))}))
+        return 0
     if args.workload in ("index512", "index256"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the index pass has no separate "
@@ -860,16 +870,6 @@ def main():
                               "reference arm; the oracle arm runs on the 512^3 workload"}))
             return 0
         return run_serve_bench(args)
-    if args.persistence_only:
-        if args.impl == "reference" or WORKLOADS[args.workload]["kind"] not in ("noise", "noiseq", "gauss", "broad"):
-            print(json.dumps({"impl": args.impl, "unavailable": "--persistence-only times the GPU pairing of "
-                              "one field workload"}))
-            return 0
-        import torch
-
-        torch.cuda.set_device(0)
-        print(json.dumps({"persistence": persistence_summary(args, make_field(args.workload))}))
-        return 0
     if args.impl == "reference" and args.workload != "batch256":
         return run_reference(args)
     if args.workload == "batch256":
