@@ -914,7 +914,14 @@ def main():
         ms.ms_segment(ctx, field, dims, dtype, asc, desc, msid)
     k_regions = ms.ms_last_region_count(ctx)
 
-    # ---- device-resident timed region
+    # ---- device-resident timed region.  A field whose input and labels are
+    # not well above L2 gets L2 flushed before every step (a write of twice
+    # L2, outside the per-step events), and the time is the sum of the steps.
+    esz = 2 if w["dtype"] == "f16" else 4
+    io_bytes = n * esz + 3 * n * 4
+    l2_bytes = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or (129 << 20))
+    flush_buf = (torch.empty(2 * l2_bytes, dtype=torch.uint8, device=dev) if io_bytes < 4 * l2_bytes
+                 else None)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -922,15 +929,19 @@ def main():
     with ClockSampler(dev) as clk:
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
-        # events on the stream the library's kernels are launched on; one more
-        # between steps for the per-step statistics
-        step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        # events on the stream the library's kernels are launched on, around
+        # every step for the per-step statistics
+        step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
         ev0.record(stream)
         t_host = time.perf_counter()
         for i in range(args.steps):
-            step_ev[i].record(stream)
+            if flush_buf is not None:
+                with torch.cuda.stream(stream):
+                    flush_buf.fill_(i & 255)
+            step_ev[i][0].record(stream)
             ms.ms_segment(ctx, field, dims, dtype, asc, desc, msid)
-        step_ev[args.steps].record(stream)
+            step_ev[i][1].record(stream)
         ev1.record(stream)
         torch.cuda.synchronize()
         t_host = time.perf_counter() - t_host
@@ -938,12 +949,21 @@ def main():
     ms.ms_profile_enable(ctx, False)
     barrier()
     torch.cuda.synchronize()
-    elapsed_ms = max_over_ranks(max(ev0.elapsed_time(ev1), 1e3 * t_host), dist, dev)
-    ms_per_step = elapsed_ms / args.steps
-    value = whole_job_rate(n * args.steps, ws, elapsed_ms / 1e3)
     # per-step times: median, and the paper's protocol (10 runs, the best and
     # the worst dropped, the mean of the other 8) over the last 10 steps
-    per_step = [step_ev[i].elapsed_time(step_ev[i + 1]) for i in range(args.steps)]
+    per_step = [a.elapsed_time(b) for a, b in step_ev]
+    if flush_buf is None:
+        local_ms = max(ev0.elapsed_time(ev1), 1e3 * t_host)
+        l2_note = (f"inputs larger than L2 (field {n * esz / 2**20:.0f} MiB, labels 3 x {n * 4 / 2**20:.0f} MiB "
+                   f"> {l2_bytes / 2**20:.0f} MiB L2)")
+    else:
+        local_ms = sum(per_step)
+        l2_note = (f"L2 flushed before every step (a {2 * l2_bytes / 2**20:.0f} MiB write outside the step's "
+                   f"events; field and labels {io_bytes / 2**20:.1f} MiB); time = sum of the per-step events")
+        del flush_buf
+    elapsed_ms = max_over_ranks(local_ms, dist, dev)
+    ms_per_step = elapsed_ms / args.steps
+    value = whole_job_rate(n * args.steps, ws, elapsed_ms / 1e3)
     step_stats = {"median_ms": statistics.median(per_step), "min_ms": min(per_step),
                   "max_ms": max(per_step)}
     if len(per_step) >= 10:
@@ -951,7 +971,6 @@ def main():
         step_stats["paper_protocol_ms"] = sum(last[1:-1]) / 8
 
     # ---- end to end through ms_segment_host (pinned host memory)
-    esz = 2 if w["dtype"] == "f16" else 4
     e2e_value = e2e_single = None
     if args.e2e_steps > 0:
         h_field = torch.from_numpy(f_np).pin_memory()
@@ -1035,7 +1054,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "desc": w["desc"], "dims": list(dims),
                    "input_dtype": w["dtype"], "regions_K": k_regions,
-                   "l2": "inputs larger than L2 (field 512 MiB, labels 3 x 512 MiB > 129 MB L2)",
+                   "l2": l2_note,
                    "parallelism": f"replicas x{ws} (no data-path collective)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
                      "peak_kind": peak_kind, "unit": "GB/s",
