@@ -224,7 +224,7 @@ __device__ __forceinline__ void block_insert(BlockTable &T, const ScanArgs &A, u
 // entry key of the later of v, w, in the block's table.  (Merging a lane's
 // or a warp's crossings of one pair first costs more instructions than the
 // shared-memory inserts it saves.)
-template <bool kFlat>
+template <bool kFlat, bool kHalf>
 __global__ void __launch_bounds__(256) k_basin_edges(ScanArgs A) {
   __shared__ BlockTable T;
   // forward half of the Freudenthal stencil (the other half is its negation)
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(256) k_basin_edges(ScanArgs A) {
         } else if (__ldg(&A.labels[lv]) != lv) {
           bad = true;
         }
-        const uint32_t bits = load_bits(A.field, A.dtype, v);
+        const uint32_t bits = load_bits(A.field, kHalf ? MS_F16 : MS_F32, v);
         nan |= is_nan_bits(bits);
         kv = entry_key(bits, v, A.maxima);
         uint32_t q;
@@ -295,7 +295,8 @@ __global__ void __launch_bounds__(256) k_basin_edges(ScanArgs A) {
       for (int j = 0; j < kNb; ++j) {
         bw[j] = 0;
         if (lw[j] != lv)
-          bw[j] = load_bits(A.field, A.dtype, v + kOx[j] + kOy[j] * A.nx + (kFlat ? 0u : kOz[j] * A.nxy));
+          bw[j] = load_bits(A.field, kHalf ? MS_F16 : MS_F32,
+                            v + kOx[j] + kOy[j] * A.nx + (kFlat ? 0u : kOz[j] * A.nxy));
       }
 #pragma unroll
       for (int j = 0; j < kNb; ++j) {
@@ -520,10 +521,10 @@ unsigned int grid_for(uint64_t n, int per_sm = 8) {
 }
 
 // One resident wave of the basin-edge scan (a block takes chunks in turn).
-template <bool kFlat>
+template <bool kFlat, bool kHalf>
 unsigned int edges_grid(uint64_t n) {
   static int per_sm = 0;
-  if (!per_sm && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_basin_edges<kFlat>, 256, 0) !=
+  if (!per_sm && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_basin_edges<kFlat, kHalf>, 256, 0) !=
                       cudaSuccess ||
                   per_sm < 1))
     per_sm = 1;
@@ -582,10 +583,15 @@ cudaError_t persist_run(const PersistCall &P, void *scratch, void *host_counters
   A.maxima = maxima;
   A.S = S;
   ++tl_launches;
-  if (A.nz == 1)
-    k_basin_edges<true><<<edges_grid<true>(n), 256, 0, s>>>(A);
+  const bool half = A.dtype == MS_F16;
+  if (A.nz == 1 && half)
+    k_basin_edges<true, true><<<edges_grid<true, true>(n), 256, 0, s>>>(A);
+  else if (A.nz == 1)
+    k_basin_edges<true, false><<<edges_grid<true, false>(n), 256, 0, s>>>(A);
+  else if (half)
+    k_basin_edges<false, true><<<edges_grid<false, true>(n), 256, 0, s>>>(A);
   else
-    k_basin_edges<false><<<edges_grid<false>(n), 256, 0, s>>>(A);
+    k_basin_edges<false, false><<<edges_grid<false, false>(n), 256, 0, s>>>(A);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = read_counters(S, h, s)) != cudaSuccess) return e;
   if (h->nan_flag) {
