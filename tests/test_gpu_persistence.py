@@ -107,9 +107,10 @@ def test_white_noise(ctx, shape):
     assert infos[0]["rounds"] >= 3
 
 
-def test_float16_field(ctx):
-    f = sf.smoothed_noise((48, 40, 36), 2, sigma=2.0).astype(np.float16)
-    check(ctx, f, "fp16")
+@pytest.mark.parametrize("dims", [(48, 40, 36), (120, 90, 1)])
+def test_float16_field(ctx, dims):
+    f = sf.smoothed_noise(dims, 2, sigma=2.0).astype(np.float16)
+    check(ctx, f, f"fp16 {dims}")
 
 
 def test_oracle_labels_give_the_same_pairs(ctx):
