@@ -28,7 +28,7 @@ _lib = None
 
 _DT = {np.dtype(np.float32): 0, np.dtype(np.float16): 1, np.dtype(np.float64): 2}
 _ERR = {1: "NaN in the input field", 2: "invalid argument", 3: "out of memory",
-        4: "pointer cycle (not a forest)"}
+        4: "pointer cycle (not a forest)", 5: "simplification regions neither nested nor disjoint"}
 
 i32p = ctypes.POINTER(ctypes.c_int32)
 i64p = ctypes.POINTER(ctypes.c_int64)
@@ -52,6 +52,9 @@ def lib():
             L.ms_oracle_persistence.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, ctypes.c_int,
                                                 i32p, i32p, ctypes.POINTER(ctypes.c_int64)]
             L.ms_oracle_persistence.restype = ctypes.c_int
+            L.ms_oracle_simplify.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, ctypes.c_double, ctypes.c_int,
+                                             i64p, ctypes.POINTER(ctypes.c_double), i64p]
+            L.ms_oracle_simplify.restype = ctypes.c_int
             L.ms_oracle_neighbors.argtypes = [i64p, ctypes.c_int64, i64p]
             L.ms_oracle_neighbors.restype = ctypes.c_int
             L.ms_oracle_steepest.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, i32p, i32p]
@@ -278,3 +281,24 @@ def persistence(field: np.ndarray, direction: int = -1):
     _check(lib().ms_oracle_persistence(f.ctypes.data, dt, dims, int(direction), _ptr32(ext),
                                        _ptr32(dth), ctypes.byref(k)))
     return {"extremum": ext[:k.value].copy(), "death": dth[:k.value].copy()}
+
+
+def simplify(field: np.ndarray, threshold: float, which: int = 3):
+    """The field's order after removing the extrema whose persistence is below
+    ``threshold`` (which: 1 minima, 2 maxima, 3 both, minima first): a dict
+    with ``rank`` (int64, each vertex's position in the simplified order,
+    ascending, shaped like the field), ``value`` (float64, the value each
+    vertex carries), ``removed_minima`` and ``removed_maxima``.  ``rank`` as a
+    float64 field is the simplified field to segment (its values are distinct,
+    so the (value, index) order is the rank order)."""
+    f, dt, dims = _prep(field)
+    n = f.size
+    rank = np.empty(n, np.int64)
+    value = np.empty(n, np.float64)
+    removed = np.zeros(3, np.int64)
+    _check(lib().ms_oracle_simplify(f.ctypes.data, dt, dims, float(threshold), int(which),
+                                    rank.ctypes.data_as(i64p),
+                                    value.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    removed.ctypes.data_as(i64p)))
+    return {"rank": rank.reshape(f.shape), "value": value.reshape(f.shape),
+            "removed_minima": int(removed[0]), "removed_maxima": int(removed[1]), "rounds": int(removed[2])}

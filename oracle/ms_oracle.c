@@ -41,6 +41,10 @@
  *               (thresholds): the 0-dimensional persistence pairs of the
  *               extrema -- sublevel-set components for minima, superlevel-set
  *               components for maxima, the elder rule at every merge.
+ *   simplify    Sec. 4.1 + Sec. 6 again: the order after removing the
+ *               extrema whose persistence is below a threshold, in the
+ *               reading stated at ms_oracle_simplify (the paper names the
+ *               operation and its thresholds, not its procedure).
  *
  * Vertex numbering: v = x + nx*(y + ny*z), x fastest (Fig. 1 numbers the
  * nodes of its grid along x first).
@@ -1006,5 +1010,223 @@ int ms_oracle_persistence(const void *field, int dtype, const int64_t dims[3], i
   free(parent);
   free(eldest);
   free(dies);
+  return OR_OK;
+}
+
+/* ---- simplification of the order ----------------------------------------
+ * Sec. 4.1 simplifies the field before segmenting it, removing the extrema
+ * whose persistence lies below a threshold (Sec. 6 quotes the thresholds);
+ * the paper does not spell out the procedure.  This follows the reading
+ * written down for it, one pass per extremum type (minima on sublevel sets,
+ * then maxima on superlevel sets, each on the order the previous pass left):
+ *   1. the pairs of the pass by the elder rule on the current order (as in
+ *      ms_oracle_persistence);
+ *   2. an extremum m paired with d is removed when |value(d) - value(m)| is
+ *      below the threshold; its region R(m) is m's component among the
+ *      vertices that enter before d;
+ *   3. regions are nested or disjoint; each vertex takes the outermost
+ *      removed region that contains it.  The vertices of a region take d's
+ *      value and enter right after d, before any vertex that entered after d,
+ *      in order of their breadth-first distance from d inside the region and
+ *      then of their vertex index.
+ * A minima pass leaves exactly the minima of persistence >= threshold, but
+ * the maxima pass after it can leave new minima: a flattened maximum region
+ * that reaches the box boundary can hold a vertex with no lower neighbour
+ * (the one farthest from d), of persistence 0.  So with both kinds the passes
+ * alternate until a maxima pass removes nothing (on random fields: two rounds,
+ * at most three); the order then has no extremum of either kind below the
+ * threshold.  A vertex region that d does not reach, or two regions that
+ * overlap without nesting, would contradict the reading: OR_ERR_REGIONS.
+ * rank[v]: the position of v in the simplified order, ascending (0 .. n-1);
+ * value[v]: the value it carries; removed[0], removed[1]: the minima and the
+ * maxima removed, removed[2]: the rounds run.  which: 1 one minima pass, 2 one
+ * maxima pass, 3 both kinds, alternating (minima first). */
+enum { OR_ERR_REGIONS = 5 };
+static const int64_t kSimplifyRounds = 256;
+
+typedef struct {
+  int64_t k0, k1, k2;
+} skey_t;
+
+static int cmp_skey(const void *a, const void *b) {
+  const skey_t *x = (const skey_t *)a, *y = (const skey_t *)b;
+  if (x->k0 != y->k0) return x->k0 < y->k0 ? -1 : 1;
+  if (x->k1 != y->k1) return x->k1 < y->k1 ? -1 : 1;
+  return x->k2 < y->k2 ? -1 : (x->k2 > y->k2);
+}
+
+/* entry step of v in a pass: ascending rank for minima, descending for maxima */
+static int64_t entry_of(const int64_t *rank, int64_t n, int dir, int64_t v) {
+  return dir < 0 ? rank[v] : n - 1 - rank[v];
+}
+
+static int simplify_pass(const field_t *F, int64_t *rank, double *val, int dir, double threshold,
+                         int64_t *removed) {
+  const int64_t n = F->n;
+  int64_t *byent = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t *eldest = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t *death = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t *owner = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t *dist = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  skey_t *keys = (skey_t *)malloc(sizeof(skey_t) * (size_t)n);
+  int st = OR_OK;
+  if (!byent || !parent || !eldest || !death || !owner || !dist || !queue || !keys) {
+    st = OR_ERR_NOMEM;
+    goto done;
+  }
+  for (int64_t v = 0; v < n; ++v) {
+    byent[entry_of(rank, n, dir, v)] = v;
+    parent[v] = -1; /* not entered yet */
+    death[v] = -2;  /* not an extremum */
+    owner[v] = -1;
+    dist[v] = -1;
+  }
+  /* 1. elder rule over the entry order */
+  for (int64_t s = 0; s < n; ++s) {
+    const int64_t v = byent[s];
+    int64_t nb[14], roots[14];
+    const int c = neighbours_of(F, v, nb);
+    int nr = 0;
+    for (int i = 0; i < c; ++i) {
+      if (parent[nb[i]] < 0) continue;
+      const int64_t r = uf_root(parent, nb[i]);
+      int seen = 0;
+      for (int j = 0; j < nr; ++j) seen |= roots[j] == r;
+      if (!seen) roots[nr++] = r;
+    }
+    if (nr == 0) {
+      parent[v] = v;
+      eldest[v] = v;
+      death[v] = -1;
+      continue;
+    }
+    int keep = 0;
+    for (int j = 1; j < nr; ++j)
+      if (entry_of(rank, n, dir, eldest[roots[j]]) < entry_of(rank, n, dir, eldest[roots[keep]])) keep = j;
+    for (int j = 0; j < nr; ++j) {
+      if (j == keep) continue;
+      death[eldest[roots[j]]] = v;
+      parent[roots[j]] = roots[keep];
+    }
+    parent[v] = roots[keep];
+  }
+  /* 2. the removed extrema, latest death first (outer regions before the
+   * regions nested in them); keys[] holds (-entry(d), m) for the sort */
+  int64_t nrm = 0;
+  for (int64_t m = 0; m < n; ++m) {
+    const int64_t d = death[m];
+    if (d < 0 || !(fabs(val[d] - val[m]) < threshold)) continue;
+    keys[nrm].k0 = -entry_of(rank, n, dir, d);
+    keys[nrm].k1 = m;
+    keys[nrm].k2 = 0;
+    ++nrm;
+  }
+  qsort(keys, (size_t)nrm, sizeof(skey_t), cmp_skey);
+  *removed = nrm;
+  /* 3. regions: claimed outermost first, then breadth-first distances from d */
+  for (int64_t i = 0; i < nrm; ++i) {
+    const int64_t m = keys[i].k1, d = death[m], sd = entry_of(rank, n, dir, d);
+    if (owner[m] >= 0) continue; /* inside a region claimed already */
+    int64_t head = 0, tail = 0;
+    owner[m] = m;
+    queue[tail++] = m;
+    while (head < tail) {
+      const int64_t x = queue[head++];
+      int64_t nb[14];
+      const int c = neighbours_of(F, x, nb);
+      for (int j = 0; j < c; ++j) {
+        const int64_t w = nb[j];
+        if (entry_of(rank, n, dir, w) >= sd || owner[w] == m) continue;
+        if (owner[w] >= 0) { /* regions that overlap without nesting */
+          st = OR_ERR_REGIONS;
+          goto done;
+        }
+        owner[w] = m;
+        queue[tail++] = w;
+      }
+    }
+    const int64_t size = tail;
+    head = tail = 0;
+    dist[d] = 0;
+    queue[tail++] = d;
+    while (head < tail) {
+      const int64_t x = queue[head++];
+      int64_t nb[14];
+      const int c = neighbours_of(F, x, nb);
+      for (int j = 0; j < c; ++j) {
+        const int64_t w = nb[j];
+        if (owner[w] != m || dist[w] >= 0) continue;
+        dist[w] = dist[x] + 1;
+        queue[tail++] = w;
+      }
+    }
+    dist[d] = -1;
+    if (tail - 1 != size) { /* a region that d does not reach */
+      st = OR_ERR_REGIONS;
+      goto done;
+    }
+  }
+  /* the new entry order */
+  for (int64_t v = 0; v < n; ++v) {
+    if (owner[v] >= 0) {
+      const int64_t d = death[owner[v]];
+      keys[v].k0 = entry_of(rank, n, dir, d);
+      keys[v].k1 = dist[v];
+    } else {
+      keys[v].k0 = entry_of(rank, n, dir, v);
+      keys[v].k1 = 0;
+    }
+    keys[v].k2 = v;
+  }
+  qsort(keys, (size_t)n, sizeof(skey_t), cmp_skey);
+  for (int64_t v = 0; v < n; ++v)
+    if (owner[v] >= 0) val[v] = val[death[owner[v]]];
+  for (int64_t s = 0; s < n; ++s) rank[keys[s].k2] = dir < 0 ? s : n - 1 - s;
+done:
+  free(byent);
+  free(parent);
+  free(eldest);
+  free(death);
+  free(owner);
+  free(dist);
+  free(queue);
+  free(keys);
+  return st;
+}
+
+int ms_oracle_simplify(const void *field, int dtype, const int64_t dims[3], double threshold, int which,
+                       int64_t *rank, double *value, int64_t *removed) {
+  field_t F;
+  int st = make_field(&F, field, dtype, dims);
+  if (st != OR_OK) return st;
+  if (which < 1 || which > 3 || !rank || !value || !removed || threshold != threshold) return OR_ERR_ARG;
+  if (has_nan(&F)) return OR_ERR_NAN;
+  const int64_t n = F.n;
+  ordered_t *ord = (ordered_t *)malloc(sizeof(ordered_t) * (size_t)n);
+  if (!ord) return OR_ERR_NOMEM;
+  for (int64_t v = 0; v < n; ++v) {
+    ord[v].value = value_at(&F, v);
+    ord[v].index = v;
+    value[v] = ord[v].value;
+  }
+  qsort(ord, (size_t)n, sizeof(ordered_t), cmp_ordered);
+  for (int64_t s = 0; s < n; ++s) rank[ord[s].index] = s;
+  free(ord);
+  removed[0] = removed[1] = removed[2] = 0;
+  for (int64_t round = 0;; ++round) {
+    if (round == kSimplifyRounds) return OR_ERR_CYCLE;
+    int64_t rm[2] = {0, 0};
+    if (which & 1) st = simplify_pass(&F, rank, value, -1, threshold, &rm[0]);
+    if (st == OR_OK && (which & 2)) st = simplify_pass(&F, rank, value, 1, threshold, &rm[1]);
+    if (st != OR_OK) return st;
+    removed[0] += rm[0];
+    removed[1] += rm[1];
+    removed[2] = round + 1;
+    /* a minima pass leaves only minima of persistence >= threshold; when the
+     * maxima pass after it removes nothing, neither kind is left below it */
+    if (which != 3 || rm[1] == 0) break;
+  }
   return OR_OK;
 }
