@@ -46,6 +46,28 @@ def test_chain_worked_by_hand():
     assert (r["removed_minima"], r["removed_maxima"]) == (3, 0)
 
 
+def test_nested_regions_worked_by_hand():
+    # values 0, 6, 2, 4, 3, 5, 1, 7.  Sublevel entry: v0 v6 v2 v4 v3 v5 v1 v7.
+    # v3 joins {v2} and {v4}: v4 dies at v3 (persistence 1); v5 joins {v2 v3 v4}
+    # and {v6}: v2 dies at v5 (3, v6 is older); v1 joins {v0} and the rest: v6
+    # dies at v1 (5).  Threshold 3.5 removes v4 and v2; R(v4) = {v4} lies inside
+    # R(v2) = {v2 v3 v4} (v2's component before v5 enters), so the outer region
+    # decides: v2, v3, v4 take value 5 and enter right after v5 by distance
+    # from it: v4 (1), v3 (2), v2 (3).  Order: v0 v6 v5 v4 v3 v2 v1 v7.  The
+    # maxima pass on it pairs v1 with v6 (persistence 5): nothing removed.
+    f = np.array([[0, 6, 2, 4, 3, 5, 1, 7]], np.float32)
+    r = oracle.simplify(f, 3.5)
+    assert r["rank"].ravel().tolist() == [0, 6, 5, 4, 3, 2, 1, 7]
+    assert r["value"].ravel().tolist() == [0, 6, 5, 5, 5, 5, 1, 7]
+    assert (r["removed_minima"], r["removed_maxima"], r["rounds"]) == (2, 0, 1)
+
+
+def test_single_vertex():
+    r = oracle.simplify(np.array([[4.0]], np.float32), 1.0)
+    assert r["rank"].tolist() == [[0]] and r["value"].tolist() == [[4.0]]
+    assert (r["removed_minima"], r["removed_maxima"]) == (0, 0)
+
+
 def test_maxima_flattened_below_their_death():
     # 5 0 5: maxima v0, v2 (v2 is higher: equal values, higher index); v0 dies
     # at v1 with persistence 5.  Above 5 it is removed: it takes value 0 and
